@@ -1,0 +1,251 @@
+/* mdsolve: GB300 solver for mixed-dimensional scalar elliptic problems.
+ *
+ * C ABI of the CUDA library libmdsolve.so.  It implements the block-
+ * factorisation preconditioner of Hu, Keilegavlen and Nordbotten,
+ * "Effective preconditioners for mixed-dimensional scalar elliptic problems"
+ * (arXiv:2206.03203) on one GPU:
+ *   - the 2x2 block system  [A_mm A_mf; A_fm A_ff] [p_m; p_f] = [f_m; f_f]
+ *     (Sec. 3.1, Eq. (4)), here with matrix-cell pressures m and fracture-cell
+ *     pressures f from a cell-centred two-point-flux discretisation of the
+ *     model of Sec. 2.1 (Eq. (1)-(3));
+ *   - the approximate Schur complement S~ = A_mm - A_mf diag(A_ff)^-1 A_fm
+ *     (Sec. 3.2, Eq. (7));
+ *   - the inexact block lower-triangular preconditioner M_L (Sec. 3.2,
+ *     Eq. (8)) applied by Algorithm 1 (Sec. 3.3), each diagonal block
+ *     approximately inverted by one aggregation-AMG V-cycle (Sec. 3.3);
+ *   - right-preconditioned flexible GMRES with zero initial guess and a
+ *     relative-residual stopping rule (Sec. 3.2 and Sec. 4), or PCG with the
+ *     block-diagonal preconditioner B_D (Sec. 3.2).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns an int status: MDS_OK (0), a warning (> 0) or an
+ *     error (< 0).  mds_error_string() names a status; mds_last_error()
+ *     returns the context's last detailed message.  No call aborts or traps.
+ *   - Handles are owned by the library and freed by their _destroy call.
+ *     Host arrays passed in are copied before the call returns.  Device
+ *     pointers passed in stay owned by the caller and must stay valid for
+ *     the duration stated at each call.
+ *   - All GPU work is enqueued on the context's CUDA stream.  Calls that
+ *     return sizes or statistics synchronise that stream.
+ *   - A context is not thread-safe; use one context per host thread.
+ *   - Sparse matrices are CSR with int32 row pointers and column indices
+ *     (columns ascending within a row) and FP64 values; vectors are FP64.
+ */
+#ifndef MDSOLVE_H
+#define MDSOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define MDS_OK 0
+#define MDS_WARN_NOT_CONVERGED 1   /* some right-hand side hit max_iters */
+#define MDS_ERR_INVALID (-1)       /* bad argument, size or handle */
+#define MDS_ERR_CUDA (-2)          /* a CUDA runtime call failed */
+#define MDS_ERR_OOM (-3)           /* device allocation failed */
+#define MDS_ERR_NOT_SPD (-4)       /* coarsest Cholesky met a pivot <= 0 */
+#define MDS_ERR_BREAKDOWN (-5)     /* Krylov breakdown (non-finite or zero norm) */
+#define MDS_ERR_NONFINITE (-6)     /* NaN/Inf in the right-hand side or residual */
+#define MDS_ERR_CAPACITY (-7)      /* a sparse row exceeded a kernel's row capacity */
+#define MDS_ERR_TIMEOUT (-8)       /* an iterative setup loop exceeded its bound */
+#define MDS_ERR_ZERO_DIAG (-9)     /* zero diagonal in A_ff (Eq. (7) undefined) */
+
+typedef struct mds_ctx_s *mds_ctx;
+typedef struct mds_system_s *mds_system;
+typedef struct mds_precond_s *mds_precond;
+
+/* Optional device allocator (for example a framework's caching allocator).
+ * alloc returns a device pointer of at least `bytes` bytes aligned to 256
+ * bytes or NULL on failure; free releases it.  Both are called on the host
+ * thread that calls into the library, with the context's stream current
+ * for stream-ordered allocators. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *user);
+    void (*free)(void *ptr, void *user);
+    void *user;
+} mds_allocator;
+
+/* Create a context on CUDA device `device` that enqueues on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  `alloc` may be NULL
+ * for stream-ordered cudaMallocAsync/cudaFreeAsync.  The allocator struct is
+ * copied; its callbacks must stay valid for the context's lifetime. */
+int mds_create(mds_ctx *out, int device, void *cuda_stream, const mds_allocator *alloc);
+int mds_destroy(mds_ctx ctx);
+/* Change the stream later calls enqueue on. */
+int mds_set_stream(mds_ctx ctx, void *cuda_stream);
+const char *mds_error_string(int status);
+/* Detailed message of the last failing call on this context (static storage
+ * owned by the context, valid until its next call). */
+const char *mds_last_error(mds_ctx ctx);
+
+/* ---- problem input ----
+ * A Cartesian instance on the unit square (dim 2) or cube (dim 3) with n
+ * cells per side (h = 1/n), matrix cells indexed x-fastest.  Fracture cells
+ * are interior grid faces (codimension-1 subdomains, Sec. 2.1) given by their
+ * normal axis and position (x, y, z): the coordinate along the normal axis is
+ * the face-plane index 1..n-1, the others are cell indices.  Each has a
+ * tangential permeability k_f and an aperture a.  Dirichlet data lives on the
+ * x = 0 (pD_left) and x = 1 (pD_right) faces, one value per boundary face
+ * (index y + n z) and right-hand side; other boundary faces are no-flow.
+ * Transmissibilities (two-point flux, Eq. (1)-(3)):
+ *   matrix-matrix      |F| / (h/(2 k_i) + h/(2 k_j))
+ *   matrix-fracture    |F| / (h/(2 k_i) + 1/kappa),  kappa = 2 k_f / a
+ *   fracture-fracture  t_i t_j / (t_i + t_j) for every pair of fracture cells
+ *                      meeting at a vertex (2D) / edge (3D) e,
+ *                      t = k_f a |e| / (h/2)
+ *   Dirichlet          matrix |F| 2 k / h; fracture end on x = 0/1: t, with
+ *                      the mean of the two boundary faces at that end.
+ * `on_device` = 1 means every array pointer below is a device pointer that
+ * must stay valid until mds_assemble returns; 0 means host arrays. */
+typedef struct {
+    int dim;
+    int n;
+    const double *km;        /* [n^dim] */
+    int64_t n_f;
+    const int32_t *fc_axis;  /* [n_f]   normal axis 0..dim-1 */
+    const int32_t *fc_pos;   /* [3 n_f] (x, y, z) per fracture cell */
+    const double *fc_kf;     /* [n_f] */
+    const double *fc_a;      /* [n_f] */
+    int nrhs;                /* >= 1 */
+    const double *pD_left;   /* [nrhs n^(dim-1)] */
+    const double *pD_right;  /* [nrhs n^(dim-1)] */
+    int on_device;
+} mds_instance;
+
+/* Device CSR view.  row_ptr [nrow+1], col/val [nnz]. */
+typedef struct {
+    int64_t nrow, ncol, nnz;
+    int32_t *row_ptr;
+    int32_t *col;
+    double *val;
+} mds_csr;
+
+/* Assemble the block system of one instance on the GPU (Eq. (4)): the four
+ * blocks, the full matrix and the nrhs right-hand sides b (column r at
+ * b + r (n_m + n_f)).  Fails with MDS_ERR_INVALID on a fracture cell outside
+ * the interior faces or two fracture cells on one face. */
+int mds_assemble(mds_ctx ctx, const mds_instance *inst, mds_system *out);
+
+/* Wrap caller CSR blocks (device, borrowed until mds_system_destroy) and an
+ * optional device right-hand side b [n_m + n_f] (NULL: zero).  The library
+ * builds its own merged copy of the full matrix. */
+int mds_system_from_csr(mds_ctx ctx, const mds_csr *Amm, const mds_csr *Amf,
+                        const mds_csr *Afm, const mds_csr *Aff, const double *b,
+                        mds_system *out);
+int mds_system_destroy(mds_system sys);
+/* Sizes: n_m, n_f, nrhs and nnz of (A_mm, A_mf, A_fm, A_ff, full). */
+int mds_system_info(mds_system sys, int64_t *n_m, int64_t *n_f, int *nrhs, int64_t nnz[5]);
+/* Borrowed device views of the blocks (index 0..3 = mm, mf, fm, ff), the full
+ * matrix (index 4) and the right-hand sides; valid until the system is
+ * destroyed. */
+int mds_system_view(mds_system sys, mds_csr blocks[5], const double **b);
+
+/* ---- preconditioner set-up ---- */
+#define MDS_SMOOTHER_L1JACOBI 0
+#define MDS_SMOOTHER_CHEBYSHEV 1
+#define MDS_PREC_FP64 64        /* V-cycles stored and applied in FP64 */
+#define MDS_PREC_FP32 32        /* FP32 values and vectors */
+#define MDS_PREC_MIXED16 16     /* FP32 fine levels, BF16 row-scaled from lowp_from_level */
+#define MDS_BLOCK_LOWER 0       /* M_L, Eq. (8), Algorithm 1 */
+#define MDS_BLOCK_DIAG 1        /* block diagonal B_D with Q blocks */
+#define MDS_BLOCK_UPPER 2       /* block upper triangular B_U with Q blocks */
+
+typedef struct {
+    double theta;            /* strength threshold (0.08) */
+    int64_t n_coarse;        /* dense Cholesky once a level has <= n_coarse rows (512) */
+    int max_levels;          /* (25) */
+    double stall_ratio;      /* stop coarsening when n_{l+1} > stall_ratio n_l (0.9) */
+    uint64_t seed;           /* MIS-2 hash seed */
+    int smoother;            /* MDS_SMOOTHER_* */
+    int precision;           /* MDS_PREC_* */
+    int lowp_from_level;     /* first BF16 level for MDS_PREC_MIXED16 (1) */
+    int kind;                /* MDS_BLOCK_* */
+} mds_setup_opts;
+
+/* Fill `o` with the defaults listed above. */
+int mds_setup_opts_default(mds_setup_opts *o);
+
+/* Build S~ (Eq. (7)) and one aggregation-AMG hierarchy for each of S~ and
+ * A_ff: strength graph, MIS-2 with SplitMix64 priorities, aggregates,
+ * piecewise-constant P, Galerkin P^T A P, L1 diagonals, coarsest dense
+ * Cholesky.  The system must outlive the preconditioner. */
+int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_precond *out);
+int mds_precond_destroy(mds_precond prec);
+/* Hierarchy of block 0 (S~) or 1 (A_ff): number of levels, and per level the
+ * rows and nonzeros (arrays of length >= 32).  *dense = 1 when the last level
+ * is solved by dense Cholesky, 0 when it is smoothed only. */
+int mds_precond_info(mds_precond prec, int block, int *nlevels, int64_t *level_n,
+                     int64_t *level_nnz, int *dense);
+/* Borrowed device views of level `level` of a block: its FP64 matrix, the
+ * aggregate map to the next level (int32 [n], -1 = not aggregated; NULL on
+ * the last level) and the MIS-2 root flags (int8 [n]). */
+int mds_precond_level(mds_precond prec, int block, int level, mds_csr *A,
+                      const int32_t **agg, const int8_t **roots);
+/* z = M r for device FP64 vectors of length n_m + n_f. */
+int mds_precond_apply(mds_ctx ctx, mds_precond prec, const double *r, double *z);
+/* x = V(b): one V-cycle of block 0 or 1 on device FP64 vectors. */
+int mds_vcycle(mds_ctx ctx, mds_precond prec, int block, const double *b, double *x);
+/* y = A x with the full system matrix (device FP64 vectors). */
+int mds_spmv(mds_ctx ctx, mds_system sys, const double *x, double *y);
+
+/* ---- solve ---- */
+#define MDS_KRYLOV_FGMRES 0
+#define MDS_KRYLOV_PCG 1
+
+typedef struct {
+    int krylov;          /* MDS_KRYLOV_* */
+    int restart;         /* FGMRES restart length (30) */
+    double rtol;         /* stop when ||b - A x|| <= rtol ||b|| (1e-8) */
+    int max_iters;       /* preconditioner applications per right-hand side (1000) */
+    int use_precond;     /* 1 = the set-up preconditioner, 0 = identity */
+} mds_solve_opts;
+
+typedef struct {
+    int iterations;      /* preconditioner applications */
+    int restarts;
+    int status;          /* MDS_OK, MDS_WARN_NOT_CONVERGED or an error */
+    double relres_est;   /* last Arnoldi / recurrence estimate */
+    double relres_true;  /* ||b - A x|| / ||b|| recomputed at exit */
+} mds_rhs_stats;
+
+int mds_solve_opts_default(mds_solve_opts *o);
+
+/* Solve A x = b for nrhs right-hand sides.  b: [nrhs][n] FP64 (column r at
+ * b + r n), NULL = the assembled right-hand sides.  x: [nrhs][n], holds the
+ * initial guess on entry (zeros give the x0 = 0 of Sec. 4) and the solution on
+ * return.  b and x may be device or host pointers (host ones are staged
+ * through device buffers inside the call).  `prec` may be NULL when
+ * use_precond = 0.  stats: host array [nrhs], may be NULL.  Returns MDS_OK,
+ * MDS_WARN_NOT_CONVERGED or an error. */
+int mds_solve(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, double *x,
+              int nrhs, const mds_solve_opts *opts, mds_rhs_stats *stats);
+
+/* ---- measurement ----
+ * Kernel classes timed with CUDA events on the context stream when enabled:
+ * 0 = full-system SpMV, 1 = V-cycle residual (pre-smooth + residual),
+ * 2 = V-cycle post-smooth (prolongation + correction + smoothing),
+ * 3 = Gram-Schmidt dot products, 4 = Gram-Schmidt updates, 5 = all V-cycle
+ * kernels together, 6 = restriction.  Bytes are algorithmic (each matrix and
+ * vector byte counted once per launch). */
+#define MDS_KCLASS_COUNT 8
+int mds_timing_enable(mds_ctx ctx, int kclass, int enable);
+int mds_timing_reset(mds_ctx ctx);
+/* Synchronises the stream; returns launches, summed event time (ms) and summed
+ * algorithmic bytes of a class since the last reset. */
+int mds_timing_query(mds_ctx ctx, int kclass, int64_t *launches, double *ms, double *bytes);
+/* Copy `bytes` bytes from src to dst (each a host or device pointer) on the
+ * context stream and synchronise it.  A convenience for callers without
+ * their own CUDA runtime binding. */
+int mds_memcpy(mds_ctx ctx, void *dst, const void *src, size_t bytes);
+
+/* Number of kernels the library launched since the last reset (all classes). */
+int mds_launch_count(mds_ctx ctx, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

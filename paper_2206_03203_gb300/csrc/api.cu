@@ -1,0 +1,589 @@
+// The C ABI of libmdsolve (include/mdsolve.h): contexts, memory, systems,
+// preconditioner set-up, Algorithm 1, solves and timing.
+#include <cmath>
+#include <cstdio>
+#include <new>
+
+#include "internal.cuh"
+#include "krylov.cuh"
+
+namespace mds {
+
+// ---------------------------------------------------------------- memory
+
+Buf::Buf(Ctx *c, size_t n) : ctx(c), bytes(n) {
+    if (n == 0) n = 1;
+    p = c->raw_alloc(n);
+}
+
+Buf::~Buf() { reset(); }
+
+Buf &Buf::operator=(Buf &&o) noexcept {
+    if (this != &o) {
+        reset();
+        ctx = o.ctx;
+        p = o.p;
+        bytes = o.bytes;
+        o.p = nullptr;
+        o.bytes = 0;
+    }
+    return *this;
+}
+
+void Buf::reset() {
+    if (p && ctx) ctx->raw_free(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+void *Ctx::raw_alloc(size_t n) {
+    void *p = nullptr;
+    if (custom_alloc) {
+        p = alloc.alloc(n, alloc.user);
+        if (!p) throw Error(MDS_ERR_OOM, "allocator returned NULL for " + std::to_string(n) + " bytes");
+    } else {
+        cudaError_t e = cudaMallocAsync(&p, n, stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw Error(MDS_ERR_OOM, "cudaMallocAsync(" + std::to_string(n) + "): " + cudaGetErrorString(e));
+        }
+    }
+    return p;
+}
+
+void Ctx::raw_free(void *p) {
+    if (custom_alloc)
+        alloc.free(p, alloc.user);
+    else
+        cudaFreeAsync(p, stream);
+}
+
+void Ctx::check_err(const char *where) {
+    int e = read(d_err);
+    if (!e) return;
+    MDS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), stream));
+    std::string w(where);
+    if (e & DERR_DUP_FACE) throw Error(MDS_ERR_INVALID, w + ": two fracture cells on one face");
+    if (e & DERR_BAD_FRACTURE) throw Error(MDS_ERR_INVALID, w + ": fracture cell not on an interior face");
+    if (e & DERR_CAPACITY) throw Error(MDS_ERR_CAPACITY, w + ": a row exceeded the kernel's row capacity");
+    if (e & DERR_NOT_SPD) throw Error(MDS_ERR_NOT_SPD, w + ": non-positive pivot");
+    if (e & DERR_ZERO_DIAG) throw Error(MDS_ERR_ZERO_DIAG, w + ": zero diagonal");
+    throw Error(MDS_ERR_NONFINITE, w + ": non-finite value");
+}
+
+KTimer::KTimer(Ctx &ctx, int k, double b) : c(ctx), cls(k) {
+    if (k < 0 || k >= MDS_KCLASS_COUNT) return;
+    c.launches[k]++;
+    c.bytes[k] += b;
+    if (!c.timing[k]) return;
+    auto &v = c.evs[k];
+    if (c.ev_used[k] == v.size()) {
+        KTimerRec r;
+        MDS_CUDA(cudaEventCreate(&r.e0));
+        MDS_CUDA(cudaEventCreate(&r.e1));
+        v.push_back(r);
+    }
+    rec = &v[c.ev_used[k]++];
+    cudaEventRecord(rec->e0, c.stream);
+}
+
+KTimer::~KTimer() {
+    if (rec) cudaEventRecord(rec->e1, c.stream);
+}
+
+}  // namespace mds
+
+using namespace mds;
+
+#define API_BEGIN try {
+#define API_END(ctxp)                                                     \
+    }                                                                     \
+    catch (const Error &e) {                                              \
+        if (ctxp) (ctxp)->last_error = e.msg;                             \
+        return e.code;                                                    \
+    }                                                                     \
+    catch (const std::bad_alloc &) {                                      \
+        if (ctxp) (ctxp)->last_error = "host allocation failed";          \
+        return MDS_ERR_OOM;                                               \
+    }                                                                     \
+    catch (...) {                                                         \
+        if (ctxp) (ctxp)->last_error = "unexpected exception";            \
+        return MDS_ERR_INVALID;                                           \
+    }                                                                     \
+    return MDS_OK;
+
+extern "C" {
+
+const char *mds_error_string(int s) {
+    switch (s) {
+        case MDS_OK: return "ok";
+        case MDS_WARN_NOT_CONVERGED: return "not converged within max_iters";
+        case MDS_ERR_INVALID: return "invalid argument";
+        case MDS_ERR_CUDA: return "CUDA runtime error";
+        case MDS_ERR_OOM: return "out of device memory";
+        case MDS_ERR_NOT_SPD: return "coarsest matrix not positive definite";
+        case MDS_ERR_BREAKDOWN: return "Krylov breakdown";
+        case MDS_ERR_NONFINITE: return "non-finite value";
+        case MDS_ERR_CAPACITY: return "row capacity exceeded";
+        case MDS_ERR_TIMEOUT: return "iteration bound exceeded";
+        case MDS_ERR_ZERO_DIAG: return "zero diagonal in A_ff";
+        default: return "unknown status";
+    }
+}
+
+const char *mds_last_error(mds_ctx ctx) { return ctx ? ctx->c.last_error.c_str() : "null context"; }
+
+int mds_create(mds_ctx *out, int device, void *stream, const mds_allocator *alloc) {
+    if (!out) return MDS_ERR_INVALID;
+    *out = nullptr;
+    mds_ctx h = new (std::nothrow) mds_ctx_s;
+    if (!h) return MDS_ERR_OOM;
+    Ctx *c = &h->c;
+    try {
+        int ndev = 0;
+        MDS_CUDA(cudaGetDeviceCount(&ndev));
+        MDS_REQUIRE(device >= 0 && device < ndev, MDS_ERR_INVALID, "no such CUDA device");
+        MDS_CUDA(cudaSetDevice(device));
+        c->device = device;
+        c->stream = (cudaStream_t)stream;
+        if (alloc && alloc->alloc && alloc->free) {
+            c->alloc = *alloc;
+            c->custom_alloc = true;
+        }
+        MDS_CUDA(cudaMalloc(&c->d_err, sizeof(int)));
+        MDS_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
+        MDS_CUDA(cudaMallocHost(&c->h_pin, 4096));
+    } catch (const Error &e) {
+        int code = e.code;
+        if (c->d_err) cudaFree(c->d_err);
+        delete h;
+        return code;
+    }
+    *out = h;
+    return MDS_OK;
+}
+
+int mds_destroy(mds_ctx ctx) {
+    if (!ctx) return MDS_ERR_INVALID;
+    Ctx &c = ctx->c;
+    cudaStreamSynchronize(c.stream);
+    for (int k = 0; k < MDS_KCLASS_COUNT; k++)
+        for (auto &r : c.evs[k]) {
+            cudaEventDestroy(r.e0);
+            cudaEventDestroy(r.e1);
+        }
+    cudaFree(c.d_err);
+    cudaFreeHost(c.h_pin);
+    delete ctx;
+    return MDS_OK;
+}
+
+int mds_set_stream(mds_ctx ctx, void *stream) {
+    if (!ctx) return MDS_ERR_INVALID;
+    ctx->c.stream = (cudaStream_t)stream;
+    return MDS_OK;
+}
+
+int mds_assemble(mds_ctx ctx, const mds_instance *inst, mds_system *out) {
+    if (!ctx || !inst || !out) return MDS_ERR_INVALID;
+    Ctx *c = &ctx->c;
+    *out = nullptr;
+    API_BEGIN
+    MDS_CUDA(cudaSetDevice(c->device));
+    auto *s = new mds_system_s;
+    try {
+        s->ctx = c;
+        assemble_instance(*c, *inst, s->own);
+        s->n_m = s->own.n_m;
+        s->n_f = s->own.n_f;
+        s->nrhs = s->own.nrhs;
+        for (int q = 0; q < 4; q++) s->view[q] = s->own.blk[q].view();
+        s->view[4] = s->own.full.view();
+        s->b = s->own.b.as<double>();
+    } catch (...) {
+        delete s;
+        throw;
+    }
+    *out = s;
+    API_END(c)
+}
+
+static void check_csr(const mds_csr *A, int64_t nrow, int64_t ncol, const char *name) {
+    MDS_REQUIRE(A && A->nrow == nrow && A->ncol == ncol && A->nnz >= 0, MDS_ERR_INVALID,
+                std::string("block ") + name + " has the wrong shape");
+    MDS_REQUIRE(A->row_ptr && (A->nnz == 0 || (A->col && A->val)), MDS_ERR_INVALID,
+                std::string("block ") + name + " has null arrays");
+}
+
+int mds_system_from_csr(mds_ctx ctx, const mds_csr *Amm, const mds_csr *Amf, const mds_csr *Afm, const mds_csr *Aff,
+                        const double *b, mds_system *out) {
+    if (!ctx || !out || !Amm || !Aff) return MDS_ERR_INVALID;
+    Ctx *c = &ctx->c;
+    *out = nullptr;
+    API_BEGIN
+    MDS_CUDA(cudaSetDevice(c->device));
+    int64_t nm = Amm->nrow, nf = Aff->nrow;
+    check_csr(Amm, nm, nm, "A_mm");
+    check_csr(Amf, nm, nf, "A_mf");
+    check_csr(Afm, nf, nm, "A_fm");
+    check_csr(Aff, nf, nf, "A_ff");
+    MDS_REQUIRE(nm + nf < INT32_MAX, MDS_ERR_INVALID, "too many unknowns");
+    auto *s = new mds_system_s;
+    try {
+        s->ctx = c;
+        s->n_m = nm;
+        s->n_f = nf;
+        s->nrhs = 1;
+        s->view[0] = *Amm;
+        s->view[1] = *Amf;
+        s->view[2] = *Afm;
+        s->view[3] = *Aff;
+        merge_blocks(*c, s->view, nm, nf, s->own.full);
+        s->view[4] = s->own.full.view();
+        s->own.b = Buf(c, sizeof(double) * (size_t)(nm + nf));
+        if (b)
+            MDS_CUDA(cudaMemcpyAsync(s->own.b.p, b, sizeof(double) * (size_t)(nm + nf), cudaMemcpyDeviceToDevice,
+                                     c->stream));
+        else
+            fill_f64(*c, s->own.b.as<double>(), 0.0, nm + nf);
+        s->b = s->own.b.as<double>();
+        c->sync();
+    } catch (...) {
+        delete s;
+        throw;
+    }
+    *out = s;
+    API_END(c)
+}
+
+int mds_system_destroy(mds_system sys) {
+    if (!sys) return MDS_ERR_INVALID;
+    cudaSetDevice(sys->ctx->device);
+    delete sys;
+    return MDS_OK;
+}
+
+int mds_system_info(mds_system sys, int64_t *n_m, int64_t *n_f, int *nrhs, int64_t nnz[5]) {
+    if (!sys) return MDS_ERR_INVALID;
+    if (n_m) *n_m = sys->n_m;
+    if (n_f) *n_f = sys->n_f;
+    if (nrhs) *nrhs = sys->nrhs;
+    if (nnz)
+        for (int q = 0; q < 5; q++) nnz[q] = sys->view[q].nnz;
+    return MDS_OK;
+}
+
+int mds_system_view(mds_system sys, mds_csr blocks[5], const double **b) {
+    if (!sys) return MDS_ERR_INVALID;
+    if (blocks)
+        for (int q = 0; q < 5; q++) blocks[q] = sys->view[q];
+    if (b) *b = sys->b;
+    return MDS_OK;
+}
+
+int mds_setup_opts_default(mds_setup_opts *o) {
+    if (!o) return MDS_ERR_INVALID;
+    o->theta = 0.08;
+    o->n_coarse = 512;
+    o->max_levels = 25;
+    o->stall_ratio = 0.9;
+    o->seed = 0x220603203ULL;
+    o->smoother = MDS_SMOOTHER_L1JACOBI;
+    o->precision = MDS_PREC_FP64;
+    o->lowp_from_level = 1;
+    o->kind = MDS_BLOCK_LOWER;
+    return MDS_OK;
+}
+
+int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_precond *out) {
+    if (!ctx || !sys || !out) return MDS_ERR_INVALID;
+    Ctx *c = &ctx->c;
+    *out = nullptr;
+    API_BEGIN
+    MDS_CUDA(cudaSetDevice(c->device));
+    mds_setup_opts o;
+    mds_setup_opts_default(&o);
+    if (opts) o = *opts;
+    MDS_REQUIRE(o.precision == MDS_PREC_FP64 || o.precision == MDS_PREC_FP32, MDS_ERR_INVALID,
+                "precision must be MDS_PREC_FP64 or MDS_PREC_FP32");
+    MDS_REQUIRE(o.smoother == MDS_SMOOTHER_L1JACOBI, MDS_ERR_INVALID, "smoother not available");
+    MDS_REQUIRE(o.kind >= 0 && o.kind <= 2, MDS_ERR_INVALID, "bad preconditioner kind");
+    MDS_REQUIRE(o.theta >= 0.0 && o.n_coarse >= 1 && o.n_coarse <= 8192, MDS_ERR_INVALID, "bad AMG options");
+    auto *p = new mds_precond_s;
+    try {
+        p->ctx = c;
+        p->sys = sys;
+        p->o = o;
+        p->S = schur_build(*c, sys->view[0], sys->view[1], sys->view[2], sys->view[3], p->dk);
+        amg_setup(*c, p->S.view(), o, p->h[0]);
+        p->has_f = sys->n_f > 0;
+        if (p->has_f) amg_setup(*c, sys->view[3], o, p->h[1]);
+        int64_t mx = sys->n_m > sys->n_f ? sys->n_m : sys->n_f;
+        p->tf64 = Buf(c, sizeof(double) * (size_t)(mx > 0 ? mx : 1));
+    } catch (...) {
+        delete p;
+        throw;
+    }
+    *out = p;
+    API_END(c)
+}
+
+int mds_precond_destroy(mds_precond p) {
+    if (!p) return MDS_ERR_INVALID;
+    cudaSetDevice(p->ctx->device);
+    delete p;
+    return MDS_OK;
+}
+
+int mds_precond_info(mds_precond p, int block, int *nlevels, int64_t *level_n, int64_t *level_nnz, int *dense) {
+    if (!p || block < 0 || block > 1) return MDS_ERR_INVALID;
+    if (block == 1 && !p->has_f) {
+        if (nlevels) *nlevels = 0;
+        if (dense) *dense = 0;
+        return MDS_OK;
+    }
+    const Hierarchy &h = p->h[block];
+    if (nlevels) *nlevels = (int)h.lv.size();
+    for (size_t l = 0; l < h.lv.size() && l < 32; l++) {
+        if (level_n) level_n[l] = h.lv[l].A.nrow;
+        if (level_nnz) level_nnz[l] = h.lv[l].A.nnz;
+    }
+    if (dense) *dense = h.dense ? 1 : 0;
+    return MDS_OK;
+}
+
+int mds_precond_level(mds_precond p, int block, int level, mds_csr *A, const int32_t **agg, const int8_t **roots) {
+    if (!p || block < 0 || block > 1 || (block == 1 && !p->has_f)) return MDS_ERR_INVALID;
+    const Hierarchy &h = p->h[block];
+    if (level < 0 || level >= (int)h.lv.size()) return MDS_ERR_INVALID;
+    const Level &L = h.lv[level];
+    if (A) *A = L.A.view();
+    if (agg) *agg = L.has_coarse ? L.agg.as<int32_t>() : nullptr;
+    if (roots) *roots = L.roots.as<int8_t>();
+    return MDS_OK;
+}
+
+}  // extern "C"
+
+namespace mds {
+
+// V-cycle on FP64 input/output regardless of the hierarchy's precision.
+static void vcycle_f64(Ctx &c, Hierarchy &h, const double *b, double *x) {
+    if (h.prec == 64) {
+        vcycle_apply(c, h, b, x);
+        return;
+    }
+    int64_t n = h.lv[0].A.nrow;
+    cast_f64_f32(c, b, h.lv[0].b.as<float>(), n);
+    vcycle_apply(c, h, h.lv[0].b.p, h.lv[0].x.p);
+    cast_f32_f64(c, h.lv[0].x.as<float>(), x, n);
+}
+
+// Algorithm 1 (block lower), and the block-diagonal / block-upper variants.
+static void precond_apply(mds_precond p, const double *r, double *z) {
+    Ctx &c = *p->ctx;
+    mds_system s = p->sys;
+    int64_t nm = s->n_m, nf = s->n_f;
+    Hierarchy &HS = p->h[0];
+    Hierarchy &HF = p->h[1];
+    const mds_csr &Afm = s->view[2], &Amf = s->view[1];
+    int kind = p->o.kind;
+    if (kind == MDS_BLOCK_UPPER && p->has_f) {
+        // z_f = Q_ff r_f; r_m <- r_m - A_mf z_f; z_m = Q_mm r_m
+        vcycle_f64(c, HF, r + nm, z + nm);
+        spmv_sub_f64(c, Amf, r, z + nm, p->tf64.as<double>());
+        vcycle_f64(c, HS, p->tf64.as<double>(), z);
+        return;
+    }
+    // step 1: z_m = Q_mm r_m
+    if (HS.prec == 64) {
+        vcycle_apply(c, HS, r, z);
+    } else {
+        cast_f64_f32(c, r, HS.lv[0].b.as<float>(), nm);
+        vcycle_apply(c, HS, HS.lv[0].b.p, HS.lv[0].x.p);
+        cast_f32_f64(c, HS.lv[0].x.as<float>(), z, nm);
+    }
+    if (!p->has_f) return;
+    // step 2: r_f <- r_f - A_fm z_m (block lower only); step 3: z_f = Q_ff r_f
+    if (HF.prec == 64) {
+        if (kind == MDS_BLOCK_LOWER) {
+            spmv_sub_f64(c, Afm, r + nm, z, p->tf64.as<double>());
+            vcycle_apply(c, HF, p->tf64.as<double>(), z + nm);
+        } else {
+            vcycle_apply(c, HF, r + nm, z + nm);
+        }
+    } else {
+        float *bf = HF.lv[0].b.as<float>();
+        if (kind == MDS_BLOCK_LOWER)
+            spmv_sub_f64_xf(c, Afm, r + nm, HS.lv[0].x.as<float>(), bf);
+        else
+            cast_f64_f32(c, r + nm, bf, nf);
+        vcycle_apply(c, HF, HF.lv[0].b.p, HF.lv[0].x.p);
+        cast_f32_f64(c, HF.lv[0].x.as<float>(), z + nm, nf);
+    }
+}
+
+static bool is_device_ptr(const void *p) {
+    if (!p) return true;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace mds
+
+extern "C" {
+
+int mds_precond_apply(mds_ctx ctx, mds_precond p, const double *r, double *z) {
+    if (!ctx || !p || !r || !z) return MDS_ERR_INVALID;
+    Ctx *c = &ctx->c;
+    API_BEGIN
+    precond_apply(p, r, z);
+    API_END(c)
+}
+
+int mds_vcycle(mds_ctx ctx, mds_precond p, int block, const double *b, double *x) {
+    if (!ctx || !p || !b || !x || block < 0 || block > 1 || (block == 1 && !p->has_f)) return MDS_ERR_INVALID;
+    Ctx *c = &ctx->c;
+    API_BEGIN
+    vcycle_f64(*c, p->h[block], b, x);
+    API_END(c)
+}
+
+int mds_spmv(mds_ctx ctx, mds_system sys, const double *x, double *y) {
+    if (!ctx || !sys || !x || !y) return MDS_ERR_INVALID;
+    Ctx *c = &ctx->c;
+    API_BEGIN
+    spmv_f64(*c, sys->view[4], x, y, KC_SPMV);
+    API_END(c)
+}
+
+int mds_solve_opts_default(mds_solve_opts *o) {
+    if (!o) return MDS_ERR_INVALID;
+    o->krylov = MDS_KRYLOV_FGMRES;
+    o->restart = 30;
+    o->rtol = 1e-8;
+    o->max_iters = 1000;
+    o->use_precond = 1;
+    return MDS_OK;
+}
+
+int mds_solve(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, double *x, int nrhs,
+              const mds_solve_opts *opts, mds_rhs_stats *stats) {
+    if (!ctx || !sys || !x || nrhs < 1) return MDS_ERR_INVALID;
+    Ctx *c = &ctx->c;
+    int worst = MDS_OK;
+    API_BEGIN
+    MDS_CUDA(cudaSetDevice(c->device));
+    mds_solve_opts o;
+    mds_solve_opts_default(&o);
+    if (opts) o = *opts;
+    MDS_REQUIRE(o.rtol > 0.0 && o.max_iters >= 0 && o.restart >= 1, MDS_ERR_INVALID, "bad solve options");
+    MDS_REQUIRE(!o.use_precond || (prec && prec->sys == sys), MDS_ERR_INVALID, "preconditioner of another system");
+    MDS_REQUIRE(b || nrhs <= sys->nrhs, MDS_ERR_INVALID, "more right-hand sides than assembled");
+    int64_t n = sys->n_m + sys->n_f;
+    const double *B = b ? b : sys->b;
+    bool bdev = is_device_ptr(B), xdev = is_device_ptr(x);
+    Buf bst, xst;
+    const double *Bd = B;
+    double *Xd = x;
+    size_t bytes = sizeof(double) * (size_t)n * (size_t)nrhs;
+    if (!bdev) {
+        bst = Buf(c, bytes);
+        MDS_CUDA(cudaMemcpyAsync(bst.p, B, bytes, cudaMemcpyHostToDevice, c->stream));
+        Bd = bst.as<double>();
+    }
+    if (!xdev) {
+        xst = Buf(c, bytes);
+        MDS_CUDA(cudaMemcpyAsync(xst.p, x, bytes, cudaMemcpyHostToDevice, c->stream));
+        Xd = xst.as<double>();
+    }
+    PrecFn M;
+    if (o.use_precond) {
+        M = [prec](const double *r, double *z) { precond_apply(prec, r, z); };
+    } else {
+        M = [c, n](const double *r, double *z) {
+            MDS_CUDA(cudaMemcpyAsync(z, r, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, c->stream));
+        };
+    }
+    for (int k = 0; k < nrhs; k++) {
+        const double *bk = Bd + (size_t)k * n;
+        double *xk = Xd + (size_t)k * n;
+        KrylovResult r = o.krylov == MDS_KRYLOV_PCG ? pcg(*c, sys->view[4], M, bk, xk, n, o)
+                                                    : fgmres(*c, sys->view[4], M, bk, xk, n, o);
+        if (stats) {
+            stats[k].iterations = r.iterations;
+            stats[k].restarts = r.restarts;
+            stats[k].status = r.status;
+            stats[k].relres_est = r.relres_est;
+            stats[k].relres_true = r.relres_true;
+        }
+        if (r.status < 0) {
+            if (worst >= 0) worst = r.status;
+        } else if (r.status > worst && worst >= 0) {
+            worst = r.status;
+        }
+    }
+    if (!xdev) MDS_CUDA(cudaMemcpyAsync(x, Xd, bytes, cudaMemcpyDeviceToHost, c->stream));
+    c->sync();
+    if (worst < 0) c->last_error = "a right-hand side failed; see its stats";
+    return worst;
+    API_END(c)
+}
+
+int mds_timing_enable(mds_ctx ctx, int k, int enable) {
+    if (!ctx || k < 0 || k >= MDS_KCLASS_COUNT) return MDS_ERR_INVALID;
+    ctx->c.timing[k] = enable != 0;
+    return MDS_OK;
+}
+
+int mds_timing_reset(mds_ctx ctx) {
+    if (!ctx) return MDS_ERR_INVALID;
+    Ctx &c = ctx->c;
+    cudaStreamSynchronize(c.stream);
+    for (int k = 0; k < MDS_KCLASS_COUNT; k++) {
+        c.ev_used[k] = 0;
+        c.launches[k] = 0;
+        c.bytes[k] = 0.0;
+    }
+    c.total_launches = 0;
+    return MDS_OK;
+}
+
+int mds_timing_query(mds_ctx ctx, int k, int64_t *launches, double *ms, double *bytes) {
+    if (!ctx || k < 0 || k >= MDS_KCLASS_COUNT) return MDS_ERR_INVALID;
+    Ctx *c = &ctx->c;
+    API_BEGIN
+    c->sync();
+    double tot = 0.0;
+    for (size_t q = 0; q < c->ev_used[k]; q++) {
+        float t = 0.f;
+        MDS_CUDA(cudaEventElapsedTime(&t, c->evs[k][q].e0, c->evs[k][q].e1));
+        tot += t;
+    }
+    if (launches) *launches = c->launches[k];
+    if (ms) *ms = tot;
+    if (bytes) *bytes = c->bytes[k];
+    API_END(c)
+}
+
+int mds_memcpy(mds_ctx ctx, void *dst, const void *src, size_t bytes) {
+    if (!ctx || (!dst && bytes) || (!src && bytes)) return MDS_ERR_INVALID;
+    Ctx *c = &ctx->c;
+    API_BEGIN
+    if (bytes) MDS_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
+    c->sync();
+    API_END(c)
+}
+
+int mds_launch_count(mds_ctx ctx, int64_t *launches) {
+    if (!ctx || !launches) return MDS_ERR_INVALID;
+    *launches = ctx->c.total_launches;
+    return MDS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,249 @@
+// Internal declarations of libmdsolve (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "mdsolve.h"
+
+namespace mds {
+
+struct Error {
+    int code;
+    std::string msg;
+    Error(int c, std::string m) : code(c), msg(std::move(m)) {}
+};
+
+#define MDS_CUDA(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            throw ::mds::Error(e_ == cudaErrorMemoryAllocation ? MDS_ERR_OOM : MDS_ERR_CUDA, \
+                               std::string(#call) + ": " + cudaGetErrorString(e_));      \
+    } while (0)
+
+#define MDS_REQUIRE(cond, code, msg)                        \
+    do {                                                    \
+        if (!(cond)) throw ::mds::Error((code), (msg));     \
+    } while (0)
+
+// Device error word bits set by kernels (never trap).
+enum : int {
+    DERR_DUP_FACE = 1,
+    DERR_BAD_FRACTURE = 2,
+    DERR_CAPACITY = 4,
+    DERR_NOT_SPD = 8,
+    DERR_ZERO_DIAG = 16,
+    DERR_NONFINITE = 32,
+};
+
+// Kernel classes for event timing (match the C ABI's numbering).
+enum : int {
+    KC_NONE = -1,
+    KC_SPMV = 0,
+    KC_VC_RESID = 1,
+    KC_VC_POST = 2,
+    KC_GS_DOT = 3,
+    KC_GS_AXPY = 4,
+    KC_VCYCLE = 5,
+    KC_VC_RESTRICT = 6,
+};
+
+struct Ctx;
+
+// Owned device allocation from the context's allocator (move-only).
+struct Buf {
+    Ctx *ctx = nullptr;
+    void *p = nullptr;
+    size_t bytes = 0;
+    Buf() = default;
+    Buf(Ctx *c, size_t n);
+    ~Buf();
+    Buf(const Buf &) = delete;
+    Buf &operator=(const Buf &) = delete;
+    Buf(Buf &&o) noexcept { *this = std::move(o); }
+    Buf &operator=(Buf &&o) noexcept;
+    void reset();
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+struct KTimerRec {
+    cudaEvent_t e0, e1;
+};
+
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    mds_allocator alloc{};
+    bool custom_alloc = false;
+    std::string last_error;
+    int *d_err = nullptr;      // device error word
+    void *h_pin = nullptr;     // pinned host scratch (4 KB)
+    bool timing[MDS_KCLASS_COUNT] = {};
+    std::vector<KTimerRec> evs[MDS_KCLASS_COUNT];
+    size_t ev_used[MDS_KCLASS_COUNT] = {};
+    int64_t launches[MDS_KCLASS_COUNT] = {};
+    double bytes[MDS_KCLASS_COUNT] = {};
+    int64_t total_launches = 0;
+
+    void *raw_alloc(size_t n);
+    void raw_free(void *p);
+    void sync() { MDS_CUDA(cudaStreamSynchronize(stream)); }
+    void post_launch() {
+        total_launches++;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) throw Error(MDS_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    }
+    // read device value (synchronises)
+    template <class T> T read(const T *d) {
+        MDS_CUDA(cudaMemcpyAsync(h_pin, d, sizeof(T), cudaMemcpyDeviceToHost, stream));
+        sync();
+        T v;
+        std::memcpy(&v, h_pin, sizeof(T));
+        return v;
+    }
+    void clear_err() { MDS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), stream)); }
+    // raise the matching status if a kernel set the device error word
+    void check_err(const char *where);
+};
+
+// Scope that brackets one launch with events when its class is being timed.
+struct KTimer {
+    Ctx &c;
+    int cls;
+    KTimerRec *rec = nullptr;
+    KTimer(Ctx &ctx, int k, double bytes);
+    ~KTimer();
+};
+
+#define MDS_LAUNCH(ctx, cls, bytes, kern, grid, block, smem, ...)                  \
+    do {                                                                           \
+        ::mds::KTimer kt_((ctx), (cls), (double)(bytes));                          \
+        kern<<<(grid), (block), (smem), (ctx).stream>>>(__VA_ARGS__);               \
+        (ctx).post_launch();                                                       \
+    } while (0)
+
+inline unsigned grid_for(int64_t n, int block) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+// Owned CSR (int32 row pointers and columns, FP64 values).
+struct DCsr {
+    int64_t nrow = 0, ncol = 0, nnz = 0;
+    Buf rp, ci, v;
+    int32_t *rowp() const { return rp.as<int32_t>(); }
+    int32_t *cols() const { return ci.as<int32_t>(); }
+    double *vals() const { return v.as<double>(); }
+    mds_csr view() const { return mds_csr{nrow, ncol, nnz, rowp(), cols(), vals()}; }
+};
+
+inline DCsr csr_alloc(Ctx &c, int64_t nrow, int64_t ncol, int64_t nnz) {
+    DCsr A;
+    A.nrow = nrow;
+    A.ncol = ncol;
+    A.nnz = nnz;
+    A.rp = Buf(&c, sizeof(int32_t) * (size_t)(nrow + 1));
+    A.ci = Buf(&c, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+    A.v = Buf(&c, sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+    return A;
+}
+
+// ---- primitives (k_prim.cu) ----
+// out[0..n] = exclusive scan of cnt[0..n-1], out[n] = total; returns total.
+int64_t scan_counts(Ctx &c, const int32_t *cnt, int32_t *out, int64_t n);
+void fill_i32(Ctx &c, int32_t *p, int32_t v, int64_t n);
+void fill_f64(Ctx &c, double *p, double v, int64_t n);
+void cast_f64_f32(Ctx &c, const double *in, float *out, int64_t n);
+void cast_f32_f64(Ctx &c, const float *in, double *out, int64_t n);
+// y = A x (FP64 CSR)
+void spmv_f64(Ctx &c, const mds_csr &A, const double *x, double *y, int kclass);
+// out = r - A x with out in FP64 or FP32
+void spmv_sub_f64(Ctx &c, const mds_csr &A, const double *r, const double *x, double *out);
+void spmv_sub_f64_xf(Ctx &c, const mds_csr &A, const double *r, const float *x, float *out);
+
+// ---- assembly (k_assemble.cu) ----
+struct SystemData {
+    int64_t n_m = 0, n_f = 0;
+    int nrhs = 1;
+    DCsr full;
+    DCsr blk[4];
+    Buf b;  // [nrhs][N]
+};
+void assemble_instance(Ctx &c, const mds_instance &inst, SystemData &out);
+void split_blocks(Ctx &c, const mds_csr &full, int64_t n_m, DCsr blk[4]);
+void merge_blocks(Ctx &c, const mds_csr blk[4], int64_t n_m, int64_t n_f, DCsr &full);
+
+// ---- set-up (k_setup.cu) ----
+DCsr schur_build(Ctx &c, const mds_csr &Amm, const mds_csr &Amf, const mds_csr &Afm,
+                 const mds_csr &Aff, Buf &dk);
+
+struct Level {
+    DCsr A;           // FP64 master
+    Buf agg;          // int32 [n], next-level aggregate or -1
+    Buf roots;        // int8 [n]
+    Buf mem_off;      // int32 [nc+1] members of each next-level aggregate
+    Buf mem;          // int32 [#aggregated], ascending within an aggregate
+    Buf l1;           // FP64 [n]
+    Buf dinv;         // [n] 1/l1 in the vector precision
+    Buf vals_lp;      // values in the level precision (FP32) when not FP64
+    Buf b, x, r;      // work vectors in the vector precision
+    bool has_coarse = false;
+    int64_t nc = 0;
+};
+
+struct Hierarchy {
+    std::vector<Level> lv;
+    bool dense = false;
+    int64_t nd = 0;
+    Buf Ainv;         // FP64 [nd nd] inverse of the coarsest matrix
+    int prec = 64;    // 64 or 32
+    int smoother = 0;
+};
+
+void amg_setup(Ctx &c, const mds_csr &A, const mds_setup_opts &o, Hierarchy &h);
+
+// ---- dense (k_dense.cu) ----
+// Cholesky of the n x n SPD matrix stored densely, then its inverse.
+void dense_spd_inverse(Ctx &c, const mds_csr &A, Buf &Ainv);
+void dense_gemv_f64(Ctx &c, const double *M, int64_t n, const double *x, double *y);
+void dense_gemv_f32(Ctx &c, const double *M, int64_t n, const float *x, float *y);
+
+// ---- V-cycle (k_vcycle.cu) ----
+// x = V(b) on level 0 of h; b and x in the hierarchy's vector precision.
+void vcycle_apply(Ctx &c, Hierarchy &h, const void *b, void *x);
+
+// ---- Krylov (k_krylov.cu) ----
+struct KrylovWork;
+}  // namespace mds
+
+// Handle structs (opaque in the C ABI).
+struct mds_ctx_s {
+    mds::Ctx c;
+};
+
+struct mds_system_s {
+    mds::Ctx *ctx = nullptr;
+    int64_t n_m = 0, n_f = 0;
+    int nrhs = 0;
+    mds_csr view[5]{};       // 0..3 blocks, 4 full
+    mds::SystemData own;     // owned storage (blocks borrowed for from_csr)
+    const double *b = nullptr;
+};
+
+struct mds_precond_s {
+    mds::Ctx *ctx = nullptr;
+    mds_system sys = nullptr;
+    mds_setup_opts o{};
+    mds::DCsr S;
+    mds::Buf dk;
+    mds::Hierarchy h[2];
+    bool has_f = false;
+    mds::Buf t32, z32m, z32f, tf64;  // Algorithm 1 work vectors
+};

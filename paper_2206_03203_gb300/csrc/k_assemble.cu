@@ -1,0 +1,418 @@
+// Two-point-flux assembly of the mixed-dimensional block system on the GPU.
+//
+// Sec. 2.1 of the paper (Eq. (1) per subdomain, Eq. (2)-(3) across each
+// matrix-fracture interface) discretised cell-centred on a Cartesian grid;
+// the interface flux is eliminated into a matrix-fracture transmissibility.
+// Unknowns are ordered [matrix cells (x fastest); fracture cells], giving the
+// 2x2 block structure of Eq. (4).  Compiled with -fmad=false: every product
+// and sum is rounded as written, so values are reproducible to the bit.
+#include "internal.cuh"
+
+namespace mds {
+
+struct GridD {
+    int dim, n;
+    int64_t ext[3][3];
+    int64_t off[3];
+    double h, F, elen;
+    int64_t n_m, nf, N, nb;
+};
+
+__device__ __forceinline__ int64_t face_id(const GridD &g, int d, int64_t x, int64_t y, int64_t z) {
+    const int64_t *e = g.ext[d];
+    if (x < 0 || y < 0 || z < 0 || x >= e[0] || y >= e[1] || z >= e[2]) return -1;
+    return g.off[d] + x + e[0] * (y + e[1] * z);
+}
+
+__device__ __forceinline__ int32_t frac_at(const GridD &g, const int32_t *map, int d, const int64_t c[3]) {
+    int64_t f = face_id(g, d, c[0], c[1], c[2]);
+    return f < 0 ? -1 : map[f];
+}
+
+__device__ __forceinline__ int64_t cell_id(const GridD &g, const int64_t c[3]) {
+    return c[0] + (int64_t)g.n * (c[1] + (int64_t)g.n * c[2]);
+}
+
+__global__ void k_map_scatter(GridD g, const int32_t *__restrict__ axis, const int32_t *__restrict__ pos,
+                              int32_t *__restrict__ map, int *err) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.nf) return;
+    int d = axis[k];
+    int64_t x = pos[3 * k], y = pos[3 * k + 1], z = g.dim == 3 ? pos[3 * k + 2] : 0;
+    int64_t c[3] = {x, y, z};
+    if (d < 0 || d >= g.dim || c[d] < 1 || c[d] > g.n - 1) {
+        atomicOr(err, DERR_BAD_FRACTURE);
+        return;
+    }
+    int64_t f = face_id(g, d, x, y, z);
+    if (f < 0) {
+        atomicOr(err, DERR_BAD_FRACTURE);
+        return;
+    }
+    if (atomicCAS(map + f, -1, (int32_t)k) != -1) atomicOr(err, DERR_DUP_FACE);
+}
+
+struct Ent {
+    int32_t c;
+    double t;
+};
+
+__device__ __forceinline__ void sort_ents(Ent *e, int cnt) {
+    for (int a = 1; a < cnt; a++) {
+        Ent x = e[a];
+        int q = a - 1;
+        while (q >= 0 && e[q].c > x.c) {
+            e[q + 1] = e[q];
+            q--;
+        }
+        e[q + 1] = x;
+    }
+}
+
+// Entries of matrix row i (without the diagonal); returns their count and the
+// Dirichlet coefficients of the x=0 / x=1 faces.
+__device__ int matrix_entries(const GridD &g, const int32_t *map, const double *km, const double *kf,
+                              const double *ap, int64_t i, Ent *row, double tb[2], int has[2]) {
+    int64_t n = g.n;
+    int64_t c[3] = {i % n, (i / n) % n, g.dim == 3 ? i / (n * n) : 0};
+    double ki = km[i];
+    int cnt = 0;
+    has[0] = has[1] = 0;
+    tb[0] = tb[1] = 0.0;
+    for (int d = 0; d < g.dim; d++) {
+        for (int s = 0; s < 2; s++) {
+            int64_t plane = c[d] + s;
+            if (plane == 0 || plane == n) {
+                if (d == 0) {
+                    tb[s] = (g.F * (2.0 * ki)) / g.h;
+                    has[s] = 1;
+                }
+                continue;
+            }
+            int64_t fc[3] = {c[0], c[1], c[2]};
+            fc[d] = plane;
+            int32_t k = frac_at(g, map, d, fc);
+            if (k >= 0) {
+                double kappa = (2.0 * kf[k]) / ap[k];
+                row[cnt].c = (int32_t)(g.n_m + k);
+                row[cnt].t = g.F / (g.h / (2.0 * ki) + 1.0 / kappa);
+            } else {
+                int64_t nc[3] = {c[0], c[1], c[2]};
+                nc[d] = c[d] + (s ? 1 : -1);
+                int64_t j = cell_id(g, nc);
+                row[cnt].c = (int32_t)j;
+                row[cnt].t = g.F / (g.h / (2.0 * ki) + g.h / (2.0 * km[j]));
+            }
+            cnt++;
+        }
+    }
+    return cnt;
+}
+
+// Entries of fracture row k (without the diagonal).  bfa/bfb are the two
+// boundary faces sharing a Dirichlet end edge.
+__device__ int fracture_entries(const GridD &g, const int32_t *map, const double *km, const int32_t *axis,
+                                const int32_t *pos, const double *kf, const double *ap, int64_t k, Ent *row,
+                                double tb[2], int has[2], int64_t bfa[2], int64_t bfb[2]) {
+    int d = axis[k];
+    int64_t c[3] = {pos[3 * k], pos[3 * k + 1], g.dim == 3 ? pos[3 * k + 2] : 0};
+    int64_t plane = c[d];
+    double kappa = (2.0 * kf[k]) / ap[k];
+    double tk = ((kf[k] * ap[k]) * g.elen) / (0.5 * g.h);
+    int cnt = 0;
+    has[0] = has[1] = 0;
+    tb[0] = tb[1] = 0.0;
+    bfa[0] = bfa[1] = bfb[0] = bfb[1] = 0;
+    for (int s = 0; s < 2; s++) {
+        int64_t mc[3] = {c[0], c[1], c[2]};
+        mc[d] = plane - 1 + s;
+        int64_t j = cell_id(g, mc);
+        row[cnt].c = (int32_t)j;
+        row[cnt].t = g.F / (g.h / (2.0 * km[j]) + 1.0 / kappa);
+        cnt++;
+    }
+    for (int e = 0; e < g.dim; e++) {
+        if (e == d) continue;
+        for (int s = 0; s < 2; s++) {
+            int64_t u = c[e] + s;
+            if (e == 0 && (u == 0 || u == g.n)) {
+                int side = u == 0 ? 0 : 1;
+                tb[side] = tk;
+                has[side] = 1;
+                int64_t fa[3] = {c[0], c[1], c[2]}, fb[3] = {c[0], c[1], c[2]};
+                fa[d] = plane - 1;
+                fb[d] = plane;
+                bfa[side] = fa[1] + (int64_t)g.n * fa[2];
+                bfb[side] = fb[1] + (int64_t)g.n * fb[2];
+                continue;
+            }
+            // the four faces incident to the edge
+            for (int q = 0; q < 4; q++) {
+                int64_t f[3] = {c[0], c[1], c[2]};
+                int fd;
+                if (q < 2) {
+                    f[e] = u - 1 + q;
+                    fd = d;
+                } else {
+                    f[e] = u;
+                    f[d] = plane - 1 + (q - 2);
+                    fd = e;
+                }
+                int32_t l = frac_at(g, map, fd, f);
+                if (l < 0 || l == k) continue;
+                double tl = ((kf[l] * ap[l]) * g.elen) / (0.5 * g.h);
+                row[cnt].c = (int32_t)(g.n_m + l);
+                row[cnt].t = (tk * tl) / (tk + tl);
+                cnt++;
+            }
+        }
+    }
+    return cnt;
+}
+
+__global__ void k_count(GridD g, const int32_t *__restrict__ map, const double *__restrict__ km,
+                        const int32_t *__restrict__ axis, const int32_t *__restrict__ pos,
+                        const double *__restrict__ kf, const double *__restrict__ ap, int32_t *__restrict__ cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    Ent row[16];
+    double tb[2];
+    int has[2];
+    int64_t bfa[2], bfb[2];
+    int m = i < g.n_m ? matrix_entries(g, map, km, kf, ap, i, row, tb, has)
+                      : fracture_entries(g, map, km, axis, pos, kf, ap, i - g.n_m, row, tb, has, bfa, bfb);
+    cnt[i] = m + 1;
+}
+
+__global__ void k_fill(GridD g, const int32_t *__restrict__ map, const double *__restrict__ km,
+                       const int32_t *__restrict__ axis, const int32_t *__restrict__ pos,
+                       const double *__restrict__ kf, const double *__restrict__ ap, int nrhs,
+                       const double *__restrict__ pL, const double *__restrict__ pR, const int32_t *__restrict__ rp,
+                       int32_t *__restrict__ ci, double *__restrict__ val, double *__restrict__ b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    Ent row[16];
+    double tb[2];
+    int has[2];
+    int64_t bfa[2] = {0, 0}, bfb[2] = {0, 0};
+    bool is_m = i < g.n_m;
+    int cnt = is_m ? matrix_entries(g, map, km, kf, ap, i, row, tb, has)
+                   : fracture_entries(g, map, km, axis, pos, kf, ap, i - g.n_m, row, tb, has, bfa, bfb);
+    sort_ents(row, cnt);
+    double diag = 0.0;
+    for (int q = 0; q < cnt; q++) diag += row[q].t;
+    for (int s = 0; s < 2; s++)
+        if (has[s]) diag += tb[s];
+    int64_t p = rp[i];
+    bool placed = false;
+    for (int q = 0; q < cnt; q++) {
+        if (!placed && row[q].c > i) {
+            ci[p] = (int32_t)i;
+            val[p++] = diag;
+            placed = true;
+        }
+        ci[p] = row[q].c;
+        val[p++] = -row[q].t;
+    }
+    if (!placed) {
+        ci[p] = (int32_t)i;
+        val[p] = diag;
+    }
+    for (int r = 0; r < nrhs; r++) {
+        const double *L = pL + (int64_t)r * g.nb, *R = pR + (int64_t)r * g.nb;
+        double acc = 0.0;
+        if (is_m) {
+            int64_t n = g.n;
+            int64_t bf = (i / n) % n + (g.dim == 3 ? n * (i / (n * n)) : 0);
+            if (has[0]) acc += tb[0] * L[bf];
+            if (has[1]) acc += tb[1] * R[bf];
+        } else {
+            for (int s = 0; s < 2; s++) {
+                if (!has[s]) continue;
+                const double *P = s == 0 ? L : R;
+                double pv = (P[bfa[s]] + P[bfb[s]]) * 0.5;
+                acc += tb[s] * pv;
+            }
+        }
+        b[(int64_t)r * g.N + i] = acc;
+    }
+}
+
+// ---------------------------------------------------------------- block split / merge
+
+__global__ void k_split_count(int64_t N, int64_t n_m, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                              int32_t *__restrict__ lo, int32_t *__restrict__ hi) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int32_t a = rp[i], e = rp[i + 1], m = a;
+    while (m < e && ci[m] < n_m) m++;
+    lo[i] = m - a;
+    hi[i] = e - m;
+}
+
+__global__ void k_split_fill(int64_t N, int64_t n_m, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                             const double *__restrict__ v, const int32_t *__restrict__ rp_mm,
+                             int32_t *__restrict__ c_mm, double *__restrict__ v_mm, const int32_t *__restrict__ rp_mf,
+                             int32_t *__restrict__ c_mf, double *__restrict__ v_mf, const int32_t *__restrict__ rp_fm,
+                             int32_t *__restrict__ c_fm, double *__restrict__ v_fm, const int32_t *__restrict__ rp_ff,
+                             int32_t *__restrict__ c_ff, double *__restrict__ v_ff) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    bool mrow = i < n_m;
+    int64_t li = mrow ? i : i - n_m;
+    int32_t plo = mrow ? rp_mm[li] : rp_fm[li];
+    int32_t phi = mrow ? rp_mf[li] : rp_ff[li];
+    int32_t *clo = mrow ? c_mm : c_fm, *chi = mrow ? c_mf : c_ff;
+    double *vlo = mrow ? v_mm : v_fm, *vhi = mrow ? v_mf : v_ff;
+    for (int32_t p = rp[i]; p < rp[i + 1]; p++) {
+        int32_t j = ci[p];
+        if (j < n_m) {
+            clo[plo] = j;
+            vlo[plo++] = v[p];
+        } else {
+            chi[phi] = (int32_t)(j - n_m);
+            vhi[phi++] = v[p];
+        }
+    }
+}
+
+void split_blocks(Ctx &c, const mds_csr &full, int64_t n_m, DCsr blk[4]) {
+    int64_t N = full.nrow, n_f = N - n_m;
+    Buf lo(&c, sizeof(int32_t) * (size_t)(N + 1)), hi(&c, sizeof(int32_t) * (size_t)(N + 1));
+    MDS_LAUNCH(c, KC_NONE, 0, k_split_count, grid_for(N, 256), 256, 0, N, n_m, full.row_ptr, full.col,
+               lo.as<int32_t>(), hi.as<int32_t>());
+    int64_t rows[4] = {n_m, n_m, n_f, n_f};
+    int64_t cols[4] = {n_m, n_f, n_m, n_f};
+    const int32_t *src[4] = {lo.as<int32_t>(), hi.as<int32_t>(), lo.as<int32_t>() + n_m, hi.as<int32_t>() + n_m};
+    for (int q = 0; q < 4; q++) {
+        Buf rp(&c, sizeof(int32_t) * (size_t)(rows[q] + 1));
+        int64_t nnz = scan_counts(c, src[q], rp.as<int32_t>(), rows[q]);
+        blk[q].nrow = rows[q];
+        blk[q].ncol = cols[q];
+        blk[q].nnz = nnz;
+        blk[q].rp = std::move(rp);
+        blk[q].ci = Buf(&c, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+        blk[q].v = Buf(&c, sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+    }
+    MDS_LAUNCH(c, KC_NONE, 0, k_split_fill, grid_for(N, 256), 256, 0, N, n_m, full.row_ptr, full.col, full.val,
+               blk[0].rowp(), blk[0].cols(), blk[0].vals(), blk[1].rowp(), blk[1].cols(), blk[1].vals(),
+               blk[2].rowp(), blk[2].cols(), blk[2].vals(), blk[3].rowp(), blk[3].cols(), blk[3].vals());
+}
+
+__global__ void k_merge_count(int64_t N, int64_t n_m, const int32_t *rp0, const int32_t *rp1, const int32_t *rp2,
+                              const int32_t *rp3, int32_t *cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    if (i < n_m)
+        cnt[i] = (rp0[i + 1] - rp0[i]) + (rp1[i + 1] - rp1[i]);
+    else {
+        int64_t k = i - n_m;
+        cnt[i] = (rp2[k + 1] - rp2[k]) + (rp3[k + 1] - rp3[k]);
+    }
+}
+
+__global__ void k_merge_fill(int64_t N, int64_t n_m, mds_csr b0, mds_csr b1, mds_csr b2, mds_csr b3,
+                             const int32_t *__restrict__ rp, int32_t *__restrict__ ci, double *__restrict__ v) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const mds_csr &L = i < n_m ? b0 : b2;
+    const mds_csr &R = i < n_m ? b1 : b3;
+    int64_t li = i < n_m ? i : i - n_m;
+    int32_t p = rp[i];
+    for (int32_t q = L.row_ptr[li]; q < L.row_ptr[li + 1]; q++) {
+        ci[p] = L.col[q];
+        v[p++] = L.val[q];
+    }
+    for (int32_t q = R.row_ptr[li]; q < R.row_ptr[li + 1]; q++) {
+        ci[p] = (int32_t)(R.col[q] + n_m);
+        v[p++] = R.val[q];
+    }
+}
+
+void merge_blocks(Ctx &c, const mds_csr blk[4], int64_t n_m, int64_t n_f, DCsr &full) {
+    int64_t N = n_m + n_f;
+    Buf cnt(&c, sizeof(int32_t) * (size_t)(N + 1));
+    MDS_LAUNCH(c, KC_NONE, 0, k_merge_count, grid_for(N, 256), 256, 0, N, n_m, blk[0].row_ptr, blk[1].row_ptr,
+               blk[2].row_ptr, blk[3].row_ptr, cnt.as<int32_t>());
+    full.nrow = N;
+    full.ncol = N;
+    full.rp = Buf(&c, sizeof(int32_t) * (size_t)(N + 1));
+    full.nnz = scan_counts(c, cnt.as<int32_t>(), full.rowp(), N);
+    full.ci = Buf(&c, sizeof(int32_t) * (size_t)(full.nnz > 0 ? full.nnz : 1));
+    full.v = Buf(&c, sizeof(double) * (size_t)(full.nnz > 0 ? full.nnz : 1));
+    MDS_LAUNCH(c, KC_NONE, 0, k_merge_fill, grid_for(N, 256), 256, 0, N, n_m, blk[0], blk[1], blk[2], blk[3],
+               full.rowp(), full.cols(), full.vals());
+}
+
+// ---------------------------------------------------------------- driver
+
+template <class T>
+static const T *stage(Ctx &c, const T *p, size_t count, bool on_device, Buf &hold) {
+    if (on_device || count == 0) return p;
+    hold = Buf(&c, sizeof(T) * count);
+    MDS_CUDA(cudaMemcpyAsync(hold.p, p, sizeof(T) * count, cudaMemcpyHostToDevice, c.stream));
+    return hold.as<T>();
+}
+
+void assemble_instance(Ctx &c, const mds_instance &in, SystemData &out) {
+    MDS_REQUIRE(in.dim == 2 || in.dim == 3, MDS_ERR_INVALID, "dim must be 2 or 3");
+    MDS_REQUIRE(in.n >= 1 && in.nrhs >= 1 && in.n_f >= 0, MDS_ERR_INVALID, "bad instance sizes");
+    MDS_REQUIRE(in.km && in.pD_left && in.pD_right, MDS_ERR_INVALID, "missing instance arrays");
+    MDS_REQUIRE(in.n_f == 0 || (in.fc_axis && in.fc_pos && in.fc_kf && in.fc_a), MDS_ERR_INVALID,
+                "missing fracture arrays");
+    GridD g{};
+    g.dim = in.dim;
+    g.n = in.n;
+    int64_t n = in.n;
+    int64_t total = 0;
+    for (int d = 0; d < 3; d++) {
+        for (int a = 0; a < 3; a++) g.ext[d][a] = (a < in.dim) ? (a == d ? n + 1 : n) : 1;
+        g.off[d] = total;
+        if (d < in.dim) total += g.ext[d][0] * g.ext[d][1] * g.ext[d][2];
+    }
+    g.h = 1.0 / (double)in.n;
+    g.F = in.dim == 2 ? g.h : g.h * g.h;
+    g.elen = in.dim == 2 ? 1.0 : g.h;
+    g.n_m = in.dim == 3 ? n * n * n : n * n;
+    g.nf = in.n_f;
+    g.N = g.n_m + g.nf;
+    g.nb = in.dim == 3 ? n * n : n;
+    MDS_REQUIRE(g.N < INT32_MAX, MDS_ERR_INVALID, "too many unknowns for int32 indices");
+
+    bool dev = in.on_device != 0;
+    Buf h0, h1, h2, h3, h4, h5, h6;
+    const double *km = stage(c, in.km, (size_t)g.n_m, dev, h0);
+    const int32_t *ax = stage(c, in.fc_axis, (size_t)g.nf, dev, h1);
+    const int32_t *ps = stage(c, in.fc_pos, (size_t)(3 * g.nf), dev, h2);
+    const double *kf = stage(c, in.fc_kf, (size_t)g.nf, dev, h3);
+    const double *ap = stage(c, in.fc_a, (size_t)g.nf, dev, h4);
+    const double *pL = stage(c, in.pD_left, (size_t)(in.nrhs * g.nb), dev, h5);
+    const double *pR = stage(c, in.pD_right, (size_t)(in.nrhs * g.nb), dev, h6);
+
+    Buf map(&c, sizeof(int32_t) * (size_t)total);
+    fill_i32(c, map.as<int32_t>(), -1, total);
+    c.clear_err();
+    if (g.nf > 0)
+        MDS_LAUNCH(c, KC_NONE, 0, k_map_scatter, grid_for(g.nf, 256), 256, 0, g, ax, ps, map.as<int32_t>(), c.d_err);
+    c.check_err("fracture list");
+
+    Buf cnt(&c, sizeof(int32_t) * (size_t)(g.N + 1));
+    MDS_LAUNCH(c, KC_NONE, 0, k_count, grid_for(g.N, 128), 128, 0, g, map.as<int32_t>(), km, ax, ps, kf, ap,
+               cnt.as<int32_t>());
+    DCsr &A = out.full;
+    A.nrow = A.ncol = g.N;
+    A.rp = Buf(&c, sizeof(int32_t) * (size_t)(g.N + 1));
+    A.nnz = scan_counts(c, cnt.as<int32_t>(), A.rowp(), g.N);
+    A.ci = Buf(&c, sizeof(int32_t) * (size_t)A.nnz);
+    A.v = Buf(&c, sizeof(double) * (size_t)A.nnz);
+    out.b = Buf(&c, sizeof(double) * (size_t)(g.N * in.nrhs));
+    MDS_LAUNCH(c, KC_NONE, 0, k_fill, grid_for(g.N, 128), 128, 0, g, map.as<int32_t>(), km, ax, ps, kf, ap, in.nrhs,
+               pL, pR, A.rowp(), A.cols(), A.vals(), out.b.as<double>());
+    out.n_m = g.n_m;
+    out.n_f = g.nf;
+    out.nrhs = in.nrhs;
+    split_blocks(c, A.view(), g.n_m, out.blk);
+    c.sync();  // staged host copies are released on return
+}
+
+}  // namespace mds

@@ -1,0 +1,182 @@
+// Coarsest-level dense solve: FP64 Cholesky A = L L^T (blocked, right-looking)
+// followed by the explicit inverse A^-1 = L^-T L^-1 (one warp per column), so
+// that each V-cycle applies the coarsest solve as one parallel dense
+// matrix-vector product instead of two sequential triangular solves.
+#include "internal.cuh"
+
+namespace mds {
+
+constexpr int NB = 32;
+
+__global__ void k_densify(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                          const double *__restrict__ v, double *__restrict__ D) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int32_t p = rp[i]; p < rp[i + 1]; p++) D[i * n + ci[p]] = v[p];
+}
+
+// factor the nb x nb diagonal tile at k0 in shared memory
+__global__ void k_chol_diag(double *D, int64_t n, int64_t k0, int nb, int *err) {
+    __shared__ double T[NB][NB + 1];
+    __shared__ int bad;
+    int t = threadIdx.x;
+    if (t == 0) bad = 0;
+    for (int q = t; q < nb * nb; q += blockDim.x) {
+        int i = q / nb, j = q % nb;
+        T[i][j] = D[(k0 + i) * n + k0 + j];
+    }
+    __syncthreads();
+    for (int j = 0; j < nb; j++) {
+        if (t == 0) {
+            double s = T[j][j];
+            if (!(s > 0.0)) {
+                bad = 1;
+                s = 1.0;
+            }
+            T[j][j] = sqrt(s);
+        }
+        __syncthreads();
+        for (int i = j + 1 + t; i < nb; i += blockDim.x) T[i][j] /= T[j][j];
+        __syncthreads();
+        for (int q = t; q < nb * nb; q += blockDim.x) {
+            int i = q / nb, k = q % nb;
+            if (k > j && i >= k) T[i][k] -= T[i][j] * T[k][j];
+        }
+        __syncthreads();
+    }
+    for (int q = t; q < nb * nb; q += blockDim.x) {
+        int i = q / nb, j = q % nb;
+        if (i >= j) D[(k0 + i) * n + k0 + j] = T[i][j];
+    }
+    if (t == 0 && bad) atomicOr(err, DERR_NOT_SPD);
+}
+
+// rows below the panel: L21 = A21 L11^-T, one thread per row
+__global__ void k_chol_trsm(double *D, int64_t n, int64_t k0, int nb) {
+    __shared__ double L[NB][NB + 1];
+    for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
+        int i = q / nb, j = q % nb;
+        L[i][j] = D[(k0 + i) * n + k0 + j];
+    }
+    __syncthreads();
+    int64_t i = k0 + nb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x[NB];
+    for (int j = 0; j < nb; j++) {
+        double s = D[i * n + k0 + j];
+        for (int k = 0; k < j; k++) s -= x[k] * L[j][k];
+        x[j] = s / L[j][j];
+    }
+    for (int j = 0; j < nb; j++) D[i * n + k0 + j] = x[j];
+}
+
+// trailing update A22 -= L21 L21^T on the lower tiles
+__global__ void k_chol_update(double *D, int64_t n, int64_t k0, int nb) {
+    __shared__ double Li[NB][NB + 1], Lj[NB][NB + 1];
+    int64_t base = k0 + nb;
+    int64_t b = blockIdx.x;
+    // map b -> (bi, bj), bj <= bi
+    int64_t bi = (int64_t)((sqrt(8.0 * (double)b + 1.0) - 1.0) / 2.0);
+    while ((bi + 1) * (bi + 2) / 2 <= b) bi++;
+    while (bi * (bi + 1) / 2 > b) bi--;
+    int64_t bj = b - bi * (bi + 1) / 2;
+    int64_t r0 = base + bi * NB, c0 = base + bj * NB;
+    for (int q = threadIdx.x; q < NB * nb; q += blockDim.x) {
+        int r = q / nb, k = q % nb;
+        Li[r][k] = (r0 + r < n) ? D[(r0 + r) * n + k0 + k] : 0.0;
+        Lj[r][k] = (c0 + r < n) ? D[(c0 + r) * n + k0 + k] : 0.0;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) {
+        int r = q / NB, s = q % NB;
+        int64_t gi = r0 + r, gj = c0 + s;
+        if (gi >= n || gj >= n || gj > gi) continue;
+        double acc = 0.0;
+        for (int k = 0; k < nb; k++) acc += Li[r][k] * Lj[s][k];
+        D[gi * n + gj] -= acc;
+    }
+}
+
+__global__ void k_transpose_lower(const double *__restrict__ L, double *__restrict__ U, int64_t n) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n * n) return;
+    int64_t i = q / n, j = q % n;
+    U[j * n + i] = (i >= j) ? L[i * n + j] : 0.0;
+}
+
+// column j of A^-1: L y = e_j, then L^T x = y (x overwrites y); one warp per column
+__global__ void k_chol_inverse(const double *__restrict__ L, const double *__restrict__ U, int64_t n,
+                               double *__restrict__ X) {
+    extern __shared__ double ys[];
+    int wpb = blockDim.x / 32;
+    int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+    int64_t j = (int64_t)blockIdx.x * wpb + w;
+    if (j >= n) return;
+    double *y = ys + (size_t)w * n;
+    for (int64_t i = lane; i < n; i += 32) y[i] = 0.0;
+    __syncwarp();
+    for (int64_t i = j; i < n; i++) {
+        double s = 0.0;
+        for (int64_t k = j + lane; k < i; k += 32) s += L[i * n + k] * y[k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) y[i] = ((i == j ? 1.0 : 0.0) - s) / L[i * n + i];
+        __syncwarp();
+    }
+    for (int64_t i = n - 1; i >= 0; i--) {
+        double s = 0.0;
+        for (int64_t k = i + 1 + lane; k < n; k += 32) s += U[i * n + k] * y[k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) y[i] = (y[i] - s) / L[i * n + i];
+        __syncwarp();
+    }
+    for (int64_t i = lane; i < n; i += 32) X[j * n + i] = y[i];
+}
+
+void dense_spd_inverse(Ctx &c, const mds_csr &A, Buf &Ainv) {
+    int64_t n = A.nrow;
+    MDS_REQUIRE(n >= 1 && n <= 8192, MDS_ERR_INVALID, "coarsest level size out of range for dense Cholesky");
+    Buf D(&c, sizeof(double) * (size_t)(n * n));
+    MDS_CUDA(cudaMemsetAsync(D.p, 0, sizeof(double) * (size_t)(n * n), c.stream));
+    MDS_LAUNCH(c, KC_NONE, 0, k_densify, grid_for(n, 128), 128, 0, n, A.row_ptr, A.col, A.val, D.as<double>());
+    c.clear_err();
+    for (int64_t k0 = 0; k0 < n; k0 += NB) {
+        int nb = (int)((n - k0) < NB ? (n - k0) : NB);
+        MDS_LAUNCH(c, KC_NONE, 0, k_chol_diag, 1, 256, 0, D.as<double>(), n, k0, nb, c.d_err);
+        int64_t rest = n - k0 - nb;
+        if (rest <= 0) break;
+        MDS_LAUNCH(c, KC_NONE, 0, k_chol_trsm, grid_for(rest, 64), 64, 0, D.as<double>(), n, k0, nb);
+        int64_t m = (rest + NB - 1) / NB;
+        MDS_LAUNCH(c, KC_NONE, 0, k_chol_update, (unsigned)(m * (m + 1) / 2), 256, 0, D.as<double>(), n, k0, nb);
+    }
+    c.check_err("coarsest Cholesky");
+    Buf U(&c, sizeof(double) * (size_t)(n * n));
+    MDS_LAUNCH(c, KC_NONE, 0, k_transpose_lower, grid_for(n * n, 256), 256, 0, D.as<double>(), U.as<double>(), n);
+    Ainv = Buf(&c, sizeof(double) * (size_t)(n * n));
+    int wpb = 4;
+    while (wpb > 1 && (size_t)wpb * n * sizeof(double) > 48 * 1024) wpb /= 2;
+    size_t smem = (size_t)wpb * n * sizeof(double);
+    if (smem > 48 * 1024) MDS_CUDA(cudaFuncSetAttribute(k_chol_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MDS_LAUNCH(c, KC_NONE, 0, k_chol_inverse, grid_for(n, wpb), 32 * wpb, smem, D.as<double>(), U.as<double>(), n,
+               Ainv.as<double>());
+}
+
+template <class XT>
+__global__ void k_gemv(const double *__restrict__ M, int64_t n, const XT *__restrict__ x, XT *__restrict__ y) {
+    int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    int lane = threadIdx.x % 32;
+    if (row >= n) return;
+    double s = 0.0;
+    for (int64_t k = lane; k < n; k += 32) s += M[row * n + k] * (double)x[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) y[row] = (XT)s;
+}
+
+void dense_gemv_f64(Ctx &c, const double *M, int64_t n, const double *x, double *y) {
+    MDS_LAUNCH(c, KC_NONE, 8.0 * n * n + 16.0 * n, k_gemv<double>, grid_for(n * 32, 256), 256, 0, M, n, x, y);
+}
+
+void dense_gemv_f32(Ctx &c, const double *M, int64_t n, const float *x, float *y) {
+    MDS_LAUNCH(c, KC_NONE, 8.0 * n * n + 8.0 * n, k_gemv<float>, grid_for(n * 32, 256), 256, 0, M, n, x, y);
+}
+
+}  // namespace mds

@@ -1,0 +1,355 @@
+// Krylov solvers in FP64: right-preconditioned flexible GMRES(m) with
+// classical Gram-Schmidt applied twice (CGS2) and device-side Givens
+// rotations, and preconditioned conjugate gradients.  Sec. 3.2 studies the
+// right-preconditioned operator A B_L; Sec. 4 fixes x0 = 0 and a relative-
+// residual stopping rule.  All reductions are two-stage with a fixed order,
+// so results are run-to-run reproducible.
+#include <cmath>
+#include <functional>
+
+#include "internal.cuh"
+#include "krylov.cuh"
+
+namespace mds {
+
+constexpr int QMAX = 32;
+constexpr int RED_BLOCK = 256;
+
+static unsigned red_grid(int64_t n) {
+    int64_t g = (n + RED_BLOCK * 4 - 1) / (RED_BLOCK * 4);
+    if (g < 1) g = 1;
+    if (g > 1216) g = 1216;  // 8 blocks per SM on 152 SMs
+    return (unsigned)g;
+}
+
+// partial[blk][q] = sum_i V[q][i] w[i] over this block's rows
+__global__ void __launch_bounds__(RED_BLOCK) k_mdot(int64_t n, const double *__restrict__ V, int64_t ldv, int nq,
+                                                     const double *__restrict__ w, double *__restrict__ partial) {
+    __shared__ double ws[RED_BLOCK / 32][QMAX];
+    double acc[QMAX];
+#pragma unroll
+    for (int q = 0; q < QMAX; q++) acc[q] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double wi = w[i];
+#pragma unroll
+        for (int q = 0; q < QMAX; q++)
+            if (q < nq) acc[q] += V[q * ldv + i] * wi;
+    }
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < QMAX; q++) {
+        if (q < nq) {
+            double s = acc[q];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (lane == 0) ws[wid][q] = s;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < nq) {
+        double s = 0.0;
+        for (int k = 0; k < RED_BLOCK / 32; k++) s += ws[k][threadIdx.x];
+        partial[(int64_t)blockIdx.x * QMAX + threadIdx.x] = s;
+    }
+}
+
+// out[q] (+)= sum over blocks of partial[blk][q], fixed order
+__global__ void k_reduce_cols(const double *__restrict__ partial, int nblk, int nq, double *__restrict__ out,
+                              int accumulate) {
+    int q = threadIdx.x;
+    if (q >= nq) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; b++) s += partial[(int64_t)b * QMAX + q];
+    out[q] = accumulate ? out[q] + s : s;
+}
+
+// w_i += sign * sum_q coef_q V[q][i]; optional block partials of w_i^2
+template <int SIGN>
+__global__ void __launch_bounds__(RED_BLOCK) k_maxpy(int64_t n, const double *__restrict__ V, int64_t ldv, int nq,
+                                                      const double *__restrict__ coef, double *__restrict__ w,
+                                                      double *__restrict__ partial) {
+    __shared__ double cs[QMAX];
+    __shared__ double ws[RED_BLOCK / 32];
+    if (threadIdx.x < QMAX) cs[threadIdx.x] = threadIdx.x < nq ? coef[threadIdx.x] : 0.0;
+    __syncthreads();
+    double nrm = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < QMAX; q++)
+            if (q < nq) s += cs[q] * V[q * ldv + i];
+        double wi = SIGN > 0 ? w[i] + s : w[i] - s;
+        w[i] = wi;
+        nrm += wi * wi;
+    }
+    if (partial) {
+        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
+        if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = nrm;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int k = 0; k < RED_BLOCK / 32; k++) s += ws[k];
+            partial[(int64_t)blockIdx.x * QMAX] = s;
+        }
+    }
+}
+
+// block partials of sum a_i b_i
+__global__ void __launch_bounds__(RED_BLOCK) k_dot(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
+                                                    double *__restrict__ partial) {
+    __shared__ double ws[RED_BLOCK / 32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += a[i] * b[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < RED_BLOCK / 32; k++) t += ws[k];
+        partial[(int64_t)blockIdx.x * QMAX] = t;
+    }
+}
+
+__global__ void k_scale(int64_t n, const double *__restrict__ w, const double *__restrict__ f, double *__restrict__ o) {
+    double s = *f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        o[i] = w[i] * s;
+}
+
+// scal[0] = beta = sqrt(normsq); g = (beta, 0, ...); scal[1] = 1/beta
+__global__ void k_cycle_start(const double *__restrict__ normsq, double *__restrict__ g, int m,
+                              double *__restrict__ scal) {
+    double beta = sqrt(normsq[0]);
+    scal[0] = beta;
+    scal[1] = beta > 0.0 ? 1.0 / beta : 0.0;
+    g[0] = beta;
+    for (int q = 1; q <= m; q++) g[q] = 0.0;
+}
+
+// Arnoldi column j: H[0..j][j] = h, H[j+1][j] = ||w||; apply the previous
+// rotations, form the new one, update g.  scal[2] = |g_{j+1}|, scal[3] =
+// 1/H[j+1][j] (0 on breakdown), scal[4] = breakdown flag.
+__global__ void k_arnoldi(int j, int m, double *__restrict__ H, const double *__restrict__ h,
+                          const double *__restrict__ normsq, double *__restrict__ cs, double *__restrict__ sn,
+                          double *__restrict__ g, double *__restrict__ scal) {
+    for (int q = 0; q <= j; q++) H[q * m + j] = h[q];
+    double hn = sqrt(normsq[0]);
+    H[(j + 1) * m + j] = hn;
+    for (int q = 0; q < j; q++) {
+        double a = H[q * m + j], c = H[(q + 1) * m + j];
+        H[q * m + j] = cs[q] * a + sn[q] * c;
+        H[(q + 1) * m + j] = -sn[q] * a + cs[q] * c;
+    }
+    double a = H[j * m + j], c = H[(j + 1) * m + j];
+    double rr = sqrt(a * a + c * c);
+    cs[j] = rr == 0.0 ? 1.0 : a / rr;
+    sn[j] = rr == 0.0 ? 0.0 : c / rr;
+    H[j * m + j] = rr;
+    H[(j + 1) * m + j] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    scal[2] = fabs(g[j + 1]);
+    bool bad = !(hn > 0.0) || !isfinite(hn) || !isfinite(rr);
+    scal[3] = bad ? 0.0 : 1.0 / hn;
+    scal[4] = !isfinite(hn) || !isfinite(rr) ? 2.0 : (hn == 0.0 ? 1.0 : 0.0);
+}
+
+// upper-triangular solve H y = g (k columns)
+__global__ void k_backsolve(int k, int m, const double *__restrict__ H, const double *__restrict__ g,
+                            double *__restrict__ y) {
+    for (int q = k - 1; q >= 0; q--) {
+        double s = g[q];
+        for (int p = q + 1; p < k; p++) s -= H[q * m + p] * y[p];
+        y[q] = H[q * m + q] == 0.0 ? 0.0 : s / H[q * m + q];
+    }
+}
+
+// PCG helpers
+__global__ void k_pcg_p(int64_t n, const double *__restrict__ z, double *__restrict__ p, const double *__restrict__ sc,
+                        int first) {
+    double beta = first ? 0.0 : sc[0] / sc[1];  // rz_new / rz
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = first ? z[i] : z[i] + beta * p[i];
+}
+
+__global__ void __launch_bounds__(RED_BLOCK) k_pcg_xr(int64_t n, double *__restrict__ x, double *__restrict__ r,
+                                                       const double *__restrict__ p, const double *__restrict__ q,
+                                                       const double *__restrict__ sc, double *__restrict__ partial) {
+    __shared__ double ws[RED_BLOCK / 32];
+    double alpha = sc[0] / sc[2];  // rz / (p, q)
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] += alpha * p[i];
+        double ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        s += ri * ri;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < RED_BLOCK / 32; k++) t += ws[k];
+        partial[(int64_t)blockIdx.x * QMAX] = t;
+    }
+}
+
+__global__ void k_copy1(const double *__restrict__ a, double *__restrict__ b) { *b = *a; }
+
+// ---------------------------------------------------------------- host side
+
+struct Red {
+    Buf partial;
+    unsigned grid = 1;
+};
+
+static void dot_dev(Ctx &c, Red &R, int64_t n, const double *a, const double *b, double *out) {
+    MDS_LAUNCH(c, KC_NONE, 16.0 * n, k_dot, R.grid, RED_BLOCK, 0, n, a, b, R.partial.as<double>());
+    MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.partial.as<double>(), (int)R.grid, 1, out, 0);
+}
+
+KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, double *x, int64_t n,
+                    const mds_solve_opts &o) {
+    KrylovResult res;
+    const int m = o.restart < 1 ? 1 : (o.restart > QMAX - 1 ? QMAX - 1 : o.restart);
+    Red R;
+    R.grid = red_grid(n);
+    R.partial = Buf(&c, sizeof(double) * (size_t)R.grid * QMAX);
+    Buf V(&c, sizeof(double) * (size_t)(m + 1) * (size_t)n);
+    Buf Z(&c, sizeof(double) * (size_t)m * (size_t)n);
+    Buf H(&c, sizeof(double) * (size_t)(m + 1) * m);
+    Buf small(&c, sizeof(double) * 256);
+    double *d = small.as<double>();
+    // cs, sn, g, y, h (first CGS pass), h + 32 (second pass), scalars, norms
+    double *cs = d, *sn = d + 32, *g = d + 64, *y = d + 96, *h = d + 128, *scal = d + 192, *nsq = d + 224;
+    double *Vp = V.as<double>(), *Zp = Z.as<double>();
+    // ||b||
+    dot_dev(c, R, n, b, b, nsq);
+    double bn = std::sqrt(c.read(nsq));
+    if (!(bn < INFINITY)) {
+        res.status = MDS_ERR_NONFINITE;
+        return res;
+    }
+    if (bn == 0.0) bn = 1.0;
+    int it = 0, restarts = 0;
+    double est = 0.0;
+    for (;;) {
+        spmv_sub_f64(c, A, b, x, Vp);  // V0 = b - A x
+        dot_dev(c, R, n, Vp, Vp, nsq);
+        MDS_LAUNCH(c, KC_NONE, 0, k_cycle_start, 1, 1, 0, nsq, g, m, scal);
+        double beta = c.read(scal);
+        if (!std::isfinite(beta)) {
+            res.status = MDS_ERR_NONFINITE;
+            break;
+        }
+        est = beta / bn;
+        if (est <= o.rtol) {
+            res.status = MDS_OK;
+            break;
+        }
+        if (it >= o.max_iters) {
+            res.status = MDS_WARN_NOT_CONVERGED;
+            break;
+        }
+        MDS_LAUNCH(c, KC_NONE, 16.0 * n, k_scale, red_grid(n), RED_BLOCK, 0, n, Vp, scal + 1, Vp);
+        int kdone = 0;
+        int flag = 0;
+        for (int j = 0; j < m; j++) {
+            double *vj = Vp + (size_t)j * n, *zj = Zp + (size_t)j * n, *w = Vp + (size_t)(j + 1) * n;
+            M(vj, zj);
+            it++;
+            spmv_f64(c, A, zj, w, KC_SPMV);
+            // CGS2: h = V^T w; w -= V h; twice
+            int nq = j + 1;
+            for (int pass = 0; pass < 2; pass++) {
+                MDS_LAUNCH(c, KC_GS_DOT, 8.0 * n * (nq + 1), k_mdot, R.grid, RED_BLOCK, 0, n, Vp, n, nq, w,
+                           R.partial.as<double>());
+                MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.partial.as<double>(), (int)R.grid, nq,
+                           pass == 0 ? h : h + 32, 0);
+                MDS_LAUNCH(c, KC_GS_AXPY, 8.0 * n * (nq + 2), k_maxpy<-1>, R.grid, RED_BLOCK, 0, n, Vp, n, nq,
+                           pass == 0 ? h : h + 32, w, pass == 1 ? R.partial.as<double>() : nullptr);
+            }
+            MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.partial.as<double>(), (int)R.grid, 1, nsq, 0);
+            // h += h2
+            MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, h + 32, 1, nq, h, 1);
+            MDS_LAUNCH(c, KC_NONE, 0, k_arnoldi, 1, 1, 0, j, m, H.as<double>(), h, nsq, cs, sn, g, scal);
+            MDS_LAUNCH(c, KC_NONE, 16.0 * n, k_scale, red_grid(n), RED_BLOCK, 0, n, w, scal + 3, w);
+            MDS_CUDA(cudaMemcpyAsync(c.h_pin, scal, 5 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+            c.sync();
+            double sv[5];
+            std::memcpy(sv, c.h_pin, sizeof sv);
+            est = sv[2] / bn;
+            kdone = j + 1;
+            if (sv[4] == 2.0 || !std::isfinite(est)) {
+                flag = 2;
+                break;
+            }
+            if (est <= o.rtol || it >= o.max_iters || sv[4] == 1.0) break;
+        }
+        if (flag == 2) {
+            res.status = MDS_ERR_BREAKDOWN;
+            break;
+        }
+        MDS_LAUNCH(c, KC_NONE, 0, k_backsolve, 1, 1, 0, kdone, m, H.as<double>(), g, y);
+        MDS_LAUNCH(c, KC_NONE, 8.0 * n * (kdone + 2), k_maxpy<1>, R.grid, RED_BLOCK, 0, n, Zp, n, kdone, y, x,
+                   nullptr);
+        restarts++;
+    }
+    // true residual at exit
+    spmv_sub_f64(c, A, b, x, Vp);
+    dot_dev(c, R, n, Vp, Vp, nsq);
+    res.relres_true = std::sqrt(c.read(nsq)) / bn;
+    res.iterations = it;
+    res.restarts = restarts;
+    res.relres_est = est;
+    return res;
+}
+
+KrylovResult pcg(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, double *x, int64_t n,
+                 const mds_solve_opts &o) {
+    KrylovResult res;
+    Red R;
+    R.grid = red_grid(n);
+    R.partial = Buf(&c, sizeof(double) * (size_t)R.grid * QMAX);
+    Buf rb(&c, sizeof(double) * (size_t)n), zb(&c, sizeof(double) * (size_t)n), pb(&c, sizeof(double) * (size_t)n),
+        qb(&c, sizeof(double) * (size_t)n);
+    Buf small(&c, sizeof(double) * 8);
+    double *sc = small.as<double>();  // [rz_new, rz, pq, rn2, bn2]
+    double *r = rb.as<double>(), *z = zb.as<double>(), *p = pb.as<double>(), *q = qb.as<double>();
+    dot_dev(c, R, n, b, b, sc + 4);
+    double bn = std::sqrt(c.read(sc + 4));
+    if (!(bn < INFINITY)) {
+        res.status = MDS_ERR_NONFINITE;
+        return res;
+    }
+    if (bn == 0.0) bn = 1.0;
+    spmv_sub_f64(c, A, b, x, r);
+    dot_dev(c, R, n, r, r, sc + 3);
+    double rn = std::sqrt(c.read(sc + 3));
+    int it = 0;
+    while (rn / bn > o.rtol && it < o.max_iters) {
+        M(r, z);
+        it++;
+        dot_dev(c, R, n, r, z, sc);  // rz_new
+        MDS_LAUNCH(c, KC_NONE, 24.0 * n, k_pcg_p, red_grid(n), RED_BLOCK, 0, n, z, p, sc, it == 1 ? 1 : 0);
+        MDS_LAUNCH(c, KC_NONE, 0, k_copy1, 1, 1, 0, sc, sc + 1);  // rz = rz_new
+        spmv_f64(c, A, p, q, KC_SPMV);
+        dot_dev(c, R, n, p, q, sc + 2);
+        MDS_LAUNCH(c, KC_NONE, 56.0 * n, k_pcg_xr, R.grid, RED_BLOCK, 0, n, x, r, p, q, sc, R.partial.as<double>());
+        MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.partial.as<double>(), (int)R.grid, 1, sc + 3, 0);
+        rn = std::sqrt(c.read(sc + 3));
+        if (!std::isfinite(rn)) {
+            res.status = MDS_ERR_BREAKDOWN;
+            break;
+        }
+    }
+    spmv_sub_f64(c, A, b, x, r);
+    dot_dev(c, R, n, r, r, sc + 3);
+    res.relres_true = std::sqrt(c.read(sc + 3)) / bn;
+    res.relres_est = rn / bn;
+    res.iterations = it;
+    if (res.status != MDS_ERR_BREAKDOWN) res.status = res.relres_true <= o.rtol ? MDS_OK : MDS_WARN_NOT_CONVERGED;
+    return res;
+}
+
+}  // namespace mds

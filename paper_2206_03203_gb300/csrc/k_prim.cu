@@ -1,0 +1,174 @@
+// Primitives: scan, fills, precision casts, CSR SpMV.
+#include "internal.cuh"
+#include "spmv.cuh"
+
+namespace mds {
+
+// ---------------------------------------------------------------- scan
+
+constexpr int SCAN_BLOCK = 1024;
+
+__global__ void k_scan_block(const int32_t *__restrict__ cnt, int64_t n, int32_t *__restrict__ out,
+                             int64_t *__restrict__ bsum) {
+    __shared__ int64_t wsum[32];
+    int64_t i = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
+    int64_t v = i < n ? (int64_t)cnt[i] : 0;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t s = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += t;
+    }
+    if (lane == 31) wsum[w] = s;
+    __syncthreads();
+    if (w == 0) {
+        int64_t ws = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t t = __shfl_up_sync(0xffffffffu, ws, o);
+            if (lane >= o) ws += t;
+        }
+        wsum[lane] = ws;
+    }
+    __syncthreads();
+    int64_t incl = s + (w > 0 ? wsum[w - 1] : 0);
+    if (i < n) out[i] = (int32_t)(incl - v);  // block-local exclusive
+    if (threadIdx.x == SCAN_BLOCK - 1) bsum[blockIdx.x] = incl;
+}
+
+// exclusive scan of the block sums in place (one block, chunks of 1024)
+__global__ void k_scan_bsums(int64_t *__restrict__ bsum, int64_t nb, int64_t *__restrict__ total) {
+    __shared__ int64_t wsum[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t base = 0; base < nb; base += SCAN_BLOCK) {
+        int64_t i = base + threadIdx.x;
+        int64_t v = i < nb ? bsum[i] : 0;
+        int64_t s = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t t = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += t;
+        }
+        if (lane == 31) wsum[w] = s;
+        __syncthreads();
+        if (w == 0) {
+            int64_t ws = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int64_t t = __shfl_up_sync(0xffffffffu, ws, o);
+                if (lane >= o) ws += t;
+            }
+            wsum[lane] = ws;
+        }
+        __syncthreads();
+        int64_t incl = s + (w > 0 ? wsum[w - 1] : 0);
+        if (i < nb) bsum[i] = carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == SCAN_BLOCK - 1) carry += incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_add(int32_t *__restrict__ out, int64_t n, const int64_t *__restrict__ bsum,
+                           const int64_t *__restrict__ total) {
+    int64_t i = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
+    if (i < n) out[i] = (int32_t)((int64_t)out[i] + bsum[blockIdx.x]);
+    if (i == n) out[n] = (int32_t)*total;
+}
+
+int64_t scan_counts(Ctx &c, const int32_t *cnt, int32_t *out, int64_t n) {
+    int64_t nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    if (nb < 1) nb = 1;
+    Buf bs(&c, sizeof(int64_t) * (size_t)(nb + 1));
+    int64_t *bsum = bs.as<int64_t>();
+    int64_t *total = bsum + nb;
+    MDS_LAUNCH(c, KC_NONE, 0, k_scan_block, (unsigned)nb, SCAN_BLOCK, 0, cnt, n, out, bsum);
+    MDS_LAUNCH(c, KC_NONE, 0, k_scan_bsums, 1, SCAN_BLOCK, 0, bsum, nb, total);
+    // one extra thread writes out[n]
+    int64_t nb2 = (n + 1 + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    MDS_LAUNCH(c, KC_NONE, 0, k_scan_add, (unsigned)nb2, SCAN_BLOCK, 0, out, n, bsum, total);
+    int64_t t = c.read(total);
+    MDS_REQUIRE(t <= INT32_MAX, MDS_ERR_INVALID, "sparse matrix exceeds 2^31-1 nonzeros");
+    return t;
+}
+
+// ---------------------------------------------------------------- fills, casts
+
+template <class T>
+__global__ void k_fill(T *__restrict__ p, T v, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+void fill_i32(Ctx &c, int32_t *p, int32_t v, int64_t n) {
+    if (n <= 0) return;
+    MDS_LAUNCH(c, KC_NONE, 0, k_fill<int32_t>, grid_for(n, 256) > 4096 ? 4096 : grid_for(n, 256), 256, 0, p, v, n);
+}
+
+void fill_f64(Ctx &c, double *p, double v, int64_t n) {
+    if (n <= 0) return;
+    MDS_LAUNCH(c, KC_NONE, 0, k_fill<double>, grid_for(n, 256) > 4096 ? 4096 : grid_for(n, 256), 256, 0, p, v, n);
+}
+
+template <class A, class B>
+__global__ void k_cast(const A *__restrict__ in, B *__restrict__ out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (B)in[i];
+}
+
+void cast_f64_f32(Ctx &c, const double *in, float *out, int64_t n) {
+    if (n <= 0) return;
+    unsigned g = grid_for(n, 256);
+    MDS_LAUNCH(c, KC_NONE, 0, (k_cast<double, float>), g, 256, 0, in, out, n);
+}
+
+void cast_f32_f64(Ctx &c, const float *in, double *out, int64_t n) {
+    if (n <= 0) return;
+    unsigned g = grid_for(n, 256);
+    MDS_LAUNCH(c, KC_NONE, 0, (k_cast<float, double>), g, 256, 0, in, out, n);
+}
+
+// ---------------------------------------------------------------- SpMV
+
+template <int G, class XT, class OT, int MODE>
+static void spmv_launch(Ctx &c, const mds_csr &A, const XT *x, const double *r, OT *y, int kclass) {
+    const int block = 256;
+    unsigned grid = grid_for(A.nrow * G, block);
+    double bytes = 12.0 * (double)A.nnz + 4.0 * (double)(A.nrow + 1) + sizeof(XT) * (double)A.ncol +
+                   sizeof(OT) * (double)A.nrow + (MODE == 1 ? 8.0 * A.nrow : 0.0);
+    MDS_LAUNCH(c, kclass, bytes, (k_spmv_csr<G, double, XT, OT, MODE>), grid, block, 0, A.nrow, A.row_ptr,
+               A.col, A.val, x, r, y);
+}
+
+template <class XT, class OT, int MODE>
+static void spmv_dispatch(Ctx &c, const mds_csr &A, const XT *x, const double *r, OT *y, int kclass) {
+    if (A.nrow <= 0) return;
+    double avg = A.nrow ? (double)A.nnz / (double)A.nrow : 0.0;
+    if (avg <= 4.0)
+        spmv_launch<2, XT, OT, MODE>(c, A, x, r, y, kclass);
+    else if (avg <= 10.0)
+        spmv_launch<4, XT, OT, MODE>(c, A, x, r, y, kclass);
+    else if (avg <= 24.0)
+        spmv_launch<8, XT, OT, MODE>(c, A, x, r, y, kclass);
+    else
+        spmv_launch<32, XT, OT, MODE>(c, A, x, r, y, kclass);
+}
+
+void spmv_f64(Ctx &c, const mds_csr &A, const double *x, double *y, int kclass) {
+    spmv_dispatch<double, double, 0>(c, A, x, nullptr, y, kclass);
+}
+
+void spmv_sub_f64(Ctx &c, const mds_csr &A, const double *r, const double *x, double *out) {
+    spmv_dispatch<double, double, 1>(c, A, x, r, out, KC_NONE);
+}
+
+void spmv_sub_f64_xf(Ctx &c, const mds_csr &A, const double *r, const float *x, float *out) {
+    spmv_dispatch<float, float, 1>(c, A, x, r, out, KC_NONE);
+}
+
+}  // namespace mds

@@ -1,0 +1,542 @@
+// Set-up on the GPU: the approximate Schur complement of Eq. (7) and the
+// aggregation-AMG hierarchy used for one V-cycle per diagonal block
+// (Sec. 3.3): strength graph, deterministic parallel MIS-2 with hash
+// priorities, aggregates, piecewise-constant P, Galerkin P^T A P, L1
+// diagonals.  Compiled with -fmad=false and a fixed summation order so that
+// sparsity, aggregates and FP64 values are reproducible to the bit.
+#include "internal.cuh"
+
+namespace mds {
+
+constexpr int SCHUR_CAP = 64;
+constexpr int RAP_CAP = 512;
+
+__device__ __forceinline__ int32_t find_col(const int32_t *ci, int32_t a, int32_t e, int32_t j) {
+    // binary search in a sorted row segment; -1 if absent
+    int32_t lo = a, hi = e - 1;
+    while (lo <= hi) {
+        int32_t m = (lo + hi) >> 1;
+        int32_t c = ci[m];
+        if (c == j) return m;
+        if (c < j)
+            lo = m + 1;
+        else
+            hi = m - 1;
+    }
+    return -1;
+}
+
+__global__ void k_diag(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                       const double *__restrict__ v, double *__restrict__ d, int need_nonzero, int *err) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t p = find_col(ci, rp[i], rp[i + 1], (int32_t)i);
+    double x = p >= 0 ? v[p] : 0.0;
+    d[i] = x;
+    if (need_nonzero && x == 0.0) atomicOr(err, DERR_ZERO_DIAG);
+}
+
+// ---------------------------------------------------------------- Schur (Eq. 7)
+
+// Row i of S~: start from row i of A_mm, then for each k of row i of A_mf in
+// ascending order subtract (A_mf)_ik (A_fm)_kj / d_k from entry j.
+template <bool FILL>
+__global__ void k_schur(int64_t nm, mds_csr Amm, mds_csr Amf, mds_csr Afm, const double *__restrict__ dk,
+                        int32_t *__restrict__ cnt, const int32_t *__restrict__ rp, int32_t *__restrict__ ci,
+                        double *__restrict__ val, int *err) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nm) return;
+    int32_t cols[SCHUR_CAP];
+    double acc[SCHUR_CAP];
+    int m = 0;
+    for (int32_t p = Amm.row_ptr[i]; p < Amm.row_ptr[i + 1]; p++) {
+        if (m >= SCHUR_CAP) {
+            atomicOr(err, DERR_CAPACITY);
+            return;
+        }
+        cols[m] = Amm.col[p];
+        acc[m++] = Amm.val[p];
+    }
+    for (int32_t p = Amf.row_ptr[i]; p < Amf.row_ptr[i + 1]; p++) {
+        int32_t k = Amf.col[p];
+        double a = Amf.val[p];
+        double d = dk[k];
+        for (int32_t q = Afm.row_ptr[k]; q < Afm.row_ptr[k + 1]; q++) {
+            int32_t j = Afm.col[q];
+            int t = 0;
+            while (t < m && cols[t] != j) t++;
+            if (t == m) {
+                if (m >= SCHUR_CAP) {
+                    atomicOr(err, DERR_CAPACITY);
+                    return;
+                }
+                cols[m] = j;
+                acc[m++] = 0.0;
+            }
+            acc[t] = acc[t] - (a * Afm.val[q]) / d;
+        }
+    }
+    if constexpr (!FILL) {
+        cnt[i] = m;
+        return;
+    } else {
+    for (int a = 1; a < m; a++) {
+        int32_t x = cols[a];
+        double y = acc[a];
+        int q = a - 1;
+        while (q >= 0 && cols[q] > x) {
+            cols[q + 1] = cols[q];
+            acc[q + 1] = acc[q];
+            q--;
+        }
+        cols[q + 1] = x;
+        acc[q + 1] = y;
+    }
+    int32_t o = rp[i];
+    for (int a = 0; a < m; a++) {
+        ci[o + a] = cols[a];
+        val[o + a] = acc[a];
+    }
+    }
+}
+
+DCsr schur_build(Ctx &c, const mds_csr &Amm, const mds_csr &Amf, const mds_csr &Afm, const mds_csr &Aff, Buf &dk) {
+    int64_t nm = Amm.nrow, nf = Aff.nrow;
+    dk = Buf(&c, sizeof(double) * (size_t)(nf > 0 ? nf : 1));
+    c.clear_err();
+    if (nf > 0)
+        MDS_LAUNCH(c, KC_NONE, 0, k_diag, grid_for(nf, 256), 256, 0, nf, Aff.row_ptr, Aff.col, Aff.val,
+                   dk.as<double>(), 1, c.d_err);
+    c.check_err("diag(A_ff)");
+    Buf cnt(&c, sizeof(int32_t) * (size_t)(nm + 1));
+    MDS_LAUNCH(c, KC_NONE, 0, k_schur<false>, grid_for(nm, 128), 128, 0, nm, Amm, Amf, Afm, dk.as<double>(),
+               cnt.as<int32_t>(), nullptr, nullptr, nullptr, c.d_err);
+    c.check_err("Schur complement (symbolic)");
+    DCsr S;
+    S.nrow = S.ncol = nm;
+    S.rp = Buf(&c, sizeof(int32_t) * (size_t)(nm + 1));
+    S.nnz = scan_counts(c, cnt.as<int32_t>(), S.rowp(), nm);
+    S.ci = Buf(&c, sizeof(int32_t) * (size_t)(S.nnz > 0 ? S.nnz : 1));
+    S.v = Buf(&c, sizeof(double) * (size_t)(S.nnz > 0 ? S.nnz : 1));
+    MDS_LAUNCH(c, KC_NONE, 0, k_schur<true>, grid_for(nm, 128), 128, 0, nm, Amm, Amf, Afm, dk.as<double>(), nullptr,
+               S.rowp(), S.cols(), S.vals(), c.d_err);
+    c.check_err("Schur complement");
+    return S;
+}
+
+// ---------------------------------------------------------------- strength
+
+// j != i is strong for i when a_ij^2 >= (theta^2 a_ii) a_jj; i and j are
+// linked in the graph G when either direction is strong.
+__global__ void k_strength(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           const double *__restrict__ v, const double *__restrict__ dg, double th2,
+                           int8_t *__restrict__ g, int32_t *__restrict__ deg) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int cnt = 0;
+    for (int32_t p = rp[i]; p < rp[i + 1]; p++) {
+        int32_t j = ci[p];
+        int8_t s = 0;
+        if (j != i) {
+            double a = v[p];
+            s = (a * a) >= (th2 * dg[i]) * dg[j];
+            if (!s) {
+                int32_t q = find_col(ci, rp[j], rp[j + 1], (int32_t)i);
+                if (q >= 0) {
+                    double b = v[q];
+                    s = (b * b) >= (th2 * dg[j]) * dg[i];
+                }
+            }
+        }
+        g[p] = s;
+        cnt += s;
+    }
+    deg[i] = cnt;
+}
+
+// ---------------------------------------------------------------- MIS-2
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// Priority of vertex i on a level: high 32 bits of a SplitMix64 hash, low 32
+// bits the index (unique).  Stored +1 so that 0 means "no undecided vertex".
+__device__ __forceinline__ uint64_t mis_key1(uint64_t lkey, int64_t i) {
+    uint64_t hv = mix64(lkey + 0x9E3779B97F4A7C15ULL * (uint64_t)(i + 1));
+    return ((hv & 0xFFFFFFFF00000000ULL) | (uint64_t)(uint32_t)i) + 1ULL;
+}
+
+__global__ void k_mis_init(int64_t n, const int32_t *__restrict__ deg, int8_t *__restrict__ state) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) state[i] = deg[i] == 0 ? 2 : 0;
+}
+
+// m1_i = max key over undecided vertices of {i} and its strong neighbours
+__global__ void k_mis_max1(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           const int8_t *__restrict__ g, const int8_t *__restrict__ state, uint64_t lkey,
+                           uint64_t *__restrict__ m1) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t m = state[i] == 0 ? mis_key1(lkey, i) : 0;
+    for (int32_t p = rp[i]; p < rp[i + 1]; p++) {
+        if (!g[p]) continue;
+        int32_t j = ci[p];
+        if (state[j] == 0) {
+            uint64_t k = mis_key1(lkey, j);
+            m = k > m ? k : m;
+        }
+    }
+    m1[i] = m;
+}
+
+// a vertex whose key is the largest among undecided vertices within distance
+// two becomes a root
+__global__ void k_mis_select(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                             const int8_t *__restrict__ g, const uint64_t *__restrict__ m1, uint64_t lkey,
+                             int8_t *__restrict__ state) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || state[i] != 0) return;
+    uint64_t m = m1[i];
+    for (int32_t p = rp[i]; p < rp[i + 1]; p++)
+        if (g[p]) {
+            uint64_t k = m1[ci[p]];
+            m = k > m ? k : m;
+        }
+    if (m == mis_key1(lkey, i)) state[i] = 1;
+}
+
+__global__ void k_mis_near_root(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                const int8_t *__restrict__ g, const int8_t *__restrict__ state,
+                                int8_t *__restrict__ e1) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int8_t e = state[i] == 1;
+    for (int32_t p = rp[i]; p < rp[i + 1] && !e; p++)
+        if (g[p] && state[ci[p]] == 1) e = 1;
+    e1[i] = e;
+}
+
+__global__ void k_mis_exclude(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                              const int8_t *__restrict__ g, const int8_t *__restrict__ e1, int8_t *__restrict__ state,
+                              int32_t *__restrict__ undecided) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || state[i] != 0) return;
+    bool ex = e1[i];
+    for (int32_t p = rp[i]; p < rp[i + 1] && !ex; p++)
+        if (g[p] && e1[ci[p]]) ex = true;
+    if (ex)
+        state[i] = 2;
+    else
+        atomicAdd(undecided, 1);
+}
+
+// ---------------------------------------------------------------- aggregation
+
+__global__ void k_root_flags(int64_t n, const int8_t *__restrict__ state, int8_t *__restrict__ roots,
+                             int32_t *__restrict__ flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int8_t r = state[i] == 1;
+    roots[i] = r;
+    flag[i] = r;
+}
+
+__global__ void k_agg_first(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const int8_t *__restrict__ g, const int8_t *__restrict__ roots,
+                            const int32_t *__restrict__ rootid, int32_t *__restrict__ first) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t f = -1;
+    if (roots[i]) {
+        f = rootid[i];
+    } else {
+        for (int32_t p = rp[i]; p < rp[i + 1]; p++)
+            if (g[p] && roots[ci[p]]) f = rootid[ci[p]];
+    }
+    first[i] = f;
+}
+
+__global__ void k_agg_second(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                             const double *__restrict__ v, const int8_t *__restrict__ g,
+                             const int8_t *__restrict__ roots, const int32_t *__restrict__ deg,
+                             const int32_t *__restrict__ first, int32_t *__restrict__ agg) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (first[i] >= 0 || deg[i] == 0) {
+        agg[i] = first[i];
+        return;
+    }
+    double best = -1.0;
+    int32_t ba = -1;
+    for (int32_t p = rp[i]; p < rp[i + 1]; p++) {
+        if (!g[p]) continue;
+        int32_t j = ci[p];
+        if (roots[j] || first[j] < 0) continue;
+        double w = fabs(v[p]);
+        if (w > best || (w == best && first[j] < ba)) {
+            best = w;
+            ba = first[j];
+        }
+    }
+    agg[i] = ba;
+}
+
+// ---------------------------------------------------------------- Galerkin P^T A P
+
+__global__ void k_agg_count(int64_t n, const int32_t *__restrict__ agg, int32_t *__restrict__ cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && agg[i] >= 0) atomicAdd(cnt + agg[i], 1);
+}
+
+__global__ void k_agg_scatter(int64_t n, const int32_t *__restrict__ agg, const int32_t *__restrict__ off,
+                              int32_t *__restrict__ cursor, int32_t *__restrict__ mem) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && agg[i] >= 0) {
+        int32_t q = atomicAdd(cursor + agg[i], 1);
+        mem[off[agg[i]] + q] = (int32_t)i;
+    }
+}
+
+__global__ void k_agg_sort(int64_t nc, const int32_t *__restrict__ off, int32_t *__restrict__ mem) {
+    int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    int32_t a = off[I], e = off[I + 1];
+    for (int32_t p = a + 1; p < e; p++) {
+        int32_t x = mem[p];
+        int32_t q = p - 1;
+        while (q >= a && mem[q] > x) {
+            mem[q + 1] = mem[q];
+            q--;
+        }
+        mem[q + 1] = x;
+    }
+}
+
+// Coarse row I = sum over members i of I (ascending) of row i of A mapped
+// through agg, accumulated in CSR order.
+template <bool FILL>
+__global__ void k_rap(int64_t nc, const int32_t *__restrict__ off, const int32_t *__restrict__ mem,
+                      const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
+                      const int32_t *__restrict__ agg, int32_t *__restrict__ cnt, const int32_t *__restrict__ crp,
+                      int32_t *__restrict__ cci, double *__restrict__ cv, int *err) {
+    int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    int32_t cols[RAP_CAP];
+    double acc[RAP_CAP];
+    int m = 0;
+    for (int32_t q = off[I]; q < off[I + 1]; q++) {
+        int32_t i = mem[q];
+        for (int32_t p = rp[i]; p < rp[i + 1]; p++) {
+            int32_t J = agg[ci[p]];
+            if (J < 0) continue;
+            int t = 0;
+            while (t < m && cols[t] != J) t++;
+            if (t == m) {
+                if (m >= RAP_CAP) {
+                    atomicOr(err, DERR_CAPACITY);
+                    return;
+                }
+                cols[m] = J;
+                acc[m++] = 0.0;
+            }
+            acc[t] = acc[t] + v[p];
+        }
+    }
+    if constexpr (!FILL) {
+        cnt[I] = m;
+        return;
+    } else {
+    for (int a = 1; a < m; a++) {
+        int32_t x = cols[a];
+        double y = acc[a];
+        int q = a - 1;
+        while (q >= 0 && cols[q] > x) {
+            cols[q + 1] = cols[q];
+            acc[q + 1] = acc[q];
+            q--;
+        }
+        cols[q + 1] = x;
+        acc[q + 1] = y;
+    }
+    int32_t o = crp[I];
+    for (int a = 0; a < m; a++) {
+        cci[o + a] = cols[a];
+        cv[o + a] = acc[a];
+    }
+    }
+}
+
+// ---------------------------------------------------------------- per-level data
+
+// L1 diagonal a_ii + sum_{j != i} |a_ij| and its reciprocal
+template <class DT>
+__global__ void k_l1(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                     const double *__restrict__ v, double *__restrict__ l1, DT *__restrict__ dinv) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t p = find_col(ci, rp[i], rp[i + 1], (int32_t)i);
+    double s = p >= 0 ? v[p] : 0.0;
+    for (int32_t q = rp[i]; q < rp[i + 1]; q++)
+        if (ci[q] != i) s = s + fabs(v[q]);
+    l1[i] = s;
+    dinv[i] = (DT)(1.0 / s);
+}
+
+__global__ void k_vals_f32(int64_t nnz, const double *__restrict__ v, float *__restrict__ o) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+        o[p] = (float)v[p];
+}
+
+static DCsr copy_csr(Ctx &c, const mds_csr &A) {
+    DCsr B = csr_alloc(c, A.nrow, A.ncol, A.nnz);
+    MDS_CUDA(cudaMemcpyAsync(B.rowp(), A.row_ptr, sizeof(int32_t) * (size_t)(A.nrow + 1), cudaMemcpyDeviceToDevice,
+                             c.stream));
+    if (A.nnz > 0) {
+        MDS_CUDA(cudaMemcpyAsync(B.cols(), A.col, sizeof(int32_t) * (size_t)A.nnz, cudaMemcpyDeviceToDevice, c.stream));
+        MDS_CUDA(cudaMemcpyAsync(B.vals(), A.val, sizeof(double) * (size_t)A.nnz, cudaMemcpyDeviceToDevice, c.stream));
+    }
+    return B;
+}
+
+static uint64_t host_mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// MIS-2 on the strength graph of level l: fills roots, returns their count.
+static int64_t mis2(Ctx &c, const DCsr &A, const int8_t *g, const int32_t *deg, uint64_t seed, int level,
+                    Buf &state) {
+    int64_t n = A.nrow;
+    unsigned gr = grid_for(n, 256);
+    state = Buf(&c, (size_t)(n > 0 ? n : 1));
+    Buf m1(&c, sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+    Buf e1(&c, (size_t)(n > 0 ? n : 1));
+    Buf und(&c, sizeof(int32_t));
+    uint64_t lkey = host_mix64(seed + 0x9E3779B97F4A7C15ULL * (uint64_t)(level + 1));
+    MDS_LAUNCH(c, KC_NONE, 0, k_mis_init, gr, 256, 0, n, deg, state.as<int8_t>());
+    for (int round = 0;; round++) {
+        MDS_REQUIRE(round < 10000, MDS_ERR_TIMEOUT, "MIS-2 did not terminate");
+        MDS_CUDA(cudaMemsetAsync(und.p, 0, sizeof(int32_t), c.stream));
+        MDS_LAUNCH(c, KC_NONE, 0, k_mis_max1, gr, 256, 0, n, A.rowp(), A.cols(), g, state.as<int8_t>(), lkey,
+                   m1.as<uint64_t>());
+        MDS_LAUNCH(c, KC_NONE, 0, k_mis_select, gr, 256, 0, n, A.rowp(), A.cols(), g, m1.as<uint64_t>(), lkey,
+                   state.as<int8_t>());
+        MDS_LAUNCH(c, KC_NONE, 0, k_mis_near_root, gr, 256, 0, n, A.rowp(), A.cols(), g, state.as<int8_t>(),
+                   e1.as<int8_t>());
+        MDS_LAUNCH(c, KC_NONE, 0, k_mis_exclude, gr, 256, 0, n, A.rowp(), A.cols(), g, e1.as<int8_t>(),
+                   state.as<int8_t>(), und.as<int32_t>());
+        if (c.read(und.as<int32_t>()) == 0) break;
+    }
+    return 0;
+}
+
+void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h) {
+    h.lv.clear();
+    h.dense = false;
+    h.prec = o.precision == MDS_PREC_FP64 ? 64 : 32;
+    h.smoother = o.smoother;
+    int maxl = o.max_levels < 1 ? 1 : (o.max_levels > 32 ? 32 : o.max_levels);
+    h.lv.emplace_back();
+    h.lv[0].A = copy_csr(c, A0);
+    double th2 = o.theta * o.theta;
+    for (int l = 0;; l++) {
+        Level &L = h.lv[l];
+        int64_t n = L.A.nrow;
+        L.roots = Buf(&c, (size_t)(n > 0 ? n : 1));
+        MDS_CUDA(cudaMemsetAsync(L.roots.p, 0, (size_t)(n > 0 ? n : 1), c.stream));
+        if (n <= o.n_coarse) {
+            h.dense = true;
+            break;
+        }
+        if (l == maxl - 1) break;
+        unsigned gr = grid_for(n, 256);
+        Buf dg(&c, sizeof(double) * (size_t)n), gf(&c, (size_t)(L.A.nnz > 0 ? L.A.nnz : 1));
+        Buf deg(&c, sizeof(int32_t) * (size_t)(n + 1));
+        MDS_LAUNCH(c, KC_NONE, 0, k_diag, gr, 256, 0, n, L.A.rowp(), L.A.cols(), L.A.vals(), dg.as<double>(), 0,
+                   c.d_err);
+        MDS_LAUNCH(c, KC_NONE, 0, k_strength, gr, 256, 0, n, L.A.rowp(), L.A.cols(), L.A.vals(), dg.as<double>(), th2,
+                   gf.as<int8_t>(), deg.as<int32_t>());
+        Buf state;
+        mis2(c, L.A, gf.as<int8_t>(), deg.as<int32_t>(), o.seed, l, state);
+        Buf flag(&c, sizeof(int32_t) * (size_t)(n + 1)), rootid(&c, sizeof(int32_t) * (size_t)(n + 1));
+        MDS_LAUNCH(c, KC_NONE, 0, k_root_flags, gr, 256, 0, n, state.as<int8_t>(), L.roots.as<int8_t>(),
+                   flag.as<int32_t>());
+        int64_t nc = scan_counts(c, flag.as<int32_t>(), rootid.as<int32_t>(), n);
+        Buf first(&c, sizeof(int32_t) * (size_t)n);
+        L.agg = Buf(&c, sizeof(int32_t) * (size_t)n);
+        MDS_LAUNCH(c, KC_NONE, 0, k_agg_first, gr, 256, 0, n, L.A.rowp(), L.A.cols(), gf.as<int8_t>(),
+                   L.roots.as<int8_t>(), rootid.as<int32_t>(), first.as<int32_t>());
+        MDS_LAUNCH(c, KC_NONE, 0, k_agg_second, gr, 256, 0, n, L.A.rowp(), L.A.cols(), L.A.vals(), gf.as<int8_t>(),
+                   L.roots.as<int8_t>(), deg.as<int32_t>(), first.as<int32_t>(), L.agg.as<int32_t>());
+        if (nc == 0 || (double)nc > o.stall_ratio * (double)n) {
+            L.agg.reset();
+            break;
+        }
+        // members of each aggregate, ascending
+        Buf acnt(&c, sizeof(int32_t) * (size_t)(nc + 1));
+        MDS_CUDA(cudaMemsetAsync(acnt.p, 0, sizeof(int32_t) * (size_t)(nc + 1), c.stream));
+        MDS_LAUNCH(c, KC_NONE, 0, k_agg_count, gr, 256, 0, n, L.agg.as<int32_t>(), acnt.as<int32_t>());
+        L.mem_off = Buf(&c, sizeof(int32_t) * (size_t)(nc + 1));
+        int64_t nmem = scan_counts(c, acnt.as<int32_t>(), L.mem_off.as<int32_t>(), nc);
+        L.mem = Buf(&c, sizeof(int32_t) * (size_t)(nmem > 0 ? nmem : 1));
+        MDS_CUDA(cudaMemsetAsync(acnt.p, 0, sizeof(int32_t) * (size_t)(nc + 1), c.stream));
+        MDS_LAUNCH(c, KC_NONE, 0, k_agg_scatter, gr, 256, 0, n, L.agg.as<int32_t>(), L.mem_off.as<int32_t>(),
+                   acnt.as<int32_t>(), L.mem.as<int32_t>());
+        MDS_LAUNCH(c, KC_NONE, 0, k_agg_sort, grid_for(nc, 128), 128, 0, nc, L.mem_off.as<int32_t>(),
+                   L.mem.as<int32_t>());
+        // Galerkin product
+        c.clear_err();
+        Buf ccnt(&c, sizeof(int32_t) * (size_t)(nc + 1));
+        MDS_LAUNCH(c, KC_NONE, 0, k_rap<false>, grid_for(nc, 64), 64, 0, nc, L.mem_off.as<int32_t>(),
+                   L.mem.as<int32_t>(), L.A.rowp(), L.A.cols(), L.A.vals(), L.agg.as<int32_t>(), ccnt.as<int32_t>(),
+                   nullptr, nullptr, nullptr, c.d_err);
+        c.check_err("Galerkin product (symbolic)");
+        DCsr Ac;
+        Ac.nrow = Ac.ncol = nc;
+        Ac.rp = Buf(&c, sizeof(int32_t) * (size_t)(nc + 1));
+        Ac.nnz = scan_counts(c, ccnt.as<int32_t>(), Ac.rowp(), nc);
+        Ac.ci = Buf(&c, sizeof(int32_t) * (size_t)(Ac.nnz > 0 ? Ac.nnz : 1));
+        Ac.v = Buf(&c, sizeof(double) * (size_t)(Ac.nnz > 0 ? Ac.nnz : 1));
+        MDS_LAUNCH(c, KC_NONE, 0, k_rap<true>, grid_for(nc, 64), 64, 0, nc, L.mem_off.as<int32_t>(),
+                   L.mem.as<int32_t>(), L.A.rowp(), L.A.cols(), L.A.vals(), L.agg.as<int32_t>(), nullptr,
+                   Ac.rowp(), Ac.cols(), Ac.vals(), c.d_err);
+        c.check_err("Galerkin product");
+        L.has_coarse = true;
+        L.nc = nc;
+        h.lv.emplace_back();
+        h.lv.back().A = std::move(Ac);
+    }
+    // per-level smoother data, precision copies and work vectors
+    size_t vb = h.prec == 64 ? sizeof(double) : sizeof(float);
+    for (auto &L : h.lv) {
+        int64_t n = L.A.nrow;
+        unsigned gr = grid_for(n, 256);
+        L.l1 = Buf(&c, sizeof(double) * (size_t)(n > 0 ? n : 1));
+        L.dinv = Buf(&c, vb * (size_t)(n > 0 ? n : 1));
+        if (h.prec == 64) {
+            MDS_LAUNCH(c, KC_NONE, 0, k_l1<double>, gr, 256, 0, n, L.A.rowp(), L.A.cols(), L.A.vals(),
+                       L.l1.as<double>(), L.dinv.as<double>());
+        } else {
+            MDS_LAUNCH(c, KC_NONE, 0, k_l1<float>, gr, 256, 0, n, L.A.rowp(), L.A.cols(), L.A.vals(),
+                       L.l1.as<double>(), L.dinv.as<float>());
+            L.vals_lp = Buf(&c, sizeof(float) * (size_t)(L.A.nnz > 0 ? L.A.nnz : 1));
+            MDS_LAUNCH(c, KC_NONE, 0, k_vals_f32, grid_for(L.A.nnz, 256) > 8192 ? 8192 : grid_for(L.A.nnz, 256), 256, 0,
+                       L.A.nnz, L.A.vals(), L.vals_lp.as<float>());
+        }
+        L.b = Buf(&c, vb * (size_t)(n > 0 ? n : 1));
+        L.x = Buf(&c, vb * (size_t)(n > 0 ? n : 1));
+        L.r = Buf(&c, vb * (size_t)(n > 0 ? n : 1));
+    }
+    if (h.dense) {
+        Level &L = h.lv.back();
+        h.nd = L.A.nrow;
+        dense_spd_inverse(c, L.A.view(), h.Ainv);
+    }
+    c.sync();
+}
+
+}  // namespace mds

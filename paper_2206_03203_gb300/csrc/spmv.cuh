@@ -1,0 +1,33 @@
+// CSR SpMV kernel with G lanes per row (G in {2, 4, 8, 16, 32}).
+#pragma once
+#include <cstdint>
+
+namespace mds {
+
+template <class T> __device__ __forceinline__ double to_d(T v) { return (double)v; }
+
+// MODE 0: y = A x;  MODE 1: y = r - A x.  Accumulation in FP64.
+template <int G, class VT, class XT, class OT, int MODE>
+__global__ void __launch_bounds__(256) k_spmv_csr(int64_t nrow, const int32_t *__restrict__ rp,
+                                                   const int32_t *__restrict__ ci, const VT *__restrict__ v,
+                                                   const XT *__restrict__ x, const double *__restrict__ r,
+                                                   OT *__restrict__ y) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t row = t / G;
+    int lane = (int)(t % G);
+    double s = 0.0;
+    if (row < nrow) {
+        int32_t p0 = rp[row], p1 = rp[row + 1];
+        for (int32_t p = p0 + lane; p < p1; p += G) s += to_d(v[p]) * to_d(__ldg(x + ci[p]));
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, G);
+    if (row < nrow && lane == 0) {
+        if (MODE == 1)
+            y[row] = (OT)(r[row] - s);
+        else
+            y[row] = (OT)s;
+    }
+}
+
+}  // namespace mds

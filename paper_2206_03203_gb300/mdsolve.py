@@ -1,0 +1,351 @@
+"""Thin ctypes binding of libmdsolve (include/mdsolve.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library.
+PyTorch provides device memory and the CUDA stream.  If the library is
+missing this module raises; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_build", "libmdsolve.so")
+
+MDS_OK = 0
+MDS_WARN_NOT_CONVERGED = 1
+PREC = {"fp64": 64, "fp32": 32, "mixed16": 16}
+SMOOTHER = {"l1jacobi": 0, "chebyshev": 1}
+KIND = {"lower": 0, "diag": 1, "upper": 2}
+KRYLOV = {"fgmres": 0, "pcg": 1}
+KCLASS = {"spmv": 0, "vc_resid": 1, "vc_post": 2, "gs_dot": 3, "gs_axpy": 4, "vcycle": 5, "vc_restrict": 6}
+
+
+class MDSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mdsolve error {code}: {msg}")
+        self.code = code
+
+
+class Instance(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int), ("km", C.c_void_p), ("n_f", C.c_int64),
+                ("fc_axis", C.c_void_p), ("fc_pos", C.c_void_p), ("fc_kf", C.c_void_p), ("fc_a", C.c_void_p),
+                ("nrhs", C.c_int), ("pD_left", C.c_void_p), ("pD_right", C.c_void_p), ("on_device", C.c_int)]
+
+
+class Csr(C.Structure):
+    _fields_ = [("nrow", C.c_int64), ("ncol", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class SetupOpts(C.Structure):
+    _fields_ = [("theta", C.c_double), ("n_coarse", C.c_int64), ("max_levels", C.c_int),
+                ("stall_ratio", C.c_double), ("seed", C.c_uint64), ("smoother", C.c_int),
+                ("precision", C.c_int), ("lowp_from_level", C.c_int), ("kind", C.c_int)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("krylov", C.c_int), ("restart", C.c_int), ("rtol", C.c_double), ("max_iters", C.c_int),
+                ("use_precond", C.c_int)]
+
+
+class RhsStats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("restarts", C.c_int), ("status", C.c_int),
+                ("relres_est", C.c_double), ("relres_true", C.c_double)]
+
+
+_lib = None
+
+# Every entry point of include/mdsolve.h with its ctypes signature.
+_SIGS = {
+    "mds_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_void_p]),
+    "mds_destroy": (C.c_int, [C.c_void_p]),
+    "mds_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mds_error_string": (C.c_char_p, [C.c_int]),
+    "mds_last_error": (C.c_char_p, [C.c_void_p]),
+    "mds_assemble": (C.c_int, [C.c_void_p, C.POINTER(Instance), C.POINTER(C.c_void_p)]),
+    "mds_system_from_csr": (C.c_int, [C.c_void_p] + [C.POINTER(Csr)] * 4 + [C.c_void_p, C.POINTER(C.c_void_p)]),
+    "mds_system_destroy": (C.c_int, [C.c_void_p]),
+    "mds_system_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_int64)]),
+    "mds_system_view": (C.c_int, [C.c_void_p, C.POINTER(Csr), C.POINTER(C.c_void_p)]),
+    "mds_setup_opts_default": (C.c_int, [C.POINTER(SetupOpts)]),
+    "mds_setup": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(SetupOpts), C.POINTER(C.c_void_p)]),
+    "mds_precond_destroy": (C.c_int, [C.c_void_p]),
+    "mds_precond_info": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
+    "mds_precond_level": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(Csr), C.POINTER(C.c_void_p),
+                                    C.POINTER(C.c_void_p)]),
+    "mds_precond_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mds_vcycle": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "mds_spmv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mds_solve_opts_default": (C.c_int, [C.POINTER(SolveOpts)]),
+    "mds_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                            C.POINTER(SolveOpts), C.POINTER(RhsStats)]),
+    "mds_timing_enable": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "mds_timing_reset": (C.c_int, [C.c_void_p]),
+    "mds_timing_query": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double)]),
+    "mds_memcpy": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t]),
+    "mds_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+}
+
+
+def lib():
+    """Load libmdsolve.so (built by paper_2206_03203_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libmdsolve.so not built ({LIB_PATH}); run paper_2206_03203_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a) -> int:
+    """Address of a torch tensor or numpy array (None -> 0)."""
+    if a is None:
+        return 0
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def setup_opts(**kw) -> SetupOpts:
+    o = SetupOpts()
+    lib().mds_setup_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if k == "precision":
+            v = PREC.get(v, v)
+        elif k == "smoother":
+            v = SMOOTHER.get(v, v)
+        elif k == "kind":
+            v = KIND.get(v, v)
+        setattr(o, k, v)
+    return o
+
+
+def solve_opts(**kw) -> SolveOpts:
+    o = SolveOpts()
+    lib().mds_solve_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if k == "krylov":
+            v = KRYLOV.get(v, v)
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class Stats:
+    iterations: int
+    restarts: int
+    status: int
+    relres_est: float
+    relres_true: float
+
+
+class Context:
+    """A library context on one device and stream (torch's current stream by default)."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None):
+        import torch
+        L = lib()
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self.device = device
+        h = C.c_void_p()
+        self._check(L.mds_create(C.byref(h), device, C.c_void_p(stream), None), ctx=False)
+        self.h = h
+
+    def _check(self, code, ctx=True):
+        if code < 0:
+            msg = lib().mds_last_error(self.h).decode() if ctx else lib().mds_error_string(code).decode()
+            raise MDSError(code, msg)
+        return code
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mds_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream: int):
+        self._check(lib().mds_set_stream(self.h, C.c_void_p(stream)))
+
+    # ---- problem ----
+    def assemble(self, inst, device_arrays: Optional[dict] = None) -> "System":
+        """Assemble an instance (paper_2206_03203_gb300.inputs.Instance).  With
+        ``device_arrays`` (torch CUDA tensors keyed by field name) the device
+        copies are used instead of the host arrays."""
+        keep = []
+        if device_arrays is None:
+            arrs = dict(km=np.ascontiguousarray(inst.km, dtype=np.float64),
+                        fc_axis=np.ascontiguousarray(inst.fc_axis, dtype=np.int32),
+                        fc_pos=np.ascontiguousarray(inst.fc_pos, dtype=np.int32).reshape(-1),
+                        fc_kf=np.ascontiguousarray(inst.fc_kf, dtype=np.float64),
+                        fc_a=np.ascontiguousarray(inst.fc_a, dtype=np.float64),
+                        pD_left=np.ascontiguousarray(inst.pD_left, dtype=np.float64),
+                        pD_right=np.ascontiguousarray(inst.pD_right, dtype=np.float64))
+            on_dev = 0
+        else:
+            arrs = device_arrays
+            on_dev = 1
+        keep.append(arrs)
+        s = Instance(inst.dim, inst.n, _ptr(arrs["km"]), inst.n_f, _ptr(arrs["fc_axis"]), _ptr(arrs["fc_pos"]),
+                     _ptr(arrs["fc_kf"]), _ptr(arrs["fc_a"]), inst.nrhs, _ptr(arrs["pD_left"]),
+                     _ptr(arrs["pD_right"]), on_dev)
+        h = C.c_void_p()
+        self._check(lib().mds_assemble(self.h, C.byref(s), C.byref(h)))
+        return System(self, h)
+
+    def system_from_csr(self, blocks, b=None) -> "System":
+        """blocks: four (row_ptr, col, val, nrow, ncol) tuples of torch CUDA
+        tensors (int32, int32, float64), kept alive by the returned System."""
+        cs = [Csr(nr, nc, int(v.numel()), _ptr(rp), _ptr(ci), _ptr(v)) for (rp, ci, v, nr, nc) in blocks]
+        h = C.c_void_p()
+        self._check(lib().mds_system_from_csr(self.h, *[C.byref(x) for x in cs], C.c_void_p(_ptr(b)), C.byref(h)))
+        s = System(self, h)
+        s._keep = (blocks, b)
+        return s
+
+    def setup(self, sys: "System", **opts) -> "Precond":
+        o = setup_opts(**opts)
+        h = C.c_void_p()
+        self._check(lib().mds_setup(self.h, sys.h, C.byref(o), C.byref(h)))
+        return Precond(self, sys, h)
+
+    def solve(self, sys: "System", prec: Optional["Precond"], b=None, x=None, nrhs: int = 1, **opts):
+        """Solve on device tensors (or host numpy arrays).  x holds x0 and is
+        overwritten.  Returns (status, [Stats])."""
+        o = solve_opts(**opts)
+        st = (RhsStats * nrhs)()
+        code = lib().mds_solve(self.h, sys.h, prec.h if prec is not None else None, C.c_void_p(_ptr(b)),
+                               C.c_void_p(_ptr(x)), nrhs, C.byref(o), st)
+        self._check(code)
+        return code, [Stats(s.iterations, s.restarts, s.status, s.relres_est, s.relres_true) for s in st]
+
+    def spmv(self, sys, x, y):
+        self._check(lib().mds_spmv(self.h, sys.h, C.c_void_p(_ptr(x)), C.c_void_p(_ptr(y))))
+
+    def precond_apply(self, prec, r, z):
+        self._check(lib().mds_precond_apply(self.h, prec.h, C.c_void_p(_ptr(r)), C.c_void_p(_ptr(z))))
+
+    def vcycle(self, prec, block, b, x):
+        self._check(lib().mds_vcycle(self.h, prec.h, block, C.c_void_p(_ptr(b)), C.c_void_p(_ptr(x))))
+
+    def memcpy(self, dst: int, src: int, nbytes: int):
+        self._check(lib().mds_memcpy(self.h, C.c_void_p(dst), C.c_void_p(src), nbytes))
+
+    def to_host(self, ptr: int, count: int, dtype) -> np.ndarray:
+        out = np.empty(count, dtype=dtype)
+        if count:
+            self.memcpy(out.ctypes.data, ptr, out.nbytes)
+        return out
+
+    def csr_to_host(self, c: Csr):
+        import scipy.sparse as sp
+        rp = self.to_host(c.row_ptr, c.nrow + 1, np.int32)
+        ci = self.to_host(c.col, c.nnz, np.int32)
+        v = self.to_host(c.val, c.nnz, np.float64)
+        return sp.csr_matrix((v, ci, rp), shape=(c.nrow, c.ncol))
+
+    # ---- measurement ----
+    def timing_enable(self, kclass, on=True):
+        k = KCLASS.get(kclass, kclass)
+        self._check(lib().mds_timing_enable(self.h, k, 1 if on else 0))
+
+    def timing_reset(self):
+        self._check(lib().mds_timing_reset(self.h))
+
+    def timing_query(self, kclass):
+        k = KCLASS.get(kclass, kclass)
+        n, ms, by = C.c_int64(), C.c_double(), C.c_double()
+        self._check(lib().mds_timing_query(self.h, k, C.byref(n), C.byref(ms), C.byref(by)))
+        return n.value, ms.value, by.value
+
+    def launch_count(self) -> int:
+        n = C.c_int64()
+        self._check(lib().mds_launch_count(self.h, C.byref(n)))
+        return n.value
+
+
+class System:
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+        n_m, n_f, nrhs = C.c_int64(), C.c_int64(), C.c_int()
+        nnz = (C.c_int64 * 5)()
+        ctx._check(lib().mds_system_info(h, C.byref(n_m), C.byref(n_f), C.byref(nrhs), nnz))
+        self.n_m, self.n_f, self.nrhs = n_m.value, n_f.value, nrhs.value
+        self.nnz = list(nnz)
+        self.N = self.n_m + self.n_f
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mds_system_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def views(self):
+        v = (Csr * 5)()
+        b = C.c_void_p()
+        self.ctx._check(lib().mds_system_view(self.h, v, C.byref(b)))
+        return list(v), b.value
+
+    def to_host(self):
+        """(A_mm, A_mf, A_fm, A_ff, A) as scipy CSR and b [nrhs, N] as numpy."""
+        v, b = self.views()
+        mats = [self.ctx.csr_to_host(x) for x in v]
+        bh = self.ctx.to_host(b, self.N * self.nrhs, np.float64).reshape(self.nrhs, self.N)
+        return mats, bh
+
+    def b_ptr(self, k: int = 0) -> int:
+        return self.views()[1] + 8 * k * self.N
+
+
+class Precond:
+    def __init__(self, ctx: Context, sys: System, h):
+        self.ctx, self.sys, self.h = ctx, sys, h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mds_precond_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self, block: int):
+        nl, dense = C.c_int(), C.c_int()
+        ln, lz = (C.c_int64 * 32)(), (C.c_int64 * 32)()
+        self.ctx._check(lib().mds_precond_info(self.h, block, C.byref(nl), ln, lz, C.byref(dense)))
+        return dict(nlevels=nl.value, n=list(ln)[:nl.value], nnz=list(lz)[:nl.value], dense=bool(dense.value))
+
+    def level_host(self, block: int, level: int):
+        A = Csr()
+        agg, roots = C.c_void_p(), C.c_void_p()
+        self.ctx._check(lib().mds_precond_level(self.h, block, level, C.byref(A), C.byref(agg), C.byref(roots)))
+        M = self.ctx.csr_to_host(A)
+        ag = self.ctx.to_host(agg.value, A.nrow, np.int32) if agg.value else None
+        ro = self.ctx.to_host(roots.value, A.nrow, np.int8).astype(bool)
+        return M, ag, ro

@@ -1,0 +1,364 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded instances.
+
+Bit-exact: sparsity, FP64 matrix values, right-hand sides, the Schur
+complement, every AMG level's matrix, MIS-2 roots and aggregates (integer and
+set-up work with a fixed summation order on both sides).  Tolerance: V-cycle
+and preconditioner outputs (1e-12 relative in FP64, 2e-5 in FP32), solves
+(iteration count within one of the oracle, true relative residual <= rtol).
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from paper_2206_03203_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "fixed2d-64": lambda: inputs.fixed_2d(),
+    "fixed2d-37": lambda: inputs.fixed_2d(n=37),
+    "seg2d-96": lambda: inputs.random_segments_2d(n=96, n_seg=12),
+    "seg2d-61-c1": lambda: inputs.random_segments_2d(n=61, n_seg=9, contrast=1.0),
+    "planes3d-16": lambda: inputs.planes_3d(n=16),
+    "planes3d-13-kf1": lambda: inputs.planes_3d(n=13, kf=1.0),
+    "rects3d-18": lambda: inputs.random_rects_3d(18, 22060305, 0, 6, sigma=2.0),
+}
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ctx(torch_mod):
+    from paper_2206_03203_gb300 import build, mdsolve
+    build.build()
+    return mdsolve.Context(0)
+
+
+def dev(torch, a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def same_csr(A, B):
+    return (A.shape == B.shape and np.array_equal(A.indptr, B.indptr) and np.array_equal(A.indices, B.indices)
+            and np.array_equal(A.data, B.data))
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_assembly_bit_exact(ctx, oracle_mod, case):
+    inst = CASES[case]()
+    sys_ = ctx.assemble(inst)
+    (Amm, Amf, Afm, Aff, A), b = sys_.to_host()
+    Ao, bo = oracle_mod.assemble(inst)
+    assert same_csr(A, Ao)
+    assert np.array_equal(b, bo)
+    for G, O in zip((Amm, Amf, Afm, Aff), oracle_mod.split(Ao, inst.n_m)):
+        assert same_csr(G, O)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_schur_and_hierarchies_bit_exact(ctx, oracle_mod, case):
+    inst = CASES[case]()
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_)
+    Ao, _ = oracle_mod.assemble(inst)
+    M = oracle_mod.ML(Ao, inst.n_m)
+    S_gpu, _, _ = prec.level_host(0, 0)
+    assert same_csr(S_gpu, M.schur)
+    for block in (0, 1):
+        amg = M.amg(block)
+        info = prec.info(block)
+        assert info["nlevels"] == amg.nlevels
+        assert info["dense"] == amg.coarsest_dense
+        for l in range(amg.nlevels):
+            Ag, agg, roots = prec.level_host(block, l)
+            assert same_csr(Ag, amg.level_A(l)), (block, l)
+            assert np.array_equal(roots, amg.roots(l)), (block, l)
+            ao = amg.agg(l)
+            if ao is None:
+                assert agg is None
+            else:
+                assert np.array_equal(agg, ao), (block, l)
+
+
+@pytest.mark.parametrize("prec_name,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("case", ["fixed2d-64", "seg2d-96", "planes3d-16", "rects3d-18"])
+def test_vcycle_parity(ctx, oracle_mod, torch_mod, case, prec_name, tol):
+    torch = torch_mod
+    inst = CASES[case]()
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_, precision=prec_name)
+    Ao, _ = oracle_mod.assemble(inst)
+    M = oracle_mod.ML(Ao, inst.n_m, prec=64 if prec_name == "fp64" else 32)
+    rng = np.random.default_rng(7)
+    for block, n in ((0, inst.n_m), (1, inst.n_f)):
+        b = rng.standard_normal(n)
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        ctx.vcycle(prec, block, dev(torch, b), x)
+        xo = M.amg(block).vcycle(b)
+        err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+        assert err < tol, (block, err)
+
+
+@pytest.mark.parametrize("kind", ["lower", "diag", "upper"])
+@pytest.mark.parametrize("prec_name,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_precond_apply_parity(ctx, oracle_mod, torch_mod, kind, prec_name, tol):
+    torch = torch_mod
+    inst = CASES["seg2d-96"]()
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_, precision=prec_name, kind=kind)
+    Ao, _ = oracle_mod.assemble(inst)
+    M = oracle_mod.ML(Ao, inst.n_m, kind=kind, prec=64 if prec_name == "fp64" else 32)
+    r = np.random.default_rng(3).standard_normal(sys_.N)
+    z = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+    ctx.precond_apply(prec, dev(torch, r), z)
+    zo = M.apply(r)
+    err = np.linalg.norm(z.cpu().numpy() - zo) / np.linalg.norm(zo)
+    assert err < tol, err
+
+
+def test_spmv_parity(ctx, oracle_mod, torch_mod):
+    torch = torch_mod
+    inst = CASES["rects3d-18"]()
+    sys_ = ctx.assemble(inst)
+    Ao, _ = oracle_mod.assemble(inst)
+    x = np.random.default_rng(1).standard_normal(sys_.N)
+    y = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+    ctx.spmv(sys_, dev(torch, x), y)
+    yo = oracle_mod.spmv(Ao, x)
+    assert np.max(np.abs(y.cpu().numpy() - yo)) <= 1e-13 * np.max(np.abs(yo))
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", list(CASES))
+def test_solve_parity(ctx, oracle_mod, torch_mod, case, prec_name):
+    torch = torch_mod
+    inst = CASES[case]()
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_, precision=prec_name)
+    x = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+    code, st = ctx.solve(sys_, prec, None, x, rtol=1e-8, max_iters=3000)
+    res, Ao, bo, _ = oracle_mod.solve(inst, prec=64 if prec_name == "fp64" else 32, maxit=3000)
+    assert code == 0 and res.converged
+    assert abs(st[0].iterations - res.iterations) <= 1, (st[0].iterations, res.iterations)
+    xg = x.cpu().numpy()
+    rel = np.linalg.norm(bo[0] - Ao @ xg) / np.linalg.norm(bo[0])
+    assert rel <= 1e-8 * 1.01 and abs(rel - st[0].relres_true) <= 1e-3 * rel + 1e-15
+    # both solutions are within the same residual bound of the exact one
+    assert np.linalg.norm(Ao @ (xg - res.x)) / np.linalg.norm(bo[0]) <= 2.1e-8
+
+
+def test_solve_matches_direct(ctx, oracle_mod, torch_mod):
+    torch = torch_mod
+    inst = CASES["fixed2d-64"]()
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_)
+    x = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+    ctx.solve(sys_, prec, None, x, rtol=1e-12)
+    Ao, bo = oracle_mod.assemble(inst)
+    xd = spla.spsolve(Ao.tocsc(), bo[0])
+    assert np.max(np.abs(x.cpu().numpy() - xd)) < 1e-8
+
+
+def test_pcg_block_diagonal(ctx, oracle_mod, torch_mod):
+    torch = torch_mod
+    inst = CASES["planes3d-13-kf1"]()
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_, kind="diag")
+    x = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+    code, st = ctx.solve(sys_, prec, None, x, krylov="pcg", max_iters=2000)
+    res, Ao, bo, _ = oracle_mod.solve(inst, kind="diag", krylov="pcg", maxit=2000)
+    assert code == 0 and abs(st[0].iterations - res.iterations) <= 1
+    assert st[0].relres_true <= 1e-8
+
+
+def test_identity_preconditioner(ctx, oracle_mod, torch_mod):
+    torch = torch_mod
+    inst = inputs.fixed_2d(n=12)
+    sys_ = ctx.assemble(inst)
+    x = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+    code, st = ctx.solve(sys_, None, None, x, use_precond=0, max_iters=5000, restart=30)
+    Ao, bo = oracle_mod.assemble(inst)
+    res = oracle_mod.fgmres(Ao, bo[0], "identity", restart=30, maxit=5000)
+    assert abs(st[0].iterations - res.iterations) <= 1 and st[0].relres_true <= 1e-8
+
+
+def test_system_from_csr(ctx, oracle_mod, torch_mod):
+    torch = torch_mod
+    inst = CASES["seg2d-61-c1"]()
+    Ao, bo = oracle_mod.assemble(inst)
+    blocks = []
+    for B in oracle_mod.split(Ao, inst.n_m):
+        blocks.append((dev(torch, B.indptr.astype(np.int32)), dev(torch, B.indices.astype(np.int32)),
+                       dev(torch, B.data), B.shape[0], B.shape[1]))
+    b = dev(torch, bo[0])
+    sys_ = ctx.system_from_csr(blocks, b)
+    (_, _, _, _, A), bh = sys_.to_host()
+    assert same_csr(A, Ao) and np.array_equal(bh[0], bo[0])
+    prec = ctx.setup(sys_)
+    x = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+    code, st = ctx.solve(sys_, prec, None, x)
+    res, *_ = oracle_mod.solve(inst)
+    assert code == 0 and abs(st[0].iterations - res.iterations) <= 1
+
+
+def test_host_buffers_and_nonzero_x0(ctx, oracle_mod):
+    inst = CASES["fixed2d-37"]()
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_)
+    Ao, bo = oracle_mod.assemble(inst)
+    x = np.zeros(sys_.N)
+    code, st = ctx.solve(sys_, prec, np.ascontiguousarray(bo[0]), x)
+    assert code == 0 and np.linalg.norm(bo[0] - Ao @ x) / np.linalg.norm(bo[0]) <= 1e-8
+    # restart from the solution: zero iterations
+    code, st = ctx.solve(sys_, prec, np.ascontiguousarray(bo[0]), x)
+    assert st[0].iterations == 0
+
+
+def test_multiple_rhs(ctx, oracle_mod):
+    inst = inputs.random_rects_3d(12, 5, 1, 4, nrhs=3, random_dirichlet=True)
+    sys_ = ctx.assemble(inst)
+    assert sys_.nrhs == 3
+    prec = ctx.setup(sys_)
+    x = np.zeros(3 * sys_.N)
+    code, st = ctx.solve(sys_, prec, None, x, nrhs=3)
+    Ao, bo = oracle_mod.assemble(inst)
+    for k in range(3):
+        xk = x[k * sys_.N:(k + 1) * sys_.N]
+        assert np.linalg.norm(bo[k] - Ao @ xk) / np.linalg.norm(bo[k]) <= 1e-8
+        r = oracle_mod.fgmres(Ao, bo[k], oracle_mod.ML(Ao, inst.n_m))
+        assert abs(st[k].iterations - r.iterations) <= 1
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_no_fractures(ctx, oracle_mod, torch_mod):
+    torch = torch_mod
+    inst = inputs.make_instance("plain", 2, 40, inputs.lognormal_km(1, 0, 1600, 1.0), [])
+    sys_ = ctx.assemble(inst)
+    assert sys_.n_f == 0
+    prec = ctx.setup(sys_)
+    assert prec.info(1)["nlevels"] == 0
+    x = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+    code, st = ctx.solve(sys_, prec, None, x)
+    res, *_ = oracle_mod.solve(inst)
+    assert code == 0 and abs(st[0].iterations - res.iterations) <= 1
+
+
+def test_tiny_grids(ctx, oracle_mod, torch_mod):
+    torch = torch_mod
+    for inst in (inputs.make_instance("one", 2, 1, np.ones(1), []),
+                 inputs.make_instance("two", 3, 2, np.array([1., 2, 3, 4, 5, 6, 7, 8]),
+                                      [inputs.Rect(2, 1, (0, 0), (1, 2), 3.0, 0.1)])):
+        sys_ = ctx.assemble(inst)
+        (_, _, _, _, A), b = sys_.to_host()
+        Ao, bo = oracle_mod.assemble(inst)
+        assert same_csr(A, Ao) and np.array_equal(b, bo)
+        prec = ctx.setup(sys_)
+        x = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+        code, st = ctx.solve(sys_, prec, None, x)
+        assert code == 0 and st[0].relres_true <= 1e-8
+
+
+def test_coarsening_stall_is_smoother_only(ctx, oracle_mod, torch_mod):
+    """Blocking fractures make A_ff strongly diagonal: no strong couplings, the
+    hierarchy stops at level 0 and the V-cycle is two L1-Jacobi sweeps."""
+    torch = torch_mod
+    inst = inputs.random_segments_2d(n=200, n_seg=20, contrast=1e-4)
+    inst.fc_kf[:] = 1e-4
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_, n_coarse=16)
+    Ao, _ = oracle_mod.assemble(inst)
+    M = oracle_mod.ML(Ao, inst.n_m, n_coarse=16)
+    info = prec.info(1)
+    assert info["nlevels"] == M.amg(1).nlevels and info["dense"] == M.amg(1).coarsest_dense
+    b = np.random.default_rng(0).standard_normal(inst.n_f)
+    x = torch.zeros(inst.n_f, dtype=torch.float64, device="cuda")
+    ctx.vcycle(prec, 1, dev(torch, b), x)
+    xo = M.amg(1).vcycle(b)
+    assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-12 * np.linalg.norm(xo)
+
+
+def test_rejects_duplicate_fracture_face(ctx):
+    from paper_2206_03203_gb300 import mdsolve
+    inst = inputs.make_instance("d", 2, 8, np.ones(64), [inputs.Rect(0, 4, (0,), (2,), 1.0, 1.0)])
+    inst.fc_pos = np.vstack([inst.fc_pos, inst.fc_pos[:1]])
+    inst.fc_axis = np.concatenate([inst.fc_axis, inst.fc_axis[:1]])
+    inst.fc_kf = np.concatenate([inst.fc_kf, inst.fc_kf[:1]])
+    inst.fc_a = np.concatenate([inst.fc_a, inst.fc_a[:1]])
+    with pytest.raises(mdsolve.MDSError) as e:
+        ctx.assemble(inst)
+    assert e.value.code == -1
+    # the context stays usable
+    ctx.assemble(inputs.fixed_2d(n=8))
+
+
+def test_rejects_interior_plane_violation(ctx):
+    from paper_2206_03203_gb300 import mdsolve
+    inst = inputs.make_instance("b", 2, 8, np.ones(64), [inputs.Rect(0, 4, (0,), (2,), 1.0, 1.0)])
+    inst.fc_pos = inst.fc_pos.copy()
+    inst.fc_pos[0, 0] = 8  # boundary plane
+    with pytest.raises(mdsolve.MDSError):
+        ctx.assemble(inst)
+
+
+def test_nonfinite_rhs_reports_error(ctx, torch_mod):
+    torch = torch_mod
+    inst = inputs.fixed_2d(n=16)
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_)
+    b = torch.full((sys_.N,), float("nan"), dtype=torch.float64, device="cuda")
+    x = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+    from paper_2206_03203_gb300 import mdsolve
+    with pytest.raises(mdsolve.MDSError):
+        ctx.solve(sys_, prec, b, x)
+
+
+def test_iteration_cap_warns(ctx, torch_mod):
+    torch = torch_mod
+    inst = inputs.fixed_2d(n=32)
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_)
+    x = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+    code, st = ctx.solve(sys_, prec, None, x, max_iters=3)
+    assert code == 1 and st[0].status == 1 and st[0].iterations == 3
+
+
+# ---------------------------------------------------------------- full size
+
+def test_full_size_random_segments(ctx, oracle_mod, torch_mod):
+    """1024 x 1024, 64 segments, contrast 1e4: assembly, S~ and every AMG level
+    bit-exact; the solve meets the stopping rule on an independent residual."""
+    torch = torch_mod
+    inst = inputs.random_segments_2d()
+    sys_ = ctx.assemble(inst)
+    (Amm, Amf, Afm, Aff, A), b = sys_.to_host()
+    Ao, bo = oracle_mod.assemble(inst)
+    assert same_csr(A, Ao) and np.array_equal(b, bo)
+    prec = ctx.setup(sys_)
+    M = oracle_mod.ML(Ao, inst.n_m)
+    for block in (0, 1):
+        amg = M.amg(block)
+        assert prec.info(block)["nlevels"] == amg.nlevels
+        for l in range(amg.nlevels):
+            Ag, agg, roots = prec.level_host(block, l)
+            assert same_csr(Ag, amg.level_A(l))
+            ao = amg.agg(l)
+            assert (agg is None and ao is None) or np.array_equal(agg, ao)
+    x = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+    code, st = ctx.solve(sys_, prec, None, x, max_iters=5000)
+    xg = x.cpu().numpy()
+    rel = np.linalg.norm(bo[0] - Ao @ xg) / np.linalg.norm(bo[0])
+    assert code == 0 and rel <= 1.01e-8
+    # sampled rows of M_L: one application against the oracle
+    r = np.random.default_rng(5).standard_normal(sys_.N)
+    z = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+    ctx.precond_apply(prec, dev(torch, r), z)
+    zo = M.apply(r)
+    assert np.linalg.norm(z.cpu().numpy() - zo) <= 1e-12 * np.linalg.norm(zo)
