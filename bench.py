@@ -318,6 +318,24 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_case(args):
+    """A short fixed run for ncu: the contrast-1e4 member of the sweep,
+    assembled, set up and solved for --max-iters FGMRES iterations."""
+    import torch
+
+    from paper_2206_03203_gb300 import build, inputs, mdsolve
+    build.build()
+    ctx = mdsolve.Context(0)
+    inst = inputs.random_segments_2d(n=args.n, contrast=1e4)
+    s = ctx.assemble(inst)
+    p = ctx.setup(s, precision=args.precision)
+    x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    code, st = ctx.solve(s, p, None, x, rtol=1e-8, max_iters=args.max_iters)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": inst.name, "N": s.N, "iterations": st[0].iterations,
+                      "relres": st[0].relres_true, "launches": ctx.launch_count()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -325,7 +343,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true", help="short fixed run for ncu captures")
+    ap.add_argument("--max-iters", type=int, default=60)
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--precision", default="fp64")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3
     if args.impl == "reference":

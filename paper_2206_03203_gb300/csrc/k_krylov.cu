@@ -22,37 +22,47 @@ static unsigned red_grid(int64_t n) {
     return (unsigned)g;
 }
 
-// partial[blk][q] = sum_i V[q][i] w[i] over this block's rows
-__global__ void __launch_bounds__(RED_BLOCK) k_mdot(int64_t n, const double *__restrict__ V, int64_t ldv, int nq,
+// partial[q][blk] = sum over this block's rows of V[q][i] w[i]; grid.y = q.
+// One dot product per block row keeps registers low; w is re-read once per q
+// and stays resident in L2, V is read once from HBM.
+__global__ void __launch_bounds__(RED_BLOCK) k_mdot(int64_t n, const double *__restrict__ V, int64_t ldv,
                                                      const double *__restrict__ w, double *__restrict__ partial) {
-    __shared__ double ws[RED_BLOCK / 32][QMAX];
-    double acc[QMAX];
-#pragma unroll
-    for (int q = 0; q < QMAX; q++) acc[q] = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double wi = w[i];
-#pragma unroll
-        for (int q = 0; q < QMAX; q++)
-            if (q < nq) acc[q] += V[q * ldv + i] * wi;
+    __shared__ double ws[RED_BLOCK / 32];
+    const double *v = V + (int64_t)blockIdx.y * ldv;
+    double s = 0.0;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        double a0 = v[i], a1 = v[i + stride], a2 = v[i + 2 * stride], a3 = v[i + 3 * stride];
+        double b0 = w[i], b1 = w[i + stride], b2 = w[i + 2 * stride], b3 = w[i + 3 * stride];
+        s += a0 * b0;
+        s += a1 * b1;
+        s += a2 * b2;
+        s += a3 * b3;
     }
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < QMAX; q++) {
-        if (q < nq) {
-            double s = acc[q];
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-            if (lane == 0) ws[wid][q] = s;
-        }
-    }
+    for (; i < n; i += stride) s += v[i] * w[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
     __syncthreads();
-    if (threadIdx.x < nq) {
-        double s = 0.0;
-        for (int k = 0; k < RED_BLOCK / 32; k++) s += ws[k][threadIdx.x];
-        partial[(int64_t)blockIdx.x * QMAX + threadIdx.x] = s;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < RED_BLOCK / 32; k++) t += ws[k];
+        partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
     }
 }
 
-// out[q] (+)= sum over blocks of partial[blk][q], fixed order
+// out[q] (+)= sum_b partial[q][b], one warp per q, fixed order
+__global__ void k_reduce_rows(const double *__restrict__ partial, int nblk, int nq, double *__restrict__ out,
+                              int accumulate) {
+    int q = blockIdx.x;
+    if (q >= nq) return;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 32) s += partial[(int64_t)q * nblk + b];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) out[q] = accumulate ? out[q] + s : s;
+}
+
+// out[q] (+)= sum over blocks of partial[blk][q] (stride QMAX), fixed order
 __global__ void k_reduce_cols(const double *__restrict__ partial, int nblk, int nq, double *__restrict__ out,
                               int accumulate) {
     int q = threadIdx.x;
@@ -110,7 +120,7 @@ __global__ void __launch_bounds__(RED_BLOCK) k_dot(int64_t n, const double *__re
     }
 }
 
-__global__ void k_scale(int64_t n, const double *__restrict__ w, const double *__restrict__ f, double *__restrict__ o) {
+__global__ void k_scale(int64_t n, const double *w, const double *__restrict__ f, double *o) {
     double s = *f;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         o[i] = w[i] * s;
@@ -200,8 +210,16 @@ __global__ void k_copy1(const double *__restrict__ a, double *__restrict__ b) { 
 
 struct Red {
     Buf partial;
-    unsigned grid = 1;
+    unsigned grid = 1;   // blocks of the single-vector reductions
+    unsigned mgrid = 1;  // row blocks per basis vector in k_mdot
 };
+
+static unsigned mdot_grid(int64_t n) {
+    int64_t g = (n + RED_BLOCK * 16 - 1) / (RED_BLOCK * 16);
+    if (g < 1) g = 1;
+    if (g > 1024) g = 1024;
+    return (unsigned)g;
+}
 
 static void dot_dev(Ctx &c, Red &R, int64_t n, const double *a, const double *b, double *out) {
     MDS_LAUNCH(c, KC_NONE, 16.0 * n, k_dot, R.grid, RED_BLOCK, 0, n, a, b, R.partial.as<double>());
@@ -214,7 +232,8 @@ KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, 
     const int m = o.restart < 1 ? 1 : (o.restart > QMAX - 1 ? QMAX - 1 : o.restart);
     Red R;
     R.grid = red_grid(n);
-    R.partial = Buf(&c, sizeof(double) * (size_t)R.grid * QMAX);
+    R.mgrid = mdot_grid(n);
+    R.partial = Buf(&c, sizeof(double) * (size_t)(R.grid > R.mgrid ? R.grid : R.mgrid) * QMAX);
     Buf V(&c, sizeof(double) * (size_t)(m + 1) * (size_t)n);
     Buf Z(&c, sizeof(double) * (size_t)m * (size_t)n);
     Buf H(&c, sizeof(double) * (size_t)(m + 1) * m);
@@ -262,9 +281,9 @@ KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, 
             // CGS2: h = V^T w; w -= V h; twice
             int nq = j + 1;
             for (int pass = 0; pass < 2; pass++) {
-                MDS_LAUNCH(c, KC_GS_DOT, 8.0 * n * (nq + 1), k_mdot, R.grid, RED_BLOCK, 0, n, Vp, n, nq, w,
+                MDS_LAUNCH(c, KC_GS_DOT, 8.0 * n * (nq + 1), k_mdot, dim3(R.mgrid, nq), RED_BLOCK, 0, n, Vp, n, w,
                            R.partial.as<double>());
-                MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.partial.as<double>(), (int)R.grid, nq,
+                MDS_LAUNCH(c, KC_NONE, 0, k_reduce_rows, nq, 32, 0, R.partial.as<double>(), (int)R.mgrid, nq,
                            pass == 0 ? h : h + 32, 0);
                 MDS_LAUNCH(c, KC_GS_AXPY, 8.0 * n * (nq + 2), k_maxpy<-1>, R.grid, RED_BLOCK, 0, n, Vp, n, nq,
                            pass == 0 ? h : h + 32, w, pass == 1 ? R.partial.as<double>() : nullptr);
