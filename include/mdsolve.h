@@ -149,7 +149,12 @@ int mds_system_view(mds_system sys, mds_csr blocks[5], const double **b);
 #define MDS_SMOOTHER_CHEBYSHEV 1
 #define MDS_PREC_FP64 64        /* V-cycles stored and applied in FP64 */
 #define MDS_PREC_FP32 32        /* FP32 values and vectors */
-#define MDS_PREC_MIXED16 16     /* FP32 fine levels, BF16 row-scaled from lowp_from_level */
+#define MDS_PREC_BF16 16        /* FP32 vectors; levels >= lowp_from_level stored in BF16 with
+                                   power-of-two row scales, finer levels in FP32 */
+#define MDS_PREC_FP16 17        /* as MDS_PREC_BF16 with FP16 storage */
+#define MDS_FORMAT_AUTO 0       /* timed choice per level (autotuner) */
+#define MDS_FORMAT_CSR 1
+#define MDS_FORMAT_SELL 2       /* sliced ELLPACK, slice height sell_c, sort window sell_sigma */
 #define MDS_BLOCK_LOWER 0       /* M_L, Eq. (8), Algorithm 1 */
 #define MDS_BLOCK_DIAG 1        /* block diagonal B_D with Q blocks */
 #define MDS_BLOCK_UPPER 2       /* block upper triangular B_U with Q blocks */
@@ -162,8 +167,12 @@ typedef struct {
     uint64_t seed;           /* MIS-2 hash seed */
     int smoother;            /* MDS_SMOOTHER_* */
     int precision;           /* MDS_PREC_* */
-    int lowp_from_level;     /* first BF16 level for MDS_PREC_MIXED16 (1) */
+    int lowp_from_level;     /* first BF16/FP16 level for MDS_PREC_BF16/FP16 (1) */
     int kind;                /* MDS_BLOCK_* */
+    int format;              /* MDS_FORMAT_* for the V-cycle level matrices (MDS_FORMAT_CSR) */
+    int sell_c;              /* SELL slice height: 8, 16 or 32 (32) */
+    int sell_sigma;          /* SELL sort window in rows: 1 or a multiple of sell_c up to 1024 (1) */
+    int sweeps;              /* smoother applications before and after the coarse correction (1) */
 } mds_setup_opts;
 
 /* Fill `o` with the defaults listed above. */
@@ -172,7 +181,9 @@ int mds_setup_opts_default(mds_setup_opts *o);
 /* Build S~ (Eq. (7)) and one aggregation-AMG hierarchy for each of S~ and
  * A_ff: strength graph, MIS-2 with SplitMix64 priorities, aggregates,
  * piecewise-constant P, Galerkin P^T A P, L1 diagonals, coarsest dense
- * Cholesky.  The system must outlive the preconditioner. */
+ * Cholesky; then the per-level storage (precision, format) used by the
+ * V-cycle, chosen by timing when format = MDS_FORMAT_AUTO.  The system must
+ * outlive the preconditioner. */
 int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_precond *out);
 int mds_precond_destroy(mds_precond prec);
 /* Hierarchy of block 0 (S~) or 1 (A_ff): number of levels, and per level the
@@ -234,9 +245,10 @@ int mds_solve(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, do
 #define MDS_KCLASS_COUNT 8
 int mds_timing_enable(mds_ctx ctx, int kclass, int enable);
 int mds_timing_reset(mds_ctx ctx);
-/* Synchronises the stream; returns launches, summed event time (ms) and summed
- * algorithmic bytes of a class since the last reset. */
-int mds_timing_query(mds_ctx ctx, int kclass, int64_t *launches, double *ms, double *bytes);
+/* Synchronises the stream; returns launches, summed event time (ms), summed
+ * algorithmic bytes and summed algorithmic floating-point operations of a
+ * class since the last reset (any output pointer may be NULL). */
+int mds_timing_query(mds_ctx ctx, int kclass, int64_t *launches, double *ms, double *bytes, double *flops);
 /* Copy `bytes` bytes from src to dst (each a host or device pointer) on the
  * context stream and synchronise it.  A convenience for callers without
  * their own CUDA runtime binding. */

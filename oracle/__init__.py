@@ -45,7 +45,7 @@ class _CSR(C.Structure):
 class AMGOpts(C.Structure):
     _fields_ = [("theta", C.c_double), ("n_coarse", C.c_int64), ("max_levels", C.c_int),
                 ("stall_ratio", C.c_double), ("seed", C.c_uint64), ("smoother", C.c_int),
-                ("prec", C.c_int), ("lowp_from_level", C.c_int)]
+                ("prec", C.c_int), ("lowp_from_level", C.c_int), ("sweeps", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -81,6 +81,8 @@ def lib():
             L.orc_strength.argtypes = [P(_CSR), C.c_double]
             L.orc_mis_key.restype = C.c_uint64
             L.orc_mis_key.argtypes = [C.c_uint64, C.c_int, C.c_int64]
+            L.orc_round_lowp.restype = C.c_double
+            L.orc_round_lowp.argtypes = [C.c_double, C.c_int]
             L.orc_amg_setup.restype = C.c_void_p
             L.orc_amg_setup.argtypes = [P(_CSR), P(AMGOpts)]
             L.orc_amg_free.argtypes = [C.c_void_p]
@@ -205,8 +207,12 @@ DEFAULT_SEED = 0x2206_0320_3
 
 
 def amg_opts(theta=0.08, n_coarse=512, max_levels=25, stall_ratio=0.9, seed=DEFAULT_SEED,
-             smoother=0, prec=64, lowp_from_level=1) -> AMGOpts:
-    return AMGOpts(theta, n_coarse, max_levels, stall_ratio, seed, smoother, prec, lowp_from_level)
+             smoother=0, prec=64, lowp_from_level=1, sweeps=1) -> AMGOpts:
+    return AMGOpts(theta, n_coarse, max_levels, stall_ratio, seed, smoother, prec, lowp_from_level, sweeps)
+
+
+def round_lowp(x, prec):
+    return float(lib().orc_round_lowp(float(x), prec))
 
 
 class AMG:

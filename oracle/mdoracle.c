@@ -678,6 +678,28 @@ static float to_bf16(float x) {
     return y;
 }
 
+/* fp16 rounding of a float: round to nearest even with 10 fraction bits,
+ * subnormals down to 2^-24, overflow to infinity (IEEE 754 binary16). */
+static double to_fp16(float xf) {
+    double x = (double)xf;
+    if (x == 0.0 || !isfinite(x)) return x;
+    double ax = fabs(x);
+    if (ax >= 65520.0) return copysign(INFINITY, x);
+    int e;
+    frexp(ax, &e); /* ax = f 2^e, f in [0.5, 1): exponent of the leading bit is e-1 */
+    int E = e - 1;
+    double ulp = E >= -14 ? ldexp(1.0, E - 10) : ldexp(1.0, -24);
+    double q = nearbyint(ax / ulp);
+    return copysign(q * ulp, x);
+}
+
+double orc_round_lowp(double x, int prec) {
+    if (prec == 16) return (double)to_bf16((float)x);
+    if (prec == 17) return to_fp16((float)x);
+    if (prec == 32) return (double)(float)x;
+    return x;
+}
+
 static double rnd(double x, int prec) {
     if (prec == 64) return x;
     return (double)(float)x;
@@ -720,7 +742,7 @@ orc_amg *orc_amg_setup(const ocsr *A0, const orc_amg_opts *o) {
     for (int q = 0; q < h->nlev; q++) {
         ocsr *M = h->A[q];
         int64_t n = M->nrow;
-        int lp = (o->prec == 16 && q >= o->lowp_from_level) ? 1 : 0;
+        int lp = ((o->prec == 16 || o->prec == 17) && q >= o->lowp_from_level) ? o->prec : 0;
         h->lowp[q] = lp;
         h->l1[q] = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
         h->dinv[q] = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
@@ -741,8 +763,10 @@ orc_amg *orc_amg_setup(const ocsr *A0, const orc_amg_opts *o) {
                 double fr = frexp(mx, &e); /* mx = fr 2^e, fr in [0.5,1) */
                 if (fr == 0.5) e -= 1;     /* exact power of two */
                 double sc = ldexp(1.0, e);
-                for (int64_t p = M->rp[i]; p < M->rp[i + 1]; p++)
-                    h->av[q][p] = (double)to_bf16((float)(M->v[p] / sc)) * sc;
+                for (int64_t p = M->rp[i]; p < M->rp[i + 1]; p++) {
+                    float t = (float)(M->v[p] / sc);
+                    h->av[q][p] = (lp == 16 ? (double)to_bf16(t) : to_fp16(t)) * sc;
+                }
             } else {
                 for (int64_t p = M->rp[i]; p < M->rp[i + 1]; p++)
                     h->av[q][p] = rnd(M->v[p], o->prec == 64 ? 64 : 32);
@@ -890,7 +914,8 @@ static void vcycle_level(orc_amg *h, int l, const double *b, double *x) {
         for (int64_t i = 0; i < n; i++) x[i] = rnd(x[i], pv);
         return;
     }
-    smooth(h, l, b, x, 1);
+    int ns = h->o.sweeps < 1 ? 1 : h->o.sweeps;
+    for (int s = 0; s < ns; s++) smooth(h, l, b, x, s == 0);
     if (h->agg[l]) {
         int64_t nc = h->A[l + 1]->nrow;
         double *r = h->vr[l];
@@ -905,7 +930,7 @@ static void vcycle_level(orc_amg *h, int l, const double *b, double *x) {
         for (int64_t i = 0; i < n; i++)
             if (h->agg[l][i] >= 0) x[i] = rnd(x[i] + xc[h->agg[l][i]], pv);
     }
-    smooth(h, l, b, x, 0);
+    for (int s = 0; s < ns; s++) smooth(h, l, b, x, 0);
 }
 
 void orc_vcycle(orc_amg *h, const double *b, double *x) {

@@ -63,9 +63,15 @@ typedef struct {
     double stall_ratio;  /* stop when n_{l+1} > stall_ratio n_l */
     uint64_t seed;
     int smoother;        /* 0 = L1-Jacobi, 1 = Chebyshev degree 2 */
-    int prec;            /* 64, 32 (float storage), 16 (bf16 coarse rows, float vectors) */
-    int lowp_from_level; /* for prec 16: first level stored in bf16 */
+    int prec;            /* 64, 32 (float storage), 16 / 17 (bf16 / fp16 row-scaled levels, float vectors) */
+    int lowp_from_level; /* for prec 16/17: first level stored in bf16/fp16 */
+    int sweeps;          /* smoother applications before and after the coarse correction */
 } orc_amg_opts;
+
+/* Storage rounding used by the precision emulation: 32 -> float,
+ * 16 -> bfloat16 of the float, 17 -> binary16 of the float (all round to
+ * nearest even); 64 -> x. */
+double orc_round_lowp(double x, int prec);
 
 orc_amg *orc_amg_setup(const ocsr *A, const orc_amg_opts *o);
 void orc_amg_free(orc_amg *h);

@@ -71,10 +71,11 @@ void Ctx::check_err(const char *where) {
     throw Error(MDS_ERR_NONFINITE, w + ": non-finite value");
 }
 
-KTimer::KTimer(Ctx &ctx, int k, double b) : c(ctx), cls(k) {
+KTimer::KTimer(Ctx &ctx, int k, double b, double f) : c(ctx), cls(k) {
     if (k < 0 || k >= MDS_KCLASS_COUNT) return;
     c.launches[k]++;
     c.bytes[k] += b;
+    c.flops[k] += f;
     if (!c.timing[k]) return;
     auto &v = c.evs[k];
     if (c.ev_used[k] == v.size()) {
@@ -292,6 +293,10 @@ int mds_setup_opts_default(mds_setup_opts *o) {
     o->precision = MDS_PREC_FP64;
     o->lowp_from_level = 1;
     o->kind = MDS_BLOCK_LOWER;
+    o->format = MDS_FORMAT_CSR;
+    o->sell_c = 32;
+    o->sell_sigma = 1;
+    o->sweeps = 1;
     return MDS_OK;
 }
 
@@ -304,9 +309,16 @@ int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_preco
     mds_setup_opts o;
     mds_setup_opts_default(&o);
     if (opts) o = *opts;
-    MDS_REQUIRE(o.precision == MDS_PREC_FP64 || o.precision == MDS_PREC_FP32, MDS_ERR_INVALID,
-                "precision must be MDS_PREC_FP64 or MDS_PREC_FP32");
-    MDS_REQUIRE(o.smoother == MDS_SMOOTHER_L1JACOBI, MDS_ERR_INVALID, "smoother not available");
+    MDS_REQUIRE(o.precision == MDS_PREC_FP64 || o.precision == MDS_PREC_FP32 || o.precision == MDS_PREC_BF16 ||
+                    o.precision == MDS_PREC_FP16,
+                MDS_ERR_INVALID, "unknown precision");
+    MDS_REQUIRE(o.smoother == MDS_SMOOTHER_L1JACOBI || o.smoother == MDS_SMOOTHER_CHEBYSHEV, MDS_ERR_INVALID,
+                "unknown smoother");
+    MDS_REQUIRE(o.format >= MDS_FORMAT_AUTO && o.format <= MDS_FORMAT_SELL, MDS_ERR_INVALID, "unknown format");
+    MDS_REQUIRE(o.sell_c == 8 || o.sell_c == 16 || o.sell_c == 32, MDS_ERR_INVALID, "sell_c must be 8, 16 or 32");
+    MDS_REQUIRE(o.sell_sigma == 1 || (o.sell_sigma % o.sell_c == 0 && o.sell_sigma <= 1024), MDS_ERR_INVALID,
+                "sell_sigma must be 1 or a multiple of sell_c up to 1024");
+    MDS_REQUIRE(o.sweeps >= 1 && o.sweeps <= 8, MDS_ERR_INVALID, "sweeps must be 1..8");
     MDS_REQUIRE(o.kind >= 0 && o.kind <= 2, MDS_ERR_INVALID, "bad preconditioner kind");
     MDS_REQUIRE(o.theta >= 0.0 && o.n_coarse >= 1 && o.n_coarse <= 8192, MDS_ERR_INVALID, "bad AMG options");
     auto *p = new mds_precond_s;
@@ -549,12 +561,13 @@ int mds_timing_reset(mds_ctx ctx) {
         c.ev_used[k] = 0;
         c.launches[k] = 0;
         c.bytes[k] = 0.0;
+        c.flops[k] = 0.0;
     }
     c.total_launches = 0;
     return MDS_OK;
 }
 
-int mds_timing_query(mds_ctx ctx, int k, int64_t *launches, double *ms, double *bytes) {
+int mds_timing_query(mds_ctx ctx, int k, int64_t *launches, double *ms, double *bytes, double *flops) {
     if (!ctx || k < 0 || k >= MDS_KCLASS_COUNT) return MDS_ERR_INVALID;
     Ctx *c = &ctx->c;
     API_BEGIN
@@ -568,6 +581,7 @@ int mds_timing_query(mds_ctx ctx, int k, int64_t *launches, double *ms, double *
     if (launches) *launches = c->launches[k];
     if (ms) *ms = tot;
     if (bytes) *bytes = c->bytes[k];
+    if (flops) *flops = c->flops[k];
     API_END(c)
 }
 

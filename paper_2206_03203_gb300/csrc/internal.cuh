@@ -5,7 +5,9 @@
 
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -54,6 +56,14 @@ enum : int {
     KC_VC_RESTRICT = 6,
 };
 
+// Storage of a V-cycle level: value type and sparse format.
+enum : int { VT_F64 = 0, VT_F32 = 1, VT_BF16 = 2, VT_F16 = 3 };
+enum : int { FMT_CSR = 0, FMT_SELL = 1 };
+
+struct TuneChoice {
+    int fmt, G, C, sigma;
+};
+
 struct Ctx;
 
 // Owned device allocation from the context's allocator (move-only).
@@ -89,7 +99,10 @@ struct Ctx {
     size_t ev_used[MDS_KCLASS_COUNT] = {};
     int64_t launches[MDS_KCLASS_COUNT] = {};
     double bytes[MDS_KCLASS_COUNT] = {};
+    double flops[MDS_KCLASS_COUNT] = {};
     int64_t total_launches = 0;
+    // autotuner choices by (rows, nonzeros, value type)
+    std::map<std::tuple<int64_t, int64_t, int>, TuneChoice> tune_cache;
 
     void *raw_alloc(size_t n);
     void raw_free(void *p);
@@ -117,13 +130,21 @@ struct KTimer {
     Ctx &c;
     int cls;
     KTimerRec *rec = nullptr;
-    KTimer(Ctx &ctx, int k, double bytes);
+    KTimer(Ctx &ctx, int k, double bytes, double flops = 0.0);
     ~KTimer();
 };
 
 #define MDS_LAUNCH(ctx, cls, bytes, kern, grid, block, smem, ...)                  \
     do {                                                                           \
         ::mds::KTimer kt_((ctx), (cls), (double)(bytes));                          \
+        kern<<<(grid), (block), (smem), (ctx).stream>>>(__VA_ARGS__);               \
+        (ctx).post_launch();                                                       \
+    } while (0)
+
+// as MDS_LAUNCH, also counting the launch's algorithmic floating-point operations
+#define MDS_LAUNCH_F(ctx, cls, bytes, flops, kern, grid, block, smem, ...)         \
+    do {                                                                           \
+        ::mds::KTimer kt_((ctx), (cls), (double)(bytes), (double)(flops));         \
         kern<<<(grid), (block), (smem), (ctx).stream>>>(__VA_ARGS__);               \
         (ctx).post_launch();                                                       \
     } while (0)
@@ -192,10 +213,18 @@ struct Level {
     Buf mem;          // int32 [#aggregated], ascending within an aggregate
     Buf l1;           // FP64 [n]
     Buf dinv;         // [n] 1/l1 in the vector precision
-    Buf vals_lp;      // values in the level precision (FP32) when not FP64
-    Buf b, x, r;      // work vectors in the vector precision
     bool has_coarse = false;
     int64_t nc = 0;
+    // storage used by the V-cycle
+    int vt = VT_F64;  // value type
+    int fmt = FMT_CSR;
+    int G = 4;        // CSR lanes per row
+    Buf vals_lp;      // CSR values in vt (not for FP64)
+    Buf rscale;       // float [n] power-of-two row scales (BF16/FP16)
+    int sell_c = 32;
+    int64_t sell_nslice = 0, sell_nnz = 0;
+    Buf sell_ptr, sell_len, sell_col, sell_val, sell_perm;
+    Buf b, x, r, y, d, t;  // work vectors in the vector precision
 };
 
 struct Hierarchy {
@@ -203,11 +232,14 @@ struct Hierarchy {
     bool dense = false;
     int64_t nd = 0;
     Buf Ainv;         // FP64 [nd nd] inverse of the coarsest matrix
-    int prec = 64;    // 64 or 32
+    int prec = 64;    // vector precision: 64 or 32
     int smoother = 0;
+    int sweeps = 1;
 };
 
 void amg_setup(Ctx &c, const mds_csr &A, const mds_setup_opts &o, Hierarchy &h);
+// per-level value storage and format (k_vcycle.cu), run at the end of amg_setup
+void level_storage(Ctx &c, Hierarchy &h, const mds_setup_opts &o);
 
 // ---- dense (k_dense.cu) ----
 // Cholesky of the n x n SPD matrix stored densely, then its inverse.

@@ -25,22 +25,33 @@ static unsigned red_grid(int64_t n) {
 // partial[q][blk] = sum over this block's rows of V[q][i] w[i]; grid.y = q.
 // One dot product per block row keeps registers low; w is re-read once per q
 // and stays resident in L2, V is read once from HBM.
-__global__ void __launch_bounds__(RED_BLOCK) k_mdot(int64_t n, const double *__restrict__ V, int64_t ldv,
-                                                     const double *__restrict__ w, double *__restrict__ partial) {
+__global__ void __launch_bounds__(RED_BLOCK) k_mdot(int64_t n, const double *__restrict__ V, int64_t ldv, int nq,
+                                                     const double *__restrict__ w, double *__restrict__ partial,
+                                                     const double *__restrict__ run_flag) {
+    if (run_flag && *run_flag == 0.0) return;
     __shared__ double ws[RED_BLOCK / 32];
-    const double *v = V + (int64_t)blockIdx.y * ldv;
-    double s = 0.0;
+    // rows of V are 16-byte aligned (ldv even); w is a row of V
+    const double *v = (int)blockIdx.y < nq ? V + (int64_t)blockIdx.y * ldv : w;
+    const double2 *v2 = reinterpret_cast<const double2 *>(v);
+    const double2 *w2 = reinterpret_cast<const double2 *>(w);
+    int64_t n2 = n >> 1;
+    double s0 = 0.0, s1 = 0.0;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    for (; i + 3 * stride < n; i += 4 * stride) {
-        double a0 = v[i], a1 = v[i + stride], a2 = v[i + 2 * stride], a3 = v[i + 3 * stride];
-        double b0 = w[i], b1 = w[i + stride], b2 = w[i + 2 * stride], b3 = w[i + 3 * stride];
-        s += a0 * b0;
-        s += a1 * b1;
-        s += a2 * b2;
-        s += a3 * b3;
+    for (; i + stride < n2; i += 2 * stride) {
+        double2 a = v2[i], b = w2[i], c = v2[i + stride], d = w2[i + stride];
+        s0 += a.x * b.x;
+        s1 += a.y * b.y;
+        s0 += c.x * d.x;
+        s1 += c.y * d.y;
     }
-    for (; i < n; i += stride) s += v[i] * w[i];
+    for (; i < n2; i += stride) {
+        double2 a = v2[i], b = w2[i];
+        s0 += a.x * b.x;
+        s1 += a.y * b.y;
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) s0 += v[n - 1] * w[n - 1];
+    double s = s0 + s1;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
     __syncthreads();
@@ -53,7 +64,8 @@ __global__ void __launch_bounds__(RED_BLOCK) k_mdot(int64_t n, const double *__r
 
 // out[q] (+)= sum_b partial[q][b], one warp per q, fixed order
 __global__ void k_reduce_rows(const double *__restrict__ partial, int nblk, int nq, double *__restrict__ out,
-                              int accumulate) {
+                              int accumulate, const double *__restrict__ run_flag) {
+    if (run_flag && *run_flag == 0.0) return;
     int q = blockIdx.x;
     if (q >= nq) return;
     double s = 0.0;
@@ -62,34 +74,62 @@ __global__ void k_reduce_rows(const double *__restrict__ partial, int nblk, int 
     if (threadIdx.x == 0) out[q] = accumulate ? out[q] + s : s;
 }
 
-// out[q] (+)= sum over blocks of partial[blk][q] (stride QMAX), fixed order
+// out[q] (+)= sum over blocks of partial[blk][q] (stride QMAX); one warp per q,
+// fixed order
 __global__ void k_reduce_cols(const double *__restrict__ partial, int nblk, int nq, double *__restrict__ out,
                               int accumulate) {
-    int q = threadIdx.x;
+    int q = blockIdx.x;
     if (q >= nq) return;
     double s = 0.0;
-    for (int b = 0; b < nblk; b++) s += partial[(int64_t)b * QMAX + q];
-    out[q] = accumulate ? out[q] + s : s;
+    for (int b = threadIdx.x; b < nblk; b += 32) s += partial[(int64_t)b * QMAX + q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) out[q] = accumulate ? out[q] + s : s;
 }
 
-// w_i += sign * sum_q coef_q V[q][i]; optional block partials of w_i^2
-template <int SIGN>
+// w_i += sign * sum_q coef_q V[q][i]; optional block partials of w_i^2.
+// VEC: w and the rows of V are 16-byte aligned, two elements per thread.
+template <int SIGN, bool VEC>
 __global__ void __launch_bounds__(RED_BLOCK) k_maxpy(int64_t n, const double *__restrict__ V, int64_t ldv, int nq,
                                                       const double *__restrict__ coef, double *__restrict__ w,
-                                                      double *__restrict__ partial) {
+                                                      double *__restrict__ partial, const double *__restrict__ run_flag) {
+    if (run_flag && *run_flag == 0.0) return;
     __shared__ double cs[QMAX];
     __shared__ double ws[RED_BLOCK / 32];
     if (threadIdx.x < QMAX) cs[threadIdx.x] = threadIdx.x < nq ? coef[threadIdx.x] : 0.0;
     __syncthreads();
     double nrm = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
-#pragma unroll
-        for (int q = 0; q < QMAX; q++)
-            if (q < nq) s += cs[q] * V[q * ldv + i];
-        double wi = SIGN > 0 ? w[i] + s : w[i] - s;
-        w[i] = wi;
-        nrm += wi * wi;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (VEC) {
+        int64_t n2 = n >> 1;
+        double2 *w2 = reinterpret_cast<double2 *>(w);
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+            double s0 = 0.0, s1 = 0.0;
+            for (int q = 0; q < nq; q++) {
+                double2 a = reinterpret_cast<const double2 *>(V + (int64_t)q * ldv)[i];
+                s0 += cs[q] * a.x;
+                s1 += cs[q] * a.y;
+            }
+            double2 x = w2[i];
+            x.x = SIGN > 0 ? x.x + s0 : x.x - s0;
+            x.y = SIGN > 0 ? x.y + s1 : x.y - s1;
+            w2[i] = x;
+            nrm += x.x * x.x + x.y * x.y;
+        }
+        if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+            double s = 0.0;
+            for (int q = 0; q < nq; q++) s += cs[q] * V[(int64_t)q * ldv + n - 1];
+            double x = SIGN > 0 ? w[n - 1] + s : w[n - 1] - s;
+            w[n - 1] = x;
+            nrm += x * x;
+        }
+    } else {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+            double s = 0.0;
+            for (int q = 0; q < nq; q++) s += cs[q] * V[(int64_t)q * ldv + i];
+            double wi = SIGN > 0 ? w[i] + s : w[i] - s;
+            w[i] = wi;
+            nrm += wi * wi;
+        }
     }
     if (partial) {
         for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
@@ -136,14 +176,27 @@ __global__ void k_cycle_start(const double *__restrict__ normsq, double *__restr
     for (int q = 1; q <= m; q++) g[q] = 0.0;
 }
 
-// Arnoldi column j: H[0..j][j] = h, H[j+1][j] = ||w||; apply the previous
-// rotations, form the new one, update g.  scal[2] = |g_{j+1}|, scal[3] =
-// 1/H[j+1][j] (0 on breakdown), scal[4] = breakdown flag.
+// DGKS test after the first Gram-Schmidt pass: reorthogonalise when the
+// projection removed more than half of ||w||^2 (||w_new|| < ||w|| / sqrt(2)).
+// flag[0] = 1 to run the second pass; the second-pass coefficients start at 0.
+__global__ void k_dgks(const double *__restrict__ nsq_before, const double *__restrict__ nsq_after,
+                       double *__restrict__ flag, double *__restrict__ h2, int nq) {
+    double run = (nsq_after[0] < 0.5 * nsq_before[0]) ? 1.0 : 0.0;
+    flag[0] = run;
+    for (int q = 0; q < nq; q++) h2[q] = 0.0;
+}
+
+// Arnoldi column j: H[0..j][j] = h1 + h2, H[j+1][j] = ||w|| (after the second
+// pass when it ran); apply the previous rotations, form the new one, update
+// g.  scal[2] = |g_{j+1}|, scal[3] = 1/H[j+1][j] (0 on breakdown), scal[4] =
+// breakdown flag (1 lucky, 2 non-finite).
 __global__ void k_arnoldi(int j, int m, double *__restrict__ H, const double *__restrict__ h,
-                          const double *__restrict__ normsq, double *__restrict__ cs, double *__restrict__ sn,
-                          double *__restrict__ g, double *__restrict__ scal) {
-    for (int q = 0; q <= j; q++) H[q * m + j] = h[q];
-    double hn = sqrt(normsq[0]);
+                          const double *__restrict__ h2, const double *__restrict__ nsq1,
+                          const double *__restrict__ nsq2, const double *__restrict__ flag, double *__restrict__ cs,
+                          double *__restrict__ sn, double *__restrict__ g, double *__restrict__ scal) {
+    bool two = flag[0] != 0.0;
+    for (int q = 0; q <= j; q++) H[q * m + j] = two ? h[q] + h2[q] : h[q];
+    double hn = sqrt(two ? nsq2[0] : nsq1[0]);
     H[(j + 1) * m + j] = hn;
     for (int q = 0; q < j; q++) {
         double a = H[q * m + j], c = H[(q + 1) * m + j];
@@ -162,6 +215,7 @@ __global__ void k_arnoldi(int j, int m, double *__restrict__ H, const double *__
     bool bad = !(hn > 0.0) || !isfinite(hn) || !isfinite(rr);
     scal[3] = bad ? 0.0 : 1.0 / hn;
     scal[4] = !isfinite(hn) || !isfinite(rr) ? 2.0 : (hn == 0.0 ? 1.0 : 0.0);
+    scal[5] += two ? 1.0 : 0.0;
 }
 
 // upper-triangular solve H y = g (k columns)
@@ -234,13 +288,17 @@ KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, 
     R.grid = red_grid(n);
     R.mgrid = mdot_grid(n);
     R.partial = Buf(&c, sizeof(double) * (size_t)(R.grid > R.mgrid ? R.grid : R.mgrid) * QMAX);
-    Buf V(&c, sizeof(double) * (size_t)(m + 1) * (size_t)n);
-    Buf Z(&c, sizeof(double) * (size_t)m * (size_t)n);
+    // basis rows padded to 64 elements: 16-byte aligned rows for vector loads
+    const int64_t ld = (n + 63) / 64 * 64;
+    Buf V(&c, sizeof(double) * (size_t)(m + 1) * (size_t)ld);
+    Buf Z(&c, sizeof(double) * (size_t)m * (size_t)ld);
     Buf H(&c, sizeof(double) * (size_t)(m + 1) * m);
     Buf small(&c, sizeof(double) * 256);
     double *d = small.as<double>();
+    MDS_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * 256, c.stream));
     // cs, sn, g, y, h (first CGS pass), h + 32 (second pass), scalars, norms
-    double *cs = d, *sn = d + 32, *g = d + 64, *y = d + 96, *h = d + 128, *scal = d + 192, *nsq = d + 224;
+    double *cs = d, *sn = d + 32, *g = d + 64, *y = d + 96, *h = d + 128, *h2 = d + 160, *scal = d + 192,
+           *nsq = d + 224, *nsq2 = d + 225, *dflag = d + 226;
     double *Vp = V.as<double>(), *Zp = Z.as<double>();
     // ||b||
     dot_dev(c, R, n, b, b, nsq);
@@ -274,24 +332,31 @@ KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, 
         int kdone = 0;
         int flag = 0;
         for (int j = 0; j < m; j++) {
-            double *vj = Vp + (size_t)j * n, *zj = Zp + (size_t)j * n, *w = Vp + (size_t)(j + 1) * n;
+            double *vj = Vp + (size_t)j * ld, *zj = Zp + (size_t)j * ld, *w = Vp + (size_t)(j + 1) * ld;
             M(vj, zj);
             it++;
             spmv_f64(c, A, zj, w, KC_SPMV);
-            // CGS2: h = V^T w; w -= V h; twice
+            // classical Gram-Schmidt: h = V^T w (and ||w||^2), w -= V h, ||w||^2;
+            // a second pass only when the DGKS test asks for it (device flag)
             int nq = j + 1;
-            for (int pass = 0; pass < 2; pass++) {
-                MDS_LAUNCH(c, KC_GS_DOT, 8.0 * n * (nq + 1), k_mdot, dim3(R.mgrid, nq), RED_BLOCK, 0, n, Vp, n, w,
-                           R.partial.as<double>());
-                MDS_LAUNCH(c, KC_NONE, 0, k_reduce_rows, nq, 32, 0, R.partial.as<double>(), (int)R.mgrid, nq,
-                           pass == 0 ? h : h + 32, 0);
-                MDS_LAUNCH(c, KC_GS_AXPY, 8.0 * n * (nq + 2), k_maxpy<-1>, R.grid, RED_BLOCK, 0, n, Vp, n, nq,
-                           pass == 0 ? h : h + 32, w, pass == 1 ? R.partial.as<double>() : nullptr);
-            }
+            double fl = 2.0 * (double)n * nq;
+            MDS_LAUNCH_F(c, KC_GS_DOT, 8.0 * n * (nq + 1), fl + 2.0 * n, k_mdot, dim3(R.mgrid, nq + 1), RED_BLOCK, 0,
+                         n, Vp, ld, nq, w, R.partial.as<double>(), (const double *)nullptr);
+            MDS_LAUNCH(c, KC_NONE, 0, k_reduce_rows, nq + 1, 32, 0, R.partial.as<double>(), (int)R.mgrid, nq + 1, h,
+                       0, (const double *)nullptr);
+            MDS_LAUNCH_F(c, KC_GS_AXPY, 8.0 * n * (nq + 2), fl + 2.0 * n, (k_maxpy<-1, true>), R.grid, RED_BLOCK, 0,
+                         n, Vp, ld, nq, h, w, R.partial.as<double>(), (const double *)nullptr);
             MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.partial.as<double>(), (int)R.grid, 1, nsq, 0);
-            // h += h2
-            MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, h + 32, 1, nq, h, 1);
-            MDS_LAUNCH(c, KC_NONE, 0, k_arnoldi, 1, 1, 0, j, m, H.as<double>(), h, nsq, cs, sn, g, scal);
+            MDS_LAUNCH(c, KC_NONE, 0, k_dgks, 1, 1, 0, h + nq, nsq, dflag, h2, nq);
+            MDS_LAUNCH_F(c, KC_GS_DOT, 8.0 * n * (nq + 1), fl, k_mdot, dim3(R.mgrid, nq), RED_BLOCK, 0, n, Vp, ld, nq,
+                         w, R.partial.as<double>(), (const double *)dflag);
+            MDS_LAUNCH(c, KC_NONE, 0, k_reduce_rows, nq, 32, 0, R.partial.as<double>(), (int)R.mgrid, nq, h2, 0,
+                       (const double *)dflag);
+            MDS_LAUNCH_F(c, KC_GS_AXPY, 8.0 * n * (nq + 2), fl + 2.0 * n, (k_maxpy<-1, true>), R.grid, RED_BLOCK, 0,
+                         n, Vp, ld, nq, h2, w, R.partial.as<double>(), (const double *)dflag);
+            MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.partial.as<double>(), (int)R.grid, 1, nsq2, 0);
+            MDS_LAUNCH(c, KC_NONE, 0, k_arnoldi, 1, 1, 0, j, m, H.as<double>(), h, h2, nsq, nsq2, dflag, cs, sn, g,
+                       scal);
             MDS_LAUNCH(c, KC_NONE, 16.0 * n, k_scale, red_grid(n), RED_BLOCK, 0, n, w, scal + 3, w);
             MDS_CUDA(cudaMemcpyAsync(c.h_pin, scal, 5 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
             c.sync();
@@ -310,8 +375,8 @@ KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, 
             break;
         }
         MDS_LAUNCH(c, KC_NONE, 0, k_backsolve, 1, 1, 0, kdone, m, H.as<double>(), g, y);
-        MDS_LAUNCH(c, KC_NONE, 8.0 * n * (kdone + 2), k_maxpy<1>, R.grid, RED_BLOCK, 0, n, Zp, n, kdone, y, x,
-                   nullptr);
+        MDS_LAUNCH(c, KC_NONE, 8.0 * n * (kdone + 2), (k_maxpy<1, false>), R.grid, RED_BLOCK, 0, n, Zp, ld, kdone,
+                   y, x, nullptr, (const double *)nullptr);
         restarts++;
     }
     // true residual at exit

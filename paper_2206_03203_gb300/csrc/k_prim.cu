@@ -141,7 +141,7 @@ static void spmv_launch(Ctx &c, const mds_csr &A, const XT *x, const double *r, 
     unsigned grid = grid_for(A.nrow * G, block);
     double bytes = 12.0 * (double)A.nnz + 4.0 * (double)(A.nrow + 1) + sizeof(XT) * (double)A.ncol +
                    sizeof(OT) * (double)A.nrow + (MODE == 1 ? 8.0 * A.nrow : 0.0);
-    MDS_LAUNCH(c, kclass, bytes, (k_spmv_csr<G, double, XT, OT, MODE>), grid, block, 0, A.nrow, A.row_ptr,
+    MDS_LAUNCH_F(c, kclass, bytes, 2.0 * A.nnz, (k_spmv_csr<G, double, XT, OT, MODE>), grid, block, 0, A.nrow, A.row_ptr,
                A.col, A.val, x, r, y);
 }
 

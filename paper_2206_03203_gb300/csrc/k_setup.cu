@@ -385,11 +385,6 @@ __global__ void k_l1(int64_t n, const int32_t *__restrict__ rp, const int32_t *_
     dinv[i] = (DT)(1.0 / s);
 }
 
-__global__ void k_vals_f32(int64_t nnz, const double *__restrict__ v, float *__restrict__ o) {
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
-        o[p] = (float)v[p];
-}
-
 static DCsr copy_csr(Ctx &c, const mds_csr &A) {
     DCsr B = csr_alloc(c, A.nrow, A.ncol, A.nnz);
     MDS_CUDA(cudaMemcpyAsync(B.rowp(), A.row_ptr, sizeof(int32_t) * (size_t)(A.nrow + 1), cudaMemcpyDeviceToDevice,
@@ -439,6 +434,7 @@ void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h)
     h.dense = false;
     h.prec = o.precision == MDS_PREC_FP64 ? 64 : 32;
     h.smoother = o.smoother;
+    h.sweeps = o.sweeps < 1 ? 1 : o.sweeps;
     int maxl = o.max_levels < 1 ? 1 : (o.max_levels > 32 ? 32 : o.max_levels);
     h.lv.emplace_back();
     h.lv[0].A = copy_csr(c, A0);
@@ -510,32 +506,33 @@ void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h)
         h.lv.emplace_back();
         h.lv.back().A = std::move(Ac);
     }
-    // per-level smoother data, precision copies and work vectors
+    // per-level smoother data and work vectors
     size_t vb = h.prec == 64 ? sizeof(double) : sizeof(float);
     for (auto &L : h.lv) {
         int64_t n = L.A.nrow;
         unsigned gr = grid_for(n, 256);
+        size_t nb = vb * (size_t)(n > 0 ? n : 1);
         L.l1 = Buf(&c, sizeof(double) * (size_t)(n > 0 ? n : 1));
-        L.dinv = Buf(&c, vb * (size_t)(n > 0 ? n : 1));
-        if (h.prec == 64) {
+        L.dinv = Buf(&c, nb);
+        if (h.prec == 64)
             MDS_LAUNCH(c, KC_NONE, 0, k_l1<double>, gr, 256, 0, n, L.A.rowp(), L.A.cols(), L.A.vals(),
                        L.l1.as<double>(), L.dinv.as<double>());
-        } else {
+        else
             MDS_LAUNCH(c, KC_NONE, 0, k_l1<float>, gr, 256, 0, n, L.A.rowp(), L.A.cols(), L.A.vals(),
                        L.l1.as<double>(), L.dinv.as<float>());
-            L.vals_lp = Buf(&c, sizeof(float) * (size_t)(L.A.nnz > 0 ? L.A.nnz : 1));
-            MDS_LAUNCH(c, KC_NONE, 0, k_vals_f32, grid_for(L.A.nnz, 256) > 8192 ? 8192 : grid_for(L.A.nnz, 256), 256, 0,
-                       L.A.nnz, L.A.vals(), L.vals_lp.as<float>());
-        }
-        L.b = Buf(&c, vb * (size_t)(n > 0 ? n : 1));
-        L.x = Buf(&c, vb * (size_t)(n > 0 ? n : 1));
-        L.r = Buf(&c, vb * (size_t)(n > 0 ? n : 1));
+        L.b = Buf(&c, nb);
+        L.x = Buf(&c, nb);
+        L.r = Buf(&c, nb);
+        L.y = Buf(&c, nb);
+        L.t = Buf(&c, nb);
+        if (h.smoother == MDS_SMOOTHER_CHEBYSHEV) L.d = Buf(&c, nb);
     }
     if (h.dense) {
         Level &L = h.lv.back();
         h.nd = L.A.nrow;
         dense_spd_inverse(c, L.A.view(), h.Ainv);
     }
+    level_storage(c, h, o);
     c.sync();
 }
 

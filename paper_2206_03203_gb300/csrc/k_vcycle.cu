@@ -1,37 +1,191 @@
-// One aggregation-AMG V-cycle (Sec. 3.3: Q_mm and Q_ff of Algorithm 1).
+// One aggregation-AMG V-cycle (Sec. 3.3: Q_mm and Q_ff of Algorithm 1), and
+// the per-level storage it runs on.
 //
 // Per level, with L1 diagonal D1 and piecewise-constant P:
-//   pre-smooth from zero      x = D1^-1 b
+//   pre-smoothing from zero   x = S(0; b)            (L1-Jacobi or Chebyshev)
 //   residual + restriction    b_c = P^T (b - A x)
-//   coarse correction         x_c = V(b_c)      (dense inverse on the last level)
-//   prolongation + smoothing  x <- x + P x_c;  x <- x + D1^-1 (b - A x)
-// The pre-smoothed x is never stored: the residual kernel forms D1^-1 b on
-// the fly, and the post-smoothing kernel forms x + P x_c on the fly at every
-// neighbour, so each level costs two passes over its matrix.
+//   coarse correction         x_c = V(b_c)           (dense inverse on the last level)
+//   prolongation + smoothing  y = x + P x_c;  x = S(y; b)
+// Storage per level: values in FP64, FP32, or BF16/FP16 with power-of-two
+// row scales (a_ij = s_i q_ij, |q_ij| <= 1); matrix in CSR (G lanes per row)
+// or SELL-C-sigma (one thread per row, slices of C rows stored column-major,
+// rows sorted by length inside windows of sigma rows).
+//
+// Two kernel forms.  Memory-bound levels (FP32 and below, one L1-Jacobi
+// sweep) form D1^-1 b and x + P x_c on the fly at every neighbour, so a level
+// costs two matrix passes and the smoothed iterates are never stored.  FP64
+// levels are bound by GB300's FP64 pipe, so there the iterates are stored
+// once per row instead of being re-formed per nonzero; Chebyshev and
+// multi-sweep smoothing also use the stored form.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <map>
+#include <tuple>
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace mds {
 
-// r_i = b_i - sum_j a_ij (dinv_j b_j)
-template <int G, class VT, class XT>
-__global__ void __launch_bounds__(256) k_vc_resid0(int64_t n, const int32_t *__restrict__ rp,
-                                                    const int32_t *__restrict__ ci, const VT *__restrict__ v,
-                                                    const XT *__restrict__ dinv, const XT *__restrict__ b,
-                                                    XT *__restrict__ r) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t row = t / G;
-    int lane = (int)(t % G);
+template <class XT, class VT> __device__ __forceinline__ XT cvt(VT v) { return (XT)v; }
+template <> __device__ __forceinline__ float cvt<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ float cvt<float, __half>(__half v) { return __half2float(v); }
+
+// Device view of one level's operator in its storage format.
+template <class VT> struct LvlMat {
+    int64_t n;
+    const int32_t *rp, *ci;    // CSR
+    const VT *v;               // CSR values or SELL values
+    const int32_t *sp, *sl;    // SELL slice offsets and lengths
+    const int32_t *sc;         // SELL columns
+    const int32_t *perm;       // SELL stored row -> original row (NULL: identity)
+    int C;                     // SELL slice height
+    const float *rscale;       // row scales (NULL: unscaled)
+};
+
+// Sum over the nonzeros of one row of a_ij * f(j): CSR with G lanes per row
+// (lane-partial sums), or SELL with one thread per row (G == 0).
+template <int G, class VT, class XT, class F>
+__device__ __forceinline__ XT row_sum(const LvlMat<VT> &A, int64_t row, int lane, F f) {
     XT s = 0;
-    if (row < n) {
-        int32_t p0 = rp[row], p1 = rp[row + 1];
-        for (int32_t p = p0 + lane; p < p1; p += G) {
-            int32_t j = ci[p];
-            s += (XT)v[p] * (__ldg(dinv + j) * __ldg(b + j));
+    if (G > 0) {
+        int32_t p0 = A.rp[row], p1 = A.rp[row + 1];
+        for (int32_t p = p0 + lane; p < p1; p += G) s += cvt<XT>(A.v[p]) * f(A.ci[p]);
+    } else {
+        int64_t sl = row / A.C;
+        int r = (int)(row - sl * A.C);
+        int32_t off = A.sp[sl], len = A.sl[sl];
+        for (int32_t k = 0; k < len; k++) {
+            int32_t p = off + k * A.C + r;
+            s += cvt<XT>(A.v[p]) * f(A.sc[p]);
         }
     }
+    return s;
+}
+
+template <int G, class XT> __device__ __forceinline__ XT lane_reduce(XT s) {
+    if (G > 1) {
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, G);
-    if (row < n && lane == 0) r[row] = b[row] - s;
+        for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, G);
+    }
+    return s;
+}
+
+template <int G> __device__ __forceinline__ void row_of(int64_t &row, int &lane) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (G > 0) {
+        row = t / G;
+        lane = (int)(t % G);
+    } else {
+        row = t;
+        lane = 0;
+    }
+}
+
+enum { VK_RESID0 = 0, VK_POST = 1, VK_RESID = 2, VK_SMOOTH = 3 };
+
+// Functors giving the neighbour value each kernel multiplies by a_ij.
+template <class XT> struct NbD1b {  // D1^-1 b
+    const XT *dinv, *b;
+    __device__ XT operator()(int32_t j) const { return __ldg(dinv + j) * __ldg(b + j); }
+};
+template <class XT> struct NbPost {  // D1^-1 b + P x_c
+    const XT *dinv, *b, *xc;
+    const int32_t *agg;
+    __device__ XT operator()(int32_t j) const {
+        XT y = __ldg(dinv + j) * __ldg(b + j);
+        if (agg) {
+            int32_t a = __ldg(agg + j);
+            if (a >= 0) y += __ldg(xc + a);
+        }
+        return y;
+    }
+};
+template <class XT> struct NbStored {  // a stored vector
+    const XT *x;
+    __device__ XT operator()(int32_t j) const { return __ldg(x + j); }
+};
+
+// VK_RESID0: r = b - A (D1^-1 b)
+// VK_POST:   x = y + D1^-1 (b - A y),  y = D1^-1 b + P x_c   (formed per neighbour)
+// VK_RESID:  r = b - A x
+// VK_SMOOTH: x = y + D1^-1 (b - A y)                       (y stored)
+template <int G, class VT, class XT, int K>
+__global__ void __launch_bounds__(256) k_level(LvlMat<VT> A, const XT *__restrict__ dinv, const XT *__restrict__ b,
+                                               const XT *__restrict__ xin, const int32_t *__restrict__ agg,
+                                               const XT *__restrict__ xc, XT *__restrict__ out) {
+    int64_t row;
+    int lane;
+    row_of<G>(row, lane);
+    XT s = 0;
+    bool live = row < A.n;
+    if (live) {
+        if (K == VK_RESID0)
+            s = row_sum<G, VT, XT>(A, row, lane, NbD1b<XT>{dinv, b});
+        else if (K == VK_POST)
+            s = row_sum<G, VT, XT>(A, row, lane, NbPost<XT>{dinv, b, xc, agg});
+        else
+            s = row_sum<G, VT, XT>(A, row, lane, NbStored<XT>{xin});
+    }
+    s = lane_reduce<G, XT>(s);
+    if (live && lane == 0) {
+        int64_t o = (G == 0 && A.perm) ? A.perm[row] : row;
+        if (A.rscale) s *= (XT)A.rscale[o];
+        if (K == VK_RESID0 || K == VK_RESID) {
+            out[o] = b[o] - s;
+        } else if (K == VK_POST) {
+            XT y = dinv[o] * b[o];
+            if (agg) {
+                int32_t a = agg[o];
+                if (a >= 0) y += xc[a];
+            }
+            out[o] = y + dinv[o] * (b[o] - s);
+        } else {
+            out[o] = xin[o] + dinv[o] * (b[o] - s);
+        }
+    }
+}
+
+// ---- elementwise kernels of the stored form
+template <class XT>
+__global__ void k_vc_x0(int64_t n, const XT *__restrict__ dinv, const XT *__restrict__ b, XT *__restrict__ x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = dinv[i] * b[i];
+}
+
+// y_i += x_c[agg_i]
+template <class XT>
+__global__ void k_vc_prolong(int64_t n, const int32_t *__restrict__ agg, const XT *__restrict__ xc,
+                             XT *__restrict__ y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t a = agg[i];
+        if (a >= 0) y[i] += xc[a];
+    }
+}
+
+// Chebyshev (Saad, Iterative Methods, Alg. 12.1 for D1^-1 A on [lo, hi]):
+// first step d = (D1^-1 r) / theta, x = x0 + d; later steps
+// d = c1 d + c2 D1^-1 r, x += d.
+template <class XT>
+__global__ void k_cheb_first(int64_t n, const XT *__restrict__ dinv, const XT *__restrict__ r,
+                             const XT *__restrict__ x0, XT inv_theta, XT *__restrict__ d, XT *__restrict__ x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        XT di = dinv[i] * r[i] * inv_theta;
+        d[i] = di;
+        x[i] = x0 ? x0[i] + di : di;
+    }
+}
+
+template <class XT>
+__global__ void k_cheb_next(int64_t n, const XT *__restrict__ dinv, const XT *__restrict__ r, XT c1, XT c2,
+                            XT *__restrict__ d, XT *__restrict__ x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        XT di = c1 * d[i] + c2 * (dinv[i] * r[i]);
+        d[i] = di;
+        x[i] += di;
+    }
 }
 
 // b_c[I] = sum of r over the members of aggregate I (ascending)
@@ -45,89 +199,133 @@ __global__ void k_vc_restrict(int64_t nc, const int32_t *__restrict__ off, const
     bc[I] = s;
 }
 
-// x_i = y_i + dinv_i (b_i - sum_j a_ij y_j),  y_j = dinv_j b_j + x_c[agg_j]
-template <int G, class VT, class XT>
-__global__ void __launch_bounds__(256) k_vc_post(int64_t n, const int32_t *__restrict__ rp,
-                                                  const int32_t *__restrict__ ci, const VT *__restrict__ v,
-                                                  const XT *__restrict__ dinv, const XT *__restrict__ b,
-                                                  const int32_t *__restrict__ agg, const XT *__restrict__ xc,
-                                                  XT *__restrict__ x) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t row = t / G;
-    int lane = (int)(t % G);
-    XT s = 0;
-    if (row < n) {
-        int32_t p0 = rp[row], p1 = rp[row + 1];
-        for (int32_t p = p0 + lane; p < p1; p += G) {
-            int32_t j = ci[p];
-            XT y = __ldg(dinv + j) * __ldg(b + j);
-            if (agg) {
-                int32_t a = __ldg(agg + j);
-                if (a >= 0) y += __ldg(xc + a);
-            }
-            s += (XT)v[p] * y;
-        }
+// ---------------------------------------------------------------- host dispatch
+
+template <class VT> static LvlMat<VT> lvl_view(const Level &L) {
+    LvlMat<VT> m{};
+    m.n = L.A.nrow;
+    m.rp = L.A.rowp();
+    m.ci = L.A.cols();
+    m.rscale = L.rscale.p ? L.rscale.as<float>() : nullptr;
+    if (L.fmt == FMT_SELL) {
+        m.v = L.sell_val.as<VT>();
+        m.sp = L.sell_ptr.as<int32_t>();
+        m.sl = L.sell_len.as<int32_t>();
+        m.sc = L.sell_col.as<int32_t>();
+        m.perm = L.sell_perm.p ? L.sell_perm.as<int32_t>() : nullptr;
+        m.C = L.sell_c;
+    } else {
+        m.v = std::is_same<VT, double>::value ? (const VT *)L.A.vals() : L.vals_lp.as<VT>();
+        m.C = 1;
     }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, G);
-    if (row < n && lane == 0) {
-        XT yi = dinv[row] * b[row];
-        if (agg) {
-            int32_t a = agg[row];
-            if (a >= 0) yi += xc[a];
-        }
-        x[row] = yi + dinv[row] * (b[row] - s);
-    }
+    return m;
 }
 
-template <class XT> struct VcKernels {
-    template <int G>
-    static void resid(Ctx &c, int64_t n, const Level &L, const XT *vals, const XT *b, XT *r) {
-        double bytes = (sizeof(XT) + 4.0) * L.A.nnz + 4.0 * (n + 1) + 3.0 * sizeof(XT) * n;
-        MDS_LAUNCH(c, KC_VC_RESID, bytes, (k_vc_resid0<G, XT, XT>), grid_for(n * G, 256),
-                   256, 0, n, L.A.rowp(), L.A.cols(), vals, L.dinv.as<XT>(), b, r);
-    }
-    template <int G>
-    static void post(Ctx &c, int64_t n, const Level &L, const XT *vals, const XT *b, const int32_t *agg,
-                     const XT *xc, XT *x, int64_t nc) {
-        double bytes = (sizeof(XT) + 4.0) * L.A.nnz + 4.0 * (n + 1) + 3.0 * sizeof(XT) * n +
-                       (agg ? 4.0 * n + sizeof(XT) * (double)nc : 0.0);
-        MDS_LAUNCH(c, KC_VC_POST, bytes, (k_vc_post<G, XT, XT>), grid_for(n * G, 256), 256, 0, n, L.A.rowp(),
-                   L.A.cols(), vals, L.dinv.as<XT>(), b, agg, xc, x);
-    }
-};
-
-template <class XT>
-static int pick_g(const Level &L) {
-    double avg = L.A.nrow ? (double)L.A.nnz / (double)L.A.nrow : 0.0;
-    return avg <= 4.0 ? 2 : avg <= 10.0 ? 4 : avg <= 24.0 ? 8 : 32;
-}
-
-template <class XT>
-static void level_resid(Ctx &c, const Level &L, const XT *vals, const XT *b, XT *r) {
+template <class VT, class XT, int K>
+static void launch_level(Ctx &c, const Level &L, const XT *dinv, const XT *b, const XT *xin, const int32_t *agg,
+                         const XT *xc, XT *out, int64_t nc) {
+    LvlMat<VT> m = lvl_view<VT>(L);
     int64_t n = L.A.nrow;
-    switch (pick_g<XT>(L)) {
-        case 2: VcKernels<XT>::template resid<2>(c, n, L, vals, b, r); break;
-        case 4: VcKernels<XT>::template resid<4>(c, n, L, vals, b, r); break;
-        case 8: VcKernels<XT>::template resid<8>(c, n, L, vals, b, r); break;
-        default: VcKernels<XT>::template resid<32>(c, n, L, vals, b, r); break;
+    double vb = L.fmt == FMT_SELL ? (sizeof(VT) + 4.0) * (double)L.sell_nnz : (sizeof(VT) + 4.0) * L.A.nnz;
+    double bytes = vb + (L.fmt == FMT_SELL ? 8.0 * L.sell_nslice : 4.0 * (n + 1)) + 3.0 * sizeof(XT) * n +
+                   (K == VK_POST && agg ? 4.0 * n + sizeof(XT) * (double)nc : 0.0) + (L.rscale.p ? 4.0 * n : 0.0) +
+                   (K >= VK_RESID ? sizeof(XT) * (double)n : 0.0) - (K == VK_RESID ? sizeof(XT) * (double)n : 0.0);
+    double flops = 2.0 * L.A.nnz + (K == VK_RESID0 ? n : K == VK_POST ? 5.0 * n : K == VK_SMOOTH ? 3.0 * n : 0.0);
+    int cls = (K == VK_RESID0 || K == VK_RESID) ? KC_VC_RESID : KC_VC_POST;
+    if (L.fmt == FMT_SELL) {
+        int64_t rows = L.sell_nslice * L.sell_c;
+        MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<0, VT, XT, K>), grid_for(rows, 256), 256, 0, m, dinv, b, xin, agg,
+                     xc, out);
+        return;
+    }
+    switch (L.G) {
+        case 2:
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<2, VT, XT, K>), grid_for(n * 2, 256), 256, 0, m, dinv, b, xin,
+                         agg, xc, out);
+            break;
+        case 4:
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<4, VT, XT, K>), grid_for(n * 4, 256), 256, 0, m, dinv, b, xin,
+                         agg, xc, out);
+            break;
+        case 8:
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<8, VT, XT, K>), grid_for(n * 8, 256), 256, 0, m, dinv, b, xin,
+                         agg, xc, out);
+            break;
+        case 16:
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<16, VT, XT, K>), grid_for(n * 16, 256), 256, 0, m, dinv, b,
+                         xin, agg, xc, out);
+            break;
+        default:
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<32, VT, XT, K>), grid_for(n * 32, 256), 256, 0, m, dinv, b,
+                         xin, agg, xc, out);
+            break;
     }
 }
 
-template <class XT>
-static void level_post(Ctx &c, const Level &L, const XT *vals, const XT *b, const int32_t *agg, const XT *xc, XT *x,
-                       int64_t nc) {
-    int64_t n = L.A.nrow;
-    switch (pick_g<XT>(L)) {
-        case 2: VcKernels<XT>::template post<2>(c, n, L, vals, b, agg, xc, x, nc); break;
-        case 4: VcKernels<XT>::template post<4>(c, n, L, vals, b, agg, xc, x, nc); break;
-        case 8: VcKernels<XT>::template post<8>(c, n, L, vals, b, agg, xc, x, nc); break;
-        default: VcKernels<XT>::template post<32>(c, n, L, vals, b, agg, xc, x, nc); break;
+template <class XT, int K>
+static void level_op(Ctx &c, const Level &L, const XT *b, const XT *xin, const int32_t *agg, const XT *xc, XT *out,
+                     int64_t nc) {
+    const XT *dinv = L.dinv.as<XT>();
+    if constexpr (std::is_same<XT, double>::value) {
+        launch_level<double, XT, K>(c, L, dinv, b, xin, agg, xc, out, nc);
+    } else {
+        switch (L.vt) {
+            case VT_BF16: launch_level<__nv_bfloat16, XT, K>(c, L, dinv, b, xin, agg, xc, out, nc); break;
+            case VT_F16: launch_level<__half, XT, K>(c, L, dinv, b, xin, agg, xc, out, nc); break;
+            default: launch_level<float, XT, K>(c, L, dinv, b, xin, agg, xc, out, nc); break;
+        }
     }
 }
 
 static void gemv(Ctx &c, const double *M, int64_t n, const double *x, double *y) { dense_gemv_f64(c, M, n, x, y); }
 static void gemv(Ctx &c, const double *M, int64_t n, const float *x, float *y) { dense_gemv_f32(c, M, n, x, y); }
+
+static unsigned ew_grid(int64_t n) {
+    unsigned g = grid_for(n, 256);
+    return g > 4096 ? 4096 : g;
+}
+
+// x = S(x0; b): `sweeps` smoother applications starting from x0 (NULL = 0).
+// x0 and x must differ; uses L.r (residual), L.t (ping-pong) and L.d
+// (Chebyshev direction) as scratch.
+template <class XT>
+static void smooth_stored(Ctx &c, const Hierarchy &h, const Level &L, const XT *b, const XT *x0, XT *x) {
+    int64_t n = L.A.nrow;
+    XT *r = L.r.as<XT>();
+    const XT *dinv = L.dinv.as<XT>();
+    const double lo = 0.3, hi = 1.0;
+    const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta, rho = 1.0 / sigma;
+    const double rho1 = 1.0 / (2.0 * sigma - rho);
+    const XT *cur = x0;
+    for (int s = 0; s < h.sweeps; s++) {
+        // this sweep writes `dst`; the last sweep writes x
+        XT *dst = x;
+        if (cur == x) {
+            MDS_CUDA(cudaMemcpyAsync(L.t.p, x, sizeof(XT) * (size_t)n, cudaMemcpyDeviceToDevice, c.stream));
+            cur = L.t.as<XT>();
+        }
+        if (h.smoother == MDS_SMOOTHER_L1JACOBI) {
+            if (!cur)
+                MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n, k_vc_x0<XT>, ew_grid(n), 256, 0, n, dinv, b, dst);
+            else
+                level_op<XT, VK_SMOOTH>(c, L, b, cur, nullptr, nullptr, dst, 0);
+        } else {
+            XT *d = L.d.as<XT>();
+            if (cur) {
+                level_op<XT, VK_RESID>(c, L, b, cur, nullptr, nullptr, r, 0);
+                MDS_LAUNCH(c, KC_NONE, 0, k_cheb_first<XT>, ew_grid(n), 256, 0, n, dinv, r, cur, (XT)(1.0 / theta), d,
+                           dst);
+            } else {
+                MDS_LAUNCH(c, KC_NONE, 0, k_cheb_first<XT>, ew_grid(n), 256, 0, n, dinv, b, (const XT *)nullptr,
+                           (XT)(1.0 / theta), d, dst);
+            }
+            level_op<XT, VK_RESID>(c, L, b, dst, nullptr, nullptr, r, 0);
+            MDS_LAUNCH(c, KC_NONE, 0, k_cheb_next<XT>, ew_grid(n), 256, 0, n, dinv, r, (XT)(rho1 * rho),
+                       (XT)(2.0 * rho1 / delta), d, dst);
+        }
+        cur = dst;
+    }
+}
 
 template <class XT>
 static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
@@ -137,19 +335,35 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
         gemv(c, h.Ainv.as<double>(), h.nd, b, x);
         return;
     }
-    const XT *vals = h.prec == 64 ? (const XT *)L.A.vals() : (const XT *)L.vals_lp.p;
+    int64_t n = L.A.nrow;
+    XT *r = L.r.as<XT>();
+    double rbytes = 4.0 * (L.nc + 1) + 4.0 * n + sizeof(XT) * (double)(n + L.nc);
+    bool fused = !std::is_same<XT, double>::value && h.smoother == MDS_SMOOTHER_L1JACOBI && h.sweeps == 1;
+    if (fused) {
+        if (L.has_coarse) {
+            Level &C = h.lv[l + 1];
+            level_op<XT, VK_RESID0>(c, L, b, nullptr, nullptr, nullptr, r, 0);
+            MDS_LAUNCH(c, KC_VC_RESTRICT, rbytes, k_vc_restrict<XT>, grid_for(L.nc, 256), 256, 0, L.nc,
+                       L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r, C.b.as<XT>());
+            vcycle_level<XT>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
+            level_op<XT, VK_POST>(c, L, b, nullptr, L.agg.as<int32_t>(), C.x.as<XT>(), x, L.nc);
+        } else {
+            level_op<XT, VK_POST>(c, L, b, nullptr, nullptr, nullptr, x, 0);
+        }
+        return;
+    }
+    XT *y = L.y.as<XT>();
+    smooth_stored<XT>(c, h, L, b, nullptr, y);  // y = S(0; b)
     if (L.has_coarse) {
         Level &C = h.lv[l + 1];
-        XT *r = L.r.as<XT>();
-        level_resid<XT>(c, L, vals, b, r);
-        double rbytes = 4.0 * (L.nc + 1) + 4.0 * L.A.nrow + sizeof(XT) * (double)(L.A.nrow + L.nc);
+        level_op<XT, VK_RESID>(c, L, b, y, nullptr, nullptr, r, 0);
         MDS_LAUNCH(c, KC_VC_RESTRICT, rbytes, k_vc_restrict<XT>, grid_for(L.nc, 256), 256, 0, L.nc,
                    L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r, C.b.as<XT>());
         vcycle_level<XT>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
-        level_post<XT>(c, L, vals, b, L.agg.as<int32_t>(), C.x.as<XT>(), x, L.nc);
-    } else {
-        level_post<XT>(c, L, vals, b, (const int32_t *)nullptr, (const XT *)nullptr, x, 0);
+        MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n, k_vc_prolong<XT>, ew_grid(n), 256, 0, n, L.agg.as<int32_t>(),
+                   C.x.as<XT>(), y);
     }
+    smooth_stored<XT>(c, h, L, b, y, x);  // x = S(y; b)
 }
 
 void vcycle_apply(Ctx &c, Hierarchy &h, const void *b, void *x) {
@@ -158,6 +372,260 @@ void vcycle_apply(Ctx &c, Hierarchy &h, const void *b, void *x) {
         vcycle_level<double>(c, h, 0, (const double *)b, (double *)x);
     else
         vcycle_level<float>(c, h, 0, (const float *)b, (float *)x);
+}
+
+// ---------------------------------------------------------------- level storage
+
+// s_i = 2^ceil(log2 max_j |a_ij|) (1 for a zero row)
+__global__ void k_row_scale(int64_t n, const int32_t *__restrict__ rp, const double *__restrict__ v,
+                            float *__restrict__ s) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double mx = 0.0;
+    for (int32_t p = rp[i]; p < rp[i + 1]; p++) mx = fmax(mx, fabs(v[p]));
+    if (mx == 0.0) {
+        s[i] = 1.0f;
+        return;
+    }
+    int e = 0;
+    double fr = frexp(mx, &e);
+    if (fr == 0.5) e -= 1;
+    s[i] = (float)ldexp(1.0, e);
+}
+
+template <class VT> __device__ __forceinline__ VT from_d(double a, double sc);
+template <> __device__ __forceinline__ double from_d<double>(double a, double) { return a; }
+template <> __device__ __forceinline__ float from_d<float>(double a, double) { return (float)a; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(double a, double sc) {
+    return __float2bfloat16_rn((float)(a / sc));
+}
+template <> __device__ __forceinline__ __half from_d<__half>(double a, double sc) {
+    return __float2half_rn((float)(a / sc));
+}
+
+// CSR values in the storage type
+template <class VT>
+__global__ void k_csr_lowp(int64_t n, const int32_t *__restrict__ rp, const double *__restrict__ v,
+                           const float *__restrict__ s, VT *__restrict__ o) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double sc = s ? (double)s[i] : 1.0;
+    for (int32_t p = rp[i]; p < rp[i + 1]; p++) o[p] = from_d<VT>(v[p], sc);
+}
+
+// SELL: window sort of rows by decreasing length (stable), one thread per window
+__global__ void k_sell_perm(int64_t n, const int32_t *__restrict__ rp, int sigma, int32_t *__restrict__ perm) {
+    int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t a = w * sigma;
+    if (a >= n) return;
+    int64_t e = a + sigma < n ? a + sigma : n;
+    for (int64_t i = a; i < e; i++) perm[i] = (int32_t)i;
+    for (int64_t i = a + 1; i < e; i++) {
+        int32_t x = perm[i];
+        int32_t lx = rp[x + 1] - rp[x];
+        int64_t q = i - 1;
+        while (q >= a && (rp[perm[q] + 1] - rp[perm[q]]) < lx) {
+            perm[q + 1] = perm[q];
+            q--;
+        }
+        perm[q + 1] = x;
+    }
+}
+
+__global__ void k_sell_len(int64_t n, int64_t nslice, int C, const int32_t *__restrict__ rp,
+                           const int32_t *__restrict__ perm, int32_t *__restrict__ len, int32_t *__restrict__ cnt) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nslice) return;
+    int32_t mx = 0;
+    for (int r = 0; r < C; r++) {
+        int64_t row = s * C + r;
+        if (row >= n) break;
+        int64_t o = perm ? perm[row] : row;
+        int32_t l = rp[o + 1] - rp[o];
+        mx = l > mx ? l : mx;
+    }
+    len[s] = mx;
+    cnt[s] = mx * C;
+}
+
+template <class VT>
+__global__ void k_sell_fill(int64_t n, int64_t nslice, int C, const int32_t *__restrict__ rp,
+                            const int32_t *__restrict__ ci, const double *__restrict__ v, const float *__restrict__ s,
+                            const int32_t *__restrict__ perm, const int32_t *__restrict__ sp,
+                            const int32_t *__restrict__ sl, int32_t *__restrict__ sc, VT *__restrict__ sv) {
+    int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= nslice * C) return;
+    int64_t sli = row / C;
+    int r = (int)(row - sli * C);
+    int64_t o = row < n ? (perm ? perm[row] : row) : -1;
+    int32_t a = o >= 0 ? rp[o] : 0, l = o >= 0 ? rp[o + 1] - rp[o] : 0;
+    double scale = (o >= 0 && s) ? (double)s[o] : 1.0;
+    for (int32_t k = 0; k < sl[sli]; k++) {
+        int32_t p = sp[sli] + k * C + r;
+        if (k < l) {
+            sc[p] = ci[a + k];
+            sv[p] = from_d<VT>(v[a + k], scale);
+        } else {
+            sc[p] = o >= 0 ? (int32_t)o : 0;  // padding: a valid column with a zero value
+            sv[p] = from_d<VT>(0.0, 1.0);
+        }
+    }
+}
+
+template <class VT> static void build_sell(Ctx &c, Level &L, int C, int sigma) {
+    int64_t n = L.A.nrow;
+    L.sell_c = C;
+    L.sell_nslice = (n + C - 1) / C;
+    int64_t ns = L.sell_nslice;
+    L.sell_perm.reset();
+    if (sigma > 1) {
+        L.sell_perm = Buf(&c, sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+        int64_t nw = (n + sigma - 1) / sigma;
+        MDS_LAUNCH(c, KC_NONE, 0, k_sell_perm, grid_for(nw, 64), 64, 0, n, L.A.rowp(), sigma, L.sell_perm.as<int32_t>());
+    }
+    L.sell_len = Buf(&c, sizeof(int32_t) * (size_t)(ns + 1));
+    L.sell_ptr = Buf(&c, sizeof(int32_t) * (size_t)(ns + 1));
+    Buf cnt(&c, sizeof(int32_t) * (size_t)(ns + 1));
+    const int32_t *perm = L.sell_perm.p ? L.sell_perm.as<int32_t>() : nullptr;
+    MDS_LAUNCH(c, KC_NONE, 0, k_sell_len, grid_for(ns, 256), 256, 0, n, ns, C, L.A.rowp(), perm,
+               L.sell_len.as<int32_t>(), cnt.as<int32_t>());
+    L.sell_nnz = scan_counts(c, cnt.as<int32_t>(), L.sell_ptr.as<int32_t>(), ns);
+    L.sell_col = Buf(&c, sizeof(int32_t) * (size_t)(L.sell_nnz > 0 ? L.sell_nnz : 1));
+    L.sell_val = Buf(&c, sizeof(VT) * (size_t)(L.sell_nnz > 0 ? L.sell_nnz : 1));
+    MDS_LAUNCH(c, KC_NONE, 0, k_sell_fill<VT>, grid_for(ns * C, 256), 256, 0, n, ns, C, L.A.rowp(), L.A.cols(),
+               L.A.vals(), L.rscale.p ? L.rscale.as<float>() : nullptr, perm, L.sell_ptr.as<int32_t>(),
+               L.sell_len.as<int32_t>(), L.sell_col.as<int32_t>(), L.sell_val.as<VT>());
+    L.fmt = FMT_SELL;
+}
+
+static void build_sell_vt(Ctx &c, Level &L, int C, int sigma) {
+    switch (L.vt) {
+        case VT_F64: build_sell<double>(c, L, C, sigma); break;
+        case VT_F32: build_sell<float>(c, L, C, sigma); break;
+        case VT_BF16: build_sell<__nv_bfloat16>(c, L, C, sigma); break;
+        case VT_F16: build_sell<__half>(c, L, C, sigma); break;
+    }
+}
+
+static void drop_sell(Level &L) {
+    L.sell_perm.reset();
+    L.sell_len.reset();
+    L.sell_ptr.reset();
+    L.sell_col.reset();
+    L.sell_val.reset();
+    L.sell_nnz = 0;
+    L.fmt = FMT_CSR;
+}
+
+static int default_g(const Level &L) {
+    double avg = L.A.nrow ? (double)L.A.nnz / (double)L.A.nrow : 0.0;
+    return avg <= 4.0 ? 2 : avg <= 10.0 ? 4 : avg <= 20.0 ? 8 : avg <= 40.0 ? 16 : 32;
+}
+
+// Time the stored-residual kernel on the level in its current storage (best
+// of three after a warm-up launch).
+template <class XT> static float time_level(Ctx &c, const Level &L) {
+    cudaEvent_t e0, e1;
+    MDS_CUDA(cudaEventCreate(&e0));
+    MDS_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; rep++) {
+        MDS_CUDA(cudaEventRecord(e0, c.stream));
+        level_op<XT, VK_RESID>(c, L, L.b.as<XT>(), L.x.as<XT>(), nullptr, nullptr, L.r.as<XT>(), 0);
+        MDS_CUDA(cudaEventRecord(e1, c.stream));
+        MDS_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        MDS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+// Autotuner: time CSR with G/2, G, 2G lanes per row and SELL-C-sigma for a
+// few (C, sigma) pairs on this level, keep the fastest.  Choices are cached in
+// the context by (rows, nonzeros, storage type).
+template <class XT> static void autotune_level(Ctx &c, Level &L) {
+    auto key = std::make_tuple(L.A.nrow, L.A.nnz, L.vt);
+    auto it = c.tune_cache.find(key);
+    if (it != c.tune_cache.end()) {
+        const TuneChoice &t = it->second;
+        if (t.fmt == FMT_SELL)
+            build_sell_vt(c, L, t.C, t.sigma);
+        else
+            L.G = t.G;
+        return;
+    }
+    // defined inputs for the timing runs
+    size_t vb = sizeof(XT) * (size_t)L.A.nrow;
+    MDS_CUDA(cudaMemsetAsync(L.b.p, 0, vb, c.stream));
+    MDS_CUDA(cudaMemsetAsync(L.x.p, 0, vb, c.stream));
+    TuneChoice best{FMT_CSR, default_g(L), 32, 1};
+    float tbest = 1e30f;
+    int g0 = default_g(L);
+    for (int G : {g0 / 2, g0, g0 * 2}) {
+        if (G < 2 || G > 32) continue;
+        L.fmt = FMT_CSR;
+        L.G = G;
+        float t = time_level<XT>(c, L);
+        if (t < tbest) {
+            tbest = t;
+            best = TuneChoice{FMT_CSR, G, 32, 1};
+        }
+    }
+    const int cand[][2] = {{32, 1}, {32, 256}, {16, 1}};
+    for (auto &cs : cand) {
+        build_sell_vt(c, L, cs[0], cs[1]);
+        float t = time_level<XT>(c, L);
+        if (t < tbest) {
+            tbest = t;
+            best = TuneChoice{FMT_SELL, 0, cs[0], cs[1]};
+        }
+        drop_sell(L);
+    }
+    c.tune_cache[key] = best;
+    L.G = best.fmt == FMT_CSR ? best.G : default_g(L);
+    if (best.fmt == FMT_SELL) build_sell_vt(c, L, best.C, best.sigma);
+}
+
+void level_storage(Ctx &c, Hierarchy &h, const mds_setup_opts &o) {
+    for (size_t l = 0; l < h.lv.size(); l++) {
+        Level &L = h.lv[l];
+        int64_t n = L.A.nrow;
+        bool lowp = (o.precision == MDS_PREC_BF16 || o.precision == MDS_PREC_FP16) && (int)l >= o.lowp_from_level;
+        L.vt = h.prec == 64 ? VT_F64 : !lowp ? VT_F32 : (o.precision == MDS_PREC_BF16 ? VT_BF16 : VT_F16);
+        L.G = default_g(L);
+        L.fmt = FMT_CSR;
+        if (l + 1 == h.lv.size() && h.dense) continue;  // applied through the dense inverse
+        unsigned gr = grid_for(n, 256);
+        if (L.vt == VT_BF16 || L.vt == VT_F16) {
+            L.rscale = Buf(&c, sizeof(float) * (size_t)(n > 0 ? n : 1));
+            MDS_LAUNCH(c, KC_NONE, 0, k_row_scale, gr, 256, 0, n, L.A.rowp(), L.A.vals(), L.rscale.as<float>());
+        }
+        const float *s = L.rscale.p ? L.rscale.as<float>() : nullptr;
+        size_t nz = (size_t)(L.A.nnz > 0 ? L.A.nnz : 1);
+        if (L.vt == VT_F32) {
+            L.vals_lp = Buf(&c, 4 * nz);
+            MDS_LAUNCH(c, KC_NONE, 0, k_csr_lowp<float>, gr, 256, 0, n, L.A.rowp(), L.A.vals(), s, L.vals_lp.as<float>());
+        } else if (L.vt == VT_BF16) {
+            L.vals_lp = Buf(&c, 2 * nz);
+            MDS_LAUNCH(c, KC_NONE, 0, k_csr_lowp<__nv_bfloat16>, gr, 256, 0, n, L.A.rowp(), L.A.vals(), s,
+                       L.vals_lp.as<__nv_bfloat16>());
+        } else if (L.vt == VT_F16) {
+            L.vals_lp = Buf(&c, 2 * nz);
+            MDS_LAUNCH(c, KC_NONE, 0, k_csr_lowp<__half>, gr, 256, 0, n, L.A.rowp(), L.A.vals(), s,
+                       L.vals_lp.as<__half>());
+        }
+        if (o.format == MDS_FORMAT_SELL) {
+            build_sell_vt(c, L, o.sell_c, o.sell_sigma);
+        } else if (o.format == MDS_FORMAT_AUTO && n >= 20000) {
+            if (h.prec == 64)
+                autotune_level<double>(c, L);
+            else
+                autotune_level<float>(c, L);
+        }
+    }
 }
 
 }  // namespace mds

@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(PKG, "_build", "libmdsolve.so")
 
 MDS_OK = 0
 MDS_WARN_NOT_CONVERGED = 1
-PREC = {"fp64": 64, "fp32": 32, "mixed16": 16}
+PREC = {"fp64": 64, "fp32": 32, "bf16": 16, "fp16": 17}
+FORMAT = {"auto": 0, "csr": 1, "sell": 2}
 SMOOTHER = {"l1jacobi": 0, "chebyshev": 1}
 KIND = {"lower": 0, "diag": 1, "upper": 2}
 KRYLOV = {"fgmres": 0, "pcg": 1}
@@ -45,7 +46,8 @@ class Csr(C.Structure):
 class SetupOpts(C.Structure):
     _fields_ = [("theta", C.c_double), ("n_coarse", C.c_int64), ("max_levels", C.c_int),
                 ("stall_ratio", C.c_double), ("seed", C.c_uint64), ("smoother", C.c_int),
-                ("precision", C.c_int), ("lowp_from_level", C.c_int), ("kind", C.c_int)]
+                ("precision", C.c_int), ("lowp_from_level", C.c_int), ("kind", C.c_int), ("format", C.c_int),
+                ("sell_c", C.c_int), ("sell_sigma", C.c_int), ("sweeps", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -89,7 +91,7 @@ _SIGS = {
     "mds_timing_enable": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "mds_timing_reset": (C.c_int, [C.c_void_p]),
     "mds_timing_query": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
-                                   C.POINTER(C.c_double)]),
+                                   C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mds_memcpy": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t]),
     "mds_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
 }
@@ -129,6 +131,8 @@ def setup_opts(**kw) -> SetupOpts:
             v = SMOOTHER.get(v, v)
         elif k == "kind":
             v = KIND.get(v, v)
+        elif k == "format":
+            v = FORMAT.get(v, v)
         setattr(o, k, v)
     return o
 
@@ -272,9 +276,9 @@ class Context:
 
     def timing_query(self, kclass):
         k = KCLASS.get(kclass, kclass)
-        n, ms, by = C.c_int64(), C.c_double(), C.c_double()
-        self._check(lib().mds_timing_query(self.h, k, C.byref(n), C.byref(ms), C.byref(by)))
-        return n.value, ms.value, by.value
+        n, ms, by, fl = C.c_int64(), C.c_double(), C.c_double(), C.c_double()
+        self._check(lib().mds_timing_query(self.h, k, C.byref(n), C.byref(ms), C.byref(by), C.byref(fl)))
+        return n.value, ms.value, by.value, fl.value
 
     def launch_count(self) -> int:
         n = C.c_int64()

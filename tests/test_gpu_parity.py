@@ -362,3 +362,84 @@ def test_full_size_random_segments(ctx, oracle_mod, torch_mod):
     ctx.precond_apply(prec, dev(torch, r), z)
     zo = M.apply(r)
     assert np.linalg.norm(z.cpu().numpy() - zo) <= 1e-12 * np.linalg.norm(zo)
+
+
+# ---------------------------------------------------------------- storage and smoother options
+
+PREC_CODE = {"fp64": 64, "fp32": 32, "bf16": 16, "fp16": 17}
+OPTION_CASES = [
+    dict(precision="fp64", smoother="chebyshev"),
+    dict(precision="fp32", smoother="chebyshev"),
+    dict(precision="fp64", sweeps=2),
+    dict(precision="fp32", sweeps=2),
+    dict(precision="bf16"),
+    dict(precision="fp16"),
+    dict(precision="fp16", lowp_from_level=0),
+    dict(precision="fp32", format="sell"),
+    dict(precision="fp32", format="sell", sell_c=16, sell_sigma=64),
+    dict(precision="fp64", format="sell", sell_c=8, sell_sigma=32),
+    dict(precision="bf16", format="sell", sell_sigma=256),
+    dict(precision="fp32", format="auto"),
+    dict(precision="fp64", format="auto", smoother="chebyshev"),
+]
+
+
+def oracle_kw(cfg):
+    return dict(prec=PREC_CODE[cfg.get("precision", "fp64")], smoother=1 if cfg.get("smoother") == "chebyshev" else 0,
+                sweeps=cfg.get("sweeps", 1), lowp_from_level=cfg.get("lowp_from_level", 1))
+
+
+def tol_of(cfg):
+    return {"fp64": 1e-12, "fp32": 2e-5}.get(cfg.get("precision"), 5e-5)
+
+
+@pytest.mark.parametrize("cfg", OPTION_CASES, ids=lambda c: "-".join(f"{k}={v}" for k, v in c.items()))
+@pytest.mark.parametrize("case", ["seg2d-256", "rects3d-18"])
+def test_vcycle_options_parity(ctx, oracle_mod, torch_mod, case, cfg):
+    torch = torch_mod
+    inst = inputs.random_segments_2d(n=256, n_seg=20) if case == "seg2d-256" else CASES[case]()
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_, **cfg)
+    Ao, _ = oracle_mod.assemble(inst)
+    M = oracle_mod.ML(Ao, inst.n_m, **oracle_kw(cfg))
+    rng = np.random.default_rng(11)
+    for block, n in ((0, inst.n_m), (1, inst.n_f)):
+        b = rng.standard_normal(n)
+        for rep in range(2):  # repeated application uses the same stored state
+            x = torch.zeros(n, dtype=torch.float64, device="cuda")
+            ctx.vcycle(prec, block, dev(torch, b), x)
+            xo = M.amg(block).vcycle(b)
+            err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+            assert err < tol_of(cfg), (block, rep, err)
+
+
+@pytest.mark.parametrize("cfg", [dict(precision="bf16"), dict(precision="fp16"), dict(smoother="chebyshev"),
+                                 dict(precision="fp32", smoother="chebyshev", format="sell"),
+                                 dict(precision="fp32", sweeps=2, format="auto")],
+                         ids=lambda c: "-".join(f"{k}={v}" for k, v in c.items()))
+@pytest.mark.parametrize("case", ["seg2d-96", "planes3d-16", "rects3d-18"])
+def test_solve_options_parity(ctx, oracle_mod, torch_mod, case, cfg):
+    torch = torch_mod
+    inst = CASES[case]()
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_, **cfg)
+    x = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+    code, st = ctx.solve(sys_, prec, None, x, max_iters=3000)
+    res, Ao, bo, _ = oracle_mod.solve(inst, maxit=3000, **oracle_kw(cfg))
+    assert code == 0 and res.converged
+    assert abs(st[0].iterations - res.iterations) <= 1, (st[0].iterations, res.iterations)
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(bo[0] - Ao @ xg) / np.linalg.norm(bo[0]) <= 1.01e-8
+
+
+def test_autotuner_cache_reuses_choice(ctx, torch_mod):
+    inst = inputs.random_segments_2d(n=256, n_seg=20)
+    s1 = ctx.assemble(inst)
+    p1 = ctx.setup(s1, precision="fp32", format="auto")
+    p2 = ctx.setup(s1, precision="fp32", format="auto")
+    r = np.random.default_rng(0).standard_normal(s1.N)
+    z1 = torch_mod.zeros(s1.N, dtype=torch_mod.float64, device="cuda")
+    z2 = torch_mod.zeros_like(z1)
+    ctx.precond_apply(p1, dev(torch_mod, r), z1)
+    ctx.precond_apply(p2, dev(torch_mod, r), z2)
+    assert torch_mod.equal(z1, z2)

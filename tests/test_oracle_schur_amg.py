@@ -261,3 +261,46 @@ def test_l1_diagonal(oracle_mod):
     A = lap2(6, eps=0.5)
     amg = oracle_mod.AMG(A, n_coarse=1)
     assert np.array_equal(amg.l1(0), np.asarray(abs(A).sum(axis=1)).ravel())
+
+
+def test_lowp_rounding(oracle_mod):
+    """bf16 keeps 8 significant bits, fp16 11, both round to nearest even."""
+    r = oracle_mod.round_lowp
+    # bf16: 1 + 2^-8 is halfway between 1 and 1 + 2^-7 -> even (1); 1 + 3 2^-8 -> 1 + 2^-6
+    assert r(1 + 2 ** -8, 16) == 1.0
+    assert r(1 + 3 * 2 ** -8, 16) == 1 + 2 ** -6
+    assert r(1 + 2 ** -8 + 2 ** -20, 16) == 1 + 2 ** -7
+    assert r(-3.0, 16) == -3.0 and r(2.0 ** -130, 16) == 2.0 ** -130
+    # fp16 against numpy's IEEE binary16 conversion of the float
+    rng = np.random.default_rng(0)
+    xs = np.concatenate([rng.standard_normal(2000) * 10.0 ** rng.uniform(-9, 5, 2000), [65519.0, 65520.0, 6e-8,
+                                                                                       2 ** -25, 3 * 2 ** -26]])
+    for x in xs:
+        ref = float(np.float16(np.float32(x)))
+        assert r(x, 17) == ref or (np.isinf(ref) and np.isinf(r(x, 17))), x
+    assert r(1.0 / 3.0, 32) == float(np.float32(1.0 / 3.0))
+
+
+@pytest.mark.parametrize("smoother", [0, 1])
+def test_vcycle_two_sweeps(oracle_mod, smoother):
+    """Two sweeps: E = S^2 (I - P A_c^-1 P^T A) S^2 for the two-level cycle."""
+    A = sp.csr_matrix(lap2(8, eps=0.7) + sp.diags(np.linspace(0, 0.3, 64)))
+    amg = oracle_mod.AMG(A, n_coarse=20, smoother=smoother, sweeps=2)
+    n = 64
+    Ad = A.toarray()
+    V = dense_operator(amg.vcycle, n)
+    E = np.eye(n) - V @ Ad
+    agg = amg.agg(0)
+    P = np.zeros((n, agg.max() + 1))
+    P[np.nonzero(agg >= 0)[0], agg[agg >= 0]] = 1.0
+    CG = np.eye(n) - P @ np.linalg.solve(P.T @ Ad @ P, P.T @ Ad)
+    Minv = np.diag(1.0 / amg.l1(0))
+    if smoother == 0:
+        Sm = np.eye(n) - Minv @ Ad
+    else:
+        lo, hi = 0.3, 1.0
+        Y = ((hi + lo) * np.eye(n) - 2 * Minv @ Ad) / (hi - lo)
+        s = (hi + lo) / (hi - lo)
+        Sm = (2 * Y @ Y - np.eye(n)) / (2 * s * s - 1)
+    S2 = Sm @ Sm
+    assert np.max(np.abs(E - S2 @ CG @ S2)) < 1e-12
