@@ -213,6 +213,8 @@ typedef struct {
     double rtol;         /* stop when ||b - A x|| <= rtol ||b|| (1e-8) */
     int max_iters;       /* preconditioner applications per right-hand side (1000) */
     int use_precond;     /* 1 = the set-up preconditioner, 0 = identity */
+    int graphs;          /* 1 = capture each Krylov step as a CUDA graph on its first use and
+                            replay it (1); 0 = launch every kernel directly */
 } mds_solve_opts;
 
 typedef struct {

@@ -73,6 +73,17 @@ void Ctx::check_err(const char *where) {
 
 KTimer::KTimer(Ctx &ctx, int k, double b, double f) : c(ctx), cls(k) {
     if (k < 0 || k >= MDS_KCLASS_COUNT) return;
+    if (c.capturing) {
+        GraphRec r{k, b, f, c.timing[k], nullptr, nullptr};
+        if (r.timed) {
+            MDS_CUDA(cudaEventCreate(&r.e0));
+            MDS_CUDA(cudaEventCreate(&r.e1));
+            cudaEventRecord(r.e0, c.stream);
+        }
+        c.capturing->recs.push_back(r);
+        grec = (int)c.capturing->recs.size() - 1;
+        return;
+    }
     c.launches[k]++;
     c.bytes[k] += b;
     c.flops[k] += f;
@@ -90,6 +101,34 @@ KTimer::KTimer(Ctx &ctx, int k, double b, double f) : c(ctx), cls(k) {
 
 KTimer::~KTimer() {
     if (rec) cudaEventRecord(rec->e1, c.stream);
+    if (grec >= 0 && c.capturing && c.capturing->recs[grec].timed) cudaEventRecord(c.capturing->recs[grec].e1, c.stream);
+}
+
+Graph::~Graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (auto &r : recs)
+        if (r.timed) {
+            cudaEventDestroy(r.e0);
+            cudaEventDestroy(r.e1);
+        }
+}
+
+void graph_launch(Ctx &c, Graph &g) {
+    MDS_CUDA(cudaGraphLaunch(g.exec, c.stream));
+    for (auto &r : g.recs) {
+        c.launches[r.cls]++;
+        c.bytes[r.cls] += r.bytes;
+        c.flops[r.cls] += r.flops;
+    }
+    c.total_launches += g.launches;
+}
+
+void graph_collect(Ctx &c, Graph &g) {
+    for (auto &r : g.recs)
+        if (r.timed && c.timing[r.cls]) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, r.e0, r.e1) == cudaSuccess) c.graph_ms[r.cls] += t;
+        }
 }
 
 }  // namespace mds
@@ -175,6 +214,7 @@ int mds_destroy(mds_ctx ctx) {
         }
     cudaFree(c.d_err);
     cudaFreeHost(c.h_pin);
+    if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
     delete ctx;
     return MDS_OK;
 }
@@ -481,6 +521,7 @@ int mds_solve_opts_default(mds_solve_opts *o) {
     o->rtol = 1e-8;
     o->max_iters = 1000;
     o->use_precond = 1;
+    o->graphs = 1;
     return MDS_OK;
 }
 
@@ -562,6 +603,7 @@ int mds_timing_reset(mds_ctx ctx) {
         c.launches[k] = 0;
         c.bytes[k] = 0.0;
         c.flops[k] = 0.0;
+        c.graph_ms[k] = 0.0;
     }
     c.total_launches = 0;
     return MDS_OK;
@@ -579,7 +621,7 @@ int mds_timing_query(mds_ctx ctx, int k, int64_t *launches, double *ms, double *
         tot += t;
     }
     if (launches) *launches = c->launches[k];
-    if (ms) *ms = tot;
+    if (ms) *ms = tot + c->graph_ms[k];
     if (bytes) *bytes = c->bytes[k];
     if (flops) *flops = c->flops[k];
     API_END(c)

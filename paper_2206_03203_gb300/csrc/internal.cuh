@@ -86,6 +86,26 @@ struct KTimerRec {
     cudaEvent_t e0, e1;
 };
 
+// One launch recorded while a CUDA graph is being captured: its accounting is
+// replayed, and its events (when its class is timed) read, at every replay.
+struct GraphRec {
+    int cls;
+    double bytes, flops;
+    bool timed;
+    cudaEvent_t e0, e1;
+};
+
+// A captured sequence of launches and its executable graph.
+struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<GraphRec> recs;
+    int64_t launches = 0;
+    Graph() = default;
+    Graph(const Graph &) = delete;
+    Graph &operator=(const Graph &) = delete;
+    ~Graph();
+};
+
 struct Ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -101,6 +121,9 @@ struct Ctx {
     double bytes[MDS_KCLASS_COUNT] = {};
     double flops[MDS_KCLASS_COUNT] = {};
     int64_t total_launches = 0;
+    double graph_ms[MDS_KCLASS_COUNT] = {};
+    Graph *capturing = nullptr;   // recording target while a stream capture is open
+    cudaStream_t cap_stream = nullptr;
     // autotuner choices by (rows, nonzeros, value type)
     std::map<std::tuple<int64_t, int64_t, int>, TuneChoice> tune_cache;
 
@@ -108,7 +131,10 @@ struct Ctx {
     void raw_free(void *p);
     void sync() { MDS_CUDA(cudaStreamSynchronize(stream)); }
     void post_launch() {
-        total_launches++;
+        if (capturing)
+            capturing->launches++;
+        else
+            total_launches++;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) throw Error(MDS_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     }
@@ -125,11 +151,22 @@ struct Ctx {
     void check_err(const char *where);
 };
 
+// Capture the launches issued by f() into g (on an internal capture stream),
+// then instantiate it.  Returns false, with nothing recorded and no work
+// done, when the capture cannot be made.
+template <class F> bool graph_capture(Ctx &c, Graph &g, F f);
+// Launch a captured graph on the context stream and replay its accounting.
+void graph_launch(Ctx &c, Graph &g);
+// After the stream has been synchronised: add the timed launches of the last
+// replay to the per-class event time.
+void graph_collect(Ctx &c, Graph &g);
+
 // Scope that brackets one launch with events when its class is being timed.
 struct KTimer {
     Ctx &c;
     int cls;
     KTimerRec *rec = nullptr;
+    int grec = -1;
     KTimer(Ctx &ctx, int k, double bytes, double flops = 0.0);
     ~KTimer();
 };
@@ -148,6 +185,41 @@ struct KTimer {
         kern<<<(grid), (block), (smem), (ctx).stream>>>(__VA_ARGS__);               \
         (ctx).post_launch();                                                       \
     } while (0)
+
+template <class F> bool graph_capture(Ctx &c, Graph &g, F f) {
+    if (!c.cap_stream) MDS_CUDA(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = c.stream;
+    MDS_CUDA(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal));
+    c.stream = c.cap_stream;
+    c.capturing = &g;
+    cudaGraph_t graph = nullptr;
+    bool ok = true;
+    try {
+        f();
+    } catch (...) {
+        ok = false;
+    }
+    c.capturing = nullptr;
+    c.stream = user;
+    cudaError_t e = cudaStreamEndCapture(c.cap_stream, &graph);
+    if (e != cudaSuccess || !ok || !graph) {
+        cudaGetLastError();
+        if (graph) cudaGraphDestroy(graph);
+        g.recs.clear();
+        g.launches = 0;
+        return false;
+    }
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        g.exec = nullptr;
+        g.recs.clear();
+        g.launches = 0;
+        return false;
+    }
+    return true;
+}
 
 inline unsigned grid_for(int64_t n, int block) {
     int64_t g = (n + block - 1) / block;

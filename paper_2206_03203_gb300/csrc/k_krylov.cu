@@ -6,6 +6,7 @@
 // so results are run-to-run reproducible.
 #include <cmath>
 #include <functional>
+#include <memory>
 
 #include "internal.cuh"
 #include "krylov.cuh"
@@ -308,6 +309,57 @@ KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, 
         return res;
     }
     if (bn == 0.0) bn = 1.0;
+    // One Arnoldi step j: z_j = M v_j, w = A z_j, Gram-Schmidt, Givens, and
+    // the step's scalars copied to pinned host memory.  Captured as a CUDA
+    // graph on first use and replayed on later restart cycles.
+    auto body = [&](int j) {
+        double *vj = Vp + (size_t)j * ld, *zj = Zp + (size_t)j * ld, *w = Vp + (size_t)(j + 1) * ld;
+        M(vj, zj);
+        spmv_f64(c, A, zj, w, KC_SPMV);
+        // classical Gram-Schmidt: h = V^T w (and ||w||^2), w -= V h, ||w||^2;
+        // a second pass only when the DGKS test asks for it (device flag)
+        int nq = j + 1;
+        double fl = 2.0 * (double)n * nq;
+        MDS_LAUNCH_F(c, KC_GS_DOT, 8.0 * n * (nq + 1), fl + 2.0 * n, k_mdot, dim3(R.mgrid, nq + 1), RED_BLOCK, 0, n,
+                     Vp, ld, nq, w, R.partial.as<double>(), (const double *)nullptr);
+        MDS_LAUNCH(c, KC_NONE, 0, k_reduce_rows, nq + 1, 32, 0, R.partial.as<double>(), (int)R.mgrid, nq + 1, h, 0,
+                   (const double *)nullptr);
+        MDS_LAUNCH_F(c, KC_GS_AXPY, 8.0 * n * (nq + 2), fl + 2.0 * n, (k_maxpy<-1, true>), R.grid, RED_BLOCK, 0, n,
+                     Vp, ld, nq, h, w, R.partial.as<double>(), (const double *)nullptr);
+        MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.partial.as<double>(), (int)R.grid, 1, nsq, 0);
+        MDS_LAUNCH(c, KC_NONE, 0, k_dgks, 1, 1, 0, h + nq, nsq, dflag, h2, nq);
+        MDS_LAUNCH_F(c, KC_GS_DOT, 8.0 * n * (nq + 1), fl, k_mdot, dim3(R.mgrid, nq), RED_BLOCK, 0, n, Vp, ld, nq, w,
+                     R.partial.as<double>(), (const double *)dflag);
+        MDS_LAUNCH(c, KC_NONE, 0, k_reduce_rows, nq, 32, 0, R.partial.as<double>(), (int)R.mgrid, nq, h2, 0,
+                   (const double *)dflag);
+        MDS_LAUNCH_F(c, KC_GS_AXPY, 8.0 * n * (nq + 2), fl + 2.0 * n, (k_maxpy<-1, true>), R.grid, RED_BLOCK, 0, n,
+                     Vp, ld, nq, h2, w, R.partial.as<double>(), (const double *)dflag);
+        MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.partial.as<double>(), (int)R.grid, 1, nsq2, 0);
+        MDS_LAUNCH(c, KC_NONE, 0, k_arnoldi, 1, 1, 0, j, m, H.as<double>(), h, h2, nsq, nsq2, dflag, cs, sn, g, scal);
+        MDS_LAUNCH(c, KC_NONE, 16.0 * n, k_scale, red_grid(n), RED_BLOCK, 0, n, w, scal + 3, w);
+        MDS_CUDA(cudaMemcpyAsync(c.h_pin, scal, 5 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    };
+    std::vector<std::unique_ptr<Graph>> graphs(m);
+    bool graphs_ok = o.graphs != 0;
+    auto run_step = [&](int j) {
+        Graph *gj = nullptr;
+        if (graphs_ok) {
+            if (!graphs[j]) {
+                graphs[j].reset(new Graph);
+                if (!graph_capture(c, *graphs[j], [&] { body(j); })) {
+                    graphs[j].reset();
+                    graphs_ok = false;
+                }
+            }
+            gj = graphs[j].get();
+        }
+        if (gj)
+            graph_launch(c, *gj);
+        else
+            body(j);
+        c.sync();
+        if (gj) graph_collect(c, *gj);
+    };
     int it = 0, restarts = 0;
     double est = 0.0;
     for (;;) {
@@ -332,36 +384,10 @@ KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, 
         int kdone = 0;
         int flag = 0;
         for (int j = 0; j < m; j++) {
-            double *vj = Vp + (size_t)j * ld, *zj = Zp + (size_t)j * ld, *w = Vp + (size_t)(j + 1) * ld;
-            M(vj, zj);
-            it++;
-            spmv_f64(c, A, zj, w, KC_SPMV);
-            // classical Gram-Schmidt: h = V^T w (and ||w||^2), w -= V h, ||w||^2;
-            // a second pass only when the DGKS test asks for it (device flag)
-            int nq = j + 1;
-            double fl = 2.0 * (double)n * nq;
-            MDS_LAUNCH_F(c, KC_GS_DOT, 8.0 * n * (nq + 1), fl + 2.0 * n, k_mdot, dim3(R.mgrid, nq + 1), RED_BLOCK, 0,
-                         n, Vp, ld, nq, w, R.partial.as<double>(), (const double *)nullptr);
-            MDS_LAUNCH(c, KC_NONE, 0, k_reduce_rows, nq + 1, 32, 0, R.partial.as<double>(), (int)R.mgrid, nq + 1, h,
-                       0, (const double *)nullptr);
-            MDS_LAUNCH_F(c, KC_GS_AXPY, 8.0 * n * (nq + 2), fl + 2.0 * n, (k_maxpy<-1, true>), R.grid, RED_BLOCK, 0,
-                         n, Vp, ld, nq, h, w, R.partial.as<double>(), (const double *)nullptr);
-            MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.partial.as<double>(), (int)R.grid, 1, nsq, 0);
-            MDS_LAUNCH(c, KC_NONE, 0, k_dgks, 1, 1, 0, h + nq, nsq, dflag, h2, nq);
-            MDS_LAUNCH_F(c, KC_GS_DOT, 8.0 * n * (nq + 1), fl, k_mdot, dim3(R.mgrid, nq), RED_BLOCK, 0, n, Vp, ld, nq,
-                         w, R.partial.as<double>(), (const double *)dflag);
-            MDS_LAUNCH(c, KC_NONE, 0, k_reduce_rows, nq, 32, 0, R.partial.as<double>(), (int)R.mgrid, nq, h2, 0,
-                       (const double *)dflag);
-            MDS_LAUNCH_F(c, KC_GS_AXPY, 8.0 * n * (nq + 2), fl + 2.0 * n, (k_maxpy<-1, true>), R.grid, RED_BLOCK, 0,
-                         n, Vp, ld, nq, h2, w, R.partial.as<double>(), (const double *)dflag);
-            MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.partial.as<double>(), (int)R.grid, 1, nsq2, 0);
-            MDS_LAUNCH(c, KC_NONE, 0, k_arnoldi, 1, 1, 0, j, m, H.as<double>(), h, h2, nsq, nsq2, dflag, cs, sn, g,
-                       scal);
-            MDS_LAUNCH(c, KC_NONE, 16.0 * n, k_scale, red_grid(n), RED_BLOCK, 0, n, w, scal + 3, w);
-            MDS_CUDA(cudaMemcpyAsync(c.h_pin, scal, 5 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-            c.sync();
+            run_step(j);
             double sv[5];
             std::memcpy(sv, c.h_pin, sizeof sv);
+            it++;
             est = sv[2] / bn;
             kdone = j + 1;
             if (sv[4] == 2.0 || !std::isfinite(est)) {
@@ -411,17 +437,43 @@ KrylovResult pcg(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, dou
     dot_dev(c, R, n, r, r, sc + 3);
     double rn = std::sqrt(c.read(sc + 3));
     int it = 0;
-    while (rn / bn > o.rtol && it < o.max_iters) {
+    // one PCG iteration; graph 0 is the first iteration (p = z), graph 1 the rest
+    auto body = [&](int first) {
         M(r, z);
-        it++;
         dot_dev(c, R, n, r, z, sc);  // rz_new
-        MDS_LAUNCH(c, KC_NONE, 24.0 * n, k_pcg_p, red_grid(n), RED_BLOCK, 0, n, z, p, sc, it == 1 ? 1 : 0);
+        MDS_LAUNCH(c, KC_NONE, 24.0 * n, k_pcg_p, red_grid(n), RED_BLOCK, 0, n, z, p, sc, first);
         MDS_LAUNCH(c, KC_NONE, 0, k_copy1, 1, 1, 0, sc, sc + 1);  // rz = rz_new
         spmv_f64(c, A, p, q, KC_SPMV);
         dot_dev(c, R, n, p, q, sc + 2);
         MDS_LAUNCH(c, KC_NONE, 56.0 * n, k_pcg_xr, R.grid, RED_BLOCK, 0, n, x, r, p, q, sc, R.partial.as<double>());
         MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.partial.as<double>(), (int)R.grid, 1, sc + 3, 0);
-        rn = std::sqrt(c.read(sc + 3));
+        MDS_CUDA(cudaMemcpyAsync(c.h_pin, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    };
+    std::unique_ptr<Graph> graphs[2];
+    bool graphs_ok = o.graphs != 0;
+    while (rn / bn > o.rtol && it < o.max_iters) {
+        int first = it == 0 ? 1 : 0;
+        Graph *gj = nullptr;
+        if (graphs_ok) {
+            if (!graphs[first]) {
+                graphs[first].reset(new Graph);
+                if (!graph_capture(c, *graphs[first], [&] { body(first); })) {
+                    graphs[first].reset();
+                    graphs_ok = false;
+                }
+            }
+            gj = graphs[first].get();
+        }
+        if (gj)
+            graph_launch(c, *gj);
+        else
+            body(first);
+        c.sync();
+        if (gj) graph_collect(c, *gj);
+        it++;
+        double rn2;
+        std::memcpy(&rn2, c.h_pin, sizeof rn2);
+        rn = std::sqrt(rn2);
         if (!std::isfinite(rn)) {
             res.status = MDS_ERR_BREAKDOWN;
             break;

@@ -47,20 +47,33 @@ template <class VT> struct LvlMat {
 
 // Sum over the nonzeros of one row of a_ij * f(j): CSR with G lanes per row
 // (lane-partial sums), or SELL with one thread per row (G == 0).
+// Matrix entries are streamed once per launch: load them evict-first so the
+// L1/L2 capacity stays with the gathered vectors.
+template <class T> __device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
+template <> __device__ __forceinline__ __nv_bfloat16 ld_stream(const __nv_bfloat16 *p) {
+    unsigned short u = __ldcs(reinterpret_cast<const unsigned short *>(p));
+    return __ushort_as_bfloat16(u);
+}
+template <> __device__ __forceinline__ __half ld_stream(const __half *p) {
+    unsigned short u = __ldcs(reinterpret_cast<const unsigned short *>(p));
+    return __ushort_as_half(u);
+}
+
 template <int G, class VT, class XT, class F>
 __device__ __forceinline__ XT row_sum(const LvlMat<VT> &A, int64_t row, int lane, F f) {
     XT s = 0;
     if (G > 0) {
         int32_t p0 = A.rp[row], p1 = A.rp[row + 1];
-        for (int32_t p = p0 + lane; p < p1; p += G) s += cvt<XT>(A.v[p]) * f(A.ci[p]);
+#pragma unroll 4
+        for (int32_t p = p0 + lane; p < p1; p += G) s += cvt<XT>(ld_stream(A.v + p)) * f(ld_stream(A.ci + p));
     } else {
         int64_t sl = row / A.C;
         int r = (int)(row - sl * A.C);
         int32_t off = A.sp[sl], len = A.sl[sl];
-        for (int32_t k = 0; k < len; k++) {
-            int32_t p = off + k * A.C + r;
-            s += cvt<XT>(A.v[p]) * f(A.sc[p]);
-        }
+        const VT *v = A.v + off + r;
+        const int32_t *cc = A.sc + off + r;
+#pragma unroll 8
+        for (int32_t k = 0; k < len; k++) s += cvt<XT>(ld_stream(v + k * A.C)) * f(ld_stream(cc + k * A.C));
     }
     return s;
 }

@@ -18,7 +18,8 @@ __global__ void __launch_bounds__(256) k_spmv_csr(int64_t nrow, const int32_t *_
     double s = 0.0;
     if (row < nrow) {
         int32_t p0 = rp[row], p1 = rp[row + 1];
-        for (int32_t p = p0 + lane; p < p1; p += G) s += to_d(v[p]) * to_d(__ldg(x + ci[p]));
+#pragma unroll 4
+        for (int32_t p = p0 + lane; p < p1; p += G) s += to_d(__ldcs(v + p)) * to_d(__ldg(x + __ldcs(ci + p)));
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, G);

@@ -6,8 +6,10 @@ missing this module raises; there is no CPU fallback.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import os
+import weakref
 from dataclasses import dataclass
 from typing import Optional
 
@@ -52,7 +54,7 @@ class SetupOpts(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("krylov", C.c_int), ("restart", C.c_int), ("rtol", C.c_double), ("max_iters", C.c_int),
-                ("use_precond", C.c_int)]
+                ("use_precond", C.c_int), ("graphs", C.c_int)]
 
 
 class RhsStats(C.Structure):
@@ -61,6 +63,29 @@ class RhsStats(C.Structure):
 
 
 _lib = None
+
+# Live handles, closed in dependency order (preconditioners, systems, contexts)
+# before interpreter teardown, whatever order the garbage collector would pick.
+_live = {0: weakref.WeakSet(), 1: weakref.WeakSet(), 2: weakref.WeakSet()}
+_atexit_registered = False
+
+
+def _close_all():
+    for rank in (0, 1, 2):
+        for obj in list(_live[rank]):
+            try:
+                obj.close()
+            except Exception:
+                pass
+
+
+def _track(obj, rank):
+    global _atexit_registered
+    _live[rank].add(obj)
+    if not _atexit_registered:
+        # registered after torch is imported, so it runs before torch's own exit handlers
+        atexit.register(_close_all)
+        _atexit_registered = True
 
 # Every entry point of include/mdsolve.h with its ctypes signature.
 _SIGS = {
@@ -168,6 +193,7 @@ class Context:
         h = C.c_void_p()
         self._check(L.mds_create(C.byref(h), device, C.c_void_p(stream), None), ctx=False)
         self.h = h
+        _track(self, 2)
 
     def _check(self, code, ctx=True):
         if code < 0:
@@ -177,6 +203,11 @@ class Context:
 
     def close(self):
         if getattr(self, "h", None):
+            # dependents first
+            for rank in (0, 1):
+                for obj in list(_live[rank]):
+                    if obj.ctx is self:
+                        obj.close()
             lib().mds_destroy(self.h)
             self.h = None
 
@@ -295,9 +326,13 @@ class System:
         self.n_m, self.n_f, self.nrhs = n_m.value, n_f.value, nrhs.value
         self.nnz = list(nnz)
         self.N = self.n_m + self.n_f
+        _track(self, 1)
 
     def close(self):
         if getattr(self, "h", None):
+            for obj in list(_live[0]):
+                if obj.sys is self:
+                    obj.close()
             lib().mds_system_destroy(self.h)
             self.h = None
 
@@ -327,6 +362,7 @@ class System:
 class Precond:
     def __init__(self, ctx: Context, sys: System, h):
         self.ctx, self.sys, self.h = ctx, sys, h
+        _track(self, 0)
 
     def close(self):
         if getattr(self, "h", None):

@@ -443,3 +443,24 @@ def test_autotuner_cache_reuses_choice(ctx, torch_mod):
     ctx.precond_apply(p1, dev(torch_mod, r), z1)
     ctx.precond_apply(p2, dev(torch_mod, r), z2)
     assert torch_mod.equal(z1, z2)
+
+
+@pytest.mark.parametrize("krylov,kind,precision", [("fgmres", "lower", "fp64"), ("fgmres", "lower", "fp32"),
+                                                    ("pcg", "diag", "fp64")])
+def test_graphs_match_direct_launches(ctx, torch_mod, krylov, kind, precision):
+    """Replaying captured Krylov steps gives bit-identical results and the same
+    launch accounting as launching every kernel directly."""
+    torch = torch_mod
+    inst = CASES["planes3d-13-kf1"]() if krylov == "pcg" else CASES["seg2d-96"]()
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_, kind=kind, precision=precision)
+    out = []
+    for graphs in (0, 1):
+        x = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+        ctx.timing_reset()
+        code, st = ctx.solve(sys_, prec, None, x, krylov=krylov, restart=10, graphs=graphs, max_iters=2000)
+        out.append((x, st[0], ctx.launch_count(), ctx.timing_query("gs_dot")[0], ctx.timing_query("spmv")[0]))
+    (x0, s0, l0, d0, p0), (x1, s1, l1, d1, p1) = out
+    assert torch.equal(x0, x1)
+    assert s0.iterations == s1.iterations and s0.relres_true == s1.relres_true
+    assert l0 == l1 and d0 == d1 and p0 == p1
