@@ -74,6 +74,9 @@ typedef struct {
  * for stream-ordered cudaMallocAsync/cudaFreeAsync.  The allocator struct is
  * copied; its callbacks must stay valid for the context's lifetime. */
 int mds_create(mds_ctx *out, int device, void *cuda_stream, const mds_allocator *alloc);
+/* Systems and preconditioners keep their context alive: destroying a context
+ * that still has some only marks it, and it is released when the last of them
+ * is destroyed (in any order).  A context must not be used after this call. */
 int mds_destroy(mds_ctx ctx);
 /* Change the stream later calls enqueue on. */
 int mds_set_stream(mds_ctx ctx, void *cuda_stream);

@@ -1,6 +1,7 @@
 // The C ABI of libmdsolve (include/mdsolve.h): contexts, memory, systems,
 // preconditioner set-up, Algorithm 1, solves and timing.
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <new>
 
@@ -185,6 +186,7 @@ int mds_create(mds_ctx *out, int device, void *stream, const mds_allocator *allo
         MDS_REQUIRE(device >= 0 && device < ndev, MDS_ERR_INVALID, "no such CUDA device");
         MDS_CUDA(cudaSetDevice(device));
         c->device = device;
+        c->owner = h;
         c->stream = (cudaStream_t)stream;
         if (alloc && alloc->alloc && alloc->free) {
             c->alloc = *alloc;
@@ -203,9 +205,9 @@ int mds_create(mds_ctx *out, int device, void *stream, const mds_allocator *allo
     return MDS_OK;
 }
 
-int mds_destroy(mds_ctx ctx) {
-    if (!ctx) return MDS_ERR_INVALID;
+static void ctx_release(mds_ctx ctx) {
     Ctx &c = ctx->c;
+    cudaSetDevice(c.device);
     cudaStreamSynchronize(c.stream);
     for (int k = 0; k < MDS_KCLASS_COUNT; k++)
         for (auto &r : c.evs[k]) {
@@ -216,6 +218,23 @@ int mds_destroy(mds_ctx ctx) {
     cudaFreeHost(c.h_pin);
     if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
     delete ctx;
+}
+
+// Systems and preconditioners keep their context alive: destroying a context
+// that still has dependents only marks it, and the last dependent's destroy
+// releases it.
+static void ctx_drop_dependent(Ctx *c) {
+    if (--c->dependents == 0 && c->destroy_requested) ctx_release(static_cast<mds_ctx>(c->owner));
+}
+
+int mds_destroy(mds_ctx ctx) {
+    if (!ctx) return MDS_ERR_INVALID;
+    if (ctx->c.destroy_requested) return MDS_ERR_INVALID;
+    if (ctx->c.dependents > 0) {
+        ctx->c.destroy_requested = true;
+        return MDS_OK;
+    }
+    ctx_release(ctx);
     return MDS_OK;
 }
 
@@ -245,6 +264,7 @@ int mds_assemble(mds_ctx ctx, const mds_instance *inst, mds_system *out) {
         delete s;
         throw;
     }
+    c->dependents++;
     *out = s;
     API_END(c)
 }
@@ -293,14 +313,17 @@ int mds_system_from_csr(mds_ctx ctx, const mds_csr *Amm, const mds_csr *Amf, con
         delete s;
         throw;
     }
+    c->dependents++;
     *out = s;
     API_END(c)
 }
 
 int mds_system_destroy(mds_system sys) {
     if (!sys) return MDS_ERR_INVALID;
-    cudaSetDevice(sys->ctx->device);
+    Ctx *c = sys->ctx;
+    cudaSetDevice(c->device);
     delete sys;
+    ctx_drop_dependent(c);
     return MDS_OK;
 }
 
@@ -376,14 +399,17 @@ int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_preco
         delete p;
         throw;
     }
+    c->dependents++;
     *out = p;
     API_END(c)
 }
 
 int mds_precond_destroy(mds_precond p) {
     if (!p) return MDS_ERR_INVALID;
-    cudaSetDevice(p->ctx->device);
+    Ctx *c = p->ctx;
+    cudaSetDevice(c->device);
     delete p;
+    ctx_drop_dependent(c);
     return MDS_OK;
 }
 

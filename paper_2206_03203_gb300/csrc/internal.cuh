@@ -123,6 +123,9 @@ struct Ctx {
     int64_t total_launches = 0;
     double graph_ms[MDS_KCLASS_COUNT] = {};
     Graph *capturing = nullptr;   // recording target while a stream capture is open
+    void *owner = nullptr;        // the mds_ctx handle that holds this context
+    int dependents = 0;           // live systems and preconditioners made on this context
+    bool destroy_requested = false;
     cudaStream_t cap_stream = nullptr;
     // autotuner choices by (rows, nonzeros, value type)
     std::map<std::tuple<int64_t, int64_t, int>, TuneChoice> tune_cache;

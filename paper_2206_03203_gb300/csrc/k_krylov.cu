@@ -265,6 +265,7 @@ __global__ void k_copy1(const double *__restrict__ a, double *__restrict__ b) { 
 
 struct Red {
     Buf partial;
+    double *pp = nullptr;  // the partials buffer in use
     unsigned grid = 1;   // blocks of the single-vector reductions
     unsigned mgrid = 1;  // row blocks per basis vector in k_mdot
 };
@@ -277,30 +278,68 @@ static unsigned mdot_grid(int64_t n) {
 }
 
 static void dot_dev(Ctx &c, Red &R, int64_t n, const double *a, const double *b, double *out) {
-    MDS_LAUNCH(c, KC_NONE, 16.0 * n, k_dot, R.grid, RED_BLOCK, 0, n, a, b, R.partial.as<double>());
-    MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.partial.as<double>(), (int)R.grid, 1, out, 0);
+    MDS_LAUNCH(c, KC_NONE, 16.0 * n, k_dot, R.grid, RED_BLOCK, 0, n, a, b, R.pp);
+    MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.pp, (int)R.grid, 1, out, 0);
+}
+
+static size_t round256(size_t doubles) { return (doubles + 31) / 32 * 32; }
+
+// Workspace parts in order: reduction partials, V ((m+1) rows), Z (m rows),
+// Hessenberg ((m+1) x m), small scalars (256).
+size_t fgmres_workspace_doubles(int64_t n, int m) {
+    const int64_t ld = (n + 63) / 64 * 64;
+    unsigned g = red_grid(n) > mdot_grid(n) ? red_grid(n) : mdot_grid(n);
+    return round256((size_t)g * QMAX) + round256((size_t)(m + 1) * ld) + round256((size_t)m * ld) +
+           round256((size_t)(m + 1) * m) + 256;
+}
+
+FgmresWorkspace fgmres_workspace_carve(double *base, int64_t n, int m) {
+    const int64_t ld = (n + 63) / 64 * 64;
+    unsigned g = red_grid(n) > mdot_grid(n) ? red_grid(n) : mdot_grid(n);
+    FgmresWorkspace w;
+    w.partial = base;
+    w.V = w.partial + round256((size_t)g * QMAX);
+    w.Z = w.V + round256((size_t)(m + 1) * ld);
+    w.H = w.Z + round256((size_t)m * ld);
+    w.small = w.H + round256((size_t)(m + 1) * m);
+    return w;
 }
 
 KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, double *x, int64_t n,
-                    const mds_solve_opts &o) {
+                    const mds_solve_opts &o, const FgmresWorkspace *ws) {
     KrylovResult res;
     const int m = o.restart < 1 ? 1 : (o.restart > QMAX - 1 ? QMAX - 1 : o.restart);
     Red R;
     R.grid = red_grid(n);
     R.mgrid = mdot_grid(n);
-    R.partial = Buf(&c, sizeof(double) * (size_t)(R.grid > R.mgrid ? R.grid : R.mgrid) * QMAX);
     // basis rows padded to 64 elements: 16-byte aligned rows for vector loads
     const int64_t ld = (n + 63) / 64 * 64;
-    Buf V(&c, sizeof(double) * (size_t)(m + 1) * (size_t)ld);
-    Buf Z(&c, sizeof(double) * (size_t)m * (size_t)ld);
-    Buf H(&c, sizeof(double) * (size_t)(m + 1) * m);
-    Buf small(&c, sizeof(double) * 256);
-    double *d = small.as<double>();
+    Buf V, Z, H, small;
+    double *Vp, *Zp, *Hp, *d, *partial;
+    if (ws) {
+        partial = ws->partial;
+        Vp = ws->V;
+        Zp = ws->Z;
+        Hp = ws->H;
+        d = ws->small;
+    } else {
+        R.partial = Buf(&c, sizeof(double) * (size_t)(R.grid > R.mgrid ? R.grid : R.mgrid) * QMAX);
+        V = Buf(&c, sizeof(double) * (size_t)(m + 1) * (size_t)ld);
+        Z = Buf(&c, sizeof(double) * (size_t)m * (size_t)ld);
+        H = Buf(&c, sizeof(double) * (size_t)(m + 1) * m);
+        small = Buf(&c, sizeof(double) * 256);
+        partial = R.partial.as<double>();
+        Vp = V.as<double>();
+        Zp = Z.as<double>();
+        Hp = H.as<double>();
+        d = small.as<double>();
+    }
+    R.pp = partial;
+    MDS_REQUIRE(partial && Vp && Zp && Hp && d, MDS_ERR_INVALID, "FGMRES workspace pointer missing");
     MDS_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * 256, c.stream));
     // cs, sn, g, y, h (first CGS pass), h + 32 (second pass), scalars, norms
     double *cs = d, *sn = d + 32, *g = d + 64, *y = d + 96, *h = d + 128, *h2 = d + 160, *scal = d + 192,
            *nsq = d + 224, *nsq2 = d + 225, *dflag = d + 226;
-    double *Vp = V.as<double>(), *Zp = Z.as<double>();
     // ||b||
     dot_dev(c, R, n, b, b, nsq);
     double bn = std::sqrt(c.read(nsq));
@@ -321,21 +360,21 @@ KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, 
         int nq = j + 1;
         double fl = 2.0 * (double)n * nq;
         MDS_LAUNCH_F(c, KC_GS_DOT, 8.0 * n * (nq + 1), fl + 2.0 * n, k_mdot, dim3(R.mgrid, nq + 1), RED_BLOCK, 0, n,
-                     Vp, ld, nq, w, R.partial.as<double>(), (const double *)nullptr);
-        MDS_LAUNCH(c, KC_NONE, 0, k_reduce_rows, nq + 1, 32, 0, R.partial.as<double>(), (int)R.mgrid, nq + 1, h, 0,
+                     Vp, ld, nq, w, R.pp, (const double *)nullptr);
+        MDS_LAUNCH(c, KC_NONE, 0, k_reduce_rows, nq + 1, 32, 0, R.pp, (int)R.mgrid, nq + 1, h, 0,
                    (const double *)nullptr);
         MDS_LAUNCH_F(c, KC_GS_AXPY, 8.0 * n * (nq + 2), fl + 2.0 * n, (k_maxpy<-1, true>), R.grid, RED_BLOCK, 0, n,
-                     Vp, ld, nq, h, w, R.partial.as<double>(), (const double *)nullptr);
-        MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.partial.as<double>(), (int)R.grid, 1, nsq, 0);
+                     Vp, ld, nq, h, w, R.pp, (const double *)nullptr);
+        MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.pp, (int)R.grid, 1, nsq, 0);
         MDS_LAUNCH(c, KC_NONE, 0, k_dgks, 1, 1, 0, h + nq, nsq, dflag, h2, nq);
         MDS_LAUNCH_F(c, KC_GS_DOT, 8.0 * n * (nq + 1), fl, k_mdot, dim3(R.mgrid, nq), RED_BLOCK, 0, n, Vp, ld, nq, w,
-                     R.partial.as<double>(), (const double *)dflag);
-        MDS_LAUNCH(c, KC_NONE, 0, k_reduce_rows, nq, 32, 0, R.partial.as<double>(), (int)R.mgrid, nq, h2, 0,
+                     R.pp, (const double *)dflag);
+        MDS_LAUNCH(c, KC_NONE, 0, k_reduce_rows, nq, 32, 0, R.pp, (int)R.mgrid, nq, h2, 0,
                    (const double *)dflag);
         MDS_LAUNCH_F(c, KC_GS_AXPY, 8.0 * n * (nq + 2), fl + 2.0 * n, (k_maxpy<-1, true>), R.grid, RED_BLOCK, 0, n,
-                     Vp, ld, nq, h2, w, R.partial.as<double>(), (const double *)dflag);
-        MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.partial.as<double>(), (int)R.grid, 1, nsq2, 0);
-        MDS_LAUNCH(c, KC_NONE, 0, k_arnoldi, 1, 1, 0, j, m, H.as<double>(), h, h2, nsq, nsq2, dflag, cs, sn, g, scal);
+                     Vp, ld, nq, h2, w, R.pp, (const double *)dflag);
+        MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.pp, (int)R.grid, 1, nsq2, 0);
+        MDS_LAUNCH(c, KC_NONE, 0, k_arnoldi, 1, 1, 0, j, m, Hp, h, h2, nsq, nsq2, dflag, cs, sn, g, scal);
         MDS_LAUNCH(c, KC_NONE, 16.0 * n, k_scale, red_grid(n), RED_BLOCK, 0, n, w, scal + 3, w);
         MDS_CUDA(cudaMemcpyAsync(c.h_pin, scal, 5 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     };
@@ -400,7 +439,7 @@ KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, 
             res.status = MDS_ERR_BREAKDOWN;
             break;
         }
-        MDS_LAUNCH(c, KC_NONE, 0, k_backsolve, 1, 1, 0, kdone, m, H.as<double>(), g, y);
+        MDS_LAUNCH(c, KC_NONE, 0, k_backsolve, 1, 1, 0, kdone, m, Hp, g, y);
         MDS_LAUNCH(c, KC_NONE, 8.0 * n * (kdone + 2), (k_maxpy<1, false>), R.grid, RED_BLOCK, 0, n, Zp, ld, kdone,
                    y, x, nullptr, (const double *)nullptr);
         restarts++;
@@ -421,6 +460,7 @@ KrylovResult pcg(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, dou
     Red R;
     R.grid = red_grid(n);
     R.partial = Buf(&c, sizeof(double) * (size_t)R.grid * QMAX);
+    R.pp = R.partial.as<double>();
     Buf rb(&c, sizeof(double) * (size_t)n), zb(&c, sizeof(double) * (size_t)n), pb(&c, sizeof(double) * (size_t)n),
         qb(&c, sizeof(double) * (size_t)n);
     Buf small(&c, sizeof(double) * 8);
@@ -445,8 +485,8 @@ KrylovResult pcg(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, dou
         MDS_LAUNCH(c, KC_NONE, 0, k_copy1, 1, 1, 0, sc, sc + 1);  // rz = rz_new
         spmv_f64(c, A, p, q, KC_SPMV);
         dot_dev(c, R, n, p, q, sc + 2);
-        MDS_LAUNCH(c, KC_NONE, 56.0 * n, k_pcg_xr, R.grid, RED_BLOCK, 0, n, x, r, p, q, sc, R.partial.as<double>());
-        MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.partial.as<double>(), (int)R.grid, 1, sc + 3, 0);
+        MDS_LAUNCH(c, KC_NONE, 56.0 * n, k_pcg_xr, R.grid, RED_BLOCK, 0, n, x, r, p, q, sc, R.pp);
+        MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.pp, (int)R.grid, 1, sc + 3, 0);
         MDS_CUDA(cudaMemcpyAsync(c.h_pin, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     };
     std::unique_ptr<Graph> graphs[2];

@@ -62,7 +62,7 @@ template <> __device__ __forceinline__ __half ld_stream(const __half *p) {
 template <int G, class VT, class XT, class F>
 __device__ __forceinline__ XT row_sum(const LvlMat<VT> &A, int64_t row, int lane, F f) {
     XT s = 0;
-    if (G > 0) {
+    if constexpr (G > 0) {
         int32_t p0 = A.rp[row], p1 = A.rp[row + 1];
 #pragma unroll 4
         for (int32_t p = p0 + lane; p < p1; p += G) s += cvt<XT>(ld_stream(A.v + p)) * f(ld_stream(A.ci + p));
@@ -79,7 +79,7 @@ __device__ __forceinline__ XT row_sum(const LvlMat<VT> &A, int64_t row, int lane
 }
 
 template <int G, class XT> __device__ __forceinline__ XT lane_reduce(XT s) {
-    if (G > 1) {
+    if constexpr (G > 1) {
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, G);
     }
@@ -88,7 +88,7 @@ template <int G, class XT> __device__ __forceinline__ XT lane_reduce(XT s) {
 
 template <int G> __device__ __forceinline__ void row_of(int64_t &row, int &lane) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (G > 0) {
+    if constexpr (G > 0) {
         row = t / G;
         lane = (int)(t % G);
     } else {

@@ -16,8 +16,19 @@ struct KrylovResult {
     double relres_true = 0.0;
 };
 
+// Caller-provided FGMRES workspace (device pointers, 256-byte aligned).
+struct FgmresWorkspace {
+    double *partial, *V, *Z, *H, *small;
+};
+// Doubles the workspace of an FGMRES(m) solve of size n occupies, with each
+// part rounded up to 256 bytes, and its carving from one base pointer.
+size_t fgmres_workspace_doubles(int64_t n, int m);
+FgmresWorkspace fgmres_workspace_carve(double *base, int64_t n, int m);
+
+// ws == nullptr: the workspace is allocated from the context.
 KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, double *x, int64_t n,
-                    const mds_solve_opts &o);
+                    const mds_solve_opts &o, const FgmresWorkspace *ws = nullptr);
+
 KrylovResult pcg(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, double *x, int64_t n,
                  const mds_solve_opts &o);
 

@@ -464,3 +464,18 @@ def test_graphs_match_direct_launches(ctx, torch_mod, krylov, kind, precision):
     assert torch.equal(x0, x1)
     assert s0.iterations == s1.iterations and s0.relres_true == s1.relres_true
     assert l0 == l1 and d0 == d1 and p0 == p1
+
+
+def test_context_outlives_dependents_in_any_order(torch_mod):
+    """mds_destroy with live systems/preconditioners defers the release until
+    the last of them is destroyed (any finalisation order is safe)."""
+    from paper_2206_03203_gb300 import mdsolve
+    L = mdsolve.lib()
+    c2 = mdsolve.Context(0)
+    s = c2.assemble(inputs.fixed_2d(n=16))
+    p = c2.setup(s)
+    h_ctx, h_s, h_p = c2.h, s.h, p.h
+    c2.h = s.h = p.h = None  # detach the Python wrappers
+    assert L.mds_destroy(h_ctx) == 0
+    assert L.mds_system_destroy(h_s) == 0
+    assert L.mds_precond_destroy(h_p) == 0
