@@ -240,6 +240,32 @@ int mds_solve_opts_default(mds_solve_opts *o);
 int mds_solve(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, double *x,
               int nrhs, const mds_solve_opts *opts, mds_rhs_stats *stats);
 
+/* ---- solve without device allocation ----
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory while solving: code running inside a
+ * framework that owns every allocation (a memory-capped serving process, a
+ * caller between pool resets) or a caller that must not synchronise on the
+ * allocator.  It runs the same FGMRES as mds_solve (nrhs = 1, kernels
+ * launched directly, no CUDA graphs) with its Krylov workspace (bases V and
+ * Z, Hessenberg matrix, reduction partials) in one file-scope static device
+ * array of MDS_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library
+ * holds until the process exits.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   - n_m + n_f must be <= MDS_NOALLOC_MAX_N and restart <= 30; larger
+ *     problems are rejected with MDS_ERR_INVALID.
+ *   - b (NULL: the assembled right-hand side) and x must be device pointers;
+ *     x holds x0 on entry and the solution on return.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - Every call on a device shares the one array and leaves its contents
+ *     behind (the parts that must start at zero are cleared on entry); calls
+ *     whose GPU work overlaps, from any context or stream, race on it.
+ *   - The preconditioner's own work vectors were allocated by mds_setup. */
+#define MDS_NOALLOC_MAX_N 16384
+#define MDS_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
+int mds_solve_noalloc(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, double *x,
+                      const mds_solve_opts *opts, mds_rhs_stats *stats);
+
 /* ---- measurement ----
  * Kernel classes timed with CUDA events on the context stream when enabled:
  * 0 = full-system SpMV, 1 = V-cycle residual (pre-smooth + residual),

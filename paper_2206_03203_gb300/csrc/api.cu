@@ -614,6 +614,51 @@ int mds_solve(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, do
     API_END(c)
 }
 
+int mds_solve_noalloc(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, double *x,
+                      const mds_solve_opts *opts, mds_rhs_stats *stats) {
+    if (!ctx || !sys || !x) return MDS_ERR_INVALID;
+    Ctx *c = &ctx->c;
+    API_BEGIN
+    MDS_CUDA(cudaSetDevice(c->device));
+    mds_solve_opts o;
+    mds_solve_opts_default(&o);
+    if (opts) o = *opts;
+    o.graphs = 0;  // graph instantiation may allocate
+    int64_t n = sys->n_m + sys->n_f;
+    MDS_REQUIRE(o.krylov == MDS_KRYLOV_FGMRES, MDS_ERR_INVALID, "mds_solve_noalloc runs FGMRES only");
+    MDS_REQUIRE(n <= MDS_NOALLOC_MAX_N, MDS_ERR_INVALID,
+                "mds_solve_noalloc: n_m + n_f = " + std::to_string(n) + " exceeds MDS_NOALLOC_MAX_N = " +
+                    std::to_string(MDS_NOALLOC_MAX_N));
+    MDS_REQUIRE(o.restart >= 1 && o.restart <= 30, MDS_ERR_INVALID, "mds_solve_noalloc: restart must be 1..30");
+    MDS_REQUIRE(o.rtol > 0.0 && o.max_iters >= 0, MDS_ERR_INVALID, "bad solve options");
+    MDS_REQUIRE(!o.use_precond || (prec && prec->sys == sys), MDS_ERR_INVALID, "preconditioner of another system");
+    const double *B = b ? b : sys->b;
+    MDS_REQUIRE(is_device_ptr(B) && is_device_ptr(x), MDS_ERR_INVALID,
+                "mds_solve_noalloc needs device pointers for b and x");
+    size_t need = fgmres_workspace_doubles(n, o.restart);
+    MDS_REQUIRE(need <= noalloc_scratch_doubles(), MDS_ERR_INVALID, "mds_solve_noalloc: workspace exceeds the array");
+    FgmresWorkspace ws = fgmres_workspace_carve(noalloc_scratch(*c), n, o.restart);
+    PrecFn M;
+    if (o.use_precond)
+        M = [prec](const double *r, double *z) { precond_apply(prec, r, z); };
+    else
+        M = [c, n](const double *r, double *z) {
+            MDS_CUDA(cudaMemcpyAsync(z, r, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, c->stream));
+        };
+    KrylovResult r = fgmres(*c, sys->view[4], M, B, x, n, o, &ws);
+    c->sync();
+    if (stats) {
+        stats->iterations = r.iterations;
+        stats->restarts = r.restarts;
+        stats->status = r.status;
+        stats->relres_est = r.relres_est;
+        stats->relres_true = r.relres_true;
+    }
+    if (r.status < 0) c->last_error = "solve failed; see its stats";
+    return r.status;
+    API_END(c)
+}
+
 int mds_timing_enable(mds_ctx ctx, int k, int enable) {
     if (!ctx || k < 0 || k >= MDS_KCLASS_COUNT) return MDS_ERR_INVALID;
     ctx->c.timing[k] = enable != 0;

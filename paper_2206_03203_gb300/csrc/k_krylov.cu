@@ -7,6 +7,7 @@
 #include <cmath>
 #include <functional>
 #include <memory>
+#include <mutex>
 
 #include "internal.cuh"
 #include "krylov.cuh"
@@ -526,6 +527,31 @@ KrylovResult pcg(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, dou
     res.iterations = it;
     if (res.status != MDS_ERR_BREAKDOWN) res.status = res.relres_true <= o.rtol ? MDS_OK : MDS_WARN_NOT_CONVERGED;
     return res;
+}
+
+// ---------------------------------------------------------------- no-allocation workspace
+
+// Static FGMRES workspace for mds_solve_noalloc: 8 MiB in every device that
+// loads the library, enough for n <= MDS_NOALLOC_MAX_N and restart <= 30.
+constexpr size_t NOALLOC_DOUBLES = (size_t)MDS_NOALLOC_SCRATCH_BYTES / sizeof(double);
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+
+size_t noalloc_scratch_doubles() { return NOALLOC_DOUBLES; }
+
+// The symbol's device address, looked up once per device with that device
+// current (the host-side name is only a stand-in, never a device address).
+double *noalloc_scratch(Ctx &c) {
+    static std::mutex mu;
+    static double *addr[256] = {};
+    std::lock_guard<std::mutex> lock(mu);
+    MDS_REQUIRE(c.device >= 0 && c.device < 256, MDS_ERR_INVALID, "device index out of range");
+    if (!addr[c.device]) {
+        MDS_CUDA(cudaSetDevice(c.device));
+        void *p = nullptr;
+        MDS_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        addr[c.device] = static_cast<double *>(p);
+    }
+    return addr[c.device];
 }
 
 }  // namespace mds

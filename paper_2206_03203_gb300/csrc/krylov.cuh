@@ -29,6 +29,10 @@ FgmresWorkspace fgmres_workspace_carve(double *base, int64_t n, int m);
 KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, double *x, int64_t n,
                     const mds_solve_opts &o, const FgmresWorkspace *ws = nullptr);
 
+// Base of the library's static no-allocation workspace on the current device
+// (see mds_solve_noalloc) and its size in doubles.
+double *noalloc_scratch(Ctx &c);
+size_t noalloc_scratch_doubles();
 KrylovResult pcg(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, double *x, int64_t n,
                  const mds_solve_opts &o);
 

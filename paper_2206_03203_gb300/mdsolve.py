@@ -113,6 +113,8 @@ _SIGS = {
     "mds_solve_opts_default": (C.c_int, [C.POINTER(SolveOpts)]),
     "mds_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                             C.POINTER(SolveOpts), C.POINTER(RhsStats)]),
+    "mds_solve_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.POINTER(SolveOpts), C.POINTER(RhsStats)]),
     "mds_timing_enable": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "mds_timing_reset": (C.c_int, [C.c_void_p]),
     "mds_timing_query": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
@@ -271,6 +273,16 @@ class Context:
                                C.c_void_p(_ptr(x)), nrhs, C.byref(o), st)
         self._check(code)
         return code, [Stats(s.iterations, s.restarts, s.status, s.relres_est, s.relres_true) for s in st]
+
+    def solve_noalloc(self, sys: "System", prec: Optional["Precond"], b=None, x=None, **opts):
+        """FGMRES with the library's static workspace (device tensors only,
+        n_m + n_f <= 16384).  Returns (status, Stats)."""
+        o = solve_opts(**opts)
+        st = RhsStats()
+        code = lib().mds_solve_noalloc(self.h, sys.h, prec.h if prec is not None else None, C.c_void_p(_ptr(b)),
+                                       C.c_void_p(_ptr(x)), C.byref(o), C.byref(st))
+        self._check(code)
+        return code, Stats(st.iterations, st.restarts, st.status, st.relres_est, st.relres_true)
 
     def spmv(self, sys, x, y):
         self._check(lib().mds_spmv(self.h, sys.h, C.c_void_p(_ptr(x)), C.c_void_p(_ptr(y))))
