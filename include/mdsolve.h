@@ -133,6 +133,19 @@ typedef struct {
  * the interior faces or two fracture cells on one face. */
 int mds_assemble(mds_ctx ctx, const mds_instance *inst, mds_system *out);
 
+/* Assemble n_inst independent instances (uneven sizes allowed, equal nrhs)
+ * into one packed block-diagonal system.  Unknowns are ordered
+ * [matrix cells of instance 0..n_inst-1; fracture cells of instance
+ * 0..n_inst-1], so the packed system keeps the 2x2 block structure of
+ * Eq. (4) with block-diagonal blocks, and every preconditioner set up on it
+ * acts on each instance separately.  mds_solve on such a system solves every
+ * (instance, right-hand side) pair as its own problem. */
+int mds_assemble_batch(mds_ctx ctx, const mds_instance *inst, int n_inst, mds_system *out);
+/* Instances of a packed system: instance k owns matrix rows
+ * [m_off[k], m_off[k+1]) and fracture rows n_m + [f_off[k], f_off[k+1]);
+ * m_off and f_off have n_inst + 1 entries (either may be NULL). */
+int mds_system_instances(mds_system sys, int *n_inst, int64_t *m_off, int64_t *f_off);
+
 /* Wrap caller CSR blocks (device, borrowed until mds_system_destroy) and an
  * optional device right-hand side b [n_m + n_f] (NULL: zero).  The library
  * builds its own merged copy of the full matrix. */
@@ -218,6 +231,9 @@ typedef struct {
     int use_precond;     /* 1 = the set-up preconditioner, 0 = identity */
     int graphs;          /* 1 = capture each Krylov step as a CUDA graph on its first use and
                             replay it (1); 0 = launch every kernel directly */
+    int batched;         /* 1 = solve the nrhs columns together in lockstep, each as its own
+                            FGMRES problem with shared matrix reads (1); packed multi-instance
+                            systems are always solved this way */
 } mds_solve_opts;
 
 typedef struct {
@@ -231,7 +247,9 @@ typedef struct {
 int mds_solve_opts_default(mds_solve_opts *o);
 
 /* Solve A x = b for nrhs right-hand sides.  b: [nrhs][n] FP64 (column r at
- * b + r n), NULL = the assembled right-hand sides.  x: [nrhs][n], holds the
+ * b + r n), NULL = the assembled right-hand sides.  On a packed batch every
+ * (instance k, column r) pair is an independent problem with its own
+ * stopping test, and stats has n_inst * nrhs entries (index k nrhs + r).  x: [nrhs][n], holds the
  * initial guess on entry (zeros give the x0 = 0 of Sec. 4) and the solution on
  * return.  b and x may be device or host pointers (host ones are staged
  * through device buffers inside the call).  `prec` may be NULL when

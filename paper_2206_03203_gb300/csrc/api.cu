@@ -194,7 +194,7 @@ int mds_create(mds_ctx *out, int device, void *stream, const mds_allocator *allo
         }
         MDS_CUDA(cudaMalloc(&c->d_err, sizeof(int)));
         MDS_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
-        MDS_CUDA(cudaMallocHost(&c->h_pin, 4096));
+        MDS_CUDA(cudaMallocHost(&c->h_pin, Ctx::PIN_BYTES));
     } catch (const Error &e) {
         int code = e.code;
         if (c->d_err) cudaFree(c->d_err);
@@ -244,8 +244,8 @@ int mds_set_stream(mds_ctx ctx, void *stream) {
     return MDS_OK;
 }
 
-int mds_assemble(mds_ctx ctx, const mds_instance *inst, mds_system *out) {
-    if (!ctx || !inst || !out) return MDS_ERR_INVALID;
+int mds_assemble_batch(mds_ctx ctx, const mds_instance *inst, int n_inst, mds_system *out) {
+    if (!ctx || !inst || !out || n_inst < 1) return MDS_ERR_INVALID;
     Ctx *c = &ctx->c;
     *out = nullptr;
     API_BEGIN
@@ -253,10 +253,17 @@ int mds_assemble(mds_ctx ctx, const mds_instance *inst, mds_system *out) {
     auto *s = new mds_system_s;
     try {
         s->ctx = c;
-        assemble_instance(*c, *inst, s->own);
+        if (n_inst == 1) {
+            assemble_instance(*c, inst[0], s->own);
+        } else {
+            std::vector<SystemData> parts(n_inst);
+            for (int k = 0; k < n_inst; k++) assemble_instance(*c, inst[k], parts[k]);
+            pack_instances(*c, parts, s->own);
+        }
         s->n_m = s->own.n_m;
         s->n_f = s->own.n_f;
         s->nrhs = s->own.nrhs;
+        s->n_inst = n_inst;
         for (int q = 0; q < 4; q++) s->view[q] = s->own.blk[q].view();
         s->view[4] = s->own.full.view();
         s->b = s->own.b.as<double>();
@@ -267,6 +274,20 @@ int mds_assemble(mds_ctx ctx, const mds_instance *inst, mds_system *out) {
     c->dependents++;
     *out = s;
     API_END(c)
+}
+
+int mds_assemble(mds_ctx ctx, const mds_instance *inst, mds_system *out) {
+    return mds_assemble_batch(ctx, inst, 1, out);
+}
+
+int mds_system_instances(mds_system sys, int *n_inst, int64_t *m_off, int64_t *f_off) {
+    if (!sys) return MDS_ERR_INVALID;
+    if (n_inst) *n_inst = sys->n_inst;
+    for (int k = 0; k <= sys->n_inst; k++) {
+        if (m_off) m_off[k] = sys->own.moff.size() > (size_t)k ? sys->own.moff[k] : (k ? sys->n_m : 0);
+        if (f_off) f_off[k] = sys->own.foff.size() > (size_t)k ? sys->own.foff[k] : (k ? sys->n_f : 0);
+    }
+    return MDS_OK;
 }
 
 static void check_csr(const mds_csr *A, int64_t nrow, int64_t ncol, const char *name) {
@@ -301,6 +322,8 @@ int mds_system_from_csr(mds_ctx ctx, const mds_csr *Amm, const mds_csr *Amf, con
         s->view[3] = *Aff;
         merge_blocks(*c, s->view, nm, nf, s->own.full);
         s->view[4] = s->own.full.view();
+        s->own.moff = {0, nm};
+        s->own.foff = {0, nf};
         s->own.b = Buf(c, sizeof(double) * (size_t)(nm + nf));
         if (b)
             MDS_CUDA(cudaMemcpyAsync(s->own.b.p, b, sizeof(double) * (size_t)(nm + nf), cudaMemcpyDeviceToDevice,
@@ -395,6 +418,7 @@ int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_preco
         if (p->has_f) amg_setup(*c, sys->view[3], o, p->h[1]);
         int64_t mx = sys->n_m > sys->n_f ? sys->n_m : sys->n_f;
         p->tf64 = Buf(c, sizeof(double) * (size_t)(mx > 0 ? mx : 1));
+        p->tf_cap = mx;
     } catch (...) {
         delete p;
         throw;
@@ -446,58 +470,68 @@ int mds_precond_level(mds_precond p, int block, int level, mds_csr *A, const int
 namespace mds {
 
 // V-cycle on FP64 input/output regardless of the hierarchy's precision.
-static void vcycle_f64(Ctx &c, Hierarchy &h, const double *b, double *x) {
+static void vcycle_f64(Ctx &c, Hierarchy &h, const double *b, double *x, int nr) {
     if (h.prec == 64) {
-        vcycle_apply(c, h, b, x);
+        vcycle_apply(c, h, b, x, nr);
         return;
     }
-    int64_t n = h.lv[0].A.nrow;
+    int64_t n = h.lv[0].A.nrow * nr;
     cast_f64_f32(c, b, h.lv[0].b.as<float>(), n);
-    vcycle_apply(c, h, h.lv[0].b.p, h.lv[0].x.p);
+    vcycle_apply(c, h, h.lv[0].b.p, h.lv[0].x.p, nr);
     cast_f32_f64(c, h.lv[0].x.as<float>(), x, n);
 }
 
-// Algorithm 1 (block lower), and the block-diagonal / block-upper variants.
-static void precond_apply(mds_precond p, const double *r, double *z) {
+// Algorithm 1 (block lower), and the block-diagonal / block-upper variants,
+// on nr interleaved columns (entry (i, c) at i nr + c).
+void precond_apply(mds_precond p, const double *r, double *z, int nr) {
     Ctx &c = *p->ctx;
     mds_system s = p->sys;
     int64_t nm = s->n_m, nf = s->n_f;
     Hierarchy &HS = p->h[0];
     Hierarchy &HF = p->h[1];
+    hierarchy_reserve(c, HS, nr);
+    if (p->has_f) hierarchy_reserve(c, HF, nr);
+    if ((int64_t)p->tf_cap < (nm > nf ? nm : nf) * nr) {
+        int64_t mx = (nm > nf ? nm : nf) * nr;
+        p->tf64 = Buf(&c, sizeof(double) * (size_t)(mx > 0 ? mx : 1));
+        p->tf_cap = mx;
+    }
     const mds_csr &Afm = s->view[2], &Amf = s->view[1];
     int kind = p->o.kind;
+    const double *rm = r, *rf = r + nm * nr;
+    double *zm = z, *zf = z + nm * nr;
     if (kind == MDS_BLOCK_UPPER && p->has_f) {
         // z_f = Q_ff r_f; r_m <- r_m - A_mf z_f; z_m = Q_mm r_m
-        vcycle_f64(c, HF, r + nm, z + nm);
-        spmv_sub_f64(c, Amf, r, z + nm, p->tf64.as<double>());
-        vcycle_f64(c, HS, p->tf64.as<double>(), z);
+        vcycle_f64(c, HF, rf, zf, nr);
+        spmv_sub_f64(c, Amf, rm, zf, p->tf64.as<double>(), nr);
+        vcycle_f64(c, HS, p->tf64.as<double>(), zm, nr);
         return;
     }
     // step 1: z_m = Q_mm r_m
     if (HS.prec == 64) {
-        vcycle_apply(c, HS, r, z);
+        vcycle_apply(c, HS, rm, zm, nr);
     } else {
-        cast_f64_f32(c, r, HS.lv[0].b.as<float>(), nm);
-        vcycle_apply(c, HS, HS.lv[0].b.p, HS.lv[0].x.p);
-        cast_f32_f64(c, HS.lv[0].x.as<float>(), z, nm);
+        cast_f64_f32(c, rm, HS.lv[0].b.as<float>(), nm * nr);
+        vcycle_apply(c, HS, HS.lv[0].b.p, HS.lv[0].x.p, nr);
+        cast_f32_f64(c, HS.lv[0].x.as<float>(), zm, nm * nr);
     }
     if (!p->has_f) return;
     // step 2: r_f <- r_f - A_fm z_m (block lower only); step 3: z_f = Q_ff r_f
     if (HF.prec == 64) {
         if (kind == MDS_BLOCK_LOWER) {
-            spmv_sub_f64(c, Afm, r + nm, z, p->tf64.as<double>());
-            vcycle_apply(c, HF, p->tf64.as<double>(), z + nm);
+            spmv_sub_f64(c, Afm, rf, zm, p->tf64.as<double>(), nr);
+            vcycle_apply(c, HF, p->tf64.as<double>(), zf, nr);
         } else {
-            vcycle_apply(c, HF, r + nm, z + nm);
+            vcycle_apply(c, HF, rf, zf, nr);
         }
     } else {
         float *bf = HF.lv[0].b.as<float>();
         if (kind == MDS_BLOCK_LOWER)
-            spmv_sub_f64_xf(c, Afm, r + nm, HS.lv[0].x.as<float>(), bf);
+            spmv_sub_f64_xf(c, Afm, rf, HS.lv[0].x.as<float>(), bf, nr);
         else
-            cast_f64_f32(c, r + nm, bf, nf);
-        vcycle_apply(c, HF, HF.lv[0].b.p, HF.lv[0].x.p);
-        cast_f32_f64(c, HF.lv[0].x.as<float>(), z + nm, nf);
+            cast_f64_f32(c, rf, bf, nf * nr);
+        vcycle_apply(c, HF, HF.lv[0].b.p, HF.lv[0].x.p, nr);
+        cast_f32_f64(c, HF.lv[0].x.as<float>(), zf, nf * nr);
     }
 }
 
@@ -520,7 +554,7 @@ int mds_precond_apply(mds_ctx ctx, mds_precond p, const double *r, double *z) {
     if (!ctx || !p || !r || !z) return MDS_ERR_INVALID;
     Ctx *c = &ctx->c;
     API_BEGIN
-    precond_apply(p, r, z);
+    precond_apply(p, r, z, 1);
     API_END(c)
 }
 
@@ -528,7 +562,7 @@ int mds_vcycle(mds_ctx ctx, mds_precond p, int block, const double *b, double *x
     if (!ctx || !p || !b || !x || block < 0 || block > 1 || (block == 1 && !p->has_f)) return MDS_ERR_INVALID;
     Ctx *c = &ctx->c;
     API_BEGIN
-    vcycle_f64(*c, p->h[block], b, x);
+    vcycle_f64(*c, p->h[block], b, x, 1);
     API_END(c)
 }
 
@@ -548,6 +582,7 @@ int mds_solve_opts_default(mds_solve_opts *o) {
     o->max_iters = 1000;
     o->use_precond = 1;
     o->graphs = 1;
+    o->batched = 1;
     return MDS_OK;
 }
 
@@ -581,15 +616,48 @@ int mds_solve(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, do
         MDS_CUDA(cudaMemcpyAsync(xst.p, x, bytes, cudaMemcpyHostToDevice, c->stream));
         Xd = xst.as<double>();
     }
+    bool batched = sys->n_inst > 1 || (nrhs > 1 && o.batched);
+    if (batched) {
+        MDS_REQUIRE(o.krylov == MDS_KRYLOV_FGMRES, MDS_ERR_INVALID, "batched solves run FGMRES");
+        BatchPrecFn BM;
+        if (o.use_precond)
+            BM = [prec](const double *r, double *z, int nr) { precond_apply(prec, r, z, nr); };
+        else
+            BM = [c, n](const double *r, double *z, int nr) {
+                MDS_CUDA(cudaMemcpyAsync(z, r, sizeof(double) * (size_t)n * nr, cudaMemcpyDeviceToDevice, c->stream));
+            };
+        std::vector<int64_t> moff = sys->own.moff, foff = sys->own.foff;
+        if (moff.size() < 2) {
+            moff = {0, sys->n_m};
+            foff = {0, sys->n_f};
+        }
+        std::vector<KrylovResult> res;
+        fgmres_batched(*c, sys->view[4], BM, moff, foff, Bd, Xd, nrhs, o, res);
+        for (size_t q = 0; q < res.size(); q++) {
+            const KrylovResult &r = res[q];
+            if (stats) {
+                stats[q].iterations = r.iterations;
+                stats[q].restarts = r.restarts;
+                stats[q].status = r.status;
+                stats[q].relres_est = r.relres_est;
+                stats[q].relres_true = r.relres_true;
+            }
+            if (r.status < 0) {
+                if (worst >= 0) worst = r.status;
+            } else if (r.status > worst && worst >= 0) {
+                worst = r.status;
+            }
+        }
+    }
     PrecFn M;
     if (o.use_precond) {
-        M = [prec](const double *r, double *z) { precond_apply(prec, r, z); };
+        M = [prec](const double *r, double *z) { precond_apply(prec, r, z, 1); };
     } else {
         M = [c, n](const double *r, double *z) {
             MDS_CUDA(cudaMemcpyAsync(z, r, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, c->stream));
         };
     }
-    for (int k = 0; k < nrhs; k++) {
+    for (int k = 0; k < (batched ? 0 : nrhs); k++) {
         const double *bk = Bd + (size_t)k * n;
         double *xk = Xd + (size_t)k * n;
         KrylovResult r = o.krylov == MDS_KRYLOV_PCG ? pcg(*c, sys->view[4], M, bk, xk, n, o)
@@ -640,7 +708,7 @@ int mds_solve_noalloc(mds_ctx ctx, mds_system sys, mds_precond prec, const doubl
     FgmresWorkspace ws = fgmres_workspace_carve(noalloc_scratch(*c), n, o.restart);
     PrecFn M;
     if (o.use_precond)
-        M = [prec](const double *r, double *z) { precond_apply(prec, r, z); };
+        M = [prec](const double *r, double *z) { precond_apply(prec, r, z, 1); };
     else
         M = [c, n](const double *r, double *z) {
             MDS_CUDA(cudaMemcpyAsync(z, r, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, c->stream));

@@ -113,7 +113,8 @@ struct Ctx {
     bool custom_alloc = false;
     std::string last_error;
     int *d_err = nullptr;      // device error word
-    void *h_pin = nullptr;     // pinned host scratch (4 KB)
+    void *h_pin = nullptr;     // pinned host scratch (PIN_BYTES)
+    static constexpr size_t PIN_BYTES = 1 << 20;
     bool timing[MDS_KCLASS_COUNT] = {};
     std::vector<KTimerRec> evs[MDS_KCLASS_COUNT];
     size_t ev_used[MDS_KCLASS_COUNT] = {};
@@ -258,21 +259,26 @@ void fill_i32(Ctx &c, int32_t *p, int32_t v, int64_t n);
 void fill_f64(Ctx &c, double *p, double v, int64_t n);
 void cast_f64_f32(Ctx &c, const double *in, float *out, int64_t n);
 void cast_f32_f64(Ctx &c, const float *in, double *out, int64_t n);
-// y = A x (FP64 CSR)
-void spmv_f64(Ctx &c, const mds_csr &A, const double *x, double *y, int kclass);
+// y = A x (FP64 CSR), nr in {1, 2, 4, 8} interleaved columns
+void spmv_f64(Ctx &c, const mds_csr &A, const double *x, double *y, int kclass, int nr = 1);
 // out = r - A x with out in FP64 or FP32
-void spmv_sub_f64(Ctx &c, const mds_csr &A, const double *r, const double *x, double *out);
-void spmv_sub_f64_xf(Ctx &c, const mds_csr &A, const double *r, const float *x, float *out);
+void spmv_sub_f64(Ctx &c, const mds_csr &A, const double *r, const double *x, double *out, int nr = 1);
+void spmv_sub_f64_xf(Ctx &c, const mds_csr &A, const double *r, const float *x, float *out, int nr = 1);
 
 // ---- assembly (k_assemble.cu) ----
 struct SystemData {
     int64_t n_m = 0, n_f = 0;
     int nrhs = 1;
+    // packed instances: instance k owns matrix rows [moff[k], moff[k+1]) and
+    // fracture rows n_m + [foff[k], foff[k+1])
+    std::vector<int64_t> moff, foff;
     DCsr full;
     DCsr blk[4];
     Buf b;  // [nrhs][N]
 };
 void assemble_instance(Ctx &c, const mds_instance &inst, SystemData &out);
+// pack several assembled instances into one block-diagonal system
+void pack_instances(Ctx &c, std::vector<SystemData> &parts, SystemData &out);
 void split_blocks(Ctx &c, const mds_csr &full, int64_t n_m, DCsr blk[4]);
 void merge_blocks(Ctx &c, const mds_csr blk[4], int64_t n_m, int64_t n_f, DCsr &full);
 
@@ -310,6 +316,7 @@ struct Hierarchy {
     int prec = 64;    // vector precision: 64 or 32
     int smoother = 0;
     int sweeps = 1;
+    int nr_cap = 0;   // columns the level work vectors hold
 };
 
 void amg_setup(Ctx &c, const mds_csr &A, const mds_setup_opts &o, Hierarchy &h);
@@ -319,15 +326,21 @@ void level_storage(Ctx &c, Hierarchy &h, const mds_setup_opts &o);
 // ---- dense (k_dense.cu) ----
 // Cholesky of the n x n SPD matrix stored densely, then its inverse.
 void dense_spd_inverse(Ctx &c, const mds_csr &A, Buf &Ainv);
-void dense_gemv_f64(Ctx &c, const double *M, int64_t n, const double *x, double *y);
-void dense_gemv_f32(Ctx &c, const double *M, int64_t n, const float *x, float *y);
+// y = M x for nr in {1, 2, 4, 8} interleaved columns
+void dense_apply(Ctx &c, const double *M, int64_t n, int nr, const double *x, double *y);
+void dense_apply(Ctx &c, const double *M, int64_t n, int nr, const float *x, float *y);
 
 // ---- V-cycle (k_vcycle.cu) ----
-// x = V(b) on level 0 of h; b and x in the hierarchy's vector precision.
-void vcycle_apply(Ctx &c, Hierarchy &h, const void *b, void *x);
+// x = V(b) on level 0 of h for nr in {1, 2, 4, 8} interleaved columns; b and
+// x in the hierarchy's vector precision.
+void vcycle_apply(Ctx &c, Hierarchy &h, const void *b, void *x, int nr = 1);
+// grow the level work vectors to hold nr interleaved columns
+void hierarchy_reserve(Ctx &c, Hierarchy &h, int nr);
 
 // ---- Krylov (k_krylov.cu) ----
 struct KrylovWork;
+// z = M r on nr interleaved columns (api.cu)
+void precond_apply(mds_precond p, const double *r, double *z, int nr);
 }  // namespace mds
 
 // Handle structs (opaque in the C ABI).
@@ -339,6 +352,7 @@ struct mds_system_s {
     mds::Ctx *ctx = nullptr;
     int64_t n_m = 0, n_f = 0;
     int nrhs = 0;
+    int n_inst = 1;
     mds_csr view[5]{};       // 0..3 blocks, 4 full
     mds::SystemData own;     // owned storage (blocks borrowed for from_csr)
     const double *b = nullptr;
@@ -352,5 +366,6 @@ struct mds_precond_s {
     mds::Buf dk;
     mds::Hierarchy h[2];
     bool has_f = false;
-    mds::Buf t32, z32m, z32f, tf64;  // Algorithm 1 work vectors
+    mds::Buf tf64;            // Algorithm 1 work vector (interleaved columns)
+    int64_t tf_cap = 0;
 };

@@ -344,6 +344,80 @@ void merge_blocks(Ctx &c, const mds_csr blk[4], int64_t n_m, int64_t n_f, DCsr &
                full.rowp(), full.cols(), full.vals());
 }
 
+// ---------------------------------------------------------------- packing of instances
+
+// rows of one block of one instance into the packed block: row r goes to
+// row_off + r, its entries to nnz_off + ..., columns shifted by col_off
+__global__ void k_concat_rows(int64_t nrow, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                              const double *__restrict__ v, int64_t row_off, int64_t nnz_off, int64_t col_off,
+                              int32_t *__restrict__ rp_dst, int32_t *__restrict__ ci_dst, double *__restrict__ v_dst) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrow) return;
+    rp_dst[row_off + r] = (int32_t)(nnz_off + rp[r]);
+    for (int32_t p = rp[r]; p < rp[r + 1]; p++) {
+        ci_dst[nnz_off + p] = (int32_t)(ci[p] + col_off);
+        v_dst[nnz_off + p] = v[p];
+    }
+}
+
+// Block-diagonal packing: unknowns [m_0 .. m_{K-1}; f_0 .. f_{K-1}], so the
+// packed system keeps the 2x2 block structure of Eq. (4) and each diagonal
+// block is block diagonal over the instances.
+void pack_instances(Ctx &c, std::vector<SystemData> &parts, SystemData &out) {
+    const int K = (int)parts.size();
+    MDS_REQUIRE(K >= 1, MDS_ERR_INVALID, "no instances");
+    out.nrhs = parts[0].nrhs;
+    out.moff.assign(K + 1, 0);
+    out.foff.assign(K + 1, 0);
+    for (int k = 0; k < K; k++) {
+        MDS_REQUIRE(parts[k].nrhs == out.nrhs, MDS_ERR_INVALID, "instances of a batch need the same nrhs");
+        out.moff[k + 1] = out.moff[k] + parts[k].n_m;
+        out.foff[k + 1] = out.foff[k] + parts[k].n_f;
+    }
+    const int64_t NM = out.moff[K], NF = out.foff[K], N = NM + NF;
+    MDS_REQUIRE(N < INT32_MAX, MDS_ERR_INVALID, "packed batch exceeds int32 indices");
+    out.n_m = NM;
+    out.n_f = NF;
+    for (int q = 0; q < 4; q++) {
+        bool mrow = q < 2, mcol = q % 2 == 0;
+        int64_t nrow = mrow ? NM : NF, ncol = mcol ? NM : NF, nnz = 0;
+        for (int k = 0; k < K; k++) nnz += parts[k].blk[q].nnz;
+        MDS_REQUIRE(nnz < INT32_MAX, MDS_ERR_INVALID, "packed batch exceeds 2^31-1 nonzeros");
+        out.blk[q] = csr_alloc(c, nrow, ncol, nnz);
+        int64_t at = 0;
+        for (int k = 0; k < K; k++) {
+            const DCsr &B = parts[k].blk[q];
+            int64_t roff = mrow ? out.moff[k] : out.foff[k], coff = mcol ? out.moff[k] : out.foff[k];
+            if (B.nrow > 0)
+                MDS_LAUNCH(c, KC_NONE, 0, k_concat_rows, grid_for(B.nrow, 256), 256, 0, B.nrow, B.rowp(), B.cols(),
+                           B.vals(), roff, at, coff, out.blk[q].rowp(), out.blk[q].cols(), out.blk[q].vals());
+            at += B.nnz;
+        }
+        int32_t last = (int32_t)nnz;
+        std::memcpy(c.h_pin, &last, sizeof last);
+        MDS_CUDA(cudaMemcpyAsync(out.blk[q].rowp() + nrow, c.h_pin, sizeof last, cudaMemcpyHostToDevice, c.stream));
+        c.sync();
+    }
+    mds_csr views[4] = {out.blk[0].view(), out.blk[1].view(), out.blk[2].view(), out.blk[3].view()};
+    merge_blocks(c, views, NM, NF, out.full);
+    out.b = Buf(&c, sizeof(double) * (size_t)(N * out.nrhs));
+    for (int k = 0; k < K; k++) {
+        const SystemData &S = parts[k];
+        int64_t Nk = S.n_m + S.n_f;
+        for (int r = 0; r < out.nrhs; r++) {
+            const double *src = S.b.as<double>() + (int64_t)r * Nk;
+            double *dst = out.b.as<double>() + (int64_t)r * N;
+            if (S.n_m)
+                MDS_CUDA(cudaMemcpyAsync(dst + out.moff[k], src, sizeof(double) * (size_t)S.n_m,
+                                         cudaMemcpyDeviceToDevice, c.stream));
+            if (S.n_f)
+                MDS_CUDA(cudaMemcpyAsync(dst + NM + out.foff[k], src + S.n_m, sizeof(double) * (size_t)S.n_f,
+                                         cudaMemcpyDeviceToDevice, c.stream));
+        }
+    }
+    c.sync();
+}
+
 // ---------------------------------------------------------------- driver
 
 template <class T>
@@ -411,6 +485,8 @@ void assemble_instance(Ctx &c, const mds_instance &in, SystemData &out) {
     out.n_m = g.n_m;
     out.n_f = g.nf;
     out.nrhs = in.nrhs;
+    out.moff = {0, g.n_m};
+    out.foff = {0, g.nf};
     split_blocks(c, A.view(), g.n_m, out.blk);
     c.sync();  // staged host copies are released on return
 }

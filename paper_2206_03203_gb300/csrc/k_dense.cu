@@ -160,23 +160,48 @@ void dense_spd_inverse(Ctx &c, const mds_csr &A, Buf &Ainv) {
                Ainv.as<double>());
 }
 
-template <class XT>
-__global__ void k_gemv(const double *__restrict__ M, int64_t n, const XT *__restrict__ x, XT *__restrict__ y) {
+// y = M x for NR interleaved columns (entry (i, c) at i * NR + c); one warp
+// per row, FP64 accumulation.
+template <class XT, int NR>
+__global__ void k_dense_apply(const double *__restrict__ M, int64_t n, const XT *__restrict__ x, XT *__restrict__ y) {
     int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     int lane = threadIdx.x % 32;
     if (row >= n) return;
-    double s = 0.0;
-    for (int64_t k = lane; k < n; k += 32) s += M[row * n + k] * (double)x[k];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) y[row] = (XT)s;
+    double s[NR];
+#pragma unroll
+    for (int c = 0; c < NR; c++) s[c] = 0.0;
+    for (int64_t k = lane; k < n; k += 32) {
+        double m = M[row * n + k];
+#pragma unroll
+        for (int c = 0; c < NR; c++) s[c] += m * (double)x[k * NR + c];
+    }
+#pragma unroll
+    for (int c = 0; c < NR; c++)
+        for (int o = 16; o > 0; o >>= 1) s[c] += __shfl_down_sync(0xffffffffu, s[c], o);
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < NR; c++) y[row * NR + c] = (XT)s[c];
 }
 
-void dense_gemv_f64(Ctx &c, const double *M, int64_t n, const double *x, double *y) {
-    MDS_LAUNCH(c, KC_NONE, 8.0 * n * n + 16.0 * n, k_gemv<double>, grid_for(n * 32, 256), 256, 0, M, n, x, y);
+template <class XT>
+static void dense_apply_t(Ctx &c, const double *M, int64_t n, int nr, const XT *x, XT *y) {
+    double bytes = 8.0 * n * n + 2.0 * sizeof(XT) * n * nr;
+    unsigned g = grid_for(n * 32, 256);
+    switch (nr) {
+        case 1: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 1>), g, 256, 0, M, n, x, y); break;
+        case 2: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 2>), g, 256, 0, M, n, x, y); break;
+        case 4: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 4>), g, 256, 0, M, n, x, y); break;
+        case 8: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 8>), g, 256, 0, M, n, x, y); break;
+        default: throw Error(MDS_ERR_INVALID, "dense apply: column count must be 1, 2, 4 or 8");
+    }
 }
 
-void dense_gemv_f32(Ctx &c, const double *M, int64_t n, const float *x, float *y) {
-    MDS_LAUNCH(c, KC_NONE, 8.0 * n * n + 8.0 * n, k_gemv<float>, grid_for(n * 32, 256), 256, 0, M, n, x, y);
+void dense_apply(Ctx &c, const double *M, int64_t n, int nr, const double *x, double *y) {
+    dense_apply_t<double>(c, M, n, nr, x, y);
+}
+
+void dense_apply(Ctx &c, const double *M, int64_t n, int nr, const float *x, float *y) {
+    dense_apply_t<float>(c, M, n, nr, x, y);
 }
 
 }  // namespace mds

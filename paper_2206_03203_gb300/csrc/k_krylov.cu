@@ -4,6 +4,7 @@
 // right-preconditioned operator A B_L; Sec. 4 fixes x0 = 0 and a relative-
 // residual stopping rule.  All reductions are two-stage with a fixed order,
 // so results are run-to-run reproducible.
+#include <algorithm>
 #include <cmath>
 #include <functional>
 #include <memory>
@@ -552,6 +553,406 @@ double *noalloc_scratch(Ctx &c) {
         addr[c.device] = static_cast<double *>(p);
     }
     return addr[c.device];
+}
+
+}  // namespace mds
+
+// ================================================================ batched lockstep FGMRES
+//
+// P = K instances x NR columns independent problems on one packed system:
+// instance k owns the matrix rows [moff_k, moff_k+1) and the fracture rows
+// [NM + foff_k, NM + foff_k+1); vectors hold NR interleaved columns.  Every
+// problem runs its own right-preconditioned FGMRES(m) (own Krylov basis,
+// Hessenberg matrix, rotations, restarts and convergence); the SpMV, the
+// V-cycles and the Gram-Schmidt passes of all problems share one launch each,
+// so every matrix entry is read once per NR columns.  A problem whose
+// estimate has converged sits out (mask) until the common restart; its x is
+// updated with its own step count.
+
+namespace mds {
+
+struct Chunk {
+    int64_t b, e;  // row range
+    int32_t inst;
+};
+
+// partial[(q * nchunk + chunk) * NR + c] = sum over the chunk's rows of
+// V_q(i, c) W(i, c); row q == nq is W itself (squared norm).
+template <int NR>
+__global__ void __launch_bounds__(RED_BLOCK) k_bdot(const Chunk *__restrict__ ch, int nchunk, const double *__restrict__ V,
+                                                     int64_t ldq, int nq, const double *__restrict__ W,
+                                                     double *__restrict__ partial) {
+    __shared__ double ws[RED_BLOCK / 32][NR];
+    Chunk k = ch[blockIdx.x];
+    int q = blockIdx.y;
+    const double *v = q < nq ? V + (int64_t)q * ldq : W;
+    double s[NR];
+#pragma unroll
+    for (int c = 0; c < NR; c++) s[c] = 0.0;
+    for (int64_t i = k.b + threadIdx.x; i < k.e; i += blockDim.x)
+#pragma unroll
+        for (int c = 0; c < NR; c++) s[c] += v[i * NR + c] * W[i * NR + c];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < NR; c++) {
+        double t = s[c];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) ws[w][c] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < NR) {
+        double t = 0.0;
+        for (int k2 = 0; k2 < RED_BLOCK / 32; k2++) t += ws[k2][threadIdx.x];
+        partial[((int64_t)q * nchunk + blockIdx.x) * NR + threadIdx.x] = t;
+    }
+}
+
+// out[p * 32 + q] (+)= sum over instance k's chunks of partial[q][chunk][c],
+// p = k NR + c; one warp per (q, p), fixed order.
+__global__ void k_breduce(const double *__restrict__ partial, int nchunk, int nq, int NR,
+                          const int32_t *__restrict__ ioff, const int32_t *__restrict__ ichunk, int P,
+                          double *__restrict__ out, int accumulate) {
+    int q = blockIdx.y;
+    int p = blockIdx.x;
+    if (p >= P || q >= nq) return;
+    int k = p / NR, c = p % NR;
+    double s = 0.0;
+    for (int t = ioff[k] + threadIdx.x; t < ioff[k + 1]; t += 32)
+        s += partial[((int64_t)q * nchunk + ichunk[t]) * NR + c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) out[(int64_t)p * 32 + q] = accumulate ? out[(int64_t)p * 32 + q] + s : s;
+}
+
+// W(i, c) += SIGN sum_q coef[p][q] V_q(i, c) over one chunk per block;
+// optional partials of W(i, c)^2 as partial[chunk][c] (q = 0 layout).
+template <int NR, int SIGN>
+__global__ void __launch_bounds__(RED_BLOCK) k_bmaxpy(const Chunk *__restrict__ ch, const double *__restrict__ V,
+                                                       int64_t ldq, int nq, const double *__restrict__ coef,
+                                                       double *__restrict__ W, double *__restrict__ partial) {
+    __shared__ double cs[NR][32];
+    __shared__ double ws[RED_BLOCK / 32][NR];
+    Chunk k = ch[blockIdx.x];
+    for (int t = threadIdx.x; t < NR * 32; t += blockDim.x) {
+        int c = t / 32, q = t % 32;
+        cs[c][q] = q < nq ? coef[((int64_t)k.inst * NR + c) * 32 + q] : 0.0;
+    }
+    __syncthreads();
+    double nrm[NR];
+#pragma unroll
+    for (int c = 0; c < NR; c++) nrm[c] = 0.0;
+    for (int64_t i = k.b + threadIdx.x; i < k.e; i += blockDim.x) {
+        double s[NR];
+#pragma unroll
+        for (int c = 0; c < NR; c++) s[c] = 0.0;
+        for (int q = 0; q < nq; q++) {
+            const double *v = V + (int64_t)q * ldq + i * NR;
+#pragma unroll
+            for (int c = 0; c < NR; c++) s[c] += cs[c][q] * v[c];
+        }
+#pragma unroll
+        for (int c = 0; c < NR; c++) {
+            double x = SIGN > 0 ? W[i * NR + c] + s[c] : W[i * NR + c] - s[c];
+            W[i * NR + c] = x;
+            nrm[c] += x * x;
+        }
+    }
+    if (partial) {
+        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+        for (int c = 0; c < NR; c++) {
+            double t = nrm[c];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0) ws[w][c] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x < NR) {
+            double t = 0.0;
+            for (int k2 = 0; k2 < RED_BLOCK / 32; k2++) t += ws[k2][threadIdx.x];
+            partial[(int64_t)blockIdx.x * NR + threadIdx.x] = t;
+        }
+    }
+}
+
+// W(i, c) *= f[p]  (f = sc[p * 8 + slot])
+template <int NR>
+__global__ void k_bscale(const Chunk *__restrict__ ch, double *__restrict__ W, const double *__restrict__ sc, int slot) {
+    Chunk k = ch[blockIdx.x];
+    for (int64_t i = k.b + threadIdx.x; i < k.e; i += blockDim.x)
+#pragma unroll
+        for (int c = 0; c < NR; c++) W[i * NR + c] *= sc[((int64_t)k.inst * NR + c) * 8 + slot];
+}
+
+// per problem: beta = sqrt(nsq), g = (beta, 0, ...), sc[1] = 1/beta
+__global__ void k_bcycle_start(int P, const double *__restrict__ nsq, int m, double *__restrict__ g,
+                               double *__restrict__ sc) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    double beta = sqrt(nsq[(int64_t)p * 32]);
+    sc[p * 8 + 0] = beta;
+    sc[p * 8 + 1] = beta > 0.0 ? 1.0 / beta : 0.0;
+    g[p * 32] = beta;
+    for (int q = 1; q <= m; q++) g[p * 32 + q] = 0.0;
+}
+
+// per active problem: Hessenberg column j from h1 + h2 and ||w||, rotations,
+// g; sc[2] = |g_{j+1}|, sc[3] = 1/H[j+1][j], sc[4] = breakdown (1 lucky, 2 bad)
+__global__ void k_barnoldi(int P, int j, int m, const int8_t *__restrict__ active, double *__restrict__ H,
+                           const double *__restrict__ h1, const double *__restrict__ h2,
+                           const double *__restrict__ nsq, double *__restrict__ cs, double *__restrict__ sn,
+                           double *__restrict__ g, double *__restrict__ sc) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P || !active[p]) return;
+    double *Hp = H + (int64_t)p * (m + 1) * m;
+    const double *a1 = h1 + (int64_t)p * 32, *a2 = h2 + (int64_t)p * 32;
+    double *c_ = cs + (int64_t)p * 32, *s_ = sn + (int64_t)p * 32, *gp = g + (int64_t)p * 32, *scp = sc + p * 8;
+    for (int q = 0; q <= j; q++) Hp[q * m + j] = a1[q] + a2[q];
+    double hn = sqrt(nsq[(int64_t)p * 32]);
+    Hp[(j + 1) * m + j] = hn;
+    for (int q = 0; q < j; q++) {
+        double a = Hp[q * m + j], c = Hp[(q + 1) * m + j];
+        Hp[q * m + j] = c_[q] * a + s_[q] * c;
+        Hp[(q + 1) * m + j] = -s_[q] * a + c_[q] * c;
+    }
+    double a = Hp[j * m + j], c = Hp[(j + 1) * m + j];
+    double rr = sqrt(a * a + c * c);
+    c_[j] = rr == 0.0 ? 1.0 : a / rr;
+    s_[j] = rr == 0.0 ? 0.0 : c / rr;
+    Hp[j * m + j] = rr;
+    Hp[(j + 1) * m + j] = 0.0;
+    gp[j + 1] = -s_[j] * gp[j];
+    gp[j] = c_[j] * gp[j];
+    scp[2] = fabs(gp[j + 1]);
+    bool bad = !(hn > 0.0) || !isfinite(hn) || !isfinite(rr);
+    scp[3] = bad ? 0.0 : 1.0 / hn;
+    scp[4] = !isfinite(hn) || !isfinite(rr) ? 2.0 : (hn == 0.0 ? 1.0 : 0.0);
+}
+
+// per problem: solve H y = g with its own step count kdone[p]; y zero beyond
+__global__ void k_bbacksolve(int P, const int32_t *__restrict__ kdone, int m, const double *__restrict__ H,
+                             const double *__restrict__ g, double *__restrict__ y) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    int k = kdone[p];
+    const double *Hp = H + (int64_t)p * (m + 1) * m;
+    const double *gp = g + (int64_t)p * 32;
+    double *yp = y + (int64_t)p * 32;
+    for (int q = 0; q < 32; q++) yp[q] = 0.0;
+    for (int q = k - 1; q >= 0; q--) {
+        double s = gp[q];
+        for (int t = q + 1; t < k; t++) s -= Hp[q * m + t] * yp[t];
+        yp[q] = Hp[q * m + q] == 0.0 ? 0.0 : s / Hp[q * m + q];
+    }
+}
+
+// interleave NR columns of a column-major [ncol][N] array / scatter back
+template <int NR>
+__global__ void k_to_interleaved(int64_t N, const double *__restrict__ src, int c0, double *__restrict__ dst) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N * NR; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = src[(int64_t)(c0 + e % NR) * N + e / NR];
+}
+template <int NR>
+__global__ void k_from_interleaved(int64_t N, const double *__restrict__ src, int c0, double *__restrict__ dst) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N * NR; e += (int64_t)gridDim.x * blockDim.x)
+        dst[(int64_t)(c0 + e % NR) * N + e / NR] = src[e];
+}
+
+template <int NR>
+static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const std::vector<int64_t> &moff,
+                         const std::vector<int64_t> &foff, const double *Bcol, double *Xcol, int c0,
+                         const mds_solve_opts &o, std::vector<KrylovResult> &out) {
+    const int K = (int)moff.size() - 1;
+    const int64_t NM = moff[K], N = NM + foff[K];
+    const int P = K * NR;
+    const int m = o.restart < 1 ? 1 : (o.restart > QMAX - 1 ? QMAX - 1 : o.restart);
+    // chunks of at most CH rows, never crossing an instance's segment
+    int64_t CH = std::max<int64_t>(1024, std::min<int64_t>(16384, N / (4 * 152) + 1));
+    std::vector<Chunk> chunks;
+    std::vector<std::vector<int32_t>> per(K);
+    auto add = [&](int64_t b, int64_t e, int k) {
+        for (int64_t s = b; s < e; s += CH) {
+            per[k].push_back((int32_t)chunks.size());
+            chunks.push_back(Chunk{s, std::min(e, s + CH), k});
+        }
+    };
+    for (int k = 0; k < K; k++) add(moff[k], moff[k + 1], k);
+    for (int k = 0; k < K; k++) add(NM + foff[k], NM + foff[k + 1], k);
+    std::vector<int32_t> ioff(K + 1, 0), ilist;
+    for (int k = 0; k < K; k++) {
+        ioff[k + 1] = ioff[k] + (int32_t)per[k].size();
+        ilist.insert(ilist.end(), per[k].begin(), per[k].end());
+    }
+    const int nch = (int)chunks.size();
+    Buf dch(&c, sizeof(Chunk) * chunks.size()), dioff(&c, sizeof(int32_t) * ioff.size()),
+        dil(&c, sizeof(int32_t) * (ilist.size() ? ilist.size() : 1));
+    MDS_CUDA(cudaMemcpyAsync(dch.p, chunks.data(), sizeof(Chunk) * chunks.size(), cudaMemcpyHostToDevice, c.stream));
+    MDS_CUDA(cudaMemcpyAsync(dioff.p, ioff.data(), sizeof(int32_t) * ioff.size(), cudaMemcpyHostToDevice, c.stream));
+    if (ilist.size())
+        MDS_CUDA(cudaMemcpyAsync(dil.p, ilist.data(), sizeof(int32_t) * ilist.size(), cudaMemcpyHostToDevice, c.stream));
+    const Chunk *CHp = dch.as<Chunk>();
+    const int32_t *IO = dioff.as<int32_t>(), *IL = dil.as<int32_t>();
+
+    const int64_t ld = (N + 63) / 64 * 64, ldq = ld * NR;
+    Buf Bi(&c, sizeof(double) * (size_t)(N * NR)), Xi(&c, sizeof(double) * (size_t)(N * NR));
+    Buf V(&c, sizeof(double) * (size_t)(m + 1) * ldq), Z(&c, sizeof(double) * (size_t)m * ldq);
+    Buf H(&c, sizeof(double) * (size_t)P * (m + 1) * m);
+    Buf part(&c, sizeof(double) * (size_t)(QMAX * nch * NR));
+    // per-problem arrays with stride 32: cs, sn, g, y, h1, h2, nsq; scalars stride 8
+    Buf pa(&c, sizeof(double) * (size_t)P * 32 * 7), psc(&c, sizeof(double) * (size_t)P * 8);
+    Buf act(&c, (size_t)P), kd(&c, sizeof(int32_t) * (size_t)P);
+    double *cs = pa.as<double>(), *sn = cs + (size_t)P * 32, *g = sn + (size_t)P * 32, *y = g + (size_t)P * 32,
+           *h1 = y + (size_t)P * 32, *h2 = h1 + (size_t)P * 32, *nsq = h2 + (size_t)P * 32;
+    double *sc = psc.as<double>();
+    double *Vp = V.as<double>(), *Zp = Z.as<double>(), *PT = part.as<double>();
+    MDS_CUDA(cudaMemsetAsync(pa.p, 0, pa.bytes, c.stream));
+    MDS_CUDA(cudaMemsetAsync(psc.p, 0, psc.bytes, c.stream));
+    unsigned eg = red_grid(N * NR);
+    MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, (k_to_interleaved<NR>), eg, RED_BLOCK, 0, N, Bcol, c0, Bi.as<double>());
+    MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, (k_to_interleaved<NR>), eg, RED_BLOCK, 0, N, Xcol, c0, Xi.as<double>());
+    dim3 pgrid((unsigned)P, 1);
+    // per-problem squared norms of a vector into nsq[p * 32]
+    auto norms = [&](const double *w) {
+        MDS_LAUNCH(c, KC_NONE, 8.0 * N * NR, (k_bdot<NR>), dim3(nch, 1), RED_BLOCK, 0, CHp, nch, Vp, ldq, 0, w, PT);
+        MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, 1), 32, 0, PT, nch, 1, NR, IO, IL, P, nsq, 0);
+    };
+    std::vector<double> host(P * 8), bn(P);
+    auto fetch = [&](const double *d, int stride, int slot) {
+        MDS_CUDA(cudaMemcpyAsync(c.h_pin, d, sizeof(double) * (size_t)P * stride, cudaMemcpyDeviceToHost, c.stream));
+        c.sync();
+        const double *hp = static_cast<const double *>(c.h_pin);
+        std::vector<double> v(P);
+        for (int p = 0; p < P; p++) v[p] = hp[(size_t)p * stride + slot];
+        return v;
+    };
+    MDS_REQUIRE((size_t)P * 32 * sizeof(double) <= Ctx::PIN_BYTES, MDS_ERR_INVALID,
+                "too many batched problems (instances x columns > 4096)");
+    norms(Bi.as<double>());
+    {
+        std::vector<double> b2 = fetch(nsq, 32, 0);
+        for (int p = 0; p < P; p++) {
+            bn[p] = std::sqrt(b2[p]);
+            if (!std::isfinite(bn[p])) out[p].status = MDS_ERR_NONFINITE;
+            if (bn[p] == 0.0) bn[p] = 1.0;
+        }
+    }
+    std::vector<int> it(P, 0), rs(P, 0), done(P, 0);
+    std::vector<double> est(P, 0.0);
+    for (int p = 0; p < P; p++)
+        if (out[p].status == MDS_ERR_NONFINITE) done[p] = 1;
+    std::vector<int8_t> hact(P);
+    std::vector<int32_t> hkd(P);
+    for (;;) {
+        spmv_sub_f64(c, A, Bi.as<double>(), Xi.as<double>(), Vp, NR);  // V0 = B - A X
+        norms(Vp);
+        std::vector<double> r2 = fetch(nsq, 32, 0);
+        bool any = false;
+        for (int p = 0; p < P; p++) {
+            if (done[p]) continue;
+            est[p] = std::sqrt(r2[p]) / bn[p];
+            if (!std::isfinite(est[p])) {
+                out[p].status = MDS_ERR_NONFINITE;
+                done[p] = 1;
+            } else if (est[p] <= o.rtol) {
+                out[p].status = MDS_OK;
+                done[p] = 1;
+            } else if (it[p] >= o.max_iters) {
+                out[p].status = MDS_WARN_NOT_CONVERGED;
+                done[p] = 1;
+            } else {
+                any = true;
+            }
+        }
+        if (!any) break;
+        for (int p = 0; p < P; p++) {
+            hact[p] = done[p] ? 0 : 1;
+            hkd[p] = 0;
+        }
+        MDS_LAUNCH(c, KC_NONE, 0, k_bcycle_start, grid_for(P, 128), 128, 0, P, nsq, m, g, sc);
+        MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, nch, RED_BLOCK, 0, CHp, Vp, sc, 1);
+        for (int j = 0; j < m; j++) {
+            std::memcpy(c.h_pin, hact.data(), (size_t)P);
+            MDS_CUDA(cudaMemcpyAsync(act.p, c.h_pin, (size_t)P, cudaMemcpyHostToDevice, c.stream));
+            double *vj = Vp + (size_t)j * ldq, *zj = Zp + (size_t)j * ldq, *w = Vp + (size_t)(j + 1) * ldq;
+            M(vj, zj, NR);
+            spmv_f64(c, A, zj, w, KC_SPMV, NR);
+            int nq = j + 1;
+            double fl = 2.0 * (double)N * NR * nq;
+            // CGS2 for every problem
+            for (int pass = 0; pass < 2; pass++) {
+                double *hh = pass == 0 ? h1 : h2;
+                MDS_LAUNCH_F(c, KC_GS_DOT, 8.0 * N * NR * (nq + 1), fl, (k_bdot<NR>), dim3(nch, nq), RED_BLOCK, 0,
+                             CHp, nch, Vp, ldq, nq, w, PT);
+                MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, nq), 32, 0, PT, nch, nq, NR, IO, IL, P, hh, 0);
+                MDS_LAUNCH_F(c, KC_GS_AXPY, 8.0 * N * NR * (nq + 2), fl, (k_bmaxpy<NR, -1>), nch, RED_BLOCK, 0, CHp,
+                             Vp, ldq, nq, hh, w, pass == 1 ? PT : nullptr);
+            }
+            MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, 1), 32, 0, PT, nch, 1, NR, IO, IL, P, nsq, 0);
+            MDS_LAUNCH(c, KC_NONE, 0, k_barnoldi, grid_for(P, 128), 128, 0, P, j, m, act.as<int8_t>(), H.as<double>(),
+                       h1, h2, nsq, cs, sn, g, sc);
+            MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, nch, RED_BLOCK, 0, CHp, w, sc, 3);
+            MDS_CUDA(cudaMemcpyAsync(c.h_pin, sc, sizeof(double) * (size_t)P * 8, cudaMemcpyDeviceToHost, c.stream));
+            c.sync();
+            const double *hp = static_cast<const double *>(c.h_pin);
+            bool live = false;
+            for (int p = 0; p < P; p++) {
+                if (!hact[p]) continue;
+                it[p]++;
+                hkd[p] = j + 1;
+                est[p] = hp[p * 8 + 2] / bn[p];
+                bool bad = hp[p * 8 + 4] == 2.0 || !std::isfinite(est[p]);
+                if (bad) {
+                    out[p].status = MDS_ERR_BREAKDOWN;
+                    done[p] = 1;
+                    hact[p] = 0;
+                    hkd[p] = 0;  // keep x as it was at the cycle start
+                } else if (est[p] <= o.rtol || it[p] >= o.max_iters || hp[p * 8 + 4] == 1.0) {
+                    hact[p] = 0;
+                }
+                live = live || hact[p];
+            }
+            if (!live) break;
+        }
+        std::memcpy(c.h_pin, hkd.data(), sizeof(int32_t) * (size_t)P);
+        MDS_CUDA(cudaMemcpyAsync(kd.p, c.h_pin, sizeof(int32_t) * (size_t)P, cudaMemcpyHostToDevice, c.stream));
+        MDS_LAUNCH(c, KC_NONE, 0, k_bbacksolve, grid_for(P, 128), 128, 0, P, kd.as<int32_t>(), m, H.as<double>(), g, y);
+        MDS_LAUNCH(c, KC_NONE, 8.0 * N * NR * (m + 2), (k_bmaxpy<NR, 1>), nch, RED_BLOCK, 0, CHp, Zp, ldq, m, y,
+                   Xi.as<double>(), nullptr);
+        for (int p = 0; p < P; p++)
+            if (hkd[p] > 0) rs[p]++;
+    }
+    // true residuals at exit
+    spmv_sub_f64(c, A, Bi.as<double>(), Xi.as<double>(), Vp, NR);
+    norms(Vp);
+    std::vector<double> r2 = fetch(nsq, 32, 0);
+    for (int p = 0; p < P; p++) {
+        out[p].iterations = it[p];
+        out[p].restarts = rs[p];
+        out[p].relres_est = est[p];
+        out[p].relres_true = std::sqrt(r2[p]) / bn[p];
+    }
+    MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, (k_from_interleaved<NR>), eg, RED_BLOCK, 0, N, Xi.as<double>(), c0, Xcol);
+    c.sync();
+}
+
+void fgmres_batched(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const std::vector<int64_t> &moff,
+                    const std::vector<int64_t> &foff, const double *B, double *X, int nrhs, const mds_solve_opts &o,
+                    std::vector<KrylovResult> &res) {
+    const int K = (int)moff.size() - 1;
+    res.assign((size_t)K * nrhs, KrylovResult());
+    int c0 = 0;
+    while (c0 < nrhs) {
+        int left = nrhs - c0;
+        int NR = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        std::vector<KrylovResult> part((size_t)K * NR);
+        switch (NR) {
+            case 8: fgmres_group<8>(c, A, M, moff, foff, B, X, c0, o, part); break;
+            case 4: fgmres_group<4>(c, A, M, moff, foff, B, X, c0, o, part); break;
+            case 2: fgmres_group<2>(c, A, M, moff, foff, B, X, c0, o, part); break;
+            default: fgmres_group<1>(c, A, M, moff, foff, B, X, c0, o, part); break;
+        }
+        for (int k = 0; k < K; k++)
+            for (int cc = 0; cc < NR; cc++) res[(size_t)k * nrhs + c0 + cc] = part[(size_t)k * NR + cc];
+        c0 += NR;
+    }
 }
 
 }  // namespace mds

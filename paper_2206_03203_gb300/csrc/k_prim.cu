@@ -135,40 +135,51 @@ void cast_f32_f64(Ctx &c, const float *in, double *out, int64_t n) {
 
 // ---------------------------------------------------------------- SpMV
 
-template <int G, class XT, class OT, int MODE>
+template <int G, class XT, class OT, int MODE, int NR>
 static void spmv_launch(Ctx &c, const mds_csr &A, const XT *x, const double *r, OT *y, int kclass) {
     const int block = 256;
     unsigned grid = grid_for(A.nrow * G, block);
-    double bytes = 12.0 * (double)A.nnz + 4.0 * (double)(A.nrow + 1) + sizeof(XT) * (double)A.ncol +
-                   sizeof(OT) * (double)A.nrow + (MODE == 1 ? 8.0 * A.nrow : 0.0);
-    MDS_LAUNCH_F(c, kclass, bytes, 2.0 * A.nnz, (k_spmv_csr<G, double, XT, OT, MODE>), grid, block, 0, A.nrow, A.row_ptr,
-               A.col, A.val, x, r, y);
+    double bytes = 12.0 * (double)A.nnz + 4.0 * (double)(A.nrow + 1) +
+                   NR * (sizeof(XT) * (double)A.ncol + sizeof(OT) * (double)A.nrow + (MODE == 1 ? 8.0 * A.nrow : 0.0));
+    MDS_LAUNCH_F(c, kclass, bytes, 2.0 * NR * A.nnz, (k_spmv_csr<G, double, XT, OT, MODE, NR>), grid, block, 0, A.nrow,
+                 A.row_ptr, A.col, A.val, x, r, y);
+}
+
+template <int G, class XT, class OT, int MODE>
+static void spmv_nr(Ctx &c, const mds_csr &A, const XT *x, const double *r, OT *y, int kclass, int nr) {
+    switch (nr) {
+        case 1: spmv_launch<G, XT, OT, MODE, 1>(c, A, x, r, y, kclass); break;
+        case 2: spmv_launch<G, XT, OT, MODE, 2>(c, A, x, r, y, kclass); break;
+        case 4: spmv_launch<G, XT, OT, MODE, 4>(c, A, x, r, y, kclass); break;
+        case 8: spmv_launch<G, XT, OT, MODE, 8>(c, A, x, r, y, kclass); break;
+        default: throw Error(MDS_ERR_INVALID, "SpMV column count must be 1, 2, 4 or 8");
+    }
 }
 
 template <class XT, class OT, int MODE>
-static void spmv_dispatch(Ctx &c, const mds_csr &A, const XT *x, const double *r, OT *y, int kclass) {
+static void spmv_dispatch(Ctx &c, const mds_csr &A, const XT *x, const double *r, OT *y, int kclass, int nr) {
     if (A.nrow <= 0) return;
     double avg = A.nrow ? (double)A.nnz / (double)A.nrow : 0.0;
     if (avg <= 4.0)
-        spmv_launch<2, XT, OT, MODE>(c, A, x, r, y, kclass);
+        spmv_nr<2, XT, OT, MODE>(c, A, x, r, y, kclass, nr);
     else if (avg <= 10.0)
-        spmv_launch<4, XT, OT, MODE>(c, A, x, r, y, kclass);
+        spmv_nr<4, XT, OT, MODE>(c, A, x, r, y, kclass, nr);
     else if (avg <= 24.0)
-        spmv_launch<8, XT, OT, MODE>(c, A, x, r, y, kclass);
+        spmv_nr<8, XT, OT, MODE>(c, A, x, r, y, kclass, nr);
     else
-        spmv_launch<32, XT, OT, MODE>(c, A, x, r, y, kclass);
+        spmv_nr<32, XT, OT, MODE>(c, A, x, r, y, kclass, nr);
 }
 
-void spmv_f64(Ctx &c, const mds_csr &A, const double *x, double *y, int kclass) {
-    spmv_dispatch<double, double, 0>(c, A, x, nullptr, y, kclass);
+void spmv_f64(Ctx &c, const mds_csr &A, const double *x, double *y, int kclass, int nr) {
+    spmv_dispatch<double, double, 0>(c, A, x, nullptr, y, kclass, nr);
 }
 
-void spmv_sub_f64(Ctx &c, const mds_csr &A, const double *r, const double *x, double *out) {
-    spmv_dispatch<double, double, 1>(c, A, x, r, out, KC_NONE);
+void spmv_sub_f64(Ctx &c, const mds_csr &A, const double *r, const double *x, double *out, int nr) {
+    spmv_dispatch<double, double, 1>(c, A, x, r, out, KC_NONE, nr);
 }
 
-void spmv_sub_f64_xf(Ctx &c, const mds_csr &A, const double *r, const float *x, float *out) {
-    spmv_dispatch<float, float, 1>(c, A, x, r, out, KC_NONE);
+void spmv_sub_f64_xf(Ctx &c, const mds_csr &A, const double *r, const float *x, float *out, int nr) {
+    spmv_dispatch<float, float, 1>(c, A, x, r, out, KC_NONE, nr);
 }
 
 }  // namespace mds

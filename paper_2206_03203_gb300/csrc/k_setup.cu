@@ -520,13 +520,9 @@ void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h)
         else
             MDS_LAUNCH(c, KC_NONE, 0, k_l1<float>, gr, 256, 0, n, L.A.rowp(), L.A.cols(), L.A.vals(),
                        L.l1.as<double>(), L.dinv.as<float>());
-        L.b = Buf(&c, nb);
-        L.x = Buf(&c, nb);
-        L.r = Buf(&c, nb);
-        L.y = Buf(&c, nb);
-        L.t = Buf(&c, nb);
-        if (h.smoother == MDS_SMOOTHER_CHEBYSHEV) L.d = Buf(&c, nb);
     }
+    h.nr_cap = 0;
+    hierarchy_reserve(c, h, 1);
     if (h.dense) {
         Level &L = h.lv.back();
         h.nd = L.A.nrow;

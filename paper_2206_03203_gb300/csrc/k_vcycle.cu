@@ -45,8 +45,6 @@ template <class VT> struct LvlMat {
     const float *rscale;       // row scales (NULL: unscaled)
 };
 
-// Sum over the nonzeros of one row of a_ij * f(j): CSR with G lanes per row
-// (lane-partial sums), or SELL with one thread per row (G == 0).
 // Matrix entries are streamed once per launch: load them evict-first so the
 // L1/L2 capacity stays with the gathered vectors.
 template <class T> __device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
@@ -59,13 +57,59 @@ template <> __device__ __forceinline__ __half ld_stream(const __half *p) {
     return __ushort_as_half(u);
 }
 
-template <int G, class VT, class XT, class F>
-__device__ __forceinline__ XT row_sum(const LvlMat<VT> &A, int64_t row, int lane, F f) {
-    XT s = 0;
+// NR right-hand sides are stored interleaved: entry (i, c) at i * NR + c, so
+// one matrix entry multiplies NR contiguous vector entries (one vector load).
+template <class XT, int NR> struct alignas(sizeof(XT) * NR >= 16 ? 16 : sizeof(XT) * NR) Vec {
+    XT v[NR];
+};
+template <class XT, int NR> __device__ __forceinline__ Vec<XT, NR> ldv(const XT *p, int64_t j) {
+    return reinterpret_cast<const Vec<XT, NR> *>(p)[j];
+}
+template <class XT, int NR> __device__ __forceinline__ void stv(XT *p, int64_t j, const Vec<XT, NR> &x) {
+    reinterpret_cast<Vec<XT, NR> *>(p)[j] = x;
+}
+
+enum { VK_RESID0 = 0, VK_POST = 1, VK_RESID = 2, VK_SMOOTH = 3 };
+
+// Neighbour values each kernel multiplies by a_ij (NR columns at once).
+template <class XT, int NR, int K> struct Nb {
+    const XT *dinv, *b, *xin, *xc;
+    const int32_t *agg;
+    __device__ __forceinline__ Vec<XT, NR> operator()(int32_t j) const {
+        Vec<XT, NR> y;
+        if (K == VK_RESID0 || K == VK_POST) {
+            XT d = __ldg(dinv + j);
+            Vec<XT, NR> bj = ldv<XT, NR>(b, j);
+#pragma unroll
+            for (int c = 0; c < NR; c++) y.v[c] = d * bj.v[c];
+            if (K == VK_POST && agg) {
+                int32_t a = __ldg(agg + j);
+                if (a >= 0) {
+                    Vec<XT, NR> xa = ldv<XT, NR>(xc, a);
+#pragma unroll
+                    for (int c = 0; c < NR; c++) y.v[c] += xa.v[c];
+                }
+            }
+        } else {
+            y = ldv<XT, NR>(xin, j);
+        }
+        return y;
+    }
+};
+
+// Per-row sums over the nonzeros: CSR with G lanes per row (lane-partial
+// sums), or SELL with one thread per row (G == 0).
+template <int G, class VT, class XT, int NR, class F>
+__device__ __forceinline__ void row_sum(const LvlMat<VT> &A, int64_t row, int lane, F f, XT (&s)[NR]) {
     if constexpr (G > 0) {
         int32_t p0 = A.rp[row], p1 = A.rp[row + 1];
 #pragma unroll 4
-        for (int32_t p = p0 + lane; p < p1; p += G) s += cvt<XT>(ld_stream(A.v + p)) * f(ld_stream(A.ci + p));
+        for (int32_t p = p0 + lane; p < p1; p += G) {
+            XT a = cvt<XT>(ld_stream(A.v + p));
+            Vec<XT, NR> y = f(ld_stream(A.ci + p));
+#pragma unroll
+            for (int c = 0; c < NR; c++) s[c] += a * y.v[c];
+        }
     } else {
         int64_t sl = row / A.C;
         int r = (int)(row - sl * A.C);
@@ -73,9 +117,13 @@ __device__ __forceinline__ XT row_sum(const LvlMat<VT> &A, int64_t row, int lane
         const VT *v = A.v + off + r;
         const int32_t *cc = A.sc + off + r;
 #pragma unroll 8
-        for (int32_t k = 0; k < len; k++) s += cvt<XT>(ld_stream(v + k * A.C)) * f(ld_stream(cc + k * A.C));
+        for (int32_t k = 0; k < len; k++) {
+            XT a = cvt<XT>(ld_stream(v + k * A.C));
+            Vec<XT, NR> y = f(ld_stream(cc + k * A.C));
+#pragma unroll
+            for (int c = 0; c < NR; c++) s[c] += a * y.v[c];
+        }
     }
-    return s;
 }
 
 template <int G, class XT> __device__ __forceinline__ XT lane_reduce(XT s) {
@@ -97,119 +145,110 @@ template <int G> __device__ __forceinline__ void row_of(int64_t &row, int &lane)
     }
 }
 
-enum { VK_RESID0 = 0, VK_POST = 1, VK_RESID = 2, VK_SMOOTH = 3 };
-
-// Functors giving the neighbour value each kernel multiplies by a_ij.
-template <class XT> struct NbD1b {  // D1^-1 b
-    const XT *dinv, *b;
-    __device__ XT operator()(int32_t j) const { return __ldg(dinv + j) * __ldg(b + j); }
-};
-template <class XT> struct NbPost {  // D1^-1 b + P x_c
-    const XT *dinv, *b, *xc;
-    const int32_t *agg;
-    __device__ XT operator()(int32_t j) const {
-        XT y = __ldg(dinv + j) * __ldg(b + j);
-        if (agg) {
-            int32_t a = __ldg(agg + j);
-            if (a >= 0) y += __ldg(xc + a);
-        }
-        return y;
-    }
-};
-template <class XT> struct NbStored {  // a stored vector
-    const XT *x;
-    __device__ XT operator()(int32_t j) const { return __ldg(x + j); }
-};
-
 // VK_RESID0: r = b - A (D1^-1 b)
 // VK_POST:   x = y + D1^-1 (b - A y),  y = D1^-1 b + P x_c   (formed per neighbour)
 // VK_RESID:  r = b - A x
 // VK_SMOOTH: x = y + D1^-1 (b - A y)                       (y stored)
-template <int G, class VT, class XT, int K>
+template <int G, class VT, class XT, int K, int NR>
 __global__ void __launch_bounds__(256) k_level(LvlMat<VT> A, const XT *__restrict__ dinv, const XT *__restrict__ b,
                                                const XT *__restrict__ xin, const int32_t *__restrict__ agg,
                                                const XT *__restrict__ xc, XT *__restrict__ out) {
     int64_t row;
     int lane;
     row_of<G>(row, lane);
-    XT s = 0;
+    XT s[NR];
+#pragma unroll
+    for (int c = 0; c < NR; c++) s[c] = 0;
     bool live = row < A.n;
-    if (live) {
-        if (K == VK_RESID0)
-            s = row_sum<G, VT, XT>(A, row, lane, NbD1b<XT>{dinv, b});
-        else if (K == VK_POST)
-            s = row_sum<G, VT, XT>(A, row, lane, NbPost<XT>{dinv, b, xc, agg});
-        else
-            s = row_sum<G, VT, XT>(A, row, lane, NbStored<XT>{xin});
-    }
-    s = lane_reduce<G, XT>(s);
+    if (live) row_sum<G, VT, XT, NR>(A, row, lane, Nb<XT, NR, K>{dinv, b, xin, xc, agg}, s);
+#pragma unroll
+    for (int c = 0; c < NR; c++) s[c] = lane_reduce<G, XT>(s[c]);
     if (live && lane == 0) {
         int64_t o = (G == 0 && A.perm) ? A.perm[row] : row;
-        if (A.rscale) s *= (XT)A.rscale[o];
+        XT sc = A.rscale ? (XT)A.rscale[o] : (XT)1;
+        Vec<XT, NR> bo = ldv<XT, NR>(b, o), res;
         if (K == VK_RESID0 || K == VK_RESID) {
-            out[o] = b[o] - s;
-        } else if (K == VK_POST) {
-            XT y = dinv[o] * b[o];
-            if (agg) {
-                int32_t a = agg[o];
-                if (a >= 0) y += xc[a];
-            }
-            out[o] = y + dinv[o] * (b[o] - s);
+#pragma unroll
+            for (int c = 0; c < NR; c++) res.v[c] = bo.v[c] - s[c] * sc;
         } else {
-            out[o] = xin[o] + dinv[o] * (b[o] - s);
+            XT d = dinv[o];
+            Vec<XT, NR> y;
+            if (K == VK_POST) {
+#pragma unroll
+                for (int c = 0; c < NR; c++) y.v[c] = d * bo.v[c];
+                if (agg) {
+                    int32_t a = agg[o];
+                    if (a >= 0) {
+                        Vec<XT, NR> xa = ldv<XT, NR>(xc, a);
+#pragma unroll
+                        for (int c = 0; c < NR; c++) y.v[c] += xa.v[c];
+                    }
+                }
+            } else {
+                y = ldv<XT, NR>(xin, o);
+            }
+#pragma unroll
+            for (int c = 0; c < NR; c++) res.v[c] = y.v[c] + d * (bo.v[c] - s[c] * sc);
         }
+        stv<XT, NR>(out, o, res);
     }
 }
 
-// ---- elementwise kernels of the stored form
-template <class XT>
+// ---- elementwise kernels (NR interleaved columns; row of entry e = e / NR)
+template <class XT, int NR>
 __global__ void k_vc_x0(int64_t n, const XT *__restrict__ dinv, const XT *__restrict__ b, XT *__restrict__ x) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] = dinv[i] * b[i];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * NR; e += (int64_t)gridDim.x * blockDim.x)
+        x[e] = dinv[e / NR] * b[e];
 }
 
-// y_i += x_c[agg_i]
-template <class XT>
+// y_(i,c) += x_c(agg_i, c)
+template <class XT, int NR>
 __global__ void k_vc_prolong(int64_t n, const int32_t *__restrict__ agg, const XT *__restrict__ xc,
                              XT *__restrict__ y) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        int32_t a = agg[i];
-        if (a >= 0) y[i] += xc[a];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * NR; e += (int64_t)gridDim.x * blockDim.x) {
+        int32_t a = agg[e / NR];
+        if (a >= 0) y[e] += xc[(int64_t)a * NR + e % NR];
     }
 }
 
 // Chebyshev (Saad, Iterative Methods, Alg. 12.1 for D1^-1 A on [lo, hi]):
 // first step d = (D1^-1 r) / theta, x = x0 + d; later steps
 // d = c1 d + c2 D1^-1 r, x += d.
-template <class XT>
+template <class XT, int NR>
 __global__ void k_cheb_first(int64_t n, const XT *__restrict__ dinv, const XT *__restrict__ r,
                              const XT *__restrict__ x0, XT inv_theta, XT *__restrict__ d, XT *__restrict__ x) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        XT di = dinv[i] * r[i] * inv_theta;
-        d[i] = di;
-        x[i] = x0 ? x0[i] + di : di;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * NR; e += (int64_t)gridDim.x * blockDim.x) {
+        XT di = dinv[e / NR] * r[e] * inv_theta;
+        d[e] = di;
+        x[e] = x0 ? x0[e] + di : di;
     }
 }
 
-template <class XT>
+template <class XT, int NR>
 __global__ void k_cheb_next(int64_t n, const XT *__restrict__ dinv, const XT *__restrict__ r, XT c1, XT c2,
                             XT *__restrict__ d, XT *__restrict__ x) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        XT di = c1 * d[i] + c2 * (dinv[i] * r[i]);
-        d[i] = di;
-        x[i] += di;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * NR; e += (int64_t)gridDim.x * blockDim.x) {
+        XT di = c1 * d[e] + c2 * (dinv[e / NR] * r[e]);
+        d[e] = di;
+        x[e] += di;
     }
 }
 
-// b_c[I] = sum of r over the members of aggregate I (ascending)
-template <class XT>
+// b_c[I] = sum of r over the members of aggregate I (ascending), NR columns
+template <class XT, int NR>
 __global__ void k_vc_restrict(int64_t nc, const int32_t *__restrict__ off, const int32_t *__restrict__ mem,
                               const XT *__restrict__ r, XT *__restrict__ bc) {
     int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
-    XT s = 0;
-    for (int32_t q = off[I]; q < off[I + 1]; q++) s += r[mem[q]];
-    bc[I] = s;
+    Vec<XT, NR> s;
+#pragma unroll
+    for (int c = 0; c < NR; c++) s.v[c] = 0;
+    for (int32_t q = off[I]; q < off[I + 1]; q++) {
+        Vec<XT, NR> x = ldv<XT, NR>(r, mem[q]);
+#pragma unroll
+        for (int c = 0; c < NR; c++) s.v[c] += x.v[c];
+    }
+    stv<XT, NR>(bc, I, s);
 }
 
 // ---------------------------------------------------------------- host dispatch
@@ -234,64 +273,62 @@ template <class VT> static LvlMat<VT> lvl_view(const Level &L) {
     return m;
 }
 
-template <class VT, class XT, int K>
+template <class VT, class XT, int K, int NR>
 static void launch_level(Ctx &c, const Level &L, const XT *dinv, const XT *b, const XT *xin, const int32_t *agg,
                          const XT *xc, XT *out, int64_t nc) {
     LvlMat<VT> m = lvl_view<VT>(L);
     int64_t n = L.A.nrow;
     double vb = L.fmt == FMT_SELL ? (sizeof(VT) + 4.0) * (double)L.sell_nnz : (sizeof(VT) + 4.0) * L.A.nnz;
-    double bytes = vb + (L.fmt == FMT_SELL ? 8.0 * L.sell_nslice : 4.0 * (n + 1)) + 3.0 * sizeof(XT) * n +
-                   (K == VK_POST && agg ? 4.0 * n + sizeof(XT) * (double)nc : 0.0) + (L.rscale.p ? 4.0 * n : 0.0) +
-                   (K >= VK_RESID ? sizeof(XT) * (double)n : 0.0) - (K == VK_RESID ? sizeof(XT) * (double)n : 0.0);
-    double flops = 2.0 * L.A.nnz + (K == VK_RESID0 ? n : K == VK_POST ? 5.0 * n : K == VK_SMOOTH ? 3.0 * n : 0.0);
+    double xb = sizeof(XT) * (double)NR;
+    double bytes = vb + (L.fmt == FMT_SELL ? 8.0 * L.sell_nslice : 4.0 * (n + 1)) + sizeof(XT) * n + 2.0 * xb * n +
+                   (K == VK_POST && agg ? 4.0 * n + xb * (double)nc : 0.0) + (L.rscale.p ? 4.0 * n : 0.0) +
+                   (K == VK_SMOOTH ? xb * (double)n : 0.0);
+    double flops = NR * (2.0 * L.A.nnz + (K == VK_RESID0 ? n : K == VK_POST ? 5.0 * n : K == VK_SMOOTH ? 3.0 * n : 0.0));
     int cls = (K == VK_RESID0 || K == VK_RESID) ? KC_VC_RESID : KC_VC_POST;
     if (L.fmt == FMT_SELL) {
         int64_t rows = L.sell_nslice * L.sell_c;
-        MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<0, VT, XT, K>), grid_for(rows, 256), 256, 0, m, dinv, b, xin, agg,
-                     xc, out);
+        MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<0, VT, XT, K, NR>), grid_for(rows, 256), 256, 0, m, dinv, b, xin,
+                     agg, xc, out);
         return;
     }
     switch (L.G) {
         case 2:
-            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<2, VT, XT, K>), grid_for(n * 2, 256), 256, 0, m, dinv, b, xin,
-                         agg, xc, out);
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<2, VT, XT, K, NR>), grid_for(n * 2, 256), 256, 0, m, dinv, b,
+                         xin, agg, xc, out);
             break;
         case 4:
-            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<4, VT, XT, K>), grid_for(n * 4, 256), 256, 0, m, dinv, b, xin,
-                         agg, xc, out);
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<4, VT, XT, K, NR>), grid_for(n * 4, 256), 256, 0, m, dinv, b,
+                         xin, agg, xc, out);
             break;
         case 8:
-            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<8, VT, XT, K>), grid_for(n * 8, 256), 256, 0, m, dinv, b, xin,
-                         agg, xc, out);
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<8, VT, XT, K, NR>), grid_for(n * 8, 256), 256, 0, m, dinv, b,
+                         xin, agg, xc, out);
             break;
         case 16:
-            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<16, VT, XT, K>), grid_for(n * 16, 256), 256, 0, m, dinv, b,
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<16, VT, XT, K, NR>), grid_for(n * 16, 256), 256, 0, m, dinv, b,
                          xin, agg, xc, out);
             break;
         default:
-            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<32, VT, XT, K>), grid_for(n * 32, 256), 256, 0, m, dinv, b,
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<32, VT, XT, K, NR>), grid_for(n * 32, 256), 256, 0, m, dinv, b,
                          xin, agg, xc, out);
             break;
     }
 }
 
-template <class XT, int K>
+template <class XT, int K, int NR>
 static void level_op(Ctx &c, const Level &L, const XT *b, const XT *xin, const int32_t *agg, const XT *xc, XT *out,
                      int64_t nc) {
     const XT *dinv = L.dinv.as<XT>();
     if constexpr (std::is_same<XT, double>::value) {
-        launch_level<double, XT, K>(c, L, dinv, b, xin, agg, xc, out, nc);
+        launch_level<double, XT, K, NR>(c, L, dinv, b, xin, agg, xc, out, nc);
     } else {
         switch (L.vt) {
-            case VT_BF16: launch_level<__nv_bfloat16, XT, K>(c, L, dinv, b, xin, agg, xc, out, nc); break;
-            case VT_F16: launch_level<__half, XT, K>(c, L, dinv, b, xin, agg, xc, out, nc); break;
-            default: launch_level<float, XT, K>(c, L, dinv, b, xin, agg, xc, out, nc); break;
+            case VT_BF16: launch_level<__nv_bfloat16, XT, K, NR>(c, L, dinv, b, xin, agg, xc, out, nc); break;
+            case VT_F16: launch_level<__half, XT, K, NR>(c, L, dinv, b, xin, agg, xc, out, nc); break;
+            default: launch_level<float, XT, K, NR>(c, L, dinv, b, xin, agg, xc, out, nc); break;
         }
     }
 }
-
-static void gemv(Ctx &c, const double *M, int64_t n, const double *x, double *y) { dense_gemv_f64(c, M, n, x, y); }
-static void gemv(Ctx &c, const double *M, int64_t n, const float *x, float *y) { dense_gemv_f32(c, M, n, x, y); }
 
 static unsigned ew_grid(int64_t n) {
     unsigned g = grid_for(n, 256);
@@ -299,9 +336,9 @@ static unsigned ew_grid(int64_t n) {
 }
 
 // x = S(x0; b): `sweeps` smoother applications starting from x0 (NULL = 0).
-// x0 and x must differ; uses L.r (residual), L.t (ping-pong) and L.d
-// (Chebyshev direction) as scratch.
-template <class XT>
+// x0 and x must differ; uses L.r (residual), L.t (copy) and L.d (Chebyshev
+// direction) as scratch.
+template <class XT, int NR>
 static void smooth_stored(Ctx &c, const Hierarchy &h, const Level &L, const XT *b, const XT *x0, XT *x) {
     int64_t n = L.A.nrow;
     XT *r = L.r.as<XT>();
@@ -311,80 +348,108 @@ static void smooth_stored(Ctx &c, const Hierarchy &h, const Level &L, const XT *
     const double rho1 = 1.0 / (2.0 * sigma - rho);
     const XT *cur = x0;
     for (int s = 0; s < h.sweeps; s++) {
-        // this sweep writes `dst`; the last sweep writes x
         XT *dst = x;
         if (cur == x) {
-            MDS_CUDA(cudaMemcpyAsync(L.t.p, x, sizeof(XT) * (size_t)n, cudaMemcpyDeviceToDevice, c.stream));
+            MDS_CUDA(cudaMemcpyAsync(L.t.p, x, sizeof(XT) * (size_t)n * NR, cudaMemcpyDeviceToDevice, c.stream));
             cur = L.t.as<XT>();
         }
         if (h.smoother == MDS_SMOOTHER_L1JACOBI) {
             if (!cur)
-                MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n, k_vc_x0<XT>, ew_grid(n), 256, 0, n, dinv, b, dst);
+                MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n * NR, (k_vc_x0<XT, NR>), ew_grid(n * NR), 256, 0, n, dinv,
+                           b, dst);
             else
-                level_op<XT, VK_SMOOTH>(c, L, b, cur, nullptr, nullptr, dst, 0);
+                level_op<XT, VK_SMOOTH, NR>(c, L, b, cur, nullptr, nullptr, dst, 0);
         } else {
             XT *d = L.d.as<XT>();
             if (cur) {
-                level_op<XT, VK_RESID>(c, L, b, cur, nullptr, nullptr, r, 0);
-                MDS_LAUNCH(c, KC_NONE, 0, k_cheb_first<XT>, ew_grid(n), 256, 0, n, dinv, r, cur, (XT)(1.0 / theta), d,
-                           dst);
-            } else {
-                MDS_LAUNCH(c, KC_NONE, 0, k_cheb_first<XT>, ew_grid(n), 256, 0, n, dinv, b, (const XT *)nullptr,
+                level_op<XT, VK_RESID, NR>(c, L, b, cur, nullptr, nullptr, r, 0);
+                MDS_LAUNCH(c, KC_NONE, 0, (k_cheb_first<XT, NR>), ew_grid(n * NR), 256, 0, n, dinv, r, cur,
                            (XT)(1.0 / theta), d, dst);
+            } else {
+                MDS_LAUNCH(c, KC_NONE, 0, (k_cheb_first<XT, NR>), ew_grid(n * NR), 256, 0, n, dinv, b,
+                           (const XT *)nullptr, (XT)(1.0 / theta), d, dst);
             }
-            level_op<XT, VK_RESID>(c, L, b, dst, nullptr, nullptr, r, 0);
-            MDS_LAUNCH(c, KC_NONE, 0, k_cheb_next<XT>, ew_grid(n), 256, 0, n, dinv, r, (XT)(rho1 * rho),
+            level_op<XT, VK_RESID, NR>(c, L, b, dst, nullptr, nullptr, r, 0);
+            MDS_LAUNCH(c, KC_NONE, 0, (k_cheb_next<XT, NR>), ew_grid(n * NR), 256, 0, n, dinv, r, (XT)(rho1 * rho),
                        (XT)(2.0 * rho1 / delta), d, dst);
         }
         cur = dst;
     }
 }
 
-template <class XT>
+template <class XT, int NR>
 static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
     Level &L = h.lv[l];
     int last = (int)h.lv.size() - 1;
     if (l == last && h.dense) {
-        gemv(c, h.Ainv.as<double>(), h.nd, b, x);
+        dense_apply(c, h.Ainv.as<double>(), h.nd, NR, b, x);
         return;
     }
     int64_t n = L.A.nrow;
     XT *r = L.r.as<XT>();
-    double rbytes = 4.0 * (L.nc + 1) + 4.0 * n + sizeof(XT) * (double)(n + L.nc);
+    double rbytes = 4.0 * (L.nc + 1) + 4.0 * n + sizeof(XT) * NR * (double)(n + L.nc);
     bool fused = !std::is_same<XT, double>::value && h.smoother == MDS_SMOOTHER_L1JACOBI && h.sweeps == 1;
     if (fused) {
         if (L.has_coarse) {
             Level &C = h.lv[l + 1];
-            level_op<XT, VK_RESID0>(c, L, b, nullptr, nullptr, nullptr, r, 0);
-            MDS_LAUNCH(c, KC_VC_RESTRICT, rbytes, k_vc_restrict<XT>, grid_for(L.nc, 256), 256, 0, L.nc,
+            level_op<XT, VK_RESID0, NR>(c, L, b, nullptr, nullptr, nullptr, r, 0);
+            MDS_LAUNCH(c, KC_VC_RESTRICT, rbytes, (k_vc_restrict<XT, NR>), grid_for(L.nc, 256), 256, 0, L.nc,
                        L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r, C.b.as<XT>());
-            vcycle_level<XT>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
-            level_op<XT, VK_POST>(c, L, b, nullptr, L.agg.as<int32_t>(), C.x.as<XT>(), x, L.nc);
+            vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
+            level_op<XT, VK_POST, NR>(c, L, b, nullptr, L.agg.as<int32_t>(), C.x.as<XT>(), x, L.nc);
         } else {
-            level_op<XT, VK_POST>(c, L, b, nullptr, nullptr, nullptr, x, 0);
+            level_op<XT, VK_POST, NR>(c, L, b, nullptr, nullptr, nullptr, x, 0);
         }
         return;
     }
     XT *y = L.y.as<XT>();
-    smooth_stored<XT>(c, h, L, b, nullptr, y);  // y = S(0; b)
+    smooth_stored<XT, NR>(c, h, L, b, nullptr, y);  // y = S(0; b)
     if (L.has_coarse) {
         Level &C = h.lv[l + 1];
-        level_op<XT, VK_RESID>(c, L, b, y, nullptr, nullptr, r, 0);
-        MDS_LAUNCH(c, KC_VC_RESTRICT, rbytes, k_vc_restrict<XT>, grid_for(L.nc, 256), 256, 0, L.nc,
+        level_op<XT, VK_RESID, NR>(c, L, b, y, nullptr, nullptr, r, 0);
+        MDS_LAUNCH(c, KC_VC_RESTRICT, rbytes, (k_vc_restrict<XT, NR>), grid_for(L.nc, 256), 256, 0, L.nc,
                    L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r, C.b.as<XT>());
-        vcycle_level<XT>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
-        MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n, k_vc_prolong<XT>, ew_grid(n), 256, 0, n, L.agg.as<int32_t>(),
-                   C.x.as<XT>(), y);
+        vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
+        MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n * NR, (k_vc_prolong<XT, NR>), ew_grid(n * NR), 256, 0, n,
+                   L.agg.as<int32_t>(), C.x.as<XT>(), y);
     }
-    smooth_stored<XT>(c, h, L, b, y, x);  // x = S(y; b)
+    smooth_stored<XT, NR>(c, h, L, b, y, x);  // x = S(y; b)
 }
 
-void vcycle_apply(Ctx &c, Hierarchy &h, const void *b, void *x) {
+// The level work vectors hold up to nr_cap interleaved columns.
+void hierarchy_reserve(Ctx &c, Hierarchy &h, int nr) {
+    if (nr <= h.nr_cap) return;
+    size_t vb = h.prec == 64 ? sizeof(double) : sizeof(float);
+    for (auto &L : h.lv) {
+        size_t nb = vb * (size_t)(L.A.nrow > 0 ? L.A.nrow : 1) * (size_t)nr;
+        L.b = Buf(&c, nb);
+        L.x = Buf(&c, nb);
+        L.r = Buf(&c, nb);
+        L.y = Buf(&c, nb);
+        L.t = Buf(&c, nb);
+        if (h.smoother == MDS_SMOOTHER_CHEBYSHEV) L.d = Buf(&c, nb);
+    }
+    h.nr_cap = nr;
+}
+
+template <class XT>
+static void vcycle_nr(Ctx &c, Hierarchy &h, const XT *b, XT *x, int nr) {
+    switch (nr) {
+        case 1: vcycle_level<XT, 1>(c, h, 0, b, x); break;
+        case 2: vcycle_level<XT, 2>(c, h, 0, b, x); break;
+        case 4: vcycle_level<XT, 4>(c, h, 0, b, x); break;
+        case 8: vcycle_level<XT, 8>(c, h, 0, b, x); break;
+        default: throw Error(MDS_ERR_INVALID, "V-cycle column count must be 1, 2, 4 or 8");
+    }
+}
+
+void vcycle_apply(Ctx &c, Hierarchy &h, const void *b, void *x, int nr) {
+    MDS_REQUIRE(nr <= h.nr_cap, MDS_ERR_INVALID, "V-cycle work vectors hold fewer columns");
     KTimer all(c, KC_VCYCLE, 0.0);
     if (h.prec == 64)
-        vcycle_level<double>(c, h, 0, (const double *)b, (double *)x);
+        vcycle_nr<double>(c, h, (const double *)b, (double *)x, nr);
     else
-        vcycle_level<float>(c, h, 0, (const float *)b, (float *)x);
+        vcycle_nr<float>(c, h, (const float *)b, (float *)x, nr);
 }
 
 // ---------------------------------------------------------------- level storage
@@ -544,7 +609,7 @@ template <class XT> static float time_level(Ctx &c, const Level &L) {
     float best = 1e30f;
     for (int rep = 0; rep < 4; rep++) {
         MDS_CUDA(cudaEventRecord(e0, c.stream));
-        level_op<XT, VK_RESID>(c, L, L.b.as<XT>(), L.x.as<XT>(), nullptr, nullptr, L.r.as<XT>(), 0);
+        level_op<XT, VK_RESID, 1>(c, L, L.b.as<XT>(), L.x.as<XT>(), nullptr, nullptr, L.r.as<XT>(), 0);
         MDS_CUDA(cudaEventRecord(e1, c.stream));
         MDS_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;

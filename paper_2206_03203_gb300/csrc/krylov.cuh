@@ -1,12 +1,15 @@
 // Krylov solver interfaces (internal).
 #pragma once
 #include <functional>
+#include <vector>
 
 #include "internal.cuh"
 
 namespace mds {
 
 using PrecFn = std::function<void(const double *r, double *z)>;
+// z = M r on nr interleaved columns
+using BatchPrecFn = std::function<void(const double *r, double *z, int nr)>;
 
 struct KrylovResult {
     int iterations = 0;
@@ -33,6 +36,12 @@ KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, 
 // (see mds_solve_noalloc) and its size in doubles.
 double *noalloc_scratch(Ctx &c);
 size_t noalloc_scratch_doubles();
+// K instances (row segments [moff_k, moff_k+1) and [NM + foff_k, NM +
+// foff_k+1)) x nrhs columns (column-major [nrhs][N] in B and X) solved as
+// independent FGMRES problems in lockstep; res[k * nrhs + c].
+void fgmres_batched(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const std::vector<int64_t> &moff,
+                    const std::vector<int64_t> &foff, const double *B, double *X, int nrhs, const mds_solve_opts &o,
+                    std::vector<KrylovResult> &res);
 KrylovResult pcg(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, double *x, int64_t n,
                  const mds_solve_opts &o);
 

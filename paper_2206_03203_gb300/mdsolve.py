@@ -54,7 +54,7 @@ class SetupOpts(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("krylov", C.c_int), ("restart", C.c_int), ("rtol", C.c_double), ("max_iters", C.c_int),
-                ("use_precond", C.c_int), ("graphs", C.c_int)]
+                ("use_precond", C.c_int), ("graphs", C.c_int), ("batched", C.c_int)]
 
 
 class RhsStats(C.Structure):
@@ -95,6 +95,8 @@ _SIGS = {
     "mds_error_string": (C.c_char_p, [C.c_int]),
     "mds_last_error": (C.c_char_p, [C.c_void_p]),
     "mds_assemble": (C.c_int, [C.c_void_p, C.POINTER(Instance), C.POINTER(C.c_void_p)]),
+    "mds_assemble_batch": (C.c_int, [C.c_void_p, C.POINTER(Instance), C.c_int, C.POINTER(C.c_void_p)]),
+    "mds_system_instances": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "mds_system_from_csr": (C.c_int, [C.c_void_p] + [C.POINTER(Csr)] * 4 + [C.c_void_p, C.POINTER(C.c_void_p)]),
     "mds_system_destroy": (C.c_int, [C.c_void_p]),
     "mds_system_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int),
@@ -223,6 +225,24 @@ class Context:
         self._check(lib().mds_set_stream(self.h, C.c_void_p(stream)))
 
     # ---- problem ----
+    def assemble_batch(self, insts) -> "System":
+        """Pack several instances (host arrays) into one block-diagonal system."""
+        keep, arr = [], (Instance * len(insts))()
+        for k, inst in enumerate(insts):
+            a = dict(km=np.ascontiguousarray(inst.km, dtype=np.float64),
+                     fc_axis=np.ascontiguousarray(inst.fc_axis, dtype=np.int32),
+                     fc_pos=np.ascontiguousarray(inst.fc_pos, dtype=np.int32).reshape(-1),
+                     fc_kf=np.ascontiguousarray(inst.fc_kf, dtype=np.float64),
+                     fc_a=np.ascontiguousarray(inst.fc_a, dtype=np.float64),
+                     pD_left=np.ascontiguousarray(inst.pD_left, dtype=np.float64),
+                     pD_right=np.ascontiguousarray(inst.pD_right, dtype=np.float64))
+            keep.append(a)
+            arr[k] = Instance(inst.dim, inst.n, _ptr(a["km"]), inst.n_f, _ptr(a["fc_axis"]), _ptr(a["fc_pos"]),
+                              _ptr(a["fc_kf"]), _ptr(a["fc_a"]), inst.nrhs, _ptr(a["pD_left"]), _ptr(a["pD_right"]), 0)
+        h = C.c_void_p()
+        self._check(lib().mds_assemble_batch(self.h, arr, len(insts), C.byref(h)))
+        return System(self, h)
+
     def assemble(self, inst, device_arrays: Optional[dict] = None) -> "System":
         """Assemble an instance (paper_2206_03203_gb300.inputs.Instance).  With
         ``device_arrays`` (torch CUDA tensors keyed by field name) the device
@@ -268,7 +288,7 @@ class Context:
         """Solve on device tensors (or host numpy arrays).  x holds x0 and is
         overwritten.  Returns (status, [Stats])."""
         o = solve_opts(**opts)
-        st = (RhsStats * nrhs)()
+        st = (RhsStats * (nrhs * sys.n_inst))()
         code = lib().mds_solve(self.h, sys.h, prec.h if prec is not None else None, C.c_void_p(_ptr(b)),
                                C.c_void_p(_ptr(x)), nrhs, C.byref(o), st)
         self._check(code)
@@ -338,6 +358,9 @@ class System:
         self.n_m, self.n_f, self.nrhs = n_m.value, n_f.value, nrhs.value
         self.nnz = list(nnz)
         self.N = self.n_m + self.n_f
+        ni = C.c_int()
+        ctx._check(lib().mds_system_instances(h, C.byref(ni), None, None))
+        self.n_inst = ni.value
         _track(self, 1)
 
     def close(self):
@@ -366,6 +389,13 @@ class System:
         mats = [self.ctx.csr_to_host(x) for x in v]
         bh = self.ctx.to_host(b, self.N * self.nrhs, np.float64).reshape(self.nrhs, self.N)
         return mats, bh
+
+    def instances(self):
+        """(m_off, f_off) row offsets of the packed instances."""
+        mo = (C.c_int64 * (self.n_inst + 1))()
+        fo = (C.c_int64 * (self.n_inst + 1))()
+        self.ctx._check(lib().mds_system_instances(self.h, None, mo, fo))
+        return list(mo), list(fo)
 
     def b_ptr(self, k: int = 0) -> int:
         return self.views()[1] + 8 * k * self.N

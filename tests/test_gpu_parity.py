@@ -479,3 +479,80 @@ def test_context_outlives_dependents_in_any_order(torch_mod):
     assert L.mds_destroy(h_ctx) == 0
     assert L.mds_system_destroy(h_s) == 0
     assert L.mds_precond_destroy(h_p) == 0
+
+
+# ---------------------------------------------------------------- batching (multi-RHS, packed instances)
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_multi_rhs_lockstep(ctx, oracle_mod, torch_mod, precision):
+    """Several right-hand sides solved together (shared SpMV / V-cycle reads,
+    per-column FGMRES) agree with column-by-column solves and the oracle."""
+    inst = inputs.random_rects_3d(14, 7, 2, 5, nrhs=5, random_dirichlet=True)
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_, precision=precision)
+    xb = np.zeros(5 * sys_.N)
+    code, stb = ctx.solve(sys_, prec, None, xb, nrhs=5)
+    xs = np.zeros(5 * sys_.N)
+    code2, sts = ctx.solve(sys_, prec, None, xs, nrhs=5, batched=0)
+    assert code == 0 and code2 == 0
+    Ao, bo = oracle_mod.assemble(inst)
+    M = oracle_mod.ML(Ao, inst.n_m, prec=64 if precision == "fp64" else 32)
+    for k in range(5):
+        xk = xb[k * sys_.N:(k + 1) * sys_.N]
+        assert np.linalg.norm(bo[k] - Ao @ xk) / np.linalg.norm(bo[k]) <= 1.01e-8
+        assert abs(stb[k].iterations - sts[k].iterations) <= 1
+        r = oracle_mod.fgmres(Ao, bo[k], M)
+        assert abs(stb[k].iterations - r.iterations) <= 1, (k, stb[k].iterations, r.iterations)
+
+
+def packed_oracle(oracle_mod, insts):
+    """Block-diagonal packing [m_0..m_K-1; f_0..f_K-1] of oracle assemblies."""
+    import scipy.sparse as sp
+    blocks = [oracle_mod.split(*oracle_mod.assemble(i)[:1], i.n_m) for i in insts]
+    bs = [oracle_mod.assemble(i)[1] for i in insts]
+    Amm = sp.block_diag([b[0] for b in blocks], format="csr")
+    Amf = sp.block_diag([b[1] for b in blocks], format="csr")
+    Afm = sp.block_diag([b[2] for b in blocks], format="csr")
+    Aff = sp.block_diag([b[3] for b in blocks], format="csr")
+    A = sp.bmat([[Amm, Amf], [Afm, Aff]], format="csr")
+    A.sort_indices()
+    nrhs = insts[0].nrhs
+    b = np.stack([np.concatenate([bs[k][r][:insts[k].n_m] for k in range(len(insts))] +
+                                 [bs[k][r][insts[k].n_m:] for k in range(len(insts))]) for r in range(nrhs)])
+    return A, b, Amm.shape[0]
+
+
+def test_packed_batch_of_uneven_instances(ctx, oracle_mod, torch_mod):
+    insts = [inputs.random_rects_3d(n, 22060304, k, 1 + k % 4, nrhs=2, random_dirichlet=True)
+             for k, n in enumerate([9, 12, 8, 14, 11])]
+    sys_ = ctx.assemble_batch(insts)
+    assert sys_.n_inst == 5
+    (_, _, _, _, A), b = sys_.to_host()
+    Ao, bo, NM = packed_oracle(oracle_mod, insts)
+    assert same_csr(A, Ao) and np.array_equal(b, bo)
+    mo, fo = sys_.instances()
+    prec = ctx.setup(sys_)
+    x = np.zeros(2 * sys_.N)
+    code, st = ctx.solve(sys_, prec, None, x, nrhs=2)
+    assert code == 0 and len(st) == 10
+    M = oracle_mod.ML(Ao, NM)
+    for k in range(5):
+        rows = np.r_[mo[k]:mo[k + 1], NM + fo[k]:NM + fo[k + 1]]
+        for c in range(2):
+            be = np.zeros(sys_.N)
+            be[rows] = bo[c][rows]
+            r = oracle_mod.fgmres(Ao, be, M)
+            s = st[k * 2 + c]
+            assert s.status == 0 and abs(s.iterations - r.iterations) <= 1, (k, c, s.iterations, r.iterations)
+            xk = x[c * sys_.N:(c + 1) * sys_.N][rows]
+            Ak = Ao[rows][:, rows]
+            assert np.linalg.norm(be[rows] - Ak @ xk) / np.linalg.norm(be[rows]) <= 1.01e-8
+
+
+def test_packed_batch_per_problem_iteration_cap(ctx, torch_mod):
+    insts = [inputs.random_rects_3d(n, 3, k, 2, nrhs=1) for k, n in enumerate([8, 10])]
+    sys_ = ctx.assemble_batch(insts)
+    prec = ctx.setup(sys_)
+    x = np.zeros(sys_.N)
+    code, st = ctx.solve(sys_, prec, None, x, max_iters=4)
+    assert code == 1 and all(s.iterations == 4 and s.status == 1 for s in st)
