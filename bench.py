@@ -153,7 +153,7 @@ def run_gpu(args):
         its = []
         for k, inst in enumerate(insts):
             s = ctx.assemble(inst, device_arrays=dev_arrays[k])
-            p = ctx.setup(s, precision="fp64")
+            p = ctx.setup(s, precision="fp64", format="auto")
             xs[k].zero_()
             code, st = ctx.solve(s, p, None, xs[k], **sopt)
             if code != 0:
@@ -222,7 +222,7 @@ def run_gpu(args):
         t0 = time.perf_counter()
         for k, inst in enumerate(insts):
             s = ctx.assemble(inst)
-            p = ctx.setup(s, precision="fp64")
+            p = ctx.setup(s, precision="fp64", format="auto")
             xh = np.zeros(N[k])
             code, st = ctx.solve(s, p, None, xh, **sopt)
             p.close()
@@ -272,12 +272,91 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if not args.no_variants:
+        line["variants"] = variants(ctx, insts, dev_arrays, N, flush)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _timed(fn, flush, warmup=1, steps=1):
+    """Device-timed seconds per step of fn() (CUDA events, L2 flushed before
+    each step)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    tot = 0.0
+    out = None
+    for _ in range(steps):
+        flush.fill_(0.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1) / 1e3
+    return tot / steps, out
+
+
+def variants(ctx, insts, dev_arrays, N, flush):
+    """Secondary measurements (not the headline): the FP32 V-cycle path on the
+    same sweep, the nine-plane 3D instance, and the 256-instance batch."""
+    import torch
+
+    from paper_2206_03203_gb300 import inputs
+    out = {}
+
+    def sweep(prec):
+        its = []
+        for k, inst in enumerate(insts):
+            s = ctx.assemble(inst, device_arrays=dev_arrays[k])
+            p = ctx.setup(s, precision=prec, format="auto")
+            x = torch.zeros(N[k], dtype=torch.float64, device="cuda")
+            code, st = ctx.solve(s, p, None, x, rtol=1e-8, max_iters=5000)
+            assert code == 0
+            its.append(st[0].iterations)
+            p.close()
+            s.close()
+        return its
+
+    t, its = _timed(lambda: sweep("fp32"), flush)
+    out["seg2d_1024_sweep_fp32_vcycle"] = {"solves_per_s": len(insts) / t, "s_per_step": t, "iterations": its,
+                                           "precision": "FP32 V-cycle values/vectors, FP64 FGMRES"}
+    p3 = inputs.planes_3d(128, kf=1e4)
+    for prec in ("fp64", "fp32"):
+        def one(prec=prec):
+            s = ctx.assemble(p3)
+            p = ctx.setup(s, precision=prec, format="auto")
+            x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+            code, st = ctx.solve(s, p, None, x, rtol=1e-8, max_iters=5000)
+            p.close()
+            s.close()
+            return st[0].iterations
+        t, it = _timed(one, flush)
+        out[f"planes3d_128_kf1e4_{prec}"] = {"solves_per_s": 1.0 / t, "s_per_step": t, "iterations": it,
+                                             "N": p3.n_m + p3.n_f}
+    batch = inputs.batch_3d(256)
+
+    def batched():
+        s = ctx.assemble_batch(batch)
+        p = ctx.setup(s, precision="bf16", format="auto")
+        x = torch.zeros(s.N * 4, dtype=torch.float64, device="cuda")
+        code, st = ctx.solve(s, p, None, x, nrhs=4, rtol=1e-8, max_iters=5000)
+        assert code == 0
+        n = s.N
+        p.close()
+        s.close()
+        return [q.iterations for q in st], n
+    t, (its, n) = _timed(batched, flush)
+    out["batch3d_256inst_x4rhs_bf16"] = {"solves_per_s": len(its) / t, "s_per_step": t, "solves": len(its),
+                                         "iterations_min_mean_max": [min(its), float(np.mean(its)), max(its)],
+                                         "N_packed": n, "precision": "FP32 fine level, BF16 row-scaled coarse levels, "
+                                         "FP64 FGMRES; packed lockstep batch"}
+    return out
 
 
 def cpu_baseline(samples: int = 1):
@@ -357,6 +436,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--profile-case", action="store_true", help="short fixed run for ncu captures")
     ap.add_argument("--max-iters", type=int, default=60)
     ap.add_argument("--n", type=int, default=1024)

@@ -673,13 +673,22 @@ __global__ void __launch_bounds__(RED_BLOCK) k_bmaxpy(const Chunk *__restrict__ 
     }
 }
 
-// W(i, c) *= f[p]  (f = sc[p * 8 + slot])
+// W(i, c) *= f[p]  (f = sc[p * 8 + slot]) for active problems; inactive ones
+// get exact zeros, so the vectors of a problem that has stopped stay bounded
+// (and 0 * their entries stays 0 in the shared kernels).
 template <int NR>
-__global__ void k_bscale(const Chunk *__restrict__ ch, double *__restrict__ W, const double *__restrict__ sc, int slot) {
+__global__ void k_bscale(const Chunk *__restrict__ ch, double *__restrict__ W, const double *__restrict__ sc, int slot,
+                         const int8_t *__restrict__ active) {
     Chunk k = ch[blockIdx.x];
+    double f[NR];
+#pragma unroll
+    for (int c = 0; c < NR; c++) {
+        int64_t p = (int64_t)k.inst * NR + c;
+        f[c] = active[p] ? sc[p * 8 + slot] : 0.0;
+    }
     for (int64_t i = k.b + threadIdx.x; i < k.e; i += blockDim.x)
 #pragma unroll
-        for (int c = 0; c < NR; c++) W[i * NR + c] *= sc[((int64_t)k.inst * NR + c) * 8 + slot];
+        for (int c = 0; c < NR; c++) W[i * NR + c] = f[c] == 0.0 ? 0.0 : W[i * NR + c] * f[c];
 }
 
 // per problem: beta = sqrt(nsq), g = (beta, 0, ...), sc[1] = 1/beta
@@ -866,11 +875,15 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
             hact[p] = done[p] ? 0 : 1;
             hkd[p] = 0;
         }
+        std::memcpy(c.h_pin, hact.data(), (size_t)P);
+        MDS_CUDA(cudaMemcpyAsync(act.p, c.h_pin, (size_t)P, cudaMemcpyHostToDevice, c.stream));
         MDS_LAUNCH(c, KC_NONE, 0, k_bcycle_start, grid_for(P, 128), 128, 0, P, nsq, m, g, sc);
-        MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, nch, RED_BLOCK, 0, CHp, Vp, sc, 1);
+        MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, nch, RED_BLOCK, 0, CHp, Vp, sc, 1, act.as<int8_t>());
         for (int j = 0; j < m; j++) {
-            std::memcpy(c.h_pin, hact.data(), (size_t)P);
-            MDS_CUDA(cudaMemcpyAsync(act.p, c.h_pin, (size_t)P, cudaMemcpyHostToDevice, c.stream));
+            if (j > 0) {
+                std::memcpy(c.h_pin, hact.data(), (size_t)P);
+                MDS_CUDA(cudaMemcpyAsync(act.p, c.h_pin, (size_t)P, cudaMemcpyHostToDevice, c.stream));
+            }
             double *vj = Vp + (size_t)j * ldq, *zj = Zp + (size_t)j * ldq, *w = Vp + (size_t)(j + 1) * ldq;
             M(vj, zj, NR);
             spmv_f64(c, A, zj, w, KC_SPMV, NR);
@@ -888,7 +901,7 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
             MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, 1), 32, 0, PT, nch, 1, NR, IO, IL, P, nsq, 0);
             MDS_LAUNCH(c, KC_NONE, 0, k_barnoldi, grid_for(P, 128), 128, 0, P, j, m, act.as<int8_t>(), H.as<double>(),
                        h1, h2, nsq, cs, sn, g, sc);
-            MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, nch, RED_BLOCK, 0, CHp, w, sc, 3);
+            MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, nch, RED_BLOCK, 0, CHp, w, sc, 3, act.as<int8_t>());
             MDS_CUDA(cudaMemcpyAsync(c.h_pin, sc, sizeof(double) * (size_t)P * 8, cudaMemcpyDeviceToHost, c.stream));
             c.sync();
             const double *hp = static_cast<const double *>(c.h_pin);

@@ -556,3 +556,21 @@ def test_packed_batch_per_problem_iteration_cap(ctx, torch_mod):
     x = np.zeros(sys_.N)
     code, st = ctx.solve(sys_, prec, None, x, max_iters=4)
     assert code == 1 and all(s.iterations == 4 and s.status == 1 for s in st)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
+def test_packed_batch_four_columns_uneven_convergence(ctx, torch_mod, precision):
+    """Problems stop at different steps; the stopped ones must not disturb the
+    others (shared coarsest dense solve) nor their own solution."""
+    insts = [inputs.random_rects_3d(n, 22060304, k, 2 + k, nrhs=4, random_dirichlet=True)
+             for k, n in enumerate([16, 11, 14, 9])]
+    sys_ = ctx.assemble_batch(insts)
+    prec = ctx.setup(sys_, precision=precision)
+    x = np.zeros(4 * sys_.N)
+    code, st = ctx.solve(sys_, prec, None, x, nrhs=4)
+    assert code == 0 and all(s.status == 0 and s.relres_true <= 1.01e-8 for s in st)
+    assert np.all(np.isfinite(x))
+    # problems of one instance differ only in their boundary data: similar counts
+    for k in range(4):
+        its = [st[k * 4 + c].iterations for c in range(4)]
+        assert max(its) - min(its) <= max(3, min(its) // 4), its
