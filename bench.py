@@ -421,7 +421,7 @@ def run_profile_case(args):
     ctx = mdsolve.Context(0)
     inst = inputs.random_segments_2d(n=args.n, contrast=1e4)
     s = ctx.assemble(inst)
-    p = ctx.setup(s, precision=args.precision)
+    p = ctx.setup(s, precision=args.precision, format="auto")
     x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
     code, st = ctx.solve(s, p, None, x, rtol=1e-8, max_iters=args.max_iters)
     torch.cuda.synchronize()

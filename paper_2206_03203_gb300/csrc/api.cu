@@ -583,6 +583,7 @@ int mds_solve_opts_default(mds_solve_opts *o) {
     o->use_precond = 1;
     o->graphs = 1;
     o->batched = 1;
+    o->reorth_eta2 = 1e-8;
     return MDS_OK;
 }
 
@@ -596,7 +597,8 @@ int mds_solve(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, do
     mds_solve_opts o;
     mds_solve_opts_default(&o);
     if (opts) o = *opts;
-    MDS_REQUIRE(o.rtol > 0.0 && o.max_iters >= 0 && o.restart >= 1, MDS_ERR_INVALID, "bad solve options");
+    MDS_REQUIRE(o.rtol > 0.0 && o.max_iters >= 0 && o.restart >= 1 && o.reorth_eta2 >= 0.0, MDS_ERR_INVALID,
+                "bad solve options");
     MDS_REQUIRE(!o.use_precond || (prec && prec->sys == sys), MDS_ERR_INVALID, "preconditioner of another system");
     MDS_REQUIRE(b || nrhs <= sys->nrhs, MDS_ERR_INVALID, "more right-hand sides than assembled");
     int64_t n = sys->n_m + sys->n_f;

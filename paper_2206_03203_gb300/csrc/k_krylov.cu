@@ -179,12 +179,14 @@ __global__ void k_cycle_start(const double *__restrict__ normsq, double *__restr
     for (int q = 1; q <= m; q++) g[q] = 0.0;
 }
 
-// DGKS test after the first Gram-Schmidt pass: reorthogonalise when the
-// projection removed more than half of ||w||^2 (||w_new|| < ||w|| / sqrt(2)).
-// flag[0] = 1 to run the second pass; the second-pass coefficients start at 0.
+// Cancellation test after the first Gram-Schmidt pass: reorthogonalise when
+// ||w_new||^2 < eta2 ||w||^2.  One classical pass leaves an orthogonality
+// error of about eps ||w|| / ||w_new||; eta2 = 1/2 is the DGKS "twice is
+// enough" rule, eta2 = 1e-8 reorthogonalises only when that error could
+// exceed ~1e-12.  flag[0] = 1 runs the second pass; its coefficients start at 0.
 __global__ void k_dgks(const double *__restrict__ nsq_before, const double *__restrict__ nsq_after,
-                       double *__restrict__ flag, double *__restrict__ h2, int nq) {
-    double run = (nsq_after[0] < 0.5 * nsq_before[0]) ? 1.0 : 0.0;
+                       double *__restrict__ flag, double *__restrict__ h2, int nq, double eta2) {
+    double run = (nsq_after[0] < eta2 * nsq_before[0]) ? 1.0 : 0.0;
     flag[0] = run;
     for (int q = 0; q < nq; q++) h2[q] = 0.0;
 }
@@ -368,7 +370,7 @@ KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, 
         MDS_LAUNCH_F(c, KC_GS_AXPY, 8.0 * n * (nq + 2), fl + 2.0 * n, (k_maxpy<-1, true>), R.grid, RED_BLOCK, 0, n,
                      Vp, ld, nq, h, w, R.pp, (const double *)nullptr);
         MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.pp, (int)R.grid, 1, nsq, 0);
-        MDS_LAUNCH(c, KC_NONE, 0, k_dgks, 1, 1, 0, h + nq, nsq, dflag, h2, nq);
+        MDS_LAUNCH(c, KC_NONE, 0, k_dgks, 1, 1, 0, h + nq, nsq, dflag, h2, nq, o.reorth_eta2);
         MDS_LAUNCH_F(c, KC_GS_DOT, 8.0 * n * (nq + 1), fl, k_mdot, dim3(R.mgrid, nq), RED_BLOCK, 0, n, Vp, ld, nq, w,
                      R.pp, (const double *)dflag);
         MDS_LAUNCH(c, KC_NONE, 0, k_reduce_rows, nq, 32, 0, R.pp, (int)R.mgrid, nq, h2, 0,

@@ -54,7 +54,7 @@ class SetupOpts(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("krylov", C.c_int), ("restart", C.c_int), ("rtol", C.c_double), ("max_iters", C.c_int),
-                ("use_precond", C.c_int), ("graphs", C.c_int), ("batched", C.c_int)]
+                ("use_precond", C.c_int), ("graphs", C.c_int), ("batched", C.c_int), ("reorth_eta2", C.c_double)]
 
 
 class RhsStats(C.Structure):

@@ -574,3 +574,19 @@ def test_packed_batch_four_columns_uneven_convergence(ctx, torch_mod, precision)
     for k in range(4):
         its = [st[k * 4 + c].iterations for c in range(4)]
         assert max(its) - min(its) <= max(3, min(its) // 4), its
+
+
+@pytest.mark.parametrize("eta2", [0.0, 0.5, 2.0])
+def test_reorthogonalisation_threshold(ctx, oracle_mod, torch_mod, eta2):
+    """One classical Gram-Schmidt pass (eta2 = 0), the DGKS rule (0.5) and
+    always two passes (>= 1) all reach the stopping rule within one iteration
+    of the oracle's modified Gram-Schmidt."""
+    torch = torch_mod
+    inst = CASES["rects3d-18"]()
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_)
+    x = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+    code, st = ctx.solve(sys_, prec, None, x, reorth_eta2=eta2)
+    res, Ao, bo, _ = oracle_mod.solve(inst)
+    assert code == 0 and abs(st[0].iterations - res.iterations) <= 1
+    assert st[0].relres_true <= 1e-8
