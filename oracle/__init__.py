@@ -45,7 +45,7 @@ class _CSR(C.Structure):
 class AMGOpts(C.Structure):
     _fields_ = [("theta", C.c_double), ("n_coarse", C.c_int64), ("max_levels", C.c_int),
                 ("stall_ratio", C.c_double), ("seed", C.c_uint64), ("smoother", C.c_int),
-                ("prec", C.c_int), ("lowp_from_level", C.c_int), ("sweeps", C.c_int)]
+                ("prec", C.c_int), ("lowp_from_level", C.c_int), ("sweeps", C.c_int), ("smoothed", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -95,6 +95,8 @@ def lib():
             L.orc_amg_level_agg.argtypes = [C.c_void_p, C.c_int, _i32p]
             L.orc_amg_level_roots.argtypes = [C.c_void_p, C.c_int, _i8p]
             L.orc_amg_level_l1.argtypes = [C.c_void_p, C.c_int, _f64p]
+            L.orc_amg_level_P.restype = P(_CSR)
+            L.orc_amg_level_P.argtypes = [C.c_void_p, C.c_int]
             L.orc_amg_coarsest_dense.argtypes = [C.c_void_p]
             L.orc_vcycle.argtypes = [C.c_void_p, _f64p, _f64p]
             L.orc_ml_new.restype = C.c_void_p
@@ -207,8 +209,9 @@ DEFAULT_SEED = 0x2206_0320_3
 
 
 def amg_opts(theta=0.08, n_coarse=512, max_levels=25, stall_ratio=0.9, seed=DEFAULT_SEED,
-             smoother=0, prec=64, lowp_from_level=1, sweeps=1) -> AMGOpts:
-    return AMGOpts(theta, n_coarse, max_levels, stall_ratio, seed, smoother, prec, lowp_from_level, sweeps)
+             smoother=0, prec=64, lowp_from_level=1, sweeps=1, smoothed=0) -> AMGOpts:
+    return AMGOpts(theta, n_coarse, max_levels, stall_ratio, seed, smoother, prec, lowp_from_level, sweeps,
+                   smoothed)
 
 
 def round_lowp(x, prec):
@@ -255,6 +258,10 @@ class AMG:
         out = np.zeros(n)
         lib().orc_amg_level_l1(self.h, l, _p(out, _f64p))
         return out
+
+    def P(self, l):
+        ptr = lib().orc_amg_level_P(self.h, l)
+        return _from_csr(ptr, free=False) if ptr else None
 
     @property
     def coarsest_dense(self):

@@ -507,6 +507,8 @@ struct orc_amg {
     double *av[MAXLEV];    /* matrix values as the smoother/residual use them */
     double *dinv[MAXLEV];  /* 1 / l1, rounded to the storage precision */
     int lowp[MAXLEV];      /* level stored with bf16 row-scaled values */
+    ocsr *P[MAXLEV];       /* smoothed prolongator of level l (NULL: injection by agg) */
+    ocsr *R[MAXLEV];       /* its transpose */
     int dense;             /* last level solved by dense Cholesky */
     double *L;             /* dense Cholesky factor (row-major, lower) */
     int64_t nd;
@@ -666,6 +668,174 @@ static ocsr *galerkin(const ocsr *A, const int32_t *agg, int64_t nc) {
     return C;
 }
 
+/* Smoothed aggregation (Sec. 3.3 uses smoothed-aggregation AMG;
+ * Vanek, Mandel, Brezina 1996): P = P0 - w D1F^-1 AF P0, with P0 the 0/1
+ * aggregate injection, AF the filtered matrix (weak off-diagonals removed and
+ * added to the diagonal, so row sums are kept), D1F the L1 diagonal of AF and
+ * w = 4/3 (lambda_max(D1F^-1 AF) <= 1, so w / lambda_max >= 4/3 needs no
+ * eigenvalue estimate).  Row i: (agg(i), 1) when aggregated, then for each
+ * entry of row i kept in AF, in CSR order, with J = agg(col) >= 0:
+ * P_iJ = P_iJ - (c_i aF_ij), c_i = (4/3) / d1f_i.  Parity pins: dense formula,
+ * dense P^T A P, two-grid error propagation. */
+static ocsr *smoothed_prolongator(const ocsr *A, const ocsr *G, const int32_t *agg, int64_t nc) {
+    int64_t n = A->nrow;
+    int64_t cap = A->nnz + n + 16;
+    ocsr *P = orc_csr_new(n, nc, cap);
+    int32_t *cols = (int32_t *)malloc(sizeof(int32_t) * 4096);
+    double *vals = (double *)malloc(sizeof(double) * 4096);
+    int64_t pos = 0;
+    for (int64_t i = 0; i < n; i++) {
+        /* strong flags of row i by merging the sorted rows of A and G */
+        int64_t g = G->rp[i];
+        double afd = 0.0, d1 = 0.0;
+        int found_d = 0;
+        for (int64_t p = A->rp[i]; p < A->rp[i + 1]; p++)
+            if (A->ci[p] == i) {
+                afd = A->v[p];
+                found_d = 1;
+            }
+        (void)found_d;
+        /* filtered diagonal: a_ii + sum of weak off-diagonals (CSR order) */
+        for (int64_t p = A->rp[i]; p < A->rp[i + 1]; p++) {
+            int32_t j = A->ci[p];
+            if (j == i) continue;
+            while (g < G->rp[i + 1] && G->ci[g] < j) g++;
+            int strong = g < G->rp[i + 1] && G->ci[g] == j;
+            if (!strong) afd = afd + A->v[p];
+        }
+        d1 = afd;
+        g = G->rp[i];
+        for (int64_t p = A->rp[i]; p < A->rp[i + 1]; p++) {
+            int32_t j = A->ci[p];
+            if (j == i) continue;
+            while (g < G->rp[i + 1] && G->ci[g] < j) g++;
+            if (g < G->rp[i + 1] && G->ci[g] == j) d1 = d1 + fabs(A->v[p]);
+        }
+        double ci = (4.0 / 3.0) / d1;
+        int m = 0;
+        if (agg[i] >= 0) {
+            cols[m] = agg[i];
+            vals[m++] = 1.0;
+        }
+        g = G->rp[i];
+        for (int64_t p = A->rp[i]; p < A->rp[i + 1]; p++) {
+            int32_t j = A->ci[p];
+            double a;
+            if (j == i) {
+                a = afd;
+            } else {
+                while (g < G->rp[i + 1] && G->ci[g] < j) g++;
+                if (!(g < G->rp[i + 1] && G->ci[g] == j)) continue;
+                a = A->v[p];
+            }
+            int32_t J = agg[j];
+            if (J < 0) continue;
+            int t = 0;
+            while (t < m && cols[t] != J) t++;
+            if (t == m) {
+                cols[m] = J;
+                vals[m++] = 0.0;
+            }
+            vals[t] = vals[t] - ci * a;
+        }
+        for (int a2 = 1; a2 < m; a2++) {
+            int32_t x = cols[a2];
+            double y = vals[a2];
+            int q = a2 - 1;
+            while (q >= 0 && cols[q] > x) {
+                cols[q + 1] = cols[q];
+                vals[q + 1] = vals[q];
+                q--;
+            }
+            cols[q + 1] = x;
+            vals[q + 1] = y;
+        }
+        if (pos + m > cap) {
+            cap = 2 * cap + m;
+            P->ci = (int32_t *)realloc(P->ci, (size_t)cap * sizeof(int32_t));
+            P->v = (double *)realloc(P->v, (size_t)cap * sizeof(double));
+        }
+        for (int a2 = 0; a2 < m; a2++) {
+            P->ci[pos] = cols[a2];
+            P->v[pos++] = vals[a2];
+        }
+        P->rp[i + 1] = pos;
+    }
+    P->nnz = pos;
+    free(cols);
+    free(vals);
+    return P;
+}
+
+/* R = P^T with the entries of each row in ascending fine index. */
+static ocsr *transpose_csr(const ocsr *P) {
+    ocsr *R = orc_csr_new(P->ncol, P->nrow, P->nnz);
+    for (int64_t p = 0; p < P->nnz; p++) R->rp[P->ci[p] + 1]++;
+    for (int64_t I = 0; I < P->ncol; I++) R->rp[I + 1] += R->rp[I];
+    int64_t *at = (int64_t *)malloc(sizeof(int64_t) * (size_t)(P->ncol > 0 ? P->ncol : 1));
+    for (int64_t I = 0; I < P->ncol; I++) at[I] = R->rp[I];
+    for (int64_t i = 0; i < P->nrow; i++)
+        for (int64_t p = P->rp[i]; p < P->rp[i + 1]; p++) {
+            int64_t q = at[P->ci[p]]++;
+            R->ci[q] = (int32_t)i;
+            R->v[q] = P->v[p];
+        }
+    free(at);
+    return R;
+}
+
+/* C = X Y: entry (i, k) accumulates x_ij y_jk over the entries of row i of X
+ * in order, then the entries of row j of Y in order. */
+static ocsr *spgemm(const ocsr *X, const ocsr *Y) {
+    int64_t n = X->nrow, nc = Y->ncol;
+    double *acc = (double *)calloc((size_t)(nc > 0 ? nc : 1), sizeof(double));
+    int8_t *mark = (int8_t *)calloc((size_t)(nc > 0 ? nc : 1), 1);
+    int32_t *cols = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nc > 0 ? nc : 1));
+    int64_t cap = X->nnz + Y->nnz + 16;
+    ocsr *C = orc_csr_new(n, nc, cap);
+    int64_t pos = 0;
+    for (int64_t i = 0; i < n; i++) {
+        int64_t m = 0;
+        for (int64_t p = X->rp[i]; p < X->rp[i + 1]; p++) {
+            int32_t j = X->ci[p];
+            for (int64_t q = Y->rp[j]; q < Y->rp[j + 1]; q++) {
+                int32_t k = Y->ci[q];
+                if (!mark[k]) {
+                    mark[k] = 1;
+                    acc[k] = 0.0;
+                    cols[m++] = k;
+                }
+                acc[k] = acc[k] + X->v[p] * Y->v[q];
+            }
+        }
+        for (int64_t a = 1; a < m; a++) {
+            int32_t x = cols[a];
+            int64_t q = a - 1;
+            while (q >= 0 && cols[q] > x) {
+                cols[q + 1] = cols[q];
+                q--;
+            }
+            cols[q + 1] = x;
+        }
+        if (pos + m > cap) {
+            cap = 2 * cap + m;
+            C->ci = (int32_t *)realloc(C->ci, (size_t)cap * sizeof(int32_t));
+            C->v = (double *)realloc(C->v, (size_t)cap * sizeof(double));
+        }
+        for (int64_t a = 0; a < m; a++) {
+            C->ci[pos] = cols[a];
+            C->v[pos++] = acc[cols[a]];
+            mark[cols[a]] = 0;
+        }
+        C->rp[i + 1] = pos;
+    }
+    C->nnz = pos;
+    free(acc);
+    free(mark);
+    free(cols);
+    return C;
+}
+
 /* bf16 rounding: round to nearest even on the top 16 bits of a float. */
 static float to_bf16(float x) {
     uint32_t u;
@@ -729,13 +899,22 @@ orc_amg *orc_amg_setup(const ocsr *A0, const orc_amg_opts *o) {
         (void)nr;
         h->agg[l] = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
         int64_t nc = aggregate(G, h->root[l], h->agg[l]);
-        orc_csr_free(G);
         if (nc == 0 || (double)nc > o->stall_ratio * (double)n) {
+            orc_csr_free(G);
             free(h->agg[l]);
             h->agg[l] = NULL;
             break;
         }
-        A = galerkin(A, h->agg[l], nc);
+        if (o->smoothed) {
+            h->P[l] = smoothed_prolongator(A, G, h->agg[l], nc);
+            h->R[l] = transpose_csr(h->P[l]);
+            ocsr *B = spgemm(A, h->P[l]);
+            A = spgemm(h->R[l], B);
+            orc_csr_free(B);
+        } else {
+            A = galerkin(A, h->agg[l], nc);
+        }
+        orc_csr_free(G);
         l++;
     }
     h->nlev = l + 1;
@@ -808,6 +987,8 @@ void orc_amg_free(orc_amg *h) {
     if (!h) return;
     for (int q = 0; q < MAXLEV; q++) {
         orc_csr_free(h->A[q]);
+        orc_csr_free(h->P[q]);
+        orc_csr_free(h->R[q]);
         free(h->agg[q]);
         free(h->root[q]);
         free(h->l1[q]);
@@ -830,6 +1011,11 @@ int orc_amg_level_agg(const orc_amg *h, int l, int32_t *out) {
     if (l < 0 || l >= h->nlev || !h->agg[l]) return -1;
     memcpy(out, h->agg[l], (size_t)h->A[l]->nrow * sizeof(int32_t));
     return 0;
+}
+
+const ocsr *orc_amg_level_P(const orc_amg *h, int l) {
+    if (l < 0 || l >= h->nlev) return NULL;
+    return h->P[l];
 }
 
 int orc_amg_level_roots(const orc_amg *h, int l, int8_t *out) {
@@ -922,13 +1108,29 @@ static void vcycle_level(orc_amg *h, int l, const double *b, double *x) {
         level_residual(h, l, b, x, r);
         for (int64_t i = 0; i < n; i++) r[i] = rnd(r[i], pv);
         double *bc = h->vb[l + 1], *xc = h->vx[l + 1];
-        for (int64_t I = 0; I < nc; I++) bc[I] = 0.0;
-        for (int64_t i = 0; i < n; i++)
-            if (h->agg[l][i] >= 0) bc[h->agg[l][i]] += r[i];
-        for (int64_t I = 0; I < nc; I++) bc[I] = rnd(bc[I], pv);
-        vcycle_level(h, l + 1, bc, xc);
-        for (int64_t i = 0; i < n; i++)
-            if (h->agg[l][i] >= 0) x[i] = rnd(x[i] + xc[h->agg[l][i]], pv);
+        if (h->P[l]) {
+            /* b_c = R r, x += P x_c (values rounded to the storage precision) */
+            const ocsr *R = h->R[l], *P = h->P[l];
+            for (int64_t I = 0; I < nc; I++) {
+                double s = 0.0;
+                for (int64_t p = R->rp[I]; p < R->rp[I + 1]; p++) s += rnd(R->v[p], pv) * r[R->ci[p]];
+                bc[I] = rnd(s, pv);
+            }
+            vcycle_level(h, l + 1, bc, xc);
+            for (int64_t i = 0; i < n; i++) {
+                double s = 0.0;
+                for (int64_t p = P->rp[i]; p < P->rp[i + 1]; p++) s += rnd(P->v[p], pv) * xc[P->ci[p]];
+                x[i] = rnd(x[i] + s, pv);
+            }
+        } else {
+            for (int64_t I = 0; I < nc; I++) bc[I] = 0.0;
+            for (int64_t i = 0; i < n; i++)
+                if (h->agg[l][i] >= 0) bc[h->agg[l][i]] += r[i];
+            for (int64_t I = 0; I < nc; I++) bc[I] = rnd(bc[I], pv);
+            vcycle_level(h, l + 1, bc, xc);
+            for (int64_t i = 0; i < n; i++)
+                if (h->agg[l][i] >= 0) x[i] = rnd(x[i] + xc[h->agg[l][i]], pv);
+        }
     }
     for (int s = 0; s < ns; s++) smooth(h, l, b, x, 0);
 }

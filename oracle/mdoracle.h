@@ -66,6 +66,7 @@ typedef struct {
     int prec;            /* 64, 32 (float storage), 16 / 17 (bf16 / fp16 row-scaled levels, float vectors) */
     int lowp_from_level; /* for prec 16/17: first level stored in bf16/fp16 */
     int sweeps;          /* smoother applications before and after the coarse correction */
+    int smoothed;        /* 0 = piecewise-constant P, 1 = smoothed aggregation P */
 } orc_amg_opts;
 
 /* Storage rounding used by the precision emulation: 32 -> float,
@@ -81,6 +82,8 @@ const ocsr *orc_amg_level_A(const orc_amg *h, int l);
 int orc_amg_level_agg(const orc_amg *h, int l, int32_t *out);  /* -1 = not aggregated */
 int orc_amg_level_roots(const orc_amg *h, int l, int8_t *out);
 int orc_amg_level_l1(const orc_amg *h, int l, double *out);
+/* Prolongator of level l (fine rows x coarse columns) when smoothed; NULL otherwise. */
+const ocsr *orc_amg_level_P(const orc_amg *h, int l);
 int orc_amg_coarsest_dense(const orc_amg *h);  /* 1 if the last level is a dense solve */
 /* One V-cycle x = V(b) on level 0. */
 void orc_vcycle(orc_amg *h, const double *b, double *x);

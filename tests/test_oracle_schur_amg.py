@@ -304,3 +304,56 @@ def test_vcycle_two_sweeps(oracle_mod, smoother):
         Sm = (2 * Y @ Y - np.eye(n)) / (2 * s * s - 1)
     S2 = Sm @ Sm
     assert np.max(np.abs(E - S2 @ CG @ S2)) < 1e-12
+
+
+def sa_reference(A, G, agg, nc):
+    """P = P0 - (4/3) D1F^-1 AF P0 written densely: AF keeps the strong
+    off-diagonals and moves the weak ones to the diagonal."""
+    n = A.shape[0]
+    Ad = A.toarray()
+    S = np.zeros((n, n), dtype=bool)
+    S[G.nonzero()] = True
+    AF = np.where(S, Ad, 0.0)
+    weak = ~S & ~np.eye(n, dtype=bool) & (Ad != 0)
+    np.fill_diagonal(AF, np.diag(Ad) + np.where(weak, Ad, 0.0).sum(axis=1))
+    d1 = np.diag(AF) + np.abs(AF - np.diag(np.diag(AF))).sum(axis=1)
+    P0 = np.zeros((n, nc))
+    P0[np.nonzero(agg >= 0)[0], agg[agg >= 0]] = 1.0
+    return P0 - (4.0 / 3.0) * (AF / d1[:, None]) @ P0
+
+
+@pytest.mark.parametrize("make", [lambda: lap2(12), lambda: lap2(10, eps=1e-3), lambda: None])
+def test_smoothed_prolongator_and_galerkin(oracle_mod, make):
+    A = make()
+    if A is None:
+        inst = inputs.random_segments_2d(n=20, n_seg=5)
+        Af, _ = oracle_mod.assemble(inst)
+        A = oracle_mod.schur(*oracle_mod.split(Af, inst.n_m))
+    amg = oracle_mod.AMG(A, n_coarse=8, smoothed=1)
+    assert amg.nlevels >= 2
+    for l in range(amg.nlevels - 1):
+        Al = amg.level_A(l)
+        G = oracle_mod.strength(Al, 0.08)
+        agg = amg.agg(l)
+        nc = amg.level_A(l + 1).shape[0]
+        P = amg.P(l)
+        ref = sa_reference(Al, G, agg, nc)
+        assert np.max(np.abs(P.toarray() - ref)) <= 1e-14 * max(1.0, np.abs(ref).max())
+        Ac = amg.level_A(l + 1).toarray()
+        Pd = P.toarray()
+        cref = Pd.T @ Al.toarray() @ Pd
+        assert np.max(np.abs(Ac - cref)) <= 1e-12 * np.abs(cref).max()
+        np.linalg.cholesky(Ac)
+
+
+def test_smoothed_two_grid_error_propagation(oracle_mod):
+    A = sp.csr_matrix(lap2(8, eps=0.7) + sp.diags(np.linspace(0, 0.3, 64)))
+    amg = oracle_mod.AMG(A, n_coarse=20, smoothed=1)
+    assert amg.nlevels == 2 and amg.coarsest_dense
+    n = 64
+    Ad = A.toarray()
+    E = np.eye(n) - dense_operator(amg.vcycle, n) @ Ad
+    P = amg.P(0).toarray()
+    CG = np.eye(n) - P @ np.linalg.solve(P.T @ Ad @ P, P.T @ Ad)
+    Sm = np.eye(n) - np.diag(1.0 / amg.l1(0)) @ Ad
+    assert np.max(np.abs(E - Sm @ CG @ Sm)) < 1e-12
