@@ -168,6 +168,8 @@ int mds_system_view(mds_system sys, mds_csr blocks[5], const double **b);
 #define MDS_PREC_BF16 16        /* FP32 vectors; levels >= lowp_from_level stored in BF16 with
                                    power-of-two row scales, finer levels in FP32 */
 #define MDS_PREC_FP16 17        /* as MDS_PREC_BF16 with FP16 storage */
+#define MDS_PROLONG_PIECEWISE 0 /* piecewise-constant aggregate injection */
+#define MDS_PROLONG_SMOOTHED 1  /* smoothed aggregation: P = (I - 4/3 D1F^-1 AF) P0 */
 #define MDS_FORMAT_AUTO 0       /* timed choice per level (autotuner) */
 #define MDS_FORMAT_CSR 1
 #define MDS_FORMAT_SELL 2       /* sliced ELLPACK, slice height sell_c, sort window sell_sigma */
@@ -189,6 +191,9 @@ typedef struct {
     int sell_c;              /* SELL slice height: 8, 16 or 32 (32) */
     int sell_sigma;          /* SELL sort window in rows: 1 or a multiple of sell_c up to 1024 (1) */
     int sweeps;              /* smoother applications before and after the coarse correction (1) */
+    int prolongation;        /* MDS_PROLONG_* (MDS_PROLONG_PIECEWISE).  Smoothed: AF keeps the
+                                strong couplings and adds the weak ones to its diagonal, D1F is
+                                its L1 diagonal, A_c = P^T (A P) */
 } mds_setup_opts;
 
 /* Fill `o` with the defaults listed above. */
@@ -212,6 +217,9 @@ int mds_precond_info(mds_precond prec, int block, int *nlevels, int64_t *level_n
  * the last level) and the MIS-2 root flags (int8 [n]). */
 int mds_precond_level(mds_precond prec, int block, int level, mds_csr *A,
                       const int32_t **agg, const int8_t **roots);
+/* Borrowed device view of the smoothed prolongator of a level (fine rows x
+ * coarse columns); P->nnz = 0 and null arrays when the level uses injection. */
+int mds_precond_prolongator(mds_precond prec, int block, int level, mds_csr *P);
 /* z = M r for device FP64 vectors of length n_m + n_f. */
 int mds_precond_apply(mds_ctx ctx, mds_precond prec, const double *r, double *z);
 /* x = V(b): one V-cycle of block 0 or 1 on device FP64 vectors. */

@@ -383,6 +383,7 @@ int mds_setup_opts_default(mds_setup_opts *o) {
     o->sell_c = 32;
     o->sell_sigma = 1;
     o->sweeps = 1;
+    o->prolongation = MDS_PROLONG_PIECEWISE;
     return MDS_OK;
 }
 
@@ -405,6 +406,8 @@ int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_preco
     MDS_REQUIRE(o.sell_sigma == 1 || (o.sell_sigma % o.sell_c == 0 && o.sell_sigma <= 1024), MDS_ERR_INVALID,
                 "sell_sigma must be 1 or a multiple of sell_c up to 1024");
     MDS_REQUIRE(o.sweeps >= 1 && o.sweeps <= 8, MDS_ERR_INVALID, "sweeps must be 1..8");
+    MDS_REQUIRE(o.prolongation == MDS_PROLONG_PIECEWISE || o.prolongation == MDS_PROLONG_SMOOTHED, MDS_ERR_INVALID,
+                "unknown prolongation");
     MDS_REQUIRE(o.kind >= 0 && o.kind <= 2, MDS_ERR_INVALID, "bad preconditioner kind");
     MDS_REQUIRE(o.theta >= 0.0 && o.n_coarse >= 1 && o.n_coarse <= 8192, MDS_ERR_INVALID, "bad AMG options");
     auto *p = new mds_precond_s;
@@ -462,6 +465,15 @@ int mds_precond_level(mds_precond p, int block, int level, mds_csr *A, const int
     if (A) *A = L.A.view();
     if (agg) *agg = L.has_coarse ? L.agg.as<int32_t>() : nullptr;
     if (roots) *roots = L.roots.as<int8_t>();
+    return MDS_OK;
+}
+
+int mds_precond_prolongator(mds_precond p, int block, int level, mds_csr *P) {
+    if (!p || !P || block < 0 || block > 1 || (block == 1 && !p->has_f)) return MDS_ERR_INVALID;
+    const Hierarchy &h = p->h[block];
+    if (level < 0 || level >= (int)h.lv.size()) return MDS_ERR_INVALID;
+    const Level &L = h.lv[level];
+    *P = L.smoothed ? L.P.view() : mds_csr{L.A.nrow, L.nc, 0, nullptr, nullptr, nullptr};
     return MDS_OK;
 }
 

@@ -296,6 +296,9 @@ struct Level {
     Buf dinv;         // [n] 1/l1 in the vector precision
     bool has_coarse = false;
     int64_t nc = 0;
+    bool smoothed = false;    // smoothed prolongator P (and R = P^T) instead of agg injection
+    DCsr P, R;
+    Buf Pv_lp, Rv_lp;         // their values in FP32 (FP32 and lower-precision hierarchies)
     // storage used by the V-cycle
     int vt = VT_F64;  // value type
     int fmt = FMT_CSR;

@@ -369,6 +369,226 @@ __global__ void k_rap(int64_t nc, const int32_t *__restrict__ off, const int32_t
     }
 }
 
+// ---------------------------------------------------------------- smoothed aggregation
+
+constexpr int SA_P_CAP = 64;
+constexpr int SPGEMM_CAP = 512;
+
+// Filtered diagonal aF_ii = a_ii + sum of weak off-diagonals, and the L1
+// diagonal of the filtered matrix d1f_i = aF_ii + sum of strong |a_ij|
+// (both summed in CSR order).
+__global__ void k_sa_diag(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                          const double *__restrict__ v, const int8_t *__restrict__ g, double *__restrict__ afd,
+                          double *__restrict__ d1f) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t pd = find_col(ci, rp[i], rp[i + 1], (int32_t)i);
+    double a = pd >= 0 ? v[pd] : 0.0;
+    for (int32_t p = rp[i]; p < rp[i + 1]; p++)
+        if (ci[p] != i && !g[p]) a = a + v[p];
+    double d = a;
+    for (int32_t p = rp[i]; p < rp[i + 1]; p++)
+        if (ci[p] != i && g[p]) d = d + fabs(v[p]);
+    afd[i] = a;
+    d1f[i] = d;
+}
+
+// Smoothed prolongator P = P0 - (4/3) D1F^-1 AF P0, row i: (agg(i), 1) when
+// aggregated, then for each entry kept in AF, in CSR order, with
+// J = agg(col) >= 0: P_iJ = P_iJ - c_i aF_ij, c_i = (4/3) / d1f_i.
+template <bool FILL>
+__global__ void k_sa_prolongator(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                 const double *__restrict__ v, const int8_t *__restrict__ g,
+                                 const double *__restrict__ afd, const double *__restrict__ d1f,
+                                 const int32_t *__restrict__ agg, int32_t *__restrict__ cnt,
+                                 const int32_t *__restrict__ prp, int32_t *__restrict__ pci, double *__restrict__ pv,
+                                 int *err) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t cols[SA_P_CAP];
+    double acc[SA_P_CAP];
+    int m = 0;
+    if (agg[i] >= 0) {
+        cols[0] = agg[i];
+        acc[0] = 1.0;
+        m = 1;
+    }
+    double c = (4.0 / 3.0) / d1f[i];
+    for (int32_t p = rp[i]; p < rp[i + 1]; p++) {
+        int32_t j = ci[p];
+        double a;
+        if (j == i)
+            a = afd[i];
+        else if (g[p])
+            a = v[p];
+        else
+            continue;
+        int32_t J = agg[j];
+        if (J < 0) continue;
+        int t = 0;
+        while (t < m && cols[t] != J) t++;
+        if (t == m) {
+            if (m >= SA_P_CAP) {
+                atomicOr(err, DERR_CAPACITY);
+                return;
+            }
+            cols[m] = J;
+            acc[m++] = 0.0;
+        }
+        acc[t] = acc[t] - c * a;
+    }
+    if constexpr (!FILL) {
+        cnt[i] = m;
+    } else {
+        for (int a2 = 1; a2 < m; a2++) {
+            int32_t x = cols[a2];
+            double y = acc[a2];
+            int q = a2 - 1;
+            while (q >= 0 && cols[q] > x) {
+                cols[q + 1] = cols[q];
+                acc[q + 1] = acc[q];
+                q--;
+            }
+            cols[q + 1] = x;
+            acc[q + 1] = y;
+        }
+        int32_t o = prp[i];
+        for (int a2 = 0; a2 < m; a2++) {
+            pci[o + a2] = cols[a2];
+            pv[o + a2] = acc[a2];
+        }
+    }
+}
+
+// Transpose: counts per column, scatter with an atomic cursor, then each row
+// sorted by column so that the result is deterministic.
+__global__ void k_tr_count(int64_t nnz, const int32_t *__restrict__ ci, int32_t *__restrict__ cnt) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < nnz) atomicAdd(cnt + ci[p], 1);
+}
+
+__global__ void k_tr_fill(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                          const double *__restrict__ v, const int32_t *__restrict__ trp, int32_t *__restrict__ cur,
+                          int32_t *__restrict__ tci, double *__restrict__ tv) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int32_t p = rp[i]; p < rp[i + 1]; p++) {
+        int32_t J = ci[p];
+        int32_t q = trp[J] + atomicAdd(cur + J, 1);
+        tci[q] = (int32_t)i;
+        tv[q] = v[p];
+    }
+}
+
+__global__ void k_sort_rows(int64_t n, const int32_t *__restrict__ rp, int32_t *__restrict__ ci,
+                            double *__restrict__ v) {
+    int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= n) return;
+    int32_t a = rp[I], e = rp[I + 1];
+    for (int32_t p = a + 1; p < e; p++) {
+        int32_t x = ci[p];
+        double y = v[p];
+        int32_t q = p - 1;
+        while (q >= a && ci[q] > x) {
+            ci[q + 1] = ci[q];
+            v[q + 1] = v[q];
+            q--;
+        }
+        ci[q + 1] = x;
+        v[q + 1] = y;
+    }
+}
+
+// C = X Y, one thread per row: entry (i, k) accumulates x_ij y_jk over row i
+// of X in order and row j of Y in order.
+template <bool FILL>
+__global__ void k_spgemm(int64_t n, mds_csr X, mds_csr Y, int32_t *__restrict__ cnt, const int32_t *__restrict__ crp,
+                         int32_t *__restrict__ cci, double *__restrict__ cv, int *err) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t cols[SPGEMM_CAP];
+    double acc[SPGEMM_CAP];
+    int m = 0;
+    for (int32_t p = X.row_ptr[i]; p < X.row_ptr[i + 1]; p++) {
+        int32_t j = X.col[p];
+        double x = X.val[p];
+        for (int32_t q = Y.row_ptr[j]; q < Y.row_ptr[j + 1]; q++) {
+            int32_t k = Y.col[q];
+            int t = 0;
+            while (t < m && cols[t] != k) t++;
+            if (t == m) {
+                if (m >= SPGEMM_CAP) {
+                    atomicOr(err, DERR_CAPACITY);
+                    return;
+                }
+                cols[m] = k;
+                acc[m++] = 0.0;
+            }
+            acc[t] = acc[t] + x * Y.val[q];
+        }
+    }
+    if constexpr (!FILL) {
+        cnt[i] = m;
+    } else {
+        for (int a2 = 1; a2 < m; a2++) {
+            int32_t xk = cols[a2];
+            double y = acc[a2];
+            int q = a2 - 1;
+            while (q >= 0 && cols[q] > xk) {
+                cols[q + 1] = cols[q];
+                acc[q + 1] = acc[q];
+                q--;
+            }
+            cols[q + 1] = xk;
+            acc[q + 1] = y;
+        }
+        int32_t o = crp[i];
+        for (int a2 = 0; a2 < m; a2++) {
+            cci[o + a2] = cols[a2];
+            cv[o + a2] = acc[a2];
+        }
+    }
+}
+
+static DCsr spgemm_gpu(Ctx &c, const mds_csr &X, const mds_csr &Y) {
+    int64_t n = X.nrow;
+    Buf cnt(&c, sizeof(int32_t) * (size_t)(n + 1));
+    c.clear_err();
+    MDS_LAUNCH(c, KC_NONE, 0, k_spgemm<false>, grid_for(n, 64), 64, 0, n, X, Y, cnt.as<int32_t>(), nullptr, nullptr,
+               nullptr, c.d_err);
+    c.check_err("sparse product (symbolic)");
+    DCsr C;
+    C.nrow = n;
+    C.ncol = Y.ncol;
+    C.rp = Buf(&c, sizeof(int32_t) * (size_t)(n + 1));
+    C.nnz = scan_counts(c, cnt.as<int32_t>(), C.rowp(), n);
+    C.ci = Buf(&c, sizeof(int32_t) * (size_t)(C.nnz > 0 ? C.nnz : 1));
+    C.v = Buf(&c, sizeof(double) * (size_t)(C.nnz > 0 ? C.nnz : 1));
+    MDS_LAUNCH(c, KC_NONE, 0, k_spgemm<true>, grid_for(n, 64), 64, 0, n, X, Y, nullptr, C.rowp(), C.cols(), C.vals(),
+               c.d_err);
+    c.check_err("sparse product");
+    return C;
+}
+
+static DCsr transpose_gpu(Ctx &c, const DCsr &P) {
+    DCsr R;
+    R.nrow = P.ncol;
+    R.ncol = P.nrow;
+    R.nnz = P.nnz;
+    Buf cnt(&c, sizeof(int32_t) * (size_t)(R.nrow + 1));
+    MDS_CUDA(cudaMemsetAsync(cnt.p, 0, cnt.bytes, c.stream));
+    if (P.nnz) MDS_LAUNCH(c, KC_NONE, 0, k_tr_count, grid_for(P.nnz, 256), 256, 0, P.nnz, P.cols(), cnt.as<int32_t>());
+    R.rp = Buf(&c, sizeof(int32_t) * (size_t)(R.nrow + 1));
+    scan_counts(c, cnt.as<int32_t>(), R.rowp(), R.nrow);
+    R.ci = Buf(&c, sizeof(int32_t) * (size_t)(R.nnz > 0 ? R.nnz : 1));
+    R.v = Buf(&c, sizeof(double) * (size_t)(R.nnz > 0 ? R.nnz : 1));
+    MDS_CUDA(cudaMemsetAsync(cnt.p, 0, cnt.bytes, c.stream));
+    MDS_LAUNCH(c, KC_NONE, 0, k_tr_fill, grid_for(P.nrow, 256), 256, 0, P.nrow, P.rowp(), P.cols(), P.vals(),
+               R.rowp(), cnt.as<int32_t>(), R.cols(), R.vals());
+    MDS_LAUNCH(c, KC_NONE, 0, k_sort_rows, grid_for(R.nrow, 128), 128, 0, R.nrow, R.rowp(), R.cols(), R.vals());
+    return R;
+}
+
 // ---------------------------------------------------------------- per-level data
 
 // L1 diagonal a_ii + sum_{j != i} |a_ij| and its reciprocal
@@ -484,6 +704,36 @@ void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h)
                    acnt.as<int32_t>(), L.mem.as<int32_t>());
         MDS_LAUNCH(c, KC_NONE, 0, k_agg_sort, grid_for(nc, 128), 128, 0, nc, L.mem_off.as<int32_t>(),
                    L.mem.as<int32_t>());
+        if (o.prolongation == MDS_PROLONG_SMOOTHED) {
+            Buf afd(&c, sizeof(double) * (size_t)n), d1f(&c, sizeof(double) * (size_t)n);
+            MDS_LAUNCH(c, KC_NONE, 0, k_sa_diag, gr, 256, 0, n, L.A.rowp(), L.A.cols(), L.A.vals(), gf.as<int8_t>(),
+                       afd.as<double>(), d1f.as<double>());
+            Buf pcnt(&c, sizeof(int32_t) * (size_t)(n + 1));
+            c.clear_err();
+            MDS_LAUNCH(c, KC_NONE, 0, k_sa_prolongator<false>, grid_for(n, 128), 128, 0, n, L.A.rowp(), L.A.cols(),
+                       L.A.vals(), gf.as<int8_t>(), afd.as<double>(), d1f.as<double>(), L.agg.as<int32_t>(),
+                       pcnt.as<int32_t>(), nullptr, nullptr, nullptr, c.d_err);
+            c.check_err("smoothed prolongator (symbolic)");
+            L.P.nrow = n;
+            L.P.ncol = nc;
+            L.P.rp = Buf(&c, sizeof(int32_t) * (size_t)(n + 1));
+            L.P.nnz = scan_counts(c, pcnt.as<int32_t>(), L.P.rowp(), n);
+            L.P.ci = Buf(&c, sizeof(int32_t) * (size_t)(L.P.nnz > 0 ? L.P.nnz : 1));
+            L.P.v = Buf(&c, sizeof(double) * (size_t)(L.P.nnz > 0 ? L.P.nnz : 1));
+            MDS_LAUNCH(c, KC_NONE, 0, k_sa_prolongator<true>, grid_for(n, 128), 128, 0, n, L.A.rowp(), L.A.cols(),
+                       L.A.vals(), gf.as<int8_t>(), afd.as<double>(), d1f.as<double>(), L.agg.as<int32_t>(), nullptr,
+                       L.P.rowp(), L.P.cols(), L.P.vals(), c.d_err);
+            c.check_err("smoothed prolongator");
+            L.R = transpose_gpu(c, L.P);
+            DCsr B = spgemm_gpu(c, L.A.view(), L.P.view());
+            DCsr Ac = spgemm_gpu(c, L.R.view(), B.view());
+            L.smoothed = true;
+            L.has_coarse = true;
+            L.nc = nc;
+            h.lv.emplace_back();
+            h.lv.back().A = std::move(Ac);
+            continue;
+        }
         // Galerkin product
         c.clear_err();
         Buf ccnt(&c, sizeof(int32_t) * (size_t)(nc + 1));

@@ -251,6 +251,44 @@ __global__ void k_vc_restrict(int64_t nc, const int32_t *__restrict__ off, const
     stv<XT, NR>(bc, I, s);
 }
 
+// Smoothed aggregation transfers (NR columns): b_c = R r and y += P x_c, one
+// thread per output row, entries in CSR order.
+template <class XT, int NR>
+__global__ void k_sa_restrict(int64_t nc, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                              const XT *__restrict__ v, const XT *__restrict__ r, XT *__restrict__ bc) {
+    int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    Vec<XT, NR> s;
+#pragma unroll
+    for (int c = 0; c < NR; c++) s.v[c] = 0;
+    for (int32_t p = rp[I]; p < rp[I + 1]; p++) {
+        XT a = v[p];
+        Vec<XT, NR> x = ldv<XT, NR>(r, ci[p]);
+#pragma unroll
+        for (int c = 0; c < NR; c++) s.v[c] += a * x.v[c];
+    }
+    stv<XT, NR>(bc, I, s);
+}
+
+template <class XT, int NR>
+__global__ void k_sa_prolong(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                             const XT *__restrict__ v, const XT *__restrict__ xc, XT *__restrict__ y) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Vec<XT, NR> s = ldv<XT, NR>(y, i), t;
+#pragma unroll
+    for (int c = 0; c < NR; c++) t.v[c] = 0;
+    for (int32_t p = rp[i]; p < rp[i + 1]; p++) {
+        XT a = v[p];
+        Vec<XT, NR> x = ldv<XT, NR>(xc, ci[p]);
+#pragma unroll
+        for (int c = 0; c < NR; c++) t.v[c] += a * x.v[c];
+    }
+#pragma unroll
+    for (int c = 0; c < NR; c++) s.v[c] += t.v[c];
+    stv<XT, NR>(y, i, s);
+}
+
 // ---------------------------------------------------------------- host dispatch
 
 template <class VT> static LvlMat<VT> lvl_view(const Level &L) {
@@ -388,7 +426,8 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
     int64_t n = L.A.nrow;
     XT *r = L.r.as<XT>();
     double rbytes = 4.0 * (L.nc + 1) + 4.0 * n + sizeof(XT) * NR * (double)(n + L.nc);
-    bool fused = !std::is_same<XT, double>::value && h.smoother == MDS_SMOOTHER_L1JACOBI && h.sweeps == 1;
+    bool fused = !std::is_same<XT, double>::value && h.smoother == MDS_SMOOTHER_L1JACOBI && h.sweeps == 1 &&
+                 !L.smoothed;
     if (fused) {
         if (L.has_coarse) {
             Level &C = h.lv[l + 1];
@@ -407,11 +446,22 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
     if (L.has_coarse) {
         Level &C = h.lv[l + 1];
         level_op<XT, VK_RESID, NR>(c, L, b, y, nullptr, nullptr, r, 0);
-        MDS_LAUNCH(c, KC_VC_RESTRICT, rbytes, (k_vc_restrict<XT, NR>), grid_for(L.nc, 256), 256, 0, L.nc,
-                   L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r, C.b.as<XT>());
-        vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
-        MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n * NR, (k_vc_prolong<XT, NR>), ew_grid(n * NR), 256, 0, n,
-                   L.agg.as<int32_t>(), C.x.as<XT>(), y);
+        if (L.smoothed) {
+            const XT *rv = std::is_same<XT, double>::value ? (const XT *)L.R.vals() : L.Rv_lp.as<XT>();
+            const XT *pv = std::is_same<XT, double>::value ? (const XT *)L.P.vals() : L.Pv_lp.as<XT>();
+            double tb = (sizeof(XT) + 4.0) * L.R.nnz + 4.0 * (L.nc + 1) + sizeof(XT) * NR * (double)(n + L.nc);
+            MDS_LAUNCH(c, KC_VC_RESTRICT, tb, (k_sa_restrict<XT, NR>), grid_for(L.nc, 256), 256, 0, L.nc, L.R.rowp(),
+                       L.R.cols(), rv, r, C.b.as<XT>());
+            vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
+            MDS_LAUNCH(c, KC_NONE, tb + sizeof(XT) * NR * (double)n, (k_sa_prolong<XT, NR>), grid_for(n, 256), 256, 0,
+                       n, L.P.rowp(), L.P.cols(), pv, C.x.as<XT>(), y);
+        } else {
+            MDS_LAUNCH(c, KC_VC_RESTRICT, rbytes, (k_vc_restrict<XT, NR>), grid_for(L.nc, 256), 256, 0, L.nc,
+                       L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r, C.b.as<XT>());
+            vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
+            MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n * NR, (k_vc_prolong<XT, NR>), ew_grid(n * NR), 256, 0, n,
+                       L.agg.as<int32_t>(), C.x.as<XT>(), y);
+        }
     }
     smooth_stored<XT, NR>(c, h, L, b, y, x);  // x = S(y; b)
 }
@@ -675,6 +725,14 @@ void level_storage(Ctx &c, Hierarchy &h, const mds_setup_opts &o) {
         L.vt = h.prec == 64 ? VT_F64 : !lowp ? VT_F32 : (o.precision == MDS_PREC_BF16 ? VT_BF16 : VT_F16);
         L.G = default_g(L);
         L.fmt = FMT_CSR;
+        if (L.smoothed && h.prec != 64) {
+            L.Pv_lp = Buf(&c, sizeof(float) * (size_t)(L.P.nnz > 0 ? L.P.nnz : 1));
+            L.Rv_lp = Buf(&c, sizeof(float) * (size_t)(L.R.nnz > 0 ? L.R.nnz : 1));
+            MDS_LAUNCH(c, KC_NONE, 0, k_csr_lowp<float>, grid_for(L.P.nrow, 256), 256, 0, L.P.nrow, L.P.rowp(),
+                       L.P.vals(), (const float *)nullptr, L.Pv_lp.as<float>());
+            MDS_LAUNCH(c, KC_NONE, 0, k_csr_lowp<float>, grid_for(L.R.nrow, 256), 256, 0, L.R.nrow, L.R.rowp(),
+                       L.R.vals(), (const float *)nullptr, L.Rv_lp.as<float>());
+        }
         if (l + 1 == h.lv.size() && h.dense) continue;  // applied through the dense inverse
         unsigned gr = grid_for(n, 256);
         if (L.vt == VT_BF16 || L.vt == VT_F16) {

@@ -22,6 +22,7 @@ MDS_OK = 0
 MDS_WARN_NOT_CONVERGED = 1
 PREC = {"fp64": 64, "fp32": 32, "bf16": 16, "fp16": 17}
 FORMAT = {"auto": 0, "csr": 1, "sell": 2}
+PROLONG = {"piecewise": 0, "smoothed": 1}
 SMOOTHER = {"l1jacobi": 0, "chebyshev": 1}
 KIND = {"lower": 0, "diag": 1, "upper": 2}
 KRYLOV = {"fgmres": 0, "pcg": 1}
@@ -49,7 +50,7 @@ class SetupOpts(C.Structure):
     _fields_ = [("theta", C.c_double), ("n_coarse", C.c_int64), ("max_levels", C.c_int),
                 ("stall_ratio", C.c_double), ("seed", C.c_uint64), ("smoother", C.c_int),
                 ("precision", C.c_int), ("lowp_from_level", C.c_int), ("kind", C.c_int), ("format", C.c_int),
-                ("sell_c", C.c_int), ("sell_sigma", C.c_int), ("sweeps", C.c_int)]
+                ("sell_c", C.c_int), ("sell_sigma", C.c_int), ("sweeps", C.c_int), ("prolongation", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -109,6 +110,7 @@ _SIGS = {
                                    C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
     "mds_precond_level": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(Csr), C.POINTER(C.c_void_p),
                                     C.POINTER(C.c_void_p)]),
+    "mds_precond_prolongator": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(Csr)]),
     "mds_precond_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mds_vcycle": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "mds_spmv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -162,6 +164,8 @@ def setup_opts(**kw) -> SetupOpts:
             v = KIND.get(v, v)
         elif k == "format":
             v = FORMAT.get(v, v)
+        elif k == "prolongation":
+            v = PROLONG.get(v, v)
         setattr(o, k, v)
     return o
 
@@ -422,6 +426,12 @@ class Precond:
         ln, lz = (C.c_int64 * 32)(), (C.c_int64 * 32)()
         self.ctx._check(lib().mds_precond_info(self.h, block, C.byref(nl), ln, lz, C.byref(dense)))
         return dict(nlevels=nl.value, n=list(ln)[:nl.value], nnz=list(lz)[:nl.value], dense=bool(dense.value))
+
+    def prolongator_host(self, block: int, level: int):
+        """Smoothed prolongator of a level as scipy CSR (None for injection)."""
+        P = Csr()
+        self.ctx._check(lib().mds_precond_prolongator(self.h, block, level, C.byref(P)))
+        return self.ctx.csr_to_host(P) if P.row_ptr else None
 
     def level_host(self, block: int, level: int):
         A = Csr()

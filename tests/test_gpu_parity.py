@@ -590,3 +590,55 @@ def test_reorthogonalisation_threshold(ctx, oracle_mod, torch_mod, eta2):
     res, Ao, bo, _ = oracle_mod.solve(inst)
     assert code == 0 and abs(st[0].iterations - res.iterations) <= 1
     assert st[0].relres_true <= 1e-8
+
+
+# ---------------------------------------------------------------- smoothed aggregation
+
+@pytest.mark.parametrize("case", ["fixed2d-37", "seg2d-96", "planes3d-13-kf1", "rects3d-18"])
+def test_smoothed_hierarchy_bit_exact(ctx, oracle_mod, case):
+    inst = CASES[case]()
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_, prolongation="smoothed")
+    Ao, _ = oracle_mod.assemble(inst)
+    M = oracle_mod.ML(Ao, inst.n_m, smoothed=1)
+    for block in (0, 1):
+        amg = M.amg(block)
+        assert prec.info(block)["nlevels"] == amg.nlevels
+        for l in range(amg.nlevels):
+            Ag, agg, roots = prec.level_host(block, l)
+            assert same_csr(Ag, amg.level_A(l)), (block, l)
+            Po = amg.P(l)
+            Pg = prec.prolongator_host(block, l)
+            assert (Po is None and Pg is None) or same_csr(Pg, Po), (block, l)
+
+
+@pytest.mark.parametrize("prec_name,tol", [("fp64", 1e-12), ("fp32", 2e-5), ("bf16", 5e-5)])
+def test_smoothed_vcycle_and_solve_parity(ctx, oracle_mod, torch_mod, prec_name, tol):
+    torch = torch_mod
+    inst = CASES["rects3d-18"]()
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_, precision=prec_name, prolongation="smoothed", format="auto")
+    Ao, bo = oracle_mod.assemble(inst)
+    code_p = {"fp64": 64, "fp32": 32, "bf16": 16}[prec_name]
+    M = oracle_mod.ML(Ao, inst.n_m, prec=code_p, smoothed=1)
+    b = np.random.default_rng(4).standard_normal(inst.n_m)
+    x = torch.zeros(inst.n_m, dtype=torch.float64, device="cuda")
+    ctx.vcycle(prec, 0, dev(torch, b), x)
+    xo = M.amg(0).vcycle(b)
+    assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) < tol
+    xs = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+    code, st = ctx.solve(sys_, prec, None, xs)
+    r = oracle_mod.fgmres(Ao, bo[0], M)
+    assert code == 0 and abs(st[0].iterations - r.iterations) <= 1
+
+
+def test_smoothed_batched_multi_rhs(ctx, torch_mod):
+    inst = inputs.random_rects_3d(14, 7, 2, 5, nrhs=4, random_dirichlet=True)
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_, precision="fp32", prolongation="smoothed")
+    x = np.zeros(4 * sys_.N)
+    code, st = ctx.solve(sys_, prec, None, x, nrhs=4)
+    xs = np.zeros(4 * sys_.N)
+    code2, st2 = ctx.solve(sys_, prec, None, xs, nrhs=4, batched=0)
+    assert code == 0 and code2 == 0
+    assert all(abs(a.iterations - b.iterations) <= 1 for a, b in zip(st, st2))
