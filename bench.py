@@ -123,7 +123,7 @@ def run_gpu(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2206_03203_gb300 import build, inputs, mdsolve
+    from paper_2206_03203_gb300 import build, inputs, mdsolve, sharding
 
     rank, local, world = rank_info()
     torch.cuda.set_device(local)
@@ -206,10 +206,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-        t = torch.tensor([t_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
-    solves = len(insts) * args.steps * world
+    # replicas: every rank ran the whole sweep; slowest rank's time, all ranks' solves
+    t_total, solves = sharding.reduce_over_ranks(t_total, len(insts) * args.steps)
     value = solves / t_total
     dof_iter = sum(n * i for n, i in zip(N, iters)) * args.steps * world / t_total
 
@@ -274,6 +272,9 @@ def run_gpu(args):
     }
     if not args.no_variants:
         line["variants"] = variants(ctx, insts, dev_arrays, N, flush)
+        if world > 1:
+            line["variants"]["note"] = ("sweep/3D variants: replicas (rank 0's time); batch: instances "
+                                        "sharded by unknown count, slowest rank's time")
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -307,7 +308,7 @@ def variants(ctx, insts, dev_arrays, N, flush):
     same sweep, the nine-plane 3D instance, and the 256-instance batch."""
     import torch
 
-    from paper_2206_03203_gb300 import inputs
+    from paper_2206_03203_gb300 import inputs, sharding
     out = {}
 
     def sweep(prec):
@@ -340,6 +341,11 @@ def variants(ctx, insts, dev_arrays, N, flush):
         out[f"planes3d_128_kf1e4_{prec}"] = {"solves_per_s": 1.0 / t, "s_per_step": t, "iterations": it,
                                              "N": p3.n_m + p3.n_f}
     batch = inputs.batch_3d(256)
+    world = rank_info()[2]
+    if world > 1:
+        # instances are independent: each rank solves its own share, no exchange
+        shard = sharding.shard_by_work([sharding.instance_work(b.n_m, b.n_f) for b in batch], world)
+        batch = [batch[i] for i in shard[rank_info()[0]]]
 
     def batched():
         s = ctx.assemble_batch(batch)
@@ -352,7 +358,8 @@ def variants(ctx, insts, dev_arrays, N, flush):
         s.close()
         return [q.iterations for q in st], n
     t, (its, n) = _timed(batched, flush)
-    out["batch3d_256inst_x4rhs_bf16"] = {"solves_per_s": len(its) / t, "s_per_step": t, "solves": len(its),
+    t, total_solves = sharding.reduce_over_ranks(t, len(its))
+    out["batch3d_256inst_x4rhs_bf16"] = {"solves_per_s": total_solves / t, "s_per_step": t, "solves": total_solves,
                                          "iterations_min_mean_max": [min(its), float(np.mean(its)), max(its)],
                                          "N_packed": n, "precision": "FP32 fine level, BF16 row-scaled coarse levels, "
                                          "FP64 FGMRES; packed lockstep batch"}

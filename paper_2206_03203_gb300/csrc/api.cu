@@ -1,6 +1,7 @@
 // The C ABI of libmdsolve (include/mdsolve.h): contexts, memory, systems,
 // preconditioner set-up, Algorithm 1, solves and timing.
 #include <cmath>
+#include <cstdlib>
 #include <cstddef>
 #include <cstdio>
 #include <new>
@@ -79,7 +80,9 @@ KTimer::KTimer(Ctx &ctx, int k, double b, double f) : c(ctx), cls(k) {
         if (r.timed) {
             MDS_CUDA(cudaEventCreate(&r.e0));
             MDS_CUDA(cudaEventCreate(&r.e1));
-            cudaEventRecord(r.e0, c.stream);
+            // an external record becomes an event node of the graph, so the
+            // event is written at every replay
+            MDS_CUDA(cudaEventRecordWithFlags(r.e0, c.stream, cudaEventRecordExternal));
         }
         c.capturing->recs.push_back(r);
         grec = (int)c.capturing->recs.size() - 1;
@@ -102,7 +105,8 @@ KTimer::KTimer(Ctx &ctx, int k, double b, double f) : c(ctx), cls(k) {
 
 KTimer::~KTimer() {
     if (rec) cudaEventRecord(rec->e1, c.stream);
-    if (grec >= 0 && c.capturing && c.capturing->recs[grec].timed) cudaEventRecord(c.capturing->recs[grec].e1, c.stream);
+    if (grec >= 0 && c.capturing && c.capturing->recs[grec].timed)
+        cudaEventRecordWithFlags(c.capturing->recs[grec].e1, c.stream, cudaEventRecordExternal);
 }
 
 Graph::~Graph() {
@@ -187,6 +191,8 @@ int mds_create(mds_ctx *out, int device, void *stream, const mds_allocator *allo
         MDS_CUDA(cudaSetDevice(device));
         c->device = device;
         c->owner = h;
+        // MDS_PDL=0 launches without programmatic dependent launch (diagnosis)
+        if (const char *e = std::getenv("MDS_PDL")) c->pdl = std::atoi(e) != 0;
         c->stream = (cudaStream_t)stream;
         if (alloc && alloc->alloc && alloc->free) {
             c->alloc = *alloc;
@@ -411,6 +417,14 @@ int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_preco
     MDS_REQUIRE(o.kind >= 0 && o.kind <= 2, MDS_ERR_INVALID, "bad preconditioner kind");
     MDS_REQUIRE(o.theta >= 0.0 && o.n_coarse >= 1 && o.n_coarse <= 8192, MDS_ERR_INVALID, "bad AMG options");
     auto *p = new mds_precond_s;
+    // set-up kernels write the level data that V-cycle kernels read before
+    // their dependency wait: launch them in plain stream order, and finish
+    // them before returning
+    struct SetupPhase {
+        Ctx *c;
+        explicit SetupPhase(Ctx *cc) : c(cc) { c->setup_phase = true; }
+        ~SetupPhase() { c->setup_phase = false; }
+    } phase(c);
     try {
         p->ctx = c;
         p->sys = sys;
@@ -422,6 +436,7 @@ int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_preco
         int64_t mx = sys->n_m > sys->n_f ? sys->n_m : sys->n_f;
         p->tf64 = Buf(c, sizeof(double) * (size_t)(mx > 0 ? mx : 1));
         p->tf_cap = mx;
+        c->sync();
     } catch (...) {
         delete p;
         throw;

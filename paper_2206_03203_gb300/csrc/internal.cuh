@@ -15,6 +15,27 @@
 
 namespace mds {
 
+// Programmatic dependent launch.  Every kernel of the library is launched
+// with programmatic stream serialisation allowed and starts with this call:
+// it waits until the previous kernel in the stream has completed and its
+// writes are visible, then lets the next kernel's blocks be scheduled while
+// this one runs.  The launch latency of each kernel thus overlaps the tail of
+// its predecessor; the order of memory effects is that of plain stream order.
+__device__ __forceinline__ void mds_pdl_wait() {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+__device__ __forceinline__ void mds_pdl_trigger() {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+__device__ __forceinline__ void mds_pdl_entry() {
+    mds_pdl_wait();
+    mds_pdl_trigger();
+}
+
 struct Error {
     int code;
     std::string msg;
@@ -128,6 +149,8 @@ struct Ctx {
     int dependents = 0;           // live systems and preconditioners made on this context
     bool destroy_requested = false;
     cudaStream_t cap_stream = nullptr;
+    bool pdl = true;              // launch with programmatic stream serialisation
+    bool setup_phase = false;     // set-up writes level data: launch in plain stream order
     // autotuner choices by (rows, nonzeros, value type)
     std::map<std::tuple<int64_t, int64_t, int>, TuneChoice> tune_cache;
 
@@ -175,10 +198,28 @@ struct KTimer {
     ~KTimer();
 };
 
+// Launch on the context stream (programmatic dependent launch when enabled;
+// every kernel begins with mds_pdl_entry()).
+template <typename... KArgs, typename... Args>
+inline void launch_kernel(Ctx &c, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = c.pdl && !c.setup_phase ? 1 : 0;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+    if (e != cudaSuccess) throw Error(MDS_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+}
+
 #define MDS_LAUNCH(ctx, cls, bytes, kern, grid, block, smem, ...)                  \
     do {                                                                           \
         ::mds::KTimer kt_((ctx), (cls), (double)(bytes));                          \
-        kern<<<(grid), (block), (smem), (ctx).stream>>>(__VA_ARGS__);               \
+        ::mds::launch_kernel((ctx), kern, dim3(grid), dim3(block), (size_t)(smem), __VA_ARGS__); \
         (ctx).post_launch();                                                       \
     } while (0)
 
@@ -186,7 +227,7 @@ struct KTimer {
 #define MDS_LAUNCH_F(ctx, cls, bytes, flops, kern, grid, block, smem, ...)         \
     do {                                                                           \
         ::mds::KTimer kt_((ctx), (cls), (double)(bytes), (double)(flops));         \
-        kern<<<(grid), (block), (smem), (ctx).stream>>>(__VA_ARGS__);               \
+        ::mds::launch_kernel((ctx), kern, dim3(grid), dim3(block), (size_t)(smem), __VA_ARGS__); \
         (ctx).post_launch();                                                       \
     } while (0)
 
@@ -292,6 +333,7 @@ struct Level {
     Buf roots;        // int8 [n]
     Buf mem_off;      // int32 [nc+1] members of each next-level aggregate
     Buf mem;          // int32 [#aggregated], ascending within an aggregate
+    int64_t mem_count = 0;  // #aggregated vertices
     Buf l1;           // FP64 [n]
     Buf dinv;         // [n] 1/l1 in the vector precision
     bool has_coarse = false;

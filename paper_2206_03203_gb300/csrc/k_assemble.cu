@@ -35,6 +35,7 @@ __device__ __forceinline__ int64_t cell_id(const GridD &g, const int64_t c[3]) {
 
 __global__ void k_map_scatter(GridD g, const int32_t *__restrict__ axis, const int32_t *__restrict__ pos,
                               int32_t *__restrict__ map, int *err) {
+    mds_pdl_entry();
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.nf) return;
     int d = axis[k];
@@ -173,6 +174,7 @@ __device__ int fracture_entries(const GridD &g, const int32_t *map, const double
 __global__ void k_count(GridD g, const int32_t *__restrict__ map, const double *__restrict__ km,
                         const int32_t *__restrict__ axis, const int32_t *__restrict__ pos,
                         const double *__restrict__ kf, const double *__restrict__ ap, int32_t *__restrict__ cnt) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.N) return;
     Ent row[16];
@@ -189,6 +191,7 @@ __global__ void k_fill(GridD g, const int32_t *__restrict__ map, const double *_
                        const double *__restrict__ kf, const double *__restrict__ ap, int nrhs,
                        const double *__restrict__ pL, const double *__restrict__ pR, const int32_t *__restrict__ rp,
                        int32_t *__restrict__ ci, double *__restrict__ val, double *__restrict__ b) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.N) return;
     Ent row[16];
@@ -242,6 +245,7 @@ __global__ void k_fill(GridD g, const int32_t *__restrict__ map, const double *_
 
 __global__ void k_split_count(int64_t N, int64_t n_m, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                               int32_t *__restrict__ lo, int32_t *__restrict__ hi) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     int32_t a = rp[i], e = rp[i + 1], m = a;
@@ -256,6 +260,7 @@ __global__ void k_split_fill(int64_t N, int64_t n_m, const int32_t *__restrict__
                              int32_t *__restrict__ c_mf, double *__restrict__ v_mf, const int32_t *__restrict__ rp_fm,
                              int32_t *__restrict__ c_fm, double *__restrict__ v_fm, const int32_t *__restrict__ rp_ff,
                              int32_t *__restrict__ c_ff, double *__restrict__ v_ff) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     bool mrow = i < n_m;
@@ -301,6 +306,7 @@ void split_blocks(Ctx &c, const mds_csr &full, int64_t n_m, DCsr blk[4]) {
 
 __global__ void k_merge_count(int64_t N, int64_t n_m, const int32_t *rp0, const int32_t *rp1, const int32_t *rp2,
                               const int32_t *rp3, int32_t *cnt) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     if (i < n_m)
@@ -313,6 +319,7 @@ __global__ void k_merge_count(int64_t N, int64_t n_m, const int32_t *rp0, const 
 
 __global__ void k_merge_fill(int64_t N, int64_t n_m, mds_csr b0, mds_csr b1, mds_csr b2, mds_csr b3,
                              const int32_t *__restrict__ rp, int32_t *__restrict__ ci, double *__restrict__ v) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const mds_csr &L = i < n_m ? b0 : b2;
@@ -351,6 +358,7 @@ void merge_blocks(Ctx &c, const mds_csr blk[4], int64_t n_m, int64_t n_f, DCsr &
 __global__ void k_concat_rows(int64_t nrow, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                               const double *__restrict__ v, int64_t row_off, int64_t nnz_off, int64_t col_off,
                               int32_t *__restrict__ rp_dst, int32_t *__restrict__ ci_dst, double *__restrict__ v_dst) {
+    mds_pdl_entry();
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrow) return;
     rp_dst[row_off + r] = (int32_t)(nnz_off + rp[r]);

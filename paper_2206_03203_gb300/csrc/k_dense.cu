@@ -10,6 +10,7 @@ constexpr int NB = 32;
 
 __global__ void k_densify(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                           const double *__restrict__ v, double *__restrict__ D) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     for (int32_t p = rp[i]; p < rp[i + 1]; p++) D[i * n + ci[p]] = v[p];
@@ -17,6 +18,7 @@ __global__ void k_densify(int64_t n, const int32_t *__restrict__ rp, const int32
 
 // factor the nb x nb diagonal tile at k0 in shared memory
 __global__ void k_chol_diag(double *D, int64_t n, int64_t k0, int nb, int *err) {
+    mds_pdl_entry();
     __shared__ double T[NB][NB + 1];
     __shared__ int bad;
     int t = threadIdx.x;
@@ -53,6 +55,7 @@ __global__ void k_chol_diag(double *D, int64_t n, int64_t k0, int nb, int *err) 
 
 // rows below the panel: L21 = A21 L11^-T, one thread per row
 __global__ void k_chol_trsm(double *D, int64_t n, int64_t k0, int nb) {
+    mds_pdl_entry();
     __shared__ double L[NB][NB + 1];
     for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
         int i = q / nb, j = q % nb;
@@ -72,6 +75,7 @@ __global__ void k_chol_trsm(double *D, int64_t n, int64_t k0, int nb) {
 
 // trailing update A22 -= L21 L21^T on the lower tiles
 __global__ void k_chol_update(double *D, int64_t n, int64_t k0, int nb) {
+    mds_pdl_entry();
     __shared__ double Li[NB][NB + 1], Lj[NB][NB + 1];
     int64_t base = k0 + nb;
     int64_t b = blockIdx.x;
@@ -98,6 +102,7 @@ __global__ void k_chol_update(double *D, int64_t n, int64_t k0, int nb) {
 }
 
 __global__ void k_transpose_lower(const double *__restrict__ L, double *__restrict__ U, int64_t n) {
+    mds_pdl_entry();
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n * n) return;
     int64_t i = q / n, j = q % n;
@@ -107,6 +112,7 @@ __global__ void k_transpose_lower(const double *__restrict__ L, double *__restri
 // column j of A^-1: L y = e_j, then L^T x = y (x overwrites y); one warp per column
 __global__ void k_chol_inverse(const double *__restrict__ L, const double *__restrict__ U, int64_t n,
                                double *__restrict__ X) {
+    mds_pdl_entry();
     extern __shared__ double ys[];
     int wpb = blockDim.x / 32;
     int w = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -161,16 +167,36 @@ void dense_spd_inverse(Ctx &c, const mds_csr &A, Buf &Ainv) {
 }
 
 // y = M x for NR interleaved columns (entry (i, c) at i * NR + c); one warp
-// per row, FP64 accumulation.
+// per row, FP64 accumulation over k = lane, lane + 32, ... then a lane tree.
+// M (the coarsest inverse) is fixed after set-up: each lane loads its first
+// DPRE entries of the row before waiting for the kernel that produced x.
+constexpr int DPRE = 16;
 template <class XT, int NR>
 __global__ void k_dense_apply(const double *__restrict__ M, int64_t n, const XT *__restrict__ x, XT *__restrict__ y) {
     int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     int lane = threadIdx.x % 32;
-    if (row >= n) return;
+    const bool live = row < n;
+    double pm[DPRE];
+#pragma unroll
+    for (int q = 0; q < DPRE; q++) {
+        int64_t k = lane + 32 * (int64_t)q;
+        pm[q] = live && k < n ? M[row * n + k] : 0.0;
+    }
+    mds_pdl_wait();
+    mds_pdl_trigger();
+    if (!live) return;
     double s[NR];
 #pragma unroll
     for (int c = 0; c < NR; c++) s[c] = 0.0;
-    for (int64_t k = lane; k < n; k += 32) {
+#pragma unroll
+    for (int q = 0; q < DPRE; q++) {
+        int64_t k = lane + 32 * (int64_t)q;
+        if (k < n) {
+#pragma unroll
+            for (int c = 0; c < NR; c++) s[c] += pm[q] * (double)x[k * NR + c];
+        }
+    }
+    for (int64_t k = lane + 32 * DPRE; k < n; k += 32) {
         double m = M[row * n + k];
 #pragma unroll
         for (int c = 0; c < NR; c++) s[c] += m * (double)x[k * NR + c];

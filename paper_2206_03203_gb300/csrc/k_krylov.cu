@@ -25,16 +25,49 @@ static unsigned red_grid(int64_t n) {
     return (unsigned)g;
 }
 
-// partial[q][blk] = sum over this block's rows of V[q][i] w[i]; grid.y = q.
-// One dot product per block row keeps registers low; w is re-read once per q
-// and stays resident in L2, V is read once from HBM.
-__global__ void __launch_bounds__(RED_BLOCK) k_mdot(int64_t n, const double *__restrict__ V, int64_t ldv, int nq,
-                                                     const double *__restrict__ w, double *__restrict__ partial,
-                                                     const double *__restrict__ run_flag) {
-    if (run_flag && *run_flag == 0.0) return;
+// True in exactly one block of the grid: the last to arrive after every
+// block has written its partial sums (each thread fences its writes first).
+// That block then reduces the partials in a fixed order, so the result does
+// not depend on which block it is.  The counter is reset for the next launch.
+__device__ __forceinline__ bool last_block(unsigned *counter) {
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned total = gridDim.x * gridDim.y;
+        unsigned t = atomicAdd(counter, 1u);
+        is_last = t == total - 1;
+        if (is_last) *counter = 0u;
+    }
+    __syncthreads();
+    return is_last;
+}
+
+// Sum of v over the block (fixed order: lane tree, then warps ascending);
+// valid in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
     __shared__ double ws[RED_BLOCK / 32];
-    // rows of V are 16-byte aligned (ldv even); w is a row of V
-    const double *v = (int)blockIdx.y < nq ? V + (int64_t)blockIdx.y * ldv : w;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();  // ws may still be read by an earlier call
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < RED_BLOCK / 32; k++) t += ws[k];
+    return t;
+}
+
+// Gram-Schmidt dot products in one launch: out[q] = V[q] . w for q < nq and,
+// when nout = nq + 1, out[nq] = w . w.  Grid (row blocks, nout): block (b, q)
+// writes the partial sum of its rows to partial[q][b]; the last block sums
+// each q's partials.  Rows of V are 16-byte aligned (ldv even); w is a row
+// of V.  w is re-read once per q from L2, V once from HBM.
+__global__ void __launch_bounds__(RED_BLOCK) k_gs_dot(int64_t n, const double *__restrict__ V, int64_t ldv, int nq,
+                                                       const double *__restrict__ w, double *__restrict__ partial,
+                                                       unsigned *__restrict__ counter, double *__restrict__ out) {
+    mds_pdl_entry();
+    const int q = blockIdx.y;
+    const double *v = q < nq ? V + (int64_t)q * ldv : w;
     const double2 *v2 = reinterpret_cast<const double2 *>(v);
     const double2 *w2 = reinterpret_cast<const double2 *>(w);
     int64_t n2 = n >> 1;
@@ -54,33 +87,23 @@ __global__ void __launch_bounds__(RED_BLOCK) k_mdot(int64_t n, const double *__r
         s1 += a.y * b.y;
     }
     if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) s0 += v[n - 1] * w[n - 1];
-    double s = s0 + s1;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int k = 0; k < RED_BLOCK / 32; k++) t += ws[k];
-        partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+    double t = block_sum(s0 + s1);
+    if (threadIdx.x == 0) partial[(int64_t)q * gridDim.x + blockIdx.x] = t;
+    if (!last_block(counter)) return;
+    const int nblk = gridDim.x, lane = threadIdx.x & 31;
+    for (int qq = threadIdx.x >> 5; qq < (int)gridDim.y; qq += RED_BLOCK / 32) {
+        double u = 0.0;
+        for (int b = lane; b < nblk; b += 32) u += __ldcg(partial + (int64_t)qq * nblk + b);
+        for (int o = 16; o > 0; o >>= 1) u += __shfl_down_sync(0xffffffffu, u, o);
+        if (lane == 0) out[qq] = u;
     }
-}
-
-// out[q] (+)= sum_b partial[q][b], one warp per q, fixed order
-__global__ void k_reduce_rows(const double *__restrict__ partial, int nblk, int nq, double *__restrict__ out,
-                              int accumulate, const double *__restrict__ run_flag) {
-    if (run_flag && *run_flag == 0.0) return;
-    int q = blockIdx.x;
-    if (q >= nq) return;
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += 32) s += partial[(int64_t)q * nblk + b];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) out[q] = accumulate ? out[q] + s : s;
 }
 
 // out[q] (+)= sum over blocks of partial[blk][q] (stride QMAX); one warp per q,
 // fixed order
 __global__ void k_reduce_cols(const double *__restrict__ partial, int nblk, int nq, double *__restrict__ out,
                               int accumulate) {
+    mds_pdl_entry();
     int q = blockIdx.x;
     if (q >= nq) return;
     double s = 0.0;
@@ -95,6 +118,7 @@ template <int SIGN, bool VEC>
 __global__ void __launch_bounds__(RED_BLOCK) k_maxpy(int64_t n, const double *__restrict__ V, int64_t ldv, int nq,
                                                       const double *__restrict__ coef, double *__restrict__ w,
                                                       double *__restrict__ partial, const double *__restrict__ run_flag) {
+    mds_pdl_entry();
     if (run_flag && *run_flag == 0.0) return;
     __shared__ double cs[QMAX];
     __shared__ double ws[RED_BLOCK / 32];
@@ -149,6 +173,7 @@ __global__ void __launch_bounds__(RED_BLOCK) k_maxpy(int64_t n, const double *__
 // block partials of sum a_i b_i
 __global__ void __launch_bounds__(RED_BLOCK) k_dot(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
                                                     double *__restrict__ partial) {
+    mds_pdl_entry();
     __shared__ double ws[RED_BLOCK / 32];
     double s = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -164,6 +189,7 @@ __global__ void __launch_bounds__(RED_BLOCK) k_dot(int64_t n, const double *__re
 }
 
 __global__ void k_scale(int64_t n, const double *w, const double *__restrict__ f, double *o) {
+    mds_pdl_entry();
     double s = *f;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         o[i] = w[i] * s;
@@ -172,6 +198,7 @@ __global__ void k_scale(int64_t n, const double *w, const double *__restrict__ f
 // scal[0] = beta = sqrt(normsq); g = (beta, 0, ...); scal[1] = 1/beta
 __global__ void k_cycle_start(const double *__restrict__ normsq, double *__restrict__ g, int m,
                               double *__restrict__ scal) {
+    mds_pdl_entry();
     double beta = sqrt(normsq[0]);
     scal[0] = beta;
     scal[1] = beta > 0.0 ? 1.0 / beta : 0.0;
@@ -179,53 +206,141 @@ __global__ void k_cycle_start(const double *__restrict__ normsq, double *__restr
     for (int q = 1; q <= m; q++) g[q] = 0.0;
 }
 
-// Cancellation test after the first Gram-Schmidt pass: reorthogonalise when
-// ||w_new||^2 < eta2 ||w||^2.  One classical pass leaves an orthogonality
-// error of about eps ||w|| / ||w_new||; eta2 = 1/2 is the DGKS "twice is
-// enough" rule, eta2 = 1e-8 reorthogonalises only when that error could
-// exceed ~1e-12.  flag[0] = 1 runs the second pass; its coefficients start at 0.
-__global__ void k_dgks(const double *__restrict__ nsq_before, const double *__restrict__ nsq_after,
-                       double *__restrict__ flag, double *__restrict__ h2, int nq, double eta2) {
-    double run = (nsq_after[0] < eta2 * nsq_before[0]) ? 1.0 : 0.0;
-    flag[0] = run;
-    for (int q = 0; q < nq; q++) h2[q] = 0.0;
+// Arnoldi column j, by all threads of one block: H[0..j][j] = h (+ h2 after
+// a second pass), H[j+1][j] = hn = ||w||; apply the previous rotations, form
+// the new one, update g.  The column and the rotations are staged in shared
+// memory so that the sequential rotation chain does not wait on global
+// memory.  scal[2] = |g_{j+1}|, scal[3] = 1/H[j+1][j] (0 on breakdown),
+// scal[4] = breakdown flag (1 lucky, 2 non-finite).
+__device__ void arnoldi_column(int j, int m, double *H, const double *h, const double *h2, double hn, double *cs,
+                               double *sn, double *g, double *scal) {
+    __shared__ double col[QMAX + 1], csq[QMAX], snq[QMAX];
+    const int t = threadIdx.x;
+    if (t <= j) col[t] = h2 ? h[t] + h2[t] : h[t];
+    if (t < j) {
+        csq[t] = cs[t];
+        snq[t] = sn[t];
+    }
+    __syncthreads();
+    if (t == 0) {
+        col[j + 1] = hn;
+        for (int q = 0; q < j; q++) {
+            double a = col[q], c = col[q + 1];
+            col[q] = csq[q] * a + snq[q] * c;
+            col[q + 1] = -snq[q] * a + csq[q] * c;
+        }
+        double a = col[j], c = col[j + 1];
+        double rr = sqrt(a * a + c * c);
+        double cj = rr == 0.0 ? 1.0 : a / rr, sj = rr == 0.0 ? 0.0 : c / rr;
+        cs[j] = cj;
+        sn[j] = sj;
+        col[j] = rr;
+        col[j + 1] = 0.0;
+        double gj = g[j];
+        g[j + 1] = -sj * gj;
+        g[j] = cj * gj;
+        scal[2] = fabs(sj * gj);
+        bool bad = !(hn > 0.0) || !isfinite(hn) || !isfinite(rr);
+        scal[3] = bad ? 0.0 : 1.0 / hn;
+        scal[4] = !isfinite(hn) || !isfinite(rr) ? 2.0 : (hn == 0.0 ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    if (t <= j + 1) H[t * m + j] = col[t];
 }
 
-// Arnoldi column j: H[0..j][j] = h1 + h2, H[j+1][j] = ||w|| (after the second
-// pass when it ran); apply the previous rotations, form the new one, update
-// g.  scal[2] = |g_{j+1}|, scal[3] = 1/H[j+1][j] (0 on breakdown), scal[4] =
-// breakdown flag (1 lucky, 2 non-finite).
-__global__ void k_arnoldi(int j, int m, double *__restrict__ H, const double *__restrict__ h,
-                          const double *__restrict__ h2, const double *__restrict__ nsq1,
-                          const double *__restrict__ nsq2, const double *__restrict__ flag, double *__restrict__ cs,
-                          double *__restrict__ sn, double *__restrict__ g, double *__restrict__ scal) {
-    bool two = flag[0] != 0.0;
-    for (int q = 0; q <= j; q++) H[q * m + j] = two ? h[q] + h2[q] : h[q];
-    double hn = sqrt(two ? nsq2[0] : nsq1[0]);
-    H[(j + 1) * m + j] = hn;
-    for (int q = 0; q < j; q++) {
-        double a = H[q * m + j], c = H[(q + 1) * m + j];
-        H[q * m + j] = cs[q] * a + sn[q] * c;
-        H[(q + 1) * m + j] = -sn[q] * a + cs[q] * c;
+// One Arnoldi step after the products V^T w are known.
+struct GsStep {
+    int j, m, pass;  // Arnoldi column, restart length, Gram-Schmidt pass (1 or 2)
+    double eta2;     // second-pass threshold on ||w_new||^2 / ||w||^2
+    double *H, *h, *cs, *sn, *g, *scal;
+};
+
+// w -= sum_q coef_q V[q] (unrolled over q so several rows load at once) and
+// ||w||^2; the last block finishes the step.  Pass 1 (coef = h, h[nq] =
+// ||w||^2 before the update): when ||w_new||^2 < eta2 ||w||^2 one classical
+// pass may have left an orthogonality error of order eps ||w|| / ||w_new||,
+// so scal[5] = 1 asks the host for a second pass; otherwise the Arnoldi
+// column is formed and scal[5] = 0.  Pass 2 (coef = h2): the column uses
+// h + h2 and the norm after the second pass.  eta2 = 1/2 is the DGKS "twice
+// is enough" rule; eta2 >= 1 always runs two passes.
+__global__ void __launch_bounds__(RED_BLOCK) k_gs_update(int64_t n, const double *__restrict__ V, int64_t ldv, int nq,
+                                                          const double *__restrict__ coef, double *__restrict__ w,
+                                                          double *__restrict__ partial, unsigned *__restrict__ counter,
+                                                          GsStep st) {
+    mds_pdl_entry();
+    __shared__ double cq[QMAX];
+    if (threadIdx.x < QMAX) cq[threadIdx.x] = (int)threadIdx.x < nq ? coef[threadIdx.x] : 0.0;
+    __syncthreads();
+    double nrm = 0.0;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t n2 = n >> 1;
+    double2 *w2 = reinterpret_cast<double2 *>(w);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+        double s0 = 0.0, s1 = 0.0;
+        int q = 0;
+        for (; q + 4 <= nq; q += 4) {
+            double2 a0 = reinterpret_cast<const double2 *>(V + (int64_t)q * ldv)[i];
+            double2 a1 = reinterpret_cast<const double2 *>(V + (int64_t)(q + 1) * ldv)[i];
+            double2 a2 = reinterpret_cast<const double2 *>(V + (int64_t)(q + 2) * ldv)[i];
+            double2 a3 = reinterpret_cast<const double2 *>(V + (int64_t)(q + 3) * ldv)[i];
+            s0 += cq[q] * a0.x;
+            s1 += cq[q] * a0.y;
+            s0 += cq[q + 1] * a1.x;
+            s1 += cq[q + 1] * a1.y;
+            s0 += cq[q + 2] * a2.x;
+            s1 += cq[q + 2] * a2.y;
+            s0 += cq[q + 3] * a3.x;
+            s1 += cq[q + 3] * a3.y;
+        }
+        for (; q < nq; q++) {
+            double2 a = reinterpret_cast<const double2 *>(V + (int64_t)q * ldv)[i];
+            s0 += cq[q] * a.x;
+            s1 += cq[q] * a.y;
+        }
+        double2 x = w2[i];
+        x.x -= s0;
+        x.y -= s1;
+        w2[i] = x;
+        nrm += x.x * x.x + x.y * x.y;
     }
-    double a = H[j * m + j], c = H[(j + 1) * m + j];
-    double rr = sqrt(a * a + c * c);
-    cs[j] = rr == 0.0 ? 1.0 : a / rr;
-    sn[j] = rr == 0.0 ? 0.0 : c / rr;
-    H[j * m + j] = rr;
-    H[(j + 1) * m + j] = 0.0;
-    g[j + 1] = -sn[j] * g[j];
-    g[j] = cs[j] * g[j];
-    scal[2] = fabs(g[j + 1]);
-    bool bad = !(hn > 0.0) || !isfinite(hn) || !isfinite(rr);
-    scal[3] = bad ? 0.0 : 1.0 / hn;
-    scal[4] = !isfinite(hn) || !isfinite(rr) ? 2.0 : (hn == 0.0 ? 1.0 : 0.0);
-    scal[5] += two ? 1.0 : 0.0;
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < nq; q++) s += cq[q] * V[(int64_t)q * ldv + n - 1];
+        double x = w[n - 1] - s;
+        w[n - 1] = x;
+        nrm += x * x;
+    }
+    double t = block_sum(nrm);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    if (!last_block(counter)) return;
+    double u = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += RED_BLOCK) u += __ldcg(partial + b);
+    __shared__ double nsq_s;
+    __shared__ int second;
+    double nsq = block_sum(u);
+    if (threadIdx.x == 0) {
+        nsq_s = nsq;
+        second = st.pass == 1 && nsq < st.eta2 * st.h[nq];
+        st.scal[5] = second ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    if (second) return;
+    arnoldi_column(st.j, st.m, st.H, st.h, st.pass == 2 ? coef : nullptr, sqrt(nsq_s), st.cs, st.sn, st.g, st.scal);
+}
+
+// v_{j+1} = w / H[j+1][j], unless a second Gram-Schmidt pass is pending
+__global__ void k_scale_step(int64_t n, double *__restrict__ w, const double *__restrict__ scal) {
+    mds_pdl_entry();
+    if (scal[5] != 0.0) return;
+    double s = scal[3];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        w[i] *= s;
 }
 
 // upper-triangular solve H y = g (k columns)
 __global__ void k_backsolve(int k, int m, const double *__restrict__ H, const double *__restrict__ g,
                             double *__restrict__ y) {
+    mds_pdl_entry();
     for (int q = k - 1; q >= 0; q--) {
         double s = g[q];
         for (int p = q + 1; p < k; p++) s -= H[q * m + p] * y[p];
@@ -236,6 +351,7 @@ __global__ void k_backsolve(int k, int m, const double *__restrict__ H, const do
 // PCG helpers
 __global__ void k_pcg_p(int64_t n, const double *__restrict__ z, double *__restrict__ p, const double *__restrict__ sc,
                         int first) {
+    mds_pdl_entry();
     double beta = first ? 0.0 : sc[0] / sc[1];  // rz_new / rz
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = first ? z[i] : z[i] + beta * p[i];
@@ -244,6 +360,7 @@ __global__ void k_pcg_p(int64_t n, const double *__restrict__ z, double *__restr
 __global__ void __launch_bounds__(RED_BLOCK) k_pcg_xr(int64_t n, double *__restrict__ x, double *__restrict__ r,
                                                        const double *__restrict__ p, const double *__restrict__ q,
                                                        const double *__restrict__ sc, double *__restrict__ partial) {
+    mds_pdl_entry();
     __shared__ double ws[RED_BLOCK / 32];
     double alpha = sc[0] / sc[2];  // rz / (p, q)
     double s = 0.0;
@@ -263,22 +380,42 @@ __global__ void __launch_bounds__(RED_BLOCK) k_pcg_xr(int64_t n, double *__restr
     }
 }
 
-__global__ void k_copy1(const double *__restrict__ a, double *__restrict__ b) { *b = *a; }
+__global__ void k_copy1(const double *__restrict__ a, double *__restrict__ b) { mds_pdl_entry(); *b = *a; }
 
 // ---------------------------------------------------------------- host side
 
 struct Red {
     Buf partial;
     double *pp = nullptr;  // the partials buffer in use
-    unsigned grid = 1;   // blocks of the single-vector reductions
-    unsigned mgrid = 1;  // row blocks per basis vector in k_mdot
+    unsigned grid = 1;     // blocks of the single-vector reductions
+    int slots = 1;         // resident blocks of k_gs_dot on the device
+    unsigned ugrid = 1;    // blocks of k_gs_update: at most one wave
 };
 
-static unsigned mdot_grid(int64_t n) {
-    int64_t g = (n + RED_BLOCK * 16 - 1) / (RED_BLOCK * 16);
+// Partial sums one k_gs_dot launch may write (row blocks x outputs).
+constexpr int GS_MAX_BLOCKS = 4096;
+
+// Row blocks per output of k_gs_dot for nout outputs: one wave of resident
+// blocks in total (equal work per block, and the fewest per-block
+// reductions, which cost FP64 operations), at least two elements per thread.
+static unsigned gs_dot_grid(const Red &R, int64_t n, int nout) {
+    int64_t g = (int64_t)R.slots / nout;
+    int64_t cap = (n + 2 * RED_BLOCK - 1) / (2 * RED_BLOCK);
+    if (g > cap) g = cap;
+    if (g * nout > GS_MAX_BLOCKS) g = GS_MAX_BLOCKS / nout;
     if (g < 1) g = 1;
-    if (g > 1024) g = 1024;
     return (unsigned)g;
+}
+
+static void gs_grids(Ctx &c, Red &R, int64_t n) {
+    int sms = 0, occ = 0, uocc = 0;
+    MDS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device));
+    MDS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gs_dot, RED_BLOCK, 0));
+    MDS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&uocc, k_gs_update, RED_BLOCK, 0));
+    int s = sms * (occ > 0 ? occ : 1);
+    R.slots = s > GS_MAX_BLOCKS / 2 - QMAX ? GS_MAX_BLOCKS / 2 - QMAX : s;
+    unsigned us = (unsigned)(sms * (uocc > 0 ? uocc : 1));
+    R.ugrid = red_grid(n) < us ? red_grid(n) : us;
 }
 
 static void dot_dev(Ctx &c, Red &R, int64_t n, const double *a, const double *b, double *out) {
@@ -290,19 +427,22 @@ static size_t round256(size_t doubles) { return (doubles + 31) / 32 * 32; }
 
 // Workspace parts in order: reduction partials, V ((m+1) rows), Z (m rows),
 // Hessenberg ((m+1) x m), small scalars (256).
+static size_t partial_doubles(int64_t n) {
+    size_t a = (size_t)red_grid(n) * QMAX;
+    return a > (size_t)GS_MAX_BLOCKS ? a : (size_t)GS_MAX_BLOCKS;
+}
+
 size_t fgmres_workspace_doubles(int64_t n, int m) {
     const int64_t ld = (n + 63) / 64 * 64;
-    unsigned g = red_grid(n) > mdot_grid(n) ? red_grid(n) : mdot_grid(n);
-    return round256((size_t)g * QMAX) + round256((size_t)(m + 1) * ld) + round256((size_t)m * ld) +
+    return round256(partial_doubles(n)) + round256((size_t)(m + 1) * ld) + round256((size_t)m * ld) +
            round256((size_t)(m + 1) * m) + 256;
 }
 
 FgmresWorkspace fgmres_workspace_carve(double *base, int64_t n, int m) {
     const int64_t ld = (n + 63) / 64 * 64;
-    unsigned g = red_grid(n) > mdot_grid(n) ? red_grid(n) : mdot_grid(n);
     FgmresWorkspace w;
     w.partial = base;
-    w.V = w.partial + round256((size_t)g * QMAX);
+    w.V = w.partial + round256(partial_doubles(n));
     w.Z = w.V + round256((size_t)(m + 1) * ld);
     w.H = w.Z + round256((size_t)m * ld);
     w.small = w.H + round256((size_t)(m + 1) * m);
@@ -315,7 +455,7 @@ KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, 
     const int m = o.restart < 1 ? 1 : (o.restart > QMAX - 1 ? QMAX - 1 : o.restart);
     Red R;
     R.grid = red_grid(n);
-    R.mgrid = mdot_grid(n);
+    gs_grids(c, R, n);
     // basis rows padded to 64 elements: 16-byte aligned rows for vector loads
     const int64_t ld = (n + 63) / 64 * 64;
     Buf V, Z, H, small;
@@ -327,7 +467,7 @@ KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, 
         Hp = ws->H;
         d = ws->small;
     } else {
-        R.partial = Buf(&c, sizeof(double) * (size_t)(R.grid > R.mgrid ? R.grid : R.mgrid) * QMAX);
+        R.partial = Buf(&c, sizeof(double) * partial_doubles(n));
         V = Buf(&c, sizeof(double) * (size_t)(m + 1) * (size_t)ld);
         Z = Buf(&c, sizeof(double) * (size_t)m * (size_t)ld);
         H = Buf(&c, sizeof(double) * (size_t)(m + 1) * m);
@@ -341,9 +481,12 @@ KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, 
     R.pp = partial;
     MDS_REQUIRE(partial && Vp && Zp && Hp && d, MDS_ERR_INVALID, "FGMRES workspace pointer missing");
     MDS_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * 256, c.stream));
-    // cs, sn, g, y, h (first CGS pass), h + 32 (second pass), scalars, norms
+    // cs, sn, g, y, h (first Gram-Schmidt pass, h[nq] = ||w||^2), h2 (second
+    // pass), scal (step scalars; scal[5] = second pass pending), nsq, and two
+    // block-arrival counters of the fused reductions
     double *cs = d, *sn = d + 32, *g = d + 64, *y = d + 96, *h = d + 128, *h2 = d + 160, *scal = d + 192,
-           *nsq = d + 224, *nsq2 = d + 225, *dflag = d + 226;
+           *nsq = d + 224;
+    unsigned *cnt = reinterpret_cast<unsigned *>(d + 240);
     // ||b||
     dot_dev(c, R, n, b, b, nsq);
     double bn = std::sqrt(c.read(nsq));
@@ -352,35 +495,32 @@ KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, 
         return res;
     }
     if (bn == 0.0) bn = 1.0;
-    // One Arnoldi step j: z_j = M v_j, w = A z_j, Gram-Schmidt, Givens, and
-    // the step's scalars copied to pinned host memory.  Captured as a CUDA
-    // graph on first use and replayed on later restart cycles.
-    auto body = [&](int j) {
-        double *vj = Vp + (size_t)j * ld, *zj = Zp + (size_t)j * ld, *w = Vp + (size_t)(j + 1) * ld;
-        M(vj, zj);
-        spmv_f64(c, A, zj, w, KC_SPMV);
-        // classical Gram-Schmidt: h = V^T w (and ||w||^2), w -= V h, ||w||^2;
-        // a second pass only when the DGKS test asks for it (device flag)
+    auto gs_pass = [&](int j, int pass) {
+        double *w = Vp + (size_t)(j + 1) * ld;
         int nq = j + 1;
-        double fl = 2.0 * (double)n * nq;
-        MDS_LAUNCH_F(c, KC_GS_DOT, 8.0 * n * (nq + 1), fl + 2.0 * n, k_mdot, dim3(R.mgrid, nq + 1), RED_BLOCK, 0, n,
-                     Vp, ld, nq, w, R.pp, (const double *)nullptr);
-        MDS_LAUNCH(c, KC_NONE, 0, k_reduce_rows, nq + 1, 32, 0, R.pp, (int)R.mgrid, nq + 1, h, 0,
-                   (const double *)nullptr);
-        MDS_LAUNCH_F(c, KC_GS_AXPY, 8.0 * n * (nq + 2), fl + 2.0 * n, (k_maxpy<-1, true>), R.grid, RED_BLOCK, 0, n,
-                     Vp, ld, nq, h, w, R.pp, (const double *)nullptr);
-        MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.pp, (int)R.grid, 1, nsq, 0);
-        MDS_LAUNCH(c, KC_NONE, 0, k_dgks, 1, 1, 0, h + nq, nsq, dflag, h2, nq, o.reorth_eta2);
-        MDS_LAUNCH_F(c, KC_GS_DOT, 8.0 * n * (nq + 1), fl, k_mdot, dim3(R.mgrid, nq), RED_BLOCK, 0, n, Vp, ld, nq, w,
-                     R.pp, (const double *)dflag);
-        MDS_LAUNCH(c, KC_NONE, 0, k_reduce_rows, nq, 32, 0, R.pp, (int)R.mgrid, nq, h2, 0,
-                   (const double *)dflag);
-        MDS_LAUNCH_F(c, KC_GS_AXPY, 8.0 * n * (nq + 2), fl + 2.0 * n, (k_maxpy<-1, true>), R.grid, RED_BLOCK, 0, n,
-                     Vp, ld, nq, h2, w, R.pp, (const double *)dflag);
-        MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.pp, (int)R.grid, 1, nsq2, 0);
-        MDS_LAUNCH(c, KC_NONE, 0, k_arnoldi, 1, 1, 0, j, m, Hp, h, h2, nsq, nsq2, dflag, cs, sn, g, scal);
-        MDS_LAUNCH(c, KC_NONE, 16.0 * n, k_scale, red_grid(n), RED_BLOCK, 0, n, w, scal + 3, w);
-        MDS_CUDA(cudaMemcpyAsync(c.h_pin, scal, 5 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        int nout = pass == 1 ? nq + 1 : nq;
+        double *hh = pass == 1 ? h : h2;
+        unsigned mg = gs_dot_grid(R, n, nout);
+        GsStep st{j, m, pass, o.reorth_eta2, Hp, h, cs, sn, g, scal};
+        int cls_dot = pass == 1 ? KC_GS_DOT : KC_NONE, cls_upd = pass == 1 ? KC_GS_AXPY : KC_NONE;
+        MDS_LAUNCH_F(c, cls_dot, 8.0 * n * (nq + 1), 2.0 * n * nout, k_gs_dot, dim3(mg, nout), RED_BLOCK, 0, n, Vp,
+                     ld, nq, w, R.pp, cnt, hh);
+        MDS_LAUNCH_F(c, cls_upd, 8.0 * n * (nq + 2), 2.0 * n * (nq + 1), k_gs_update, R.ugrid, RED_BLOCK, 0, n, Vp, ld,
+                     nq, hh, w, R.pp, cnt + 1, st);
+        MDS_LAUNCH(c, KC_NONE, 16.0 * n, k_scale_step, red_grid(n), RED_BLOCK, 0, n, w, scal);
+        MDS_CUDA(cudaMemcpyAsync(c.h_pin, scal, 6 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    };
+    // One Arnoldi step j: z_j = M v_j, w = A z_j, one classical Gram-Schmidt
+    // pass with its reductions, cancellation test and Givens update fused into
+    // two launches, the scaled v_{j+1}, and the step's scalars copied to
+    // pinned host memory.  Captured as a CUDA graph on first use and replayed
+    // on later restart cycles.  A second pass, when the cancellation test asks
+    // for it, is launched directly by the host (rare).
+    auto body = [&](int j) {
+        double *vj = Vp + (size_t)j * ld, *zj = Zp + (size_t)j * ld;
+        M(vj, zj);
+        spmv_f64(c, A, zj, Vp + (size_t)(j + 1) * ld, KC_SPMV);
+        gs_pass(j, 1);
     };
     std::vector<std::unique_ptr<Graph>> graphs(m);
     bool graphs_ok = o.graphs != 0;
@@ -428,8 +568,13 @@ KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, 
         int flag = 0;
         for (int j = 0; j < m; j++) {
             run_step(j);
-            double sv[5];
+            double sv[6];
             std::memcpy(sv, c.h_pin, sizeof sv);
+            if (sv[5] != 0.0) {
+                gs_pass(j, 2);
+                c.sync();
+                std::memcpy(sv, c.h_pin, sizeof sv);
+            }
             it++;
             est = sv[2] / bn;
             kdone = j + 1;
@@ -584,6 +729,7 @@ template <int NR>
 __global__ void __launch_bounds__(RED_BLOCK) k_bdot(const Chunk *__restrict__ ch, int nchunk, const double *__restrict__ V,
                                                      int64_t ldq, int nq, const double *__restrict__ W,
                                                      double *__restrict__ partial) {
+    mds_pdl_entry();
     __shared__ double ws[RED_BLOCK / 32][NR];
     Chunk k = ch[blockIdx.x];
     int q = blockIdx.y;
@@ -614,6 +760,7 @@ __global__ void __launch_bounds__(RED_BLOCK) k_bdot(const Chunk *__restrict__ ch
 __global__ void k_breduce(const double *__restrict__ partial, int nchunk, int nq, int NR,
                           const int32_t *__restrict__ ioff, const int32_t *__restrict__ ichunk, int P,
                           double *__restrict__ out, int accumulate) {
+    mds_pdl_entry();
     int q = blockIdx.y;
     int p = blockIdx.x;
     if (p >= P || q >= nq) return;
@@ -631,6 +778,7 @@ template <int NR, int SIGN>
 __global__ void __launch_bounds__(RED_BLOCK) k_bmaxpy(const Chunk *__restrict__ ch, const double *__restrict__ V,
                                                        int64_t ldq, int nq, const double *__restrict__ coef,
                                                        double *__restrict__ W, double *__restrict__ partial) {
+    mds_pdl_entry();
     __shared__ double cs[NR][32];
     __shared__ double ws[RED_BLOCK / 32][NR];
     Chunk k = ch[blockIdx.x];
@@ -681,6 +829,7 @@ __global__ void __launch_bounds__(RED_BLOCK) k_bmaxpy(const Chunk *__restrict__ 
 template <int NR>
 __global__ void k_bscale(const Chunk *__restrict__ ch, double *__restrict__ W, const double *__restrict__ sc, int slot,
                          const int8_t *__restrict__ active) {
+    mds_pdl_entry();
     Chunk k = ch[blockIdx.x];
     double f[NR];
 #pragma unroll
@@ -696,6 +845,7 @@ __global__ void k_bscale(const Chunk *__restrict__ ch, double *__restrict__ W, c
 // per problem: beta = sqrt(nsq), g = (beta, 0, ...), sc[1] = 1/beta
 __global__ void k_bcycle_start(int P, const double *__restrict__ nsq, int m, double *__restrict__ g,
                                double *__restrict__ sc) {
+    mds_pdl_entry();
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
     double beta = sqrt(nsq[(int64_t)p * 32]);
@@ -711,6 +861,7 @@ __global__ void k_barnoldi(int P, int j, int m, const int8_t *__restrict__ activ
                            const double *__restrict__ h1, const double *__restrict__ h2,
                            const double *__restrict__ nsq, double *__restrict__ cs, double *__restrict__ sn,
                            double *__restrict__ g, double *__restrict__ sc) {
+    mds_pdl_entry();
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P || !active[p]) return;
     double *Hp = H + (int64_t)p * (m + 1) * m;
@@ -741,6 +892,7 @@ __global__ void k_barnoldi(int P, int j, int m, const int8_t *__restrict__ activ
 // per problem: solve H y = g with its own step count kdone[p]; y zero beyond
 __global__ void k_bbacksolve(int P, const int32_t *__restrict__ kdone, int m, const double *__restrict__ H,
                              const double *__restrict__ g, double *__restrict__ y) {
+    mds_pdl_entry();
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
     int k = kdone[p];
@@ -758,11 +910,13 @@ __global__ void k_bbacksolve(int P, const int32_t *__restrict__ kdone, int m, co
 // interleave NR columns of a column-major [ncol][N] array / scatter back
 template <int NR>
 __global__ void k_to_interleaved(int64_t N, const double *__restrict__ src, int c0, double *__restrict__ dst) {
+    mds_pdl_entry();
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N * NR; e += (int64_t)gridDim.x * blockDim.x)
         dst[e] = src[(int64_t)(c0 + e % NR) * N + e / NR];
 }
 template <int NR>
 __global__ void k_from_interleaved(int64_t N, const double *__restrict__ src, int c0, double *__restrict__ dst) {
+    mds_pdl_entry();
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N * NR; e += (int64_t)gridDim.x * blockDim.x)
         dst[(int64_t)(c0 + e % NR) * N + e / NR] = src[e];
 }

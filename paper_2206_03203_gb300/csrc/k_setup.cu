@@ -28,6 +28,7 @@ __device__ __forceinline__ int32_t find_col(const int32_t *ci, int32_t a, int32_
 
 __global__ void k_diag(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                        const double *__restrict__ v, double *__restrict__ d, int need_nonzero, int *err) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t p = find_col(ci, rp[i], rp[i + 1], (int32_t)i);
@@ -44,6 +45,7 @@ template <bool FILL>
 __global__ void k_schur(int64_t nm, mds_csr Amm, mds_csr Amf, mds_csr Afm, const double *__restrict__ dk,
                         int32_t *__restrict__ cnt, const int32_t *__restrict__ rp, int32_t *__restrict__ ci,
                         double *__restrict__ val, int *err) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nm) return;
     int32_t cols[SCHUR_CAP];
@@ -131,6 +133,7 @@ DCsr schur_build(Ctx &c, const mds_csr &Amm, const mds_csr &Amf, const mds_csr &
 __global__ void k_strength(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                            const double *__restrict__ v, const double *__restrict__ dg, double th2,
                            int8_t *__restrict__ g, int32_t *__restrict__ deg) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int cnt = 0;
@@ -170,6 +173,7 @@ __device__ __forceinline__ uint64_t mis_key1(uint64_t lkey, int64_t i) {
 }
 
 __global__ void k_mis_init(int64_t n, const int32_t *__restrict__ deg, int8_t *__restrict__ state) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) state[i] = deg[i] == 0 ? 2 : 0;
 }
@@ -178,6 +182,7 @@ __global__ void k_mis_init(int64_t n, const int32_t *__restrict__ deg, int8_t *_
 __global__ void k_mis_max1(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                            const int8_t *__restrict__ g, const int8_t *__restrict__ state, uint64_t lkey,
                            uint64_t *__restrict__ m1) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint64_t m = state[i] == 0 ? mis_key1(lkey, i) : 0;
@@ -197,6 +202,7 @@ __global__ void k_mis_max1(int64_t n, const int32_t *__restrict__ rp, const int3
 __global__ void k_mis_select(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                              const int8_t *__restrict__ g, const uint64_t *__restrict__ m1, uint64_t lkey,
                              int8_t *__restrict__ state) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || state[i] != 0) return;
     uint64_t m = m1[i];
@@ -211,6 +217,7 @@ __global__ void k_mis_select(int64_t n, const int32_t *__restrict__ rp, const in
 __global__ void k_mis_near_root(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                 const int8_t *__restrict__ g, const int8_t *__restrict__ state,
                                 int8_t *__restrict__ e1) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int8_t e = state[i] == 1;
@@ -222,6 +229,7 @@ __global__ void k_mis_near_root(int64_t n, const int32_t *__restrict__ rp, const
 __global__ void k_mis_exclude(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                               const int8_t *__restrict__ g, const int8_t *__restrict__ e1, int8_t *__restrict__ state,
                               int32_t *__restrict__ undecided) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || state[i] != 0) return;
     bool ex = e1[i];
@@ -237,6 +245,7 @@ __global__ void k_mis_exclude(int64_t n, const int32_t *__restrict__ rp, const i
 
 __global__ void k_root_flags(int64_t n, const int8_t *__restrict__ state, int8_t *__restrict__ roots,
                              int32_t *__restrict__ flag) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int8_t r = state[i] == 1;
@@ -247,6 +256,7 @@ __global__ void k_root_flags(int64_t n, const int8_t *__restrict__ state, int8_t
 __global__ void k_agg_first(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                             const int8_t *__restrict__ g, const int8_t *__restrict__ roots,
                             const int32_t *__restrict__ rootid, int32_t *__restrict__ first) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t f = -1;
@@ -263,6 +273,7 @@ __global__ void k_agg_second(int64_t n, const int32_t *__restrict__ rp, const in
                              const double *__restrict__ v, const int8_t *__restrict__ g,
                              const int8_t *__restrict__ roots, const int32_t *__restrict__ deg,
                              const int32_t *__restrict__ first, int32_t *__restrict__ agg) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (first[i] >= 0 || deg[i] == 0) {
@@ -287,12 +298,14 @@ __global__ void k_agg_second(int64_t n, const int32_t *__restrict__ rp, const in
 // ---------------------------------------------------------------- Galerkin P^T A P
 
 __global__ void k_agg_count(int64_t n, const int32_t *__restrict__ agg, int32_t *__restrict__ cnt) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && agg[i] >= 0) atomicAdd(cnt + agg[i], 1);
 }
 
 __global__ void k_agg_scatter(int64_t n, const int32_t *__restrict__ agg, const int32_t *__restrict__ off,
                               int32_t *__restrict__ cursor, int32_t *__restrict__ mem) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && agg[i] >= 0) {
         int32_t q = atomicAdd(cursor + agg[i], 1);
@@ -301,6 +314,7 @@ __global__ void k_agg_scatter(int64_t n, const int32_t *__restrict__ agg, const 
 }
 
 __global__ void k_agg_sort(int64_t nc, const int32_t *__restrict__ off, int32_t *__restrict__ mem) {
+    mds_pdl_entry();
     int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
     int32_t a = off[I], e = off[I + 1];
@@ -322,6 +336,7 @@ __global__ void k_rap(int64_t nc, const int32_t *__restrict__ off, const int32_t
                       const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
                       const int32_t *__restrict__ agg, int32_t *__restrict__ cnt, const int32_t *__restrict__ crp,
                       int32_t *__restrict__ cci, double *__restrict__ cv, int *err) {
+    mds_pdl_entry();
     int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
     int32_t cols[RAP_CAP];
@@ -380,6 +395,7 @@ constexpr int SPGEMM_CAP = 512;
 __global__ void k_sa_diag(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                           const double *__restrict__ v, const int8_t *__restrict__ g, double *__restrict__ afd,
                           double *__restrict__ d1f) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t pd = find_col(ci, rp[i], rp[i + 1], (int32_t)i);
@@ -403,6 +419,7 @@ __global__ void k_sa_prolongator(int64_t n, const int32_t *__restrict__ rp, cons
                                  const int32_t *__restrict__ agg, int32_t *__restrict__ cnt,
                                  const int32_t *__restrict__ prp, int32_t *__restrict__ pci, double *__restrict__ pv,
                                  int *err) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t cols[SA_P_CAP];
@@ -463,6 +480,7 @@ __global__ void k_sa_prolongator(int64_t n, const int32_t *__restrict__ rp, cons
 // Transpose: counts per column, scatter with an atomic cursor, then each row
 // sorted by column so that the result is deterministic.
 __global__ void k_tr_count(int64_t nnz, const int32_t *__restrict__ ci, int32_t *__restrict__ cnt) {
+    mds_pdl_entry();
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p < nnz) atomicAdd(cnt + ci[p], 1);
 }
@@ -470,6 +488,7 @@ __global__ void k_tr_count(int64_t nnz, const int32_t *__restrict__ ci, int32_t 
 __global__ void k_tr_fill(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                           const double *__restrict__ v, const int32_t *__restrict__ trp, int32_t *__restrict__ cur,
                           int32_t *__restrict__ tci, double *__restrict__ tv) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     for (int32_t p = rp[i]; p < rp[i + 1]; p++) {
@@ -482,6 +501,7 @@ __global__ void k_tr_fill(int64_t n, const int32_t *__restrict__ rp, const int32
 
 __global__ void k_sort_rows(int64_t n, const int32_t *__restrict__ rp, int32_t *__restrict__ ci,
                             double *__restrict__ v) {
+    mds_pdl_entry();
     int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= n) return;
     int32_t a = rp[I], e = rp[I + 1];
@@ -504,6 +524,7 @@ __global__ void k_sort_rows(int64_t n, const int32_t *__restrict__ rp, int32_t *
 template <bool FILL>
 __global__ void k_spgemm(int64_t n, mds_csr X, mds_csr Y, int32_t *__restrict__ cnt, const int32_t *__restrict__ crp,
                          int32_t *__restrict__ cci, double *__restrict__ cv, int *err) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t cols[SPGEMM_CAP];
@@ -595,6 +616,7 @@ static DCsr transpose_gpu(Ctx &c, const DCsr &P) {
 template <class DT>
 __global__ void k_l1(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                      const double *__restrict__ v, double *__restrict__ l1, DT *__restrict__ dinv) {
+    mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t p = find_col(ci, rp[i], rp[i + 1], (int32_t)i);
@@ -699,6 +721,7 @@ void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h)
         L.mem_off = Buf(&c, sizeof(int32_t) * (size_t)(nc + 1));
         int64_t nmem = scan_counts(c, acnt.as<int32_t>(), L.mem_off.as<int32_t>(), nc);
         L.mem = Buf(&c, sizeof(int32_t) * (size_t)(nmem > 0 ? nmem : 1));
+        L.mem_count = nmem;
         MDS_CUDA(cudaMemsetAsync(acnt.p, 0, sizeof(int32_t) * (size_t)(nc + 1), c.stream));
         MDS_LAUNCH(c, KC_NONE, 0, k_agg_scatter, gr, 256, 0, n, L.agg.as<int32_t>(), L.mem_off.as<int32_t>(),
                    acnt.as<int32_t>(), L.mem.as<int32_t>());

@@ -1,0 +1,11 @@
+// V-cycle kernels and level operations instantiated for float vectors (one
+// translation unit per vector type, compiled in parallel).
+#include "vcycle.cuh"
+
+namespace mds {
+
+void vcycle_run_f32(Ctx &c, Hierarchy &h, const float *b, float *x, int nr) { vcycle_nr<float>(c, h, b, x, nr); }
+
+float time_level_f32(Ctx &c, const Level &L) { return time_level<float>(c, L); }
+
+}  // namespace mds

@@ -14,6 +14,7 @@ __global__ void __launch_bounds__(256) k_spmv_csr(int64_t nrow, const int32_t *_
                                                    const int32_t *__restrict__ ci, const VT *__restrict__ v,
                                                    const XT *__restrict__ x, const double *__restrict__ r,
                                                    OT *__restrict__ y) {
+    mds_pdl_entry();
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t row = t / G;
     int lane = (int)(t % G);

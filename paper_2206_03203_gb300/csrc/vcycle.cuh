@@ -1,0 +1,775 @@
+// One aggregation-AMG V-cycle (Sec. 3.3: Q_mm and Q_ff of Algorithm 1):
+// kernels and host-side level operations, included by the per-type
+// translation units.
+//
+// Per level, with L1 diagonal D1 and piecewise-constant P:
+//   pre-smoothing from zero   x = S(0; b)            (L1-Jacobi or Chebyshev)
+//   residual + restriction    b_c = P^T (b - A x)
+//   coarse correction         x_c = V(b_c)           (dense inverse on the last level)
+//   prolongation + smoothing  y = x + P x_c;  x = S(y; b)
+// Storage per level: values in FP64, FP32, or BF16/FP16 with power-of-two
+// row scales (a_ij = s_i q_ij, |q_ij| <= 1); matrix in CSR (G lanes per row)
+// or SELL-C-sigma (one thread per row, slices of C rows stored column-major,
+// rows sorted by length inside windows of sigma rows).
+//
+// Two kernel forms.  Memory-bound levels (FP32 and below, and FP64 levels
+// small enough to be latency-bound, one L1-Jacobi sweep) form D1^-1 b and
+// x + P x_c on the fly at every neighbour, so a level costs two launches and
+// the smoothed iterates are never stored.  Large FP64 levels are bound by
+// GB300's FP64 pipe, so there the iterates are stored once per row instead of
+// being re-formed per nonzero; Chebyshev and multi-sweep smoothing also use
+// the stored form.  Below the finest level the residual and the restriction
+// are one launch (k_resid_restrict).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <map>
+#include <tuple>
+#include <type_traits>
+
+#include "internal.cuh"
+
+namespace mds {
+
+template <class XT, class VT> __device__ __forceinline__ XT cvt(VT v) { return (XT)v; }
+template <> __device__ __forceinline__ float cvt<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ float cvt<float, __half>(__half v) { return __half2float(v); }
+
+// Device view of one level's operator in its storage format.
+template <class VT> struct LvlMat {
+    int64_t n;
+    const int32_t *rp, *ci;    // CSR
+    const VT *v;               // CSR values or SELL values
+    const int32_t *sp, *sl;    // SELL slice offsets and lengths
+    const int32_t *sc;         // SELL columns
+    const int32_t *perm;       // SELL stored row -> original row (NULL: identity)
+    int C;                     // SELL slice height
+    const float *rscale;       // row scales (NULL: unscaled)
+};
+
+// Matrix entries are streamed once per launch: load them evict-first so the
+// L1/L2 capacity stays with the gathered vectors.
+template <class T> __device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
+template <> __device__ __forceinline__ __nv_bfloat16 ld_stream(const __nv_bfloat16 *p) {
+    unsigned short u = __ldcs(reinterpret_cast<const unsigned short *>(p));
+    return __ushort_as_bfloat16(u);
+}
+template <> __device__ __forceinline__ __half ld_stream(const __half *p) {
+    unsigned short u = __ldcs(reinterpret_cast<const unsigned short *>(p));
+    return __ushort_as_half(u);
+}
+
+// NR right-hand sides are stored interleaved: entry (i, c) at i * NR + c, so
+// one matrix entry multiplies NR contiguous vector entries (one vector load).
+template <class XT, int NR> struct alignas(sizeof(XT) * NR >= 16 ? 16 : sizeof(XT) * NR) Vec {
+    XT v[NR];
+};
+template <class XT, int NR> __device__ __forceinline__ Vec<XT, NR> ldv(const XT *p, int64_t j) {
+    return reinterpret_cast<const Vec<XT, NR> *>(p)[j];
+}
+template <class XT, int NR> __device__ __forceinline__ void stv(XT *p, int64_t j, const Vec<XT, NR> &x) {
+    reinterpret_cast<Vec<XT, NR> *>(p)[j] = x;
+}
+
+enum { VK_RESID0 = 0, VK_POST = 1, VK_RESID = 2, VK_SMOOTH = 3 };
+
+// Neighbour values each kernel multiplies by a_ij (NR columns at once).
+template <class XT, int NR, int K> struct Nb {
+    const XT *dinv, *b, *xin, *xc;
+    const int32_t *agg;
+    __device__ __forceinline__ Vec<XT, NR> operator()(int32_t j) const {
+        Vec<XT, NR> y;
+        if (K == VK_RESID0 || K == VK_POST) {
+            XT d = __ldg(dinv + j);
+            Vec<XT, NR> bj = ldv<XT, NR>(b, j);
+#pragma unroll
+            for (int c = 0; c < NR; c++) y.v[c] = d * bj.v[c];
+            if (K == VK_POST && agg) {
+                int32_t a = __ldg(agg + j);
+                if (a >= 0) {
+                    Vec<XT, NR> xa = ldv<XT, NR>(xc, a);
+#pragma unroll
+                    for (int c = 0; c < NR; c++) y.v[c] += xa.v[c];
+                }
+            }
+        } else {
+            y = ldv<XT, NR>(xin, j);
+        }
+        return y;
+    }
+};
+
+template <int G, class XT> __device__ __forceinline__ XT lane_reduce(XT s) {
+    if constexpr (G > 1) {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, G);
+    }
+    return s;
+}
+
+template <int G> __device__ __forceinline__ void row_of(int64_t &row, int &lane) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if constexpr (G > 0) {
+        row = t / G;
+        lane = (int)(t % G);
+    } else {
+        row = t;
+        lane = 0;
+    }
+}
+
+// Entries of each lane's share of a row loaded before the dependency wait.
+constexpr int PREFETCH = 8;
+
+// VK_RESID0: r = b - A (D1^-1 b)
+// VK_POST:   x = y + D1^-1 (b - A y),  y = D1^-1 b + P x_c   (formed per neighbour)
+// VK_RESID:  r = b - A x
+// VK_SMOOTH: x = y + D1^-1 (b - A y)                       (y stored)
+// Storage: CSR with G lanes per row (G = 1: one thread per row; lane-partial
+// sums over entries lane, lane + G, ..., then a lane tree), or SELL with one
+// thread per row (G = 0).  The level's matrix, row scales, 1/D1, aggregate
+// map and SELL permutation do not change while a V-cycle runs, so each lane
+// loads its first PREFETCH entries and its row constants before waiting for
+// the previous kernel; only the vector gathers follow the wait.  (Kernels
+// that write these arrays run in set-up, which launches without programmatic
+// dependence.)  The prefetch (PF entries) pays off when the launch fits in
+// about one wave of resident blocks; larger launches (PF = 0) keep registers
+// low for occupancy instead.
+template <int G, class VT, class XT, int K, int NR, int PF>
+__global__ void __launch_bounds__(256) k_level(LvlMat<VT> A, const XT *__restrict__ dinv, const XT *__restrict__ b,
+                                               const XT *__restrict__ xin, const int32_t *__restrict__ agg,
+                                               const XT *__restrict__ xc, XT *__restrict__ out) {
+    int64_t row;
+    int lane;
+    row_of<G>(row, lane);
+    const bool live = row < A.n;
+    // this lane's entries: index i0 + k * st for k < cnt
+    const int32_t *cp = G > 0 ? A.ci : A.sc;
+    int64_t i0 = 0;
+    int st = 1, cnt = 0;
+    if (live) {
+        if constexpr (G > 0) {
+            int32_t p0 = A.rp[row], p1 = A.rp[row + 1];
+            i0 = p0 + lane;
+            st = G;
+            cnt = p1 > i0 ? (int)((p1 - i0 + G - 1) / G) : 0;
+        } else {
+            int64_t sl = row / A.C;
+            int r = (int)(row - sl * A.C);
+            i0 = (int64_t)A.sp[sl] + r;
+            st = A.C;
+            cnt = A.sl[sl];
+        }
+    }
+    VT pa[PF > 0 ? PF : 1];
+    int32_t pj[PF > 0 ? PF : 1];
+#pragma unroll
+    for (int k = 0; k < PF; k++)
+        if (k < cnt) {
+            pa[k] = ld_stream(A.v + i0 + (int64_t)k * st);
+            pj[k] = ld_stream(cp + i0 + (int64_t)k * st);
+        }
+    int64_t o = row;
+    XT sc = (XT)1, d = (XT)0;
+    int32_t ag = -1;
+    if (live && lane == 0) {
+        if (G == 0 && A.perm) o = A.perm[row];
+        if (A.rscale) sc = (XT)A.rscale[o];
+        if (K == VK_POST || K == VK_SMOOTH) d = dinv[o];
+        if (K == VK_POST && agg) ag = agg[o];
+    }
+    mds_pdl_wait();
+    mds_pdl_trigger();
+    // row terms that do not depend on the sum, loaded with the gathers
+    Vec<XT, NR> bo, yo;
+#pragma unroll
+    for (int c = 0; c < NR; c++) bo.v[c] = yo.v[c] = (XT)0;
+    if (live && lane == 0) {
+        bo = ldv<XT, NR>(b, o);
+        if (K == VK_SMOOTH) yo = ldv<XT, NR>(xin, o);
+        if (K == VK_POST && ag >= 0) yo = ldv<XT, NR>(xc, ag);
+    }
+    Nb<XT, NR, K> f{dinv, b, xin, xc, agg};
+    XT s[NR];
+#pragma unroll
+    for (int c = 0; c < NR; c++) s[c] = 0;
+#pragma unroll
+    for (int k = 0; k < PF; k++)
+        if (k < cnt) {
+            XT a = cvt<XT>(pa[k]);
+            Vec<XT, NR> y = f(pj[k]);
+#pragma unroll
+            for (int c = 0; c < NR; c++) s[c] += a * y.v[c];
+        }
+#pragma unroll 4
+    for (int k = PF; k < cnt; k++) {
+        XT a = cvt<XT>(ld_stream(A.v + i0 + (int64_t)k * st));
+        Vec<XT, NR> y = f(ld_stream(cp + i0 + (int64_t)k * st));
+#pragma unroll
+        for (int c = 0; c < NR; c++) s[c] += a * y.v[c];
+    }
+#pragma unroll
+    for (int c = 0; c < NR; c++) s[c] = lane_reduce<G, XT>(s[c]);
+    if (live && lane == 0) {
+        if (A.rscale) {
+#pragma unroll
+            for (int c = 0; c < NR; c++) s[c] *= sc;
+        }
+        Vec<XT, NR> res;
+        if (K == VK_RESID0 || K == VK_RESID) {
+#pragma unroll
+            for (int c = 0; c < NR; c++) res.v[c] = bo.v[c] - s[c];
+        } else {
+            Vec<XT, NR> y;
+            if (K == VK_POST) {
+#pragma unroll
+                for (int c = 0; c < NR; c++) y.v[c] = d * bo.v[c];
+                if (ag >= 0) {
+#pragma unroll
+                    for (int c = 0; c < NR; c++) y.v[c] += yo.v[c];
+                }
+            } else {
+                y = yo;
+            }
+#pragma unroll
+            for (int c = 0; c < NR; c++) res.v[c] = y.v[c] + d * (bo.v[c] - s[c]);
+        }
+        stv<XT, NR>(out, o, res);
+    }
+}
+
+// ---- elementwise kernels (NR interleaved columns; row of entry e = e / NR).
+// 1/D1 and the aggregate map are fixed while solving: a thread's first entry
+// of them is loaded before the dependency wait.
+template <class XT, int NR>
+__global__ void k_vc_x0(int64_t n, const XT *__restrict__ dinv, const XT *__restrict__ b, XT *__restrict__ x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const XT d0 = e < n * NR ? dinv[e / NR] : (XT)0;
+    mds_pdl_wait();
+    mds_pdl_trigger();
+    if (e < n * NR) x[e] = d0 * b[e];
+    for (e += stride; e < n * NR; e += stride) x[e] = dinv[e / NR] * b[e];
+}
+
+// y_(i,c) += x_c(agg_i, c)
+template <class XT, int NR>
+__global__ void k_vc_prolong(int64_t n, const int32_t *__restrict__ agg, const XT *__restrict__ xc,
+                             XT *__restrict__ y) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t a0 = e < n * NR ? agg[e / NR] : -1;
+    mds_pdl_wait();
+    mds_pdl_trigger();
+    if (a0 >= 0) y[e] += xc[(int64_t)a0 * NR + e % NR];
+    for (e += stride; e < n * NR; e += stride) {
+        int32_t a = agg[e / NR];
+        if (a >= 0) y[e] += xc[(int64_t)a * NR + e % NR];
+    }
+}
+
+// Chebyshev (Saad, Iterative Methods, Alg. 12.1 for D1^-1 A on [lo, hi]):
+// first step d = (D1^-1 r) / theta, x = x0 + d; later steps
+// d = c1 d + c2 D1^-1 r, x += d.
+template <class XT, int NR>
+__global__ void k_cheb_first(int64_t n, const XT *__restrict__ dinv, const XT *__restrict__ r,
+                             const XT *__restrict__ x0, XT inv_theta, XT *__restrict__ d, XT *__restrict__ x) {
+    mds_pdl_entry();
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * NR; e += (int64_t)gridDim.x * blockDim.x) {
+        XT di = dinv[e / NR] * r[e] * inv_theta;
+        d[e] = di;
+        x[e] = x0 ? x0[e] + di : di;
+    }
+}
+
+template <class XT, int NR>
+__global__ void k_cheb_next(int64_t n, const XT *__restrict__ dinv, const XT *__restrict__ r, XT c1, XT c2,
+                            XT *__restrict__ d, XT *__restrict__ x) {
+    mds_pdl_entry();
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * NR; e += (int64_t)gridDim.x * blockDim.x) {
+        XT di = c1 * d[e] + c2 * (dinv[e / NR] * r[e]);
+        d[e] = di;
+        x[e] += di;
+    }
+}
+
+// b_c[I] = sum of r over the members of aggregate I (ascending), NR columns.
+// The aggregate's member list is fixed while solving: its first entries are
+// loaded before the dependency wait.
+constexpr int RPRE = 8;
+template <class XT, int NR>
+__global__ void k_vc_restrict(int64_t nc, const int32_t *__restrict__ off, const int32_t *__restrict__ mem,
+                              const XT *__restrict__ r, XT *__restrict__ bc) {
+    int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t q0 = 0, q1 = 0;
+    if (I < nc) {
+        q0 = off[I];
+        q1 = off[I + 1];
+    }
+    int32_t pm[RPRE];
+#pragma unroll
+    for (int k = 0; k < RPRE; k++)
+        if (q0 + k < q1) pm[k] = mem[q0 + k];
+    mds_pdl_wait();
+    mds_pdl_trigger();
+    if (I >= nc) return;
+    Vec<XT, NR> s;
+#pragma unroll
+    for (int c = 0; c < NR; c++) s.v[c] = 0;
+#pragma unroll
+    for (int k = 0; k < RPRE; k++)
+        if (q0 + k < q1) {
+            Vec<XT, NR> x = ldv<XT, NR>(r, pm[k]);
+#pragma unroll
+            for (int c = 0; c < NR; c++) s.v[c] += x.v[c];
+        }
+#pragma unroll 4
+    for (int32_t q = q0 + RPRE; q < q1; q++) {
+        Vec<XT, NR> x = ldv<XT, NR>(r, mem[q]);
+#pragma unroll
+        for (int c = 0; c < NR; c++) s.v[c] += x.v[c];
+    }
+    stv<XT, NR>(bc, I, s);
+}
+
+// Residual and restriction in one pass, for levels whose data stay in L2:
+// b_c[I] = sum over the members i of aggregate I (ascending) of r_i, with
+// r = b - A y (K = VK_RESID, y stored) or r = b - A D1^-1 b (K = VK_RESID0).
+// One warp per aggregate: lane k forms the residual of member k (one thread
+// per row, entries in CSR order) and the warp adds the members in order, as
+// the separate restriction does.  Vertices outside every aggregate need no
+// residual.  The first member row of each lane is loaded before the
+// dependency wait (the level's structure is fixed while solving).
+template <class VT, class XT, int K, int NR>
+__global__ void __launch_bounds__(256) k_resid_restrict(LvlMat<VT> A, const XT *__restrict__ dinv,
+                                                        const XT *__restrict__ b, const XT *__restrict__ y,
+                                                        int64_t nc, const int32_t *__restrict__ off,
+                                                        const int32_t *__restrict__ mem, XT *__restrict__ bc) {
+    const int64_t I = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    int32_t q0 = 0, q1 = 0;
+    if (I < nc) {
+        q0 = off[I];
+        q1 = off[I + 1];
+    }
+    int32_t i = -1, p0 = 0, p1 = 0;
+    if (q0 + lane < q1) {
+        i = mem[q0 + lane];
+        p0 = A.rp[i];
+        p1 = A.rp[i + 1];
+    }
+    VT pa[PREFETCH];
+    int32_t pj[PREFETCH];
+#pragma unroll
+    for (int k = 0; k < PREFETCH; k++)
+        if (p0 + k < p1) {
+            pa[k] = ld_stream(A.v + p0 + k);
+            pj[k] = ld_stream(A.ci + p0 + k);
+        }
+    mds_pdl_wait();
+    mds_pdl_trigger();
+    Nb<XT, NR, K> f{dinv, b, y, nullptr, nullptr};
+    Vec<XT, NR> acc;
+#pragma unroll
+    for (int c = 0; c < NR; c++) acc.v[c] = (XT)0;
+    for (int32_t base = q0; base < q1; base += 32) {
+        XT r[NR];
+#pragma unroll
+        for (int c = 0; c < NR; c++) r[c] = (XT)0;
+        if (base != q0) {
+            i = base + lane < q1 ? mem[base + lane] : -1;
+            p0 = i >= 0 ? A.rp[i] : 0;
+            p1 = i >= 0 ? A.rp[i + 1] : 0;
+        }
+        if (i >= 0) {
+            XT sum[NR];
+#pragma unroll
+            for (int c = 0; c < NR; c++) sum[c] = (XT)0;
+            int32_t p = p0;
+            if (base == q0) {
+#pragma unroll
+                for (int k = 0; k < PREFETCH; k++)
+                    if (p0 + k < p1) {
+                        XT a = cvt<XT>(pa[k]);
+                        Vec<XT, NR> yy = f(pj[k]);
+#pragma unroll
+                        for (int c = 0; c < NR; c++) sum[c] += a * yy.v[c];
+                    }
+                p = p0 + PREFETCH;
+            }
+#pragma unroll 4
+            for (; p < p1; p++) {
+                XT a = cvt<XT>(ld_stream(A.v + p));
+                Vec<XT, NR> yy = f(ld_stream(A.ci + p));
+#pragma unroll
+                for (int c = 0; c < NR; c++) sum[c] += a * yy.v[c];
+            }
+            Vec<XT, NR> bi = ldv<XT, NR>(b, i);
+            if (A.rscale) {
+                XT sc = (XT)A.rscale[i];
+#pragma unroll
+                for (int c = 0; c < NR; c++) sum[c] *= sc;
+            }
+#pragma unroll
+            for (int c = 0; c < NR; c++) r[c] = bi.v[c] - sum[c];
+        }
+        int m = q1 - base < 32 ? q1 - base : 32;
+        for (int k = 0; k < m; k++)
+#pragma unroll
+            for (int c = 0; c < NR; c++) acc.v[c] += __shfl_sync(0xffffffffu, r[c], k);
+    }
+    if (I < nc && lane == 0) stv<XT, NR>(bc, I, acc);
+}
+
+// Smoothed aggregation transfers (NR columns): b_c = R r and y += P x_c, one
+// thread per output row, entries in CSR order.
+template <class XT, int NR>
+__global__ void k_sa_restrict(int64_t nc, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                              const XT *__restrict__ v, const XT *__restrict__ r, XT *__restrict__ bc) {
+    mds_pdl_entry();
+    int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    Vec<XT, NR> s;
+#pragma unroll
+    for (int c = 0; c < NR; c++) s.v[c] = 0;
+    for (int32_t p = rp[I]; p < rp[I + 1]; p++) {
+        XT a = v[p];
+        Vec<XT, NR> x = ldv<XT, NR>(r, ci[p]);
+#pragma unroll
+        for (int c = 0; c < NR; c++) s.v[c] += a * x.v[c];
+    }
+    stv<XT, NR>(bc, I, s);
+}
+
+template <class XT, int NR>
+__global__ void k_sa_prolong(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                             const XT *__restrict__ v, const XT *__restrict__ xc, XT *__restrict__ y) {
+    mds_pdl_entry();
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Vec<XT, NR> s = ldv<XT, NR>(y, i), t;
+#pragma unroll
+    for (int c = 0; c < NR; c++) t.v[c] = 0;
+    for (int32_t p = rp[i]; p < rp[i + 1]; p++) {
+        XT a = v[p];
+        Vec<XT, NR> x = ldv<XT, NR>(xc, ci[p]);
+#pragma unroll
+        for (int c = 0; c < NR; c++) t.v[c] += a * x.v[c];
+    }
+#pragma unroll
+    for (int c = 0; c < NR; c++) s.v[c] += t.v[c];
+    stv<XT, NR>(y, i, s);
+}
+
+// ---------------------------------------------------------------- host dispatch
+
+template <class VT> static LvlMat<VT> lvl_view(const Level &L) {
+    LvlMat<VT> m{};
+    m.n = L.A.nrow;
+    m.rp = L.A.rowp();
+    m.ci = L.A.cols();
+    m.rscale = L.rscale.p ? L.rscale.as<float>() : nullptr;
+    if (L.fmt == FMT_SELL) {
+        m.v = L.sell_val.as<VT>();
+        m.sp = L.sell_ptr.as<int32_t>();
+        m.sl = L.sell_len.as<int32_t>();
+        m.sc = L.sell_col.as<int32_t>();
+        m.perm = L.sell_perm.p ? L.sell_perm.as<int32_t>() : nullptr;
+        m.C = L.sell_c;
+    } else {
+        m.v = std::is_same<VT, double>::value ? (const VT *)L.A.vals() : L.vals_lp.as<VT>();
+        m.C = 1;
+    }
+    return m;
+}
+
+template <class VT, class XT, int K, int NR, int PF>
+static void launch_level_pf(Ctx &c, const Level &L, const XT *dinv, const XT *b, const XT *xin, const int32_t *agg,
+                         const XT *xc, XT *out, int64_t nc) {
+    LvlMat<VT> m = lvl_view<VT>(L);
+    int64_t n = L.A.nrow;
+    double vb = L.fmt == FMT_SELL ? (sizeof(VT) + 4.0) * (double)L.sell_nnz : (sizeof(VT) + 4.0) * L.A.nnz;
+    double xb = sizeof(XT) * (double)NR;
+    double bytes = vb + (L.fmt == FMT_SELL ? 8.0 * L.sell_nslice : 4.0 * (n + 1)) + sizeof(XT) * n + 2.0 * xb * n +
+                   (K == VK_POST && agg ? 4.0 * n + xb * (double)nc : 0.0) + (L.rscale.p ? 4.0 * n : 0.0) +
+                   (K == VK_SMOOTH ? xb * (double)n : 0.0);
+    double flops = NR * (2.0 * L.A.nnz + (K == VK_RESID0 ? n : K == VK_POST ? 5.0 * n : K == VK_SMOOTH ? 3.0 * n : 0.0));
+    int cls = (K == VK_RESID0 || K == VK_RESID) ? KC_VC_RESID : KC_VC_POST;
+    if (L.fmt == FMT_SELL) {
+        int64_t rows = L.sell_nslice * L.sell_c;
+        MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<0, VT, XT, K, NR, PF>), grid_for(rows, 256), 256, 0, m, dinv, b, xin,
+                     agg, xc, out);
+        return;
+    }
+    switch (L.G) {
+        case 1:
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<1, VT, XT, K, NR, PF>), grid_for(n, 256), 256, 0, m, dinv, b, xin,
+                         agg, xc, out);
+            break;
+        case 2:
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<2, VT, XT, K, NR, PF>), grid_for(n * 2, 256), 256, 0, m, dinv, b,
+                         xin, agg, xc, out);
+            break;
+        case 4:
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<4, VT, XT, K, NR, PF>), grid_for(n * 4, 256), 256, 0, m, dinv, b,
+                         xin, agg, xc, out);
+            break;
+        case 8:
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<8, VT, XT, K, NR, PF>), grid_for(n * 8, 256), 256, 0, m, dinv, b,
+                         xin, agg, xc, out);
+            break;
+        case 16:
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<16, VT, XT, K, NR, PF>), grid_for(n * 16, 256), 256, 0, m, dinv, b,
+                         xin, agg, xc, out);
+            break;
+        default:
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<32, VT, XT, K, NR, PF>), grid_for(n * 32, 256), 256, 0, m, dinv, b,
+                         xin, agg, xc, out);
+            break;
+    }
+}
+
+// Launches of at most this many 256-thread blocks use the prefetching form.
+constexpr int64_t PREFETCH_MAX_BLOCKS = 1216;
+
+template <class VT, class XT, int K, int NR>
+static void launch_level(Ctx &c, const Level &L, const XT *dinv, const XT *b, const XT *xin, const int32_t *agg,
+                         const XT *xc, XT *out, int64_t nc) {
+    int64_t threads = L.fmt == FMT_SELL ? L.sell_nslice * L.sell_c : L.A.nrow * (int64_t)L.G;
+    if ((threads + 255) / 256 <= PREFETCH_MAX_BLOCKS)
+        launch_level_pf<VT, XT, K, NR, PREFETCH>(c, L, dinv, b, xin, agg, xc, out, nc);
+    else
+        launch_level_pf<VT, XT, K, NR, 0>(c, L, dinv, b, xin, agg, xc, out, nc);
+}
+
+// b_c = P^T (b - A y) (K = VK_RESID) or P^T (b - A D1^-1 b) (K = VK_RESID0)
+// through k_resid_restrict on the level's CSR arrays (values of type VT).
+template <class VT, class XT, int K, int NR>
+static void resid_restrict_vt(Ctx &c, const Level &L, const XT *b, const XT *y, XT *bc) {
+    const XT *dinv = L.dinv.as<XT>();
+    int64_t n = L.A.nrow, nc = L.nc;
+    unsigned grid = grid_for(nc * 32, 256);
+    LvlMat<VT> m{};
+    m.n = n;
+    m.rp = L.A.rowp();
+    m.ci = L.A.cols();
+    m.v = std::is_same<VT, double>::value ? (const VT *)L.A.vals() : L.vals_lp.as<VT>();
+    m.C = 1;
+    m.rscale = L.rscale.p ? L.rscale.as<float>() : nullptr;
+    double xb = sizeof(XT) * (double)NR;
+    double bytes = (sizeof(VT) + 4.0) * L.A.nnz + 4.0 * (n + 1) + 4.0 * (nc + 1) + 4.0 * n + xb * (2.0 * n + nc) +
+                   (K == VK_RESID0 ? sizeof(XT) * (double)n : 0.0) + (m.rscale ? 4.0 * n : 0.0);
+    MDS_LAUNCH_F(c, KC_VC_RESID, bytes, NR * (2.0 * L.A.nnz + 2.0 * n), (k_resid_restrict<VT, XT, K, NR>), grid, 256,
+                 0, m, dinv, b, y, nc, L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), bc);
+}
+
+// Level operations on FP32 vectors whose values are stored in VT = BF16 or
+// FP16: defined here, instantiated in their own translation units
+// (k_vcycle_bf16.cu, k_vcycle_f16.cu) so that the library compiles in
+// parallel.
+template <class VT, int K, int NR>
+void level_op_lp(Ctx &c, const Level &L, const float *b, const float *xin, const int32_t *agg, const float *xc,
+                 float *out, int64_t nc) {
+    launch_level<VT, float, K, NR>(c, L, L.dinv.as<float>(), b, xin, agg, xc, out, nc);
+}
+template <class VT, int K, int NR>
+void resid_restrict_lp(Ctx &c, const Level &L, const float *b, const float *y, float *bc) {
+    resid_restrict_vt<VT, float, K, NR>(c, L, b, y, bc);
+}
+
+#define MDS_LP_EACH(X, VT)                                                                            \
+    X(VT, 0, 1) X(VT, 0, 2) X(VT, 0, 4) X(VT, 0, 8) X(VT, 1, 1) X(VT, 1, 2) X(VT, 1, 4) X(VT, 1, 8)   \
+    X(VT, 2, 1) X(VT, 2, 2) X(VT, 2, 4) X(VT, 2, 8) X(VT, 3, 1) X(VT, 3, 2) X(VT, 3, 4) X(VT, 3, 8)
+#define MDS_LP_DECL(VT, K, NR)                                                                             \
+    extern template void level_op_lp<VT, K, NR>(Ctx &, const Level &, const float *, const float *,      \
+                                                 const int32_t *, const float *, float *, int64_t);       \
+    extern template void resid_restrict_lp<VT, K, NR>(Ctx &, const Level &, const float *, const float *, \
+                                                       float *);
+#define MDS_LP_INST(VT, K, NR)                                                                                    \
+    template void level_op_lp<VT, K, NR>(Ctx &, const Level &, const float *, const float *, const int32_t *,    \
+                                          const float *, float *, int64_t);                                      \
+    template void resid_restrict_lp<VT, K, NR>(Ctx &, const Level &, const float *, const float *, float *);
+#ifndef MDS_VCYCLE_LP_UNIT
+MDS_LP_EACH(MDS_LP_DECL, __nv_bfloat16)
+MDS_LP_EACH(MDS_LP_DECL, __half)
+#endif
+
+template <class XT, int K, int NR>
+static void level_op(Ctx &c, const Level &L, const XT *b, const XT *xin, const int32_t *agg, const XT *xc, XT *out,
+                     int64_t nc) {
+    const XT *dinv = L.dinv.as<XT>();
+    if constexpr (std::is_same<XT, double>::value) {
+        launch_level<double, XT, K, NR>(c, L, dinv, b, xin, agg, xc, out, nc);
+    } else {
+        switch (L.vt) {
+            case VT_BF16: level_op_lp<__nv_bfloat16, K, NR>(c, L, b, xin, agg, xc, out, nc); break;
+            case VT_F16: level_op_lp<__half, K, NR>(c, L, b, xin, agg, xc, out, nc); break;
+            default: launch_level<float, XT, K, NR>(c, L, dinv, b, xin, agg, xc, out, nc); break;
+        }
+    }
+}
+
+template <class XT, int K, int NR>
+static void resid_restrict(Ctx &c, const Level &L, const XT *b, const XT *y, XT *bc) {
+    if constexpr (std::is_same<XT, double>::value) {
+        resid_restrict_vt<double, XT, K, NR>(c, L, b, y, bc);
+    } else {
+        switch (L.vt) {
+            case VT_BF16: resid_restrict_lp<__nv_bfloat16, K, NR>(c, L, b, y, bc); break;
+            case VT_F16: resid_restrict_lp<__half, K, NR>(c, L, b, y, bc); break;
+            default: resid_restrict_vt<float, XT, K, NR>(c, L, b, y, bc); break;
+        }
+    }
+}
+
+static unsigned ew_grid(int64_t n) {
+    unsigned g = grid_for(n, 256);
+    return g > 4096 ? 4096 : g;
+}
+
+// x = S(x0; b): `sweeps` smoother applications starting from x0 (NULL = 0).
+// x0 and x must differ; uses L.r (residual), L.t (copy) and L.d (Chebyshev
+// direction) as scratch.
+template <class XT, int NR>
+static void smooth_stored(Ctx &c, const Hierarchy &h, const Level &L, const XT *b, const XT *x0, XT *x) {
+    int64_t n = L.A.nrow;
+    XT *r = L.r.as<XT>();
+    const XT *dinv = L.dinv.as<XT>();
+    const double lo = 0.3, hi = 1.0;
+    const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta, rho = 1.0 / sigma;
+    const double rho1 = 1.0 / (2.0 * sigma - rho);
+    const XT *cur = x0;
+    for (int s = 0; s < h.sweeps; s++) {
+        XT *dst = x;
+        if (cur == x) {
+            MDS_CUDA(cudaMemcpyAsync(L.t.p, x, sizeof(XT) * (size_t)n * NR, cudaMemcpyDeviceToDevice, c.stream));
+            cur = L.t.as<XT>();
+        }
+        if (h.smoother == MDS_SMOOTHER_L1JACOBI) {
+            if (!cur)
+                MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n * NR, (k_vc_x0<XT, NR>), ew_grid(n * NR), 256, 0, n, dinv,
+                           b, dst);
+            else
+                level_op<XT, VK_SMOOTH, NR>(c, L, b, cur, nullptr, nullptr, dst, 0);
+        } else {
+            XT *d = L.d.as<XT>();
+            if (cur) {
+                level_op<XT, VK_RESID, NR>(c, L, b, cur, nullptr, nullptr, r, 0);
+                MDS_LAUNCH(c, KC_NONE, 0, (k_cheb_first<XT, NR>), ew_grid(n * NR), 256, 0, n, dinv, r, cur,
+                           (XT)(1.0 / theta), d, dst);
+            } else {
+                MDS_LAUNCH(c, KC_NONE, 0, (k_cheb_first<XT, NR>), ew_grid(n * NR), 256, 0, n, dinv, b,
+                           (const XT *)nullptr, (XT)(1.0 / theta), d, dst);
+            }
+            level_op<XT, VK_RESID, NR>(c, L, b, dst, nullptr, nullptr, r, 0);
+            MDS_LAUNCH(c, KC_NONE, 0, (k_cheb_next<XT, NR>), ew_grid(n * NR), 256, 0, n, dinv, r, (XT)(rho1 * rho),
+                       (XT)(2.0 * rho1 / delta), d, dst);
+        }
+        cur = dst;
+    }
+}
+
+constexpr int64_t FUSE_FP64_ROWS = 65536;
+
+template <class XT, int NR>
+static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
+    Level &L = h.lv[l];
+    int last = (int)h.lv.size() - 1;
+    if (l == last && h.dense) {
+        dense_apply(c, h.Ainv.as<double>(), h.nd, NR, b, x);
+        return;
+    }
+    int64_t n = L.A.nrow;
+    XT *r = L.r.as<XT>();
+    double rbytes = 4.0 * (L.nc + 1) + 4.0 * n + sizeof(XT) * NR * (double)(n + L.nc);
+    // Fused form (y = D1^-1 b [+ P x_c] formed per neighbour, no stored
+    // iterate): FP32 levels, and FP64 levels small enough to be bound by
+    // latency rather than by the FP64 units (the fused form spends one to two
+    // more FP64 operations per nonzero and saves two launches per level).
+    bool fused = h.smoother == MDS_SMOOTHER_L1JACOBI && h.sweeps == 1 && !L.smoothed &&
+                 (!std::is_same<XT, double>::value || n <= FUSE_FP64_ROWS);
+    // below the finest level, with aggregates large enough to fill most lanes
+    // of a warp (3D), the residual and the restriction share a launch
+    const bool rr = l > 0 && !L.smoothed && L.nc > 0 && L.mem_count >= 16 * L.nc;
+    if (fused) {
+        if (L.has_coarse) {
+            Level &C = h.lv[l + 1];
+            if (rr) {
+                resid_restrict<XT, VK_RESID0, NR>(c, L, b, nullptr, C.b.as<XT>());
+            } else {
+                level_op<XT, VK_RESID0, NR>(c, L, b, nullptr, nullptr, nullptr, r, 0);
+                MDS_LAUNCH(c, KC_VC_RESTRICT, rbytes, (k_vc_restrict<XT, NR>), grid_for(L.nc, 256), 256, 0, L.nc,
+                           L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r, C.b.as<XT>());
+            }
+            vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
+            level_op<XT, VK_POST, NR>(c, L, b, nullptr, L.agg.as<int32_t>(), C.x.as<XT>(), x, L.nc);
+        } else {
+            level_op<XT, VK_POST, NR>(c, L, b, nullptr, nullptr, nullptr, x, 0);
+        }
+        return;
+    }
+    XT *y = L.y.as<XT>();
+    smooth_stored<XT, NR>(c, h, L, b, nullptr, y);  // y = S(0; b)
+    if (L.has_coarse) {
+        Level &C = h.lv[l + 1];
+        if (L.smoothed) {
+            level_op<XT, VK_RESID, NR>(c, L, b, y, nullptr, nullptr, r, 0);
+            const XT *rv = std::is_same<XT, double>::value ? (const XT *)L.R.vals() : L.Rv_lp.as<XT>();
+            const XT *pv = std::is_same<XT, double>::value ? (const XT *)L.P.vals() : L.Pv_lp.as<XT>();
+            double tb = (sizeof(XT) + 4.0) * L.R.nnz + 4.0 * (L.nc + 1) + sizeof(XT) * NR * (double)(n + L.nc);
+            MDS_LAUNCH(c, KC_VC_RESTRICT, tb, (k_sa_restrict<XT, NR>), grid_for(L.nc, 256), 256, 0, L.nc, L.R.rowp(),
+                       L.R.cols(), rv, r, C.b.as<XT>());
+            vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
+            MDS_LAUNCH(c, KC_NONE, tb + sizeof(XT) * NR * (double)n, (k_sa_prolong<XT, NR>), grid_for(n, 256), 256, 0,
+                       n, L.P.rowp(), L.P.cols(), pv, C.x.as<XT>(), y);
+        } else {
+            if (rr) {
+                resid_restrict<XT, VK_RESID, NR>(c, L, b, y, C.b.as<XT>());
+            } else {
+                level_op<XT, VK_RESID, NR>(c, L, b, y, nullptr, nullptr, r, 0);
+                MDS_LAUNCH(c, KC_VC_RESTRICT, rbytes, (k_vc_restrict<XT, NR>), grid_for(L.nc, 256), 256, 0, L.nc,
+                           L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r, C.b.as<XT>());
+            }
+            vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
+            MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n * NR, (k_vc_prolong<XT, NR>), ew_grid(n * NR), 256, 0, n,
+                       L.agg.as<int32_t>(), C.x.as<XT>(), y);
+        }
+    }
+    smooth_stored<XT, NR>(c, h, L, b, y, x);  // x = S(y; b)
+}
+
+template <class XT>
+static void vcycle_nr(Ctx &c, Hierarchy &h, const XT *b, XT *x, int nr) {
+    switch (nr) {
+        case 1: vcycle_level<XT, 1>(c, h, 0, b, x); break;
+        case 2: vcycle_level<XT, 2>(c, h, 0, b, x); break;
+        case 4: vcycle_level<XT, 4>(c, h, 0, b, x); break;
+        case 8: vcycle_level<XT, 8>(c, h, 0, b, x); break;
+        default: throw Error(MDS_ERR_INVALID, "V-cycle column count must be 1, 2, 4 or 8");
+    }
+}
+
+// Time the stored-residual kernel on the level in its current storage (best
+// of three after a warm-up launch).
+template <class XT> static float time_level(Ctx &c, const Level &L) {
+    cudaEvent_t e0, e1;
+    MDS_CUDA(cudaEventCreate(&e0));
+    MDS_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; rep++) {
+        MDS_CUDA(cudaEventRecord(e0, c.stream));
+        level_op<XT, VK_RESID, 1>(c, L, L.b.as<XT>(), L.x.as<XT>(), nullptr, nullptr, L.r.as<XT>(), 0);
+        MDS_CUDA(cudaEventRecord(e1, c.stream));
+        MDS_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        MDS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+}  // namespace mds
