@@ -194,6 +194,12 @@ typedef struct {
     int prolongation;        /* MDS_PROLONG_* (MDS_PROLONG_PIECEWISE).  Smoothed: AF keeps the
                                 strong couplings and adds the weak ones to its diagonal, D1F is
                                 its L1 diagonal, A_c = P^T (A P) */
+    int coarse_tail;         /* 1: the coarse end of each V-cycle (levels of at most 8192 rows,
+                                one L1-Jacobi sweep, unsmoothed, values in the vector type, and
+                                the dense solve) runs as one kernel on a thread block cluster;
+                                0: one launch per level operation (0: on GB300 the separate
+                                launches, overlapped by programmatic dependent launch, measured
+                                faster) */
 } mds_setup_opts;
 
 /* Fill `o` with the defaults listed above. */
@@ -309,6 +315,16 @@ int mds_timing_reset(mds_ctx ctx);
  * algorithmic bytes and summed algorithmic floating-point operations of a
  * class since the last reset (any output pointer may be NULL). */
 int mds_timing_query(mds_ctx ctx, int kclass, int64_t *launches, double *ms, double *bytes, double *flops);
+/* Event brackets cost a few microseconds of pipeline time each (they end the
+ * programmatic overlap of neighbouring kernels).  With every = k > 1, FGMRES
+ * brackets the timed classes only in every k-th restart cycle (its Arnoldi
+ * steps are replayed from a second, bracketed CUDA graph); other launches run
+ * unbracketed.  Default 1: every launch of a timed class is bracketed. */
+int mds_timing_sample_every(mds_ctx ctx, int every);
+/* Like mds_timing_query, restricted to the launches that were bracketed:
+ * their count, event time, algorithmic bytes and operations.  Their ratios
+ * are the measured per-launch averages when sampling. */
+int mds_timing_sampled(mds_ctx ctx, int kclass, int64_t *launches, double *ms, double *bytes, double *flops);
 /* Copy `bytes` bytes from src to dst (each a host or device pointer) on the
  * context stream and synchronise it.  A convenience for callers without
  * their own CUDA runtime binding. */

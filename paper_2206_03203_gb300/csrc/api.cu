@@ -76,7 +76,7 @@ void Ctx::check_err(const char *where) {
 KTimer::KTimer(Ctx &ctx, int k, double b, double f) : c(ctx), cls(k) {
     if (k < 0 || k >= MDS_KCLASS_COUNT) return;
     if (c.capturing) {
-        GraphRec r{k, b, f, c.timing[k], nullptr, nullptr};
+        GraphRec r{k, b, f, c.timing[k] && !c.timing_suspended, nullptr, nullptr};
         if (r.timed) {
             MDS_CUDA(cudaEventCreate(&r.e0));
             MDS_CUDA(cudaEventCreate(&r.e1));
@@ -91,7 +91,10 @@ KTimer::KTimer(Ctx &ctx, int k, double b, double f) : c(ctx), cls(k) {
     c.launches[k]++;
     c.bytes[k] += b;
     c.flops[k] += f;
-    if (!c.timing[k]) return;
+    if (!c.timing[k] || c.timing_suspended) return;
+    c.tlaunches[k]++;
+    c.tbytes[k] += b;
+    c.tflops[k] += f;
     auto &v = c.evs[k];
     if (c.ev_used[k] == v.size()) {
         KTimerRec r;
@@ -132,7 +135,12 @@ void graph_collect(Ctx &c, Graph &g) {
     for (auto &r : g.recs)
         if (r.timed && c.timing[r.cls]) {
             float t = 0.f;
-            if (cudaEventElapsedTime(&t, r.e0, r.e1) == cudaSuccess) c.graph_ms[r.cls] += t;
+            if (cudaEventElapsedTime(&t, r.e0, r.e1) == cudaSuccess) {
+                c.graph_ms[r.cls] += t;
+                c.tlaunches[r.cls]++;
+                c.tbytes[r.cls] += r.bytes;
+                c.tflops[r.cls] += r.flops;
+            }
         }
 }
 
@@ -390,6 +398,7 @@ int mds_setup_opts_default(mds_setup_opts *o) {
     o->sell_sigma = 1;
     o->sweeps = 1;
     o->prolongation = MDS_PROLONG_PIECEWISE;
+    o->coarse_tail = 0;
     return MDS_OK;
 }
 
@@ -772,9 +781,40 @@ int mds_timing_reset(mds_ctx ctx) {
         c.bytes[k] = 0.0;
         c.flops[k] = 0.0;
         c.graph_ms[k] = 0.0;
+        c.tlaunches[k] = 0;
+        c.tbytes[k] = 0.0;
+        c.tflops[k] = 0.0;
     }
     c.total_launches = 0;
     return MDS_OK;
+}
+
+int mds_timing_sample_every(mds_ctx ctx, int every) {
+    if (!ctx || every < 1) return MDS_ERR_INVALID;
+    ctx->c.sample_every = every;
+    return MDS_OK;
+}
+
+static double event_ms(Ctx *c, int k) {
+    double tot = 0.0;
+    for (size_t q = 0; q < c->ev_used[k]; q++) {
+        float t = 0.f;
+        MDS_CUDA(cudaEventElapsedTime(&t, c->evs[k][q].e0, c->evs[k][q].e1));
+        tot += t;
+    }
+    return tot + c->graph_ms[k];
+}
+
+int mds_timing_sampled(mds_ctx ctx, int k, int64_t *launches, double *ms, double *bytes, double *flops) {
+    if (!ctx || k < 0 || k >= MDS_KCLASS_COUNT) return MDS_ERR_INVALID;
+    Ctx *c = &ctx->c;
+    API_BEGIN
+    c->sync();
+    if (launches) *launches = c->tlaunches[k];
+    if (ms) *ms = event_ms(c, k);
+    if (bytes) *bytes = c->tbytes[k];
+    if (flops) *flops = c->tflops[k];
+    API_END(c)
 }
 
 int mds_timing_query(mds_ctx ctx, int k, int64_t *launches, double *ms, double *bytes, double *flops) {
@@ -782,14 +822,8 @@ int mds_timing_query(mds_ctx ctx, int k, int64_t *launches, double *ms, double *
     Ctx *c = &ctx->c;
     API_BEGIN
     c->sync();
-    double tot = 0.0;
-    for (size_t q = 0; q < c->ev_used[k]; q++) {
-        float t = 0.f;
-        MDS_CUDA(cudaEventElapsedTime(&t, c->evs[k][q].e0, c->evs[k][q].e1));
-        tot += t;
-    }
     if (launches) *launches = c->launches[k];
-    if (ms) *ms = tot + c->graph_ms[k];
+    if (ms) *ms = event_ms(c, k);
     if (bytes) *bytes = c->bytes[k];
     if (flops) *flops = c->flops[k];
     API_END(c)

@@ -144,6 +144,12 @@ struct Ctx {
     double flops[MDS_KCLASS_COUNT] = {};
     int64_t total_launches = 0;
     double graph_ms[MDS_KCLASS_COUNT] = {};
+    // launches that were bracketed by events, and their algorithmic work
+    int64_t tlaunches[MDS_KCLASS_COUNT] = {};
+    double tbytes[MDS_KCLASS_COUNT] = {};
+    double tflops[MDS_KCLASS_COUNT] = {};
+    int sample_every = 1;          // FGMRES brackets every k-th restart cycle
+    bool timing_suspended = false; // capture of the unbracketed graph variant
     Graph *capturing = nullptr;   // recording target while a stream capture is open
     void *owner = nullptr;        // the mds_ctx handle that holds this context
     int dependents = 0;           // live systems and preconditioners made on this context
@@ -362,6 +368,7 @@ struct Hierarchy {
     int smoother = 0;
     int sweeps = 1;
     int nr_cap = 0;   // columns the level work vectors hold
+    bool use_tail = true;  // run the coarse end of the V-cycle as one cluster kernel
 };
 
 void amg_setup(Ctx &c, const mds_csr &A, const mds_setup_opts &o, Hierarchy &h);

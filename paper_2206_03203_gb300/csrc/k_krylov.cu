@@ -256,8 +256,8 @@ struct GsStep {
 };
 
 // w -= sum_q coef_q V[q] (unrolled over q so several rows load at once) and
-// ||w||^2; the last block finishes the step.  Pass 1 (coef = h, h[nq] =
-// ||w||^2 before the update): when ||w_new||^2 < eta2 ||w||^2 one classical
+// ||w||^2; the last block finishes the step.  Pass 1 (coef = h): when
+// ||w_new||^2 < eta2 ||w||^2, with ||w||^2 = ||w_new||^2 + ||h||^2, one classical
 // pass may have left an orthogonality error of order eps ||w|| / ||w_new||,
 // so scal[5] = 1 asks the host for a second pass; otherwise the Arnoldi
 // column is formed and scal[5] = 0.  Pass 2 (coef = h2): the column uses
@@ -319,8 +319,12 @@ __global__ void __launch_bounds__(RED_BLOCK) k_gs_update(int64_t n, const double
     __shared__ int second;
     double nsq = block_sum(u);
     if (threadIdx.x == 0) {
+        // ||w||^2 before the pass = ||w_new||^2 + ||h||^2 (w_new is orthogonal
+        // to the orthonormal basis up to rounding)
+        double hh = 0.0;
+        for (int q = 0; q < nq; q++) hh += cq[q] * cq[q];
         nsq_s = nsq;
-        second = st.pass == 1 && nsq < st.eta2 * st.h[nq];
+        second = st.pass == 1 && nsq < st.eta2 * (nsq + hh);
         st.scal[5] = second ? 1.0 : 0.0;
     }
     __syncthreads();
@@ -481,7 +485,7 @@ KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, 
     R.pp = partial;
     MDS_REQUIRE(partial && Vp && Zp && Hp && d, MDS_ERR_INVALID, "FGMRES workspace pointer missing");
     MDS_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * 256, c.stream));
-    // cs, sn, g, y, h (first Gram-Schmidt pass, h[nq] = ||w||^2), h2 (second
+    // cs, sn, g, y, h (first Gram-Schmidt pass), h2 (second
     // pass), scal (step scalars; scal[5] = second pass pending), nsq, and two
     // block-arrival counters of the fused reductions
     double *cs = d, *sn = d + 32, *g = d + 64, *y = d + 96, *h = d + 128, *h2 = d + 160, *scal = d + 192,
@@ -498,12 +502,12 @@ KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, 
     auto gs_pass = [&](int j, int pass) {
         double *w = Vp + (size_t)(j + 1) * ld;
         int nq = j + 1;
-        int nout = pass == 1 ? nq + 1 : nq;
+        int nout = nq;
         double *hh = pass == 1 ? h : h2;
         unsigned mg = gs_dot_grid(R, n, nout);
         GsStep st{j, m, pass, o.reorth_eta2, Hp, h, cs, sn, g, scal};
         int cls_dot = pass == 1 ? KC_GS_DOT : KC_NONE, cls_upd = pass == 1 ? KC_GS_AXPY : KC_NONE;
-        MDS_LAUNCH_F(c, cls_dot, 8.0 * n * (nq + 1), 2.0 * n * nout, k_gs_dot, dim3(mg, nout), RED_BLOCK, 0, n, Vp,
+        MDS_LAUNCH_F(c, cls_dot, 8.0 * n * (nq + 1), 2.0 * n * nq, k_gs_dot, dim3(mg, nout), RED_BLOCK, 0, n, Vp,
                      ld, nq, w, R.pp, cnt, hh);
         MDS_LAUNCH_F(c, cls_upd, 8.0 * n * (nq + 2), 2.0 * n * (nq + 1), k_gs_update, R.ugrid, RED_BLOCK, 0, n, Vp, ld,
                      nq, hh, w, R.pp, cnt + 1, st);
@@ -522,28 +526,47 @@ KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, 
         spmv_f64(c, A, zj, Vp + (size_t)(j + 1) * ld, KC_SPMV);
         gs_pass(j, 1);
     };
-    std::vector<std::unique_ptr<Graph>> graphs(m);
+    // Step graphs: one set, or with timing sampled, an unbracketed set and a
+    // bracketed set used in every sample_every-th restart cycle.
+    bool any_timed = false;
+    for (int k = 0; k < MDS_KCLASS_COUNT; k++) any_timed = any_timed || c.timing[k];
+    const bool sampled = any_timed && c.sample_every > 1;
+    std::vector<std::unique_ptr<Graph>> graphs(m), graphs_timed(sampled ? m : 0);
     bool graphs_ok = o.graphs != 0;
+    int restarts = 0;
     auto run_step = [&](int j) {
         Graph *gj = nullptr;
+        bool bracket = !sampled || restarts % c.sample_every == 0;
         if (graphs_ok) {
-            if (!graphs[j]) {
-                graphs[j].reset(new Graph);
-                if (!graph_capture(c, *graphs[j], [&] { body(j); })) {
-                    graphs[j].reset();
+            auto &slot = sampled && bracket ? graphs_timed[j] : graphs[j];
+            if (!slot) {
+                slot.reset(new Graph);
+                c.timing_suspended = !bracket;
+                bool ok = graph_capture(c, *slot, [&] { body(j); });
+                c.timing_suspended = false;
+                if (!ok) {
+                    slot.reset();
                     graphs_ok = false;
                 }
             }
-            gj = graphs[j].get();
+            gj = slot.get();
         }
-        if (gj)
+        if (gj) {
             graph_launch(c, *gj);
-        else
-            body(j);
+        } else {
+            c.timing_suspended = !bracket;
+            try {
+                body(j);
+            } catch (...) {
+                c.timing_suspended = false;
+                throw;
+            }
+            c.timing_suspended = false;
+        }
         c.sync();
         if (gj) graph_collect(c, *gj);
     };
-    int it = 0, restarts = 0;
+    int it = 0;
     double est = 0.0;
     for (;;) {
         spmv_sub_f64(c, A, b, x, Vp);  // V0 = b - A x

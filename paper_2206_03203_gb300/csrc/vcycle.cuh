@@ -671,6 +671,277 @@ static void smooth_stored(Ctx &c, const Hierarchy &h, const Level &L, const XT *
     }
 }
 
+// ---------------------------------------------------------------- coarse tail
+// The coarse end of the hierarchy (every level at most TAIL_ROWS rows, fused
+// L1-Jacobi form, values of the vector type) runs as one kernel on one thread
+// block cluster: the phases of the down sweep (residual, restriction), the
+// dense coarsest solve and the up sweep (prolongation + post-smoothing) are
+// separated by cluster barriers instead of kernel boundaries.  The same
+// arithmetic as the per-level kernels with one thread per row; vectors
+// written inside the kernel are read through L2 (ld.global.cg).
+constexpr int TAIL_MAX = 8;
+constexpr int64_t TAIL_ROWS = 8192;
+constexpr int TAIL_THREADS = 512;
+
+template <class XT> struct TailLevel {
+    int64_t n, nc;
+    const int32_t *rp, *ci;
+    const XT *v;
+    const float *rscale;
+    const XT *dinv;
+    XT *b, *x, *r;
+    const int32_t *agg, *moff, *mem;  // agg == NULL: no coarser level
+};
+template <class XT> struct TailArgs {
+    int nlev;        // levels lv[0 .. nlev-1]; lv[nlev] holds the coarsest b, x when dense
+    int dense;
+    int64_t nd;
+    const double *M;  // dense inverse of the coarsest matrix
+    TailLevel<XT> lv[TAIL_MAX + 1];
+};
+
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Lanes per row for a level of n rows on T threads: the largest power of two
+// up to 32 that still gives every row its lanes in one pass.
+__device__ __forceinline__ int tail_lanes(int64_t n, int64_t T) {
+    int G = 1;
+    while (G < 32 && (int64_t)(2 * G) * n <= T) G *= 2;
+    return G;
+}
+
+template <class XT, int NR>
+__global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(TailArgs<XT> a) {
+    mds_pdl_wait();
+    mds_pdl_trigger();
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // down sweep: r = b - A D1^-1 b, b_c = P^T r
+    for (int li = 0; li < a.nlev; li++) {
+        const TailLevel<XT> &L = a.lv[li];
+        if (!L.agg) break;
+        const int G = tail_lanes(L.n, T);
+        const int lane = (int)(t0 % G);
+        for (int64_t base = 0; base < L.n; base += T / G) {
+            const int64_t i = base + t0 / G;
+            XT s[NR];
+#pragma unroll
+            for (int c = 0; c < NR; c++) s[c] = 0;
+            if (i < L.n) {
+                const int32_t p1 = L.rp[i + 1];
+#pragma unroll 4
+                for (int32_t p = L.rp[i] + lane; p < p1; p += G) {
+                    XT av = L.v[p];
+                    int32_t j = L.ci[p];
+                    XT dj = L.dinv[j];
+#pragma unroll
+                    for (int c = 0; c < NR; c++) s[c] += av * (dj * __ldcg(L.b + (int64_t)j * NR + c));
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < NR; c++)
+                for (int o = G / 2; o > 0; o >>= 1) s[c] += __shfl_down_sync(0xffffffffu, s[c], o, G);
+            if (i < L.n && lane == 0) {
+                XT sc = L.rscale ? (XT)L.rscale[i] : (XT)1;
+#pragma unroll
+                for (int c = 0; c < NR; c++) {
+                    XT sv = L.rscale ? s[c] * sc : s[c];
+                    __stcg(L.r + i * NR + c, __ldcg(L.b + i * NR + c) - sv);
+                }
+            }
+        }
+        cluster_barrier();
+        XT *bc = a.lv[li + 1].b;
+        for (int64_t I = t0; I < L.nc; I += T) {
+            XT s[NR];
+#pragma unroll
+            for (int c = 0; c < NR; c++) s[c] = 0;
+            const int32_t q1 = L.moff[I + 1];
+#pragma unroll 4
+            for (int32_t q = L.moff[I]; q < q1; q++) {
+                int64_t m = L.mem[q];
+#pragma unroll
+                for (int c = 0; c < NR; c++) s[c] += __ldcg(L.r + m * NR + c);
+            }
+#pragma unroll
+            for (int c = 0; c < NR; c++) __stcg(bc + I * NR + c, s[c]);
+        }
+        cluster_barrier();
+    }
+    // coarsest: x = M b, one warp per row
+    if (a.dense) {
+        const XT *bd = a.lv[a.nlev].b;
+        XT *xd = a.lv[a.nlev].x;
+        const int lane = threadIdx.x & 31;
+        const int64_t w0 = t0 >> 5, nw = T >> 5;
+        for (int64_t row = w0; row < a.nd; row += nw) {
+            double s[NR];
+#pragma unroll
+            for (int c = 0; c < NR; c++) s[c] = 0.0;
+#pragma unroll 4
+            for (int64_t k = lane; k < a.nd; k += 32) {
+                double m = a.M[row * a.nd + k];
+#pragma unroll
+                for (int c = 0; c < NR; c++) s[c] += m * (double)__ldcg(bd + k * NR + c);
+            }
+#pragma unroll
+            for (int c = 0; c < NR; c++)
+                for (int o = 16; o > 0; o >>= 1) s[c] += __shfl_down_sync(0xffffffffu, s[c], o);
+            if (lane == 0)
+#pragma unroll
+                for (int c = 0; c < NR; c++) __stcg(xd + row * NR + c, (XT)s[c]);
+        }
+        cluster_barrier();
+    }
+    // up sweep: x = y + D1^-1 (b - A y), y = D1^-1 b + P x_c
+    for (int li = a.nlev - 1; li >= 0; li--) {
+        const TailLevel<XT> &L = a.lv[li];
+        const XT *xc = L.agg ? a.lv[li + 1].x : nullptr;
+        const int G = tail_lanes(L.n, T);
+        const int lane = (int)(t0 % G);
+        for (int64_t base = 0; base < L.n; base += T / G) {
+            const int64_t i = base + t0 / G;
+            XT s[NR];
+#pragma unroll
+            for (int c = 0; c < NR; c++) s[c] = 0;
+            if (i < L.n) {
+                const int32_t p1 = L.rp[i + 1];
+#pragma unroll 4
+                for (int32_t p = L.rp[i] + lane; p < p1; p += G) {
+                    XT av = L.v[p];
+                    int32_t j = L.ci[p];
+                    XT dj = L.dinv[j];
+                    int32_t aj = xc ? L.agg[j] : -1;
+#pragma unroll
+                    for (int c = 0; c < NR; c++) {
+                        XT yj = dj * __ldcg(L.b + (int64_t)j * NR + c);
+                        if (aj >= 0) yj += __ldcg(xc + (int64_t)aj * NR + c);
+                        s[c] += av * yj;
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < NR; c++)
+                for (int o = G / 2; o > 0; o >>= 1) s[c] += __shfl_down_sync(0xffffffffu, s[c], o, G);
+            if (i < L.n && lane == 0) {
+                XT di = L.dinv[i];
+                int32_t ai = xc ? L.agg[i] : -1;
+                XT sc = L.rscale ? (XT)L.rscale[i] : (XT)1;
+#pragma unroll
+                for (int c = 0; c < NR; c++) {
+                    XT bi = __ldcg(L.b + i * NR + c);
+                    XT yi = di * bi;
+                    if (ai >= 0) yi += __ldcg(xc + (int64_t)ai * NR + c);
+                    XT sv = L.rscale ? s[c] * sc : s[c];
+                    __stcg(L.x + i * NR + c, yi + di * (bi - sv));
+                }
+            }
+        }
+        if (li > 0) cluster_barrier();
+    }
+}
+
+// Cluster size of the tail kernel: 16 blocks when the device schedules such
+// clusters, else 8 (the portable size).
+template <class XT, int NR> static int tail_cluster(Ctx &c) {
+    static int cl[64] = {};
+    int &v = cl[c.device & 63];
+    if (v) return v;
+    v = 8;
+    if (cudaFuncSetAttribute(k_vcycle_tail<XT, NR>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+        cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(16);
+        cfg.blockDim = dim3(TAIL_THREADS);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 16;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_vcycle_tail<XT, NR>, &cfg) == cudaSuccess && n > 0) v = 16;
+    }
+    cudaGetLastError();
+    return v;
+}
+
+// First level of the coarse tail (levels l0 .. last run in k_vcycle_tail), or
+// -1 when the hierarchy has no eligible tail.
+template <class XT> static int tail_start(const Hierarchy &h) {
+    const int last = (int)h.lv.size() - 1;
+    const int top = h.dense ? last - 1 : last;  // smoothed levels
+    if (h.smoother != MDS_SMOOTHER_L1JACOBI || h.sweeps != 1 || top < 0) return -1;
+    const int want_vt = std::is_same<XT, double>::value ? VT_F64 : VT_F32;
+    int l0 = -1;
+    for (int l = top; l >= 0 && top - l + 1 <= TAIL_MAX; l--) {
+        const Level &L = h.lv[l];
+        if (L.A.nrow > TAIL_ROWS || L.smoothed || L.vt != want_vt) break;
+        l0 = l;
+    }
+    return l0;
+}
+
+// Launches the tail kernel; false (nothing launched, tail disabled for the
+// hierarchy) when the device refuses the cluster launch.
+template <class XT, int NR>
+static bool vcycle_tail(Ctx &c, Hierarchy &h, int l0, const XT *b, XT *x) {
+    const int last = (int)h.lv.size() - 1;
+    const int top = h.dense ? last - 1 : last;
+    TailArgs<XT> a{};
+    a.nlev = top - l0 + 1;
+    a.dense = h.dense ? 1 : 0;
+    a.nd = h.nd;
+    a.M = h.dense ? h.Ainv.as<double>() : nullptr;
+    double bytes = 0.0;
+    for (int k = 0; k <= a.nlev && l0 + k <= last; k++) {
+        Level &L = h.lv[l0 + k];
+        TailLevel<XT> &t = a.lv[k];
+        t.n = L.A.nrow;
+        t.b = k == 0 ? const_cast<XT *>(b) : L.b.as<XT>();
+        t.x = k == 0 ? x : L.x.as<XT>();
+        if (k == a.nlev) break;  // coarsest dense level: vectors only
+        t.nc = L.has_coarse ? L.nc : 0;
+        t.rp = L.A.rowp();
+        t.ci = L.A.cols();
+        t.v = std::is_same<XT, double>::value ? (const XT *)L.A.vals() : L.vals_lp.as<XT>();
+        t.rscale = L.rscale.p ? L.rscale.as<float>() : nullptr;
+        t.dinv = L.dinv.as<XT>();
+        t.r = L.r.as<XT>();
+        t.agg = L.has_coarse ? L.agg.as<int32_t>() : nullptr;
+        t.moff = L.has_coarse ? L.mem_off.as<int32_t>() : nullptr;
+        t.mem = L.has_coarse ? L.mem.as<int32_t>() : nullptr;
+        bytes += 2.0 * (sizeof(XT) + 4.0) * L.A.nnz + 8.0 * (t.n + 1) + sizeof(XT) * NR * 8.0 * t.n;
+    }
+    if (a.dense) bytes += 8.0 * (double)h.nd * h.nd;
+    const int cl = tail_cluster<XT, NR>(c);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cl);
+    cfg.blockDim = dim3(TAIL_THREADS);
+    cfg.stream = c.stream;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = c.pdl && !c.setup_phase ? 1 : 0;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    KTimer kt(c, KC_NONE, bytes);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_vcycle_tail<XT, NR>, a);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h.use_tail = false;
+        return false;
+    }
+    c.post_launch();
+    return true;
+}
+
 constexpr int64_t FUSE_FP64_ROWS = 65536;
 
 template <class XT, int NR>
@@ -681,6 +952,7 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
         dense_apply(c, h.Ainv.as<double>(), h.nd, NR, b, x);
         return;
     }
+    if (h.use_tail && l == tail_start<XT>(h) && vcycle_tail<XT, NR>(c, h, l, b, x)) return;
     int64_t n = L.A.nrow;
     XT *r = L.r.as<XT>();
     double rbytes = 4.0 * (L.nc + 1) + 4.0 * n + sizeof(XT) * NR * (double)(n + L.nc);

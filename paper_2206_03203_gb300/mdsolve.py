@@ -50,7 +50,8 @@ class SetupOpts(C.Structure):
     _fields_ = [("theta", C.c_double), ("n_coarse", C.c_int64), ("max_levels", C.c_int),
                 ("stall_ratio", C.c_double), ("seed", C.c_uint64), ("smoother", C.c_int),
                 ("precision", C.c_int), ("lowp_from_level", C.c_int), ("kind", C.c_int), ("format", C.c_int),
-                ("sell_c", C.c_int), ("sell_sigma", C.c_int), ("sweeps", C.c_int), ("prolongation", C.c_int)]
+                ("sell_c", C.c_int), ("sell_sigma", C.c_int), ("sweeps", C.c_int), ("prolongation", C.c_int),
+                ("coarse_tail", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -123,6 +124,9 @@ _SIGS = {
     "mds_timing_reset": (C.c_int, [C.c_void_p]),
     "mds_timing_query": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "mds_timing_sample_every": (C.c_int, [C.c_void_p, C.c_int]),
+    "mds_timing_sampled": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mds_memcpy": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t]),
     "mds_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
 }
@@ -345,6 +349,17 @@ class Context:
         k = KCLASS.get(kclass, kclass)
         n, ms, by, fl = C.c_int64(), C.c_double(), C.c_double(), C.c_double()
         self._check(lib().mds_timing_query(self.h, k, C.byref(n), C.byref(ms), C.byref(by), C.byref(fl)))
+        return n.value, ms.value, by.value, fl.value
+
+    def timing_sample_every(self, every: int):
+        """Bracket timed classes only in every `every`-th FGMRES restart cycle."""
+        self._check(lib().mds_timing_sample_every(self.h, every))
+
+    def timing_sampled(self, kclass):
+        """(launches, ms, bytes, flops) of the bracketed launches of a class."""
+        k = KCLASS.get(kclass, kclass)
+        n, ms, by, fl = C.c_int64(), C.c_double(), C.c_double(), C.c_double()
+        self._check(lib().mds_timing_sampled(self.h, k, C.byref(n), C.byref(ms), C.byref(by), C.byref(fl)))
         return n.value, ms.value, by.value, fl.value
 
     def launch_count(self) -> int:

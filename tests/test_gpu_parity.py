@@ -466,6 +466,63 @@ def test_graphs_match_direct_launches(ctx, torch_mod, krylov, kind, precision):
     assert l0 == l1 and d0 == d1 and p0 == p1
 
 
+@pytest.mark.parametrize("case,precision,nr", [("seg2d-96", "fp64", 1), ("planes3d-16", "fp64", 1),
+                                               ("rects3d-18", "fp32", 1), ("seg2d-96", "fp64", 4)])
+def test_coarse_tail_matches_per_level_launches(ctx, torch_mod, case, precision, nr):
+    """The coarse end of the V-cycle run as one cluster kernel gives the same
+    V-cycle (to rounding) and the same solve as one launch per level op."""
+    torch = torch_mod
+    inst = CASES[case]()
+    sys_ = ctx.assemble(inst)
+    pre = [ctx.setup(sys_, precision=precision, coarse_tail=t) for t in (0, 1)]
+    gen = torch.Generator(device="cpu").manual_seed(7)
+    for blk, n in ((0, sys_.n_m), (1, sys_.n_f)):
+        if n == 0:
+            continue
+        b = torch.rand(n, generator=gen, dtype=torch.float64).to("cuda")
+        xs = []
+        for p in pre:
+            x = torch.zeros(n, dtype=torch.float64, device="cuda")
+            ctx.vcycle(p, blk, b, x)
+            xs.append(x)
+        rel = (torch.linalg.norm(xs[0] - xs[1]) / torch.linalg.norm(xs[0])).item()
+        assert rel <= (1e-13 if precision == "fp64" else 2e-6), (blk, rel)
+    its = []
+    for p in pre:
+        x = torch.zeros(sys_.N * nr, dtype=torch.float64, device="cuda")
+        B = torch.rand(sys_.N * nr, generator=gen.manual_seed(3), dtype=torch.float64).to("cuda")
+        code, st = ctx.solve(sys_, p, B, x, nrhs=nr, max_iters=3000)
+        assert code == 0
+        its.append([s_.iterations for s_ in st])
+    assert all(abs(a - b) <= 1 for a, b in zip(*its)), its
+
+
+def test_sampled_timing(ctx, torch_mod):
+    """With timing sampled every 4th restart cycle the solution is unchanged,
+    only some launches are bracketed, and the per-launch averages of the
+    bracketed subset are positive and consistent with the class totals."""
+    torch = torch_mod
+    inst = CASES["seg2d-96"]()
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_)
+    out = []
+    for every in (1, 4):
+        ctx.timing_enable("gs_dot", True)
+        ctx.timing_sample_every(every)
+        ctx.timing_reset()
+        x = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+        code, st = ctx.solve(sys_, prec, None, x, restart=5, max_iters=2000)
+        assert code == 0
+        out.append((x, st[0], ctx.timing_query("gs_dot"), ctx.timing_sampled("gs_dot")))
+    ctx.timing_sample_every(1)
+    ctx.timing_enable("gs_dot", False)
+    (x1, s1, q1, t1), (x4, s4, q4, t4) = out
+    assert torch.equal(x1, x4) and s1.iterations == s4.iterations
+    assert q1[0] == t1[0] == s1.iterations  # every launch bracketed
+    assert q4[0] == s4.iterations and 0 < t4[0] < q4[0]
+    assert t4[1] > 0 and t4[2] > 0 and t4[2] < q4[2]
+
+
 def test_context_outlives_dependents_in_any_order(torch_mod):
     """mds_destroy with live systems/preconditioners defers the release until
     the last of them is destroyed (any finalisation order is safe)."""
