@@ -111,6 +111,8 @@ def lib():
                                      C.c_double, C.c_int, _f64p, P(_Stats)]
             L.orc_pcg.argtypes = [P(_CSR), C.c_void_p, C.c_void_p, _f64p, _f64p, C.c_double,
                                   C.c_int, _f64p, P(_Stats)]
+            L.orc_minres.argtypes = [P(_CSR), C.c_void_p, C.c_void_p, _f64p, _f64p, C.c_double,
+                                     C.c_int, _f64p, P(_Stats)]
             _lib = L
     return _lib
 
@@ -382,10 +384,28 @@ def pcg(A, b, prec=None, x0=None, rtol=1e-8, maxit=1000, hA=None) -> Result:
                   hist[:st.history_len].copy())
 
 
+def minres(A, b, prec=None, x0=None, rtol=1e-8, maxit=1000, hA=None) -> Result:
+    """Preconditioned MINRES (symmetric A, SPD preconditioner)."""
+    n = A.shape[0]
+    hA = hA or CSR(A)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
+    fn, ctx, keep = _prec_args(prec, n)
+    hist = np.zeros(maxit + 2)
+    st = _Stats()
+    lib().orc_minres(hA.ptr, fn, ctx, _p(b, _f64p), _p(x, _f64p), rtol, maxit, _p(hist, _f64p),
+                     C.byref(st))
+    del keep
+    return Result(x, st.iterations, st.restarts, bool(st.converged), st.relres_true,
+                  hist[:st.history_len].copy())
+
+
 def solve(inst, rhs=0, kind="lower", krylov="fgmres", restart=30, rtol=1e-8, maxit=1000, **kw):
     """Assemble, set up M_L and solve one right-hand side of an instance."""
     A, b = assemble(inst)
     M = ML(A, inst.n_m, kind=kind, **kw)
     if krylov == "pcg":
         return pcg(A, b[rhs], M, rtol=rtol, maxit=maxit), A, b, M
+    if krylov == "minres":
+        return minres(A, b[rhs], M, rtol=rtol, maxit=maxit), A, b, M
     return fgmres(A, b[rhs], M, restart=restart, rtol=rtol, maxit=maxit), A, b, M

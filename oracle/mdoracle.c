@@ -1397,3 +1397,140 @@ int orc_pcg(const ocsr *A, orc_prec_fn prec, void *pctx, const double *b, double
     free(q);
     return err ? -1 : (conv ? 0 : 1);
 }
+
+/* Preconditioned MINRES (Paige and Saunders 1975), in the three-term form of
+ * Elman, Silvester and Wathen (Finite Elements and Fast Iterative Solvers,
+ * preconditioned MINRES): Lanczos vectors v with z = M v normalised in the
+ * M-inner product, Givens rotations (c, s) on the tridiagonal matrix, search
+ * directions w, and eta the M^-1-norm of the residual.  The 2-norm residual
+ * r is carried along by the same recurrence as x (A w is formed from A z, so
+ * no extra product is needed); when it reaches rtol ||b|| the true residual
+ * decides, and the iteration restarts from x if it is not yet small enough.
+ * Iterations count preconditioner applications after the first. */
+int orc_minres(const ocsr *A, orc_prec_fn prec, void *pctx, const double *b, double *x,
+               double rtol, int maxit, double *hist, orc_stats *st) {
+    int64_t n = A->nrow;
+    double *r = (double *)calloc((size_t)n, sizeof(double));
+    double *v0 = (double *)calloc((size_t)n, sizeof(double));
+    double *v1 = (double *)calloc((size_t)n, sizeof(double));
+    double *z = (double *)calloc((size_t)n, sizeof(double));
+    double *az = (double *)calloc((size_t)n, sizeof(double));
+    double *w0 = (double *)calloc((size_t)n, sizeof(double));
+    double *w1 = (double *)calloc((size_t)n, sizeof(double));
+    double *aw0 = (double *)calloc((size_t)n, sizeof(double));
+    double *aw1 = (double *)calloc((size_t)n, sizeof(double));
+    double *t = (double *)calloc((size_t)n, sizeof(double));
+    int it = 0, conv = 0, hl = 0, err = 0, restarts = 0;
+    double bn = nrm2(n, b);
+    if (bn == 0.0) bn = 1.0;
+    for (;;) {
+        orc_spmv(A, x, t);
+        for (int64_t i = 0; i < n; i++) r[i] = b[i] - t[i];
+        double rn = nrm2(n, r);
+        if (hist && hl == 0) hist[hl++] = rn / bn;
+        if (rn / bn <= rtol || it >= maxit) break;
+        /* v1 = r, z = M v1, gamma1 = sqrt(z . v1) */
+        for (int64_t i = 0; i < n; i++) {
+            v1[i] = r[i];
+            v0[i] = 0.0;
+            w0[i] = w1[i] = aw0[i] = aw1[i] = 0.0;
+        }
+        if (prec(pctx, v1, z) != 0) {
+            err = 1;
+            break;
+        }
+        double g1 = sqrt(dot(n, z, v1));
+        if (!(g1 > 0.0)) {
+            err = 1;
+            break;
+        }
+        double g0 = 1.0, eta = g1, c0 = 1.0, c1 = 1.0, s0 = 0.0, s1 = 0.0;
+        int restart = 0;
+        while (it < maxit) {
+            it++;
+            /* z_j = z / gamma_j; delta_j = (A z_j) . z_j */
+            for (int64_t i = 0; i < n; i++) z[i] /= g1;
+            orc_spmv(A, z, az);
+            double delta = dot(n, az, z);
+            /* v_{j+1} = A z_j - (delta/gamma_j) v_j - (gamma_j/gamma_{j-1}) v_{j-1} */
+            for (int64_t i = 0; i < n; i++) {
+                double vn = az[i] - (delta / g1) * v1[i] - (g1 / g0) * v0[i];
+                v0[i] = v1[i];
+                v1[i] = vn;
+            }
+            /* Givens rotations on the new column of the tridiagonal matrix */
+            double a0 = c1 * delta - c0 * s1 * g1;
+            double a2 = s1 * delta + c0 * c1 * g1;
+            double a3 = s0 * g1;
+            /* z_{j+1} = M v_{j+1}, gamma_{j+1}; t keeps z_j for w */
+            for (int64_t i = 0; i < n; i++) t[i] = z[i];
+            if (prec(pctx, v1, z) != 0) {
+                err = 1;
+                break;
+            }
+            double zv = dot(n, z, v1);
+            double g2 = zv > 0.0 ? sqrt(zv) : 0.0;
+            double a1 = sqrt(a0 * a0 + g2 * g2);
+            if (!(a1 > 0.0)) {
+                err = 1;
+                break;
+            }
+            double c2 = a0 / a1, s2 = g2 / a1;
+            /* w_{j+1} = (z_j - a3 w_{j-1} - a2 w_j) / a1, and A w likewise */
+            double step = c2 * eta;
+            for (int64_t i = 0; i < n; i++) {
+                double wn = (t[i] - a3 * w0[i] - a2 * w1[i]) / a1;
+                double awn = (az[i] - a3 * aw0[i] - a2 * aw1[i]) / a1;
+                w0[i] = w1[i];
+                w1[i] = wn;
+                aw0[i] = aw1[i];
+                aw1[i] = awn;
+                x[i] += step * wn;
+                r[i] -= step * awn;
+            }
+            eta = -s2 * eta;
+            g0 = g1;
+            g1 = g2;
+            c0 = c1;
+            c1 = c2;
+            s0 = s1;
+            s1 = s2;
+            double rr = nrm2(n, r);
+            if (hist) hist[hl++] = rr / bn;
+            if (rr / bn <= rtol) break;
+            if (!(g2 > 0.0)) { /* invariant subspace: exact within the Krylov space */
+                restart = 1;
+                break;
+            }
+        }
+        if (err) break;
+        (void)restart;
+        restarts++;
+        if (it >= maxit) {
+            orc_spmv(A, x, t);
+            break;
+        }
+    }
+    orc_spmv(A, x, t);
+    for (int64_t i = 0; i < n; i++) t[i] = b[i] - t[i];
+    double tr = nrm2(n, t) / bn;
+    conv = tr <= rtol;
+    if (st) {
+        st->iterations = it;
+        st->restarts = restarts > 0 ? restarts - 1 : 0;
+        st->converged = conv;
+        st->relres_true = tr;
+        st->history_len = hl;
+    }
+    free(r);
+    free(v0);
+    free(v1);
+    free(z);
+    free(az);
+    free(w0);
+    free(w1);
+    free(aw0);
+    free(aw1);
+    free(t);
+    return err ? -1 : (conv ? 0 : 1);
+}

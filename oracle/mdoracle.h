@@ -117,6 +117,11 @@ int orc_fgmres(const ocsr *A, orc_prec_fn prec, void *pctx, const double *b, dou
 /* Preconditioned conjugate gradients (symmetric preconditioner). */
 int orc_pcg(const ocsr *A, orc_prec_fn prec, void *pctx, const double *b, double *x,
             double rtol, int maxit, double *hist, orc_stats *st);
+/* Preconditioned MINRES for symmetric A and a symmetric positive definite
+ * preconditioner (the block-diagonal B_D of Sec. 3.2 with symmetric
+ * V-cycles); same stopping rule and iteration count as orc_pcg. */
+int orc_minres(const ocsr *A, orc_prec_fn prec, void *pctx, const double *b, double *x,
+               double rtol, int maxit, double *hist, orc_stats *st);
 
 #ifdef __cplusplus
 }

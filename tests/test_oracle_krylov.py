@@ -137,3 +137,79 @@ def test_mixed_precision_emulation_converges(oracle_mod):
     assert r32.converged and r16.converged
     assert abs(r32.iterations - r64.iterations) <= 3
     assert r16.iterations <= r64.iterations + 10
+
+
+def _krylov_lsq(A, b, k):
+    """argmin ||b - A x||_2 over x in span{b, A b, ..., A^(k-1) b}, by an
+    explicit QR of the Krylov matrix (brute force, small k)."""
+    K = np.empty((A.shape[0], k))
+    v = b.copy()
+    for j in range(k):
+        K[:, j] = v / np.linalg.norm(v)
+        v = A @ K[:, j]
+    Q, _ = np.linalg.qr(K)
+    y, *_ = np.linalg.lstsq(A @ Q, b, rcond=None)
+    return Q @ y
+
+
+def test_minres_minimises_residual_over_krylov_space(oracle_mod):
+    """MINRES with the identity preconditioner: the k-th iterate is the
+    minimum-residual point of the k-th Krylov space (symmetric indefinite
+    matrix, where CG has no such property), and the 2-norm residual never
+    grows."""
+    rng = np.random.default_rng(11)
+    n = 30
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.concatenate([np.linspace(-3.0, -0.5, 12), np.linspace(0.7, 5.0, n - 12)])
+    Ad = (Q * lam) @ Q.T
+    Ad = 0.5 * (Ad + Ad.T)
+    A = sp.csr_matrix(Ad)
+    b = rng.standard_normal(n)
+    for k in (1, 3, 6, 10):
+        res = oracle_mod.minres(A, b, "identity", rtol=1e-300, maxit=k)
+        assert res.iterations == k
+        xk = _krylov_lsq(Ad, b, k)
+        assert np.linalg.norm(res.x - xk) <= 1e-8 * (1 + np.linalg.norm(xk)), k
+    full = oracle_mod.minres(A, b, "identity", rtol=1e-10, maxit=200)
+    assert full.converged
+    assert np.all(np.diff(full.history) <= 1e-12)
+    assert np.linalg.norm(full.x - np.linalg.solve(Ad, b)) <= 1e-7 * np.linalg.norm(np.linalg.solve(Ad, b))
+
+
+def test_minres_preconditioned_norm_decreases(oracle_mod):
+    """With an SPD preconditioner M, the iterates minimise the residual in the
+    M-inverse norm over the preconditioned Krylov space: that norm never
+    grows with k (checked by restarting the solve with more steps)."""
+    rng = np.random.default_rng(5)
+    n = 24
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.concatenate([np.linspace(-2.0, -0.3, 8), np.linspace(0.4, 6.0, n - 8)])
+    Ad = (Q * lam) @ Q.T
+    Ad = 0.5 * (Ad + Ad.T)
+    A = sp.csr_matrix(Ad)
+    G = rng.standard_normal((n, n))
+    Md = G @ G.T / n + np.eye(n)  # SPD preconditioner (applied as M^-1 = Md)
+    Mi = np.linalg.inv(Md)
+    b = rng.standard_normal(n)
+    norms = []
+    for k in range(1, 14):
+        res = oracle_mod.minres(A, b, lambda r: Md @ r, rtol=1e-300, maxit=k)
+        r = b - Ad @ res.x
+        norms.append(np.sqrt(r @ (Md @ r)))
+    assert all(b_ <= a_ * (1 + 1e-10) for a_, b_ in zip(norms, norms[1:]))
+    full = oracle_mod.minres(A, b, lambda r: Md @ r, rtol=1e-10, maxit=400)
+    assert full.converged
+    assert np.linalg.norm(full.x - np.linalg.solve(Ad, b)) <= 1e-7 * np.linalg.norm(np.linalg.solve(Ad, b))
+    del Mi
+
+
+def test_minres_block_diagonal_on_assembled_system(oracle_mod):
+    """B_D (one symmetric V-cycle per block) with MINRES on the assembled
+    mixed-dimensional system reaches the direct solution."""
+    inst = inputs.planes_3d(n=8, kf=1.0)
+    res, A, b, M = oracle_mod.solve(inst, kind="diag", krylov="minres", maxit=500)
+    assert res.converged and res.relres <= 1e-8
+    xd = spla.spsolve(A.tocsc(), b[0])
+    assert np.max(np.abs(res.x - xd)) < 1e-6
+    pc, *_ = oracle_mod.solve(inst, kind="diag", krylov="pcg", maxit=500)
+    assert abs(res.iterations - pc.iterations) <= max(3, pc.iterations // 4)
