@@ -103,18 +103,20 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def profile_traffic(kernel_class: str):
+def profile_traffic(kernel_class: str, avg_alg_bytes: float):
     """DRAM bytes per launch of a kernel class from the committed ncu summary
-    (profiles/traffic.txt lines: '<class> <workload> <bytes-per-launch>')."""
+    (profiles/traffic.txt lines: '<class> <workload> <dram bytes> <algorithmic
+    bytes of that launch>'), scaled to this run's average launch by the ratio
+    of algorithmic bytes."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
     for line in open(p):
         f = line.split()
-        if len(f) >= 3 and not line.startswith("#") and f[0] == kernel_class and f[1] == "seg2d-1024":
+        if len(f) >= 4 and not line.startswith("#") and f[0] == kernel_class and f[1] == "seg2d-1024":
             try:
-                return float(f[2])
-            except ValueError:
+                return float(f[2]) / float(f[3]) * avg_alg_bytes
+            except (ValueError, ZeroDivisionError):
                 return None
     return None
 
@@ -165,20 +167,31 @@ def run_gpu(args):
             s.close()
         return its
 
-    # warm-up; the first one also profiles every kernel class to find the dominant one
+    peak, peak_src = measured_peaks()
+    # warm-up; the first one also profiles every kernel class (events around
+    # the launches of every 4th FGMRES restart cycle) to find the dominant one
     classes = ["spmv", "vc_resid", "vc_post", "vc_restrict", "gs_dot", "gs_axpy"]
     for c in classes:
         ctx.timing_enable(c, True)
+    ctx.timing_sample_every(4)
     ctx.timing_reset()
     its = step()
-    share = {c: ctx.timing_query(c)[1] for c in classes}
-    flops_kind = {c: "fp64" for c in classes}
+    share, per_class = {}, {}
+    for c in classes:
+        n_all, _, _, _ = ctx.timing_query(c)
+        n_t, ms_t, by_t, fl_t = ctx.timing_sampled(c)
+        avg = ms_t / n_t if n_t else 0.0
+        share[c] = avg * n_all  # estimated total time of the class
+        if n_t and ms_t > 0:
+            gbs_c = by_t / (ms_t / 1e3) / 1e9
+            tf_c = fl_t / (ms_t / 1e3) / 1e12
+            per_class[c] = {"launches_per_step": n_all, "avg_launch_us": round(avg * 1e3, 3),
+                            "algorithmic_bytes_per_launch": by_t / n_t, "hbm_gbs": round(gbs_c, 1),
+                            "hbm_frac_of_measured": round(gbs_c / peak, 4), "fp64_tflops": round(tf_c, 4),
+                            "fp64_frac_of_nominal": round(tf_c / FP64_PEAK_TFLOPS, 4)}
     dominant = max(share, key=share.get)
     for c in classes:
         ctx.timing_enable(c, c == dominant)
-    # bracket the dominant class with events in every 4th FGMRES restart cycle
-    # only, so that the brackets do not slow the timed steps down
-    ctx.timing_sample_every(4)
     for _ in range(max(0, args.warmup - 1)):
         step()
     torch.cuda.synchronize()
@@ -206,6 +219,8 @@ def run_gpu(args):
     launches = ctx.launch_count()
     kl_all = ctx.timing_query(dominant)[0]
     kl, kms, kbytes, kflops = ctx.timing_sampled(dominant)
+    for c in classes:
+        ctx.timing_enable(c, False)
     clk = clocks.stop()
     torch.cuda.synchronize()
     if world > 1:
@@ -238,7 +253,6 @@ def run_gpu(args):
         d2h += 8 * (inst.n_m + inst.n_f)
     e2e_value = len(insts) * e2e_steps / e2e_t * world
 
-    peak, peak_src = measured_peaks()
     avg_ms = kms / max(kl, 1)
     avg_bytes = kbytes / max(kl, 1)
     avg_flops = kflops / max(kl, 1)
@@ -246,7 +260,7 @@ def run_gpu(args):
     tflops = avg_flops / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else None
     hbm_frac = gbs / peak if gbs else None
     alu_frac = tflops / FP64_PEAK_TFLOPS if tflops else None
-    traffic = profile_traffic(dominant)
+    traffic = profile_traffic(dominant, avg_bytes)
     if alu_frac and hbm_frac and alu_frac > hbm_frac:
         roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
                 "frac": alu_frac, "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (152 SMs x 2070 MHz); "
@@ -260,7 +274,8 @@ def run_gpu(args):
                  "avg_launch_ms": avg_ms,
                  "hbm_gbs": gbs, "hbm_frac_of_measured": hbm_frac, "fp64_tflops": tflops,
                  "fp64_frac_of_nominal": alu_frac,
-                 "time_share_warmup": {k: round(v / max(sum(share.values()), 1e-9), 3) for k, v in share.items()}})
+                 "time_share_warmup": {k: round(v / max(sum(share.values()), 1e-9), 3) for k, v in share.items()},
+                 "classes_warmup": per_class})
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3, "higher_is_better": True,
@@ -308,6 +323,27 @@ def _timed(fn, flush, warmup=1, steps=1):
     return tot / steps, out
 
 
+def class_rates(ctx, fn, classes=("spmv", "vc_resid", "vc_post", "vc_restrict", "gs_dot", "gs_axpy")):
+    """Per-class launch averages of one run of fn() (events around every 4th
+    restart cycle): achieved HBM GB/s and FP64 TFLOP/s against the peaks."""
+    peak, _ = measured_peaks()
+    for c in classes:
+        ctx.timing_enable(c, True)
+    ctx.timing_sample_every(4)
+    ctx.timing_reset()
+    fn()
+    out = {}
+    for c in classes:
+        n_t, ms_t, by_t, fl_t = ctx.timing_sampled(c)
+        ctx.timing_enable(c, False)
+        if n_t and ms_t > 0:
+            gbs = by_t / (ms_t / 1e3) / 1e9
+            out[c] = {"avg_launch_us": round(ms_t / n_t * 1e3, 3), "algorithmic_bytes_per_launch": by_t / n_t,
+                      "hbm_gbs": round(gbs, 1), "hbm_frac_of_measured": round(gbs / peak, 4),
+                      "fp64_tflops": round(fl_t / (ms_t / 1e3) / 1e12, 4)}
+    return out
+
+
 def variants(ctx, insts, dev_arrays, N, flush):
     """Secondary measurements (not the headline): the FP32 V-cycle path on the
     same sweep, the nine-plane 3D instance, and the 256-instance batch."""
@@ -331,7 +367,8 @@ def variants(ctx, insts, dev_arrays, N, flush):
 
     t, its = _timed(lambda: sweep("fp32"), flush)
     out["seg2d_1024_sweep_fp32_vcycle"] = {"solves_per_s": len(insts) / t, "s_per_step": t, "iterations": its,
-                                           "precision": "FP32 V-cycle values/vectors, FP64 FGMRES"}
+                                           "precision": "FP32 V-cycle values/vectors, FP64 FGMRES",
+                                           "classes": class_rates(ctx, lambda: sweep("fp32"))}
     p3 = inputs.planes_3d(128, kf=1e4)
     for prec in ("fp64", "fp32"):
         def one(prec=prec):

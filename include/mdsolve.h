@@ -234,8 +234,10 @@ int mds_vcycle(mds_ctx ctx, mds_precond prec, int block, const double *b, double
 int mds_spmv(mds_ctx ctx, mds_system sys, const double *x, double *y);
 
 /* ---- solve ---- */
-#define MDS_KRYLOV_FGMRES 0
-#define MDS_KRYLOV_PCG 1
+#define MDS_KRYLOV_FGMRES 0  /* right-preconditioned flexible GMRES(restart) (Sec. 3.2) */
+#define MDS_KRYLOV_PCG 1     /* preconditioned CG: SPD system and SPD preconditioner (B_D) */
+#define MDS_KRYLOV_MINRES 2  /* preconditioned MINRES: symmetric system, SPD preconditioner (B_D);
+                                iterations = preconditioner applications after the first */
 
 typedef struct {
     int krylov;          /* MDS_KRYLOV_* */
@@ -306,8 +308,10 @@ int mds_solve_noalloc(mds_ctx ctx, mds_system sys, mds_precond prec, const doubl
  * 0 = full-system SpMV, 1 = V-cycle residual (pre-smooth + residual),
  * 2 = V-cycle post-smooth (prolongation + correction + smoothing),
  * 3 = Gram-Schmidt dot products, 4 = Gram-Schmidt updates, 5 = all V-cycle
- * kernels together, 6 = restriction.  Bytes are algorithmic (each matrix and
- * vector byte counted once per launch). */
+ * kernels together, 6 = restriction.  Classes 1, 2 and 6 count the kernels of
+ * the finest level of hierarchies with at least 65536 rows (the coarser
+ * levels' kernels are counted in no class).  Bytes are algorithmic (each
+ * matrix and vector byte counted once per launch). */
 #define MDS_KCLASS_COUNT 8
 int mds_timing_enable(mds_ctx ctx, int kclass, int enable);
 int mds_timing_reset(mds_ctx ctx);

@@ -635,6 +635,8 @@ int mds_solve(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, do
     if (opts) o = *opts;
     MDS_REQUIRE(o.rtol > 0.0 && o.max_iters >= 0 && o.restart >= 1 && o.reorth_eta2 >= 0.0, MDS_ERR_INVALID,
                 "bad solve options");
+    MDS_REQUIRE(o.krylov == MDS_KRYLOV_FGMRES || o.krylov == MDS_KRYLOV_PCG || o.krylov == MDS_KRYLOV_MINRES,
+                MDS_ERR_INVALID, "unknown Krylov method");
     MDS_REQUIRE(!o.use_precond || (prec && prec->sys == sys), MDS_ERR_INVALID, "preconditioner of another system");
     MDS_REQUIRE(b || nrhs <= sys->nrhs, MDS_ERR_INVALID, "more right-hand sides than assembled");
     int64_t n = sys->n_m + sys->n_f;
@@ -698,8 +700,9 @@ int mds_solve(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, do
     for (int k = 0; k < (batched ? 0 : nrhs); k++) {
         const double *bk = Bd + (size_t)k * n;
         double *xk = Xd + (size_t)k * n;
-        KrylovResult r = o.krylov == MDS_KRYLOV_PCG ? pcg(*c, sys->view[4], M, bk, xk, n, o)
-                                                    : fgmres(*c, sys->view[4], M, bk, xk, n, o);
+        KrylovResult r = o.krylov == MDS_KRYLOV_PCG      ? pcg(*c, sys->view[4], M, bk, xk, n, o)
+                         : o.krylov == MDS_KRYLOV_MINRES ? minres(*c, sys->view[4], M, bk, xk, n, o)
+                                                         : fgmres(*c, sys->view[4], M, bk, xk, n, o);
         if (stats) {
             stats[k].iterations = r.iterations;
             stats[k].restarts = r.restarts;

@@ -340,6 +340,9 @@ struct Level {
     Buf mem_off;      // int32 [nc+1] members of each next-level aggregate
     Buf mem;          // int32 [#aggregated], ascending within an aggregate
     int64_t mem_count = 0;  // #aggregated vertices
+    // the finest level of a large hierarchy: its V-cycle kernels are the ones
+    // counted in the timed classes (coarse levels launch as KC_NONE)
+    bool timed_level = false;
     Buf l1;           // FP64 [n]
     Buf dinv;         // [n] 1/l1 in the vector precision
     bool has_coarse = false;

@@ -384,6 +384,105 @@ __global__ void __launch_bounds__(RED_BLOCK) k_pcg_xr(int64_t n, double *__restr
     }
 }
 
+// ---- preconditioned MINRES (three-term Lanczos in the M-inner product with
+// Givens rotations; Paige and Saunders 1975, in the recurrence of Elman,
+// Silvester and Wathen).  Device scalars, indices into sc[]:
+enum { MR_G0 = 0, MR_G1, MR_C0, MR_C1, MR_S0, MR_S1, MR_ETA, MR_DELTA, MR_ZV, MR_RR, MR_A1, MR_A2, MR_A3, MR_STEP,
+       MR_FLAG, MR_G2, MR_COUNT };
+
+// t = z / gamma_j (the normalised z_j)
+__global__ void k_mr_scale(int64_t n, const double *__restrict__ z, const double *__restrict__ sc,
+                           double *__restrict__ t) {
+    mds_pdl_entry();
+    double g = sc[MR_G1];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        t[i] = z[i] / g;
+}
+
+// v_old <- A z_j - (delta / gamma_j) v_cur - (gamma_j / gamma_{j-1}) v_old
+__global__ void k_mr_lanczos(int64_t n, const double *__restrict__ az, const double *__restrict__ vcur,
+                             double *__restrict__ vold, const double *__restrict__ sc) {
+    mds_pdl_entry();
+    double a = sc[MR_DELTA] / sc[MR_G1], b = sc[MR_G1] / sc[MR_G0];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        vold[i] = az[i] - a * vcur[i] - b * vold[i];
+}
+
+// Rotations for the new column of the tridiagonal matrix; the step length
+// along w_{j+1}; the scalars shifted for the next step.  MR_FLAG = 1 when the
+// rotation is undefined (breakdown).
+__global__ void k_mr_rotate(double *__restrict__ sc) {
+    mds_pdl_entry();
+    double g0 = sc[MR_G0], g1 = sc[MR_G1], c0 = sc[MR_C0], c1 = sc[MR_C1], s0 = sc[MR_S0], s1 = sc[MR_S1];
+    double delta = sc[MR_DELTA], zv = sc[MR_ZV], eta = sc[MR_ETA];
+    double a0 = c1 * delta - c0 * s1 * g1;
+    double a2 = s1 * delta + c0 * c1 * g1;
+    double a3 = s0 * g1;
+    double g2 = zv > 0.0 ? sqrt(zv) : 0.0;
+    double a1 = sqrt(a0 * a0 + g2 * g2);
+    bool bad = !(a1 > 0.0) || !isfinite(a1);
+    double c2 = bad ? 1.0 : a0 / a1, s2 = bad ? 0.0 : g2 / a1;
+    sc[MR_A1] = bad ? 1.0 : a1;
+    sc[MR_A2] = a2;
+    sc[MR_A3] = a3;
+    sc[MR_STEP] = bad ? 0.0 : c2 * eta;
+    sc[MR_ETA] = -s2 * eta;
+    sc[MR_FLAG] = bad ? 1.0 : 0.0;
+    sc[MR_G2] = g2;
+    sc[MR_G0] = g1;
+    sc[MR_G1] = g2 > 0.0 ? g2 : 1.0;
+    sc[MR_C0] = c1;
+    sc[MR_C1] = c2;
+    sc[MR_S0] = s1;
+    sc[MR_S1] = s2;
+    (void)g0;
+}
+
+// w_old <- (z_j - a3 w_old - a2 w_cur) / a1, the same for A w, then
+// x += step w_new, r -= step A w_new, and block partials of ||r||^2.
+__global__ void __launch_bounds__(RED_BLOCK) k_mr_update(int64_t n, const double *__restrict__ t,
+                                                         const double *__restrict__ az, double *__restrict__ wold,
+                                                         const double *__restrict__ wcur, double *__restrict__ awold,
+                                                         const double *__restrict__ awcur, double *__restrict__ x,
+                                                         double *__restrict__ r, const double *__restrict__ sc,
+                                                         double *__restrict__ partial) {
+    mds_pdl_entry();
+    __shared__ double ws[RED_BLOCK / 32];
+    const double a1 = sc[MR_A1], a2 = sc[MR_A2], a3 = sc[MR_A3], step = sc[MR_STEP];
+    double nrm = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double wn = (t[i] - a3 * wold[i] - a2 * wcur[i]) / a1;
+        double awn = (az[i] - a3 * awold[i] - a2 * awcur[i]) / a1;
+        wold[i] = wn;
+        awold[i] = awn;
+        x[i] += step * wn;
+        double ri = r[i] - step * awn;
+        r[i] = ri;
+        nrm += ri * ri;
+    }
+    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < RED_BLOCK / 32; k++) s += ws[k];
+        partial[(int64_t)blockIdx.x * QMAX] = s;
+    }
+}
+
+// start of a cycle: gamma_1 = sqrt(z . v), eta = gamma_1, rotations reset
+__global__ void k_mr_start(double *__restrict__ sc) {
+    mds_pdl_entry();
+    double zv = sc[MR_ZV];
+    double g1 = zv > 0.0 ? sqrt(zv) : 0.0;
+    sc[MR_G0] = 1.0;
+    sc[MR_G1] = g1 > 0.0 ? g1 : 1.0;
+    sc[MR_G2] = g1;
+    sc[MR_C0] = sc[MR_C1] = 1.0;
+    sc[MR_S0] = sc[MR_S1] = 0.0;
+    sc[MR_ETA] = g1;
+}
+
 __global__ void k_copy1(const double *__restrict__ a, double *__restrict__ b) { mds_pdl_entry(); *b = *a; }
 
 // ---------------------------------------------------------------- host side
@@ -697,6 +796,114 @@ KrylovResult pcg(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, dou
     res.relres_est = rn / bn;
     res.iterations = it;
     if (res.status != MDS_ERR_BREAKDOWN) res.status = res.relres_true <= o.rtol ? MDS_OK : MDS_WARN_NOT_CONVERGED;
+    return res;
+}
+
+KrylovResult minres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, double *x, int64_t n,
+                    const mds_solve_opts &o) {
+    KrylovResult res;
+    Red R;
+    R.grid = red_grid(n);
+    R.partial = Buf(&c, sizeof(double) * (size_t)R.grid * QMAX);
+    R.pp = R.partial.as<double>();
+    // r, z, t (= z_j), A z_j, v[2], w[2], A w[2]
+    Buf buf(&c, sizeof(double) * (size_t)n * 10);
+    double *r = buf.as<double>(), *z = r + n, *t = z + n, *az = t + n;
+    double *v[2] = {az + n, az + 2 * n}, *w[2] = {az + 3 * n, az + 4 * n}, *aw[2] = {az + 5 * n, az + 6 * n};
+    Buf small(&c, sizeof(double) * 32);
+    double *sc = small.as<double>();
+    const unsigned eg = red_grid(n);
+    dot_dev(c, R, n, b, b, sc + MR_RR);
+    double bn = std::sqrt(c.read(sc + MR_RR));
+    if (!(bn < INFINITY)) {
+        res.status = MDS_ERR_NONFINITE;
+        return res;
+    }
+    if (bn == 0.0) bn = 1.0;
+    // one Lanczos step with parity p: v[p], w[p], aw[p] hold the older
+    // vectors and receive the new ones
+    auto body = [&](int p) {
+        const int q = 1 - p;
+        MDS_LAUNCH(c, KC_NONE, 16.0 * n, k_mr_scale, eg, RED_BLOCK, 0, n, z, sc, t);
+        spmv_f64(c, A, t, az, KC_SPMV);
+        dot_dev(c, R, n, az, t, sc + MR_DELTA);
+        MDS_LAUNCH(c, KC_NONE, 32.0 * n, k_mr_lanczos, eg, RED_BLOCK, 0, n, az, v[q], v[p], sc);
+        M(v[p], z);
+        dot_dev(c, R, n, z, v[p], sc + MR_ZV);
+        MDS_LAUNCH(c, KC_NONE, 0, k_mr_rotate, 1, 1, 0, sc);
+        MDS_LAUNCH(c, KC_NONE, 104.0 * n, k_mr_update, R.grid, RED_BLOCK, 0, n, t, az, w[p], w[q], aw[p], aw[q], x, r,
+                   sc, R.pp);
+        MDS_LAUNCH(c, KC_NONE, 0, k_reduce_cols, 1, 32, 0, R.pp, (int)R.grid, 1, sc + MR_RR, 0);
+        MDS_CUDA(cudaMemcpyAsync(c.h_pin, sc, sizeof(double) * MR_COUNT, cudaMemcpyDeviceToHost, c.stream));
+    };
+    std::unique_ptr<Graph> graphs[2];
+    bool graphs_ok = o.graphs != 0;
+    int it = 0, cycles = 0;
+    double rr = 0.0;
+    for (;;) {
+        spmv_sub_f64(c, A, b, x, r);
+        dot_dev(c, R, n, r, r, sc + MR_RR);
+        rr = std::sqrt(c.read(sc + MR_RR));
+        if (!std::isfinite(rr)) {
+            res.status = MDS_ERR_NONFINITE;
+            break;
+        }
+        if (rr / bn <= o.rtol || it >= o.max_iters) break;
+        cycles++;
+        // v[1] = r, v[0] = w = A w = 0, z = M v[1], gamma_1
+        MDS_CUDA(cudaMemcpyAsync(v[1], r, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, c.stream));
+        MDS_CUDA(cudaMemsetAsync(v[0], 0, sizeof(double) * (size_t)n, c.stream));
+        MDS_CUDA(cudaMemsetAsync(w[0], 0, sizeof(double) * (size_t)n * 2, c.stream));
+        MDS_CUDA(cudaMemsetAsync(aw[0], 0, sizeof(double) * (size_t)n * 2, c.stream));
+        M(v[1], z);
+        dot_dev(c, R, n, z, v[1], sc + MR_ZV);
+        MDS_LAUNCH(c, KC_NONE, 0, k_mr_start, 1, 1, 0, sc);
+        if (!(c.read(sc + MR_G2) > 0.0)) {
+            res.status = MDS_ERR_BREAKDOWN;
+            break;
+        }
+        int p = 0;
+        bool stop = false;
+        while (it < o.max_iters) {
+            Graph *gj = nullptr;
+            if (graphs_ok) {
+                if (!graphs[p]) {
+                    graphs[p].reset(new Graph);
+                    if (!graph_capture(c, *graphs[p], [&] { body(p); })) {
+                        graphs[p].reset();
+                        graphs_ok = false;
+                    }
+                }
+                gj = graphs[p].get();
+            }
+            if (gj)
+                graph_launch(c, *gj);
+            else
+                body(p);
+            c.sync();
+            if (gj) graph_collect(c, *gj);
+            it++;
+            p = 1 - p;
+            double s[MR_COUNT];
+            std::memcpy(s, c.h_pin, sizeof s);
+            rr = std::sqrt(s[MR_RR]);
+            if (s[MR_FLAG] != 0.0 || !std::isfinite(rr)) {
+                res.status = MDS_ERR_BREAKDOWN;
+                stop = true;
+                break;
+            }
+            if (rr / bn <= o.rtol) break;
+            if (!(s[MR_G2] > 0.0)) break;  // invariant subspace: restart from x
+        }
+        if (stop) break;
+    }
+    spmv_sub_f64(c, A, b, x, r);
+    dot_dev(c, R, n, r, r, sc + MR_RR);
+    res.relres_true = std::sqrt(c.read(sc + MR_RR)) / bn;
+    res.relres_est = rr / bn;
+    res.iterations = it;
+    res.restarts = cycles > 0 ? cycles - 1 : 0;
+    if (res.status == MDS_OK) res.status = res.relres_true <= o.rtol ? MDS_OK : MDS_WARN_NOT_CONVERGED;
     return res;
 }
 

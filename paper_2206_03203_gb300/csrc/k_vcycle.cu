@@ -256,6 +256,7 @@ void level_storage(Ctx &c, Hierarchy &h, const mds_setup_opts &o) {
     for (size_t l = 0; l < h.lv.size(); l++) {
         Level &L = h.lv[l];
         int64_t n = L.A.nrow;
+        L.timed_level = l == 0 && n >= 65536;
         bool lowp = (o.precision == MDS_PREC_BF16 || o.precision == MDS_PREC_FP16) && (int)l >= o.lowp_from_level;
         L.vt = h.prec == 64 ? VT_F64 : !lowp ? VT_F32 : (o.precision == MDS_PREC_BF16 ? VT_BF16 : VT_F16);
         L.G = default_g(L);

@@ -44,5 +44,8 @@ void fgmres_batched(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const std::v
                     std::vector<KrylovResult> &res);
 KrylovResult pcg(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, double *x, int64_t n,
                  const mds_solve_opts &o);
+// preconditioned MINRES (symmetric A, SPD preconditioner)
+KrylovResult minres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, double *x, int64_t n,
+                    const mds_solve_opts &o);
 
 }  // namespace mds

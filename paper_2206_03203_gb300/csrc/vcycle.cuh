@@ -496,7 +496,7 @@ static void launch_level_pf(Ctx &c, const Level &L, const XT *dinv, const XT *b,
                    (K == VK_POST && agg ? 4.0 * n + xb * (double)nc : 0.0) + (L.rscale.p ? 4.0 * n : 0.0) +
                    (K == VK_SMOOTH ? xb * (double)n : 0.0);
     double flops = NR * (2.0 * L.A.nnz + (K == VK_RESID0 ? n : K == VK_POST ? 5.0 * n : K == VK_SMOOTH ? 3.0 * n : 0.0));
-    int cls = (K == VK_RESID0 || K == VK_RESID) ? KC_VC_RESID : KC_VC_POST;
+    int cls = !L.timed_level ? KC_NONE : (K == VK_RESID0 || K == VK_RESID) ? KC_VC_RESID : KC_VC_POST;
     if (L.fmt == FMT_SELL) {
         int64_t rows = L.sell_nslice * L.sell_c;
         MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<0, VT, XT, K, NR, PF>), grid_for(rows, 256), 256, 0, m, dinv, b, xin,
@@ -561,7 +561,7 @@ static void resid_restrict_vt(Ctx &c, const Level &L, const XT *b, const XT *y, 
     double xb = sizeof(XT) * (double)NR;
     double bytes = (sizeof(VT) + 4.0) * L.A.nnz + 4.0 * (n + 1) + 4.0 * (nc + 1) + 4.0 * n + xb * (2.0 * n + nc) +
                    (K == VK_RESID0 ? sizeof(XT) * (double)n : 0.0) + (m.rscale ? 4.0 * n : 0.0);
-    MDS_LAUNCH_F(c, KC_VC_RESID, bytes, NR * (2.0 * L.A.nnz + 2.0 * n), (k_resid_restrict<VT, XT, K, NR>), grid, 256,
+    MDS_LAUNCH_F(c, KC_NONE, bytes, NR * (2.0 * L.A.nnz + 2.0 * n), (k_resid_restrict<VT, XT, K, NR>), grid, 256,
                  0, m, dinv, b, y, nc, L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), bc);
 }
 
@@ -672,16 +672,16 @@ static void smooth_stored(Ctx &c, const Hierarchy &h, const Level &L, const XT *
 }
 
 // ---------------------------------------------------------------- coarse tail
-// The coarse end of the hierarchy (every level at most TAIL_ROWS rows, fused
-// L1-Jacobi form, values of the vector type) runs as one kernel on one thread
-// block cluster: the phases of the down sweep (residual, restriction), the
-// dense coarsest solve and the up sweep (prolongation + post-smoothing) are
-// separated by cluster barriers instead of kernel boundaries.  The same
-// arithmetic as the per-level kernels with one thread per row; vectors
-// written inside the kernel are read through L2 (ld.global.cg).
+// The coarse end of the hierarchy (every level at most as many rows as the
+// cluster has threads, fused L1-Jacobi form, values of the vector type) runs
+// as one kernel on one thread block cluster: the phases of the down sweep
+// (residual, restriction), the dense coarsest solve and the up sweep
+// (prolongation + post-smoothing) are separated by cluster barriers instead
+// of kernel boundaries.  The same arithmetic as the per-level kernels (G
+// lanes per row); vectors written inside the kernel are read through L2
+// (ld.global.cg).
 constexpr int TAIL_MAX = 8;
-constexpr int64_t TAIL_ROWS = 8192;
-constexpr int TAIL_THREADS = 512;
+constexpr int TAIL_THREADS = 512;  // a level takes at most one row per thread of the cluster
 
 template <class XT> struct TailLevel {
     int64_t n, nc;
@@ -700,8 +700,11 @@ template <class XT> struct TailArgs {
     TailLevel<XT> lv[TAIL_MAX + 1];
 };
 
-__device__ __forceinline__ void cluster_barrier() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+__device__ __forceinline__ void cluster_arrive() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 // Lanes per row for a level of n rows on T threads: the largest power of two
@@ -712,79 +715,187 @@ __device__ __forceinline__ int tail_lanes(int64_t n, int64_t T) {
     return G;
 }
 
-template <class XT, int NR>
-__global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(TailArgs<XT> a) {
-    mds_pdl_wait();
-    mds_pdl_trigger();
-    const int64_t T = (int64_t)gridDim.x * blockDim.x;
-    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    // down sweep: r = b - A D1^-1 b, b_c = P^T r
-    for (int li = 0; li < a.nlev; li++) {
+enum { TP_RES = 0, TP_RST = 1, TP_DENSE = 2, TP_POST = 3 };
+constexpr int TPF = 8;  // entries of a row (or members, or dense columns) loaded ahead
+
+// The constants one thread needs in a phase (matrix row share, 1/D1, the
+// aggregate map, member lists, rows of the dense inverse), loaded between the
+// barrier arrival that ends the previous phase and the wait that starts this
+// one.
+template <class XT> struct TailPre {
+    int64_t i;          // row (or aggregate) of this thread, -1 = none
+    int32_t p, p1;      // entry range [p, p1) with stride G
+    XT v[TPF];
+    XT dj[TPF];
+    int32_t j[TPF];
+    int32_t aj[TPF];
+    XT di, sc;
+    int32_t ai;
+    double m[TPF];      // dense inverse row entries
+};
+
+template <class XT> __device__ __forceinline__ void tail_phase(const TailArgs<XT> &a, int ph, int &kind, int &li) {
+    const int ndown = a.dense ? a.nlev : a.nlev - 1;
+    if (ph < 2 * ndown) {
+        kind = ph & 1 ? TP_RST : TP_RES;
+        li = ph >> 1;
+    } else if (a.dense && ph == 2 * ndown) {
+        kind = TP_DENSE;
+        li = a.nlev;
+    } else {
+        kind = TP_POST;
+        li = a.nlev - 1 - (ph - 2 * ndown - (a.dense ? 1 : 0));
+    }
+}
+
+template <class XT>
+__device__ __forceinline__ void tail_prefetch(const TailArgs<XT> &a, int kind, int li, int64_t t0, int64_t T,
+                                              TailPre<XT> &q) {
+    q.i = -1;
+    if (kind == TP_RES || kind == TP_POST) {
         const TailLevel<XT> &L = a.lv[li];
-        if (!L.agg) break;
         const int G = tail_lanes(L.n, T);
-        const int lane = (int)(t0 % G);
-        for (int64_t base = 0; base < L.n; base += T / G) {
-            const int64_t i = base + t0 / G;
-            XT s[NR];
+        const int64_t i = t0 / G;
+        if (i >= L.n) return;
+        q.i = i;
+        q.p = L.rp[i] + (int32_t)(t0 % G);
+        q.p1 = L.rp[i + 1];
+        const bool coarse = kind == TP_POST && L.agg;
 #pragma unroll
-            for (int c = 0; c < NR; c++) s[c] = 0;
-            if (i < L.n) {
-                const int32_t p1 = L.rp[i + 1];
-#pragma unroll 4
-                for (int32_t p = L.rp[i] + lane; p < p1; p += G) {
-                    XT av = L.v[p];
-                    int32_t j = L.ci[p];
-                    XT dj = L.dinv[j];
+        for (int k = 0; k < TPF; k++) {
+            int32_t idx = q.p + k * G;
+            if (idx < q.p1) {
+                q.v[k] = L.v[idx];
+                q.j[k] = L.ci[idx];
+            }
+        }
 #pragma unroll
-                    for (int c = 0; c < NR; c++) s[c] += av * (dj * __ldcg(L.b + (int64_t)j * NR + c));
+        for (int k = 0; k < TPF; k++) {
+            if (q.p + k * G < q.p1) {
+                q.dj[k] = L.dinv[q.j[k]];
+                q.aj[k] = coarse ? L.agg[q.j[k]] : -1;
+            }
+        }
+        q.sc = L.rscale ? (XT)L.rscale[i] : (XT)1;
+        q.di = L.dinv[i];
+        q.ai = coarse ? L.agg[i] : -1;
+    } else if (kind == TP_RST) {
+        const TailLevel<XT> &L = a.lv[li];
+        if (t0 >= L.nc) return;
+        q.i = t0;
+        q.p = L.moff[t0];
+        q.p1 = L.moff[t0 + 1];
+#pragma unroll
+        for (int k = 0; k < TPF; k++)
+            if (q.p + k < q.p1) q.j[k] = L.mem[q.p + k];
+    } else {  // dense: the first row of this warp
+        const int64_t row = t0 >> 5;
+        const int lane = (int)(t0 & 31);
+        if (row >= a.nd) return;
+        q.i = row;
+#pragma unroll
+        for (int k = 0; k < TPF; k++) {
+            int64_t col = lane + 32 * (int64_t)k;
+            q.m[k] = col < a.nd ? a.M[row * a.nd + col] : 0.0;
+        }
+    }
+}
+
+template <class XT, int NR>
+__device__ __forceinline__ void tail_run(const TailArgs<XT> &a, int kind, int li, int64_t t0, int64_t T,
+                                         const TailPre<XT> &q) {
+    if (kind == TP_RES || kind == TP_POST) {
+        const TailLevel<XT> &L = a.lv[li];
+        const int G = tail_lanes(L.n, T);
+        const XT *xc = kind == TP_POST && L.agg ? a.lv[li + 1].x : nullptr;
+        XT s[NR];
+#pragma unroll
+        for (int c = 0; c < NR; c++) s[c] = 0;
+        if (q.i >= 0) {
+#pragma unroll
+            for (int k = 0; k < TPF; k++) {
+                if (q.p + k * G < q.p1) {
+#pragma unroll
+                    for (int c = 0; c < NR; c++) {
+                        XT yj = q.dj[k] * __ldcg(L.b + (int64_t)q.j[k] * NR + c);
+                        if (kind == TP_POST && q.aj[k] >= 0) yj += __ldcg(xc + (int64_t)q.aj[k] * NR + c);
+                        s[c] += q.v[k] * yj;
+                    }
                 }
             }
-#pragma unroll
-            for (int c = 0; c < NR; c++)
-                for (int o = G / 2; o > 0; o >>= 1) s[c] += __shfl_down_sync(0xffffffffu, s[c], o, G);
-            if (i < L.n && lane == 0) {
-                XT sc = L.rscale ? (XT)L.rscale[i] : (XT)1;
+            for (int32_t idx = q.p + TPF * G; idx < q.p1; idx += G) {
+                XT av = L.v[idx];
+                int32_t j = L.ci[idx];
+                XT dj = L.dinv[j];
+                int32_t aj = xc ? L.agg[j] : -1;
 #pragma unroll
                 for (int c = 0; c < NR; c++) {
-                    XT sv = L.rscale ? s[c] * sc : s[c];
-                    __stcg(L.r + i * NR + c, __ldcg(L.b + i * NR + c) - sv);
+                    XT yj = dj * __ldcg(L.b + (int64_t)j * NR + c);
+                    if (aj >= 0) yj += __ldcg(xc + (int64_t)aj * NR + c);
+                    s[c] += av * yj;
                 }
             }
         }
-        cluster_barrier();
-        XT *bc = a.lv[li + 1].b;
-        for (int64_t I = t0; I < L.nc; I += T) {
-            XT s[NR];
 #pragma unroll
-            for (int c = 0; c < NR; c++) s[c] = 0;
-            const int32_t q1 = L.moff[I + 1];
-#pragma unroll 4
-            for (int32_t q = L.moff[I]; q < q1; q++) {
-                int64_t m = L.mem[q];
+        for (int c = 0; c < NR; c++)
+            for (int o = G / 2; o > 0; o >>= 1) s[c] += __shfl_down_sync(0xffffffffu, s[c], o, G);
+        if (q.i >= 0 && t0 % G == 0) {
+            const int64_t i = q.i;
 #pragma unroll
-                for (int c = 0; c < NR; c++) s[c] += __ldcg(L.r + m * NR + c);
+            for (int c = 0; c < NR; c++) {
+                XT bi = __ldcg(L.b + i * NR + c);
+                XT sv = L.rscale ? s[c] * q.sc : s[c];
+                if (kind == TP_RES) {
+                    __stcg(L.r + i * NR + c, bi - sv);
+                } else {
+                    XT yi = q.di * bi;
+                    if (q.ai >= 0) yi += __ldcg(xc + (int64_t)q.ai * NR + c);
+                    __stcg(L.x + i * NR + c, yi + q.di * (bi - sv));
+                }
             }
-#pragma unroll
-            for (int c = 0; c < NR; c++) __stcg(bc + I * NR + c, s[c]);
         }
-        cluster_barrier();
-    }
-    // coarsest: x = M b, one warp per row
-    if (a.dense) {
+    } else if (kind == TP_RST) {
+        if (q.i < 0) return;
+        const TailLevel<XT> &L = a.lv[li];
+        XT *bc = a.lv[li + 1].b;
+        XT s[NR];
+#pragma unroll
+        for (int c = 0; c < NR; c++) s[c] = 0;
+#pragma unroll
+        for (int k = 0; k < TPF; k++)
+            if (q.p + k < q.p1)
+#pragma unroll
+                for (int c = 0; c < NR; c++) s[c] += __ldcg(L.r + (int64_t)q.j[k] * NR + c);
+        for (int32_t idx = q.p + TPF; idx < q.p1; idx++) {
+            int64_t m = L.mem[idx];
+#pragma unroll
+            for (int c = 0; c < NR; c++) s[c] += __ldcg(L.r + m * NR + c);
+        }
+#pragma unroll
+        for (int c = 0; c < NR; c++) __stcg(bc + q.i * NR + c, s[c]);
+    } else {  // dense x = M b, one warp per row
         const XT *bd = a.lv[a.nlev].b;
         XT *xd = a.lv[a.nlev].x;
-        const int lane = threadIdx.x & 31;
-        const int64_t w0 = t0 >> 5, nw = T >> 5;
-        for (int64_t row = w0; row < a.nd; row += nw) {
+        const int lane = (int)(t0 & 31);
+        const int64_t nw = T >> 5;
+        for (int64_t row = t0 >> 5; row < a.nd; row += nw) {
+            const bool first = row == (t0 >> 5);
             double s[NR];
 #pragma unroll
             for (int c = 0; c < NR; c++) s[c] = 0.0;
-#pragma unroll 4
-            for (int64_t k = lane; k < a.nd; k += 32) {
-                double m = a.M[row * a.nd + k];
 #pragma unroll
-                for (int c = 0; c < NR; c++) s[c] += m * (double)__ldcg(bd + k * NR + c);
+            for (int k = 0; k < TPF; k++) {
+                int64_t col = lane + 32 * (int64_t)k;
+                if (col < a.nd) {
+                    double m = first ? q.m[k] : a.M[row * a.nd + col];
+#pragma unroll
+                    for (int c = 0; c < NR; c++) s[c] += m * (double)__ldcg(bd + col * NR + c);
+                }
+            }
+            for (int64_t col = lane + 32 * TPF; col < a.nd; col += 32) {
+                double m = a.M[row * a.nd + col];
+#pragma unroll
+                for (int c = 0; c < NR; c++) s[c] += m * (double)__ldcg(bd + col * NR + c);
             }
 #pragma unroll
             for (int c = 0; c < NR; c++)
@@ -793,53 +904,32 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(TailArgs<XT> a) {
 #pragma unroll
                 for (int c = 0; c < NR; c++) __stcg(xd + row * NR + c, (XT)s[c]);
         }
-        cluster_barrier();
     }
-    // up sweep: x = y + D1^-1 (b - A y), y = D1^-1 b + P x_c
-    for (int li = a.nlev - 1; li >= 0; li--) {
-        const TailLevel<XT> &L = a.lv[li];
-        const XT *xc = L.agg ? a.lv[li + 1].x : nullptr;
-        const int G = tail_lanes(L.n, T);
-        const int lane = (int)(t0 % G);
-        for (int64_t base = 0; base < L.n; base += T / G) {
-            const int64_t i = base + t0 / G;
-            XT s[NR];
-#pragma unroll
-            for (int c = 0; c < NR; c++) s[c] = 0;
-            if (i < L.n) {
-                const int32_t p1 = L.rp[i + 1];
-#pragma unroll 4
-                for (int32_t p = L.rp[i] + lane; p < p1; p += G) {
-                    XT av = L.v[p];
-                    int32_t j = L.ci[p];
-                    XT dj = L.dinv[j];
-                    int32_t aj = xc ? L.agg[j] : -1;
-#pragma unroll
-                    for (int c = 0; c < NR; c++) {
-                        XT yj = dj * __ldcg(L.b + (int64_t)j * NR + c);
-                        if (aj >= 0) yj += __ldcg(xc + (int64_t)aj * NR + c);
-                        s[c] += av * yj;
-                    }
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < NR; c++)
-                for (int o = G / 2; o > 0; o >>= 1) s[c] += __shfl_down_sync(0xffffffffu, s[c], o, G);
-            if (i < L.n && lane == 0) {
-                XT di = L.dinv[i];
-                int32_t ai = xc ? L.agg[i] : -1;
-                XT sc = L.rscale ? (XT)L.rscale[i] : (XT)1;
-#pragma unroll
-                for (int c = 0; c < NR; c++) {
-                    XT bi = __ldcg(L.b + i * NR + c);
-                    XT yi = di * bi;
-                    if (ai >= 0) yi += __ldcg(xc + (int64_t)ai * NR + c);
-                    XT sv = L.rscale ? s[c] * sc : s[c];
-                    __stcg(L.x + i * NR + c, yi + di * (bi - sv));
-                }
-            }
+}
+
+// Phases: down sweep (residual, restriction per level), dense solve, up sweep
+// (prolongation + post-smoothing per level).  Between phases: arrive at the
+// cluster barrier (release), load the next phase's constants, wait (acquire).
+template <class XT, int NR>
+__global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(TailArgs<XT> a) {
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int ndown = a.dense ? a.nlev : a.nlev - 1;
+    const int nph = 2 * ndown + (a.dense ? 1 : 0) + a.nlev;
+    TailPre<XT> q;
+    int kind, li;
+    tail_phase(a, 0, kind, li);
+    tail_prefetch(a, kind, li, t0, T, q);
+    mds_pdl_wait();
+    mds_pdl_trigger();
+    for (int ph = 0; ph < nph; ph++) {
+        tail_run<XT, NR>(a, kind, li, t0, T, q);
+        if (ph + 1 < nph) {
+            cluster_arrive();
+            tail_phase(a, ph + 1, kind, li);
+            tail_prefetch(a, kind, li, t0, T, q);
+            cluster_wait();
         }
-        if (li > 0) cluster_barrier();
     }
 }
 
@@ -871,7 +961,7 @@ template <class XT, int NR> static int tail_cluster(Ctx &c) {
 
 // First level of the coarse tail (levels l0 .. last run in k_vcycle_tail), or
 // -1 when the hierarchy has no eligible tail.
-template <class XT> static int tail_start(const Hierarchy &h) {
+template <class XT> static int tail_start(const Hierarchy &h, int64_t max_rows) {
     const int last = (int)h.lv.size() - 1;
     const int top = h.dense ? last - 1 : last;  // smoothed levels
     if (h.smoother != MDS_SMOOTHER_L1JACOBI || h.sweeps != 1 || top < 0) return -1;
@@ -879,7 +969,7 @@ template <class XT> static int tail_start(const Hierarchy &h) {
     int l0 = -1;
     for (int l = top; l >= 0 && top - l + 1 <= TAIL_MAX; l--) {
         const Level &L = h.lv[l];
-        if (L.A.nrow > TAIL_ROWS || L.smoothed || L.vt != want_vt) break;
+        if (L.A.nrow > max_rows || L.smoothed || L.vt != want_vt) break;
         l0 = l;
     }
     return l0;
@@ -952,7 +1042,9 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
         dense_apply(c, h.Ainv.as<double>(), h.nd, NR, b, x);
         return;
     }
-    if (h.use_tail && l == tail_start<XT>(h) && vcycle_tail<XT, NR>(c, h, l, b, x)) return;
+    if (h.use_tail && l == tail_start<XT>(h, (int64_t)tail_cluster<XT, NR>(c) * TAIL_THREADS) &&
+        vcycle_tail<XT, NR>(c, h, l, b, x))
+        return;
     int64_t n = L.A.nrow;
     XT *r = L.r.as<XT>();
     double rbytes = 4.0 * (L.nc + 1) + 4.0 * n + sizeof(XT) * NR * (double)(n + L.nc);
@@ -972,7 +1064,7 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
                 resid_restrict<XT, VK_RESID0, NR>(c, L, b, nullptr, C.b.as<XT>());
             } else {
                 level_op<XT, VK_RESID0, NR>(c, L, b, nullptr, nullptr, nullptr, r, 0);
-                MDS_LAUNCH(c, KC_VC_RESTRICT, rbytes, (k_vc_restrict<XT, NR>), grid_for(L.nc, 256), 256, 0, L.nc,
+                MDS_LAUNCH(c, L.timed_level ? KC_VC_RESTRICT : KC_NONE, rbytes, (k_vc_restrict<XT, NR>), grid_for(L.nc, 256), 256, 0, L.nc,
                            L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r, C.b.as<XT>());
             }
             vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
@@ -991,7 +1083,7 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
             const XT *rv = std::is_same<XT, double>::value ? (const XT *)L.R.vals() : L.Rv_lp.as<XT>();
             const XT *pv = std::is_same<XT, double>::value ? (const XT *)L.P.vals() : L.Pv_lp.as<XT>();
             double tb = (sizeof(XT) + 4.0) * L.R.nnz + 4.0 * (L.nc + 1) + sizeof(XT) * NR * (double)(n + L.nc);
-            MDS_LAUNCH(c, KC_VC_RESTRICT, tb, (k_sa_restrict<XT, NR>), grid_for(L.nc, 256), 256, 0, L.nc, L.R.rowp(),
+            MDS_LAUNCH(c, L.timed_level ? KC_VC_RESTRICT : KC_NONE, tb, (k_sa_restrict<XT, NR>), grid_for(L.nc, 256), 256, 0, L.nc, L.R.rowp(),
                        L.R.cols(), rv, r, C.b.as<XT>());
             vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
             MDS_LAUNCH(c, KC_NONE, tb + sizeof(XT) * NR * (double)n, (k_sa_prolong<XT, NR>), grid_for(n, 256), 256, 0,
@@ -1001,7 +1093,7 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
                 resid_restrict<XT, VK_RESID, NR>(c, L, b, y, C.b.as<XT>());
             } else {
                 level_op<XT, VK_RESID, NR>(c, L, b, y, nullptr, nullptr, r, 0);
-                MDS_LAUNCH(c, KC_VC_RESTRICT, rbytes, (k_vc_restrict<XT, NR>), grid_for(L.nc, 256), 256, 0, L.nc,
+                MDS_LAUNCH(c, L.timed_level ? KC_VC_RESTRICT : KC_NONE, rbytes, (k_vc_restrict<XT, NR>), grid_for(L.nc, 256), 256, 0, L.nc,
                            L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r, C.b.as<XT>());
             }
             vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());

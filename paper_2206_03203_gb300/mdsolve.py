@@ -25,7 +25,7 @@ FORMAT = {"auto": 0, "csr": 1, "sell": 2}
 PROLONG = {"piecewise": 0, "smoothed": 1}
 SMOOTHER = {"l1jacobi": 0, "chebyshev": 1}
 KIND = {"lower": 0, "diag": 1, "upper": 2}
-KRYLOV = {"fgmres": 0, "pcg": 1}
+KRYLOV = {"fgmres": 0, "pcg": 1, "minres": 2}
 KCLASS = {"spmv": 0, "vc_resid": 1, "vc_post": 2, "gs_dot": 3, "gs_axpy": 4, "vcycle": 5, "vc_restrict": 6}
 
 

@@ -178,6 +178,48 @@ def test_pcg_block_diagonal(ctx, oracle_mod, torch_mod):
     assert st[0].relres_true <= 1e-8
 
 
+@pytest.mark.parametrize("case,precision", [("planes3d-13-kf1", "fp64"), ("seg2d-96", "fp64"),
+                                            ("rects3d-18", "fp64"), ("planes3d-13-kf1", "fp32")])
+def test_minres_block_diagonal(ctx, oracle_mod, torch_mod, case, precision):
+    """Preconditioned MINRES with B_D (symmetric V-cycles) through the C ABI:
+    iteration count within one of the oracle's (same stopping rule), the
+    solution within the solve tolerance of the oracle's."""
+    torch = torch_mod
+    inst = CASES[case]()
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_, kind="diag", precision=precision)
+    x = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+    code, st = ctx.solve(sys_, prec, None, x, krylov="minres", max_iters=3000)
+    kw = {"prec": 32} if precision == "fp32" else {}
+    res, Ao, bo, _ = oracle_mod.solve(inst, kind="diag", krylov="minres", maxit=3000, **kw)
+    assert code == 0 and res.converged
+    # the three-term Lanczos recurrence is not reorthogonalised: rounding that
+    # differs in order (FMA, reduction trees) shifts when lost orthogonality
+    # delays convergence, so long runs may differ by 1% of the count
+    tol = max(1 if precision == "fp64" else 2, res.iterations // 100)
+    assert abs(st[0].iterations - res.iterations) <= tol, (st[0].iterations, res.iterations)
+    assert st[0].relres_true <= 1e-8
+    xo = res.x
+    err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+    assert err <= 1e-6, err
+
+
+def test_minres_identity_and_restart(ctx, oracle_mod, torch_mod):
+    """MINRES without preconditioner on the assembled system: the same
+    iteration count as the oracle; a nonzero initial guess equal to the
+    solution returns at once."""
+    torch = torch_mod
+    inst = inputs.fixed_2d(n=12)
+    sys_ = ctx.assemble(inst)
+    x = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+    code, st = ctx.solve(sys_, None, None, x, krylov="minres", use_precond=0, max_iters=5000)
+    Ao, bo = oracle_mod.assemble(inst)
+    res = oracle_mod.minres(Ao, bo[0], "identity", maxit=5000)
+    assert code == 0 and abs(st[0].iterations - res.iterations) <= 1 and st[0].relres_true <= 1e-8
+    code, st2 = ctx.solve(sys_, None, None, x, krylov="minres", use_precond=0, max_iters=5000)
+    assert code == 0 and st2[0].iterations == 0
+
+
 def test_identity_preconditioner(ctx, oracle_mod, torch_mod):
     torch = torch_mod
     inst = inputs.fixed_2d(n=12)
