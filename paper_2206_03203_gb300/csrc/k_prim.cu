@@ -143,9 +143,9 @@ void cast_f32_f64(Ctx &c, const float *in, double *out, int64_t n) {
 template <int G, class XT, class OT, int MODE, int NR>
 static void spmv_launch(Ctx &c, const mds_csr &A, const XT *x, const double *r, OT *y, int kclass) {
     const int block = 256;
-    unsigned grid = grid_for(A.nrow * G, block);
     double bytes = 12.0 * (double)A.nnz + 4.0 * (double)(A.nrow + 1) +
                    NR * (sizeof(XT) * (double)A.ncol + sizeof(OT) * (double)A.nrow + (MODE == 1 ? 8.0 * A.nrow : 0.0));
+    unsigned grid = grid_for(A.nrow * G, block);
     MDS_LAUNCH_F(c, kclass, bytes, 2.0 * NR * A.nnz, (k_spmv_csr<G, double, XT, OT, MODE, NR>), grid, block, 0, A.nrow,
                  A.row_ptr, A.col, A.val, x, r, y);
 }
