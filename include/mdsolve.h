@@ -250,9 +250,9 @@ typedef struct {
     int batched;         /* 1 = solve the nrhs columns together in lockstep, each as its own
                             FGMRES problem with shared matrix reads (1); packed multi-instance
                             systems are always solved this way */
-    double reorth_eta2;  /* single-RHS FGMRES runs a second classical Gram-Schmidt pass when
+    double reorth_eta2;  /* FGMRES runs a second classical Gram-Schmidt pass when
                             ||w_new||^2 < reorth_eta2 ||w||^2 (1e-8; 0.5 = the DGKS rule,
-                            >= 1 always); the batched path always runs two passes */
+                            >= 1 always); batched solves decide per problem */
 } mds_solve_opts;
 
 typedef struct {

@@ -955,13 +955,24 @@ struct Chunk {
 
 // partial[(q * nchunk + chunk) * NR + c] = sum over the chunk's rows of
 // V_q(i, c) W(i, c); row q == nq is W itself (squared norm).
+// Chunk-level skip for the masked second Gram-Schmidt pass: true when no
+// column of the chunk's instance is flagged.
+template <int NR> __device__ __forceinline__ bool chunk_skipped(const int8_t *mask, int32_t inst) {
+    if (!mask) return false;
+#pragma unroll
+    for (int c = 0; c < NR; c++)
+        if (mask[(int64_t)inst * NR + c]) return false;
+    return true;
+}
+
 template <int NR>
 __global__ void __launch_bounds__(RED_BLOCK) k_bdot(const Chunk *__restrict__ ch, int nchunk, const double *__restrict__ V,
                                                      int64_t ldq, int nq, const double *__restrict__ W,
-                                                     double *__restrict__ partial) {
+                                                     double *__restrict__ partial, const int8_t *__restrict__ mask) {
     mds_pdl_entry();
     __shared__ double ws[RED_BLOCK / 32][NR];
     Chunk k = ch[blockIdx.x];
+    if (chunk_skipped<NR>(mask, k.inst)) return;
     int q = blockIdx.y;
     const double *v = q < nq ? V + (int64_t)q * ldq : W;
     double s[NR];
@@ -989,11 +1000,11 @@ __global__ void __launch_bounds__(RED_BLOCK) k_bdot(const Chunk *__restrict__ ch
 // p = k NR + c; one warp per (q, p), fixed order.
 __global__ void k_breduce(const double *__restrict__ partial, int nchunk, int nq, int NR,
                           const int32_t *__restrict__ ioff, const int32_t *__restrict__ ichunk, int P,
-                          double *__restrict__ out, int accumulate) {
+                          double *__restrict__ out, int accumulate, const int8_t *__restrict__ mask) {
     mds_pdl_entry();
     int q = blockIdx.y;
     int p = blockIdx.x;
-    if (p >= P || q >= nq) return;
+    if (p >= P || q >= nq || (mask && !mask[p])) return;
     int k = p / NR, c = p % NR;
     double s = 0.0;
     for (int t = ioff[k] + threadIdx.x; t < ioff[k + 1]; t += 32)
@@ -1007,11 +1018,13 @@ __global__ void k_breduce(const double *__restrict__ partial, int nchunk, int nq
 template <int NR, int SIGN>
 __global__ void __launch_bounds__(RED_BLOCK) k_bmaxpy(const Chunk *__restrict__ ch, const double *__restrict__ V,
                                                        int64_t ldq, int nq, const double *__restrict__ coef,
-                                                       double *__restrict__ W, double *__restrict__ partial) {
+                                                       double *__restrict__ W, double *__restrict__ partial,
+                                                       const int8_t *__restrict__ mask) {
     mds_pdl_entry();
     __shared__ double cs[NR][32];
     __shared__ double ws[RED_BLOCK / 32][NR];
     Chunk k = ch[blockIdx.x];
+    if (chunk_skipped<NR>(mask, k.inst)) return;
     for (int t = threadIdx.x; t < NR * 32; t += blockDim.x) {
         int c = t / 32, q = t % 32;
         cs[c][q] = q < nq ? coef[((int64_t)k.inst * NR + c) * 32 + q] : 0.0;
@@ -1051,6 +1064,22 @@ __global__ void __launch_bounds__(RED_BLOCK) k_bmaxpy(const Chunk *__restrict__ 
             partial[(int64_t)blockIdx.x * NR + threadIdx.x] = t;
         }
     }
+}
+
+// Per problem after the first Gram-Schmidt pass: flag[p] = 1 when the pass
+// cancelled severely (||w_new||^2 < eta2 (||w_new||^2 + ||h||^2)), the
+// second-pass coefficients start at 0.
+__global__ void k_bflag(int P, int nq, const int8_t *__restrict__ active, const double *__restrict__ h1,
+                        const double *__restrict__ nsq, double eta2, int8_t *__restrict__ flag,
+                        double *__restrict__ h2) {
+    mds_pdl_entry();
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    double hh = 0.0;
+    for (int q = 0; q < nq; q++) hh += h1[(int64_t)p * 32 + q] * h1[(int64_t)p * 32 + q];
+    double w2 = nsq[(int64_t)p * 32];
+    flag[p] = active[p] && w2 < eta2 * (w2 + hh) ? 1 : 0;
+    for (int q = 0; q < 32; q++) h2[(int64_t)p * 32 + q] = 0.0;
 }
 
 // W(i, c) *= f[p]  (f = sc[p * 8 + slot]) for active problems; inactive ones
@@ -1193,7 +1222,7 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
     Buf part(&c, sizeof(double) * (size_t)(QMAX * nch * NR));
     // per-problem arrays with stride 32: cs, sn, g, y, h1, h2, nsq; scalars stride 8
     Buf pa(&c, sizeof(double) * (size_t)P * 32 * 7), psc(&c, sizeof(double) * (size_t)P * 8);
-    Buf act(&c, (size_t)P), kd(&c, sizeof(int32_t) * (size_t)P);
+    Buf act(&c, (size_t)P), kd(&c, sizeof(int32_t) * (size_t)P), f2(&c, (size_t)P);
     double *cs = pa.as<double>(), *sn = cs + (size_t)P * 32, *g = sn + (size_t)P * 32, *y = g + (size_t)P * 32,
            *h1 = y + (size_t)P * 32, *h2 = h1 + (size_t)P * 32, *nsq = h2 + (size_t)P * 32;
     double *sc = psc.as<double>();
@@ -1206,8 +1235,10 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
     dim3 pgrid((unsigned)P, 1);
     // per-problem squared norms of a vector into nsq[p * 32]
     auto norms = [&](const double *w) {
-        MDS_LAUNCH(c, KC_NONE, 8.0 * N * NR, (k_bdot<NR>), dim3(nch, 1), RED_BLOCK, 0, CHp, nch, Vp, ldq, 0, w, PT);
-        MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, 1), 32, 0, PT, nch, 1, NR, IO, IL, P, nsq, 0);
+        MDS_LAUNCH(c, KC_NONE, 8.0 * N * NR, (k_bdot<NR>), dim3(nch, 1), RED_BLOCK, 0, CHp, nch, Vp, ldq, 0, w, PT,
+                   (const int8_t *)nullptr);
+        MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, 1), 32, 0, PT, nch, 1, NR, IO, IL, P, nsq, 0,
+                   (const int8_t *)nullptr);
     };
     std::vector<double> host(P * 8), bn(P);
     auto fetch = [&](const double *d, int stride, int slot) {
@@ -1275,16 +1306,23 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
             spmv_f64(c, A, zj, w, KC_SPMV, NR);
             int nq = j + 1;
             double fl = 2.0 * (double)N * NR * nq;
-            // CGS2 for every problem
+            // classical Gram-Schmidt for every problem; the second pass runs
+            // for the problems whose first pass cancelled severely (the
+            // others' chunks return at once)
             for (int pass = 0; pass < 2; pass++) {
                 double *hh = pass == 0 ? h1 : h2;
-                MDS_LAUNCH_F(c, KC_GS_DOT, 8.0 * N * NR * (nq + 1), fl, (k_bdot<NR>), dim3(nch, nq), RED_BLOCK, 0,
-                             CHp, nch, Vp, ldq, nq, w, PT);
-                MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, nq), 32, 0, PT, nch, nq, NR, IO, IL, P, hh, 0);
-                MDS_LAUNCH_F(c, KC_GS_AXPY, 8.0 * N * NR * (nq + 2), fl, (k_bmaxpy<NR, -1>), nch, RED_BLOCK, 0, CHp,
-                             Vp, ldq, nq, hh, w, pass == 1 ? PT : nullptr);
+                const int8_t *mk = pass == 0 ? nullptr : f2.as<int8_t>();
+                int kd = pass == 0 ? KC_GS_DOT : KC_NONE, ka = pass == 0 ? KC_GS_AXPY : KC_NONE;
+                MDS_LAUNCH_F(c, kd, 8.0 * N * NR * (nq + 1), fl, (k_bdot<NR>), dim3(nch, nq), RED_BLOCK, 0, CHp, nch, Vp,
+                             ldq, nq, w, PT, mk);
+                MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, nq), 32, 0, PT, nch, nq, NR, IO, IL, P, hh, 0, mk);
+                MDS_LAUNCH_F(c, ka, 8.0 * N * NR * (nq + 2), fl, (k_bmaxpy<NR, -1>), nch, RED_BLOCK, 0, CHp, Vp, ldq,
+                             nq, hh, w, PT, mk);
+                MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, 1), 32, 0, PT, nch, 1, NR, IO, IL, P, nsq, 0, mk);
+                if (pass == 0)
+                    MDS_LAUNCH(c, KC_NONE, 0, k_bflag, grid_for(P, 128), 128, 0, P, nq, act.as<int8_t>(), h1, nsq,
+                               o.reorth_eta2, f2.as<int8_t>(), h2);
             }
-            MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, 1), 32, 0, PT, nch, 1, NR, IO, IL, P, nsq, 0);
             MDS_LAUNCH(c, KC_NONE, 0, k_barnoldi, grid_for(P, 128), 128, 0, P, j, m, act.as<int8_t>(), H.as<double>(),
                        h1, h2, nsq, cs, sn, g, sc);
             MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, nch, RED_BLOCK, 0, CHp, w, sc, 3, act.as<int8_t>());
@@ -1314,7 +1352,7 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
         MDS_CUDA(cudaMemcpyAsync(kd.p, c.h_pin, sizeof(int32_t) * (size_t)P, cudaMemcpyHostToDevice, c.stream));
         MDS_LAUNCH(c, KC_NONE, 0, k_bbacksolve, grid_for(P, 128), 128, 0, P, kd.as<int32_t>(), m, H.as<double>(), g, y);
         MDS_LAUNCH(c, KC_NONE, 8.0 * N * NR * (m + 2), (k_bmaxpy<NR, 1>), nch, RED_BLOCK, 0, CHp, Zp, ldq, m, y,
-                   Xi.as<double>(), nullptr);
+                   Xi.as<double>(), nullptr, (const int8_t *)nullptr);
         for (int p = 0; p < P; p++)
             if (hkd[p] > 0) rs[p]++;
     }
