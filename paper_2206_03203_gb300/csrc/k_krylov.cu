@@ -276,37 +276,34 @@ __global__ void __launch_bounds__(RED_BLOCK) k_gs_update(int64_t n, const double
     int64_t n2 = n >> 1;
     double2 *w2 = reinterpret_cast<double2 *>(w);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
-        double s0 = 0.0, s1 = 0.0;
+        // w_i - sum_q c_q V[q][i], accumulated from w_i (one FMA per term)
+        double2 x = w2[i];
         int q = 0;
         for (; q + 4 <= nq; q += 4) {
             double2 a0 = reinterpret_cast<const double2 *>(V + (int64_t)q * ldv)[i];
             double2 a1 = reinterpret_cast<const double2 *>(V + (int64_t)(q + 1) * ldv)[i];
             double2 a2 = reinterpret_cast<const double2 *>(V + (int64_t)(q + 2) * ldv)[i];
             double2 a3 = reinterpret_cast<const double2 *>(V + (int64_t)(q + 3) * ldv)[i];
-            s0 += cq[q] * a0.x;
-            s1 += cq[q] * a0.y;
-            s0 += cq[q + 1] * a1.x;
-            s1 += cq[q + 1] * a1.y;
-            s0 += cq[q + 2] * a2.x;
-            s1 += cq[q + 2] * a2.y;
-            s0 += cq[q + 3] * a3.x;
-            s1 += cq[q + 3] * a3.y;
+            x.x -= cq[q] * a0.x;
+            x.y -= cq[q] * a0.y;
+            x.x -= cq[q + 1] * a1.x;
+            x.y -= cq[q + 1] * a1.y;
+            x.x -= cq[q + 2] * a2.x;
+            x.y -= cq[q + 2] * a2.y;
+            x.x -= cq[q + 3] * a3.x;
+            x.y -= cq[q + 3] * a3.y;
         }
         for (; q < nq; q++) {
             double2 a = reinterpret_cast<const double2 *>(V + (int64_t)q * ldv)[i];
-            s0 += cq[q] * a.x;
-            s1 += cq[q] * a.y;
+            x.x -= cq[q] * a.x;
+            x.y -= cq[q] * a.y;
         }
-        double2 x = w2[i];
-        x.x -= s0;
-        x.y -= s1;
         w2[i] = x;
         nrm += x.x * x.x + x.y * x.y;
     }
     if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-        double s = 0.0;
-        for (int q = 0; q < nq; q++) s += cq[q] * V[(int64_t)q * ldv + n - 1];
-        double x = w[n - 1] - s;
+        double x = w[n - 1];
+        for (int q = 0; q < nq; q++) x -= cq[q] * V[(int64_t)q * ldv + n - 1];
         w[n - 1] = x;
         nrm += x * x;
     }

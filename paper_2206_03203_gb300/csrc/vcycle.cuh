@@ -99,6 +99,19 @@ template <class XT, int NR, int K> struct Nb {
         }
         return y;
     }
+    // the same with 1/D1_j and agg_j already loaded (fused forms)
+    __device__ __forceinline__ Vec<XT, NR> with(int32_t j, XT d, int32_t a) const {
+        Vec<XT, NR> y;
+        Vec<XT, NR> bj = ldv<XT, NR>(b, j);
+#pragma unroll
+        for (int c = 0; c < NR; c++) y.v[c] = d * bj.v[c];
+        if (K == VK_POST && a >= 0) {
+            Vec<XT, NR> xa = ldv<XT, NR>(xc, a);
+#pragma unroll
+            for (int c = 0; c < NR; c++) y.v[c] += xa.v[c];
+        }
+        return y;
+    }
 };
 
 template <int G, class XT> __device__ __forceinline__ XT lane_reduce(XT s) {
@@ -163,14 +176,25 @@ __global__ void __launch_bounds__(256) k_level(LvlMat<VT> A, const XT *__restric
             cnt = A.sl[sl];
         }
     }
+    constexpr bool FUSED = K == VK_RESID0 || K == VK_POST;
     VT pa[PF > 0 ? PF : 1];
     int32_t pj[PF > 0 ? PF : 1];
+    XT pd[FUSED && PF > 0 ? PF : 1];       // 1/D1 of the neighbours (fused forms)
+    int32_t pg[K == VK_POST && PF > 0 ? PF : 1];  // their aggregates (post-smoothing)
 #pragma unroll
     for (int k = 0; k < PF; k++)
         if (k < cnt) {
             pa[k] = ld_stream(A.v + i0 + (int64_t)k * st);
             pj[k] = ld_stream(cp + i0 + (int64_t)k * st);
         }
+    if constexpr (FUSED && PF > 0) {
+#pragma unroll
+        for (int k = 0; k < PF; k++)
+            if (k < cnt) {
+                pd[k] = __ldg(dinv + pj[k]);
+                if constexpr (K == VK_POST) pg[k] = agg ? __ldg(agg + pj[k]) : -1;
+            }
+    }
     int64_t o = row;
     XT sc = (XT)1, d = (XT)0;
     int32_t ag = -1;
@@ -199,7 +223,13 @@ __global__ void __launch_bounds__(256) k_level(LvlMat<VT> A, const XT *__restric
     for (int k = 0; k < PF; k++)
         if (k < cnt) {
             XT a = cvt<XT>(pa[k]);
-            Vec<XT, NR> y = f(pj[k]);
+            Vec<XT, NR> y;
+            if constexpr (K == VK_POST)
+                y = f.with(pj[k], pd[k], pg[k]);
+            else if constexpr (K == VK_RESID0)
+                y = f.with(pj[k], pd[k], -1);
+            else
+                y = f(pj[k]);
 #pragma unroll
             for (int c = 0; c < NR; c++) s[c] += a * y.v[c];
         }
