@@ -14,12 +14,12 @@
 //
 // Two kernel forms.  Memory-bound levels (FP32 and below, and FP64 levels
 // small enough to be latency-bound, one L1-Jacobi sweep) form D1^-1 b and
-// x + P x_c on the fly at every neighbour, so a level costs two launches and
-// the smoothed iterates are never stored.  Large FP64 levels are bound by
+// x + P x_c on the fly at every neighbour, so a level costs three launches
+// (residual, restriction, post-smoothing) and the smoothed iterates are never
+// stored.  Large FP64 levels are bound by
 // GB300's FP64 pipe, so there the iterates are stored once per row instead of
 // being re-formed per nonzero; Chebyshev and multi-sweep smoothing also use
-// the stored form.  Below the finest level the residual and the restriction
-// are one launch (k_resid_restrict).
+// the stored form.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -364,95 +364,6 @@ __global__ void k_vc_restrict(int64_t nc, const int32_t *__restrict__ off, const
     stv<XT, NR>(bc, I, s);
 }
 
-// Residual and restriction in one pass, for levels whose data stay in L2:
-// b_c[I] = sum over the members i of aggregate I (ascending) of r_i, with
-// r = b - A y (K = VK_RESID, y stored) or r = b - A D1^-1 b (K = VK_RESID0).
-// One warp per aggregate: lane k forms the residual of member k (one thread
-// per row, entries in CSR order) and the warp adds the members in order, as
-// the separate restriction does.  Vertices outside every aggregate need no
-// residual.  The first member row of each lane is loaded before the
-// dependency wait (the level's structure is fixed while solving).
-template <class VT, class XT, int K, int NR>
-__global__ void __launch_bounds__(256) k_resid_restrict(LvlMat<VT> A, const XT *__restrict__ dinv,
-                                                        const XT *__restrict__ b, const XT *__restrict__ y,
-                                                        int64_t nc, const int32_t *__restrict__ off,
-                                                        const int32_t *__restrict__ mem, XT *__restrict__ bc) {
-    const int64_t I = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    int32_t q0 = 0, q1 = 0;
-    if (I < nc) {
-        q0 = off[I];
-        q1 = off[I + 1];
-    }
-    int32_t i = -1, p0 = 0, p1 = 0;
-    if (q0 + lane < q1) {
-        i = mem[q0 + lane];
-        p0 = A.rp[i];
-        p1 = A.rp[i + 1];
-    }
-    VT pa[PREFETCH];
-    int32_t pj[PREFETCH];
-#pragma unroll
-    for (int k = 0; k < PREFETCH; k++)
-        if (p0 + k < p1) {
-            pa[k] = ld_stream(A.v + p0 + k);
-            pj[k] = ld_stream(A.ci + p0 + k);
-        }
-    mds_pdl_wait();
-    mds_pdl_trigger();
-    Nb<XT, NR, K> f{dinv, b, y, nullptr, nullptr};
-    Vec<XT, NR> acc;
-#pragma unroll
-    for (int c = 0; c < NR; c++) acc.v[c] = (XT)0;
-    for (int32_t base = q0; base < q1; base += 32) {
-        XT r[NR];
-#pragma unroll
-        for (int c = 0; c < NR; c++) r[c] = (XT)0;
-        if (base != q0) {
-            i = base + lane < q1 ? mem[base + lane] : -1;
-            p0 = i >= 0 ? A.rp[i] : 0;
-            p1 = i >= 0 ? A.rp[i + 1] : 0;
-        }
-        if (i >= 0) {
-            XT sum[NR];
-#pragma unroll
-            for (int c = 0; c < NR; c++) sum[c] = (XT)0;
-            int32_t p = p0;
-            if (base == q0) {
-#pragma unroll
-                for (int k = 0; k < PREFETCH; k++)
-                    if (p0 + k < p1) {
-                        XT a = cvt<XT>(pa[k]);
-                        Vec<XT, NR> yy = f(pj[k]);
-#pragma unroll
-                        for (int c = 0; c < NR; c++) sum[c] += a * yy.v[c];
-                    }
-                p = p0 + PREFETCH;
-            }
-#pragma unroll 4
-            for (; p < p1; p++) {
-                XT a = cvt<XT>(ld_stream(A.v + p));
-                Vec<XT, NR> yy = f(ld_stream(A.ci + p));
-#pragma unroll
-                for (int c = 0; c < NR; c++) sum[c] += a * yy.v[c];
-            }
-            Vec<XT, NR> bi = ldv<XT, NR>(b, i);
-            if (A.rscale) {
-                XT sc = (XT)A.rscale[i];
-#pragma unroll
-                for (int c = 0; c < NR; c++) sum[c] *= sc;
-            }
-#pragma unroll
-            for (int c = 0; c < NR; c++) r[c] = bi.v[c] - sum[c];
-        }
-        int m = q1 - base < 32 ? q1 - base : 32;
-        for (int k = 0; k < m; k++)
-#pragma unroll
-            for (int c = 0; c < NR; c++) acc.v[c] += __shfl_sync(0xffffffffu, r[c], k);
-    }
-    if (I < nc && lane == 0) stv<XT, NR>(bc, I, acc);
-}
-
 // Smoothed aggregation transfers (NR columns): b_c = R r and y += P x_c, one
 // thread per output row, entries in CSR order.
 template <class XT, int NR>
@@ -574,27 +485,6 @@ static void launch_level(Ctx &c, const Level &L, const XT *dinv, const XT *b, co
         launch_level_pf<VT, XT, K, NR, 0>(c, L, dinv, b, xin, agg, xc, out, nc);
 }
 
-// b_c = P^T (b - A y) (K = VK_RESID) or P^T (b - A D1^-1 b) (K = VK_RESID0)
-// through k_resid_restrict on the level's CSR arrays (values of type VT).
-template <class VT, class XT, int K, int NR>
-static void resid_restrict_vt(Ctx &c, const Level &L, const XT *b, const XT *y, XT *bc) {
-    const XT *dinv = L.dinv.as<XT>();
-    int64_t n = L.A.nrow, nc = L.nc;
-    unsigned grid = grid_for(nc * 32, 256);
-    LvlMat<VT> m{};
-    m.n = n;
-    m.rp = L.A.rowp();
-    m.ci = L.A.cols();
-    m.v = std::is_same<VT, double>::value ? (const VT *)L.A.vals() : L.vals_lp.as<VT>();
-    m.C = 1;
-    m.rscale = L.rscale.p ? L.rscale.as<float>() : nullptr;
-    double xb = sizeof(XT) * (double)NR;
-    double bytes = (sizeof(VT) + 4.0) * L.A.nnz + 4.0 * (n + 1) + 4.0 * (nc + 1) + 4.0 * n + xb * (2.0 * n + nc) +
-                   (K == VK_RESID0 ? sizeof(XT) * (double)n : 0.0) + (m.rscale ? 4.0 * n : 0.0);
-    MDS_LAUNCH_F(c, KC_NONE, bytes, NR * (2.0 * L.A.nnz + 2.0 * n), (k_resid_restrict<VT, XT, K, NR>), grid, 256,
-                 0, m, dinv, b, y, nc, L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), bc);
-}
-
 // Level operations on FP32 vectors whose values are stored in VT = BF16 or
 // FP16: defined here, instantiated in their own translation units
 // (k_vcycle_bf16.cu, k_vcycle_f16.cu) so that the library compiles in
@@ -604,23 +494,16 @@ void level_op_lp(Ctx &c, const Level &L, const float *b, const float *xin, const
                  float *out, int64_t nc) {
     launch_level<VT, float, K, NR>(c, L, L.dinv.as<float>(), b, xin, agg, xc, out, nc);
 }
-template <class VT, int K, int NR>
-void resid_restrict_lp(Ctx &c, const Level &L, const float *b, const float *y, float *bc) {
-    resid_restrict_vt<VT, float, K, NR>(c, L, b, y, bc);
-}
 
 #define MDS_LP_EACH(X, VT)                                                                            \
     X(VT, 0, 1) X(VT, 0, 2) X(VT, 0, 4) X(VT, 0, 8) X(VT, 1, 1) X(VT, 1, 2) X(VT, 1, 4) X(VT, 1, 8)   \
     X(VT, 2, 1) X(VT, 2, 2) X(VT, 2, 4) X(VT, 2, 8) X(VT, 3, 1) X(VT, 3, 2) X(VT, 3, 4) X(VT, 3, 8)
 #define MDS_LP_DECL(VT, K, NR)                                                                             \
     extern template void level_op_lp<VT, K, NR>(Ctx &, const Level &, const float *, const float *,      \
-                                                 const int32_t *, const float *, float *, int64_t);       \
-    extern template void resid_restrict_lp<VT, K, NR>(Ctx &, const Level &, const float *, const float *, \
-                                                       float *);
+                                                 const int32_t *, const float *, float *, int64_t);
 #define MDS_LP_INST(VT, K, NR)                                                                                    \
     template void level_op_lp<VT, K, NR>(Ctx &, const Level &, const float *, const float *, const int32_t *,    \
-                                          const float *, float *, int64_t);                                      \
-    template void resid_restrict_lp<VT, K, NR>(Ctx &, const Level &, const float *, const float *, float *);
+                                          const float *, float *, int64_t);
 #ifndef MDS_VCYCLE_LP_UNIT
 MDS_LP_EACH(MDS_LP_DECL, __nv_bfloat16)
 MDS_LP_EACH(MDS_LP_DECL, __half)
@@ -641,18 +524,6 @@ static void level_op(Ctx &c, const Level &L, const XT *b, const XT *xin, const i
     }
 }
 
-template <class XT, int K, int NR>
-static void resid_restrict(Ctx &c, const Level &L, const XT *b, const XT *y, XT *bc) {
-    if constexpr (std::is_same<XT, double>::value) {
-        resid_restrict_vt<double, XT, K, NR>(c, L, b, y, bc);
-    } else {
-        switch (L.vt) {
-            case VT_BF16: resid_restrict_lp<__nv_bfloat16, K, NR>(c, L, b, y, bc); break;
-            case VT_F16: resid_restrict_lp<__half, K, NR>(c, L, b, y, bc); break;
-            default: resid_restrict_vt<float, XT, K, NR>(c, L, b, y, bc); break;
-        }
-    }
-}
 
 static unsigned ew_grid(int64_t n) {
     unsigned g = grid_for(n, 256);
@@ -1084,19 +955,13 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
     // more FP64 operations per nonzero and saves two launches per level).
     bool fused = h.smoother == MDS_SMOOTHER_L1JACOBI && h.sweeps == 1 && !L.smoothed &&
                  (!std::is_same<XT, double>::value || n <= FUSE_FP64_ROWS);
-    // below the finest level, with aggregates large enough to fill most lanes
-    // of a warp (3D), the residual and the restriction share a launch
-    const bool rr = l > 0 && !L.smoothed && L.nc > 0 && L.mem_count >= 16 * L.nc;
     if (fused) {
         if (L.has_coarse) {
             Level &C = h.lv[l + 1];
-            if (rr) {
-                resid_restrict<XT, VK_RESID0, NR>(c, L, b, nullptr, C.b.as<XT>());
-            } else {
-                level_op<XT, VK_RESID0, NR>(c, L, b, nullptr, nullptr, nullptr, r, 0);
-                MDS_LAUNCH(c, L.timed_level ? KC_VC_RESTRICT : KC_NONE, rbytes, (k_vc_restrict<XT, NR>), grid_for(L.nc, 256), 256, 0, L.nc,
-                           L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r, C.b.as<XT>());
-            }
+            level_op<XT, VK_RESID0, NR>(c, L, b, nullptr, nullptr, nullptr, r, 0);
+            MDS_LAUNCH(c, L.timed_level ? KC_VC_RESTRICT : KC_NONE, rbytes, (k_vc_restrict<XT, NR>),
+                       grid_for(L.nc, 256), 256, 0, L.nc, L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r,
+                       C.b.as<XT>());
             vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
             level_op<XT, VK_POST, NR>(c, L, b, nullptr, L.agg.as<int32_t>(), C.x.as<XT>(), x, L.nc);
         } else {
@@ -1119,13 +984,10 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
             MDS_LAUNCH(c, KC_NONE, tb + sizeof(XT) * NR * (double)n, (k_sa_prolong<XT, NR>), grid_for(n, 256), 256, 0,
                        n, L.P.rowp(), L.P.cols(), pv, C.x.as<XT>(), y);
         } else {
-            if (rr) {
-                resid_restrict<XT, VK_RESID, NR>(c, L, b, y, C.b.as<XT>());
-            } else {
-                level_op<XT, VK_RESID, NR>(c, L, b, y, nullptr, nullptr, r, 0);
-                MDS_LAUNCH(c, L.timed_level ? KC_VC_RESTRICT : KC_NONE, rbytes, (k_vc_restrict<XT, NR>), grid_for(L.nc, 256), 256, 0, L.nc,
-                           L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r, C.b.as<XT>());
-            }
+            level_op<XT, VK_RESID, NR>(c, L, b, y, nullptr, nullptr, r, 0);
+            MDS_LAUNCH(c, L.timed_level ? KC_VC_RESTRICT : KC_NONE, rbytes, (k_vc_restrict<XT, NR>),
+                       grid_for(L.nc, 256), 256, 0, L.nc, L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r,
+                       C.b.as<XT>());
             vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
             MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n * NR, (k_vc_prolong<XT, NR>), ew_grid(n * NR), 256, 0, n,
                        L.agg.as<int32_t>(), C.x.as<XT>(), y);
