@@ -352,15 +352,17 @@ def variants(ctx, insts, dev_arrays, N, flush):
     from paper_2206_03203_gb300 import inputs, sharding
     out = {}
 
-    def sweep(prec):
+    def sweep(prec, krylov="fgmres", **setup):
         its = []
         for k, inst in enumerate(insts):
             s = ctx.assemble(inst, device_arrays=dev_arrays[k])
-            p = ctx.setup(s, precision=prec, format="auto")
+            p = ctx.setup(s, precision=prec, format="auto", **setup)
             x = torch.zeros(N[k], dtype=torch.float64, device="cuda")
-            code, st = ctx.solve(s, p, None, x, rtol=1e-8, max_iters=5000)
-            assert code == 0
-            its.append(st[0].iterations)
+            try:
+                code, st = ctx.solve(s, p, None, x, rtol=1e-8, max_iters=5000, krylov=krylov)
+                its.append(st[0].iterations if code == 0 else f"{st[0].iterations} (not converged)")
+            except Exception as e:  # a variant that breaks down is reported, not fatal
+                its.append(f"error: {e}")
             p.close()
             s.close()
         return its
@@ -369,6 +371,17 @@ def variants(ctx, insts, dev_arrays, N, flush):
     out["seg2d_1024_sweep_fp32_vcycle"] = {"solves_per_s": len(insts) / t, "s_per_step": t, "iterations": its,
                                            "precision": "FP32 V-cycle values/vectors, FP64 FGMRES",
                                            "classes": class_rates(ctx, lambda: sweep("fp32"))}
+    t, its = _timed(lambda: sweep("fp64", prolongation="smoothed"), flush)
+    out["seg2d_1024_sweep_fp64_smoothed_aggregation"] = {
+        "solves_per_s": len(insts) / t, "s_per_step": t, "iterations": its,
+        "precision": "FP64 throughout; smoothed-aggregation prolongation instead of piecewise-constant"}
+    # the other block preconditioners of Sec. 3.2 on the same sweep (FP64)
+    for name, kw in (("block_diagonal_pcg", dict(kind="diag", krylov="pcg")),
+                     ("block_diagonal_minres", dict(kind="diag", krylov="minres")),
+                     ("block_upper_fgmres", dict(kind="upper", krylov="fgmres"))):
+        kry = kw.pop("krylov")
+        t, its = _timed(lambda kry=kry, kw=kw: sweep("fp64", krylov=kry, **kw), flush, warmup=0)
+        out[f"seg2d_1024_sweep_fp64_{name}"] = {"solves_per_s": len(insts) / t, "s_per_step": t, "iterations": its}
     p3 = inputs.planes_3d(128, kf=1e4)
     for prec in ("fp64", "fp32"):
         def one(prec=prec):
