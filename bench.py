@@ -402,9 +402,9 @@ def variants(ctx, insts, dev_arrays, N, flush):
         shard = sharding.shard_by_work([sharding.instance_work(b.n_m, b.n_f) for b in batch], world)
         batch = [batch[i] for i in shard[rank_info()[0]]]
 
-    def batched():
+    def batched(prec):
         s = ctx.assemble_batch(batch)
-        p = ctx.setup(s, precision="bf16", format="auto")
+        p = ctx.setup(s, precision=prec, format="auto")
         x = torch.zeros(s.N * 4, dtype=torch.float64, device="cuda")
         code, st = ctx.solve(s, p, None, x, nrhs=4, rtol=1e-8, max_iters=5000)
         assert code == 0
@@ -412,12 +412,13 @@ def variants(ctx, insts, dev_arrays, N, flush):
         p.close()
         s.close()
         return [q.iterations for q in st], n
-    t, (its, n) = _timed(batched, flush)
-    t, total_solves = sharding.reduce_over_ranks(t, len(its))
-    out["batch3d_256inst_x4rhs_bf16"] = {"solves_per_s": total_solves / t, "s_per_step": t, "solves": total_solves,
-                                         "iterations_min_mean_max": [min(its), float(np.mean(its)), max(its)],
-                                         "N_packed": n, "precision": "FP32 fine level, BF16 row-scaled coarse levels, "
-                                         "FP64 FGMRES; packed lockstep batch"}
+    for prec, desc in (("bf16", "FP32 fine level, BF16 row-scaled coarse levels, FP64 FGMRES; packed lockstep batch"),
+                       ("fp64", "FP64 throughout (the plain GPU solve of the same batch); packed lockstep batch")):
+        t, (its, n) = _timed(lambda prec=prec: batched(prec), flush)
+        t, total_solves = sharding.reduce_over_ranks(t, len(its))
+        out[f"batch3d_256inst_x4rhs_{prec}"] = {
+            "solves_per_s": total_solves / t, "s_per_step": t, "solves": total_solves,
+            "iterations_min_mean_max": [min(its), float(np.mean(its)), max(its)], "N_packed": n, "precision": desc}
     return out
 
 
