@@ -73,6 +73,9 @@ def lib():
             L.orc_assemble.restype = P(_CSR)
             L.orc_assemble.argtypes = [C.c_int, C.c_int, _f64p, C.c_int64, _i32p, _i32p, _f64p,
                                        _f64p, C.c_int, _f64p, _f64p, _f64p]
+            L.orc_assemble_flux.restype = P(_CSR)
+            L.orc_assemble_flux.argtypes = [C.c_int, C.c_int, _f64p, C.c_int64, _i32p, _i32p, _f64p,
+                                       _f64p, C.c_int, _f64p, _f64p, _f64p]
             L.orc_split.argtypes = [P(_CSR), C.c_int64] + [P(P(_CSR))] * 4
             L.orc_schur.restype = P(_CSR)
             L.orc_schur.argtypes = [P(_CSR)] * 4
@@ -155,15 +158,19 @@ class CSR:
             pass
 
 
-def assemble(inst):
-    """Full system (scipy CSR, [m; f] order) and right-hand sides [nrhs, N]."""
+def assemble(inst, form="primal"):
+    """Full system (scipy CSR) and right-hand sides [nrhs, N].  form="primal":
+    [matrix cells; fracture cells] with the interface flux eliminated;
+    form="flux": the paper's partition [all pressures; interface fluxes]
+    (N = n_m + 3 n_f)."""
     L = lib()
-    N = inst.n_m + inst.n_f
+    N = inst.n_m + inst.n_f if form == "primal" else inst.n_m + 3 * inst.n_f
     b = np.zeros((inst.nrhs, N))
     pos = np.ascontiguousarray(inst.fc_pos, dtype=np.int32).reshape(-1)
     if pos.size == 0:
         pos = np.zeros(3, dtype=np.int32)
-    ptr = L.orc_assemble(inst.dim, inst.n, _p(inst.km, _f64p), inst.n_f,
+    fn = L.orc_assemble if form == "primal" else L.orc_assemble_flux
+    ptr = fn(inst.dim, inst.n, _p(inst.km, _f64p), inst.n_f,
                          _p(np.ascontiguousarray(inst.fc_axis, dtype=np.int32), _i32p), _p(pos, _i32p),
                          _p(np.ascontiguousarray(inst.fc_kf), _f64p),
                          _p(np.ascontiguousarray(inst.fc_a), _f64p), inst.nrhs,
@@ -267,7 +274,12 @@ class AMG:
 
     @property
     def coarsest_dense(self):
-        return bool(lib().orc_amg_coarsest_dense(self.h))
+        return lib().orc_amg_coarsest_dense(self.h) == 1
+
+    @property
+    def coarsest_diagonal(self):
+        """The last level has no couplings and is solved by x = b / a_ii."""
+        return lib().orc_amg_coarsest_dense(self.h) == 2
 
     def vcycle(self, b):
         b = np.ascontiguousarray(b, dtype=np.float64)

@@ -99,17 +99,30 @@ static int32_t face_frac(const facemap *fm, int d, const int64_t c[3]) {
     return f < 0 ? -1 : fm->map[d][f];
 }
 
-ocsr *orc_assemble(int dim, int n, const double *km, int64_t nf,
-                   const int32_t *fc_axis, const int32_t *fc_pos,
-                   const double *fc_kf, const double *fc_a, int nrhs,
-                   const double *pD_left, const double *pD_right, double *b) {
+/* flux = 0: the primal system above.  flux = 1: the paper's own partition
+ * (Sec. 3.1, Eq. (4)): unknowns [pressures of all cells; interface fluxes],
+ * one flux lambda_j per matrix-fracture face side, j = 2k + side (side 0 =
+ * the matrix cell below the fracture face, 1 = above), in the order of the
+ * fracture cells.  The pressure rows keep the matrix-matrix,
+ * fracture-fracture and Dirichlet terms (diagonal = their sum, same order);
+ * matrix cell i gets +lambda_j and fracture cell k gets -lambda_j (mass
+ * leaving i enters k); row j is the interface law of Eq. (2) written as
+ * p_i - p_k - lambda_j / T_j = 0 with T_j the series transmissibility of the
+ * matrix half cell and the normal coupling.  A_{Gamma Omega} = A_{Omega
+ * Gamma}^T and A_{Gamma Gamma} = diag(-1/T_j): symmetric indefinite;
+ * eliminating lambda gives the primal system. */
+static ocsr *assemble_impl(int dim, int n, const double *km, int64_t nf,
+                           const int32_t *fc_axis, const int32_t *fc_pos,
+                           const double *fc_kf, const double *fc_a, int nrhs,
+                           const double *pD_left, const double *pD_right, double *b, int flux) {
     if ((dim != 2 && dim != 3) || n < 1 || nrhs < 1) return NULL;
     const double h = 1.0 / (double)n;
     const double F = dim == 2 ? h : h * h;      /* face measure |F| */
     const double elen = dim == 2 ? 1.0 : h;     /* fracture edge measure |e| */
     const int64_t nz = dim == 3 ? n : 1;
     const int64_t n_m = (int64_t)n * n * nz;
-    const int64_t N = n_m + nf;
+    const int64_t N = n_m + nf;             /* pressure unknowns */
+    const int64_t NT = flux ? N + 2 * nf : N; /* all unknowns */
     const int64_t nb = dim == 3 ? (int64_t)n * n : n; /* boundary faces per x side */
 
     facemap fm;
@@ -133,11 +146,11 @@ ocsr *orc_assemble(int dim, int n, const double *km, int64_t nf,
     }
 
     /* count pass: an upper bound per row, then exact fill */
-    int64_t cap = n_m * (1 + 2 * dim) + nf * (1 + 2 + 4 * 3);
-    ocsr *A = orc_csr_new(N, N, cap);
+    int64_t cap = n_m * (1 + 2 * dim) + nf * (1 + 2 + 4 * 3) + (flux ? 6 * nf : 0);
+    ocsr *A = orc_csr_new(NT, NT, cap);
     if (!A) goto bad;
     for (int r = 0; r < nrhs; r++)
-        for (int64_t i = 0; i < N; i++) b[(int64_t)r * N + i] = 0.0;
+        for (int64_t i = 0; i < NT; i++) b[(int64_t)r * NT + i] = 0.0;
 
     entry row[32];
     int64_t pos = 0;
@@ -166,7 +179,9 @@ ocsr *orc_assemble(int dim, int n, const double *km, int64_t nf,
                         int32_t k = face_frac(&fm, d, fc);
                         if (k >= 0) {
                             double kappa = (2.0 * fc_kf[k]) / fc_a[k];
-                            row[cnt].c = (int32_t)(n_m + k);
+                            /* flux form: the interface flux column, side 0 when
+                             * the face is above this cell (s = 1) */
+                            row[cnt].c = flux ? (int32_t)(N + 2 * k + (s ? 0 : 1)) : (int32_t)(n_m + k);
                             row[cnt].t = F / (h / (2.0 * ki) + 1.0 / kappa);
                         } else {
                             int64_t nc[3] = {c[0], c[1], c[2]};
@@ -180,7 +195,8 @@ ocsr *orc_assemble(int dim, int n, const double *km, int64_t nf,
                 }
                 qsort(row, (size_t)cnt, sizeof(entry), cmp_entry);
                 double diag = 0.0;
-                for (int q = 0; q < cnt; q++) diag += row[q].t;
+                for (int q = 0; q < cnt; q++)
+                    if (row[q].c < N) diag += row[q].t; /* flux columns carry no transmissibility */
                 for (int s = 0; s < 2; s++)
                     if (has_tb[s]) diag += tb[s];
                 int64_t bf = cy + n * cz;
@@ -188,7 +204,7 @@ ocsr *orc_assemble(int dim, int n, const double *km, int64_t nf,
                     double acc = 0.0;
                     if (has_tb[0]) acc += tb[0] * pD_left[(int64_t)r * nb + bf];
                     if (has_tb[1]) acc += tb[1] * pD_right[(int64_t)r * nb + bf];
-                    b[(int64_t)r * N + i] = acc;
+                    b[(int64_t)r * NT + i] = acc;
                 }
                 int placed = 0;
                 for (int q = 0; q < cnt; q++) {
@@ -198,7 +214,7 @@ ocsr *orc_assemble(int dim, int n, const double *km, int64_t nf,
                         placed = 1;
                     }
                     A->ci[pos] = row[q].c;
-                    A->v[pos++] = -row[q].t;
+                    A->v[pos++] = row[q].c < N ? -row[q].t : 1.0;
                 }
                 if (!placed) {
                     A->ci[pos] = (int32_t)i;
@@ -220,7 +236,7 @@ ocsr *orc_assemble(int dim, int n, const double *km, int64_t nf,
             int64_t mc[3] = {c[0], c[1], c[2]};
             mc[d] = plane - 1 + s;
             int64_t j = mc[0] + n * (mc[1] + n * mc[2]);
-            row[cnt].c = (int32_t)j;
+            row[cnt].c = flux ? (int32_t)(N + 2 * k + s) : (int32_t)j;
             row[cnt].t = F / (h / (2.0 * km[j]) + 1.0 / kappa);
             cnt++;
         }
@@ -271,7 +287,8 @@ ocsr *orc_assemble(int dim, int n, const double *km, int64_t nf,
         }
         qsort(row, (size_t)cnt, sizeof(entry), cmp_entry);
         double diag = 0.0;
-        for (int q = 0; q < cnt; q++) diag += row[q].t;
+        for (int q = 0; q < cnt; q++)
+            if (row[q].c < N) diag += row[q].t;
         for (int s = 0; s < 2; s++)
             if (has_tb[s]) diag += tb[s];
         for (int r = 0; r < nrhs; r++) {
@@ -282,7 +299,7 @@ ocsr *orc_assemble(int dim, int n, const double *km, int64_t nf,
                 double pv = (pd[bfa[s]] + pd[bfb[s]]) * 0.5;
                 acc += tb[s] * pv;
             }
-            b[(int64_t)r * N + n_m + k] = acc;
+            b[(int64_t)r * NT + n_m + k] = acc;
         }
         int64_t self = n_m + k;
         int placed = 0;
@@ -293,7 +310,7 @@ ocsr *orc_assemble(int dim, int n, const double *km, int64_t nf,
                 placed = 1;
             }
             A->ci[pos] = row[q].c;
-            A->v[pos++] = -row[q].t;
+            A->v[pos++] = row[q].c < N ? -row[q].t : -1.0;
         }
         if (!placed) {
             A->ci[pos] = (int32_t)self;
@@ -301,12 +318,46 @@ ocsr *orc_assemble(int dim, int n, const double *km, int64_t nf,
         }
         A->rp[self + 1] = pos;
     }
+    /* flux rows: lambda_j (fracture k, side s): p_i - p_k - lambda_j / T_j = 0 */
+    for (int64_t k = 0; flux && k < nf; k++) {
+        int d = fc_axis[k];
+        const int32_t *p = fc_pos + 3 * k;
+        double kappa = (2.0 * fc_kf[k]) / fc_a[k];
+        for (int s = 0; s < 2; s++) {
+            int64_t mc[3] = {p[0], p[1], dim == 3 ? p[2] : 0};
+            mc[d] = p[d] - 1 + s;
+            int64_t i = mc[0] + n * (mc[1] + n * mc[2]);
+            double t = F / (h / (2.0 * km[i]) + 1.0 / kappa);
+            int64_t j = N + 2 * k + s;
+            A->ci[pos] = (int32_t)i;
+            A->v[pos++] = 1.0;
+            A->ci[pos] = (int32_t)(n_m + k);
+            A->v[pos++] = -1.0;
+            A->ci[pos] = (int32_t)j;
+            A->v[pos++] = -1.0 / t;
+            A->rp[j + 1] = pos;
+        }
+    }
     A->nnz = pos;
     for (int d = 0; d < 3; d++) free(fm.map[d]);
     return A;
 bad:
     for (int d = 0; d < 3; d++) free(fm.map[d]);
     return NULL;
+}
+
+ocsr *orc_assemble(int dim, int n, const double *km, int64_t nf,
+                   const int32_t *fc_axis, const int32_t *fc_pos,
+                   const double *fc_kf, const double *fc_a, int nrhs,
+                   const double *pD_left, const double *pD_right, double *b) {
+    return assemble_impl(dim, n, km, nf, fc_axis, fc_pos, fc_kf, fc_a, nrhs, pD_left, pD_right, b, 0);
+}
+
+ocsr *orc_assemble_flux(int dim, int n, const double *km, int64_t nf,
+                        const int32_t *fc_axis, const int32_t *fc_pos,
+                        const double *fc_kf, const double *fc_a, int nrhs,
+                        const double *pD_left, const double *pD_right, double *b) {
+    return assemble_impl(dim, n, km, nf, fc_axis, fc_pos, fc_kf, fc_a, nrhs, pD_left, pD_right, b, 1);
 }
 
 /* Slice the full system into the blocks of Eq. (4). */
@@ -510,6 +561,7 @@ struct orc_amg {
     ocsr *P[MAXLEV];       /* smoothed prolongator of level l (NULL: injection by agg) */
     ocsr *R[MAXLEV];       /* its transpose */
     int dense;             /* last level solved by dense Cholesky */
+    int diagonal;          /* last level has no couplings: solved by x = b / a_ii */
     double *L;             /* dense Cholesky factor (row-major, lower) */
     int64_t nd;
     double *vb[MAXLEV], *vx[MAXLEV], *vr[MAXLEV];
@@ -889,6 +941,16 @@ orc_amg *orc_amg_setup(const ocsr *A0, const orc_amg_opts *o) {
         h->A[l] = A;
         int64_t n = A->nrow;
         h->root[l] = (int8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+        /* a matrix without couplings (every row holds only its diagonal, of
+         * either sign) is the last level and is solved exactly by x = b / a_ii:
+         * neither coarsened nor factored */
+        int diagonal = A->nnz == n;
+        for (int64_t i = 0; diagonal && i < n; i++)
+            if (A->rp[i + 1] - A->rp[i] != 1 || A->ci[A->rp[i]] != i) diagonal = 0;
+        if (diagonal) {
+            h->diagonal = 1;
+            break;
+        }
         if (n <= o->n_coarse) {
             h->dense = 1;
             break;
@@ -1005,7 +1067,7 @@ void orc_amg_free(orc_amg *h) {
 int orc_amg_nlevels(const orc_amg *h) { return h->nlev; }
 int64_t orc_amg_level_n(const orc_amg *h, int l) { return h->A[l]->nrow; }
 const ocsr *orc_amg_level_A(const orc_amg *h, int l) { return h->A[l]; }
-int orc_amg_coarsest_dense(const orc_amg *h) { return h->dense; }
+int orc_amg_coarsest_dense(const orc_amg *h) { return h->dense ? 1 : (h->diagonal ? 2 : 0); }
 
 int orc_amg_level_agg(const orc_amg *h, int l, int32_t *out) {
     if (l < 0 || l >= h->nlev || !h->agg[l]) return -1;
@@ -1100,6 +1162,11 @@ static void vcycle_level(orc_amg *h, int l, const double *b, double *x) {
         for (int64_t i = 0; i < n; i++) x[i] = rnd(x[i], pv);
         return;
     }
+    if (l == h->nlev - 1 && h->diagonal) {
+        /* the stored 1/a_ii (1/l1 of a row without off-diagonals) */
+        for (int64_t i = 0; i < n; i++) x[i] = rnd(h->dinv[l][i] * b[i], pv);
+        return;
+    }
     int ns = h->o.sweeps < 1 ? 1 : h->o.sweeps;
     for (int s = 0; s < ns; s++) smooth(h, l, b, x, s == 0);
     if (h->agg[l]) {
@@ -1152,6 +1219,7 @@ void orc_vcycle(orc_amg *h, const double *b, double *x) {
 struct orc_ml {
     int64_t n_m, n_f;
     int kind;
+    int ff_negative; /* every diagonal entry of A_ff is negative (flux block of the paper's partition) */
     ocsr *Amm, *Amf, *Afm, *Aff, *S;
     orc_amg *amg[2];
     double *t, *u;
@@ -1170,6 +1238,11 @@ orc_ml *orc_ml_new(const ocsr *A, int64_t n_m, const orc_amg_opts *o, int kind) 
     }
     m->amg[0] = orc_amg_setup(m->S, o);
     m->amg[1] = m->n_f > 0 ? orc_amg_setup(m->Aff, o) : NULL;
+    m->ff_negative = m->n_f > 0;
+    for (int64_t k = 0; k < m->n_f; k++) {
+        int f;
+        if (!(find_val(m->Aff, k, k, &f) < 0.0)) m->ff_negative = 0;
+    }
     if (!m->amg[0] || (m->n_f > 0 && !m->amg[1])) {
         orc_ml_free(m);
         return NULL;
@@ -1216,7 +1289,11 @@ int orc_ml_apply(void *ctx, const double *r, double *z) {
     orc_vcycle(m->amg[0], rm, zm);
     if (nf == 0) return 0;
     if (m->kind == 1) {
+        /* B_D is used with CG and MINRES, which need it positive definite:
+         * for a negative definite A_ff (the flux block) its block is -Q_ff */
         orc_vcycle(m->amg[1], rf, zf);
+        if (m->ff_negative)
+            for (int64_t k = 0; k < nf; k++) zf[k] = -zf[k];
         return 0;
     }
     for (int64_t k = 0; k < nf; k++) {

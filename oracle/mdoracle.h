@@ -40,6 +40,15 @@ ocsr *orc_assemble(int dim, int n, const double *km, int64_t nf,
                    const double *fc_kf, const double *fc_a, int nrhs,
                    const double *pD_left, const double *pD_right, double *b);
 
+/* The paper's own partition (Sec. 3.1, Eq. (4)): unknowns [all cell
+ * pressures (matrix, then fracture); interface fluxes, 2 per fracture cell],
+ * a symmetric saddle-point system whose flux block is diag(-1/T).  b has
+ * n_m + 3 n_f entries per right-hand side (zero on the flux rows). */
+ocsr *orc_assemble_flux(int dim, int n, const double *km, int64_t nf,
+                        const int32_t *fc_axis, const int32_t *fc_pos,
+                        const double *fc_kf, const double *fc_a, int nrhs,
+                        const double *pD_left, const double *pD_right, double *b);
+
 /* Slice a full CSR at row/column n_m into its four blocks. */
 int orc_split(const ocsr *A, int64_t n_m, ocsr **Amm, ocsr **Amf, ocsr **Afm, ocsr **Aff);
 
@@ -84,7 +93,8 @@ int orc_amg_level_roots(const orc_amg *h, int l, int8_t *out);
 int orc_amg_level_l1(const orc_amg *h, int l, double *out);
 /* Prolongator of level l (fine rows x coarse columns) when smoothed; NULL otherwise. */
 const ocsr *orc_amg_level_P(const orc_amg *h, int l);
-int orc_amg_coarsest_dense(const orc_amg *h);  /* 1 if the last level is a dense solve */
+int orc_amg_coarsest_dense(const orc_amg *h);  /* 1: the last level is a dense solve; 2: it has no
+                                                   couplings and is solved by x = b / a_ii; 0: smoothed */
 /* One V-cycle x = V(b) on level 0. */
 void orc_vcycle(orc_amg *h, const double *b, double *x);
 
