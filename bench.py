@@ -352,12 +352,12 @@ def variants(ctx, insts, dev_arrays, N, flush):
     from paper_2206_03203_gb300 import inputs, sharding
     out = {}
 
-    def sweep(prec, krylov="fgmres", **setup):
+    def sweep(prec, krylov="fgmres", form="primal", **setup):
         its = []
         for k, inst in enumerate(insts):
-            s = ctx.assemble(inst, device_arrays=dev_arrays[k])
+            s = ctx.assemble(inst, device_arrays=dev_arrays[k], form=form)
             p = ctx.setup(s, precision=prec, format="auto", **setup)
-            x = torch.zeros(N[k], dtype=torch.float64, device="cuda")
+            x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
             try:
                 code, st = ctx.solve(s, p, None, x, rtol=1e-8, max_iters=5000, krylov=krylov)
                 its.append(st[0].iterations if code == 0 else f"{st[0].iterations} (not converged)")
@@ -382,6 +382,14 @@ def variants(ctx, insts, dev_arrays, N, flush):
         kry = kw.pop("krylov")
         t, its = _timed(lambda kry=kry, kw=kw: sweep("fp64", krylov=kry, **kw), flush, warmup=0)
         out[f"seg2d_1024_sweep_fp64_{name}"] = {"solves_per_s": len(insts) / t, "s_per_step": t, "iterations": its}
+    # the paper's own partition (pressures of all cells; interface fluxes)
+    for name, kw in (("flux_form_ML_fgmres", dict(kind="lower", krylov="fgmres")),
+                     ("flux_form_block_diagonal_minres", dict(kind="diag", krylov="minres"))):
+        kry = kw.pop("krylov")
+        t, its = _timed(lambda kry=kry, kw=kw: sweep("fp64", krylov=kry, form="flux", **kw), flush, warmup=0)
+        out[f"seg2d_1024_sweep_fp64_{name}"] = {
+            "solves_per_s": len(insts) / t, "s_per_step": t, "iterations": its,
+            "N": [int(n + 2 * inst.n_f) for n, inst in zip(N, insts)]}
     p3 = inputs.planes_3d(128, kf=1e4)
     for prec in ("fp64", "fp32"):
         def one(prec=prec):

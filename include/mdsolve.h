@@ -133,6 +133,23 @@ typedef struct {
  * the interior faces or two fracture cells on one face. */
 int mds_assemble(mds_ctx ctx, const mds_instance *inst, mds_system *out);
 
+/* Assemble one instance in the paper's own partition (Sec. 3.1, Eq. (4)):
+ * Omega = the pressures of all N = n_m + n_f cells (matrix cells, then
+ * fracture cells), Gamma = the 2 n_f interface fluxes, flux j = 2k + s of
+ * fracture cell k on side s (side 0 toward the lower coordinate along the
+ * fracture's normal).  Flux row N + j holds +1 at its matrix cell i, -1 at
+ * fracture cell n_m + k and -1/T_j at itself (the interface law
+ * p_i - p_k - lambda_j / T_j = 0, T_j the matrix-fracture transmissibility
+ * of the primal system); its transpose is the flux columns of the pressure
+ * rows, whose diagonals keep only the cell-cell and boundary
+ * transmissibilities.  The system is symmetric and indefinite; the
+ * mds_system reports n_m = N and n_f = 2 n_f, so the Omega/Gamma blocks of
+ * every preconditioner are the pressure and flux blocks.  b: the primal
+ * right-hand side in the pressure rows, 0 in the flux rows, column r at
+ * b + r (N + 2 n_f).  Eliminating the fluxes gives mds_assemble's matrix.
+ * Errors as mds_assemble. */
+int mds_assemble_flux(mds_ctx ctx, const mds_instance *inst, mds_system *out);
+
 /* Assemble n_inst independent instances (uneven sizes allowed, equal nrhs)
  * into one packed block-diagonal system.  Unknowns are ordered
  * [matrix cells of instance 0..n_inst-1; fracture cells of instance
@@ -209,13 +226,18 @@ int mds_setup_opts_default(mds_setup_opts *o);
  * A_ff: strength graph, MIS-2 with SplitMix64 priorities, aggregates,
  * piecewise-constant P, Galerkin P^T A P, L1 diagonals, coarsest dense
  * Cholesky; then the per-level storage (precision, format) used by the
- * V-cycle, chosen by timing when format = MDS_FORMAT_AUTO.  The system must
- * outlive the preconditioner. */
+ * V-cycle, chosen by timing when format = MDS_FORMAT_AUTO.  A level whose
+ * rows hold only their diagonal entry (of either sign: the flux block of
+ * mds_assemble_flux) ends its hierarchy and is solved exactly, x = b / a_ii.
+ * With kind = MDS_BLOCK_DIAG and every diagonal entry of A_ff negative the
+ * interface block of B_D is -Q_ff, so that B_D stays positive definite for
+ * PCG and MINRES.  The system must outlive the preconditioner. */
 int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_precond *out);
 int mds_precond_destroy(mds_precond prec);
 /* Hierarchy of block 0 (S~) or 1 (A_ff): number of levels, and per level the
  * rows and nonzeros (arrays of length >= 32).  *dense = 1 when the last level
- * is solved by dense Cholesky, 0 when it is smoothed only. */
+ * is solved by dense Cholesky, 2 when it has no couplings and is solved by
+ * x = b / a_ii, 0 when it is smoothed only. */
 int mds_precond_info(mds_precond prec, int block, int *nlevels, int64_t *level_n,
                      int64_t *level_nnz, int *dense);
 /* Borrowed device views of level `level` of a block: its FP64 matrix, the

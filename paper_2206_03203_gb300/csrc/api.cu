@@ -258,7 +258,7 @@ int mds_set_stream(mds_ctx ctx, void *stream) {
     return MDS_OK;
 }
 
-int mds_assemble_batch(mds_ctx ctx, const mds_instance *inst, int n_inst, mds_system *out) {
+static int assemble_any(mds_ctx ctx, const mds_instance *inst, int n_inst, mds_system *out, bool flux) {
     if (!ctx || !inst || !out || n_inst < 1) return MDS_ERR_INVALID;
     Ctx *c = &ctx->c;
     *out = nullptr;
@@ -268,10 +268,10 @@ int mds_assemble_batch(mds_ctx ctx, const mds_instance *inst, int n_inst, mds_sy
     try {
         s->ctx = c;
         if (n_inst == 1) {
-            assemble_instance(*c, inst[0], s->own);
+            assemble_instance(*c, inst[0], s->own, flux);
         } else {
             std::vector<SystemData> parts(n_inst);
-            for (int k = 0; k < n_inst; k++) assemble_instance(*c, inst[k], parts[k]);
+            for (int k = 0; k < n_inst; k++) assemble_instance(*c, inst[k], parts[k], flux);
             pack_instances(*c, parts, s->own);
         }
         s->n_m = s->own.n_m;
@@ -290,8 +290,16 @@ int mds_assemble_batch(mds_ctx ctx, const mds_instance *inst, int n_inst, mds_sy
     API_END(c)
 }
 
+int mds_assemble_batch(mds_ctx ctx, const mds_instance *inst, int n_inst, mds_system *out) {
+    return assemble_any(ctx, inst, n_inst, out, false);
+}
+
 int mds_assemble(mds_ctx ctx, const mds_instance *inst, mds_system *out) {
-    return mds_assemble_batch(ctx, inst, 1, out);
+    return assemble_any(ctx, inst, 1, out, false);
+}
+
+int mds_assemble_flux(mds_ctx ctx, const mds_instance *inst, mds_system *out) {
+    return assemble_any(ctx, inst, 1, out, true);
 }
 
 int mds_system_instances(mds_system sys, int *n_inst, int64_t *m_off, int64_t *f_off) {
@@ -441,7 +449,10 @@ int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_preco
         p->S = schur_build(*c, sys->view[0], sys->view[1], sys->view[2], sys->view[3], p->dk);
         amg_setup(*c, p->S.view(), o, p->h[0]);
         p->has_f = sys->n_f > 0;
-        if (p->has_f) amg_setup(*c, sys->view[3], o, p->h[1]);
+        if (p->has_f) {
+            amg_setup(*c, sys->view[3], o, p->h[1]);
+            p->ff_negative = !(row_kinds(*c, sys->view[3]) & 2);
+        }
         int64_t mx = sys->n_m > sys->n_f ? sys->n_m : sys->n_f;
         p->tf64 = Buf(c, sizeof(double) * (size_t)(mx > 0 ? mx : 1));
         p->tf_cap = mx;
@@ -477,7 +488,7 @@ int mds_precond_info(mds_precond p, int block, int *nlevels, int64_t *level_n, i
         if (level_n) level_n[l] = h.lv[l].A.nrow;
         if (level_nnz) level_nnz[l] = h.lv[l].A.nnz;
     }
-    if (dense) *dense = h.dense ? 1 : 0;
+    if (dense) *dense = h.dense ? 1 : (h.diagonal ? 2 : 0);
     return MDS_OK;
 }
 
@@ -560,6 +571,7 @@ void precond_apply(mds_precond p, const double *r, double *z, int nr) {
         } else {
             vcycle_apply(c, HF, rf, zf, nr);
         }
+        if (kind == MDS_BLOCK_DIAG && p->ff_negative) scale_f64(c, zf, -1.0, nf * nr);
     } else {
         float *bf = HF.lv[0].b.as<float>();
         if (kind == MDS_BLOCK_LOWER)
@@ -568,6 +580,7 @@ void precond_apply(mds_precond p, const double *r, double *z, int nr) {
             cast_f64_f32(c, rf, bf, nf * nr);
         vcycle_apply(c, HF, HF.lv[0].b.p, HF.lv[0].x.p, nr);
         cast_f32_f64(c, HF.lv[0].x.as<float>(), zf, nf * nr);
+        if (kind == MDS_BLOCK_DIAG && p->ff_negative) scale_f64(c, zf, -1.0, nf * nr);
     }
 }
 

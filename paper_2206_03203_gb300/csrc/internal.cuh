@@ -304,6 +304,7 @@ inline DCsr csr_alloc(Ctx &c, int64_t nrow, int64_t ncol, int64_t nnz) {
 int64_t scan_counts(Ctx &c, const int32_t *cnt, int32_t *out, int64_t n);
 void fill_i32(Ctx &c, int32_t *p, int32_t v, int64_t n);
 void fill_f64(Ctx &c, double *p, double v, int64_t n);
+void scale_f64(Ctx &c, double *p, double a, int64_t n);  // p <- a p
 void cast_f64_f32(Ctx &c, const double *in, float *out, int64_t n);
 void cast_f32_f64(Ctx &c, const float *in, double *out, int64_t n);
 // y = A x (FP64 CSR), nr in {1, 2, 4, 8} interleaved columns
@@ -323,7 +324,9 @@ struct SystemData {
     DCsr blk[4];
     Buf b;  // [nrhs][N]
 };
-void assemble_instance(Ctx &c, const mds_instance &inst, SystemData &out);
+// flux: the paper's partition (all pressures; interface fluxes) instead of
+// the primal [matrix; fracture] system
+void assemble_instance(Ctx &c, const mds_instance &inst, SystemData &out, bool flux = false);
 // pack several assembled instances into one block-diagonal system
 void pack_instances(Ctx &c, std::vector<SystemData> &parts, SystemData &out);
 void split_blocks(Ctx &c, const mds_csr &full, int64_t n_m, DCsr blk[4]);
@@ -365,6 +368,7 @@ struct Level {
 struct Hierarchy {
     std::vector<Level> lv;
     bool dense = false;
+    bool diagonal = false;  // last level has no couplings: x = b / a_ii
     int64_t nd = 0;
     Buf Ainv;         // FP64 [nd nd] inverse of the coarsest matrix
     int prec = 64;    // vector precision: 64 or 32
@@ -375,6 +379,9 @@ struct Hierarchy {
 };
 
 void amg_setup(Ctx &c, const mds_csr &A, const mds_setup_opts &o, Hierarchy &h);
+// bit 1: some row holds an off-diagonal entry (or no diagonal); bit 2: some
+// diagonal entry is missing or not negative (synchronises)
+int row_kinds(Ctx &c, const mds_csr &A);
 // per-level value storage and format (k_vcycle.cu), run at the end of amg_setup
 void level_storage(Ctx &c, Hierarchy &h, const mds_setup_opts &o);
 
@@ -421,6 +428,7 @@ struct mds_precond_s {
     mds::Buf dk;
     mds::Hierarchy h[2];
     bool has_f = false;
+    bool ff_negative = false;  // every a_ii of A_ff < 0 (flux block of the paper's partition)
     mds::Buf tf64;            // Algorithm 1 work vector (interleaved columns)
     int64_t tf_cap = 0;
 };

@@ -16,6 +16,8 @@ struct GridD {
     int64_t off[3];
     double h, F, elen;
     int64_t n_m, nf, N, nb;
+    int flux;    // 1: the paper's partition, interface fluxes as unknowns N + 2k + side
+    int64_t NT;  // all unknowns: N, or N + 2 nf with flux
 };
 
 __device__ __forceinline__ int64_t face_id(const GridD &g, int d, int64_t x, int64_t y, int64_t z) {
@@ -95,7 +97,9 @@ __device__ int matrix_entries(const GridD &g, const int32_t *map, const double *
             int32_t k = frac_at(g, map, d, fc);
             if (k >= 0) {
                 double kappa = (2.0 * kf[k]) / ap[k];
-                row[cnt].c = (int32_t)(g.n_m + k);
+                // flux form: the interface flux of this face side (side 0 when
+                // the face is above the cell, s = 1)
+                row[cnt].c = g.flux ? (int32_t)(g.N + 2 * k + (s ? 0 : 1)) : (int32_t)(g.n_m + k);
                 row[cnt].t = g.F / (g.h / (2.0 * ki) + 1.0 / kappa);
             } else {
                 int64_t nc[3] = {c[0], c[1], c[2]};
@@ -128,7 +132,7 @@ __device__ int fracture_entries(const GridD &g, const int32_t *map, const double
         int64_t mc[3] = {c[0], c[1], c[2]};
         mc[d] = plane - 1 + s;
         int64_t j = cell_id(g, mc);
-        row[cnt].c = (int32_t)j;
+        row[cnt].c = g.flux ? (int32_t)(g.N + 2 * k + s) : (int32_t)j;
         row[cnt].t = g.F / (g.h / (2.0 * km[j]) + 1.0 / kappa);
         cnt++;
     }
@@ -176,7 +180,11 @@ __global__ void k_count(GridD g, const int32_t *__restrict__ map, const double *
                         const double *__restrict__ kf, const double *__restrict__ ap, int32_t *__restrict__ cnt) {
     mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.N) return;
+    if (i >= g.NT) return;
+    if (i >= g.N) {  // interface flux row: matrix cell, fracture cell, itself
+        cnt[i] = 3;
+        return;
+    }
     Ent row[16];
     double tb[2];
     int has[2];
@@ -193,7 +201,27 @@ __global__ void k_fill(GridD g, const int32_t *__restrict__ map, const double *_
                        int32_t *__restrict__ ci, double *__restrict__ val, double *__restrict__ b) {
     mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.N) return;
+    if (i >= g.NT) return;
+    if (i >= g.N) {
+        // interface law of flux j = 2k + s: p_i - p_k - lambda_j / T_j = 0
+        int64_t j = i - g.N, k = j / 2;
+        int s = (int)(j % 2);
+        int d = axis[k];
+        int64_t mc[3] = {pos[3 * k], pos[3 * k + 1], g.dim == 3 ? pos[3 * k + 2] : 0};
+        mc[d] = mc[d] - 1 + s;
+        int64_t m = cell_id(g, mc);
+        double kappa = (2.0 * kf[k]) / ap[k];
+        double t = g.F / (g.h / (2.0 * km[m]) + 1.0 / kappa);
+        int64_t p = rp[i];
+        ci[p] = (int32_t)m;
+        val[p] = 1.0;
+        ci[p + 1] = (int32_t)(g.n_m + k);
+        val[p + 1] = -1.0;
+        ci[p + 2] = (int32_t)i;
+        val[p + 2] = -1.0 / t;
+        for (int r = 0; r < nrhs; r++) b[(int64_t)r * g.NT + i] = 0.0;
+        return;
+    }
     Ent row[16];
     double tb[2];
     int has[2];
@@ -202,8 +230,10 @@ __global__ void k_fill(GridD g, const int32_t *__restrict__ map, const double *_
     int cnt = is_m ? matrix_entries(g, map, km, kf, ap, i, row, tb, has)
                    : fracture_entries(g, map, km, axis, pos, kf, ap, i - g.n_m, row, tb, has, bfa, bfb);
     sort_ents(row, cnt);
+    // diagonal: the transmissibilities of the row (flux columns carry none)
     double diag = 0.0;
-    for (int q = 0; q < cnt; q++) diag += row[q].t;
+    for (int q = 0; q < cnt; q++)
+        if (row[q].c < g.N) diag += row[q].t;
     for (int s = 0; s < 2; s++)
         if (has[s]) diag += tb[s];
     int64_t p = rp[i];
@@ -215,7 +245,7 @@ __global__ void k_fill(GridD g, const int32_t *__restrict__ map, const double *_
             placed = true;
         }
         ci[p] = row[q].c;
-        val[p++] = -row[q].t;
+        val[p++] = row[q].c < g.N ? -row[q].t : (is_m ? 1.0 : -1.0);
     }
     if (!placed) {
         ci[p] = (int32_t)i;
@@ -237,7 +267,7 @@ __global__ void k_fill(GridD g, const int32_t *__restrict__ map, const double *_
                 acc += tb[s] * pv;
             }
         }
-        b[(int64_t)r * g.N + i] = acc;
+        b[(int64_t)r * g.NT + i] = acc;
     }
 }
 
@@ -436,7 +466,7 @@ static const T *stage(Ctx &c, const T *p, size_t count, bool on_device, Buf &hol
     return hold.as<T>();
 }
 
-void assemble_instance(Ctx &c, const mds_instance &in, SystemData &out) {
+void assemble_instance(Ctx &c, const mds_instance &in, SystemData &out, bool flux) {
     MDS_REQUIRE(in.dim == 2 || in.dim == 3, MDS_ERR_INVALID, "dim must be 2 or 3");
     MDS_REQUIRE(in.n >= 1 && in.nrhs >= 1 && in.n_f >= 0, MDS_ERR_INVALID, "bad instance sizes");
     MDS_REQUIRE(in.km && in.pD_left && in.pD_right, MDS_ERR_INVALID, "missing instance arrays");
@@ -458,8 +488,10 @@ void assemble_instance(Ctx &c, const mds_instance &in, SystemData &out) {
     g.n_m = in.dim == 3 ? n * n * n : n * n;
     g.nf = in.n_f;
     g.N = g.n_m + g.nf;
+    g.flux = flux ? 1 : 0;
+    g.NT = flux ? g.N + 2 * g.nf : g.N;
     g.nb = in.dim == 3 ? n * n : n;
-    MDS_REQUIRE(g.N < INT32_MAX, MDS_ERR_INVALID, "too many unknowns for int32 indices");
+    MDS_REQUIRE(g.NT < INT32_MAX, MDS_ERR_INVALID, "too many unknowns for int32 indices");
 
     bool dev = in.on_device != 0;
     Buf h0, h1, h2, h3, h4, h5, h6;
@@ -478,24 +510,26 @@ void assemble_instance(Ctx &c, const mds_instance &in, SystemData &out) {
         MDS_LAUNCH(c, KC_NONE, 0, k_map_scatter, grid_for(g.nf, 256), 256, 0, g, ax, ps, map.as<int32_t>(), c.d_err);
     c.check_err("fracture list");
 
-    Buf cnt(&c, sizeof(int32_t) * (size_t)(g.N + 1));
-    MDS_LAUNCH(c, KC_NONE, 0, k_count, grid_for(g.N, 128), 128, 0, g, map.as<int32_t>(), km, ax, ps, kf, ap,
+    Buf cnt(&c, sizeof(int32_t) * (size_t)(g.NT + 1));
+    MDS_LAUNCH(c, KC_NONE, 0, k_count, grid_for(g.NT, 128), 128, 0, g, map.as<int32_t>(), km, ax, ps, kf, ap,
                cnt.as<int32_t>());
     DCsr &A = out.full;
-    A.nrow = A.ncol = g.N;
-    A.rp = Buf(&c, sizeof(int32_t) * (size_t)(g.N + 1));
-    A.nnz = scan_counts(c, cnt.as<int32_t>(), A.rowp(), g.N);
+    A.nrow = A.ncol = g.NT;
+    A.rp = Buf(&c, sizeof(int32_t) * (size_t)(g.NT + 1));
+    A.nnz = scan_counts(c, cnt.as<int32_t>(), A.rowp(), g.NT);
     A.ci = Buf(&c, sizeof(int32_t) * (size_t)A.nnz);
     A.v = Buf(&c, sizeof(double) * (size_t)A.nnz);
-    out.b = Buf(&c, sizeof(double) * (size_t)(g.N * in.nrhs));
-    MDS_LAUNCH(c, KC_NONE, 0, k_fill, grid_for(g.N, 128), 128, 0, g, map.as<int32_t>(), km, ax, ps, kf, ap, in.nrhs,
+    out.b = Buf(&c, sizeof(double) * (size_t)(g.NT * in.nrhs));
+    MDS_LAUNCH(c, KC_NONE, 0, k_fill, grid_for(g.NT, 128), 128, 0, g, map.as<int32_t>(), km, ax, ps, kf, ap, in.nrhs,
                pL, pR, A.rowp(), A.cols(), A.vals(), out.b.as<double>());
-    out.n_m = g.n_m;
-    out.n_f = g.nf;
+    // blocks: [matrix; fracture] cells, or [all pressures; interface fluxes]
+    const int64_t nm = flux ? g.N : g.n_m, nfb = flux ? 2 * g.nf : g.nf;
+    out.n_m = nm;
+    out.n_f = nfb;
     out.nrhs = in.nrhs;
-    out.moff = {0, g.n_m};
-    out.foff = {0, g.nf};
-    split_blocks(c, A.view(), g.n_m, out.blk);
+    out.moff = {0, nm};
+    out.foff = {0, nfb};
+    split_blocks(c, A.view(), nm, out.blk);
     c.sync();  // staged host copies are released on return
 }
 

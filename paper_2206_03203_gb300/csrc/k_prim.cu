@@ -119,6 +119,18 @@ void fill_f64(Ctx &c, double *p, double v, int64_t n) {
     MDS_LAUNCH(c, KC_NONE, 0, k_fill<double>, grid_for(n, 256) > 4096 ? 4096 : grid_for(n, 256), 256, 0, p, v, n);
 }
 
+__global__ void k_scale(double *__restrict__ p, double a, int64_t n) {
+    mds_pdl_entry();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = a * p[i];
+}
+
+void scale_f64(Ctx &c, double *p, double a, int64_t n) {
+    if (n <= 0) return;
+    MDS_LAUNCH(c, KC_NONE, 2.0 * sizeof(double) * n, k_scale, grid_for(n, 256) > 4096 ? 4096 : grid_for(n, 256),
+               256, 0, p, a, n);
+}
+
 template <class A, class B>
 __global__ void k_cast(const A *__restrict__ in, B *__restrict__ out, int64_t n) {
     mds_pdl_entry();

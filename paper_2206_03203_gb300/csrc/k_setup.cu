@@ -627,6 +627,29 @@ __global__ void k_l1(int64_t n, const int32_t *__restrict__ rp, const int32_t *_
     dinv[i] = (DT)(1.0 / s);
 }
 
+// bit 1: row i holds more than its diagonal entry; bit 2: a_ii is missing
+// or not negative
+__global__ void k_row_kinds(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const double *__restrict__ v, int *flag) {
+    mds_pdl_entry();
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t b = rp[i], e = rp[i + 1];
+    int f = (e - b != 1 || ci[b] != (int32_t)i) ? 1 : 0;
+    int32_t p = find_col(ci, b, e, (int32_t)i);
+    if (!(p >= 0 && v[p] < 0.0)) f |= 2;
+    if (f) atomicOr(flag, f);
+}
+
+int row_kinds(Ctx &c, const mds_csr &A) {
+    if (A.nrow <= 0) return 0;
+    Buf f(&c, sizeof(int));
+    MDS_CUDA(cudaMemsetAsync(f.p, 0, sizeof(int), c.stream));
+    MDS_LAUNCH(c, KC_NONE, 0, k_row_kinds, grid_for(A.nrow, 256), 256, 0, A.nrow, A.row_ptr, A.col, A.val,
+               f.as<int>());
+    return c.read(f.as<int32_t>());
+}
+
 static DCsr copy_csr(Ctx &c, const mds_csr &A) {
     DCsr B = csr_alloc(c, A.nrow, A.ncol, A.nnz);
     MDS_CUDA(cudaMemcpyAsync(B.rowp(), A.row_ptr, sizeof(int32_t) * (size_t)(A.nrow + 1), cudaMemcpyDeviceToDevice,
@@ -674,6 +697,7 @@ static int64_t mis2(Ctx &c, const DCsr &A, const int8_t *g, const int32_t *deg, 
 void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h) {
     h.lv.clear();
     h.dense = false;
+    h.diagonal = false;
     h.prec = o.precision == MDS_PREC_FP64 ? 64 : 32;
     h.smoother = o.smoother;
     h.sweeps = o.sweeps < 1 ? 1 : o.sweeps;
@@ -687,6 +711,12 @@ void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h)
         int64_t n = L.A.nrow;
         L.roots = Buf(&c, (size_t)(n > 0 ? n : 1));
         MDS_CUDA(cudaMemsetAsync(L.roots.p, 0, (size_t)(n > 0 ? n : 1), c.stream));
+        // a level without couplings (each row only its diagonal, of either
+        // sign) is the last one and is solved exactly by x = b / a_ii
+        if (L.A.nnz == n && !(row_kinds(c, L.A.view()) & 1)) {
+            h.diagonal = true;
+            break;
+        }
         if (n <= o.n_coarse) {
             h.dense = true;
             break;

@@ -865,7 +865,7 @@ template <class XT, int NR> static int tail_cluster(Ctx &c) {
 template <class XT> static int tail_start(const Hierarchy &h, int64_t max_rows) {
     const int last = (int)h.lv.size() - 1;
     const int top = h.dense ? last - 1 : last;  // smoothed levels
-    if (h.smoother != MDS_SMOOTHER_L1JACOBI || h.sweeps != 1 || top < 0) return -1;
+    if (h.smoother != MDS_SMOOTHER_L1JACOBI || h.sweeps != 1 || top < 0 || h.diagonal) return -1;
     const int want_vt = std::is_same<XT, double>::value ? VT_F64 : VT_F32;
     int l0 = -1;
     for (int l = top; l >= 0 && top - l + 1 <= TAIL_MAX; l--) {
@@ -941,6 +941,12 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
     int last = (int)h.lv.size() - 1;
     if (l == last && h.dense) {
         dense_apply(c, h.Ainv.as<double>(), h.nd, NR, b, x);
+        return;
+    }
+    if (l == last && h.diagonal) {  // no couplings: exact x = b / a_ii
+        const int64_t nd = L.A.nrow;
+        MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * nd * NR, (k_vc_x0<XT, NR>), ew_grid(nd * NR), 256, 0, nd,
+                   L.dinv.as<XT>(), b, x);
         return;
     }
     if (h.use_tail && l == tail_start<XT>(h, (int64_t)tail_cluster<XT, NR>(c) * TAIL_THREADS) &&

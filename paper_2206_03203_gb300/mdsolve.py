@@ -97,6 +97,7 @@ _SIGS = {
     "mds_error_string": (C.c_char_p, [C.c_int]),
     "mds_last_error": (C.c_char_p, [C.c_void_p]),
     "mds_assemble": (C.c_int, [C.c_void_p, C.POINTER(Instance), C.POINTER(C.c_void_p)]),
+    "mds_assemble_flux": (C.c_int, [C.c_void_p, C.POINTER(Instance), C.POINTER(C.c_void_p)]),
     "mds_assemble_batch": (C.c_int, [C.c_void_p, C.POINTER(Instance), C.c_int, C.POINTER(C.c_void_p)]),
     "mds_system_instances": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "mds_system_from_csr": (C.c_int, [C.c_void_p] + [C.POINTER(Csr)] * 4 + [C.c_void_p, C.POINTER(C.c_void_p)]),
@@ -251,10 +252,13 @@ class Context:
         self._check(lib().mds_assemble_batch(self.h, arr, len(insts), C.byref(h)))
         return System(self, h)
 
-    def assemble(self, inst, device_arrays: Optional[dict] = None) -> "System":
+    def assemble(self, inst, device_arrays: Optional[dict] = None, form: str = "primal") -> "System":
         """Assemble an instance (paper_2206_03203_gb300.inputs.Instance).  With
         ``device_arrays`` (torch CUDA tensors keyed by field name) the device
-        copies are used instead of the host arrays."""
+        copies are used instead of the host arrays.  form="flux": the
+        paper's partition [pressures of all cells; interface fluxes]."""
+        if form not in ("primal", "flux"):
+            raise ValueError(f"unknown form {form!r}")
         keep = []
         if device_arrays is None:
             arrs = dict(km=np.ascontiguousarray(inst.km, dtype=np.float64),
@@ -273,7 +277,8 @@ class Context:
                      _ptr(arrs["fc_kf"]), _ptr(arrs["fc_a"]), inst.nrhs, _ptr(arrs["pD_left"]),
                      _ptr(arrs["pD_right"]), on_dev)
         h = C.c_void_p()
-        self._check(lib().mds_assemble(self.h, C.byref(s), C.byref(h)))
+        fn = lib().mds_assemble_flux if form == "flux" else lib().mds_assemble
+        self._check(fn(self.h, C.byref(s), C.byref(h)))
         return System(self, h)
 
     def system_from_csr(self, blocks, b=None) -> "System":
@@ -440,7 +445,8 @@ class Precond:
         nl, dense = C.c_int(), C.c_int()
         ln, lz = (C.c_int64 * 32)(), (C.c_int64 * 32)()
         self.ctx._check(lib().mds_precond_info(self.h, block, C.byref(nl), ln, lz, C.byref(dense)))
-        return dict(nlevels=nl.value, n=list(ln)[:nl.value], nnz=list(lz)[:nl.value], dense=bool(dense.value))
+        return dict(nlevels=nl.value, n=list(ln)[:nl.value], nnz=list(lz)[:nl.value], dense=dense.value == 1,
+                    diagonal=dense.value == 2)
 
     def prolongator_host(self, block: int, level: int):
         """Smoothed prolongator of a level as scipy CSR (None for injection)."""
