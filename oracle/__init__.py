@@ -76,6 +76,11 @@ def lib():
             L.orc_assemble_flux.restype = P(_CSR)
             L.orc_assemble_flux.argtypes = [C.c_int, C.c_int, _f64p, C.c_int64, _i32p, _i32p, _f64p,
                                        _f64p, C.c_int, _f64p, _f64p, _f64p]
+            L.orc_assemble_ex.restype = P(_CSR)
+            L.orc_assemble_ex.argtypes = [C.c_int, C.c_int, _f64p, C.c_int64, _i32p, _i32p, _f64p,
+                                          _f64p, C.c_int, _f64p, _f64p, C.c_int, C.c_int, _i64p,
+                                          P(_f64p)]
+            L.orc_free.argtypes = [C.c_void_p]
             L.orc_split.argtypes = [P(_CSR), C.c_int64] + [P(P(_CSR))] * 4
             L.orc_schur.restype = P(_CSR)
             L.orc_schur.argtypes = [P(_CSR)] * 4
@@ -158,11 +163,16 @@ class CSR:
             pass
 
 
-def assemble(inst, form="primal"):
+def assemble(inst, form="primal", junction=0, with_split=False):
     """Full system (scipy CSR) and right-hand sides [nrhs, N].  form="primal":
     [matrix cells; fracture cells] with the interface flux eliminated;
     form="flux": the paper's partition [all pressures; interface fluxes]
-    (N = n_m + 3 n_f)."""
+    (N = n_m + 3 n_f with junction 0).  junction=1: junctions of >= 3
+    fracture cells are nodes joined by half transmissibilities (star-delta in
+    the primal form, intersection cells with their own fluxes in the flux
+    form).  with_split=True also returns the size of the first block."""
+    if junction or with_split:
+        return _assemble_ex(inst, form, junction, with_split)
     L = lib()
     N = inst.n_m + inst.n_f if form == "primal" else inst.n_m + 3 * inst.n_f
     b = np.zeros((inst.nrhs, N))
@@ -178,6 +188,27 @@ def assemble(inst, form="primal"):
     if not ptr:
         raise ValueError("oracle assembly rejected the instance")
     return _from_csr(ptr), b
+
+
+def _assemble_ex(inst, form, junction, with_split):
+    L = lib()
+    pos = np.ascontiguousarray(inst.fc_pos, dtype=np.int32).reshape(-1)
+    if pos.size == 0:
+        pos = np.zeros(3, dtype=np.int32)
+    no = C.c_int64()
+    bp = _f64p()
+    ptr = L.orc_assemble_ex(inst.dim, inst.n, _p(inst.km, _f64p), inst.n_f,
+                            _p(np.ascontiguousarray(inst.fc_axis, dtype=np.int32), _i32p), _p(pos, _i32p),
+                            _p(np.ascontiguousarray(inst.fc_kf), _f64p), _p(np.ascontiguousarray(inst.fc_a), _f64p),
+                            inst.nrhs, _p(inst.pD_left, _f64p), _p(inst.pD_right, _f64p), int(form == "flux"),
+                            int(junction), C.byref(no), C.byref(bp))
+    if not ptr:
+        raise ValueError("oracle assembly rejected the instance")
+    A = _from_csr(ptr)
+    nt = A.shape[0]
+    b = np.ctypeslib.as_array(bp, shape=(inst.nrhs * nt,)).copy().reshape(inst.nrhs, nt)
+    L.orc_free(C.cast(bp, C.c_void_p))
+    return (A, b, int(no.value)) if with_split else (A, b)
 
 
 def split(A, n_m):

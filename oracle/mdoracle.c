@@ -99,6 +99,56 @@ static int32_t face_frac(const facemap *fm, int d, const int64_t c[3]) {
     return f < 0 ? -1 : fm->map[d][f];
 }
 
+/* Junction q of fracture cell k: the vertex (2D) or edge (3D) closing the
+ * cell along its (q/2)-th tangential axis e (ascending axes), on the low
+ * (q even) or high (q odd) side.  The fracture cells incident to it are the
+ * faces normal to the cell's own axis d on either side along e and the faces
+ * normal to e on either side along d.  Writes them (k included) ascending to
+ * J and returns their number, or 0 for an end on a Dirichlet face (x = 0 or
+ * x = 1), which joins no other cell; *e_out = e. */
+static int junction_members(const facemap *fm, const int32_t *fc_axis, const int32_t *fc_pos, int64_t k, int q,
+                            int *e_out, int32_t J[5]) {
+    const int dim = fm->dim, n = fm->n;
+    const int d = fc_axis[k];
+    const int32_t *p = fc_pos + 3 * k;
+    int64_t c[3] = {p[0], p[1], dim == 3 ? p[2] : 0};
+    int e = -1;
+    for (int a = 0, seen = 0; a < dim; a++) {
+        if (a == d) continue;
+        if (seen++ == q / 2) {
+            e = a;
+            break;
+        }
+    }
+    *e_out = e;
+    int64_t u = c[e] + (q & 1);
+    if (e == 0 && (u == 0 || u == n)) return 0;
+    int64_t cand[4][3];
+    int cd[4];
+    for (int r = 0; r < 4; r++) {
+        cand[r][0] = c[0];
+        cand[r][1] = c[1];
+        cand[r][2] = c[2];
+    }
+    cand[0][e] = u - 1; cd[0] = d;
+    cand[1][e] = u;     cd[1] = d;
+    cand[2][e] = u; cand[2][d] = c[d] - 1; cd[2] = e;
+    cand[3][e] = u; cand[3][d] = c[d];     cd[3] = e;
+    int m = 0;
+    J[m++] = (int32_t)k;
+    for (int r = 0; r < 4; r++) {
+        int32_t l = face_frac(fm, cd[r], cand[r]);
+        if (l >= 0 && l != k) J[m++] = l;
+    }
+    for (int a = 1; a < m; a++) /* insertion sort, ascending */
+        for (int b2 = a; b2 > 0 && J[b2 - 1] > J[b2]; b2--) {
+            int32_t t = J[b2];
+            J[b2] = J[b2 - 1];
+            J[b2 - 1] = t;
+        }
+    return m;
+}
+
 /* flux = 0: the primal system above.  flux = 1: the paper's own partition
  * (Sec. 3.1, Eq. (4)): unknowns [pressures of all cells; interface fluxes],
  * one flux lambda_j per matrix-fracture face side, j = 2k + side (side 0 =
@@ -110,20 +160,41 @@ static int32_t face_frac(const facemap *fm, int d, const int64_t c[3]) {
  * p_i - p_k - lambda_j / T_j = 0 with T_j the series transmissibility of the
  * matrix half cell and the normal coupling.  A_{Gamma Omega} = A_{Omega
  * Gamma}^T and A_{Gamma Gamma} = diag(-1/T_j): symmetric indefinite;
- * eliminating lambda gives the primal system. */
+ * eliminating lambda gives the primal system.
+ *
+ * junction = 0: every pair of fracture cells at a junction is linked by
+ * t_i t_j / (t_i + t_j).  junction = 1: a junction of m >= 3 cells is a node
+ * joined to each of its cells by the cell's half transmissibility t_l.
+ * Primal form: the node is eliminated (star-delta), T_ij = t_i t_j / sum_l
+ * t_l with the sum in ascending cell order (equal to the pairwise rule when
+ * m = 2).  Flux form: the node is an intersection cell (a subdomain of
+ * dimension N-2, Sec. 2.1) with its own pressure, appended to Omega after the
+ * fracture cells, and each member l gets an interface flux
+ * lambda = t_l (p_l - p_I) (the fracture is the higher-dimensional side),
+ * appended to Gamma after the matrix-fracture fluxes.  Intersection cells are
+ * numbered by their lowest member cell, then by that cell's junction index;
+ * their fluxes by intersection, then ascending member.  An intersection row
+ * holds an explicit zero diagonal (no pressure-pressure term) and -1 per
+ * flux.  Eliminating the fluxes and then the intersection pressures gives the
+ * star-delta primal system.  *n_omega = the number of pressure unknowns; b
+ * is written to the caller's array, or allocated (*b_out) when b is NULL. */
 static ocsr *assemble_impl(int dim, int n, const double *km, int64_t nf,
                            const int32_t *fc_axis, const int32_t *fc_pos,
                            const double *fc_kf, const double *fc_a, int nrhs,
-                           const double *pD_left, const double *pD_right, double *b, int flux) {
-    if ((dim != 2 && dim != 3) || n < 1 || nrhs < 1) return NULL;
+                           const double *pD_left, const double *pD_right, double *b, int flux, int junction,
+                           int64_t *n_omega, double **b_out) {
+    if ((dim != 2 && dim != 3) || n < 1 || nrhs < 1 || junction < 0 || junction > 1) return NULL;
     const double h = 1.0 / (double)n;
     const double F = dim == 2 ? h : h * h;      /* face measure |F| */
     const double elen = dim == 2 ? 1.0 : h;     /* fracture edge measure |e| */
     const int64_t nz = dim == 3 ? n : 1;
     const int64_t n_m = (int64_t)n * n * nz;
-    const int64_t N = n_m + nf;             /* pressure unknowns */
-    const int64_t NT = flux ? N + 2 * nf : N; /* all unknowns */
-    const int64_t nb = dim == 3 ? (int64_t)n * n : n; /* boundary faces per x side */
+    const int64_t N = n_m + nf;             /* matrix and fracture cells */
+    const int nslot = 2 * (dim - 1);        /* junctions per fracture cell */
+    ocsr *A = NULL;
+    int32_t *jid = NULL, *isz = NULL, *imem = NULL;
+    int64_t *ioff = NULL;
+    int64_t nI = 0, nIF = 0;
 
     facemap fm;
     memset(&fm, 0, sizeof fm);
@@ -145,13 +216,65 @@ static ocsr *assemble_impl(int dim, int n, const double *km, int64_t nf,
         fm.map[d][f] = (int32_t)k;
     }
 
+    /* intersection cells: junctions of >= 3 fracture cells, created by their
+     * lowest member; every member's junction slot is found by comparing
+     * member sets (two cells share at most one junction) */
+    if (flux && junction) {
+        jid = (int32_t *)malloc((size_t)(nf > 0 ? nf : 1) * 4 * sizeof(int32_t));
+        isz = (int32_t *)malloc((size_t)(nf > 0 ? 2 * nf : 1) * sizeof(int32_t));
+        imem = (int32_t *)malloc((size_t)(nf > 0 ? 2 * nf : 1) * 4 * sizeof(int32_t));
+        for (int64_t q = 0; q < nf * 4; q++) jid[q] = -1;
+        int32_t J[5], J2[5];
+        int e;
+        for (int64_t k = 0; k < nf; k++)
+            for (int q = 0; q < nslot; q++) {
+                int m = junction_members(&fm, fc_axis, fc_pos, k, q, &e, J);
+                if (m >= 3 && J[0] == k) {
+                    isz[nI] = m;
+                    for (int r = 0; r < m; r++) imem[nI * 4 + r] = J[r];
+                    nI++;
+                }
+            }
+        ioff = (int64_t *)malloc((size_t)(nI + 1) * sizeof(int64_t));
+        ioff[0] = 0;
+        for (int64_t id = 0; id < nI; id++) {
+            ioff[id + 1] = ioff[id] + isz[id];
+            for (int r = 0; r < isz[id]; r++) {
+                int32_t l = imem[id * 4 + r];
+                for (int ql = 0; ql < nslot; ql++) {
+                    int m2 = junction_members(&fm, fc_axis, fc_pos, l, ql, &e, J2);
+                    if (m2 != isz[id]) continue;
+                    int same = 1;
+                    for (int t = 0; t < m2; t++) same &= J2[t] == imem[id * 4 + t];
+                    if (same) {
+                        jid[(int64_t)l * 4 + ql] = (int32_t)id;
+                        break;
+                    }
+                }
+            }
+        }
+        nIF = ioff[nI];
+    }
+    const int64_t NO = N + nI;                        /* pressure unknowns (Omega) */
+    const int64_t GF = NO + 2 * nf;                   /* first intersection flux */
+    const int64_t NT = flux ? GF + nIF : N;           /* all unknowns */
+    const int64_t nb = dim == 3 ? (int64_t)n * n : n; /* boundary faces per x side */
+    if (n_omega) *n_omega = flux ? NO : n_m;
+    if (!b) {
+        b = (double *)malloc((size_t)(NT * nrhs > 0 ? NT * nrhs : 1) * sizeof(double));
+        if (!b) goto bad;
+        *b_out = b;
+    }
+
     /* count pass: an upper bound per row, then exact fill */
-    int64_t cap = n_m * (1 + 2 * dim) + nf * (1 + 2 + 4 * 3) + (flux ? 6 * nf : 0);
-    ocsr *A = orc_csr_new(NT, NT, cap);
+    int64_t cap = n_m * (1 + 2 * dim) + nf * (1 + 2 + 4 * 3) + (flux ? 6 * nf : 0) + 5 * nI + 3 * nIF;
+    A = orc_csr_new(NT, NT, cap);
     if (!A) goto bad;
     for (int r = 0; r < nrhs; r++)
         for (int64_t i = 0; i < NT; i++) b[(int64_t)r * NT + i] = 0.0;
 
+    /* entries: t is the transmissibility of a pressure column (written as
+     * -t) or the value itself of a flux column (+1 / -1) */
     entry row[32];
     int64_t pos = 0;
     /* matrix rows */
@@ -179,10 +302,15 @@ static ocsr *assemble_impl(int dim, int n, const double *km, int64_t nf,
                         int32_t k = face_frac(&fm, d, fc);
                         if (k >= 0) {
                             double kappa = (2.0 * fc_kf[k]) / fc_a[k];
-                            /* flux form: the interface flux column, side 0 when
-                             * the face is above this cell (s = 1) */
-                            row[cnt].c = flux ? (int32_t)(N + 2 * k + (s ? 0 : 1)) : (int32_t)(n_m + k);
-                            row[cnt].t = F / (h / (2.0 * ki) + 1.0 / kappa);
+                            if (flux) {
+                                /* the interface flux column, side 0 when the
+                                 * face is above this cell (s = 1) */
+                                row[cnt].c = (int32_t)(NO + 2 * k + (s ? 0 : 1));
+                                row[cnt].t = 1.0;
+                            } else {
+                                row[cnt].c = (int32_t)(n_m + k);
+                                row[cnt].t = F / (h / (2.0 * ki) + 1.0 / kappa);
+                            }
                         } else {
                             int64_t nc[3] = {c[0], c[1], c[2]};
                             nc[d] = c[d] + (s ? 1 : -1);
@@ -196,7 +324,7 @@ static ocsr *assemble_impl(int dim, int n, const double *km, int64_t nf,
                 qsort(row, (size_t)cnt, sizeof(entry), cmp_entry);
                 double diag = 0.0;
                 for (int q = 0; q < cnt; q++)
-                    if (row[q].c < N) diag += row[q].t; /* flux columns carry no transmissibility */
+                    if (row[q].c < NO) diag += row[q].t; /* flux columns carry no transmissibility */
                 for (int s = 0; s < 2; s++)
                     if (has_tb[s]) diag += tb[s];
                 int64_t bf = cy + n * cz;
@@ -214,7 +342,7 @@ static ocsr *assemble_impl(int dim, int n, const double *km, int64_t nf,
                         placed = 1;
                     }
                     A->ci[pos] = row[q].c;
-                    A->v[pos++] = row[q].c < N ? -row[q].t : 1.0;
+                    A->v[pos++] = row[q].c < NO ? -row[q].t : row[q].t;
                 }
                 if (!placed) {
                     A->ci[pos] = (int32_t)i;
@@ -236,59 +364,61 @@ static ocsr *assemble_impl(int dim, int n, const double *km, int64_t nf,
             int64_t mc[3] = {c[0], c[1], c[2]};
             mc[d] = plane - 1 + s;
             int64_t j = mc[0] + n * (mc[1] + n * mc[2]);
-            row[cnt].c = flux ? (int32_t)(N + 2 * k + s) : (int32_t)j;
-            row[cnt].t = F / (h / (2.0 * km[j]) + 1.0 / kappa);
+            if (flux) {
+                row[cnt].c = (int32_t)(NO + 2 * k + s);
+                row[cnt].t = -1.0;
+            } else {
+                row[cnt].c = (int32_t)j;
+                row[cnt].t = F / (h / (2.0 * km[j]) + 1.0 / kappa);
+            }
             cnt++;
         }
-        /* edges: along each tangential axis e, low (s=0) and high (s=1) side */
+        /* junctions: along each tangential axis, low (s=0) and high (s=1) end */
         double tb[2] = {0.0, 0.0};
         int has_tb[2] = {0, 0};
         int64_t bfa[2] = {0, 0}, bfb[2] = {0, 0};
-        for (int e = 0; e < dim; e++) {
-            if (e == d) continue;
-            for (int s = 0; s < 2; s++) {
-                int64_t u = c[e] + s; /* vertex coordinate of the edge along e */
-                if (e == 0 && (u == 0 || u == n)) {
-                    int side = (u == 0) ? 0 : 1;
-                    tb[side] = tk;
-                    has_tb[side] = 1;
-                    /* boundary faces sharing the edge: d-cells plane-1 and plane */
-                    int64_t fa[3] = {c[0], c[1], c[2]}, fb[3] = {c[0], c[1], c[2]};
-                    fa[d] = plane - 1;
-                    fb[d] = plane;
-                    bfa[side] = fa[1] + n * fa[2];
-                    bfb[side] = fb[1] + n * fb[2];
-                    continue;
-                }
-                /* faces incident to the edge: normal d (e-cells u-1, u) and
-                 * normal e at plane u (d-cells plane-1, plane) */
-                int64_t cand[4][3];
-                int cd[4];
-                for (int q = 0; q < 4; q++) {
-                    cand[q][0] = c[0];
-                    cand[q][1] = c[1];
-                    cand[q][2] = c[2];
-                }
-                cand[0][e] = u - 1; cd[0] = d;
-                cand[1][e] = u;     cd[1] = d;
-                /* faces normal to e: e-coordinate is the plane u, the
-                 * d-coordinate a cell index on either side of the plane */
-                cand[2][e] = u; cand[2][d] = plane - 1; cd[2] = e;
-                cand[3][e] = u; cand[3][d] = plane;     cd[3] = e;
-                for (int q = 0; q < 4; q++) {
-                    int32_t l = face_frac(&fm, cd[q], cand[q]);
-                    if (l < 0 || l == k) continue;
-                    double tl = ((fc_kf[l] * fc_a[l]) * elen) / (0.5 * h);
-                    row[cnt].c = (int32_t)(n_m + l);
-                    row[cnt].t = (tk * tl) / (tk + tl);
-                    cnt++;
-                }
+        for (int q = 0; q < nslot; q++) {
+            int32_t J[5];
+            int e;
+            int m = junction_members(&fm, fc_axis, fc_pos, k, q, &e, J);
+            if (m == 0) {
+                int side = q & 1; /* x = 0 (low end) or x = 1 (high end) */
+                tb[side] = tk;
+                has_tb[side] = 1;
+                /* boundary faces sharing the end: d-cells plane-1 and plane */
+                int64_t fa[3] = {c[0], c[1], c[2]}, fb[3] = {c[0], c[1], c[2]};
+                fa[d] = plane - 1;
+                fb[d] = plane;
+                bfa[side] = fa[1] + n * fa[2];
+                bfb[side] = fb[1] + n * fb[2];
+                continue;
+            }
+            if (flux && junction && m >= 3) {
+                /* the flux to this junction's intersection cell */
+                int32_t id = jid[k * 4 + q];
+                int rank = 0;
+                while (J[rank] != k) rank++;
+                row[cnt].c = (int32_t)(GF + ioff[id] + rank);
+                row[cnt].t = 1.0;
+                cnt++;
+                continue;
+            }
+            double S = 0.0;
+            if (junction)
+                for (int r = 0; r < m; r++) S += ((fc_kf[J[r]] * fc_a[J[r]]) * elen) / (0.5 * h);
+            for (int r = 0; r < m; r++) {
+                int32_t l = J[r];
+                if (l == k) continue;
+                double tl = ((fc_kf[l] * fc_a[l]) * elen) / (0.5 * h);
+                row[cnt].c = (int32_t)(n_m + l);
+                row[cnt].t = junction ? (tk * tl) / S : (tk * tl) / (tk + tl);
+                cnt++;
             }
         }
         qsort(row, (size_t)cnt, sizeof(entry), cmp_entry);
         double diag = 0.0;
         for (int q = 0; q < cnt; q++)
-            if (row[q].c < N) diag += row[q].t;
+            if (row[q].c < NO) diag += row[q].t;
         for (int s = 0; s < 2; s++)
             if (has_tb[s]) diag += tb[s];
         for (int r = 0; r < nrhs; r++) {
@@ -310,11 +440,23 @@ static ocsr *assemble_impl(int dim, int n, const double *km, int64_t nf,
                 placed = 1;
             }
             A->ci[pos] = row[q].c;
-            A->v[pos++] = row[q].c < N ? -row[q].t : -1.0;
+            A->v[pos++] = row[q].c < NO ? -row[q].t : row[q].t;
         }
         if (!placed) {
             A->ci[pos] = (int32_t)self;
             A->v[pos++] = diag;
+        }
+        A->rp[self + 1] = pos;
+    }
+    /* intersection rows: zero diagonal, -1 per flux (mass entering from each
+     * member fracture cell) */
+    for (int64_t id = 0; id < nI; id++) {
+        int64_t self = N + id;
+        A->ci[pos] = (int32_t)self;
+        A->v[pos++] = 0.0;
+        for (int r = 0; r < isz[id]; r++) {
+            A->ci[pos] = (int32_t)(GF + ioff[id] + r);
+            A->v[pos++] = -1.0;
         }
         A->rp[self + 1] = pos;
     }
@@ -328,7 +470,7 @@ static ocsr *assemble_impl(int dim, int n, const double *km, int64_t nf,
             mc[d] = p[d] - 1 + s;
             int64_t i = mc[0] + n * (mc[1] + n * mc[2]);
             double t = F / (h / (2.0 * km[i]) + 1.0 / kappa);
-            int64_t j = N + 2 * k + s;
+            int64_t j = NO + 2 * k + s;
             A->ci[pos] = (int32_t)i;
             A->v[pos++] = 1.0;
             A->ci[pos] = (int32_t)(n_m + k);
@@ -338,11 +480,35 @@ static ocsr *assemble_impl(int dim, int n, const double *km, int64_t nf,
             A->rp[j + 1] = pos;
         }
     }
+    /* intersection fluxes: lambda (member l of intersection I):
+     * p_l - p_I - lambda / t_l = 0 */
+    for (int64_t id = 0; id < nI; id++)
+        for (int r = 0; r < isz[id]; r++) {
+            int32_t l = imem[id * 4 + r];
+            double tl = ((fc_kf[l] * fc_a[l]) * elen) / (0.5 * h);
+            int64_t j = GF + ioff[id] + r;
+            A->ci[pos] = (int32_t)(n_m + l);
+            A->v[pos++] = 1.0;
+            A->ci[pos] = (int32_t)(N + id);
+            A->v[pos++] = -1.0;
+            A->ci[pos] = (int32_t)j;
+            A->v[pos++] = -1.0 / tl;
+            A->rp[j + 1] = pos;
+        }
     A->nnz = pos;
     for (int d = 0; d < 3; d++) free(fm.map[d]);
+    free(jid);
+    free(isz);
+    free(imem);
+    free(ioff);
     return A;
 bad:
     for (int d = 0; d < 3; d++) free(fm.map[d]);
+    free(jid);
+    free(isz);
+    free(imem);
+    free(ioff);
+    orc_csr_free(A);
     return NULL;
 }
 
@@ -350,15 +516,34 @@ ocsr *orc_assemble(int dim, int n, const double *km, int64_t nf,
                    const int32_t *fc_axis, const int32_t *fc_pos,
                    const double *fc_kf, const double *fc_a, int nrhs,
                    const double *pD_left, const double *pD_right, double *b) {
-    return assemble_impl(dim, n, km, nf, fc_axis, fc_pos, fc_kf, fc_a, nrhs, pD_left, pD_right, b, 0);
+    return assemble_impl(dim, n, km, nf, fc_axis, fc_pos, fc_kf, fc_a, nrhs, pD_left, pD_right, b, 0, 0, NULL,
+                         NULL);
 }
 
 ocsr *orc_assemble_flux(int dim, int n, const double *km, int64_t nf,
                         const int32_t *fc_axis, const int32_t *fc_pos,
                         const double *fc_kf, const double *fc_a, int nrhs,
                         const double *pD_left, const double *pD_right, double *b) {
-    return assemble_impl(dim, n, km, nf, fc_axis, fc_pos, fc_kf, fc_a, nrhs, pD_left, pD_right, b, 1);
+    return assemble_impl(dim, n, km, nf, fc_axis, fc_pos, fc_kf, fc_a, nrhs, pD_left, pD_right, b, 1, 0, NULL,
+                         NULL);
 }
+
+ocsr *orc_assemble_ex(int dim, int n, const double *km, int64_t nf,
+                      const int32_t *fc_axis, const int32_t *fc_pos,
+                      const double *fc_kf, const double *fc_a, int nrhs,
+                      const double *pD_left, const double *pD_right, int flux, int junction,
+                      int64_t *n_omega, double **b_out) {
+    *b_out = NULL;
+    ocsr *A = assemble_impl(dim, n, km, nf, fc_axis, fc_pos, fc_kf, fc_a, nrhs, pD_left, pD_right, NULL, flux,
+                            junction, n_omega, b_out);
+    if (!A) {
+        free(*b_out);
+        *b_out = NULL;
+    }
+    return A;
+}
+
+void orc_free(void *p) { free(p); }
 
 /* Slice the full system into the blocks of Eq. (4). */
 int orc_split(const ocsr *A, int64_t n_m, ocsr **Amm, ocsr **Amf, ocsr **Afm, ocsr **Aff) {

@@ -49,6 +49,20 @@ ocsr *orc_assemble_flux(int dim, int n, const double *km, int64_t nf,
                         const double *fc_kf, const double *fc_a, int nrhs,
                         const double *pD_left, const double *pD_right, double *b);
 
+/* Either form with either junction rule (0: pairwise links between the
+ * fracture cells of a junction; 1: each junction of >= 3 cells a node joined
+ * by half transmissibilities, eliminated by star-delta in the primal form,
+ * an intersection cell with interface fluxes in the flux form).  Allocates
+ * the right-hand sides (*b_out, nrhs x NT, free with orc_free);
+ * *n_omega = the size of the first block (matrix cells in the primal form,
+ * all pressures in the flux form). */
+ocsr *orc_assemble_ex(int dim, int n, const double *km, int64_t nf,
+                      const int32_t *fc_axis, const int32_t *fc_pos,
+                      const double *fc_kf, const double *fc_a, int nrhs,
+                      const double *pD_left, const double *pD_right, int flux, int junction,
+                      int64_t *n_omega, double **b_out);
+void orc_free(void *p);
+
 /* Slice a full CSR at row/column n_m into its four blocks. */
 int orc_split(const ocsr *A, int64_t n_m, ocsr **Amm, ocsr **Amf, ocsr **Afm, ocsr **Aff);
 
