@@ -102,8 +102,17 @@ const char *mds_last_error(mds_ctx ctx);
  *                      t = k_f a |e| / (h/2)
  *   Dirichlet          matrix |F| 2 k / h; fracture end on x = 0/1: t, with
  *                      the mean of the two boundary faces at that end.
+ * `junction` selects the rule at junctions of three or more fracture cells
+ * (intersections, Sec. 2.1): MDS_JUNCTION_PAIRWISE (0) links every pair as
+ * above; MDS_JUNCTION_STAR (1) joins the cells of such a junction to a node
+ * by their half transmissibilities t_l, eliminated in the primal system
+ * (star-delta: t_i t_j / sum_l t_l, the sum over the members in ascending
+ * order; two-cell junctions keep t_i t_j / (t_i + t_j)) and an intersection
+ * cell with its own pressure and interface fluxes in mds_assemble_flux.
  * `on_device` = 1 means every array pointer below is a device pointer that
  * must stay valid until mds_assemble returns; 0 means host arrays. */
+#define MDS_JUNCTION_PAIRWISE 0
+#define MDS_JUNCTION_STAR 1
 typedef struct {
     int dim;
     int n;
@@ -117,6 +126,7 @@ typedef struct {
     const double *pD_left;   /* [nrhs n^(dim-1)] */
     const double *pD_right;  /* [nrhs n^(dim-1)] */
     int on_device;
+    int junction;            /* MDS_JUNCTION_* */
 } mds_instance;
 
 /* Device CSR view.  row_ptr [nrow+1], col/val [nnz]. */
@@ -147,6 +157,16 @@ int mds_assemble(mds_ctx ctx, const mds_instance *inst, mds_system *out);
  * every preconditioner are the pressure and flux blocks.  b: the primal
  * right-hand side in the pressure rows, 0 in the flux rows, column r at
  * b + r (N + 2 n_f).  Eliminating the fluxes gives mds_assemble's matrix.
+ * With junction = MDS_JUNCTION_STAR each junction of m >= 3 fracture cells
+ * (a vertex in 2D, a grid edge in 3D) is an intersection cell appended to
+ * Omega after the fracture cells (ordered by its lowest member cell, then by
+ * that cell's junction: tangential axes ascending, low end first), and each
+ * member l gets a flux lambda = t_l (p_l - p_I) appended to Gamma after the
+ * matrix-fracture fluxes (by intersection, then ascending member): its row
+ * holds +1 at fracture cell l, -1 at the intersection cell and -1/t_l; the
+ * intersection row holds an explicit zero diagonal and -1 per member flux.
+ * n_m and n_f of the system then count these as well; eliminating the
+ * fluxes and the intersection pressures gives the star-delta primal system.
  * Errors as mds_assemble. */
 int mds_assemble_flux(mds_ctx ctx, const mds_instance *inst, mds_system *out);
 

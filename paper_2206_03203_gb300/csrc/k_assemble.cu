@@ -16,8 +16,18 @@ struct GridD {
     int64_t off[3];
     double h, F, elen;
     int64_t n_m, nf, N, nb;
-    int flux;    // 1: the paper's partition, interface fluxes as unknowns N + 2k + side
-    int64_t NT;  // all unknowns: N, or N + 2 nf with flux
+    int flux;      // 1: the paper's partition, interface fluxes as unknowns
+    int junction;  // 0: pairwise links at junctions; 1: node of >= 3 cells (star)
+    int64_t nI;    // intersection cells (flux form with junction 1)
+    int64_t nIF;   // their fluxes
+    int64_t NO;    // pressure unknowns: N + nI
+    int64_t GF;    // first intersection flux: NO + 2 nf
+    int64_t NT;    // all unknowns: N (primal) or GF + nIF (flux form)
+    // intersection tables (flux form with junction 1)
+    const int32_t *own_base;  // [nf+1] first intersection owned by each fracture cell
+    const int32_t *ioff;      // [nI+1] first flux of each intersection (relative to GF)
+    const int32_t *imem;      // [4 nI] members of each intersection, ascending
+    const int32_t *phi_int;   // [nIF] intersection of each flux
 };
 
 __device__ __forceinline__ int64_t face_id(const GridD &g, int d, int64_t x, int64_t y, int64_t z) {
@@ -99,8 +109,13 @@ __device__ int matrix_entries(const GridD &g, const int32_t *map, const double *
                 double kappa = (2.0 * kf[k]) / ap[k];
                 // flux form: the interface flux of this face side (side 0 when
                 // the face is above the cell, s = 1)
-                row[cnt].c = g.flux ? (int32_t)(g.N + 2 * k + (s ? 0 : 1)) : (int32_t)(g.n_m + k);
-                row[cnt].t = g.F / (g.h / (2.0 * ki) + 1.0 / kappa);
+                if (g.flux) {
+                    row[cnt].c = (int32_t)(g.NO + 2 * k + (s ? 0 : 1));
+                    row[cnt].t = 1.0;
+                } else {
+                    row[cnt].c = (int32_t)(g.n_m + k);
+                    row[cnt].t = g.F / (g.h / (2.0 * ki) + 1.0 / kappa);
+                }
             } else {
                 int64_t nc[3] = {c[0], c[1], c[2]};
                 nc[d] = c[d] + (s ? 1 : -1);
@@ -114,8 +129,75 @@ __device__ int matrix_entries(const GridD &g, const int32_t *map, const double *
     return cnt;
 }
 
+__device__ __forceinline__ double half_t(const GridD &g, const double *kf, const double *ap, int64_t k) {
+    return ((kf[k] * ap[k]) * g.elen) / (0.5 * g.h);
+}
+
+// Junction q of fracture cell k (normal d): the vertex (2D) / grid edge (3D)
+// closing the cell along its (q/2)-th tangential axis e, low end for even q.
+// The cells incident to it: faces normal to d at e-cells u-1 and u, faces
+// normal to e at plane u with d-cells plane-1 and plane.  J gets them, k
+// included, ascending; returns their count, 0 at a Dirichlet end (x = 0/1).
+__device__ int junction_members(const GridD &g, const int32_t *map, const int32_t *axis, const int32_t *pos,
+                                int64_t k, int q, int *e_out, int32_t J[5]) {
+    const int d = axis[k];
+    int64_t c[3] = {pos[3 * k], pos[3 * k + 1], g.dim == 3 ? pos[3 * k + 2] : 0};
+    int e = q / 2 == 0 ? (d == 0 ? 1 : 0) : (d == 2 ? 1 : 2);  // tangential axes ascending
+    *e_out = e;
+    const int64_t u = c[e] + (q & 1);
+    if (e == 0 && (u == 0 || u == g.n)) return 0;
+    int m = 0;
+    J[m++] = (int32_t)k;
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        int64_t f[3] = {c[0], c[1], c[2]};
+        int fd;
+        if (r < 2) {
+            f[e] = u - 1 + r;
+            fd = d;
+        } else {
+            f[e] = u;
+            f[d] = c[d] - 1 + (r - 2);
+            fd = e;
+        }
+        int32_t l = frac_at(g, map, fd, f);
+        if (l >= 0 && l != k) J[m++] = l;
+    }
+    for (int a = 1; a < m; a++) {
+        int32_t x = J[a];
+        int b2 = a - 1;
+        while (b2 >= 0 && J[b2] > x) {
+            J[b2 + 1] = J[b2];
+            b2--;
+        }
+        J[b2 + 1] = x;
+    }
+    return m;
+}
+
+// Intersection id of the junction with members J (m >= 3): it was created
+// by its lowest member J[0], in that cell's junction order.
+__device__ int64_t intersection_of(const GridD &g, const int32_t *map, const int32_t *axis, const int32_t *pos,
+                                   const int32_t *J, int m) {
+    const int64_t k0 = J[0];
+    const int nslot = 2 * (g.dim - 1);
+    int ord = 0;
+    for (int q = 0; q < nslot; q++) {
+        int32_t J0[5];
+        int e;
+        int m0 = junction_members(g, map, axis, pos, k0, q, &e, J0);
+        if (m0 < 3 || J0[0] != k0) continue;
+        bool same = m0 == m;
+        for (int r = 0; same && r < m; r++) same = J0[r] == J[r];
+        if (same) return g.own_base[k0] + ord;
+        ord++;
+    }
+    return -1;
+}
+
 // Entries of fracture row k (without the diagonal).  bfa/bfb are the two
-// boundary faces sharing a Dirichlet end edge.
+// boundary faces sharing a Dirichlet end edge.  Pressure columns carry their
+// transmissibility t (written -t), flux columns their value.
 __device__ int fracture_entries(const GridD &g, const int32_t *map, const double *km, const int32_t *axis,
                                 const int32_t *pos, const double *kf, const double *ap, int64_t k, Ent *row,
                                 double tb[2], int has[2], int64_t bfa[2], int64_t bfb[2]) {
@@ -123,7 +205,7 @@ __device__ int fracture_entries(const GridD &g, const int32_t *map, const double
     int64_t c[3] = {pos[3 * k], pos[3 * k + 1], g.dim == 3 ? pos[3 * k + 2] : 0};
     int64_t plane = c[d];
     double kappa = (2.0 * kf[k]) / ap[k];
-    double tk = ((kf[k] * ap[k]) * g.elen) / (0.5 * g.h);
+    double tk = half_t(g, kf, ap, k);
     int cnt = 0;
     has[0] = has[1] = 0;
     tb[0] = tb[1] = 0.0;
@@ -132,47 +214,97 @@ __device__ int fracture_entries(const GridD &g, const int32_t *map, const double
         int64_t mc[3] = {c[0], c[1], c[2]};
         mc[d] = plane - 1 + s;
         int64_t j = cell_id(g, mc);
-        row[cnt].c = g.flux ? (int32_t)(g.N + 2 * k + s) : (int32_t)j;
-        row[cnt].t = g.F / (g.h / (2.0 * km[j]) + 1.0 / kappa);
+        if (g.flux) {
+            row[cnt].c = (int32_t)(g.NO + 2 * k + s);
+            row[cnt].t = -1.0;
+        } else {
+            row[cnt].c = (int32_t)j;
+            row[cnt].t = g.F / (g.h / (2.0 * km[j]) + 1.0 / kappa);
+        }
         cnt++;
     }
-    for (int e = 0; e < g.dim; e++) {
-        if (e == d) continue;
-        for (int s = 0; s < 2; s++) {
-            int64_t u = c[e] + s;
-            if (e == 0 && (u == 0 || u == g.n)) {
-                int side = u == 0 ? 0 : 1;
-                tb[side] = tk;
-                has[side] = 1;
-                int64_t fa[3] = {c[0], c[1], c[2]}, fb[3] = {c[0], c[1], c[2]};
-                fa[d] = plane - 1;
-                fb[d] = plane;
-                bfa[side] = fa[1] + (int64_t)g.n * fa[2];
-                bfb[side] = fb[1] + (int64_t)g.n * fb[2];
-                continue;
-            }
-            // the four faces incident to the edge
-            for (int q = 0; q < 4; q++) {
-                int64_t f[3] = {c[0], c[1], c[2]};
-                int fd;
-                if (q < 2) {
-                    f[e] = u - 1 + q;
-                    fd = d;
-                } else {
-                    f[e] = u;
-                    f[d] = plane - 1 + (q - 2);
-                    fd = e;
-                }
-                int32_t l = frac_at(g, map, fd, f);
-                if (l < 0 || l == k) continue;
-                double tl = ((kf[l] * ap[l]) * g.elen) / (0.5 * g.h);
-                row[cnt].c = (int32_t)(g.n_m + l);
-                row[cnt].t = (tk * tl) / (tk + tl);
-                cnt++;
-            }
+    const int nslot = 2 * (g.dim - 1);
+    for (int q = 0; q < nslot; q++) {
+        int32_t J[5];
+        int e;
+        int m = junction_members(g, map, axis, pos, k, q, &e, J);
+        if (m == 0) {
+            int side = q & 1;
+            tb[side] = tk;
+            has[side] = 1;
+            int64_t fa[3] = {c[0], c[1], c[2]}, fb[3] = {c[0], c[1], c[2]};
+            fa[d] = plane - 1;
+            fb[d] = plane;
+            bfa[side] = fa[1] + (int64_t)g.n * fa[2];
+            bfb[side] = fb[1] + (int64_t)g.n * fb[2];
+            continue;
+        }
+        if (g.flux && g.junction && m >= 3) {  // the flux to the intersection cell
+            int64_t id = intersection_of(g, map, axis, pos, J, m);
+            if (id < 0) continue;  // unreachable: the lowest member owns every such junction
+            int rank = 0;
+            while (J[rank] != k) rank++;
+            row[cnt].c = (int32_t)(g.GF + g.ioff[id] + rank);
+            row[cnt].t = 1.0;
+            cnt++;
+            continue;
+        }
+        double S = 0.0;
+        if (g.junction)
+            for (int r = 0; r < m; r++) S += half_t(g, kf, ap, J[r]);
+        for (int r = 0; r < m; r++) {
+            const int32_t l = J[r];
+            if (l == k) continue;
+            double tl = half_t(g, kf, ap, l);
+            row[cnt].c = (int32_t)(g.n_m + l);
+            row[cnt].t = g.junction ? (tk * tl) / S : (tk * tl) / (tk + tl);
+            cnt++;
         }
     }
     return cnt;
+}
+
+// ---- intersection tables (flux form, junction rule 1)
+
+// junctions of >= 3 cells owned (lowest member) by each fracture cell
+__global__ void k_junc_own(GridD g, const int32_t *__restrict__ map, const int32_t *__restrict__ axis,
+                           const int32_t *__restrict__ pos, int32_t *__restrict__ cnt) {
+    mds_pdl_entry();
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.nf) return;
+    int own = 0;
+    for (int q = 0; q < 2 * (g.dim - 1); q++) {
+        int32_t J[5];
+        int e;
+        int m = junction_members(g, map, axis, pos, k, q, &e, J);
+        own += (m >= 3 && J[0] == k) ? 1 : 0;
+    }
+    cnt[k] = own;
+}
+
+__global__ void k_junc_list(GridD g, const int32_t *__restrict__ map, const int32_t *__restrict__ axis,
+                            const int32_t *__restrict__ pos, const int32_t *__restrict__ own_base,
+                            int32_t *__restrict__ isz, int32_t *__restrict__ imem) {
+    mds_pdl_entry();
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.nf) return;
+    int64_t id = own_base[k];
+    for (int q = 0; q < 2 * (g.dim - 1); q++) {
+        int32_t J[5];
+        int e;
+        int m = junction_members(g, map, axis, pos, k, q, &e, J);
+        if (m < 3 || J[0] != k) continue;
+        isz[id] = m;
+        for (int r = 0; r < 4; r++) imem[4 * id + r] = r < m ? J[r] : -1;
+        id++;
+    }
+}
+
+__global__ void k_junc_phi(int64_t nI, const int32_t *__restrict__ ioff, int32_t *__restrict__ phi_int) {
+    mds_pdl_entry();
+    int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nI) return;
+    for (int32_t p = ioff[I]; p < ioff[I + 1]; p++) phi_int[p] = (int32_t)I;
 }
 
 __global__ void k_count(GridD g, const int32_t *__restrict__ map, const double *__restrict__ km,
@@ -181,8 +313,13 @@ __global__ void k_count(GridD g, const int32_t *__restrict__ map, const double *
     mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.NT) return;
-    if (i >= g.N) {  // interface flux row: matrix cell, fracture cell, itself
+    if (i >= g.NO) {  // interface flux row: higher-dimensional cell, lower one, itself
         cnt[i] = 3;
+        return;
+    }
+    if (i >= g.N) {  // intersection cell: zero diagonal and its member fluxes
+        int64_t I = i - g.N;
+        cnt[i] = 1 + (g.ioff[I + 1] - g.ioff[I]);
         return;
     }
     Ent row[16];
@@ -202,9 +339,36 @@ __global__ void k_fill(GridD g, const int32_t *__restrict__ map, const double *_
     mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.NT) return;
-    if (i >= g.N) {
+    if (i >= g.GF) {
+        // intersection flux (member l of intersection I): p_l - p_I - lambda / t_l = 0
+        int64_t phi = i - g.GF;
+        int64_t I = g.phi_int[phi];
+        int32_t l = g.imem[4 * I + (phi - g.ioff[I])];
+        int64_t p = rp[i];
+        ci[p] = (int32_t)(g.n_m + l);
+        val[p] = 1.0;
+        ci[p + 1] = (int32_t)(g.N + I);
+        val[p + 1] = -1.0;
+        ci[p + 2] = (int32_t)i;
+        val[p + 2] = -1.0 / half_t(g, kf, ap, l);
+        for (int r = 0; r < nrhs; r++) b[(int64_t)r * g.NT + i] = 0.0;
+        return;
+    }
+    if (i >= g.N && i < g.NO) {  // intersection cell
+        int64_t I = i - g.N;
+        int64_t p = rp[i];
+        ci[p] = (int32_t)i;
+        val[p++] = 0.0;
+        for (int32_t f = g.ioff[I]; f < g.ioff[I + 1]; f++) {
+            ci[p] = (int32_t)(g.GF + f);
+            val[p++] = -1.0;
+        }
+        for (int r = 0; r < nrhs; r++) b[(int64_t)r * g.NT + i] = 0.0;
+        return;
+    }
+    if (i >= g.NO) {
         // interface law of flux j = 2k + s: p_i - p_k - lambda_j / T_j = 0
-        int64_t j = i - g.N, k = j / 2;
+        int64_t j = i - g.NO, k = j / 2;
         int s = (int)(j % 2);
         int d = axis[k];
         int64_t mc[3] = {pos[3 * k], pos[3 * k + 1], g.dim == 3 ? pos[3 * k + 2] : 0};
@@ -233,7 +397,7 @@ __global__ void k_fill(GridD g, const int32_t *__restrict__ map, const double *_
     // diagonal: the transmissibilities of the row (flux columns carry none)
     double diag = 0.0;
     for (int q = 0; q < cnt; q++)
-        if (row[q].c < g.N) diag += row[q].t;
+        if (row[q].c < g.NO) diag += row[q].t;
     for (int s = 0; s < 2; s++)
         if (has[s]) diag += tb[s];
     int64_t p = rp[i];
@@ -245,7 +409,7 @@ __global__ void k_fill(GridD g, const int32_t *__restrict__ map, const double *_
             placed = true;
         }
         ci[p] = row[q].c;
-        val[p++] = row[q].c < g.N ? -row[q].t : (is_m ? 1.0 : -1.0);
+        val[p++] = row[q].c < g.NO ? -row[q].t : row[q].t;
     }
     if (!placed) {
         ci[p] = (int32_t)i;
@@ -489,9 +653,11 @@ void assemble_instance(Ctx &c, const mds_instance &in, SystemData &out, bool flu
     g.nf = in.n_f;
     g.N = g.n_m + g.nf;
     g.flux = flux ? 1 : 0;
-    g.NT = flux ? g.N + 2 * g.nf : g.N;
+    MDS_REQUIRE(in.junction == MDS_JUNCTION_PAIRWISE || in.junction == MDS_JUNCTION_STAR, MDS_ERR_INVALID,
+                "unknown junction rule");
+    g.junction = in.junction;
     g.nb = in.dim == 3 ? n * n : n;
-    MDS_REQUIRE(g.NT < INT32_MAX, MDS_ERR_INVALID, "too many unknowns for int32 indices");
+    MDS_REQUIRE(g.N + 2 * g.nf < INT32_MAX, MDS_ERR_INVALID, "too many unknowns for int32 indices");
 
     bool dev = in.on_device != 0;
     Buf h0, h1, h2, h3, h4, h5, h6;
@@ -510,6 +676,38 @@ void assemble_instance(Ctx &c, const mds_instance &in, SystemData &out, bool flu
         MDS_LAUNCH(c, KC_NONE, 0, k_map_scatter, grid_for(g.nf, 256), 256, 0, g, ax, ps, map.as<int32_t>(), c.d_err);
     c.check_err("fracture list");
 
+    // intersection cells and their fluxes (flux form, junction rule 1)
+    Buf own_cnt, own_base, isz, ioff, imem, phi;
+    int64_t nI = 0, nIF = 0;
+    if (flux && g.junction && g.nf > 0) {
+        own_cnt = Buf(&c, sizeof(int32_t) * (size_t)(g.nf + 1));
+        own_base = Buf(&c, sizeof(int32_t) * (size_t)(g.nf + 1));
+        MDS_LAUNCH(c, KC_NONE, 0, k_junc_own, grid_for(g.nf, 128), 128, 0, g, map.as<int32_t>(), ax, ps,
+                   own_cnt.as<int32_t>());
+        nI = scan_counts(c, own_cnt.as<int32_t>(), own_base.as<int32_t>(), g.nf);
+        if (nI > 0) {
+            isz = Buf(&c, sizeof(int32_t) * (size_t)(nI + 1));
+            imem = Buf(&c, sizeof(int32_t) * (size_t)(4 * nI));
+            MDS_LAUNCH(c, KC_NONE, 0, k_junc_list, grid_for(g.nf, 128), 128, 0, g, map.as<int32_t>(), ax, ps,
+                       own_base.as<int32_t>(), isz.as<int32_t>(), imem.as<int32_t>());
+            ioff = Buf(&c, sizeof(int32_t) * (size_t)(nI + 1));
+            nIF = scan_counts(c, isz.as<int32_t>(), ioff.as<int32_t>(), nI);
+            phi = Buf(&c, sizeof(int32_t) * (size_t)(nIF > 0 ? nIF : 1));
+            MDS_LAUNCH(c, KC_NONE, 0, k_junc_phi, grid_for(nI, 128), 128, 0, nI, ioff.as<int32_t>(),
+                       phi.as<int32_t>());
+        }
+    }
+    g.nI = nI;
+    g.nIF = nIF;
+    g.NO = g.N + nI;
+    g.GF = g.NO + 2 * g.nf;
+    g.NT = flux ? g.GF + nIF : g.N;
+    g.own_base = own_base.p ? own_base.as<int32_t>() : nullptr;
+    g.ioff = ioff.p ? ioff.as<int32_t>() : nullptr;
+    g.imem = imem.p ? imem.as<int32_t>() : nullptr;
+    g.phi_int = phi.p ? phi.as<int32_t>() : nullptr;
+    MDS_REQUIRE(g.NT < INT32_MAX, MDS_ERR_INVALID, "too many unknowns for int32 indices");
+
     Buf cnt(&c, sizeof(int32_t) * (size_t)(g.NT + 1));
     MDS_LAUNCH(c, KC_NONE, 0, k_count, grid_for(g.NT, 128), 128, 0, g, map.as<int32_t>(), km, ax, ps, kf, ap,
                cnt.as<int32_t>());
@@ -523,7 +721,7 @@ void assemble_instance(Ctx &c, const mds_instance &in, SystemData &out, bool flu
     MDS_LAUNCH(c, KC_NONE, 0, k_fill, grid_for(g.NT, 128), 128, 0, g, map.as<int32_t>(), km, ax, ps, kf, ap, in.nrhs,
                pL, pR, A.rowp(), A.cols(), A.vals(), out.b.as<double>());
     // blocks: [matrix; fracture] cells, or [all pressures; interface fluxes]
-    const int64_t nm = flux ? g.N : g.n_m, nfb = flux ? 2 * g.nf : g.nf;
+    const int64_t nm = flux ? g.NO : g.n_m, nfb = flux ? 2 * g.nf + nIF : g.nf;
     out.n_m = nm;
     out.n_f = nfb;
     out.nrhs = in.nrhs;

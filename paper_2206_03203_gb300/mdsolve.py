@@ -38,7 +38,11 @@ class MDSError(RuntimeError):
 class Instance(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int), ("km", C.c_void_p), ("n_f", C.c_int64),
                 ("fc_axis", C.c_void_p), ("fc_pos", C.c_void_p), ("fc_kf", C.c_void_p), ("fc_a", C.c_void_p),
-                ("nrhs", C.c_int), ("pD_left", C.c_void_p), ("pD_right", C.c_void_p), ("on_device", C.c_int)]
+                ("nrhs", C.c_int), ("pD_left", C.c_void_p), ("pD_right", C.c_void_p), ("on_device", C.c_int),
+                ("junction", C.c_int)]
+
+
+JUNCTION = {"pairwise": 0, "star": 1, 0: 0, 1: 1}
 
 
 class Csr(C.Structure):
@@ -234,7 +238,7 @@ class Context:
         self._check(lib().mds_set_stream(self.h, C.c_void_p(stream)))
 
     # ---- problem ----
-    def assemble_batch(self, insts) -> "System":
+    def assemble_batch(self, insts, junction=0) -> "System":
         """Pack several instances (host arrays) into one block-diagonal system."""
         keep, arr = [], (Instance * len(insts))()
         for k, inst in enumerate(insts):
@@ -247,16 +251,20 @@ class Context:
                      pD_right=np.ascontiguousarray(inst.pD_right, dtype=np.float64))
             keep.append(a)
             arr[k] = Instance(inst.dim, inst.n, _ptr(a["km"]), inst.n_f, _ptr(a["fc_axis"]), _ptr(a["fc_pos"]),
-                              _ptr(a["fc_kf"]), _ptr(a["fc_a"]), inst.nrhs, _ptr(a["pD_left"]), _ptr(a["pD_right"]), 0)
+                              _ptr(a["fc_kf"]), _ptr(a["fc_a"]), inst.nrhs, _ptr(a["pD_left"]), _ptr(a["pD_right"]), 0,
+                              JUNCTION[junction])
         h = C.c_void_p()
         self._check(lib().mds_assemble_batch(self.h, arr, len(insts), C.byref(h)))
         return System(self, h)
 
-    def assemble(self, inst, device_arrays: Optional[dict] = None, form: str = "primal") -> "System":
+    def assemble(self, inst, device_arrays: Optional[dict] = None, form: str = "primal",
+                 junction=0) -> "System":
         """Assemble an instance (paper_2206_03203_gb300.inputs.Instance).  With
         ``device_arrays`` (torch CUDA tensors keyed by field name) the device
         copies are used instead of the host arrays.  form="flux": the
-        paper's partition [pressures of all cells; interface fluxes]."""
+        paper's partition [pressures of all cells; interface fluxes].
+        junction: "pairwise" (0) or "star" (1: star-delta in the primal form,
+        intersection cells with their own fluxes in the flux form)."""
         if form not in ("primal", "flux"):
             raise ValueError(f"unknown form {form!r}")
         keep = []
@@ -275,7 +283,7 @@ class Context:
         keep.append(arrs)
         s = Instance(inst.dim, inst.n, _ptr(arrs["km"]), inst.n_f, _ptr(arrs["fc_axis"]), _ptr(arrs["fc_pos"]),
                      _ptr(arrs["fc_kf"]), _ptr(arrs["fc_a"]), inst.nrhs, _ptr(arrs["pD_left"]),
-                     _ptr(arrs["pD_right"]), on_dev)
+                     _ptr(arrs["pD_right"]), on_dev, JUNCTION[junction])
         h = C.c_void_p()
         fn = lib().mds_assemble_flux if form == "flux" else lib().mds_assemble
         self._check(fn(self.h, C.byref(s), C.byref(h)))
