@@ -391,6 +391,20 @@ def variants(ctx, insts, dev_arrays, N, flush):
             "solves_per_s": len(insts) / t, "s_per_step": t, "iterations": its,
             "N": [int(n + 2 * inst.n_f) for n, inst in zip(N, insts)]}
     p3 = inputs.planes_3d(128, kf=1e4)
+
+    def one_flux():
+        s = ctx.assemble(p3, form="flux", junction="star")
+        p = ctx.setup(s, precision="fp64", format="auto")
+        x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+        code, st = ctx.solve(s, p, None, x, rtol=1e-8, max_iters=5000)
+        n = s.N
+        p.close()
+        s.close()
+        return st[0].iterations, n
+    t, (it, nflux) = _timed(one_flux, flush)
+    out["planes3d_128_kf1e4_fp64_flux_form_intersection_cells"] = {
+        "solves_per_s": 1.0 / t, "s_per_step": t, "iterations": it, "N": nflux,
+        "form": "paper's partition: pressures of all cells and 3,456 intersection cells; interface fluxes"}
     for prec in ("fp64", "fp32"):
         def one(prec=prec):
             s = ctx.assemble(p3)
