@@ -237,6 +237,9 @@ typedef struct {
                                 0: one launch per level operation (0: on GB300 the separate
                                 launches, overlapped by programmatic dependent launch, measured
                                 faster) */
+    int cheb_degree;         /* degree of the Chebyshev smoother, 1..8 (2): residual polynomial
+                                T_k((theta - t)/delta) / T_k(theta/delta) of D1^-1 A on
+                                [0.3, 1] (Saad, Iterative Methods, Alg. 12.1) */
 } mds_setup_opts;
 
 /* Fill `o` with the defaults listed above. */

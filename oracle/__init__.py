@@ -45,7 +45,8 @@ class _CSR(C.Structure):
 class AMGOpts(C.Structure):
     _fields_ = [("theta", C.c_double), ("n_coarse", C.c_int64), ("max_levels", C.c_int),
                 ("stall_ratio", C.c_double), ("seed", C.c_uint64), ("smoother", C.c_int),
-                ("prec", C.c_int), ("lowp_from_level", C.c_int), ("sweeps", C.c_int), ("smoothed", C.c_int)]
+                ("prec", C.c_int), ("lowp_from_level", C.c_int), ("sweeps", C.c_int), ("smoothed", C.c_int),
+                ("cheb_degree", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -249,9 +250,10 @@ DEFAULT_SEED = 0x2206_0320_3
 
 
 def amg_opts(theta=0.08, n_coarse=512, max_levels=25, stall_ratio=0.9, seed=DEFAULT_SEED,
-             smoother=0, prec=64, lowp_from_level=1, sweeps=1, smoothed=0) -> AMGOpts:
+             smoother=0, prec=64, lowp_from_level=1, sweeps=1, smoothed=0, cheb_degree=2) -> AMGOpts:
+    """smoother: 0 L1-Jacobi, 1 Chebyshev (degree cheb_degree), 2 Gauss-Seidel."""
     return AMGOpts(theta, n_coarse, max_levels, stall_ratio, seed, smoother, prec, lowp_from_level, sweeps,
-                   smoothed)
+                   smoothed, cheb_degree)
 
 
 def round_lowp(x, prec):

@@ -1288,11 +1288,16 @@ static void level_residual(const orc_amg *h, int l, const double *b, const doubl
     }
 }
 
-/* The smoother: L1-Jacobi, x <- x + D1^{-1} (b - A x) (omega = 1).
- * Chebyshev (option 1): degree-2 Chebyshev iteration for D1^{-1} A on the
- * interval [0.3, 1] (lambda_max(D1^{-1} A) <= 1 for L1 diagonals), with the
- * three-term recurrence of Saad, Iterative Methods, Alg. 12.1. */
-static void smooth(orc_amg *h, int l, const double *b, double *x, int zero_guess) {
+/* The smoothers.  0: L1-Jacobi, x <- x + D1^{-1} (b - A x) (omega = 1).
+ * 1: Chebyshev of degree cheb_degree (2 when 0) for D1^{-1} A on the
+ * interval [0.3, 1] (lambda_max(D1^{-1} A) <= 1 for L1 diagonals), by the
+ * three-term recurrence of Saad, Iterative Methods, Alg. 12.1: the residual
+ * polynomial is T_k((theta - t)/delta) / T_k(theta/delta).  2: Gauss-Seidel
+ * with the level's own diagonal, as in the paper's experiments (Sec. 4):
+ * ascending rows before the coarse correction, descending after it, so that
+ * the V-cycle stays symmetric.  Gauss-Seidel is sequential; it exists only
+ * here, to compare iteration counts with the paper's smoother. */
+static void smooth(orc_amg *h, int l, const double *b, double *x, int zero_guess, int post) {
     int64_t n = h->A[l]->nrow;
     int pv = h->o.prec == 64 ? 64 : 32;
     double *r = h->vr[l];
@@ -1306,6 +1311,25 @@ static void smooth(orc_amg *h, int l, const double *b, double *x, int zero_guess
         }
         return;
     }
+    if (h->o.smoother == 2) {
+        const ocsr *M = h->A[l];
+        const double *av = h->av[l];
+        if (zero_guess)
+            for (int64_t i = 0; i < n; i++) x[i] = 0.0;
+        for (int64_t q = 0; q < n; q++) {
+            int64_t i = post ? n - 1 - q : q;
+            double s = b[i], aii = 0.0;
+            for (int64_t p = M->rp[i]; p < M->rp[i + 1]; p++) {
+                if (M->ci[p] == i)
+                    aii = av[p];
+                else
+                    s -= av[p] * x[M->ci[p]];
+            }
+            x[i] = rnd(s / aii, pv);
+        }
+        return;
+    }
+    const int deg = h->o.cheb_degree < 1 ? 2 : h->o.cheb_degree;
     const double lo = 0.3, hi = 1.0;
     double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
     double sigma = theta / delta, rho = 1.0 / sigma;
@@ -1319,11 +1343,14 @@ static void smooth(orc_amg *h, int l, const double *b, double *x, int zero_guess
         d[i] = rnd((dv[i] * r[i]) / theta, pv);
         x[i] = rnd((zero_guess ? 0.0 : x[i]) + d[i], pv);
     }
-    double rho_new = 1.0 / (2.0 * sigma - rho);
-    level_residual(h, l, b, x, r);
-    for (int64_t i = 0; i < n; i++) {
-        d[i] = rnd(rho_new * rho * d[i] + (2.0 * rho_new / delta) * (dv[i] * r[i]), pv);
-        x[i] = rnd(x[i] + d[i], pv);
+    for (int j = 2; j <= deg; j++) {
+        double rho_new = 1.0 / (2.0 * sigma - rho);
+        level_residual(h, l, b, x, r);
+        for (int64_t i = 0; i < n; i++) {
+            d[i] = rnd(rho_new * rho * d[i] + (2.0 * rho_new / delta) * (dv[i] * r[i]), pv);
+            x[i] = rnd(x[i] + d[i], pv);
+        }
+        rho = rho_new;
     }
     free(d);
 }
@@ -1353,7 +1380,7 @@ static void vcycle_level(orc_amg *h, int l, const double *b, double *x) {
         return;
     }
     int ns = h->o.sweeps < 1 ? 1 : h->o.sweeps;
-    for (int s = 0; s < ns; s++) smooth(h, l, b, x, s == 0);
+    for (int s = 0; s < ns; s++) smooth(h, l, b, x, s == 0, 0);
     if (h->agg[l]) {
         int64_t nc = h->A[l + 1]->nrow;
         double *r = h->vr[l];
@@ -1384,7 +1411,7 @@ static void vcycle_level(orc_amg *h, int l, const double *b, double *x) {
                 if (h->agg[l][i] >= 0) x[i] = rnd(x[i] + xc[h->agg[l][i]], pv);
         }
     }
-    for (int s = 0; s < ns; s++) smooth(h, l, b, x, 0);
+    for (int s = 0; s < ns; s++) smooth(h, l, b, x, 0, 1);
 }
 
 void orc_vcycle(orc_amg *h, const double *b, double *x) {

@@ -85,11 +85,12 @@ typedef struct {
     int max_levels;
     double stall_ratio;  /* stop when n_{l+1} > stall_ratio n_l */
     uint64_t seed;
-    int smoother;        /* 0 = L1-Jacobi, 1 = Chebyshev degree 2 */
+    int smoother;        /* 0 = L1-Jacobi, 1 = Chebyshev, 2 = Gauss-Seidel (oracle only) */
     int prec;            /* 64, 32 (float storage), 16 / 17 (bf16 / fp16 row-scaled levels, float vectors) */
     int lowp_from_level; /* for prec 16/17: first level stored in bf16/fp16 */
     int sweeps;          /* smoother applications before and after the coarse correction */
     int smoothed;        /* 0 = piecewise-constant P, 1 = smoothed aggregation P */
+    int cheb_degree;     /* Chebyshev degree (0 = 2) */
 } orc_amg_opts;
 
 /* Storage rounding used by the precision emulation: 32 -> float,

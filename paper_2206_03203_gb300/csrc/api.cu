@@ -407,6 +407,7 @@ int mds_setup_opts_default(mds_setup_opts *o) {
     o->sweeps = 1;
     o->prolongation = MDS_PROLONG_PIECEWISE;
     o->coarse_tail = 0;
+    o->cheb_degree = 2;
     return MDS_OK;
 }
 
@@ -429,6 +430,7 @@ int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_preco
     MDS_REQUIRE(o.sell_sigma == 1 || (o.sell_sigma % o.sell_c == 0 && o.sell_sigma <= 1024), MDS_ERR_INVALID,
                 "sell_sigma must be 1 or a multiple of sell_c up to 1024");
     MDS_REQUIRE(o.sweeps >= 1 && o.sweeps <= 8, MDS_ERR_INVALID, "sweeps must be 1..8");
+    MDS_REQUIRE(o.cheb_degree >= 1 && o.cheb_degree <= 8, MDS_ERR_INVALID, "cheb_degree must be 1..8");
     MDS_REQUIRE(o.prolongation == MDS_PROLONG_PIECEWISE || o.prolongation == MDS_PROLONG_SMOOTHED, MDS_ERR_INVALID,
                 "unknown prolongation");
     MDS_REQUIRE(o.kind >= 0 && o.kind <= 2, MDS_ERR_INVALID, "bad preconditioner kind");

@@ -374,6 +374,7 @@ struct Hierarchy {
     int prec = 64;    // vector precision: 64 or 32
     int smoother = 0;
     int sweeps = 1;
+    int cheb_degree = 2;
     int nr_cap = 0;   // columns the level work vectors hold
     bool use_tail = true;  // run the coarse end of the V-cycle as one cluster kernel
 };

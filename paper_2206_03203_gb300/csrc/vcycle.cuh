@@ -540,7 +540,6 @@ static void smooth_stored(Ctx &c, const Hierarchy &h, const Level &L, const XT *
     const XT *dinv = L.dinv.as<XT>();
     const double lo = 0.3, hi = 1.0;
     const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta, rho = 1.0 / sigma;
-    const double rho1 = 1.0 / (2.0 * sigma - rho);
     const XT *cur = x0;
     for (int s = 0; s < h.sweeps; s++) {
         XT *dst = x;
@@ -564,9 +563,14 @@ static void smooth_stored(Ctx &c, const Hierarchy &h, const Level &L, const XT *
                 MDS_LAUNCH(c, KC_NONE, 0, (k_cheb_first<XT, NR>), ew_grid(n * NR), 256, 0, n, dinv, b,
                            (const XT *)nullptr, (XT)(1.0 / theta), d, dst);
             }
-            level_op<XT, VK_RESID, NR>(c, L, b, dst, nullptr, nullptr, r, 0);
-            MDS_LAUNCH(c, KC_NONE, 0, (k_cheb_next<XT, NR>), ew_grid(n * NR), 256, 0, n, dinv, r, (XT)(rho1 * rho),
-                       (XT)(2.0 * rho1 / delta), d, dst);
+            double rho_old = rho;
+            for (int j = 2; j <= h.cheb_degree; j++) {
+                const double rho_new = 1.0 / (2.0 * sigma - rho_old);
+                level_op<XT, VK_RESID, NR>(c, L, b, dst, nullptr, nullptr, r, 0);
+                MDS_LAUNCH(c, KC_NONE, 0, (k_cheb_next<XT, NR>), ew_grid(n * NR), 256, 0, n, dinv, r,
+                           (XT)(rho_new * rho_old), (XT)(2.0 * rho_new / delta), d, dst);
+                rho_old = rho_new;
+            }
         }
         cur = dst;
     }

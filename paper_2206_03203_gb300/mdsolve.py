@@ -55,7 +55,7 @@ class SetupOpts(C.Structure):
                 ("stall_ratio", C.c_double), ("seed", C.c_uint64), ("smoother", C.c_int),
                 ("precision", C.c_int), ("lowp_from_level", C.c_int), ("kind", C.c_int), ("format", C.c_int),
                 ("sell_c", C.c_int), ("sell_sigma", C.c_int), ("sweeps", C.c_int), ("prolongation", C.c_int),
-                ("coarse_tail", C.c_int)]
+                ("coarse_tail", C.c_int), ("cheb_degree", C.c_int)]
 
 
 class SolveOpts(C.Structure):

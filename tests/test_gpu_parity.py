@@ -423,12 +423,16 @@ OPTION_CASES = [
     dict(precision="bf16", format="sell", sell_sigma=256),
     dict(precision="fp32", format="auto"),
     dict(precision="fp64", format="auto", smoother="chebyshev"),
+    dict(precision="fp64", smoother="chebyshev", cheb_degree=1),
+    dict(precision="fp64", smoother="chebyshev", cheb_degree=3),
+    dict(precision="fp32", smoother="chebyshev", cheb_degree=4, sweeps=2),
 ]
 
 
 def oracle_kw(cfg):
     return dict(prec=PREC_CODE[cfg.get("precision", "fp64")], smoother=1 if cfg.get("smoother") == "chebyshev" else 0,
-                sweeps=cfg.get("sweeps", 1), lowp_from_level=cfg.get("lowp_from_level", 1))
+                sweeps=cfg.get("sweeps", 1), lowp_from_level=cfg.get("lowp_from_level", 1),
+                cheb_degree=cfg.get("cheb_degree", 2))
 
 
 def tol_of(cfg):
@@ -457,7 +461,8 @@ def test_vcycle_options_parity(ctx, oracle_mod, torch_mod, case, cfg):
 
 @pytest.mark.parametrize("cfg", [dict(precision="bf16"), dict(precision="fp16"), dict(smoother="chebyshev"),
                                  dict(precision="fp32", smoother="chebyshev", format="sell"),
-                                 dict(precision="fp32", sweeps=2, format="auto")],
+                                 dict(precision="fp32", sweeps=2, format="auto"),
+                                 dict(smoother="chebyshev", cheb_degree=3)],
                          ids=lambda c: "-".join(f"{k}={v}" for k, v in c.items()))
 @pytest.mark.parametrize("case", ["seg2d-96", "planes3d-16", "rects3d-18"])
 def test_solve_options_parity(ctx, oracle_mod, torch_mod, case, cfg):
