@@ -9,10 +9,15 @@ residual of 1e-8.  value = solves per second over the whole step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Under torchrun every rank runs an independent replica of the workload (the
-path does not shard); value sums the ranks' solves over the
+Under torchrun every rank runs an independent replica of the workload (a
+single solve is not split across GPUs); value sums the ranks' solves over the
 slowest rank's time.  ``--impl reference`` times the CPU oracle on a bounded
 sample instead (rank 0 only).
+
+Accuracy: the relative residual of every solve, and for the contrast-1e4
+member the relative error of the GPU solution against a sparse direct solve
+(SuperLU) of the same assembled FP64 system on the host, computed in a
+separate process while the GPU runs.
 """
 from __future__ import annotations
 
@@ -121,6 +126,15 @@ def profile_traffic(kernel_class: str, avg_alg_bytes: float):
     return None
 
 
+def _direct_solve(indptr, indices, data, b):
+    """Sparse LU (SuperLU, COLAMD ordering) of the assembled system on the
+    host: the FP64 direct solution the GPU result is compared with."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    A = sp.csc_matrix(sp.csr_matrix((data, indices, indptr), shape=(len(indptr) - 1,) * 2))
+    return spla.spsolve(A, b, permc_spec="COLAMD")
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -166,6 +180,17 @@ def run_gpu(args):
             p.close()
             s.close()
         return its
+
+    # direct reference for the contrast-1e4 member: started now, on the host,
+    # in a spawned process, so that it runs while the GPU is timed
+    direct = None
+    if rank == 0 and not args.no_direct:
+        import multiprocessing as mp
+        s = ctx.assemble(insts[-1], device_arrays=dev_arrays[-1])
+        (_, _, _, _, Ah), bh = s.to_host()
+        s.close()
+        pool = mp.get_context("spawn").Pool(1)
+        direct = (pool, pool.apply_async(_direct_solve, (Ah.indptr, Ah.indices, Ah.data, bh[0])), Ah, bh[0])
 
     peak, peak_src = measured_peaks()
     # warm-up; the first one also profiles every kernel class (events around
@@ -230,6 +255,22 @@ def run_gpu(args):
     value = solves / t_total
     dof_iter = sum(n * i for n, i in zip(N, iters)) * args.steps * world / t_total
 
+    # accuracy of the timed solves
+    accuracy = {"relres_true_per_contrast": [st.relres_true for st in stats_last]}
+    if direct is not None:
+        pool, job, Ah, bh = direct
+        xg = xs[-1].cpu().numpy()
+        try:
+            xd = job.get(timeout=600)
+            accuracy["contrast_1e4_vs_direct"] = {
+                "rel_error": float(np.linalg.norm(xg - xd) / np.linalg.norm(xd)),
+                "relres_direct": float(np.linalg.norm(bh - Ah @ xd) / np.linalg.norm(bh)),
+                "relres_gpu": float(np.linalg.norm(bh - Ah @ xg) / np.linalg.norm(bh)),
+                "direct": "scipy spsolve (SuperLU, COLAMD) of the same assembled FP64 system, host"}
+        except Exception as e:  # the reference is reported, never fatal
+            accuracy["contrast_1e4_vs_direct"] = {"error": str(e)}
+        pool.terminate()
+
     # end-to-end through the C ABI with host buffers (copies inside the timed region)
     e2e_t = 0.0
     h2d = 0
@@ -285,6 +326,7 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}", "N_per_solve": N[0],
                    "iterations_per_contrast": iters},
         "dof_iter_per_s": dof_iter,
+        "accuracy": accuracy,
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -522,6 +564,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--no-direct", action="store_true", help="skip the host direct solve of the accuracy check")
     ap.add_argument("--profile-case", action="store_true", help="short fixed run for ncu captures")
     ap.add_argument("--max-iters", type=int, default=60)
     ap.add_argument("--n", type=int, default=1024)
