@@ -38,6 +38,9 @@ import numpy as np  # noqa: E402
 METRIC = "solves/s to 1e-8 rel-res (assemble + set-up + FGMRES, contrast sweep)"
 UNIT = "solves/s"
 FP64_PEAK_TFLOPS = 1.25
+# approximate FGMRES iterations per contrast member: the order (longest
+# first) in which the solves are handed to concurrent streams
+SWEEP_WORK = [1700, 1420, 1610, 645, 226, 505, 1006, 1180, 1770]
 WORKLOAD = ("2D 1024x1024 TPFA, log-normal k_m sigma=1, 64 random segments (k_f = c / 1/c, a = 1e-4), "
             "contrast sweep c = 1e-4..1e4 (9 solves per step), FP64 FGMRES(30) + M_L, rtol 1e-8")
 
@@ -391,8 +394,11 @@ def variants(ctx, insts, dev_arrays, N, flush):
     same sweep, the nine-plane 3D instance, and the 256-instance batch."""
     import torch
 
-    from paper_2206_03203_gb300 import inputs, sharding
+    from paper_2206_03203_gb300 import inputs, mdsolve, sharding
     out = {}
+
+    def mdsolve_ctx(stream):
+        return mdsolve.Context(torch.cuda.current_device(), stream=stream)
 
     def sweep(prec, krylov="fgmres", form="primal", **setup):
         its = []
@@ -424,6 +430,58 @@ def variants(ctx, insts, dev_arrays, N, flush):
         kry = kw.pop("krylov")
         t, its = _timed(lambda kry=kry, kw=kw: sweep("fp64", krylov=kry, **kw), flush, warmup=0)
         out[f"seg2d_1024_sweep_fp64_{name}"] = {"solves_per_s": len(insts) / t, "s_per_step": t, "iterations": its}
+    # the same sweep with the nine solves spread over four library contexts,
+    # each on its own CUDA stream and host thread (longest solves first): the
+    # latency-bound phases of one solve (coarse levels, host round trips)
+    # overlap with the others' kernels
+    import queue
+    from concurrent.futures import ThreadPoolExecutor
+    T = 4
+    streams = [torch.cuda.Stream() for _ in range(T)]
+    cts = [mdsolve_ctx(s_.cuda_stream) for s_ in streams]
+    xs4 = [torch.zeros(n, dtype=torch.float64, device="cuda") for n in N]
+    torch.cuda.synchronize()
+
+    def sweep_streams():
+        q = queue.Queue()
+        for k in sorted(range(len(insts)), key=lambda k: -SWEEP_WORK[k]):
+            q.put(k)
+        its = {}
+
+        def worker(i):
+            while True:
+                try:
+                    k = q.get_nowait()
+                except queue.Empty:
+                    return
+                c_ = cts[i]
+                s = c_.assemble(insts[k], device_arrays=dev_arrays[k])
+                p = c_.setup(s, precision="fp64", format="auto")
+                xs4[k].zero_()
+                code, st = c_.solve(s, p, None, xs4[k], rtol=1e-8, max_iters=5000)
+                its[k] = st[0].iterations if code == 0 else f"{st[0].iterations} (status {code})"
+                p.close()
+                s.close()
+        with ThreadPoolExecutor(T) as ex:
+            list(ex.map(worker, range(T)))
+        for st_ in streams:
+            st_.synchronize()
+        return [its[k] for k in range(len(insts))]
+    sweep_streams()
+    ts = []
+    for _ in range(2):
+        flush.fill_(0.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its = sweep_streams()
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    out["seg2d_1024_sweep_fp64_4streams"] = {
+        "solves_per_s": len(insts) / min(ts), "s_per_step": min(ts), "iterations": its,
+        "how": "the headline sweep, nine solves over four contexts / CUDA streams / host threads; host clock"}
+    for c_ in cts:
+        c_.close()
+
     # the paper's own partition (pressures of all cells; interface fluxes)
     for name, kw in (("flux_form_ML_fgmres", dict(kind="lower", krylov="fgmres")),
                      ("flux_form_block_diagonal_minres", dict(kind="diag", krylov="minres"))):
