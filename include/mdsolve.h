@@ -322,6 +322,29 @@ int mds_solve_opts_default(mds_solve_opts *o);
 int mds_solve(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, double *x,
               int nrhs, const mds_solve_opts *opts, mds_rhs_stats *stats);
 
+/* The same solve without blocking the calling thread: the solve's host
+ * control loop runs on a library thread and mds_solve_async returns at once
+ * (MDS_OK when started, or an error for invalid arguments or an uncollected
+ * previous solve).  b, x, the system and the preconditioner must stay valid
+ * until mds_solve_wait returns.  Any other call on the context (or on a
+ * system or preconditioner of it) first waits for the solve to finish, so
+ * the context is never used by two threads at once; mds_last_error is
+ * meaningful after mds_solve_wait.  Several contexts, each on its own CUDA
+ * stream, can thus solve concurrently on one GPU from one host thread: the
+ * latency-bound phases of one solve (coarse levels, the host round trip of
+ * each Krylov step) overlap with the kernels of the others.  This has no
+ * counterpart in the paper; it serves throughput over many independent
+ * solves. */
+int mds_solve_async(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, double *x,
+                    int nrhs, const mds_solve_opts *opts);
+/* 1 when the asynchronous solve has finished, 0 while it runs,
+ * MDS_ERR_INVALID when none was started (or it was already collected). */
+int mds_solve_done(mds_ctx ctx);
+/* Waits for the asynchronous solve, copies its statistics (up to `count`
+ * entries, as mds_solve's stats; may be NULL) and returns its status (as
+ * mds_solve would).  MDS_ERR_INVALID when no solve is pending. */
+int mds_solve_wait(mds_ctx ctx, mds_rhs_stats *stats, int count);
+
 /* ---- solve without device allocation ----
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory while solving: code running inside a

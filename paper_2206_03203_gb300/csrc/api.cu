@@ -165,6 +165,14 @@ using namespace mds;
     }                                                                     \
     return MDS_OK;
 
+namespace mds {
+// Waits for the context's asynchronous solve, if one is running; its result
+// stays for mds_solve_wait.
+static void async_join(Ctx *c) {
+    if (c && c->async.th.joinable()) c->async.th.join();
+}
+}  // namespace mds
+
 extern "C" {
 
 const char *mds_error_string(int s) {
@@ -243,6 +251,7 @@ static void ctx_drop_dependent(Ctx *c) {
 
 int mds_destroy(mds_ctx ctx) {
     if (!ctx) return MDS_ERR_INVALID;
+    async_join(&ctx->c);
     if (ctx->c.destroy_requested) return MDS_ERR_INVALID;
     if (ctx->c.dependents > 0) {
         ctx->c.destroy_requested = true;
@@ -254,12 +263,14 @@ int mds_destroy(mds_ctx ctx) {
 
 int mds_set_stream(mds_ctx ctx, void *stream) {
     if (!ctx) return MDS_ERR_INVALID;
+    async_join(&ctx->c);
     ctx->c.stream = (cudaStream_t)stream;
     return MDS_OK;
 }
 
 static int assemble_any(mds_ctx ctx, const mds_instance *inst, int n_inst, mds_system *out, bool flux) {
     if (!ctx || !inst || !out || n_inst < 1) return MDS_ERR_INVALID;
+    async_join(&ctx->c);
     Ctx *c = &ctx->c;
     *out = nullptr;
     API_BEGIN
@@ -323,6 +334,7 @@ int mds_system_from_csr(mds_ctx ctx, const mds_csr *Amm, const mds_csr *Amf, con
                         const double *b, mds_system *out) {
     if (!ctx || !out || !Amm || !Aff) return MDS_ERR_INVALID;
     Ctx *c = &ctx->c;
+    async_join(c);
     *out = nullptr;
     API_BEGIN
     MDS_CUDA(cudaSetDevice(c->device));
@@ -366,6 +378,7 @@ int mds_system_from_csr(mds_ctx ctx, const mds_csr *Amm, const mds_csr *Amf, con
 int mds_system_destroy(mds_system sys) {
     if (!sys) return MDS_ERR_INVALID;
     Ctx *c = sys->ctx;
+    async_join(c);
     cudaSetDevice(c->device);
     delete sys;
     ctx_drop_dependent(c);
@@ -414,6 +427,7 @@ int mds_setup_opts_default(mds_setup_opts *o) {
 int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_precond *out) {
     if (!ctx || !sys || !out) return MDS_ERR_INVALID;
     Ctx *c = &ctx->c;
+    async_join(c);
     *out = nullptr;
     API_BEGIN
     MDS_CUDA(cudaSetDevice(c->device));
@@ -471,6 +485,7 @@ int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_preco
 int mds_precond_destroy(mds_precond p) {
     if (!p) return MDS_ERR_INVALID;
     Ctx *c = p->ctx;
+    async_join(c);
     cudaSetDevice(c->device);
     delete p;
     ctx_drop_dependent(c);
@@ -604,6 +619,7 @@ extern "C" {
 int mds_precond_apply(mds_ctx ctx, mds_precond p, const double *r, double *z) {
     if (!ctx || !p || !r || !z) return MDS_ERR_INVALID;
     Ctx *c = &ctx->c;
+    async_join(c);
     API_BEGIN
     precond_apply(p, r, z, 1);
     API_END(c)
@@ -612,6 +628,7 @@ int mds_precond_apply(mds_ctx ctx, mds_precond p, const double *r, double *z) {
 int mds_vcycle(mds_ctx ctx, mds_precond p, int block, const double *b, double *x) {
     if (!ctx || !p || !b || !x || block < 0 || block > 1 || (block == 1 && !p->has_f)) return MDS_ERR_INVALID;
     Ctx *c = &ctx->c;
+    async_join(c);
     API_BEGIN
     vcycle_f64(*c, p->h[block], b, x, 1);
     API_END(c)
@@ -620,6 +637,7 @@ int mds_vcycle(mds_ctx ctx, mds_precond p, int block, const double *b, double *x
 int mds_spmv(mds_ctx ctx, mds_system sys, const double *x, double *y) {
     if (!ctx || !sys || !x || !y) return MDS_ERR_INVALID;
     Ctx *c = &ctx->c;
+    async_join(c);
     API_BEGIN
     spmv_f64(*c, sys->view[4], x, y, KC_SPMV);
     API_END(c)
@@ -638,9 +656,10 @@ int mds_solve_opts_default(mds_solve_opts *o) {
     return MDS_OK;
 }
 
-int mds_solve(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, double *x, int nrhs,
-              const mds_solve_opts *opts, mds_rhs_stats *stats) {
-    if (!ctx || !sys || !x || nrhs < 1) return MDS_ERR_INVALID;
+}  // extern "C"
+
+static int solve_impl(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, double *x, int nrhs,
+                      const mds_solve_opts *opts, mds_rhs_stats *stats) {
     Ctx *c = &ctx->c;
     int worst = MDS_OK;
     API_BEGIN
@@ -738,10 +757,68 @@ int mds_solve(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, do
     API_END(c)
 }
 
+extern "C" {
+
+int mds_solve(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, double *x, int nrhs,
+              const mds_solve_opts *opts, mds_rhs_stats *stats) {
+    if (!ctx || !sys || !x || nrhs < 1) return MDS_ERR_INVALID;
+    async_join(&ctx->c);
+    return solve_impl(ctx, sys, prec, b, x, nrhs, opts, stats);
+}
+
+int mds_solve_async(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, double *x, int nrhs,
+                    const mds_solve_opts *opts) {
+    if (!ctx || !sys || !x || nrhs < 1) return MDS_ERR_INVALID;
+    Ctx *c = &ctx->c;
+    async_join(c);
+    auto &A = c->async;
+    if (A.pending) {
+        c->last_error = "the previous asynchronous solve was not collected by mds_solve_wait";
+        return MDS_ERR_INVALID;
+    }
+    mds_solve_opts o;
+    mds_solve_opts_default(&o);
+    if (opts) o = *opts;
+    API_BEGIN
+    A.stats.assign((size_t)nrhs * (size_t)sys->n_inst, mds_rhs_stats{});
+    A.status = MDS_OK;
+    A.done = std::make_shared<std::atomic<int>>(0);
+    auto done = A.done;
+    A.th = std::thread([ctx, sys, prec, b, x, nrhs, o, done] {
+        Ctx *cc = &ctx->c;
+        cudaSetDevice(cc->device);
+        cc->async.status = solve_impl(ctx, sys, prec, b, x, nrhs, &o, cc->async.stats.data());
+        done->store(1);
+    });
+    A.pending = true;
+    API_END(c)
+}
+
+int mds_solve_done(mds_ctx ctx) {
+    if (!ctx || !ctx->c.async.pending) return MDS_ERR_INVALID;
+    return ctx->c.async.done->load();
+}
+
+int mds_solve_wait(mds_ctx ctx, mds_rhs_stats *stats, int count) {
+    if (!ctx) return MDS_ERR_INVALID;
+    Ctx *c = &ctx->c;
+    async_join(c);
+    auto &A = c->async;
+    if (!A.pending) {
+        c->last_error = "no asynchronous solve to wait for";
+        return MDS_ERR_INVALID;
+    }
+    A.pending = false;
+    if (stats)
+        for (int q = 0; q < count && q < (int)A.stats.size(); q++) stats[q] = A.stats[q];
+    return A.status;
+}
+
 int mds_solve_noalloc(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, double *x,
                       const mds_solve_opts *opts, mds_rhs_stats *stats) {
     if (!ctx || !sys || !x) return MDS_ERR_INVALID;
     Ctx *c = &ctx->c;
+    async_join(c);
     API_BEGIN
     MDS_CUDA(cudaSetDevice(c->device));
     mds_solve_opts o;
@@ -785,6 +862,7 @@ int mds_solve_noalloc(mds_ctx ctx, mds_system sys, mds_precond prec, const doubl
 
 int mds_timing_enable(mds_ctx ctx, int k, int enable) {
     if (!ctx || k < 0 || k >= MDS_KCLASS_COUNT) return MDS_ERR_INVALID;
+    async_join(&ctx->c);
     ctx->c.timing[k] = enable != 0;
     return MDS_OK;
 }
@@ -792,6 +870,7 @@ int mds_timing_enable(mds_ctx ctx, int k, int enable) {
 int mds_timing_reset(mds_ctx ctx) {
     if (!ctx) return MDS_ERR_INVALID;
     Ctx &c = ctx->c;
+    async_join(&c);
     cudaStreamSynchronize(c.stream);
     for (int k = 0; k < MDS_KCLASS_COUNT; k++) {
         c.ev_used[k] = 0;
@@ -809,6 +888,7 @@ int mds_timing_reset(mds_ctx ctx) {
 
 int mds_timing_sample_every(mds_ctx ctx, int every) {
     if (!ctx || every < 1) return MDS_ERR_INVALID;
+    async_join(&ctx->c);
     ctx->c.sample_every = every;
     return MDS_OK;
 }
@@ -826,6 +906,7 @@ static double event_ms(Ctx *c, int k) {
 int mds_timing_sampled(mds_ctx ctx, int k, int64_t *launches, double *ms, double *bytes, double *flops) {
     if (!ctx || k < 0 || k >= MDS_KCLASS_COUNT) return MDS_ERR_INVALID;
     Ctx *c = &ctx->c;
+    async_join(c);
     API_BEGIN
     c->sync();
     if (launches) *launches = c->tlaunches[k];
@@ -838,6 +919,7 @@ int mds_timing_sampled(mds_ctx ctx, int k, int64_t *launches, double *ms, double
 int mds_timing_query(mds_ctx ctx, int k, int64_t *launches, double *ms, double *bytes, double *flops) {
     if (!ctx || k < 0 || k >= MDS_KCLASS_COUNT) return MDS_ERR_INVALID;
     Ctx *c = &ctx->c;
+    async_join(c);
     API_BEGIN
     c->sync();
     if (launches) *launches = c->launches[k];
@@ -850,6 +932,7 @@ int mds_timing_query(mds_ctx ctx, int k, int64_t *launches, double *ms, double *
 int mds_memcpy(mds_ctx ctx, void *dst, const void *src, size_t bytes) {
     if (!ctx || (!dst && bytes) || (!src && bytes)) return MDS_ERR_INVALID;
     Ctx *c = &ctx->c;
+    async_join(c);
     API_BEGIN
     if (bytes) MDS_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
     c->sync();
@@ -858,6 +941,7 @@ int mds_memcpy(mds_ctx ctx, void *dst, const void *src, size_t bytes) {
 
 int mds_launch_count(mds_ctx ctx, int64_t *launches) {
     if (!ctx || !launches) return MDS_ERR_INVALID;
+    async_join(&ctx->c);
     *launches = ctx->c.total_launches;
     return MDS_OK;
 }

@@ -6,7 +6,10 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <atomic>
+#include <memory>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <utility>
 #include <vector>
@@ -152,6 +155,15 @@ struct Ctx {
     bool timing_suspended = false; // capture of the unbracketed graph variant
     Graph *capturing = nullptr;   // recording target while a stream capture is open
     void *owner = nullptr;        // the mds_ctx handle that holds this context
+    // asynchronous solve (mds_solve_async): the host control loop of one
+    // solve on a library thread; every other call on the context joins it first
+    struct Async {
+        std::thread th;
+        bool pending = false;             // started and not yet collected by mds_solve_wait
+        std::shared_ptr<std::atomic<int>> done;
+        int status = 0;
+        std::vector<mds_rhs_stats> stats;
+    } async;
     int dependents = 0;           // live systems and preconditioners made on this context
     bool destroy_requested = false;
     cudaStream_t cap_stream = nullptr;

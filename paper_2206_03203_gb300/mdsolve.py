@@ -123,6 +123,10 @@ _SIGS = {
     "mds_solve_opts_default": (C.c_int, [C.POINTER(SolveOpts)]),
     "mds_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                             C.POINTER(SolveOpts), C.POINTER(RhsStats)]),
+    "mds_solve_async": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                  C.POINTER(SolveOpts)]),
+    "mds_solve_done": (C.c_int, [C.c_void_p]),
+    "mds_solve_wait": (C.c_int, [C.c_void_p, C.POINTER(RhsStats), C.c_int]),
     "mds_solve_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.POINTER(SolveOpts), C.POINTER(RhsStats)]),
     "mds_timing_enable": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
@@ -314,6 +318,27 @@ class Context:
                                C.c_void_p(_ptr(x)), nrhs, C.byref(o), st)
         self._check(code)
         return code, [Stats(s.iterations, s.restarts, s.status, s.relres_est, s.relres_true) for s in st]
+
+    def solve_async(self, sys: "System", prec: Optional["Precond"], b=None, x=None, nrhs: int = 1, **opts):
+        """Start the solve on a library thread and return at once; collect it
+        with solve_wait.  b, x, sys and prec must stay alive until then (the
+        context keeps references)."""
+        o = solve_opts(**opts)
+        self._check(lib().mds_solve_async(self.h, sys.h, prec.h if prec is not None else None, C.c_void_p(_ptr(b)),
+                                          C.c_void_p(_ptr(x)), nrhs, C.byref(o)))
+        self._async = (sys, prec, b, x, nrhs * sys.n_inst)
+
+    def solve_done(self) -> bool:
+        return self._check(lib().mds_solve_done(self.h)) == 1
+
+    def solve_wait(self):
+        """Wait for the asynchronous solve.  Returns (status, [Stats]) as solve."""
+        count = self._async[4] if getattr(self, "_async", None) else 0
+        st = (RhsStats * max(count, 1))()
+        code = lib().mds_solve_wait(self.h, st, count)
+        self._async = None
+        self._check(code)
+        return code, [Stats(s.iterations, s.restarts, s.status, s.relres_est, s.relres_true) for s in st[:count]]
 
     def solve_noalloc(self, sys: "System", prec: Optional["Precond"], b=None, x=None, **opts):
         """FGMRES with the library's static workspace (device tensors only,
