@@ -22,6 +22,7 @@ def env():
 
 def make(torch, mdsolve, stream, contrast):
     ctx = mdsolve.Context(0, stream=stream.cuda_stream)
+    ctx._stream = stream  # keep the stream object with the context
     inst = inputs.random_segments_2d(n=256, n_seg=20, contrast=contrast)
     sys_ = ctx.assemble(inst)
     prec = ctx.setup(sys_, format="csr")
