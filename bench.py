@@ -541,6 +541,8 @@ def variants(ctx, insts, dev_arrays, N, flush):
         out[f"batch3d_256inst_x4rhs_{prec}"] = {
             "solves_per_s": total_solves / t, "s_per_step": t, "solves": total_solves,
             "iterations_min_mean_max": [min(its), float(np.mean(its)), max(its)], "N_packed": n, "precision": desc}
+    # kernel classes of the mixed-precision batch (finest level, 4 interleaved columns)
+    out["batch3d_256inst_x4rhs_bf16"]["classes"] = class_rates(ctx, lambda: batched("bf16"))
     return out
 
 
