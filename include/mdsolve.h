@@ -210,8 +210,6 @@ int mds_system_view(mds_system sys, mds_csr blocks[5], const double **b);
 #define MDS_FORMAT_AUTO 0       /* timed choice per level (autotuner) */
 #define MDS_FORMAT_CSR 1
 #define MDS_FORMAT_SELL 2       /* sliced ELLPACK, slice height sell_c, sort window sell_sigma */
-#define MDS_FORMAT_PIPE 3       /* CSR, one thread per row over a resident grid, the next rows' entries
-                                   loaded while the current row's gathers are in flight */
 #define MDS_BLOCK_LOWER 0       /* M_L, Eq. (8), Algorithm 1 */
 #define MDS_BLOCK_DIAG 1        /* block diagonal B_D with Q blocks */
 #define MDS_BLOCK_UPPER 2       /* block upper triangular B_U with Q blocks */

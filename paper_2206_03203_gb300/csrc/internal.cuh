@@ -82,8 +82,7 @@ enum : int {
 
 // Storage of a V-cycle level: value type and sparse format.
 enum : int { VT_F64 = 0, VT_F32 = 1, VT_BF16 = 2, VT_F16 = 3 };
-enum : int { FMT_CSR = 0, FMT_SELL = 1, FMT_PIPE = 2 };  // FMT_PIPE: CSR, pipelined thread per row
-constexpr int64_t PIPE_MIN_ROWS = 262144;  // the autotuner tries FMT_PIPE from this level size on
+enum : int { FMT_CSR = 0, FMT_SELL = 1 };
 
 struct TuneChoice {
     int fmt, G, C, sigma;

@@ -211,12 +211,10 @@ template <class XT> static void autotune_level(Ctx &c, Level &L) {
     auto it = c.tune_cache.find(key);
     if (it != c.tune_cache.end()) {
         const TuneChoice &t = it->second;
-        if (t.fmt == FMT_SELL) {
+        if (t.fmt == FMT_SELL)
             build_sell_vt(c, L, t.C, t.sigma);
-        } else {
-            L.fmt = t.fmt;
+        else
             L.G = t.G;
-        }
         return;
     }
     // defined inputs for the timing runs
@@ -239,17 +237,6 @@ template <class XT> static void autotune_level(Ctx &c, Level &L) {
             best = TuneChoice{FMT_CSR, G, 32, 1};
         }
     }
-    // the pipelined thread-per-row form, for levels of more than one wave
-    if (L.A.nrow >= PIPE_MIN_ROWS) {
-        L.fmt = FMT_PIPE;
-        L.G = 1;
-        float t = time_level(c, L);
-        if (t < tbest) {
-            tbest = t;
-            best = TuneChoice{FMT_PIPE, 1, 32, 1};
-        }
-        L.fmt = FMT_CSR;
-    }
     const int cand[][2] = {{32, 1}, {32, 256}, {16, 1}};
     for (auto &cs : cand) {
         build_sell_vt(c, L, cs[0], cs[1]);
@@ -261,11 +248,8 @@ template <class XT> static void autotune_level(Ctx &c, Level &L) {
         drop_sell(L);
     }
     c.tune_cache[key] = best;
-    L.G = best.fmt != FMT_SELL ? best.G : default_g(L);
-    if (best.fmt == FMT_SELL)
-        build_sell_vt(c, L, best.C, best.sigma);
-    else
-        L.fmt = best.fmt;
+    L.G = best.fmt == FMT_CSR ? best.G : default_g(L);
+    if (best.fmt == FMT_SELL) build_sell_vt(c, L, best.C, best.sigma);
 }
 
 void level_storage(Ctx &c, Hierarchy &h, const mds_setup_opts &o) {
@@ -307,9 +291,6 @@ void level_storage(Ctx &c, Hierarchy &h, const mds_setup_opts &o) {
         }
         if (o.format == MDS_FORMAT_SELL) {
             build_sell_vt(c, L, o.sell_c, o.sell_sigma);
-        } else if (o.format == MDS_FORMAT_PIPE) {
-            L.fmt = FMT_PIPE;
-            L.G = 1;
         } else if (o.format == MDS_FORMAT_AUTO && n >= 20000) {
             if (h.prec == 64)
                 autotune_level<double>(c, L);

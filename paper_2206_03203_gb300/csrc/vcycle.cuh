@@ -406,141 +406,6 @@ __global__ void k_sa_prolong(int64_t n, const int32_t *__restrict__ rp, const in
 
 // ---------------------------------------------------------------- host dispatch
 
-// Pipelined one-thread-per-row CSR form for levels of several waves: a grid
-// of resident blocks strides over the rows, and each thread keeps three rows
-// in flight.  While the neighbour gathers of row r run, the matrix entries of
-// row r + T (up to PIPE_E of them, in registers) and the row pointers of row
-// r + 2T (T = threads in the grid) are already being loaded, so the chain
-// row pointer -> entries -> gathers costs one memory latency per row instead
-// of three.  Entries past PIPE_E are read in the row's own loop.  Per row the
-// arithmetic is that of k_level<1, ...> in the same order, so the results
-// agree to the bit.
-constexpr int PIPE_E = 8;
-template <class VT, class XT, int K, int NR>
-__global__ void __launch_bounds__(256) k_level_pipe(LvlMat<VT> A, const XT *__restrict__ dinv,
-                                                    const XT *__restrict__ b, const XT *__restrict__ xin,
-                                                    const int32_t *__restrict__ agg, const XT *__restrict__ xc,
-                                                    XT *__restrict__ out) {
-    const int64_t T = (int64_t)gridDim.x * blockDim.x;
-    int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    // current row: entries in (ca, cj), count ccnt, first entry cp0
-    VT ca[PIPE_E], na[PIPE_E];
-    int32_t cj[PIPE_E], nj[PIPE_E];
-    int32_t cp0 = 0, ccnt = 0, np0 = 0, ncnt = 0;
-    // matrix data is fixed while solving: the first rows load before the dependency wait
-    if (row < A.n) {
-        cp0 = A.rp[row];
-        ccnt = A.rp[row + 1] - cp0;
-    }
-#pragma unroll
-    for (int k = 0; k < PIPE_E; k++)
-        if (k < ccnt) {
-            ca[k] = ld_stream(A.v + cp0 + k);
-            cj[k] = ld_stream(A.ci + cp0 + k);
-        }
-    if (row + T < A.n) {
-        np0 = A.rp[row + T];
-        ncnt = A.rp[row + T + 1] - np0;
-    }
-    mds_pdl_wait();
-    mds_pdl_trigger();
-    Nb<XT, NR, K> f{dinv, b, xin, xc, agg};
-    for (; row < A.n; row += T) {
-        // entries of the next row, row pointers of the one after
-#pragma unroll
-        for (int k = 0; k < PIPE_E; k++)
-            if (k < ncnt) {
-                na[k] = ld_stream(A.v + np0 + k);
-                nj[k] = ld_stream(A.ci + np0 + k);
-            }
-        int32_t qp0 = 0, qcnt = 0;
-        if (row + 2 * T < A.n) {
-            qp0 = A.rp[row + 2 * T];
-            qcnt = A.rp[row + 2 * T + 1] - qp0;
-        }
-        // this row
-        const int64_t o = row;
-        XT sc = (XT)1, d = (XT)0;
-        int32_t ag = -1;
-        if (A.rscale) sc = (XT)A.rscale[o];
-        if (K == VK_POST || K == VK_SMOOTH) d = dinv[o];
-        if (K == VK_POST && agg) ag = agg[o];
-        Vec<XT, NR> bo = ldv<XT, NR>(b, o), yo;
-#pragma unroll
-        for (int c = 0; c < NR; c++) yo.v[c] = (XT)0;
-        if (K == VK_SMOOTH) yo = ldv<XT, NR>(xin, o);
-        if (K == VK_POST && ag >= 0) yo = ldv<XT, NR>(xc, ag);
-        XT s[NR];
-#pragma unroll
-        for (int c = 0; c < NR; c++) s[c] = 0;
-#pragma unroll
-        for (int k = 0; k < PIPE_E; k++)
-            if (k < ccnt) {
-                XT a = cvt<XT>(ca[k]);
-                Vec<XT, NR> y = f(cj[k]);
-#pragma unroll
-                for (int c = 0; c < NR; c++) s[c] += a * y.v[c];
-            }
-        for (int k = PIPE_E; k < ccnt; k++) {
-            XT a = cvt<XT>(ld_stream(A.v + cp0 + k));
-            Vec<XT, NR> y = f(ld_stream(A.ci + cp0 + k));
-#pragma unroll
-            for (int c = 0; c < NR; c++) s[c] += a * y.v[c];
-        }
-        if (A.rscale) {
-#pragma unroll
-            for (int c = 0; c < NR; c++) s[c] *= sc;
-        }
-        Vec<XT, NR> res;
-        if (K == VK_RESID0 || K == VK_RESID) {
-#pragma unroll
-            for (int c = 0; c < NR; c++) res.v[c] = bo.v[c] - s[c];
-        } else {
-            Vec<XT, NR> y;
-            if (K == VK_POST) {
-#pragma unroll
-                for (int c = 0; c < NR; c++) y.v[c] = d * bo.v[c];
-                if (ag >= 0) {
-#pragma unroll
-                    for (int c = 0; c < NR; c++) y.v[c] += yo.v[c];
-                }
-            } else {
-                y = yo;
-            }
-#pragma unroll
-            for (int c = 0; c < NR; c++) res.v[c] = y.v[c] + d * (bo.v[c] - s[c]);
-        }
-        stv<XT, NR>(out, o, res);
-        // rotate the pipeline
-#pragma unroll
-        for (int k = 0; k < PIPE_E; k++) {
-            ca[k] = na[k];
-            cj[k] = nj[k];
-        }
-        cp0 = np0;
-        ccnt = ncnt;
-        np0 = qp0;
-        ncnt = qcnt;
-    }
-}
-
-// resident 256-thread blocks of k_level_pipe per SM, times the SM count
-template <class VT, class XT, int K, int NR> static unsigned pipe_grid(Ctx &c, int64_t n) {
-    static int per_sm = -1, sms = 0;
-    if (per_sm < 0) {
-        int dev = 0, v = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_level_pipe<VT, XT, K, NR>, 256, 0) != cudaSuccess ||
-            v < 1)
-            v = 1;
-        cudaGetLastError();
-        per_sm = v;
-    }
-    int64_t want = (n + 255) / 256, cap = (int64_t)per_sm * (sms > 0 ? sms : 1);
-    return (unsigned)(want < cap ? want : cap);
-}
-
 template <class VT> static LvlMat<VT> lvl_view(const Level &L) {
     LvlMat<VT> m{};
     m.n = L.A.nrow;
@@ -573,11 +438,6 @@ static void launch_level_pf(Ctx &c, const Level &L, const XT *dinv, const XT *b,
                    (K == VK_SMOOTH ? xb * (double)n : 0.0);
     double flops = NR * (2.0 * L.A.nnz + (K == VK_RESID0 ? n : K == VK_POST ? 5.0 * n : K == VK_SMOOTH ? 3.0 * n : 0.0));
     int cls = !L.timed_level ? KC_NONE : (K == VK_RESID0 || K == VK_RESID) ? KC_VC_RESID : KC_VC_POST;
-    if (L.fmt == FMT_PIPE) {
-        MDS_LAUNCH_F(c, cls, bytes, flops, (k_level_pipe<VT, XT, K, NR>), (pipe_grid<VT, XT, K, NR>(c, n)), 256, 0, m,
-                     dinv, b, xin, agg, xc, out);
-        return;
-    }
     if (L.fmt == FMT_SELL) {
         int64_t rows = L.sell_nslice * L.sell_c;
         MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<0, VT, XT, K, NR, PF>), grid_for(rows, 256), 256, 0, m, dinv, b, xin,
@@ -619,9 +479,7 @@ template <class VT, class XT, int K, int NR>
 static void launch_level(Ctx &c, const Level &L, const XT *dinv, const XT *b, const XT *xin, const int32_t *agg,
                          const XT *xc, XT *out, int64_t nc) {
     int64_t threads = L.fmt == FMT_SELL ? L.sell_nslice * L.sell_c : L.A.nrow * (int64_t)L.G;
-    if (L.fmt == FMT_PIPE)
-        launch_level_pf<VT, XT, K, NR, 0>(c, L, dinv, b, xin, agg, xc, out, nc);
-    else if ((threads + 255) / 256 <= PREFETCH_MAX_BLOCKS)
+    if ((threads + 255) / 256 <= PREFETCH_MAX_BLOCKS)
         launch_level_pf<VT, XT, K, NR, PREFETCH>(c, L, dinv, b, xin, agg, xc, out, nc);
     else
         launch_level_pf<VT, XT, K, NR, 0>(c, L, dinv, b, xin, agg, xc, out, nc);

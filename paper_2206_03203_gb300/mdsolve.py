@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(PKG, "_build", "libmdsolve.so")
 MDS_OK = 0
 MDS_WARN_NOT_CONVERGED = 1
 PREC = {"fp64": 64, "fp32": 32, "bf16": 16, "fp16": 17}
-FORMAT = {"auto": 0, "csr": 1, "sell": 2, "pipe": 3}
+FORMAT = {"auto": 0, "csr": 1, "sell": 2}
 PROLONG = {"piecewise": 0, "smoothed": 1}
 SMOOTHER = {"l1jacobi": 0, "chebyshev": 1}
 KIND = {"lower": 0, "diag": 1, "upper": 2}

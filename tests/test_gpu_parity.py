@@ -423,10 +423,6 @@ OPTION_CASES = [
     dict(precision="bf16", format="sell", sell_sigma=256),
     dict(precision="fp32", format="auto"),
     dict(precision="fp64", format="auto", smoother="chebyshev"),
-    dict(precision="fp64", format="pipe"),
-    dict(precision="fp32", format="pipe"),
-    dict(precision="bf16", format="pipe"),
-    dict(precision="fp32", format="pipe", smoother="chebyshev", sweeps=2),
     dict(precision="fp64", smoother="chebyshev", cheb_degree=1),
     dict(precision="fp64", smoother="chebyshev", cheb_degree=3),
     dict(precision="fp32", smoother="chebyshev", cheb_degree=4, sweeps=2),
@@ -466,8 +462,7 @@ def test_vcycle_options_parity(ctx, oracle_mod, torch_mod, case, cfg):
 @pytest.mark.parametrize("cfg", [dict(precision="bf16"), dict(precision="fp16"), dict(smoother="chebyshev"),
                                  dict(precision="fp32", smoother="chebyshev", format="sell"),
                                  dict(precision="fp32", sweeps=2, format="auto"),
-                                 dict(smoother="chebyshev", cheb_degree=3), dict(format="pipe"),
-                                 dict(precision="fp32", format="pipe")],
+                                 dict(smoother="chebyshev", cheb_degree=3)],
                          ids=lambda c: "-".join(f"{k}={v}" for k, v in c.items()))
 @pytest.mark.parametrize("case", ["seg2d-96", "planes3d-16", "rects3d-18"])
 def test_solve_options_parity(ctx, oracle_mod, torch_mod, case, cfg):
@@ -751,23 +746,3 @@ def test_smoothed_batched_multi_rhs(ctx, torch_mod):
     code2, st2 = ctx.solve(sys_, prec, None, xs, nrhs=4, batched=0)
     assert code == 0 and code2 == 0
     assert all(abs(a.iterations - b.iterations) <= 1 for a, b in zip(st, st2))
-
-
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16"])
-def test_pipelined_form_multi_rhs(ctx, oracle_mod, torch_mod, precision):
-    """The pipelined thread-per-row level form on interleaved columns (4
-    right-hand sides in lockstep): every column meets the stopping rule and
-    matches the oracle's iteration count."""
-    inst = inputs.random_rects_3d(20, 7, 3, 5, nrhs=4, random_dirichlet=True)
-    sys_ = ctx.assemble(inst)
-    prec = ctx.setup(sys_, precision=precision, format="pipe")
-    x = np.zeros(4 * sys_.N)
-    code, st = ctx.solve(sys_, prec, None, x, nrhs=4)
-    assert code == 0
-    Ao, bo = oracle_mod.assemble(inst)
-    M = oracle_mod.ML(Ao, inst.n_m, prec=PREC_CODE[precision])
-    for k in range(4):
-        xk = x[k * sys_.N:(k + 1) * sys_.N]
-        assert np.linalg.norm(bo[k] - Ao @ xk) / np.linalg.norm(bo[k]) <= 1.01e-8
-        r = oracle_mod.fgmres(Ao, bo[k], M)
-        assert abs(st[k].iterations - r.iterations) <= 1, (k, st[k].iterations, r.iterations)
