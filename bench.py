@@ -168,13 +168,25 @@ def run_gpu(args):
     sopt = dict(rtol=1e-8, max_iters=5000, restart=30)
     stats_last = []
 
+    phase_ev = []  # per member of a timed step: events before assembly, after assembly, set-up, solve
+
     def step(collect=False):
         its = []
         for k, inst in enumerate(insts):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if collect else None
+            if ev:
+                ev[0].record()
             s = ctx.assemble(inst, device_arrays=dev_arrays[k])
+            if ev:
+                ev[1].record()
             p = ctx.setup(s, precision="fp64", format="auto")
+            if ev:
+                ev[2].record()
             xs[k].zero_()
             code, st = ctx.solve(s, p, None, xs[k], **sopt)
+            if ev:
+                ev[3].record()
+                phase_ev.append(ev)
             if code != 0:
                 raise RuntimeError(f"solve failed for contrast {inputs.CONTRASTS[k]}: {st[0]}")
             its.append(st[0].iterations)
@@ -235,6 +247,7 @@ def run_gpu(args):
     clocks.start()
     t_total = 0.0
     iters = []
+    step_s = []
     for s_ in range(args.steps):
         flush.fill_(float(s_))  # L2 flush between steps (256 MB > 129 MB L2)
         torch.cuda.synchronize()
@@ -243,7 +256,16 @@ def run_gpu(args):
         iters = step(collect=(s_ == args.steps - 1))
         e1.record()
         torch.cuda.synchronize()
-        t_total += e0.elapsed_time(e1) / 1e3
+        step_s.append(e0.elapsed_time(e1) / 1e3)
+        t_total += step_s[-1]
+    # phases of the last timed step (events on the library's stream)
+    ph = np.zeros(3)
+    for ev in phase_ev:
+        ph += (ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3]))
+    phases = {"assemble_ms": ph[0], "setup_ms": ph[1], "solve_ms": ph[2],
+              "solve_only_solves_per_s": len(insts) / (ph[2] / 1e3) if ph[2] > 0 else None,
+              "dof_iter_per_s_solve_only": (sum(n * i for n, i in zip(N, iters)) / (ph[2] / 1e3)
+                                            if ph[2] > 0 else None)}
     launches = ctx.launch_count()
     kl_all = ctx.timing_query(dominant)[0]
     kl, kms, kbytes, kflops = ctx.timing_sampled(dominant)
@@ -329,6 +351,9 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}", "N_per_solve": N[0],
                    "iterations_per_contrast": iters},
         "dof_iter_per_s": dof_iter,
+        "step_s": {"median": float(np.median(step_s)), "min": float(np.min(step_s)), "all": step_s},
+        "phases_last_step": phases,
+        "vcycle": vcycle_rate(ctx, insts[-1], dev_arrays[-1], flush),
         "accuracy": accuracy,
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -386,6 +411,55 @@ def class_rates(ctx, fn, classes=("spmv", "vc_resid", "vc_post", "vc_restrict", 
             out[c] = {"avg_launch_us": round(ms_t / n_t * 1e3, 3), "algorithmic_bytes_per_launch": by_t / n_t,
                       "hbm_gbs": round(gbs, 1), "hbm_frac_of_measured": round(gbs / peak, 4),
                       "fp64_tflops": round(fl_t / (ms_t / 1e3) / 1e12, 4)}
+    return out
+
+
+def vcycle_rate(ctx, inst, dev, flush, reps: int = 20):
+    """One application of M_L (Algorithm 1: V-cycle on S~, A_fm SpMV, V-cycle
+    on A_ff) on the contrast-1e4 member, FP64 and FP32 hierarchies: median
+    event time over `reps` applications with L2 flushed before each, and the
+    algorithmic bytes of the application -- per non-dense level the matrix
+    read twice (residual and post-smoothing), about eight vector passes and
+    the aggregate map, the dense coarsest inverse once, and the A_fm SpMV."""
+    import torch
+    peak, _ = measured_peaks()
+    s = ctx.assemble(inst, device_arrays=dev)
+    n_m, n_f, nnz_fm = s.n_m, s.n_f, s.nnz[2]
+    out = {}
+    for prec, bv, bx in (("fp64", 8, 8), ("fp32", 4, 4)):
+        p = ctx.setup(s, precision=prec, format="auto")
+        total = 0.0
+        for blk in (0, 1):
+            info = p.info(blk)
+            last = len(info["n"]) - 1
+            for l, (n_l, z_l) in enumerate(zip(info["n"], info["nnz"])):
+                if l == last and info["dense"]:
+                    total += 8.0 * n_l * n_l + 2 * bx * n_l
+                elif l == last and info.get("diagonal"):
+                    total += 3 * bx * n_l
+                else:
+                    total += 2 * ((bv + 4) * z_l + 4 * (n_l + 1)) + 8 * bx * n_l + 4 * n_l
+        total += 12.0 * nnz_fm + 4.0 * (n_f + 1) + 8.0 * (n_m + 2 * n_f)
+        r = torch.randn(s.N, dtype=torch.float64, device="cuda")
+        z = torch.zeros_like(r)
+        for _ in range(3):
+            ctx.precond_apply(p, r, z)
+        ts = []
+        for _ in range(reps):
+            flush.fill_(0.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.precond_apply(p, r, z)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        t = float(np.median(ts))
+        out[prec] = {"us_per_application": t * 1e6, "algorithmic_bytes": total, "hbm_gbs": total / t / 1e9,
+                     "hbm_frac_of_measured": total / t / 1e9 / peak,
+                     "levels": [p.info(0)["n"], p.info(1)["n"]]}
+        p.close()
+    s.close()
     return out
 
 
@@ -541,28 +615,76 @@ def variants(ctx, insts, dev_arrays, N, flush):
         out[f"batch3d_256inst_x4rhs_{prec}"] = {
             "solves_per_s": total_solves / t, "s_per_step": t, "solves": total_solves,
             "iterations_min_mean_max": [min(its), float(np.mean(its)), max(its)], "N_packed": n, "precision": desc}
+    # the same batch solved instance by instance (4 columns in lockstep each)
+    def per_instance():
+        its = []
+        for inst in batch:
+            s = ctx.assemble(inst)
+            p = ctx.setup(s, precision="bf16", format="auto")
+            x = torch.zeros(s.N * 4, dtype=torch.float64, device="cuda")
+            code, st = ctx.solve(s, p, None, x, nrhs=4, rtol=1e-8, max_iters=5000)
+            assert code == 0
+            its += [q.iterations for q in st]
+            p.close()
+            s.close()
+        return its
+    t, its = _timed(per_instance, flush, warmup=0)
+    t, total_solves = sharding.reduce_over_ranks(t, len(its))
+    out["batch3d_256inst_x4rhs_bf16_per_instance"] = {
+        "solves_per_s": total_solves / t, "s_per_step": t, "solves": total_solves,
+        "iterations_min_mean_max": [min(its), float(np.mean(its)), max(its)],
+        "precision": "as the packed bf16 batch, one instance (4 columns) at a time"}
     # kernel classes of the mixed-precision batch (finest level, 4 interleaved columns)
     out["batch3d_256inst_x4rhs_bf16"]["classes"] = class_rates(ctx, lambda: batched("bf16"))
     return out
 
 
-def cpu_baseline(samples: int = 1):
-    """The oracle (plain sequential FP64 C) on a bounded sample of the same
-    workload: the contrast-1 solve of the sweep, assembled, set up and solved
-    to 1e-8 (the cheapest of the nine; about 20-30 s of CPU work)."""
+def _oracle_sample():
+    """One oracle solve of the contrast-1 member (assemble, M_L set-up, FGMRES
+    to 1e-8); returns the seconds of each phase and the iteration count."""
     import oracle
     from paper_2206_03203_gb300 import inputs
     oracle.build()
     inst = inputs.random_segments_2d(contrast=1.0)
     t0 = time.perf_counter()
+    A, b = oracle.assemble(inst)
+    t1 = time.perf_counter()
+    M = oracle.ML(A, inst.n_m)
+    t2 = time.perf_counter()
+    res = oracle.fgmres(A, b[0], M, rtol=1e-8, maxit=5000)
+    t3 = time.perf_counter()
+    assert res.converged
+    return t1 - t0, t2 - t1, t3 - t2, res.iterations
+
+
+def cpu_baseline(samples: int = 1, all_cores: bool = True):
+    """The oracle (plain sequential FP64 C) on a bounded sample of the same
+    workload: the contrast-1 solve of the sweep, assembled, set up and solved
+    to 1e-8 (the cheapest of the nine; about 10-30 s of CPU work), on one
+    core; then the same sample as one process per host core at once (the
+    host's throughput with the oracle as it stands)."""
+    phases = np.zeros(3)
+    t0 = time.perf_counter()
     for _ in range(samples):
-        res, A, b, M = oracle.solve(inst, maxit=5000)
-        assert res.converged
+        a, s_, v, its = _oracle_sample()
+        phases += (a, s_, v)
     dt = time.perf_counter() - t0
-    return {"value": samples / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{samples} solve(s) of the contrast-1 member of the sweep (1024x1024, "
-                      f"{res.iterations} FGMRES iterations), assemble + set-up + solve, single thread",
-            "cpu": platform.processor() or platform.machine(), "nproc": os.cpu_count()}
+    out = {"value": samples / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{samples} solve(s) of the contrast-1 member of the sweep (1024x1024, "
+                     f"{its} FGMRES iterations), assemble + set-up + solve, single thread",
+           "phases_s": {"assemble": phases[0] / samples, "setup": phases[1] / samples,
+                        "solve": phases[2] / samples},
+           "cpu": platform.processor() or platform.machine(), "nproc": os.cpu_count()}
+    if all_cores:
+        import multiprocessing as mp
+        k = os.cpu_count() or 1
+        with mp.get_context("spawn").Pool(k) as pool:
+            t0 = time.perf_counter()
+            rs = pool.starmap(_oracle_sample, [()] * k)
+            dt = time.perf_counter() - t0
+        out["all_cores"] = {"value": k / dt, "unit": UNIT, "cores": k,
+                            "sample": f"{k} concurrent single-threaded oracle processes, one contrast-1 solve each"}
+    return out
 
 
 def run_reference(args):
