@@ -322,6 +322,31 @@ int mds_solve_opts_default(mds_solve_opts *o);
 int mds_solve(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, double *x,
               int nrhs, const mds_solve_opts *opts, mds_rhs_stats *stats);
 
+/* ---- solver tuner ----
+ * The storage autotuner of mds_setup times kernels; the options that also
+ * change convergence (smoother, sweeps, Chebyshev degree, level precision)
+ * can only be judged by time to solution.  mds_tune runs, for each
+ * candidate, mds_setup with the base options and the candidate's four
+ * fields, then mds_solve of b (NULL: the assembled first right-hand side)
+ * from x0 = 0 with the given solve options, and records the wall times of
+ * both and the outcome.  *best = the converged candidate with the least
+ * set-up + solve time (-1 if none converged: MDS_WARN_NOT_CONVERGED).  The
+ * trial solution lives in a device buffer of the call; no preconditioner
+ * is kept.  Meant for workloads that solve many systems alike (a parameter
+ * sweep, many right-hand sides): tune once on a representative one. */
+typedef struct {
+    int smoother;       /* in: MDS_SMOOTHER_* */
+    int sweeps;         /* in: 1..8 */
+    int cheb_degree;    /* in: 1..8 */
+    int precision;      /* in: MDS_PREC_* */
+    int status;         /* out: set-up error, or the solve's status */
+    int iterations;     /* out */
+    double setup_ms;    /* out: wall time of mds_setup */
+    double solve_ms;    /* out: wall time of mds_solve */
+} mds_tune_candidate;
+int mds_tune(mds_ctx ctx, mds_system sys, const mds_setup_opts *base, const mds_solve_opts *sopts,
+             const double *b, mds_tune_candidate *cands, int n_cands, int *best);
+
 /* The same solve without blocking the calling thread: the solve's host
  * control loop runs on a library thread and mds_solve_async returns at once
  * (MDS_OK when started, or an error for invalid arguments or an uncollected

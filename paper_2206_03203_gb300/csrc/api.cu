@@ -1,5 +1,6 @@
 // The C ABI of libmdsolve (include/mdsolve.h): contexts, memory, systems,
 // preconditioner set-up, Algorithm 1, solves and timing.
+#include <chrono>
 #include <cmath>
 #include <cstdlib>
 #include <cstddef>
@@ -812,6 +813,65 @@ int mds_solve_wait(mds_ctx ctx, mds_rhs_stats *stats, int count) {
     if (stats)
         for (int q = 0; q < count && q < (int)A.stats.size(); q++) stats[q] = A.stats[q];
     return A.status;
+}
+
+int mds_tune(mds_ctx ctx, mds_system sys, const mds_setup_opts *base, const mds_solve_opts *sopts, const double *b,
+             mds_tune_candidate *cands, int n_cands, int *best) {
+    if (!ctx || !sys || !cands || n_cands < 1 || !best) return MDS_ERR_INVALID;
+    Ctx *c = &ctx->c;
+    async_join(c);
+    *best = -1;
+    mds_setup_opts o0;
+    mds_setup_opts_default(&o0);
+    if (base) o0 = *base;
+    mds_solve_opts so;
+    mds_solve_opts_default(&so);
+    if (sopts) so = *sopts;
+    so.use_precond = 1;
+    const int64_t n = sys->n_m + sys->n_f;
+    API_BEGIN
+    MDS_CUDA(cudaSetDevice(c->device));
+    Buf xb(c, sizeof(double) * (size_t)(n > 0 ? n : 1));  // trial solution (the context's allocator)
+    double *x = xb.as<double>();
+    using clk = std::chrono::steady_clock;
+    double tbest = 0.0;
+    for (int q = 0; q < n_cands; q++) {
+        mds_tune_candidate &k = cands[q];
+        mds_setup_opts o = o0;
+        o.smoother = k.smoother;
+        o.sweeps = k.sweeps;
+        o.cheb_degree = k.cheb_degree;
+        o.precision = k.precision;
+        k.iterations = 0;
+        k.setup_ms = k.solve_ms = 0.0;
+        mds_precond p = nullptr;
+        cudaStreamSynchronize(c->stream);
+        auto t0 = clk::now();
+        k.status = mds_setup(ctx, sys, &o, &p);
+        auto t1 = clk::now();
+        k.setup_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        if (k.status < 0) continue;
+        mds_rhs_stats st{};
+        cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, c->stream);
+        cudaStreamSynchronize(c->stream);
+        t0 = clk::now();
+        int code = mds_solve(ctx, sys, p, b, x, 1, &so, &st);
+        t1 = clk::now();
+        k.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        k.status = code < 0 ? code : st.status;
+        k.iterations = st.iterations;
+        mds_precond_destroy(p);
+        double t = k.setup_ms + k.solve_ms;
+        if (k.status == MDS_OK && (*best < 0 || t < tbest)) {
+            *best = q;
+            tbest = t;
+        }
+    }
+    if (*best < 0) {
+        c->last_error = "mds_tune: no candidate converged";
+        return MDS_WARN_NOT_CONVERGED;
+    }
+    API_END(c)
 }
 
 int mds_solve_noalloc(mds_ctx ctx, mds_system sys, mds_precond prec, const double *b, double *x,

@@ -50,6 +50,17 @@ class Csr(C.Structure):
                 ("col", C.c_void_p), ("val", C.c_void_p)]
 
 
+class TuneCandidate(C.Structure):
+    _fields_ = [("smoother", C.c_int), ("sweeps", C.c_int), ("cheb_degree", C.c_int), ("precision", C.c_int),
+                ("status", C.c_int), ("iterations", C.c_int), ("setup_ms", C.c_double), ("solve_ms", C.c_double)]
+
+
+# smoother, sweeps, Chebyshev degree, precision
+TUNE_DEFAULT = [("l1jacobi", 1, 2, "fp64"), ("l1jacobi", 2, 2, "fp64"), ("chebyshev", 1, 2, "fp64"),
+                ("chebyshev", 1, 3, "fp64"), ("l1jacobi", 1, 2, "fp32"), ("l1jacobi", 2, 2, "fp32"),
+                ("chebyshev", 1, 2, "fp32"), ("chebyshev", 1, 3, "fp32")]
+
+
 class SetupOpts(C.Structure):
     _fields_ = [("theta", C.c_double), ("n_coarse", C.c_int64), ("max_levels", C.c_int),
                 ("stall_ratio", C.c_double), ("seed", C.c_uint64), ("smoother", C.c_int),
@@ -123,6 +134,8 @@ _SIGS = {
     "mds_solve_opts_default": (C.c_int, [C.POINTER(SolveOpts)]),
     "mds_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                             C.POINTER(SolveOpts), C.POINTER(RhsStats)]),
+    "mds_tune": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(SetupOpts), C.POINTER(SolveOpts), C.c_void_p,
+                           C.POINTER(TuneCandidate), C.c_int, C.POINTER(C.c_int)]),
     "mds_solve_async": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                   C.POINTER(SolveOpts)]),
     "mds_solve_done": (C.c_int, [C.c_void_p]),
@@ -318,6 +331,22 @@ class Context:
                                C.c_void_p(_ptr(x)), nrhs, C.byref(o), st)
         self._check(code)
         return code, [Stats(s.iterations, s.restarts, s.status, s.relres_est, s.relres_true) for s in st]
+
+    def tune(self, sys: "System", candidates=None, b=None, base: Optional[dict] = None, **solve_kw):
+        """Time set-up + solve for each (smoother, sweeps, cheb_degree,
+        precision) candidate; returns (best index or -1, [dict per
+        candidate])."""
+        cands = candidates or TUNE_DEFAULT
+        arr = (TuneCandidate * len(cands))()
+        for k, (sm, sw, dg, pr) in enumerate(cands):
+            arr[k] = TuneCandidate(SMOOTHER.get(sm, sm), sw, dg, PREC.get(pr, pr), 0, 0, 0.0, 0.0)
+        so = setup_opts(**(base or {}))
+        o = solve_opts(**solve_kw)
+        best = C.c_int(-1)
+        self._check(lib().mds_tune(self.h, sys.h, C.byref(so), C.byref(o), C.c_void_p(_ptr(b)), arr, len(cands),
+                                   C.byref(best)))
+        return best.value, [dict(candidate=cands[k], status=a.status, iterations=a.iterations,
+                                 setup_ms=a.setup_ms, solve_ms=a.solve_ms) for k, a in enumerate(arr)]
 
     def solve_async(self, sys: "System", prec: Optional["Precond"], b=None, x=None, nrhs: int = 1, **opts):
         """Start the solve on a library thread and return at once; collect it
