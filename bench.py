@@ -326,7 +326,7 @@ def run_gpu(args):
     e2e_steps = max(1, min(args.steps, 2))
     for inst in insts:
         h2d += inst.km.nbytes + inst.fc_axis.nbytes + inst.fc_pos.nbytes + inst.fc_kf.nbytes + inst.fc_a.nbytes \
-            + inst.pD_left.nbytes + inst.pD_right.nbytes
+            + inst.pD_left.nbytes + inst.pD_right.nbytes + 8 * (inst.n_m + inst.n_f)  # and the initial guess
         d2h += 8 * (inst.n_m + inst.n_f)
     e2e_value = len(insts) * e2e_steps / e2e_t * world
 
