@@ -603,18 +603,38 @@ def variants(ctx, insts, dev_arrays, N, flush):
     out["planes3d_128_kf1e4_fp64_flux_form_intersection_cells"] = {
         "solves_per_s": 1.0 / t, "s_per_step": t, "iterations": it, "N": nflux,
         "form": "paper's partition: pressures of all cells and 3,456 intersection cells; interface fluxes"}
-    for prec in ("fp64", "fp32"):
-        def one(prec=prec):
-            s = ctx.assemble(p3)
-            p = ctx.setup(s, precision=prec, format="auto")
-            x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
-            code, st = ctx.solve(s, p, None, x, rtol=1e-8, max_iters=5000)
-            p.close()
-            s.close()
-            return st[0].iterations
-        t, it = _timed(one, flush)
-        out[f"planes3d_128_kf1e4_{prec}"] = {"solves_per_s": 1.0 / t, "s_per_step": t, "iterations": it,
-                                             "N": p3.n_m + p3.n_f}
+    for kf, tag in ((1e-4, "kf1e-4"), (1.0, "kf1"), (1e4, "kf1e4")):
+        pk = p3 if kf == 1e4 else inputs.planes_3d(128, kf=kf)
+        for prec in ("fp64", "fp32"):
+            def one(prec=prec, pk=pk):
+                s = ctx.assemble(pk)
+                p = ctx.setup(s, precision=prec, format="auto")
+                x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+                code, st = ctx.solve(s, p, None, x, rtol=1e-8, max_iters=5000)
+                p.close()
+                s.close()
+                return st[0].iterations
+            t, it = _timed(one, flush)
+            out[f"planes3d_128_{tag}_{prec}"] = {"solves_per_s": 1.0 / t, "s_per_step": t, "iterations": it,
+                                                 "N": pk.n_m + pk.n_f}
+    # 256^3 with 30 rectangles, 8 random-Dirichlet right-hand sides in lockstep,
+    # FP32 finest level and FP16 row-scaled coarse levels under FP64 FGMRES
+    big = inputs.large_3d(256)
+
+    def one_big():
+        s = ctx.assemble(big)
+        p = ctx.setup(s, precision="fp16", format="auto")
+        x = torch.zeros(s.N * 8, dtype=torch.float64, device="cuda")
+        code, st = ctx.solve(s, p, None, x, nrhs=8, rtol=1e-8, max_iters=5000)
+        n = s.N
+        p.close()
+        s.close()
+        return [q.iterations for q in st], n
+    t, (its, nbig) = _timed(one_big, flush, warmup=1)
+    out["large3d_256_30rects_x8rhs_fp16"] = {
+        "solves_per_s": 8.0 / t, "s_per_step": t, "iterations": its, "N": nbig,
+        "dof_iter_per_s": nbig * sum(its) / t,
+        "precision": "FP32 finest level, FP16 row-scaled coarse levels, FP64 FGMRES; 8 columns in lockstep"}
     batch = inputs.batch_3d(256)
     world = rank_info()[2]
     if world > 1:
