@@ -240,6 +240,9 @@ static void ctx_release(mds_ctx ctx) {
     cudaFree(c.d_err);
     cudaFreeHost(c.h_pin);
     if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
+    if (c.side_stream) cudaStreamDestroy(c.side_stream);
+    if (c.ev_fork) cudaEventDestroy(c.ev_fork);
+    if (c.ev_join) cudaEventDestroy(c.ev_join);
     delete ctx;
 }
 
@@ -570,6 +573,32 @@ void precond_apply(mds_precond p, const double *r, double *z, int nr) {
         vcycle_f64(c, HF, rf, zf, nr);
         spmv_sub_f64(c, Amf, rm, zf, p->tf64.as<double>(), nr);
         vcycle_f64(c, HS, p->tf64.as<double>(), zm, nr);
+        return;
+    }
+    if (kind == MDS_BLOCK_DIAG && p->has_f) {
+        // B_D: the two V-cycles are independent.  Q_ff runs on the side
+        // stream while Q_mm runs on the main stream (fork and join by events,
+        // which a CUDA graph capture turns into parallel branches).
+        if (!c.side_stream) {
+            MDS_CUDA(cudaStreamCreateWithFlags(&c.side_stream, cudaStreamNonBlocking));
+            MDS_CUDA(cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming));
+            MDS_CUDA(cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming));
+        }
+        MDS_CUDA(cudaEventRecord(c.ev_fork, c.stream));
+        MDS_CUDA(cudaStreamWaitEvent(c.side_stream, c.ev_fork, 0));
+        cudaStream_t main = c.stream;
+        c.stream = c.side_stream;
+        try {
+            vcycle_f64(c, HF, rf, zf, nr);
+            if (p->ff_negative) scale_f64(c, zf, -1.0, nf * nr);
+            MDS_CUDA(cudaEventRecord(c.ev_join, c.stream));
+        } catch (...) {
+            c.stream = main;
+            throw;
+        }
+        c.stream = main;
+        vcycle_f64(c, HS, rm, zm, nr);
+        MDS_CUDA(cudaStreamWaitEvent(c.stream, c.ev_join, 0));
         return;
     }
     // step 1: z_m = Q_mm r_m

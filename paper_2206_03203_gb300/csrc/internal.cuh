@@ -167,6 +167,10 @@ struct Ctx {
     int dependents = 0;           // live systems and preconditioners made on this context
     bool destroy_requested = false;
     cudaStream_t cap_stream = nullptr;
+    // second stream for work that runs beside the main stream (the two
+    // independent V-cycles of the block-diagonal preconditioner)
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool pdl = true;              // launch with programmatic stream serialisation
     bool setup_phase = false;     // set-up writes level data: launch in plain stream order
     // autotuner choices by (rows, nonzeros, value type)
