@@ -96,7 +96,8 @@ const char *mds_last_error(mds_ctx ctx);
  * (index y + n z) and right-hand side; other boundary faces are no-flow.
  * Transmissibilities (two-point flux, Eq. (1)-(3)):
  *   matrix-matrix      |F| / (h/(2 k_i) + h/(2 k_j))
- *   matrix-fracture    |F| / (h/(2 k_i) + 1/kappa),  kappa = 2 k_f / a
+ *   matrix-fracture    |F| / (h/(2 k_i) + 1/kappa),  kappa = 2 k_n / a (k_n = k_f unless
+ *                      fc_kn is given: the paper's normal permeability, Eq. (2))
  *   fracture-fracture  t_i t_j / (t_i + t_j) for every pair of fracture cells
  *                      meeting at a vertex (2D) / edge (3D) e,
  *                      t = k_f a |e| / (h/2)
@@ -127,6 +128,7 @@ typedef struct {
     const double *pD_right;  /* [nrhs n^(dim-1)] */
     int on_device;
     int junction;            /* MDS_JUNCTION_* */
+    const double *fc_kn;     /* [n_f] normal permeability (kappa = 2 k_n / a), NULL: k_n = k_f */
 } mds_instance;
 
 /* Device CSR view.  row_ptr [nrow+1], col/val [nnz]. */

@@ -80,7 +80,7 @@ def lib():
             L.orc_assemble_ex.restype = P(_CSR)
             L.orc_assemble_ex.argtypes = [C.c_int, C.c_int, _f64p, C.c_int64, _i32p, _i32p, _f64p,
                                           _f64p, C.c_int, _f64p, _f64p, C.c_int, C.c_int, _i64p,
-                                          P(_f64p)]
+                                          P(_f64p), _f64p]
             L.orc_free.argtypes = [C.c_void_p]
             L.orc_split.argtypes = [P(_CSR), C.c_int64] + [P(P(_CSR))] * 4
             L.orc_schur.restype = P(_CSR)
@@ -164,6 +164,11 @@ class CSR:
             pass
 
 
+def _kn(inst):
+    kn = getattr(inst, "fc_kn", None)
+    return None if kn is None else np.ascontiguousarray(kn, dtype=np.float64)
+
+
 def assemble(inst, form="primal", junction=0, with_split=False):
     """Full system (scipy CSR) and right-hand sides [nrhs, N].  form="primal":
     [matrix cells; fracture cells] with the interface flux eliminated;
@@ -172,7 +177,7 @@ def assemble(inst, form="primal", junction=0, with_split=False):
     fracture cells are nodes joined by half transmissibilities (star-delta in
     the primal form, intersection cells with their own fluxes in the flux
     form).  with_split=True also returns the size of the first block."""
-    if junction or with_split:
+    if junction or with_split or _kn(inst) is not None:
         return _assemble_ex(inst, form, junction, with_split)
     L = lib()
     N = inst.n_m + inst.n_f if form == "primal" else inst.n_m + 3 * inst.n_f
@@ -198,11 +203,13 @@ def _assemble_ex(inst, form, junction, with_split):
         pos = np.zeros(3, dtype=np.int32)
     no = C.c_int64()
     bp = _f64p()
+    kn = _kn(inst)
+    kn_p = _p(kn, _f64p) if kn is not None else None
     ptr = L.orc_assemble_ex(inst.dim, inst.n, _p(inst.km, _f64p), inst.n_f,
                             _p(np.ascontiguousarray(inst.fc_axis, dtype=np.int32), _i32p), _p(pos, _i32p),
                             _p(np.ascontiguousarray(inst.fc_kf), _f64p), _p(np.ascontiguousarray(inst.fc_a), _f64p),
                             inst.nrhs, _p(inst.pD_left, _f64p), _p(inst.pD_right, _f64p), int(form == "flux"),
-                            int(junction), C.byref(no), C.byref(bp))
+                            int(junction), C.byref(no), C.byref(bp), kn_p)
     if not ptr:
         raise ValueError("oracle assembly rejected the instance")
     A = _from_csr(ptr)

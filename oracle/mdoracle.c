@@ -71,8 +71,9 @@ static int cmp_entry(const void *a, const void *b) {
  * each subdomain, Eq. (2)-(3) across each matrix-fracture interface), with
  * the interface flux eliminated into a matrix-fracture transmissibility:
  *   matrix-matrix     T = |F| / (h/(2k_i) + h/(2k_j))        (harmonic mean)
- *   matrix-fracture   T = |F| / (h/(2k_i) + 1/kappa), kappa = 2 k_f / a
- *                     (Eq. (2): interface law, kappa the normal permeability)
+ *   matrix-fracture   T = |F| / (h/(2k_i) + 1/kappa), kappa = 2 k_n / a
+ *                     (Eq. (2): interface law, kappa from the normal
+ *                     permeability k_n, which is k_f unless given)
  *   fracture-fracture half transmissibilities t = k_f a |e| / (h/2) at the
  *                     shared vertex (2D) / edge (3D) e, every pair of cells at
  *                     e linked by t_i t_j / (t_i + t_j)
@@ -182,7 +183,10 @@ static ocsr *assemble_impl(int dim, int n, const double *km, int64_t nf,
                            const int32_t *fc_axis, const int32_t *fc_pos,
                            const double *fc_kf, const double *fc_a, int nrhs,
                            const double *pD_left, const double *pD_right, double *b, int flux, int junction,
-                           int64_t *n_omega, double **b_out) {
+                           int64_t *n_omega, double **b_out, const double *fc_kn) {
+    /* normal permeability of each fracture cell (kappa = 2 k_n / a); the
+     * tangential one k_f when not given */
+    const double *kn = fc_kn ? fc_kn : fc_kf;
     if ((dim != 2 && dim != 3) || n < 1 || nrhs < 1 || junction < 0 || junction > 1) return NULL;
     const double h = 1.0 / (double)n;
     const double F = dim == 2 ? h : h * h;      /* face measure |F| */
@@ -301,7 +305,7 @@ static ocsr *assemble_impl(int dim, int n, const double *km, int64_t nf,
                         }
                         int32_t k = face_frac(&fm, d, fc);
                         if (k >= 0) {
-                            double kappa = (2.0 * fc_kf[k]) / fc_a[k];
+                            double kappa = (2.0 * kn[k]) / fc_a[k];
                             if (flux) {
                                 /* the interface flux column, side 0 when the
                                  * face is above this cell (s = 1) */
@@ -356,7 +360,7 @@ static ocsr *assemble_impl(int dim, int n, const double *km, int64_t nf,
         const int32_t *p = fc_pos + 3 * k;
         int64_t c[3] = {p[0], p[1], dim == 3 ? p[2] : 0};
         int64_t plane = c[d];
-        double kappa = (2.0 * fc_kf[k]) / fc_a[k];
+        double kappa = (2.0 * kn[k]) / fc_a[k];
         double tk = ((fc_kf[k] * fc_a[k]) * elen) / (0.5 * h);
         int cnt = 0;
         /* the two matrix cells on either side of the face */
@@ -464,7 +468,7 @@ static ocsr *assemble_impl(int dim, int n, const double *km, int64_t nf,
     for (int64_t k = 0; flux && k < nf; k++) {
         int d = fc_axis[k];
         const int32_t *p = fc_pos + 3 * k;
-        double kappa = (2.0 * fc_kf[k]) / fc_a[k];
+        double kappa = (2.0 * kn[k]) / fc_a[k];
         for (int s = 0; s < 2; s++) {
             int64_t mc[3] = {p[0], p[1], dim == 3 ? p[2] : 0};
             mc[d] = p[d] - 1 + s;
@@ -517,7 +521,7 @@ ocsr *orc_assemble(int dim, int n, const double *km, int64_t nf,
                    const double *fc_kf, const double *fc_a, int nrhs,
                    const double *pD_left, const double *pD_right, double *b) {
     return assemble_impl(dim, n, km, nf, fc_axis, fc_pos, fc_kf, fc_a, nrhs, pD_left, pD_right, b, 0, 0, NULL,
-                         NULL);
+                         NULL, NULL);
 }
 
 ocsr *orc_assemble_flux(int dim, int n, const double *km, int64_t nf,
@@ -525,17 +529,17 @@ ocsr *orc_assemble_flux(int dim, int n, const double *km, int64_t nf,
                         const double *fc_kf, const double *fc_a, int nrhs,
                         const double *pD_left, const double *pD_right, double *b) {
     return assemble_impl(dim, n, km, nf, fc_axis, fc_pos, fc_kf, fc_a, nrhs, pD_left, pD_right, b, 1, 0, NULL,
-                         NULL);
+                         NULL, NULL);
 }
 
 ocsr *orc_assemble_ex(int dim, int n, const double *km, int64_t nf,
                       const int32_t *fc_axis, const int32_t *fc_pos,
                       const double *fc_kf, const double *fc_a, int nrhs,
                       const double *pD_left, const double *pD_right, int flux, int junction,
-                      int64_t *n_omega, double **b_out) {
+                      int64_t *n_omega, double **b_out, const double *fc_kn) {
     *b_out = NULL;
     ocsr *A = assemble_impl(dim, n, km, nf, fc_axis, fc_pos, fc_kf, fc_a, nrhs, pD_left, pD_right, NULL, flux,
-                            junction, n_omega, b_out);
+                            junction, n_omega, b_out, fc_kn);
     if (!A) {
         free(*b_out);
         *b_out = NULL;

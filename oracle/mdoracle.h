@@ -55,12 +55,14 @@ ocsr *orc_assemble_flux(int dim, int n, const double *km, int64_t nf,
  * an intersection cell with interface fluxes in the flux form).  Allocates
  * the right-hand sides (*b_out, nrhs x NT, free with orc_free);
  * *n_omega = the size of the first block (matrix cells in the primal form,
- * all pressures in the flux form). */
+ * all pressures in the flux form).  fc_kn: the fractures' normal
+ * permeabilities (kappa = 2 k_n / a in the matrix-fracture coupling), NULL
+ * for k_n = k_f. */
 ocsr *orc_assemble_ex(int dim, int n, const double *km, int64_t nf,
                       const int32_t *fc_axis, const int32_t *fc_pos,
                       const double *fc_kf, const double *fc_a, int nrhs,
                       const double *pD_left, const double *pD_right, int flux, int junction,
-                      int64_t *n_omega, double **b_out);
+                      int64_t *n_omega, double **b_out, const double *fc_kn);
 void orc_free(void *p);
 
 /* Slice a full CSR at row/column n_m into its four blocks. */

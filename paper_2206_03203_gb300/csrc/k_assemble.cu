@@ -28,6 +28,7 @@ struct GridD {
     const int32_t *ioff;      // [nI+1] first flux of each intersection (relative to GF)
     const int32_t *imem;      // [4 nI] members of each intersection, ascending
     const int32_t *phi_int;   // [nIF] intersection of each flux
+    const double *kn;         // [nf] normal permeability (kappa = 2 kn / a)
 };
 
 __device__ __forceinline__ int64_t face_id(const GridD &g, int d, int64_t x, int64_t y, int64_t z) {
@@ -106,7 +107,7 @@ __device__ int matrix_entries(const GridD &g, const int32_t *map, const double *
             fc[d] = plane;
             int32_t k = frac_at(g, map, d, fc);
             if (k >= 0) {
-                double kappa = (2.0 * kf[k]) / ap[k];
+                double kappa = (2.0 * g.kn[k]) / ap[k];
                 // flux form: the interface flux of this face side (side 0 when
                 // the face is above the cell, s = 1)
                 if (g.flux) {
@@ -204,7 +205,7 @@ __device__ int fracture_entries(const GridD &g, const int32_t *map, const double
     int d = axis[k];
     int64_t c[3] = {pos[3 * k], pos[3 * k + 1], g.dim == 3 ? pos[3 * k + 2] : 0};
     int64_t plane = c[d];
-    double kappa = (2.0 * kf[k]) / ap[k];
+    double kappa = (2.0 * g.kn[k]) / ap[k];
     double tk = half_t(g, kf, ap, k);
     int cnt = 0;
     has[0] = has[1] = 0;
@@ -374,7 +375,7 @@ __global__ void k_fill(GridD g, const int32_t *__restrict__ map, const double *_
         int64_t mc[3] = {pos[3 * k], pos[3 * k + 1], g.dim == 3 ? pos[3 * k + 2] : 0};
         mc[d] = mc[d] - 1 + s;
         int64_t m = cell_id(g, mc);
-        double kappa = (2.0 * kf[k]) / ap[k];
+        double kappa = (2.0 * g.kn[k]) / ap[k];
         double t = g.F / (g.h / (2.0 * km[m]) + 1.0 / kappa);
         int64_t p = rp[i];
         ci[p] = (int32_t)m;
@@ -668,6 +669,8 @@ void assemble_instance(Ctx &c, const mds_instance &in, SystemData &out, bool flu
     const double *ap = stage(c, in.fc_a, (size_t)g.nf, dev, h4);
     const double *pL = stage(c, in.pD_left, (size_t)(in.nrhs * g.nb), dev, h5);
     const double *pR = stage(c, in.pD_right, (size_t)(in.nrhs * g.nb), dev, h6);
+    Buf h7;
+    g.kn = in.fc_kn ? stage(c, in.fc_kn, (size_t)g.nf, dev, h7) : kf;
 
     Buf map(&c, sizeof(int32_t) * (size_t)total);
     fill_i32(c, map.as<int32_t>(), -1, total);

@@ -84,6 +84,8 @@ class Instance:
     pD_left: np.ndarray
     pD_right: np.ndarray
     meta: dict = field(default_factory=dict)
+    # normal permeability per fracture cell (kappa = 2 k_n / a); None: k_n = k_f
+    fc_kn: Optional[np.ndarray] = None
 
     @property
     def n_m(self) -> int:
@@ -101,7 +103,7 @@ class Instance:
         """The same instance restricted to right-hand side ``k``."""
         return Instance(self.name, self.dim, self.n, self.km, self.fc_axis, self.fc_pos,
                         self.fc_kf, self.fc_a, self.pD_left[k:k + 1].copy(),
-                        self.pD_right[k:k + 1].copy(), dict(self.meta))
+                        self.pD_right[k:k + 1].copy(), dict(self.meta), self.fc_kn)
 
 
 @dataclass

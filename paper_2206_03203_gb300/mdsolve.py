@@ -39,7 +39,7 @@ class Instance(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int), ("km", C.c_void_p), ("n_f", C.c_int64),
                 ("fc_axis", C.c_void_p), ("fc_pos", C.c_void_p), ("fc_kf", C.c_void_p), ("fc_a", C.c_void_p),
                 ("nrhs", C.c_int), ("pD_left", C.c_void_p), ("pD_right", C.c_void_p), ("on_device", C.c_int),
-                ("junction", C.c_int)]
+                ("junction", C.c_int), ("fc_kn", C.c_void_p)]
 
 
 JUNCTION = {"pairwise": 0, "star": 1, 0: 0, 1: 1}
@@ -266,10 +266,12 @@ class Context:
                      fc_a=np.ascontiguousarray(inst.fc_a, dtype=np.float64),
                      pD_left=np.ascontiguousarray(inst.pD_left, dtype=np.float64),
                      pD_right=np.ascontiguousarray(inst.pD_right, dtype=np.float64))
+            if getattr(inst, "fc_kn", None) is not None:
+                a["fc_kn"] = np.ascontiguousarray(inst.fc_kn, dtype=np.float64)
             keep.append(a)
             arr[k] = Instance(inst.dim, inst.n, _ptr(a["km"]), inst.n_f, _ptr(a["fc_axis"]), _ptr(a["fc_pos"]),
                               _ptr(a["fc_kf"]), _ptr(a["fc_a"]), inst.nrhs, _ptr(a["pD_left"]), _ptr(a["pD_right"]), 0,
-                              JUNCTION[junction])
+                              JUNCTION[junction], _ptr(a.get("fc_kn")))
         h = C.c_void_p()
         self._check(lib().mds_assemble_batch(self.h, arr, len(insts), C.byref(h)))
         return System(self, h)
@@ -293,6 +295,8 @@ class Context:
                         fc_a=np.ascontiguousarray(inst.fc_a, dtype=np.float64),
                         pD_left=np.ascontiguousarray(inst.pD_left, dtype=np.float64),
                         pD_right=np.ascontiguousarray(inst.pD_right, dtype=np.float64))
+            if getattr(inst, "fc_kn", None) is not None:
+                arrs["fc_kn"] = np.ascontiguousarray(inst.fc_kn, dtype=np.float64)
             on_dev = 0
         else:
             arrs = device_arrays
@@ -300,7 +304,7 @@ class Context:
         keep.append(arrs)
         s = Instance(inst.dim, inst.n, _ptr(arrs["km"]), inst.n_f, _ptr(arrs["fc_axis"]), _ptr(arrs["fc_pos"]),
                      _ptr(arrs["fc_kf"]), _ptr(arrs["fc_a"]), inst.nrhs, _ptr(arrs["pD_left"]),
-                     _ptr(arrs["pD_right"]), on_dev, JUNCTION[junction])
+                     _ptr(arrs["pD_right"]), on_dev, JUNCTION[junction], _ptr(arrs.get("fc_kn")))
         h = C.c_void_p()
         fn = lib().mds_assemble_flux if form == "flux" else lib().mds_assemble
         self._check(fn(self.h, C.byref(s), C.byref(h)))

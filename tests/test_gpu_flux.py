@@ -212,3 +212,25 @@ def test_flux_full_size_random_segments(ctx, oracle_mod, torch_mod):
     ctx.precond_apply(prec, dev(torch, r), z)
     zo = M.apply(r)
     assert np.linalg.norm(z.cpu().numpy() - zo) <= 1e-12 * np.linalg.norm(zo)
+
+
+@pytest.mark.parametrize("form", ["primal", "flux"])
+@pytest.mark.parametrize("case", ["seg2d-96", "rects3d-18"])
+def test_normal_permeability_bit_exact(ctx, oracle_mod, torch_mod, case, form):
+    """A normal permeability k_n independent of k_f (kappa = 2 k_n / a): the
+    GPU assembly equals the oracle's, and M_L + FGMRES matches its iteration
+    count."""
+    import dataclasses
+    torch = torch_mod
+    inst = CASES[case]()
+    kn = np.exp(np.random.default_rng(21).uniform(np.log(1e-4), np.log(1e4), inst.n_f))
+    inst = dataclasses.replace(inst, fc_kn=kn)
+    sys_ = ctx.assemble(inst, form=form)
+    (_, _, _, _, A), b = sys_.to_host()
+    Ao, bo, no = oracle_mod.assemble(inst, form=form, with_split=True)
+    assert same_csr(A, Ao) and np.array_equal(b, bo)
+    prec = ctx.setup(sys_)
+    x = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+    code, st = ctx.solve(sys_, prec, None, x, rtol=1e-8, max_iters=3000)
+    res = oracle_mod.fgmres(Ao, bo[0], oracle_mod.ML(Ao, no), rtol=1e-8, maxit=3000)
+    assert code == 0 and res.converged and abs(st[0].iterations - res.iterations) <= 1
