@@ -782,6 +782,45 @@ def run_profile_case(args):
                       "relres": st[0].relres_true, "launches": ctx.launch_count()}))
 
 
+def run_table1(args):
+    """The shape of the paper's Table 1 (Sec. 4): M_L + FGMRES iteration counts
+    to a relative residual of 1e-6 over tangential fracture permeability
+    K_par in {1e-4, 1, 1e4} x normal permeability kappa (k_n) in {1e-4, 1,
+    1e4}, k_m = 1, on three refinements of a 2D and a 3D instance, in the
+    paper's partition with intersection cells and in the primal partition.
+    Stand-ins for the paper's benchmark geometries: the four-fracture unit
+    square (2D, a = 1e-4) and the nine-plane unit cube (3D, a = 1e-3)."""
+    import dataclasses
+
+    import torch
+
+    from paper_2206_03203_gb300 import build, inputs, mdsolve
+    build.build()
+    ctx = mdsolve.Context(0)
+    vals = (1e-4, 1.0, 1e4)
+    geoms = [("2d", n, lambda n, kf: inputs.fixed_2d(n=n, kf=kf)) for n in (64, 128, 256)] + \
+            [("3d", n, lambda n, kf: inputs.planes_3d(n, kf=kf)) for n in (16, 32, 64)]
+    out = {}
+    for form, junction in (("flux", "star"), ("primal", "pairwise")):
+        rows = {}
+        for kpar in vals:
+            for kap in vals:
+                its = []
+                for tag, n, make in geoms:
+                    inst = make(n, kpar)
+                    inst = dataclasses.replace(inst, fc_kn=np.full(inst.n_f, kap))
+                    s = ctx.assemble(inst, form=form, junction=junction)
+                    p = ctx.setup(s, precision="fp64", format="auto")
+                    x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+                    code, st = ctx.solve(s, p, None, x, rtol=1e-6, max_iters=5000)
+                    its.append(st[0].iterations if code == 0 else None)
+                    p.close()
+                    s.close()
+                rows[f"K_par={kpar:g} kappa={kap:g}"] = its
+        out[form] = {"columns": [f"{t} n={n}" for t, n, _ in geoms], "rows": rows}
+    print(json.dumps({"table1_shape": out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -792,6 +831,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-direct", action="store_true", help="skip the host direct solve of the accuracy check")
     ap.add_argument("--profile-case", action="store_true", help="short fixed run for ncu captures")
+    ap.add_argument("--table1", action="store_true", help="iteration counts over (K_par, kappa), the shape of "
+                                                           "the paper's Table 1")
     ap.add_argument("--max-iters", type=int, default=60)
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--precision", default="fp64")
@@ -799,6 +840,9 @@ def main():
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)
+        return
+    if args.table1:
+        run_table1(args)
         return
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3
