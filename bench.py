@@ -810,7 +810,7 @@ def run_table1(args):
                     inst = make(n, kpar)
                     inst = dataclasses.replace(inst, fc_kn=np.full(inst.n_f, kap))
                     s = ctx.assemble(inst, form=form, junction=junction)
-                    p = ctx.setup(s, precision="fp64", format="auto")
+                    p = ctx.setup(s, precision="fp64", format="auto", prolongation=args.prolongation)
                     x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
                     code, st = ctx.solve(s, p, None, x, rtol=1e-6, max_iters=5000)
                     its.append(st[0].iterations if code == 0 else None)
@@ -818,7 +818,7 @@ def run_table1(args):
                     s.close()
                 rows[f"K_par={kpar:g} kappa={kap:g}"] = its
         out[form] = {"columns": [f"{t} n={n}" for t, n, _ in geoms], "rows": rows}
-    print(json.dumps({"table1_shape": out}), flush=True)
+    print(json.dumps({"table1_shape": out, "prolongation": args.prolongation}), flush=True)
 
 
 def main():
@@ -833,6 +833,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true", help="short fixed run for ncu captures")
     ap.add_argument("--table1", action="store_true", help="iteration counts over (K_par, kappa), the shape of "
                                                            "the paper's Table 1")
+    ap.add_argument("--prolongation", default="piecewise", help="AMG prolongation of --table1 (piecewise, smoothed)")
     ap.add_argument("--max-iters", type=int, default=60)
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--precision", default="fp64")
