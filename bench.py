@@ -810,7 +810,12 @@ def run_table1(args):
                     inst = make(n, kpar)
                     inst = dataclasses.replace(inst, fc_kn=np.full(inst.n_f, kap))
                     s = ctx.assemble(inst, form=form, junction=junction)
-                    p = ctx.setup(s, precision="fp64", format="auto", prolongation=args.prolongation)
+                    try:
+                        p = ctx.setup(s, precision="fp64", format="auto", prolongation=args.prolongation)
+                    except mdsolve.MDSError as e:  # reported in the table, not fatal
+                        its.append(f"set-up: {e}")
+                        s.close()
+                        continue
                     x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
                     code, st = ctx.solve(s, p, None, x, rtol=1e-6, max_iters=5000)
                     its.append(st[0].iterations if code == 0 else None)
