@@ -70,3 +70,38 @@ def test_missing_library_fails_loudly(monkeypatch):
     monkeypatch.setattr(mdsolve, "LIB_PATH", "/nonexistent/libmdsolve.so")
     with pytest.raises(ImportError):
         mdsolve.lib()
+
+
+def test_null_handles_are_rejected_without_touching_a_device(built):
+    """Every entry point that takes a handle returns MDS_ERR_INVALID (-1) for
+    a NULL one, before any CUDA call (so this runs without a GPU)."""
+    from paper_2206_03203_gb300 import mdsolve
+    L = mdsolve.lib()
+    N = None
+    st = mdsolve.RhsStats()
+    cand = mdsolve.TuneCandidate()
+    best = ctypes.c_int()
+    out = ctypes.c_void_p()
+    calls = [
+        lambda: L.mds_destroy(N),
+        lambda: L.mds_set_stream(N, N),
+        lambda: L.mds_assemble(N, N, ctypes.byref(out)),
+        lambda: L.mds_assemble_flux(N, N, ctypes.byref(out)),
+        lambda: L.mds_assemble_batch(N, N, 1, ctypes.byref(out)),
+        lambda: L.mds_system_destroy(N),
+        lambda: L.mds_setup(N, N, N, ctypes.byref(out)),
+        lambda: L.mds_precond_destroy(N),
+        lambda: L.mds_precond_apply(N, N, N, N),
+        lambda: L.mds_vcycle(N, N, 0, N, N),
+        lambda: L.mds_spmv(N, N, N, N),
+        lambda: L.mds_solve(N, N, N, N, N, 1, N, ctypes.byref(st)),
+        lambda: L.mds_solve_async(N, N, N, N, N, 1, N),
+        lambda: L.mds_solve_done(N),
+        lambda: L.mds_solve_wait(N, ctypes.byref(st), 1),
+        lambda: L.mds_tune(N, N, N, N, N, ctypes.byref(cand), 1, ctypes.byref(best)),
+        lambda: L.mds_timing_reset(N),
+    ]
+    for k, f in enumerate(calls):
+        assert f() == -1, k
+    for code in range(-9, 2):
+        assert L.mds_error_string(code)
