@@ -912,7 +912,8 @@ static ocsr *galerkin(const ocsr *A, const int32_t *agg, int64_t nc) {
 /* Smoothed aggregation (Sec. 3.3 uses smoothed-aggregation AMG;
  * Vanek, Mandel, Brezina 1996): P = P0 - w D1F^-1 AF P0, with P0 the 0/1
  * aggregate injection, AF the filtered matrix (weak off-diagonals removed and
- * added to the diagonal, so row sums are kept), D1F the L1 diagonal of AF and
+ * added to the diagonal, so row sums are kept; a row whose lumped diagonal
+ * would not be positive keeps a_ii instead), D1F the L1 diagonal of AF and
  * w = 4/3 (lambda_max(D1F^-1 AF) <= 1, so w / lambda_max >= 4/3 needs no
  * eigenvalue estimate).  Row i: (agg(i), 1) when aggregated, then for each
  * entry of row i kept in AF, in CSR order, with J = agg(col) >= 0:
@@ -936,7 +937,11 @@ static ocsr *smoothed_prolongator(const ocsr *A, const ocsr *G, const int32_t *a
                 found_d = 1;
             }
         (void)found_d;
-        /* filtered diagonal: a_ii + sum of weak off-diagonals (CSR order) */
+        /* filtered diagonal: a_ii + sum of weak off-diagonals (CSR order);
+         * where that is not positive (coarse operators have positive
+         * off-diagonals) the row keeps a_ii and drops its weak entries
+         * without lumping them */
+        const double aii = afd;
         for (int64_t p = A->rp[i]; p < A->rp[i + 1]; p++) {
             int32_t j = A->ci[p];
             if (j == i) continue;
@@ -944,6 +949,7 @@ static ocsr *smoothed_prolongator(const ocsr *A, const ocsr *G, const int32_t *a
             int strong = g < G->rp[i + 1] && G->ci[g] == j;
             if (!strong) afd = afd + A->v[p];
         }
+        if (!(afd > 0.0)) afd = aii;
         d1 = afd;
         g = G->rp[i];
         for (int64_t p = A->rp[i]; p < A->rp[i + 1]; p++) {

@@ -389,9 +389,9 @@ __global__ void k_rap(int64_t nc, const int32_t *__restrict__ off, const int32_t
 constexpr int SA_P_CAP = 64;
 constexpr int SPGEMM_CAP = 512;
 
-// Filtered diagonal aF_ii = a_ii + sum of weak off-diagonals, and the L1
-// diagonal of the filtered matrix d1f_i = aF_ii + sum of strong |a_ij|
-// (both summed in CSR order).
+// Filtered diagonal aF_ii = a_ii + sum of weak off-diagonals (a_ii itself
+// where that sum is not positive), and the L1 diagonal of the filtered
+// matrix d1f_i = aF_ii + sum of strong |a_ij| (both summed in CSR order).
 __global__ void k_sa_diag(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                           const double *__restrict__ v, const int8_t *__restrict__ g, double *__restrict__ afd,
                           double *__restrict__ d1f) {
@@ -399,9 +399,13 @@ __global__ void k_sa_diag(int64_t n, const int32_t *__restrict__ rp, const int32
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t pd = find_col(ci, rp[i], rp[i + 1], (int32_t)i);
-    double a = pd >= 0 ? v[pd] : 0.0;
+    const double aii = pd >= 0 ? v[pd] : 0.0;
+    double a = aii;
     for (int32_t p = rp[i]; p < rp[i + 1]; p++)
         if (ci[p] != i && !g[p]) a = a + v[p];
+    // lumping the weak entries must leave a positive diagonal (coarse
+    // operators have positive off-diagonals): otherwise the row keeps a_ii
+    if (!(a > 0.0)) a = aii;
     double d = a;
     for (int32_t p = rp[i]; p < rp[i + 1]; p++)
         if (ci[p] != i && g[p]) d = d + fabs(v[p]);

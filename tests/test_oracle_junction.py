@@ -249,3 +249,27 @@ def test_intersection_form_solves(oracle_mod, case):
     assert r1.converged and np.max(np.abs(r1.x - y)) <= 1e-6 * scale
     r2 = oracle_mod.minres(A, b[0], oracle_mod.ML(A, no, kind="diag"), rtol=1e-10, maxit=5000)
     assert r2.converged and np.max(np.abs(r2.x - y)) <= 1e-6 * scale
+
+
+def test_smoothed_aggregation_on_intersection_cells(oracle_mod):
+    """Smoothed aggregation on the paper's partition with intersection cells
+    and K_par = 1e4 (coarse operators with positive off-diagonals, where
+    lumping weak entries can leave a non-positive diagonal): every level's
+    matrix is finite, the V-cycle is symmetric positive definite, and M_L +
+    FGMRES reaches the direct solution."""
+    import dataclasses
+    inst = inputs.planes_3d(16, kf=1e4)
+    inst = dataclasses.replace(inst, fc_kn=np.full(inst.n_f, 1.0))
+    A, b, no = oracle_mod.assemble(inst, form="flux", junction=1, with_split=True)
+    M = oracle_mod.ML(A, no, smoothed=1)
+    amg = M.amg(0)
+    assert amg.nlevels >= 3
+    for l in range(amg.nlevels):
+        assert np.all(np.isfinite(amg.level_A(l).data)), l
+    rng = np.random.default_rng(17)
+    v, w = rng.standard_normal((2, no))
+    x, y = v @ amg.vcycle(w), w @ amg.vcycle(v)
+    assert abs(x - y) <= 1e-10 * max(abs(x), abs(y)) and v @ amg.vcycle(v) > 0
+    y_direct = spla.spsolve(A.tocsc(), b[0])
+    r = oracle_mod.fgmres(A, b[0], M, rtol=1e-10, maxit=1000)
+    assert r.converged and np.max(np.abs(r.x - y_direct)) <= 1e-6 * max(1.0, np.max(np.abs(y_direct)))
