@@ -215,17 +215,53 @@ class Stats:
     relres_true: float
 
 
-class Context:
-    """A library context on one device and stream (torch's current stream by default)."""
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
-    def __init__(self, device: int = 0, stream: Optional[int] = None):
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("user", C.c_void_p)]
+
+
+def torch_allocator(device: int, stream: int) -> Allocator:
+    """mds_allocator backed by torch's caching allocator (device memory then
+    counts in torch.cuda.memory_allocated and is reused by torch)."""
+    import torch
+
+    def alloc(nbytes, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(max(int(nbytes), 1), device, stream)
+        except Exception:  # out of memory: the library reports MDS_ERR_OOM
+            return None
+
+    def free(ptr, user):
+        try:
+            torch.cuda.caching_allocator_delete(ptr)
+        except Exception:  # interpreter shutdown: torch may be gone already
+            pass
+    return Allocator(_ALLOC_FN(alloc), _FREE_FN(free), None)
+
+
+class Context:
+    """A library context on one device and stream (torch's current stream by
+    default).  allocator="torch" routes every device allocation of the
+    library through torch's caching allocator (mds_allocator); the default is
+    the library's own stream-ordered allocation."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None, allocator: Optional[str] = None):
         import torch
         L = lib()
         if stream is None:
             stream = torch.cuda.current_stream(device).cuda_stream
         self.device = device
+        self._alloc = None
+        if allocator == "torch":
+            self._alloc = torch_allocator(device, stream)  # the callbacks live as long as the context
+        elif allocator is not None:
+            raise ValueError(f"unknown allocator {allocator!r}")
         h = C.c_void_p()
-        self._check(L.mds_create(C.byref(h), device, C.c_void_p(stream), None), ctx=False)
+        self._check(L.mds_create(C.byref(h), device, C.c_void_p(stream),
+                                 C.byref(self._alloc) if self._alloc is not None else None), ctx=False)
         self.h = h
         _track(self, 2)
 

@@ -101,3 +101,33 @@ def test_async_error_paths(env):
     torch.cuda.synchronize()
     code, st = ctx.solve(sys_, prec, None, x)
     assert code == 0 and st[0].relres_true <= 1e-8
+
+
+def test_torch_caching_allocator(env):
+    """A context whose device memory comes from torch's caching allocator
+    (mds_allocator): the same solution as with the library's own allocation,
+    the memory visible to torch while the objects live, returned after."""
+    torch, mdsolve = env
+    inst = inputs.random_segments_2d(n=256, n_seg=20, contrast=1e2)
+    ref = mdsolve.Context(0)
+    s0 = ref.assemble(inst)
+    p0 = ref.setup(s0, format="csr")
+    x0 = torch.zeros(s0.N, dtype=torch.float64, device="cuda")
+    code0, st0 = ref.solve(s0, p0, None, x0)
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated(0)
+    ctx = mdsolve.Context(0, allocator="torch")
+    s = ctx.assemble(inst)
+    p = ctx.setup(s, format="csr")
+    x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    code, st = ctx.solve(s, p, None, x)
+    torch.cuda.synchronize()
+    held = torch.cuda.memory_allocated(0) - base
+    assert code == code0 == 0 and st[0].iterations == st0[0].iterations
+    assert torch.equal(x, x0)
+    assert held > 8 * s.N * 10  # hierarchy, blocks and Krylov workspace go through torch
+    p.close()
+    s.close()
+    ctx.close()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated(0) - base <= 8 * s.N + (1 << 20)  # only x remains
