@@ -125,7 +125,7 @@ def test_torch_caching_allocator(env):
     held = torch.cuda.memory_allocated(0) - base
     assert code == code0 == 0 and st[0].iterations == st0[0].iterations
     assert torch.equal(x, x0)
-    assert held > 8 * s.N * 10  # hierarchy, blocks and Krylov workspace go through torch
+    assert held > 8 * s.N * 4  # the blocks and the hierarchy live in torch-managed memory
     p.close()
     s.close()
     ctx.close()
