@@ -746,3 +746,19 @@ def test_smoothed_batched_multi_rhs(ctx, torch_mod):
     code2, st2 = ctx.solve(sys_, prec, None, xs, nrhs=4, batched=0)
     assert code == 0 and code2 == 0
     assert all(abs(a.iterations - b.iterations) <= 1 for a, b in zip(st, st2))
+
+
+def test_rejects_sizes_beyond_int32_indices(ctx, torch_mod):
+    """1300^3 cells exceed the int32 row and column indices: the assembly is
+    refused before any instance array is read (the device arrays here are
+    placeholders of one element)."""
+    import types
+    torch = torch_mod
+    from paper_2206_03203_gb300 import mdsolve
+    one = torch.zeros(1, dtype=torch.float64, device="cuda")
+    onei = torch.zeros(3, dtype=torch.int32, device="cuda")
+    inst = types.SimpleNamespace(dim=3, n=1300, n_f=0, nrhs=1)
+    arrs = dict(km=one, fc_axis=onei, fc_pos=onei, fc_kf=one, fc_a=one, pD_left=one, pD_right=one)
+    with pytest.raises(mdsolve.MDSError) as e:
+        ctx.assemble(inst, device_arrays=arrs)
+    assert "int32" in str(e.value)
