@@ -248,6 +248,7 @@ def run_gpu(args):
     t_total = 0.0
     iters = []
     step_s = []
+    torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed steps (ncu --nvtx-include timed/)
     for s_ in range(args.steps):
         flush.fill_(float(s_))  # L2 flush between steps (256 MB > 129 MB L2)
         torch.cuda.synchronize()
@@ -258,6 +259,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         step_s.append(e0.elapsed_time(e1) / 1e3)
         t_total += step_s[-1]
+    torch.cuda.nvtx.range_pop()
     # phases of the last timed step (events on the library's stream)
     ph = np.zeros(3)
     for ev in phase_ev:
