@@ -191,6 +191,9 @@ int mds_system_instances(mds_system sys, int *n_inst, int64_t *m_off, int64_t *f
 int mds_system_from_csr(mds_ctx ctx, const mds_csr *Amm, const mds_csr *Amf,
                         const mds_csr *Afm, const mds_csr *Aff, const double *b,
                         mds_system *out);
+/* Frees the system's own storage (borrowed caller blocks stay the caller's).
+ * Preconditioners set up on it must be destroyed first; the context is
+ * released here if it was destroyed while this was its last dependent. */
 int mds_system_destroy(mds_system sys);
 /* Sizes: n_m, n_f, nrhs and nnz of (A_mm, A_mf, A_fm, A_ff, full). */
 int mds_system_info(mds_system sys, int64_t *n_m, int64_t *n_f, int *nrhs, int64_t nnz[5]);
