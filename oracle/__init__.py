@@ -1,7 +1,7 @@
 """Python access to the C oracle: TEST INFRASTRUCTURE ONLY.
 
-Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
-``bench.py`` may import this package.  The oracle is a plain sequential FP64
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg and
+reference arm of ``bench.py`` may import this package.  The oracle is a plain sequential FP64
 implementation of the method of Hu, Keilegavlen & Nordbotten (arXiv:2206.03203)
 written independently of the CUDA library (see ``mdoracle.c``).  It never
 calls, links or imports the CUDA path.

@@ -1,7 +1,8 @@
 /* Oracle for the mixed-dimensional block solver: TEST INFRASTRUCTURE ONLY.
  *
  * Plain sequential FP64 C.  Loaded only by the tests, the smoke check and the
- * benchmark's CPU-baseline leg.  Nothing here is shared with the CUDA library.
+ * benchmark's CPU-baseline leg and reference arm.  Nothing here is shared with
+ * the CUDA library.
  * Compiled with -ffp-contract=off so every product and sum is rounded exactly
  * as written.
  *
