@@ -15,7 +15,9 @@ import pytest
 import oracle
 
 import test_oracle_assembly as T_asm
+import test_oracle_flux as T_flux
 import test_oracle_junction as T_junc
+import test_oracle_krylov as T_kry
 import test_oracle_normal_permeability as T_kn
 import test_oracle_schur_amg as T_amg
 import test_oracle_smoothers as T_sm
@@ -47,6 +49,26 @@ MUTATIONS = {
         "const double *kn = fc_kn ? fc_kn : fc_kf;",
         "const double *kn = fc_kf;",
         lambda o: T_kn.test_across_a_fracture_only_kn_counts(o, 1e4, 1e-4, 1e-4)),
+    # the strength threshold dropped: every coupling strong
+    "strength threshold": (
+        "double th2 = theta * theta;",
+        "double th2 = 0.0 * theta;",
+        lambda o: T_amg.test_strength_anisotropic(o)),
+    # a wrong sign in the Givens rotation of the Hessenberg column
+    "Givens rotation sign": (
+        "H[(q + 1) * m + j] = -sn[q] * a + cs[q] * c;",
+        "H[(q + 1) * m + j] = sn[q] * a + cs[q] * c;",
+        lambda o: T_kry.test_identity_fgmres_is_gmres_finite_termination(o)),
+    # the paper's partition: the fracture side of a flux with the wrong sign
+    "flux sign": (
+        "row[cnt].t = -1.0;",
+        "row[cnt].t = 1.0;",
+        lambda o: T_flux.test_flux_form_structure(o, "fixed2d-16")),
+    # an intersection flux row with half the member's transmissibility
+    "intersection flux law": (
+        "A->v[pos++] = -1.0 / tl;",
+        "A->v[pos++] = -1.0 / (2.0 * tl);",
+        lambda o: T_junc.test_intersection_form_structure(o, "fixed2d-16")),
     # Dirichlet faces of the matrix with half the boundary transmissibility
     "Dirichlet factor": (
         "tb[s] = (F * (2.0 * ki)) / h;",
