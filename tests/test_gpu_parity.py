@@ -762,3 +762,23 @@ def test_rejects_sizes_beyond_int32_indices(ctx, torch_mod):
     with pytest.raises(mdsolve.MDSError) as e:
         ctx.assemble(inst, device_arrays=arrs)
     assert "int32" in str(e.value)
+
+
+@pytest.mark.parametrize("case", ["fixed2d-64", "seg2d-96", "planes3d-16", "rects3d-18"])
+def test_fp64_path_agrees_with_oracle_to_1e10(ctx, oracle_mod, torch_mod, case):
+    """The FP64 path and the oracle, both solved to a relative residual of
+    1e-12, agree to 1e-10 in the relative residual of their difference (and
+    to 1e-9 in the solution against a sparse direct solve)."""
+    torch = torch_mod
+    inst = CASES[case]()
+    sys_ = ctx.assemble(inst)
+    prec = ctx.setup(sys_, format="csr")
+    x = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+    code, st = ctx.solve(sys_, prec, None, x, rtol=1e-12, max_iters=5000)
+    res, Ao, bo, _ = oracle_mod.solve(inst, rtol=1e-12, maxit=5000)
+    assert code == 0 and res.converged
+    xg = x.cpu().numpy()
+    nb = np.linalg.norm(bo[0])
+    assert np.linalg.norm(Ao @ (xg - res.x)) / nb <= 1e-10
+    xd = spla.spsolve(Ao.tocsc(), bo[0])
+    assert np.linalg.norm(xg - xd) <= 1e-9 * np.linalg.norm(xd)
