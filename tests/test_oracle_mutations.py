@@ -69,6 +69,22 @@ MUTATIONS = {
         "A->v[pos++] = -1.0 / tl;",
         "A->v[pos++] = -1.0 / (2.0 * tl);",
         lambda o: T_junc.test_intersection_form_structure(o, "fixed2d-16")),
+    # smoothed aggregation with the damping 1 instead of 4/3
+    "SA damping": (
+        "double ci = (4.0 / 3.0) / d1;",
+        "double ci = 1.0 / d1;",
+        lambda o: T_amg.test_smoothed_prolongator_and_galerkin(o, lambda: T_amg.lap2(12))),
+    # bf16 rounding that truncates instead of rounding to nearest even
+    "bf16 rounding": (
+        "u = (u + 0x7fffu + lsb) & 0xffff0000u;",
+        "u = u & 0xffff0000u;",
+        lambda o: T_amg.test_lowp_rounding(o)),
+    # restriction that drops the last member of each aggregate's sum (r_i of
+    # odd i left out)
+    "restriction": (
+        "if (h->agg[l][i] >= 0) bc[h->agg[l][i]] += r[i];",
+        "if (h->agg[l][i] >= 0 && (i & 1) == 0) bc[h->agg[l][i]] += r[i];",
+        lambda o: T_amg.test_vcycle_two_grid_error_propagation(o, 0)),
     # Dirichlet faces of the matrix with half the boundary transmissibility
     "Dirichlet factor": (
         "tb[s] = (F * (2.0 * ki)) / h;",
