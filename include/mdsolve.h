@@ -72,7 +72,10 @@ typedef struct {
 /* Create a context on CUDA device `device` that enqueues on `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream).  `alloc` may be NULL
  * for stream-ordered cudaMallocAsync/cudaFreeAsync.  The allocator struct is
- * copied; its callbacks must stay valid for the context's lifetime. */
+ * copied; its callbacks must stay valid for the context's lifetime.  The
+ * environment variable MDS_PDL=0 makes the context launch its kernels in
+ * plain stream order, without programmatic dependent launch (for diagnosis;
+ * the results are the same). */
 int mds_create(mds_ctx *out, int device, void *cuda_stream, const mds_allocator *alloc);
 /* Systems and preconditioners keep their context alive: destroying a context
  * that still has some only marks it, and it is released when the last of them
