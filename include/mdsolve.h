@@ -223,9 +223,9 @@ int mds_system_view(mds_system sys, mds_csr blocks[5], const double **b);
 #define MDS_BLOCK_UPPER 2       /* block upper triangular B_U with Q blocks */
 
 typedef struct {
-    double theta;            /* strength threshold (0.08; with smoothed prolongation 0.04 measured
-                                better: 25-48 FGMRES iterations over the 1024^2 contrast sweep in
-                                the paper's partition, against up to 512 with 0.08) */
+    double theta;            /* strength threshold; < 0 (the default) = 0.08 with piecewise-constant
+                                and 0.04 with smoothed prolongation (with 0.04 smoothed aggregation
+                                keeps its iteration counts flat over contrast and refinement) */
     int64_t n_coarse;        /* dense Cholesky once a level has <= n_coarse rows (512) */
     int max_levels;          /* (25) */
     double stall_ratio;      /* stop coarsening when n_{l+1} > stall_ratio n_l (0.9) */

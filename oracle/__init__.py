@@ -256,9 +256,12 @@ def mis_key(seed, level, i):
 DEFAULT_SEED = 0x2206_0320_3
 
 
-def amg_opts(theta=0.08, n_coarse=512, max_levels=25, stall_ratio=0.9, seed=DEFAULT_SEED,
+def amg_opts(theta=None, n_coarse=512, max_levels=25, stall_ratio=0.9, seed=DEFAULT_SEED,
              smoother=0, prec=64, lowp_from_level=1, sweeps=1, smoothed=0, cheb_degree=2) -> AMGOpts:
-    """smoother: 0 L1-Jacobi, 1 Chebyshev (degree cheb_degree), 2 Gauss-Seidel."""
+    """smoother: 0 L1-Jacobi, 1 Chebyshev (degree cheb_degree), 2 Gauss-Seidel.
+    theta None: 0.08 for piecewise-constant, 0.04 for smoothed aggregation."""
+    if theta is None or theta < 0:
+        theta = 0.04 if smoothed else 0.08
     return AMGOpts(theta, n_coarse, max_levels, stall_ratio, seed, smoother, prec, lowp_from_level, sweeps,
                    smoothed, cheb_degree)
 

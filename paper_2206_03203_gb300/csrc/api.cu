@@ -409,7 +409,7 @@ int mds_system_view(mds_system sys, mds_csr blocks[5], const double **b) {
 
 int mds_setup_opts_default(mds_setup_opts *o) {
     if (!o) return MDS_ERR_INVALID;
-    o->theta = 0.08;
+    o->theta = -1.0;  // automatic: 0.08, or 0.04 with smoothed prolongation (resolved by mds_setup)
     o->n_coarse = 512;
     o->max_levels = 25;
     o->stall_ratio = 0.9;
@@ -452,6 +452,7 @@ int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_preco
     MDS_REQUIRE(o.prolongation == MDS_PROLONG_PIECEWISE || o.prolongation == MDS_PROLONG_SMOOTHED, MDS_ERR_INVALID,
                 "unknown prolongation");
     MDS_REQUIRE(o.kind >= 0 && o.kind <= 2, MDS_ERR_INVALID, "bad preconditioner kind");
+    if (o.theta < 0.0) o.theta = o.prolongation == MDS_PROLONG_SMOOTHED ? 0.04 : 0.08;
     MDS_REQUIRE(o.theta >= 0.0 && o.n_coarse >= 1 && o.n_coarse <= 8192, MDS_ERR_INVALID, "bad AMG options");
     auto *p = new mds_precond_s;
     // set-up kernels write the level data that V-cycle kernels read before

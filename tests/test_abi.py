@@ -54,7 +54,7 @@ def test_binding_loads_without_gpu(built):
 def test_default_options(built):
     from paper_2206_03203_gb300 import mdsolve
     o = mdsolve.setup_opts()
-    assert o.theta == 0.08 and o.n_coarse == 512 and o.max_levels == 25
+    assert o.theta < 0 and o.n_coarse == 512 and o.max_levels == 25  # theta resolved by mds_setup
     s = mdsolve.solve_opts()
     assert s.restart == 30 and s.rtol == 1e-8
 

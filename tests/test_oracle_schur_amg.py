@@ -333,7 +333,7 @@ def test_smoothed_prolongator_and_galerkin(oracle_mod, make):
     assert amg.nlevels >= 2
     for l in range(amg.nlevels - 1):
         Al = amg.level_A(l)
-        G = oracle_mod.strength(Al, 0.08)
+        G = oracle_mod.strength(Al, amg.opts.theta)
         agg = amg.agg(l)
         nc = amg.level_A(l + 1).shape[0]
         P = amg.P(l)
