@@ -586,8 +586,6 @@ def variants(ctx, insts, dev_arrays, N, flush):
     for name, kw in (("flux_form_ML_fgmres", dict(kind="lower", krylov="fgmres")),
                      ("flux_form_smoothed_aggregation_ML_fgmres",
                       dict(kind="lower", krylov="fgmres", prolongation="smoothed")),
-                     ("flux_form_smoothed_aggregation_theta0.04_ML_fgmres",
-                      dict(kind="lower", krylov="fgmres", prolongation="smoothed", theta=0.04)),
                      ("flux_form_block_diagonal_minres", dict(kind="diag", krylov="minres"))):
         kry = kw.pop("krylov")
         t, its = _timed(lambda kry=kry, kw=kw: sweep("fp64", krylov=kry, form="flux", **kw), flush, warmup=0)
