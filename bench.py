@@ -786,6 +786,20 @@ def run_profile_case(args):
                       "relres": st[0].relres_true, "launches": ctx.launch_count()}))
 
 
+def refinement_growth(columns, its):
+    """Per dimension, the ratio of the iteration count on the finest grid to
+    that on the coarsest (None where a count is missing), and whether it
+    exceeds 2 (the growth the table is meant to flag)."""
+    out = {}
+    for dim in sorted({c.split()[0] for c in columns}):
+        idx = [k for k, c in enumerate(columns) if c.split()[0] == dim]
+        first, last = its[idx[0]], its[idx[-1]]
+        ok = isinstance(first, int) and isinstance(last, int) and first > 0
+        ratio = last / first if ok else None
+        out[dim] = {"ratio": ratio, "over_2x": bool(ratio is not None and ratio > 2.0)}
+    return out
+
+
 def run_table1(args):
     """The shape of the paper's Table 1 (Sec. 4): M_L + FGMRES iteration counts
     to a relative residual of 1e-6 over tangential fracture permeability
@@ -826,7 +840,9 @@ def run_table1(args):
                     p.close()
                     s.close()
                 rows[f"K_par={kpar:g} kappa={kap:g}"] = its
-        out[form] = {"columns": [f"{t} n={n}" for t, n, _ in geoms], "rows": rows}
+        cols = [f"{t} n={n}" for t, n, _ in geoms]
+        out[form] = {"columns": cols, "rows": rows,
+                     "refinement_growth": {k: refinement_growth(cols, v) for k, v in rows.items()}}
     print(json.dumps({"table1_shape": out, "prolongation": args.prolongation}), flush=True)
 
 

@@ -245,8 +245,9 @@ def torch_allocator(device: int, stream: int) -> Allocator:
 class Context:
     """A library context on one device and stream (torch's current stream by
     default).  allocator="torch" routes every device allocation of the
-    library through torch's caching allocator (mds_allocator); the default is
-    the library's own stream-ordered allocation."""
+    library through torch's caching allocator (mds_allocator), an Allocator
+    instance through its own callbacks; the default is the library's own
+    stream-ordered allocation."""
 
     def __init__(self, device: int = 0, stream: Optional[int] = None, allocator: Optional[str] = None):
         import torch
@@ -257,6 +258,8 @@ class Context:
         self._alloc = None
         if allocator == "torch":
             self._alloc = torch_allocator(device, stream)  # the callbacks live as long as the context
+        elif isinstance(allocator, Allocator):
+            self._alloc = allocator
         elif allocator is not None:
             raise ValueError(f"unknown allocator {allocator!r}")
         h = C.c_void_p()

@@ -105,3 +105,17 @@ def test_null_handles_are_rejected_without_touching_a_device(built):
         assert f() == -1, k
     for code in range(-9, 2):
         assert L.mds_error_string(code)
+
+
+def test_refinement_growth_flag():
+    """bench.py --table1 flags iteration counts that more than double from
+    the coarsest to the finest grid of a dimension."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    cols = ["2d n=64", "2d n=128", "2d n=256", "3d n=16", "3d n=32", "3d n=64"]
+    g = bench.refinement_growth(cols, [10, 14, 21, 14, 20, 28])
+    assert g["2d"] == {"ratio": 2.1, "over_2x": True} and g["3d"] == {"ratio": 2.0, "over_2x": False}
+    g = bench.refinement_growth(cols, [10, "set-up: failed", None, 14, 20, 28])
+    assert g["2d"]["ratio"] is None and not g["2d"]["over_2x"]

@@ -131,3 +131,32 @@ def test_torch_caching_allocator(env):
     ctx.close()
     torch.cuda.synchronize()
     assert torch.cuda.memory_allocated(0) - base <= 8 * s.N + (1 << 20)  # only x remains
+
+
+def test_allocator_returning_null_reports_oom(env):
+    """A caller allocator that returns NULL makes the call fail with
+    MDS_ERR_OOM (-3); the context stays usable for calls that fit."""
+    torch, mdsolve = env
+    state = {"fail": True}
+
+    def alloc(nbytes, user):
+        if state["fail"]:
+            return None
+        return torch.cuda.caching_allocator_alloc(max(int(nbytes), 1), 0)
+
+    def free(ptr, user):
+        torch.cuda.caching_allocator_delete(ptr)
+    a = mdsolve.Allocator(mdsolve._ALLOC_FN(alloc), mdsolve._FREE_FN(free), None)
+    ctx = mdsolve.Context(0, allocator=a)
+    with pytest.raises(mdsolve.MDSError) as e:
+        ctx.assemble(inputs.fixed_2d(n=8))
+    assert e.value.code == -3
+    state["fail"] = False
+    s = ctx.assemble(inputs.fixed_2d(n=8))
+    p = ctx.setup(s)
+    x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    code, st = ctx.solve(s, p, None, x)
+    assert code == 0 and st[0].relres_true <= 1e-8
+    p.close()
+    s.close()
+    ctx.close()
