@@ -392,11 +392,14 @@ int mds_solve_wait(mds_ctx ctx, mds_rhs_stats *stats, int count);
  * holds until the process exits.  It calls no cudaMalloc, cudaFree or other
  * allocating routine.
  *   - n_m + n_f must be <= MDS_NOALLOC_MAX_N and restart <= 30; larger
- *     problems are rejected with MDS_ERR_INVALID.
+ *     problems are rejected with MDS_ERR_INVALID, and so is a packed batch
+ *     of several instances (mds_solve solves those).
  *   - b (NULL: the assembled right-hand side) and x must be device pointers;
  *     x holds x0 on entry and the solution on return.
- *   - The first call on a device looks up the array's device address with
- *     that device current; make that first call before any stream capture.
+ *   - The array exists from the first mds_create on a device onwards:
+ *     mds_create resolves its device address (which loads the part of the
+ *     library that holds it) with that device current, so a call of this
+ *     entry point performs no set-up of its own.
  *   - Every call on a device shares the one array and leaves its contents
  *     behind (the parts that must start at zero are cleared on entry); calls
  *     whose GPU work overlaps, from any context or stream, race on it.

@@ -39,6 +39,15 @@ void Buf::reset() {
     bytes = 0;
 }
 
+// The second stream and its fork / join events (block-diagonal
+// preconditioner); created once per context.
+void Ctx::ensure_side_stream() {
+    if (side_stream) return;
+    MDS_CUDA(cudaStreamCreateWithFlags(&side_stream, cudaStreamNonBlocking));
+    MDS_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+    MDS_CUDA(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+}
+
 void *Ctx::raw_alloc(size_t n) {
     void *p = nullptr;
     if (custom_alloc) {
@@ -218,9 +227,13 @@ int mds_create(mds_ctx *out, int device, void *stream, const mds_allocator *allo
         MDS_CUDA(cudaMalloc(&c->d_err, sizeof(int)));
         MDS_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
         MDS_CUDA(cudaMallocHost(&c->h_pin, Ctx::PIN_BYTES));
+        // the static workspace of mds_solve_noalloc: resolving its address
+        // loads the module holding it, here rather than inside a later solve
+        c->noalloc_scratch = noalloc_scratch_lookup();
     } catch (const Error &e) {
         int code = e.code;
         if (c->d_err) cudaFree(c->d_err);
+        if (c->h_pin) cudaFreeHost(c->h_pin);
         delete h;
         return code;
     }
@@ -477,6 +490,9 @@ int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_preco
         int64_t mx = sys->n_m > sys->n_f ? sys->n_m : sys->n_f;
         p->tf64 = Buf(c, sizeof(double) * (size_t)(mx > 0 ? mx : 1));
         p->tf_cap = mx;
+        // B_D runs its two V-cycles on two streams: create the second one
+        // now, so that applying the preconditioner creates nothing
+        if (o.kind == MDS_BLOCK_DIAG && p->has_f) c->ensure_side_stream();
         c->sync();
     } catch (...) {
         delete p;
@@ -580,11 +596,7 @@ void precond_apply(mds_precond p, const double *r, double *z, int nr) {
         // B_D: the two V-cycles are independent.  Q_ff runs on the side
         // stream while Q_mm runs on the main stream (fork and join by events,
         // which a CUDA graph capture turns into parallel branches).
-        if (!c.side_stream) {
-            MDS_CUDA(cudaStreamCreateWithFlags(&c.side_stream, cudaStreamNonBlocking));
-            MDS_CUDA(cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming));
-            MDS_CUDA(cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming));
-        }
+        c.ensure_side_stream();  // created by mds_setup for this kind
         MDS_CUDA(cudaEventRecord(c.ev_fork, c.stream));
         MDS_CUDA(cudaStreamWaitEvent(c.side_stream, c.ev_fork, 0));
         cudaStream_t main = c.stream;
@@ -917,6 +929,8 @@ int mds_solve_noalloc(mds_ctx ctx, mds_system sys, mds_precond prec, const doubl
     o.graphs = 0;  // graph instantiation may allocate
     int64_t n = sys->n_m + sys->n_f;
     MDS_REQUIRE(o.krylov == MDS_KRYLOV_FGMRES, MDS_ERR_INVALID, "mds_solve_noalloc runs FGMRES only");
+    MDS_REQUIRE(sys->n_inst == 1, MDS_ERR_INVALID,
+                "mds_solve_noalloc solves one instance; a packed batch needs mds_solve");
     MDS_REQUIRE(n <= MDS_NOALLOC_MAX_N, MDS_ERR_INVALID,
                 "mds_solve_noalloc: n_m + n_f = " + std::to_string(n) + " exceeds MDS_NOALLOC_MAX_N = " +
                     std::to_string(MDS_NOALLOC_MAX_N));

@@ -171,6 +171,10 @@ struct Ctx {
     // independent V-cycles of the block-diagonal preconditioner)
     cudaStream_t side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // device address of the static workspace of mds_solve_noalloc on this
+    // context's device, resolved by mds_create
+    double *noalloc_scratch = nullptr;
+    void ensure_side_stream();
     bool pdl = true;              // launch with programmatic stream serialisation
     bool setup_phase = false;     // set-up writes level data: launch in plain stream order
     // autotuner choices by (rows, nonzeros, value type)

@@ -913,20 +913,20 @@ static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
 
 size_t noalloc_scratch_doubles() { return NOALLOC_DOUBLES; }
 
-// The symbol's device address, looked up once per device with that device
-// current (the host-side name is only a stand-in, never a device address).
+// The symbol's device address on the current device.  mds_create calls this
+// with the context's device current and keeps the result in the context: the
+// host-side name is only a stand-in, never a device address, and resolving it
+// loads the module that holds the array, so that happens while the context
+// is created rather than in the middle of a solve.
+double *noalloc_scratch_lookup() {
+    void *p = nullptr;
+    MDS_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    return static_cast<double *>(p);
+}
+
 double *noalloc_scratch(Ctx &c) {
-    static std::mutex mu;
-    static double *addr[256] = {};
-    std::lock_guard<std::mutex> lock(mu);
-    MDS_REQUIRE(c.device >= 0 && c.device < 256, MDS_ERR_INVALID, "device index out of range");
-    if (!addr[c.device]) {
-        MDS_CUDA(cudaSetDevice(c.device));
-        void *p = nullptr;
-        MDS_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        addr[c.device] = static_cast<double *>(p);
-    }
-    return addr[c.device];
+    MDS_REQUIRE(c.noalloc_scratch != nullptr, MDS_ERR_INVALID, "context has no static workspace address");
+    return c.noalloc_scratch;
 }
 
 }  // namespace mds

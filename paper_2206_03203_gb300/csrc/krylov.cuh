@@ -32,9 +32,11 @@ FgmresWorkspace fgmres_workspace_carve(double *base, int64_t n, int m);
 KrylovResult fgmres(Ctx &c, const mds_csr &A, const PrecFn &M, const double *b, double *x, int64_t n,
                     const mds_solve_opts &o, const FgmresWorkspace *ws = nullptr);
 
-// Base of the library's static no-allocation workspace on the current device
-// (see mds_solve_noalloc) and its size in doubles.
+// The library's static no-allocation workspace (see mds_solve_noalloc): its
+// device address as resolved for the context at creation, the lookup itself
+// (on the current device), and its size in doubles.
 double *noalloc_scratch(Ctx &c);
+double *noalloc_scratch_lookup();
 size_t noalloc_scratch_doubles();
 // K instances (row segments [moff_k, moff_k+1) and [NM + foff_k, NM +
 // foff_k+1)) x nrhs columns (column-major [nrhs][N] in B and X) solved as

@@ -90,6 +90,64 @@ def test_two_gloo_ranks_reduce_and_shard(tmp_path):
     assert rs[0]["shard"] == rs[0]["all"][0] and rs[1]["shard"] == rs[1]["all"][1]
 
 
+def _solve_rank_main(rank, world, port, out_dir):
+    """One gloo rank: solve this rank's shard of a small uneven 3D batch with
+    the oracle (assembly, M_L set-up, FGMRES(30) to 1e-8 for every
+    right-hand side), then gather every rank's per-instance results."""
+    import pickle
+
+    import torch.distributed as dist
+
+    import oracle
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        batch = inputs.batch_3d(count=6, lo=8, hi=12, nrhs=2)
+        work = [sharding.instance_work(b.n_m, b.n_f) for b in batch]
+        shard = sharding.shard_by_work(work, world)[rank]
+        local = {}
+        for i in shard:
+            A, b = oracle.assemble(batch[i])
+            M = oracle.ML(A, batch[i].n_m)
+            res = [oracle.fgmres(A, b[k], M, rtol=1e-8, maxit=500) for k in range(b.shape[0])]
+            local[i] = ([r.x for r in res], [r.iterations for r in res])
+        t, solves = sharding.reduce_over_ranks(1.0 + rank, sum(len(v[1]) for v in local.values()))
+        gathered = [None] * world
+        dist.all_gather_object(gathered, local)
+        with open(os.path.join(out_dir, f"solve{rank}.pkl"), "wb") as f:
+            pickle.dump({"shard": shard, "all": gathered, "t": t, "solves": solves}, f)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_solve_their_shards(tmp_path, oracle_mod):
+    """Instance sharding with real solves: two gloo ranks each solve their
+    shard of a six-instance batch with the oracle; the gathered solutions and
+    iteration counts equal, bit for bit, those of one process solving every
+    instance (the instances are independent and the oracle is sequential)."""
+    import pickle
+    world = 2
+    mp.start_processes(_solve_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    rs = [pickle.load(open(tmp_path / f"solve{r}.pkl", "rb")) for r in range(world)]
+    assert all(len(r["shard"]) > 0 for r in rs)  # both ranks had work
+    assert rs[0]["t"] == rs[1]["t"] == 2.0 and rs[0]["solves"] == rs[1]["solves"] == 12
+    merged = {}
+    for part in rs[0]["all"]:
+        assert not set(part) & set(merged)  # no instance solved twice
+        merged.update(part)
+    assert sorted(merged) == list(range(6))
+    batch = inputs.batch_3d(count=6, lo=8, hi=12, nrhs=2)
+    for i, inst in enumerate(batch):
+        A, b = oracle_mod.assemble(inst)
+        M = oracle_mod.ML(A, inst.n_m)
+        xs, its = merged[i]
+        for k in range(b.shape[0]):
+            ref = oracle_mod.fgmres(A, b[k], M, rtol=1e-8, maxit=500)
+            assert ref.converged and its[k] == ref.iterations
+            assert np.array_equal(xs[k], ref.x), (i, k)
+
+
 def test_reduce_without_process_group_is_identity():
     assert sharding.reduce_over_ranks(1.25, 7) == (1.25, 7.0)
 
