@@ -281,6 +281,16 @@ int mds_precond_level(mds_precond prec, int block, int level, mds_csr *A,
 /* Borrowed device view of the smoothed prolongator of a level (fine rows x
  * coarse columns); P->nnz = 0 and null arrays when the level uses injection. */
 int mds_precond_prolongator(mds_precond prec, int block, int level, mds_csr *P);
+/* Borrowed device views of what the V-cycle of a level multiplies by (the
+ * storage readings of Sec. 3.3's V-cycle in reduced precision): the value
+ * type (MDS_PREC_FP64 / FP32 / BF16 / FP16), the values in the CSR order of
+ * mds_precond_level's matrix (for BF16 / FP16: q_ij with a_ij ~ s_i q_ij;
+ * NULL on a last level applied through its dense inverse), the float row
+ * scales s_i (NULL unless BF16 / FP16) and 1/D1 (double for FP64
+ * hierarchies, float otherwise).  MDS_ERR_INVALID for a block or level that
+ * does not exist. */
+int mds_precond_level_storage(mds_precond prec, int block, int level, int *value_type,
+                              const void **values, const float **row_scale, const void **dinv);
 /* z = M r for device FP64 vectors of length n_m + n_f. */
 int mds_precond_apply(mds_ctx ctx, mds_precond prec, const double *r, double *z);
 /* x = V(b): one V-cycle of block 0 or 1 on device FP64 vectors. */

@@ -104,6 +104,8 @@ def lib():
             L.orc_amg_level_agg.argtypes = [C.c_void_p, C.c_int, _i32p]
             L.orc_amg_level_roots.argtypes = [C.c_void_p, C.c_int, _i8p]
             L.orc_amg_level_l1.argtypes = [C.c_void_p, C.c_int, _f64p]
+            L.orc_amg_level_stored.argtypes = [C.c_void_p, C.c_int, _f64p, _f64p, _f64p]
+            L.orc_amg_level_lowp.argtypes = [C.c_void_p, C.c_int]
             L.orc_amg_level_P.restype = P(_CSR)
             L.orc_amg_level_P.argtypes = [C.c_void_p, C.c_int]
             L.orc_amg_coarsest_dense.argtypes = [C.c_void_p]
@@ -310,6 +312,15 @@ class AMG:
         out = np.zeros(n)
         lib().orc_amg_level_l1(self.h, l, _p(out, _f64p))
         return out
+
+    def stored(self, l):
+        """(values in CSR order of level_A(l), row scales, 1/D1) as the
+        V-cycle applies them, and the level's low-precision format (16 =
+        bf16, 17 = fp16, 0 = none)."""
+        A = self.level_A(l)
+        av, rs, dv = np.zeros(A.nnz), np.zeros(A.shape[0]), np.zeros(A.shape[0])
+        lib().orc_amg_level_stored(self.h, l, _p(av, _f64p), _p(rs, _f64p), _p(dv, _f64p))
+        return av, rs, dv, lib().orc_amg_level_lowp(self.h, l)
 
     def P(self, l):
         ptr = lib().orc_amg_level_P(self.h, l)

@@ -747,6 +747,7 @@ struct orc_amg {
     double *l1[MAXLEV];    /* L1 diagonal a_ii + sum_{j!=i} |a_ij| */
     double *av[MAXLEV];    /* matrix values as the smoother/residual use them */
     double *dinv[MAXLEV];  /* 1 / l1, rounded to the storage precision */
+    double *rs[MAXLEV];    /* row scales s_i of a bf16/fp16 level (1 on other levels) */
     int lowp[MAXLEV];      /* level stored with bf16 row-scaled values */
     ocsr *P[MAXLEV];       /* smoothed prolongator of level l (NULL: injection by agg) */
     ocsr *R[MAXLEV];       /* its transpose */
@@ -1184,7 +1185,9 @@ orc_amg *orc_amg_setup(const ocsr *A0, const orc_amg_opts *o) {
         h->l1[q] = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
         h->dinv[q] = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
         h->av[q] = (double *)malloc((size_t)(M->nnz > 0 ? M->nnz : 1) * sizeof(double));
+        h->rs[q] = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
         for (int64_t i = 0; i < n; i++) {
+            h->rs[q][i] = 1.0;
             int f;
             double s = find_val(M, i, i, &f);
             for (int64_t p = M->rp[i]; p < M->rp[i + 1]; p++)
@@ -1200,6 +1203,7 @@ orc_amg *orc_amg_setup(const ocsr *A0, const orc_amg_opts *o) {
                 double fr = frexp(mx, &e); /* mx = fr 2^e, fr in [0.5,1) */
                 if (fr == 0.5) e -= 1;     /* exact power of two */
                 double sc = ldexp(1.0, e);
+                h->rs[q][i] = sc;
                 for (int64_t p = M->rp[i]; p < M->rp[i + 1]; p++) {
                     float t = (float)(M->v[p] / sc);
                     h->av[q][p] = (lp == 16 ? (double)to_bf16(t) : to_fp16(t)) * sc;
@@ -1252,6 +1256,7 @@ void orc_amg_free(orc_amg *h) {
         free(h->l1[q]);
         free(h->dinv[q]);
         free(h->av[q]);
+        free(h->rs[q]);
         free(h->vb[q]);
         free(h->vx[q]);
         free(h->vr[q]);
@@ -1270,6 +1275,19 @@ int orc_amg_level_agg(const orc_amg *h, int l, int32_t *out) {
     memcpy(out, h->agg[l], (size_t)h->A[l]->nrow * sizeof(int32_t));
     return 0;
 }
+
+/* The values the level's smoother and residual multiply by, in CSR order of
+ * the level matrix (FP64, or the FP32 / bf16 / fp16 storage value as a
+ * double), its row scales and its stored 1/D1. */
+int orc_amg_level_stored(const orc_amg *h, int l, double *av, double *rs, double *dinv) {
+    if (l < 0 || l >= h->nlev) return -1;
+    if (av) memcpy(av, h->av[l], (size_t)h->A[l]->nnz * sizeof(double));
+    if (rs) memcpy(rs, h->rs[l], (size_t)h->A[l]->nrow * sizeof(double));
+    if (dinv) memcpy(dinv, h->dinv[l], (size_t)h->A[l]->nrow * sizeof(double));
+    return 0;
+}
+
+int orc_amg_level_lowp(const orc_amg *h, int l) { return (l < 0 || l >= h->nlev) ? -1 : h->lowp[l]; }
 
 const ocsr *orc_amg_level_P(const orc_amg *h, int l) {
     if (l < 0 || l >= h->nlev) return NULL;

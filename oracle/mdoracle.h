@@ -108,6 +108,14 @@ const ocsr *orc_amg_level_A(const orc_amg *h, int l);
 int orc_amg_level_agg(const orc_amg *h, int l, int32_t *out);  /* -1 = not aggregated */
 int orc_amg_level_roots(const orc_amg *h, int l, int8_t *out);
 int orc_amg_level_l1(const orc_amg *h, int l, double *out);
+/* The level's stored operator as the V-cycle applies it: values in CSR order
+ * of orc_amg_level_A (each the FP32, or the bf16/fp16 value times its row
+ * scale, as a double), the row scales s_i (1 on levels not stored in
+ * bf16/fp16) and 1/D1 rounded to the vector precision.  Any pointer may be
+ * NULL. */
+int orc_amg_level_stored(const orc_amg *h, int l, double *av, double *rs, double *dinv);
+/* 16 / 17 when the level is stored in bf16 / fp16 with row scales, else 0. */
+int orc_amg_level_lowp(const orc_amg *h, int l);
 /* Prolongator of level l (fine rows x coarse columns) when smoothed; NULL otherwise. */
 const ocsr *orc_amg_level_P(const orc_amg *h, int l);
 int orc_amg_coarsest_dense(const orc_amg *h);  /* 1: the last level is a dense solve; 2: it has no

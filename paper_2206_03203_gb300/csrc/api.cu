@@ -550,6 +550,21 @@ int mds_precond_prolongator(mds_precond p, int block, int level, mds_csr *P) {
     return MDS_OK;
 }
 
+int mds_precond_level_storage(mds_precond p, int block, int level, int *value_type, const void **values,
+                              const float **row_scale, const void **dinv) {
+    if (!p || block < 0 || block > 1 || (block == 1 && !p->has_f)) return MDS_ERR_INVALID;
+    const Hierarchy &h = p->h[block];
+    if (level < 0 || level >= (int)h.lv.size()) return MDS_ERR_INVALID;
+    const Level &L = h.lv[level];
+    static const int code[] = {MDS_PREC_FP64, MDS_PREC_FP32, MDS_PREC_BF16, MDS_PREC_FP16};
+    const bool dense_last = level + 1 == (int)h.lv.size() && h.dense;
+    if (value_type) *value_type = code[L.vt];
+    if (values) *values = dense_last ? nullptr : L.vt == VT_F64 ? (const void *)L.A.vals() : L.vals_lp.p;
+    if (row_scale) *row_scale = L.rscale.p ? L.rscale.as<float>() : nullptr;
+    if (dinv) *dinv = L.dinv.p;
+    return MDS_OK;
+}
+
 }  // extern "C"
 
 namespace mds {

@@ -128,6 +128,9 @@ _SIGS = {
     "mds_precond_level": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(Csr), C.POINTER(C.c_void_p),
                                     C.POINTER(C.c_void_p)]),
     "mds_precond_prolongator": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(Csr)]),
+    "mds_precond_level_storage": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int),
+                                            C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                            C.POINTER(C.c_void_p)]),
     "mds_precond_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mds_vcycle": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "mds_spmv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -558,6 +561,30 @@ class Precond:
         P = Csr()
         self.ctx._check(lib().mds_precond_prolongator(self.h, block, level, C.byref(P)))
         return self.ctx.csr_to_host(P) if P.row_ptr else None
+
+    def level_storage_host(self, block: int, level: int):
+        """(value type, stored values in CSR order as float64 or None, row
+        scales or None, 1/D1) of a level, as its V-cycle applies them."""
+        vt = C.c_int()
+        vals, rs, dv = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        self.ctx._check(lib().mds_precond_level_storage(self.h, block, level, C.byref(vt), C.byref(vals),
+                                                        C.byref(rs), C.byref(dv)))
+        A, _, _ = self.level_host(block, level)
+        n, nnz = A.shape[0], A.nnz
+        v = None
+        if vals.value:
+            if vt.value == 64:
+                v = self.ctx.to_host(vals.value, nnz, np.float64)
+            elif vt.value == 32:
+                v = self.ctx.to_host(vals.value, nnz, np.float32).astype(np.float64)
+            elif vt.value == 16:
+                u = self.ctx.to_host(vals.value, nnz, np.uint16).astype(np.uint32) << 16
+                v = u.view(np.float32).astype(np.float64)
+            else:
+                v = self.ctx.to_host(vals.value, nnz, np.float16).astype(np.float64)
+        r = self.ctx.to_host(rs.value, n, np.float32).astype(np.float64) if rs.value else None
+        d = self.ctx.to_host(dv.value, n, np.float64 if vt.value == 64 else np.float32).astype(np.float64)
+        return vt.value, v, r, d
 
     def level_host(self, block: int, level: int):
         A = Csr()

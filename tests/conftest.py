@@ -13,6 +13,14 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: longer CPU test")
 
 
+def maxrel(x, ref):
+    """Element-wise agreement: max_i |x_i - ref_i| / max_i |ref_i| (a norm
+    ratio could hide a few wrong entries in small rows)."""
+    import numpy as np
+    x, ref = np.asarray(x), np.asarray(ref)
+    return float(np.max(np.abs(x - ref)) / np.max(np.abs(ref)))
+
+
 @pytest.fixture(scope="session")
 def oracle_mod():
     import oracle

@@ -19,6 +19,7 @@ import test_oracle_flux as T_flux
 import test_oracle_junction as T_junc
 import test_oracle_krylov as T_kry
 import test_oracle_normal_permeability as T_kn
+import test_oracle_precision as T_prec
 import test_oracle_schur_amg as T_amg
 import test_oracle_smoothers as T_sm
 from paper_2206_03203_gb300 import inputs
@@ -85,6 +86,21 @@ MUTATIONS = {
         "if (h->agg[l][i] >= 0) bc[h->agg[l][i]] += r[i];",
         "if (h->agg[l][i] >= 0 && (i & 1) == 0) bc[h->agg[l][i]] += r[i];",
         lambda o: T_amg.test_vcycle_two_grid_error_propagation(o, 0)),
+    # bf16 / fp16 row scales rounded down instead of up: 2^floor(log2 max|a_ij|)
+    "row scale exponent": (
+        "if (fr == 0.5) e -= 1;",
+        "e -= 1;",
+        lambda o: T_prec.test_row_scaled_storage_rule(o, 17, "rects3d-12")),
+    # the restricted right-hand side handed to the coarse level unrounded
+    "coarse rhs not rounded": (
+        "for (int64_t I = 0; I < nc; I++) bc[I] = rnd(bc[I], pv);",
+        "for (int64_t I = 0; I < nc; I++) bc[I] = bc[I];",
+        lambda o: T_prec.test_vcycle_rounding_points(o, 2, 32)),
+    # the smoothing residual rounded to FP32 before it is used
+    "extra rounding of the residual": (
+        "x[i] = rnd(x[i] + dv[i] * r[i], pv);",
+        "x[i] = rnd(x[i] + dv[i] * rnd(r[i], pv), pv);",
+        lambda o: T_prec.test_vcycle_rounding_points(o, 2, 32)),
     # Dirichlet faces of the matrix with half the boundary transmissibility
     "Dirichlet factor": (
         "tb[s] = (F * (2.0 * ki)) / h;",
