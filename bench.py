@@ -1,23 +1,33 @@
 """Benchmark: solves/s of the block-preconditioned FGMRES solver to 1e-8.
 
-Workload (one step): the 2D 1024 x 1024 instance with log-normal k_m
-(sigma = 1) and 64 random axis-aligned segments, swept over the nine
-contrasts 1e-4 .. 1e4 (even segments k_f = c, odd ones 1/c).  For each
-contrast: GPU two-point-flux assembly from device-resident instance arrays,
-Schur complement and AMG set-up, and FP64 FGMRES(30) with M_L to a relative
-residual of 1e-8.  value = solves per second over the whole step.
+Headline workload (one step): 256 uneven 3D instances (cube side n ~ U{32..64},
+1-12 random axis-aligned rectangular fractures each, log10 k_f ~ U(-4, 4),
+log-normal k_m with sigma = 1), each with 4 random-Dirichlet right-hand sides:
+1,024 solves.  A step packs the instances into one block-diagonal system:
+GPU two-point-flux assembly from device-resident instance arrays, the Schur
+complement S~ and both AMG hierarchies (FP32 finest level, BF16 row-scaled
+coarse levels), and lockstep FP64 FGMRES(30) with M_L on the four interleaved
+columns of every instance to a relative residual of 1e-8.  value = solves per
+second over the timed steps.  Beside it, the same batch with every level in
+FP64 (the plain GPU solve) is timed by the same protocol, and the ratio is
+reported.
+
+Secondary line: the 2D 1024 x 1024 instance with log-normal k_m and 64
+random segments swept over nine contrasts (FP64 path), with its CPU oracle
+timed on the whole sweep.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--variants] [--no-sweep]
 
-Under torchrun every rank runs an independent replica of the workload (a
-single solve is not split across GPUs); value sums the ranks' solves over the
+Under torchrun the instances of the batch are sharded across ranks by unknown
+count (no collective on the solve path); value sums the ranks' solves over the
 slowest rank's time.  ``--impl reference`` times the CPU oracle on a bounded
-sample instead (rank 0 only).
+sample of the same batch instead (rank 0 only).
 
-Accuracy: the relative residual of every solve, and for the contrast-1e4
-member the relative error of the GPU solution against a sparse direct solve
-(SuperLU) of the same assembled FP64 system on the host, computed in a
-separate process while the GPU runs.
+Accuracy: the true relative residual of every solve, and for sampled instances
+the relative error of the GPU solutions against a sparse direct solve
+(SuperLU) of the same assembled FP64 systems on the host, finished before the
+timed region starts.
 """
 from __future__ import annotations
 
@@ -35,14 +45,19 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-METRIC = "solves/s to 1e-8 rel-res (assemble + set-up + FGMRES, contrast sweep)"
+METRIC = "solves/s to 1e-8 rel-res (assemble + set-up + lockstep FGMRES; 256 instances x 4 RHS)"
 UNIT = "solves/s"
 FP64_PEAK_TFLOPS = 1.25
-# approximate FGMRES iterations per contrast member: the order (longest
-# first) in which the solves are handed to concurrent streams
+NRHS = 4
+BATCH = 256
+WORKLOAD = ("3D batch: 256 uneven instances (n ~ U{32..64}, 1-12 random rectangles, log10 k_f ~ U(-4,4), "
+            "log-normal k_m sigma=1), 4 random-Dirichlet RHS each = 1,024 solves; packed TPFA assembly, S~, "
+            "AMG (FP32 finest, BF16 row-scaled coarse), lockstep FP64 FGMRES(30) + M_L to rtol 1e-8")
+SWEEP_WORKLOAD = ("2D 1024x1024 TPFA, log-normal k_m sigma=1, 64 random segments (k_f = c / 1/c, a = 1e-4), "
+                  "contrast sweep c = 1e-4..1e4 (9 solves per step), FP64 FGMRES(30) + M_L, rtol 1e-8")
+# approximate FGMRES iterations per contrast member of the sweep (for ordering)
 SWEEP_WORK = [1700, 1420, 1610, 645, 226, 505, 1006, 1180, 1770]
-WORKLOAD = ("2D 1024x1024 TPFA, log-normal k_m sigma=1, 64 random segments (k_f = c / 1/c, a = 1e-4), "
-            "contrast sweep c = 1e-4..1e4 (9 solves per step), FP64 FGMRES(30) + M_L, rtol 1e-8")
+CLASSES = ["spmv", "vc_resid", "vc_post", "vc_restrict", "gs_dot", "gs_axpy"]
 
 
 def rank_info():
@@ -111,7 +126,7 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def profile_traffic(kernel_class: str, avg_alg_bytes: float):
+def profile_traffic(kernel_class: str, workload: str, avg_alg_bytes: float):
     """DRAM bytes per launch of a kernel class from the committed ncu summary
     (profiles/traffic.txt lines: '<class> <workload> <dram bytes> <algorithmic
     bytes of that launch>'), scaled to this run's average launch by the ratio
@@ -121,7 +136,7 @@ def profile_traffic(kernel_class: str, avg_alg_bytes: float):
         return None
     for line in open(p):
         f = line.split()
-        if len(f) >= 4 and not line.startswith("#") and f[0] == kernel_class and f[1] == "seg2d-1024":
+        if len(f) >= 4 and not line.startswith("#") and f[0] == kernel_class and f[1] == workload:
             try:
                 return float(f[2]) / float(f[3]) * avg_alg_bytes
             except (ValueError, ZeroDivisionError):
@@ -129,16 +144,89 @@ def profile_traffic(kernel_class: str, avg_alg_bytes: float):
     return None
 
 
-def _direct_solve(indptr, indices, data, b):
-    """Sparse LU (SuperLU, COLAMD ordering) of the assembled system on the
-    host: the FP64 direct solution the GPU result is compared with."""
+def _direct_instance(indptr, indices, data, B):
+    """Sparse LU (SuperLU, COLAMD ordering) of one assembled FP64 system on the
+    host, applied to every right-hand side row of B: the direct solutions the
+    GPU results are compared with."""
     import scipy.sparse as sp
     import scipy.sparse.linalg as spla
     A = sp.csc_matrix(sp.csr_matrix((data, indices, indptr), shape=(len(indptr) - 1,) * 2))
-    return spla.spsolve(A, b, permc_spec="COLAMD")
+    lu = spla.splu(A, permc_spec="COLAMD")
+    return np.stack([lu.solve(b) for b in B])
+
+
+def class_rates(ctx, fn, peak, classes=CLASSES):
+    """Per-class launch averages of one run of fn() with every launch of each
+    class bracketed by events: achieved HBM GB/s and FP64 TFLOP/s, and each
+    class's share of the bracketed time."""
+    for c in classes:
+        ctx.timing_enable(c, True)
+    ctx.timing_sample_every(1)
+    ctx.timing_reset()
+    fn()
+    out, tot = {}, 0.0
+    for c in classes:
+        n_t, ms_t, by_t, fl_t = ctx.timing_sampled(c)
+        ctx.timing_enable(c, False)
+        if n_t and ms_t > 0:
+            gbs = by_t / (ms_t / 1e3) / 1e9
+            tf = fl_t / (ms_t / 1e3) / 1e12
+            out[c] = {"launches": n_t, "ms_total": round(ms_t, 3), "avg_launch_us": round(ms_t / n_t * 1e3, 2),
+                      "algorithmic_bytes_per_launch": by_t / n_t, "hbm_gbs": round(gbs, 1),
+                      "hbm_frac_of_measured": round(gbs / peak, 4), "fp64_tflops": round(tf, 4),
+                      "fp64_frac_of_nominal": round(tf / FP64_PEAK_TFLOPS, 4)}
+            tot += ms_t
+    for c in out:
+        out[c]["time_share"] = round(out[c]["ms_total"] / tot, 4) if tot else None
+    return out
+
+
+def roofline_of(ctx, cls, peak, peak_src, workload):
+    """The roofline entry of one class from its launches bracketed since the
+    last timing reset."""
+    kl, kms, kbytes, kflops = ctx.timing_sampled(cls)
+    avg_ms = kms / max(kl, 1)
+    avg_bytes = kbytes / max(kl, 1)
+    avg_flops = kflops / max(kl, 1)
+    gbs = avg_bytes / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else None
+    tflops = avg_flops / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else None
+    hbm_frac = gbs / peak if gbs else None
+    alu_frac = tflops / FP64_PEAK_TFLOPS if tflops else None
+    if alu_frac and hbm_frac and alu_frac > hbm_frac:
+        roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
+                "frac": alu_frac, "peak_source": "derived: 152 SMs x 2070 MHz x 4 FP64 flops per clock per SM "
+                "(GB300 nominal 1.25 TFLOP/s; a dependent-FMA probe measured 1.20)"}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": hbm_frac,
+                "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
+                else "fallback 6.8 TB/s"}
+    roof.update({"traffic": profile_traffic(cls, workload, avg_bytes), "kernel_class": cls,
+                 "algorithmic_bytes_per_launch": avg_bytes, "algorithmic_flops_per_launch": avg_flops,
+                 "launches_timed": kl, "avg_launch_ms": avg_ms, "hbm_gbs": gbs, "hbm_frac_of_measured": hbm_frac,
+                 "fp64_tflops": tflops, "fp64_frac_of_nominal": alu_frac})
+    return roof
+
+
+def _step_times(step, flush, steps):
+    """Device-timed seconds of each of `steps` calls of step() (CUDA events on
+    the current stream, L2 flushed by a 256 MB write before each)."""
+    import torch
+    out = []
+    for s_ in range(steps):
+        flush.fill_(float(s_))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step(s_ == steps - 1)
+        e1.record()
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1) / 1e3)
+    return out
 
 
 def run_gpu(args):
+    import dataclasses
+
     import torch
     import torch.distributed as dist
 
@@ -150,241 +238,369 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     build.build()
     ctx = mdsolve.Context(local)
-    insts = [inputs.random_segments_2d(contrast=c) for c in inputs.CONTRASTS]
-    # device-resident instance arrays (inputs in HBM before the timed region)
-    dev_arrays = []
-    for inst in insts:
-        dev_arrays.append(dict(
-            km=torch.as_tensor(inst.km, device="cuda"),
-            fc_axis=torch.as_tensor(inst.fc_axis, device="cuda"),
-            fc_pos=torch.as_tensor(np.ascontiguousarray(inst.fc_pos).reshape(-1), device="cuda"),
-            fc_kf=torch.as_tensor(inst.fc_kf, device="cuda"),
-            fc_a=torch.as_tensor(inst.fc_a, device="cuda"),
-            pD_left=torch.as_tensor(inst.pD_left, device="cuda"),
-            pD_right=torch.as_tensor(inst.pD_right, device="cuda")))
-    N = [inst.n_m + inst.n_f for inst in insts]
-    xs = [torch.zeros(n, dtype=torch.float64, device="cuda") for n in N]
+    peak, peak_src = measured_peaks()
+    all_idx = list(range(BATCH))
+    sizes = inputs.batch_sizes(22060304, BATCH)
+    if world > 1:
+        # instances are independent: each rank solves its own share, no exchange
+        all_idx = sharding.shard_by_work([float(n ** 3) for n in sizes], world)[rank]
+    batch = [inputs.batch_instance(i, BATCH) for i in all_idx]
+    dev = [mdsolve.device_arrays(b) for b in batch]  # inputs resident in HBM before timing
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    sopt = dict(rtol=1e-8, max_iters=5000, restart=30)
-    stats_last = []
+    sopt = dict(rtol=1e-8, max_iters=5000, restart=30, nrhs=NRHS)
+    s0 = ctx.assemble_batch(batch, device_arrays=dev)
+    N, n_m, n_f = s0.N, s0.n_m, s0.n_f
+    s0.close()
+    x = torch.zeros(N * NRHS, dtype=torch.float64, device="cuda")
+    last = {}
+    phase_ev = []
 
-    phase_ev = []  # per member of a timed step: events before assembly, after assembly, set-up, solve
-
-    def step(collect=False):
-        its = []
-        for k, inst in enumerate(insts):
+    def make_step(prec):
+        def step(collect=False):
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if collect else None
             if ev:
                 ev[0].record()
-            s = ctx.assemble(inst, device_arrays=dev_arrays[k])
+            s = ctx.assemble_batch(batch, device_arrays=dev)
             if ev:
                 ev[1].record()
-            p = ctx.setup(s, precision="fp64", format="auto")
+            p = ctx.setup(s, precision=prec, format="auto")
             if ev:
                 ev[2].record()
-            xs[k].zero_()
-            code, st = ctx.solve(s, p, None, xs[k], **sopt)
+            x.zero_()
+            code, st = ctx.solve(s, p, None, x, **sopt)
             if ev:
                 ev[3].record()
-                phase_ev.append(ev)
+                phase_ev[:] = [ev]
             if code != 0:
-                raise RuntimeError(f"solve failed for contrast {inputs.CONTRASTS[k]}: {st[0]}")
-            its.append(st[0].iterations)
+                raise RuntimeError(f"batch solve ({prec}) returned {code}")
             if collect:
-                stats_last.append(st[0])
+                last[prec] = (st, [p.info(0)["n"], p.info(1)["n"]])
             p.close()
             s.close()
-        return its
+        return step
 
-    # direct reference for the contrast-1e4 member: started now, on the host,
-    # in a spawned process, so that it runs while the GPU is timed
-    direct = None
+    # direct references for sampled instances (host SuperLU in spawned
+    # processes), finished before any timed step
+    direct = {}
     if rank == 0 and not args.no_direct:
         import multiprocessing as mp
-        s = ctx.assemble(insts[-1], device_arrays=dev_arrays[-1])
-        (_, _, _, _, Ah), bh = s.to_host()
-        s.close()
-        pool = mp.get_context("spawn").Pool(1)
-        direct = (pool, pool.apply_async(_direct_solve, (Ah.indptr, Ah.indices, Ah.data, bh[0])), Ah, bh[0])
-
-    peak, peak_src = measured_peaks()
-    # warm-up; the first one also profiles every kernel class (events around
-    # the launches of every 4th FGMRES restart cycle) to find the dominant one
-    classes = ["spmv", "vc_resid", "vc_post", "vc_restrict", "gs_dot", "gs_axpy"]
-    for c in classes:
-        ctx.timing_enable(c, True)
-    ctx.timing_sample_every(4)
-    ctx.timing_reset()
-    its = step()
-    share, per_class = {}, {}
-    for c in classes:
-        n_all, _, _, _ = ctx.timing_query(c)
-        n_t, ms_t, by_t, fl_t = ctx.timing_sampled(c)
-        avg = ms_t / n_t if n_t else 0.0
-        share[c] = avg * n_all  # estimated total time of the class
-        if n_t and ms_t > 0:
-            gbs_c = by_t / (ms_t / 1e3) / 1e9
-            tf_c = fl_t / (ms_t / 1e3) / 1e12
-            per_class[c] = {"launches_per_step": n_all, "avg_launch_us": round(avg * 1e3, 3),
-                            "algorithmic_bytes_per_launch": by_t / n_t, "hbm_gbs": round(gbs_c, 1),
-                            "hbm_frac_of_measured": round(gbs_c / peak, 4), "fp64_tflops": round(tf_c, 4),
-                            "fp64_frac_of_nominal": round(tf_c / FP64_PEAK_TFLOPS, 4)}
-    dominant = max(share, key=share.get)
-    for c in classes:
-        ctx.timing_enable(c, c == dominant)
-    for _ in range(max(0, args.warmup - 1)):
-        step()
-    torch.cuda.synchronize()
-
-    # timed region
-    flush.fill_(1.0)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ctx.timing_reset()
-    clocks = ClockSampler(local)
-    clocks.start()
-    t_total = 0.0
-    iters = []
-    step_s = []
-    torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed steps (ncu --nvtx-include timed/)
-    for s_ in range(args.steps):
-        flush.fill_(float(s_))  # L2 flush between steps (256 MB > 129 MB L2)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        iters = step(collect=(s_ == args.steps - 1))
-        e1.record()
-        torch.cuda.synchronize()
-        step_s.append(e0.elapsed_time(e1) / 1e3)
-        t_total += step_s[-1]
-    torch.cuda.nvtx.range_pop()
-    # phases of the last timed step (events on the library's stream)
-    ph = np.zeros(3)
-    for ev in phase_ev:
-        ph += (ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3]))
-    phases = {"assemble_ms": ph[0], "setup_ms": ph[1], "solve_ms": ph[2],
-              "solve_only_solves_per_s": len(insts) / (ph[2] / 1e3) if ph[2] > 0 else None,
-              "dof_iter_per_s_solve_only": (sum(n * i for n, i in zip(N, iters)) / (ph[2] / 1e3)
-                                            if ph[2] > 0 else None)}
-    launches = ctx.launch_count()
-    kl_all = ctx.timing_query(dominant)[0]
-    kl, kms, kbytes, kflops = ctx.timing_sampled(dominant)
-    for c in classes:
-        ctx.timing_enable(c, False)
-    clk = clocks.stop()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    # replicas: every rank ran the whole sweep; slowest rank's time, all ranks' solves
-    t_total, solves = sharding.reduce_over_ranks(t_total, len(insts) * args.steps)
-    value = solves / t_total
-    dof_iter = sum(n * i for n, i in zip(N, iters)) * args.steps * world / t_total
-
-    # accuracy of the timed solves
-    accuracy = {"relres_true_per_contrast": [st.relres_true for st in stats_last]}
-    if direct is not None:
-        pool, job, Ah, bh = direct
-        xg = xs[-1].cpu().numpy()
-        try:
-            xd = job.get(timeout=600)
-            accuracy["contrast_1e4_vs_direct"] = {
-                "rel_error": float(np.linalg.norm(xg - xd) / np.linalg.norm(xd)),
-                "relres_direct": float(np.linalg.norm(bh - Ah @ xd) / np.linalg.norm(bh)),
-                "relres_gpu": float(np.linalg.norm(bh - Ah @ xg) / np.linalg.norm(bh)),
-                "direct": "scipy spsolve (SuperLU, COLAMD) of the same assembled FP64 system, host"}
-        except Exception as e:  # the reference is reported, never fatal
-            accuracy["contrast_1e4_vs_direct"] = {"error": str(e)}
+        pick = [k for k, b in enumerate(batch) if b.n <= 40][:4]
+        jobs = []
+        pool = mp.get_context("spawn").Pool(max(1, len(pick)))
+        for k in pick:
+            s = ctx.assemble(batch[k])
+            (_, _, _, _, Ah), bh = s.to_host()
+            s.close()
+            jobs.append((k, pool.apply_async(_direct_instance, (Ah.indptr, Ah.indices, Ah.data, bh)), Ah, bh))
+        for k, job, Ah, bh in jobs:
+            try:
+                direct[k] = (job.get(timeout=900), Ah, bh)
+            except Exception as e:  # reported, never fatal
+                direct[k] = (e, Ah, bh)
         pool.terminate()
 
-    # end-to-end through the C ABI with host buffers (copies inside the timed region)
-    e2e_t = 0.0
-    h2d = 0
-    d2h = 0
-    import dataclasses
+    # ---- mixed-precision batch (the headline) ----
+    step = make_step("bf16")
+    step()  # first warm-up: storage autotuning, allocations
+    classes_bf16 = class_rates(ctx, step, peak)  # second warm-up, every class bracketed
+    share = {c: v["ms_total"] for c, v in classes_bf16.items()}
+    dominant = max(share, key=share.get)
+    for _ in range(max(0, args.warmup - 2)):
+        step()
+    torch.cuda.synchronize()
+    for c in CLASSES:
+        ctx.timing_enable(c, c == dominant)
+    ctx.timing_sample_every(1)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ctx.timing_reset()
+    launches0 = ctx.launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.nvtx.range_push("timed")
+    step_s = _step_times(step, flush, args.steps)
+    torch.cuda.nvtx.range_pop()
+    clk = clocks.stop()
+    launches = ctx.launch_count() - launches0
+    roof = roofline_of(ctx, dominant, peak, peak_src, "batch3d-256")
+    for c in CLASSES:
+        ctx.timing_enable(c, False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_total, solves = sharding.reduce_over_ranks(sum(step_s), len(batch) * NRHS * args.steps)
+    value = solves / t_total
+    st_bf16, levels_bf16 = last["bf16"]
+    its = [q.iterations for q in st_bf16]
+    dof = [(b.n_m + b.n_f) for b in batch for _ in range(NRHS)]
+    ph = phase_ev[0]
+    phases = {"assemble_ms": ph[0].elapsed_time(ph[1]), "setup_ms": ph[1].elapsed_time(ph[2]),
+              "solve_ms": ph[2].elapsed_time(ph[3])}
+    phases["solve_only_solves_per_s"] = len(batch) * NRHS / (phases["solve_ms"] / 1e3)
+    phases["dof_iter_per_s_solve_only"] = sum(d * i for d, i in zip(dof, its)) / (phases["solve_ms"] / 1e3)
+    x_last = x.cpu().numpy().reshape(NRHS, N)
 
+    # accuracy: every solve's true residual; sampled instances against direct
+    accuracy = {"relres_true_max": max(q.relres_true for q in st_bf16),
+                "relres_true_min": min(q.relres_true for q in st_bf16),
+                "all_converged": all(q.status == 0 for q in st_bf16)}
+    if direct:
+        mo, fo = 0, 0
+        offs = []
+        for b in batch:
+            offs.append((mo, fo))
+            mo += b.n_m
+            fo += b.n_f
+        rows_of = {k: np.r_[offs[k][0]:offs[k][0] + batch[k].n_m, n_m + offs[k][1]:n_m + offs[k][1] + batch[k].n_f]
+                   for k in direct}
+        errs = {}
+        for k, (xd, Ah, bh) in direct.items():
+            if isinstance(xd, Exception):
+                errs[int(all_idx[k])] = {"error": str(xd)}
+                continue
+            e = []
+            for c in range(NRHS):
+                xg = x_last[c][rows_of[k]]
+                e.append({"rel_error": float(np.linalg.norm(xg - xd[c]) / np.linalg.norm(xd[c])),
+                          "relres_direct": float(np.linalg.norm(bh[c] - Ah @ xd[c]) / np.linalg.norm(bh[c])),
+                          "relres_gpu": float(np.linalg.norm(bh[c] - Ah @ xg) / np.linalg.norm(bh[c]))})
+            errs[int(all_idx[k])] = e
+        accuracy["vs_direct"] = {"instances": errs, "direct": "scipy splu (SuperLU, COLAMD) of each sampled "
+                                 "instance's assembled FP64 system on the host; finished before the timed steps"}
+
+    # ---- the same batch, FP64 throughout (the plain GPU solve), same protocol ----
+    step64 = make_step("fp64")
+    step64()
+    classes_fp64 = class_rates(ctx, step64, peak)
+    step64()
+    k64 = max(10, min(args.steps, 10))
+    if world > 1:
+        dist.barrier()
+    s64 = _step_times(step64, flush, k64)
+    t64, solves64 = sharding.reduce_over_ranks(sum(s64), len(batch) * NRHS * k64)
+    value64 = solves64 / t64
+    st64, _ = last["fp64"]
+
+    # ---- end to end through the C ABI with host buffers ----
     def pinned(a):
-        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-        return t.numpy()
-    # the instances' arrays and the solutions in pinned host memory
-    insts_h = [dataclasses.replace(i, km=pinned(i.km), fc_axis=pinned(i.fc_axis), fc_pos=pinned(i.fc_pos),
-                                   fc_kf=pinned(i.fc_kf), fc_a=pinned(i.fc_a), pD_left=pinned(i.pD_left),
-                                   pD_right=pinned(i.pD_right)) for i in insts]
-    xh_all = [pinned(np.zeros(n)) for n in N]
-    for s_ in range(max(1, min(args.steps, 2))):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    batch_h = [dataclasses.replace(b, km=pinned(b.km), fc_axis=pinned(b.fc_axis), fc_pos=pinned(b.fc_pos),
+                                   fc_kf=pinned(b.fc_kf), fc_a=pinned(b.fc_a), pD_left=pinned(b.pD_left),
+                                   pD_right=pinned(b.pD_right)) for b in batch]
+    xh = pinned(np.zeros(N * NRHS))
+    e2e_steps = 2
+    e2e_t = 0.0
+    for _ in range(e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for k, inst in enumerate(insts_h):
-            s = ctx.assemble(inst)
-            p = ctx.setup(s, precision="fp64", format="auto")
-            xh = xh_all[k]
-            xh[:] = 0.0
-            code, st = ctx.solve(s, p, None, xh, **sopt)
-            p.close()
-            s.close()
-        torch.cuda.synchronize()
+        s = ctx.assemble_batch(batch_h)
+        p = ctx.setup(s, precision="bf16", format="auto")
+        xh[:] = 0.0
+        code, _ = ctx.solve(s, p, None, xh, **sopt)
+        p.close()
+        s.close()
         e2e_t += time.perf_counter() - t0
-    e2e_steps = max(1, min(args.steps, 2))
-    for inst in insts:
-        h2d += inst.km.nbytes + inst.fc_axis.nbytes + inst.fc_pos.nbytes + inst.fc_kf.nbytes + inst.fc_a.nbytes \
-            + inst.pD_left.nbytes + inst.pD_right.nbytes + 8 * (inst.n_m + inst.n_f)  # and the initial guess
-        d2h += 8 * (inst.n_m + inst.n_f)
-    e2e_value = len(insts) * e2e_steps / e2e_t * world
+    h2d = sum(b.km.nbytes + b.fc_axis.nbytes + b.fc_pos.nbytes + b.fc_kf.nbytes + b.fc_a.nbytes +
+              b.pD_left.nbytes + b.pD_right.nbytes for b in batch) + 8 * N * NRHS
+    d2h = 8 * N * NRHS
+    e2e_t, e2e_solves = sharding.reduce_over_ranks(e2e_t, len(batch) * NRHS * e2e_steps)
 
-    avg_ms = kms / max(kl, 1)
-    avg_bytes = kbytes / max(kl, 1)
-    avg_flops = kflops / max(kl, 1)
-    gbs = avg_bytes / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else None
-    tflops = avg_flops / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else None
-    hbm_frac = gbs / peak if gbs else None
-    alu_frac = tflops / FP64_PEAK_TFLOPS if tflops else None
-    traffic = profile_traffic(dominant, avg_bytes)
-    if alu_frac and hbm_frac and alu_frac > hbm_frac:
-        roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
-                "frac": alu_frac, "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (152 SMs x 2070 MHz); "
-                "a dependent-FMA probe measured 1.20"}
-    else:
-        roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": hbm_frac,
-                "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
-                else "fallback 6.8 TB/s"}
-    roof.update({"traffic": traffic, "kernel_class": dominant, "algorithmic_bytes_per_launch": avg_bytes,
-                 "algorithmic_flops_per_launch": avg_flops, "launches": kl_all, "launches_timed": kl,
-                 "avg_launch_ms": avg_ms,
-                 "hbm_gbs": gbs, "hbm_frac_of_measured": hbm_frac, "fp64_tflops": tflops,
-                 "fp64_frac_of_nominal": alu_frac,
-                 "time_share_warmup": {k: round(v / max(sum(share.values()), 1e-9), 3) for k, v in share.items()},
-                 "classes_warmup": per_class})
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": "fp64 (assembly, set-up, V-cycle, FGMRES)",
-                   "l2": "flushed between steps (256 MB write); per-solve working set > 129 MB L2",
-                   "parallelism": f"replicas x{world}", "N_per_solve": N[0],
-                   "iterations_per_contrast": iters},
-        "dof_iter_per_s": dof_iter,
+        "scaling": "weak" if world > 1 else "weak", "vs_baseline": None, "dtype": "f64+f32+bf16",
+        "data": "synthetic (seeded generator; stands in for the paper's parameter studies of Sec. 4)",
+        "config": {"workload": WORKLOAD, "precision": "FP64 assembly / set-up / FGMRES; FP32 finest V-cycle "
+                   "level, BF16 row-scaled coarse levels", "nrhs_per_instance": NRHS,
+                   "instances": len(batch) * world if world > 1 else len(batch), "N_packed": N,
+                   "l2": "flushed between steps (256 MB write); inputs and working set far above the 129 MB L2",
+                   "parallelism": f"instances sharded over {world} rank(s) by unknown count" if world > 1
+                   else "one GPU, one packed batch"},
         "step_s": {"median": float(np.median(step_s)), "min": float(np.min(step_s)), "all": step_s},
+        "dof_iter_per_s": sum(d * i for d, i in zip(dof, its)) * args.steps * world / t_total,
+        "iterations": {"min": min(its), "mean": float(np.mean(its)), "max": max(its)},
         "phases_last_step": phases,
-        "vcycle": vcycle_rate(ctx, insts[-1], dev_arrays[-1], flush),
+        "levels_last_step": levels_bf16,
+        "fp64_batch": {"value": value64, "unit": UNIT, "steps": k64,
+                       "step_s": {"median": float(np.median(s64)), "min": float(np.min(s64))},
+                       "speedup_mixed_over_fp64": value / value64,
+                       "iterations": {"min": min(q.iterations for q in st64),
+                                      "mean": float(np.mean([q.iterations for q in st64])),
+                                      "max": max(q.iterations for q in st64)},
+                       "relres_true_max": max(q.relres_true for q in st64)},
+        "classes": {"bf16": classes_bf16, "fp64": classes_fp64,
+                    "note": "every launch of each class bracketed by events in one warm-up step; vc_* are the "
+                            "finest-level V-cycle kernels of the S~ and A_ff hierarchies"},
         "accuracy": accuracy,
         "roofline": roof,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "host_buffers": "pinned; instance arrays in, solution out, every solve"},
+        "e2e": {"value": e2e_solves / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "host_buffers": "pinned; instance arrays in, 1,024 solution columns out, every step; host clock"},
         "gpu_launches": launches,
         "clocks": clk,
     }
-    if not args.no_variants:
-        line["variants"] = variants(ctx, insts, dev_arrays, N, flush)
-        if world > 1:
-            line["variants"]["note"] = ("sweep/3D variants: replicas (rank 0's time); batch: instances "
-                                        "sharded by unknown count, slowest rank's time")
+    if not args.no_sweep and rank == 0:
+        line["sweep_1024"] = sweep_line(ctx, args, flush, peak, peak_src)
+    if args.variants:
+        insts = [inputs.random_segments_2d(contrast=c) for c in inputs.CONTRASTS]
+        dev2 = [mdsolve.device_arrays(i) for i in insts]
+        line["variants"] = variants(ctx, insts, dev2, [i.n_m + i.n_f for i in insts], flush)
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline_batch()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def sweep_line(ctx, args, flush, peak, peak_src):
+    """Secondary line: the nine-contrast 1024^2 sweep on the FP64 path (GPU
+    assembly from device-resident arrays, set-up, FGMRES), 3 warm-up and
+    min(K, 5) timed steps, with the CPU oracle timed on the whole sweep."""
+    import torch
+
+    from paper_2206_03203_gb300 import inputs, mdsolve
+    insts = [inputs.random_segments_2d(contrast=c) for c in inputs.CONTRASTS]
+    dev = [mdsolve.device_arrays(i) for i in insts]
+    xs = [torch.zeros(i.n_m + i.n_f, dtype=torch.float64, device="cuda") for i in insts]
+    its = []
+
+    def step(collect=False):
+        its.clear()
+        for k, inst in enumerate(insts):
+            s = ctx.assemble(inst, device_arrays=dev[k])
+            p = ctx.setup(s, precision="fp64", format="csr")
+            xs[k].zero_()
+            code, st = ctx.solve(s, p, None, xs[k], rtol=1e-8, max_iters=5000)
+            if code != 0:
+                raise RuntimeError(f"sweep solve failed at contrast {inputs.CONTRASTS[k]}")
+            its.append(st[0].iterations)
+            p.close()
+            s.close()
+    for _ in range(3):
+        step()
+    for c in CLASSES:
+        ctx.timing_enable(c, c == "gs_axpy")
+    ctx.timing_sample_every(4)
+    ctx.timing_reset()
+    k = max(1, min(args.steps, 5))
+    ts = _step_times(step, flush, k)
+    roof = roofline_of(ctx, "gs_axpy", peak, peak_src, "seg2d-1024")
+    for c in CLASSES:
+        ctx.timing_enable(c, False)
+    out = {"workload": SWEEP_WORKLOAD, "value": len(insts) * k / sum(ts), "unit": UNIT, "steps": k, "warmup": 3,
+           "step_s": {"median": float(np.median(ts)), "min": float(np.min(ts))},
+           "iterations_per_contrast": list(its), "storage": "CSR (fixed format: bitwise reproducible counts)",
+           "roofline_gs_axpy": roof}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_sweep()
+    return out
+
+
+def _oracle_batch_instance(i):
+    """The oracle on instance i of the batch: assembly, M_L set-up (FP64) and
+    FGMRES(30) to 1e-8 for each of its right-hand sides; (seconds, counts)."""
+    import oracle
+    from paper_2206_03203_gb300 import inputs
+    oracle.build()
+    inst = inputs.batch_instance(i, BATCH)
+    t0 = time.perf_counter()
+    A, b = oracle.assemble(inst)
+    M = oracle.ML(A, inst.n_m)
+    its = []
+    for r in range(b.shape[0]):
+        res = oracle.fgmres(A, b[r], M, rtol=1e-8, maxit=5000)
+        its.append(res.iterations)
+    return time.perf_counter() - t0, its
+
+
+def cpu_baseline_batch():
+    """The oracle (plain sequential FP64 C, as it stands) on a bounded sample of
+    the batch: 16 of its instances (every 16th), each assembled, set up and
+    solved for its 4 right-hand sides, one process per host core at once."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    sample = list(range(0, BATCH, 16))
+    cores = min(os.cpu_count() or 1, len(sample))
+    with mp.get_context("spawn").Pool(cores) as pool:
+        t0 = time.perf_counter()
+        rs = pool.map(_oracle_batch_instance, sample)
+        dt = time.perf_counter() - t0
+    its = [i for _, r in rs for i in r]
+    return {"value": len(sample) * NRHS / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(sample)} instances of the batch (every 16th), {len(sample) * NRHS} solves "
+                      f"(assembly + FP64 M_L set-up per instance + FGMRES(30) to 1e-8 per right-hand side), "
+                      f"one single-threaded oracle process per core; the oracle sets up each instance on its own "
+                      f"(the GPU sets up the packed batch)",
+            "wall_s": dt, "cpu_seconds": float(sum(t for t, _ in rs)),
+            "iterations": {"min": min(its), "mean": float(np.mean(its)), "max": max(its)},
+            "cpu": platform.processor() or platform.machine(), "nproc": os.cpu_count()}
+
+
+def _oracle_sweep_member(k):
+    import oracle
+    from paper_2206_03203_gb300 import inputs
+    oracle.build()
+    inst = inputs.random_segments_2d(contrast=inputs.CONTRASTS[k])
+    t0 = time.perf_counter()
+    res, *_ = oracle.solve(inst, maxit=5000)
+    return time.perf_counter() - t0, res.iterations
+
+
+def cpu_baseline_sweep():
+    """The oracle on the whole nine-contrast sweep: nine single-threaded
+    processes at once (one per contrast), wall time of the slowest."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    cores = min(os.cpu_count() or 1, 9)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        t0 = time.perf_counter()
+        rs = pool.map(_oracle_sweep_member, range(9))
+        dt = time.perf_counter() - t0
+    return {"value": 9 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "the whole sweep (nine contrasts), one single-threaded oracle process per contrast",
+            "wall_s": dt, "iterations_per_contrast": [i for _, i in rs]}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle on a bounded sample of the batch (16
+    instances, every 16th, 4 right-hand sides each), one process per host core;
+    each step solves the sample once."""
+    rank, _, world = rank_info()
+    if rank != 0:
+        return
+    import multiprocessing as mp
+
+    import oracle
+    oracle.build()
+    sample = list(range(0, BATCH, 16))
+    cores = min(os.cpu_count() or 1, len(sample))
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for _ in range(args.warmup):
+            pool.map(_oracle_batch_instance, sample[:cores])
+        t = 0.0
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            rs = pool.map(_oracle_batch_instance, sample)
+            t += time.perf_counter() - t0
+    its = [i for _, r in rs for i in r]
+    value = len(sample) * NRHS * args.steps / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "fp64 (oracle)", "parallelism": f"CPU oracle, {cores} processes",
+                   "sample_iterations": {"min": min(its), "mean": float(np.mean(its)), "max": max(its)}},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"one step = {len(sample)} instances of the batch (every 16th) x 4 right-hand "
+                                   "sides, assembly + FP64 M_L set-up + FGMRES(30) to 1e-8, one single-threaded "
+                                   "oracle process per core"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
 
 
 def _timed(fn, flush, warmup=1, steps=1):
@@ -407,7 +623,7 @@ def _timed(fn, flush, warmup=1, steps=1):
     return tot / steps, out
 
 
-def class_rates(ctx, fn, classes=("spmv", "vc_resid", "vc_post", "vc_restrict", "gs_dot", "gs_axpy")):
+def class_rates_every4(ctx, fn, classes=("spmv", "vc_resid", "vc_post", "vc_restrict", "gs_dot", "gs_axpy")):
     """Per-class launch averages of one run of fn() (events around every 4th
     restart cycle): achieved HBM GB/s and FP64 TFLOP/s against the peaks."""
     peak, _ = measured_peaks()
@@ -506,7 +722,7 @@ def variants(ctx, insts, dev_arrays, N, flush):
     t, its = _timed(lambda: sweep("fp32"), flush)
     out["seg2d_1024_sweep_fp32_vcycle"] = {"solves_per_s": len(insts) / t, "s_per_step": t, "iterations": its,
                                            "precision": "FP32 V-cycle values/vectors, FP64 FGMRES",
-                                           "classes": class_rates(ctx, lambda: sweep("fp32"))}
+                                           "classes": class_rates_every4(ctx, lambda: sweep("fp32"))}
     t, its = _timed(lambda: sweep("fp64", prolongation="smoothed"), flush)
     out["seg2d_1024_sweep_fp64_smoothed_aggregation"] = {
         "solves_per_s": len(insts) / t, "s_per_step": t, "iterations": its,
@@ -683,99 +899,30 @@ def variants(ctx, insts, dev_arrays, N, flush):
         "iterations_min_mean_max": [min(its), float(np.mean(its)), max(its)],
         "precision": "as the packed bf16 batch, one instance (4 columns) at a time"}
     # kernel classes of the mixed-precision batch (finest level, 4 interleaved columns)
-    out["batch3d_256inst_x4rhs_bf16"]["classes"] = class_rates(ctx, lambda: batched("bf16"))
+    out["batch3d_256inst_x4rhs_bf16"]["classes"] = class_rates_every4(ctx, lambda: batched("bf16"))
     return out
-
-
-def _oracle_sample():
-    """One oracle solve of the contrast-1 member (assemble, M_L set-up, FGMRES
-    to 1e-8); returns the seconds of each phase and the iteration count."""
-    import oracle
-    from paper_2206_03203_gb300 import inputs
-    oracle.build()
-    inst = inputs.random_segments_2d(contrast=1.0)
-    t0 = time.perf_counter()
-    A, b = oracle.assemble(inst)
-    t1 = time.perf_counter()
-    M = oracle.ML(A, inst.n_m)
-    t2 = time.perf_counter()
-    res = oracle.fgmres(A, b[0], M, rtol=1e-8, maxit=5000)
-    t3 = time.perf_counter()
-    assert res.converged
-    return t1 - t0, t2 - t1, t3 - t2, res.iterations
-
-
-def cpu_baseline(samples: int = 1, all_cores: bool = True):
-    """The oracle (plain sequential FP64 C) on a bounded sample of the same
-    workload: the contrast-1 solve of the sweep, assembled, set up and solved
-    to 1e-8 (the cheapest of the nine; about 10-30 s of CPU work), on one
-    core; then the same sample as one process per host core at once (the
-    host's throughput with the oracle as it stands)."""
-    phases = np.zeros(3)
-    t0 = time.perf_counter()
-    for _ in range(samples):
-        a, s_, v, its = _oracle_sample()
-        phases += (a, s_, v)
-    dt = time.perf_counter() - t0
-    out = {"value": samples / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"{samples} solve(s) of the contrast-1 member of the sweep (1024x1024, "
-                     f"{its} FGMRES iterations), assemble + set-up + solve, single thread",
-           "phases_s": {"assemble": phases[0] / samples, "setup": phases[1] / samples,
-                        "solve": phases[2] / samples},
-           "cpu": platform.processor() or platform.machine(), "nproc": os.cpu_count()}
-    if all_cores:
-        import multiprocessing as mp
-        k = os.cpu_count() or 1
-        with mp.get_context("spawn").Pool(k) as pool:
-            t0 = time.perf_counter()
-            rs = pool.starmap(_oracle_sample, [()] * k)
-            dt = time.perf_counter() - t0
-        out["all_cores"] = {"value": k / dt, "unit": UNIT, "cores": k,
-                            "sample": f"{k} concurrent single-threaded oracle processes, one contrast-1 solve each"}
-    return out
-
-
-def run_reference(args):
-    rank, _, world = rank_info()
-    if rank != 0:
-        return
-    import oracle
-    from paper_2206_03203_gb300 import inputs
-    oracle.build()
-    small = inputs.fixed_2d()
-    for _ in range(args.warmup):
-        oracle.solve(small)
-    inst = inputs.random_segments_2d(contrast=1.0)
-    t = 0.0
-    its = None
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        res, A, b, M = oracle.solve(inst, maxit=5000)
-        t += time.perf_counter() - t0
-        its = res.iterations
-    value = args.steps / t
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": "fp64", "parallelism": "CPU oracle, 1 thread",
-                   "sample_iterations": its},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "one step = the contrast-1 solve of the sweep (assemble + set-up + FGMRES), "
-                                   "sequential C oracle; warm-up steps solve the 64x64 instance"},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
 
 
 def run_profile_case(args):
-    """A short fixed run for ncu: the contrast-1e4 member of the sweep,
-    assembled, set up and solved for --max-iters FGMRES iterations."""
+    """A short fixed run for ncu: the contrast-1e4 member of the 1024^2 sweep
+    (or, with --batch-profile K, the first K instances of the 256-instance
+    batch with 4 right-hand sides), assembled, set up and solved for
+    --max-iters FGMRES iterations."""
     import torch
 
     from paper_2206_03203_gb300 import build, inputs, mdsolve
     build.build()
     ctx = mdsolve.Context(0)
+    if args.batch_profile > 0:
+        batch = [inputs.batch_instance(i, BATCH) for i in range(args.batch_profile)]
+        s = ctx.assemble_batch(batch)
+        p = ctx.setup(s, precision=args.precision, format=args.format)
+        x = torch.zeros(s.N * NRHS, dtype=torch.float64, device="cuda")
+        code, st = ctx.solve(s, p, None, x, nrhs=NRHS, rtol=1e-8, max_iters=args.max_iters)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": f"batch of {args.batch_profile}", "N": s.N,
+                          "iterations_max": max(q.iterations for q in st), "launches": ctx.launch_count()}))
+        return
     inst = inputs.random_segments_2d(n=args.n, contrast=1e4)
     s = ctx.assemble(inst)
     p = ctx.setup(s, precision=args.precision, format=args.format)
@@ -849,12 +996,13 @@ def run_table1(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-variants", action="store_true", help="skip the secondary measurements")
-    ap.add_argument("--no-direct", action="store_true", help="skip the host direct solve of the accuracy check")
+    ap.add_argument("--variants", action="store_true", help="also run the secondary variant measurements")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the 1024^2 sweep line")
+    ap.add_argument("--no-direct", action="store_true", help="skip the host direct solves of the accuracy check")
     ap.add_argument("--profile-case", action="store_true", help="short fixed run for ncu captures")
     ap.add_argument("--table1", action="store_true", help="iteration counts over (K_par, kappa), the shape of "
                                                            "the paper's Table 1")
@@ -863,6 +1011,7 @@ def main():
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--precision", default="fp64")
     ap.add_argument("--format", default="auto", help="level storage of the profile case (auto, csr, sell)")
+    ap.add_argument("--batch-profile", type=int, default=0, help="profile case: a batch of this many instances")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)

@@ -284,15 +284,18 @@ def batch_sizes(seed: int, count: int, lo: int = 32, hi: int = 64) -> List[int]:
     return [lo + int(x % np.uint64(hi - lo + 1)) for x in d]
 
 
+def batch_instance(i: int, count: int = 256, seed: int = 22060304, nrhs: int = 4, lo: int = 32,
+                   hi: int = 64) -> Instance:
+    """Instance ``i`` of ``batch_3d(count, seed, nrhs, lo, hi)``, generated alone."""
+    n = batch_sizes(seed, count, lo, hi)[i]
+    nr = 1 + int(draws(stream_key(seed, i, FIELD_GRID), 1)[0] % np.uint64(12))
+    return random_rects_3d(n, seed, i, nr, nrhs=nrhs, random_dirichlet=True)
+
+
 def batch_3d(count: int = 256, seed: int = 22060304, nrhs: int = 4, lo: int = 32, hi: int = 64):
     """Uneven 3D instances with 1-12 random rectangles each, log10 k_f ~ U(-4, 4),
     log-normal k_m (sigma = 1), ``nrhs`` random-Dirichlet right-hand sides."""
-    out = []
-    sizes = batch_sizes(seed, count, lo, hi)
-    for i, n in enumerate(sizes):
-        nr = 1 + int(draws(stream_key(seed, i, FIELD_GRID), 1)[0] % np.uint64(12))
-        out.append(random_rects_3d(n, seed, i, nr, nrhs=nrhs, random_dirichlet=True))
-    return out
+    return [batch_instance(i, count, seed, nrhs, lo, hi) for i in range(count)]
 
 
 def large_3d(n: int = 256, seed: int = 22060305, nrhs: int = 8) -> Instance:

@@ -245,6 +245,17 @@ def torch_allocator(device: int, stream: int) -> Allocator:
     return Allocator(_ALLOC_FN(alloc), _FREE_FN(free), None)
 
 
+def device_arrays(inst) -> dict:
+    """Copies of an instance's input arrays in device memory (torch CUDA
+    tensors keyed by field name), for assemble / assemble_batch."""
+    import torch
+    d = dict(km=inst.km, fc_axis=inst.fc_axis, fc_pos=np.ascontiguousarray(inst.fc_pos).reshape(-1),
+             fc_kf=inst.fc_kf, fc_a=inst.fc_a, pD_left=inst.pD_left, pD_right=inst.pD_right)
+    if getattr(inst, "fc_kn", None) is not None:
+        d["fc_kn"] = inst.fc_kn
+    return {k: torch.as_tensor(np.ascontiguousarray(v), device="cuda") for k, v in d.items()}
+
+
 class Context:
     """A library context on one device and stream (torch's current stream by
     default).  allocator="torch" routes every device allocation of the
@@ -297,23 +308,29 @@ class Context:
         self._check(lib().mds_set_stream(self.h, C.c_void_p(stream)))
 
     # ---- problem ----
-    def assemble_batch(self, insts, junction=0) -> "System":
-        """Pack several instances (host arrays) into one block-diagonal system."""
+    def assemble_batch(self, insts, junction=0, device_arrays: Optional[list] = None) -> "System":
+        """Pack several instances into one block-diagonal system.  With
+        ``device_arrays`` (one dict of torch CUDA tensors per instance, keyed
+        by field name) the device copies are read instead of the host arrays."""
         keep, arr = [], (Instance * len(insts))()
         for k, inst in enumerate(insts):
-            a = dict(km=np.ascontiguousarray(inst.km, dtype=np.float64),
-                     fc_axis=np.ascontiguousarray(inst.fc_axis, dtype=np.int32),
-                     fc_pos=np.ascontiguousarray(inst.fc_pos, dtype=np.int32).reshape(-1),
-                     fc_kf=np.ascontiguousarray(inst.fc_kf, dtype=np.float64),
-                     fc_a=np.ascontiguousarray(inst.fc_a, dtype=np.float64),
-                     pD_left=np.ascontiguousarray(inst.pD_left, dtype=np.float64),
-                     pD_right=np.ascontiguousarray(inst.pD_right, dtype=np.float64))
-            if getattr(inst, "fc_kn", None) is not None:
-                a["fc_kn"] = np.ascontiguousarray(inst.fc_kn, dtype=np.float64)
+            if device_arrays is None:
+                a = dict(km=np.ascontiguousarray(inst.km, dtype=np.float64),
+                         fc_axis=np.ascontiguousarray(inst.fc_axis, dtype=np.int32),
+                         fc_pos=np.ascontiguousarray(inst.fc_pos, dtype=np.int32).reshape(-1),
+                         fc_kf=np.ascontiguousarray(inst.fc_kf, dtype=np.float64),
+                         fc_a=np.ascontiguousarray(inst.fc_a, dtype=np.float64),
+                         pD_left=np.ascontiguousarray(inst.pD_left, dtype=np.float64),
+                         pD_right=np.ascontiguousarray(inst.pD_right, dtype=np.float64))
+                if getattr(inst, "fc_kn", None) is not None:
+                    a["fc_kn"] = np.ascontiguousarray(inst.fc_kn, dtype=np.float64)
+                on_dev = 0
+            else:
+                a, on_dev = device_arrays[k], 1
             keep.append(a)
             arr[k] = Instance(inst.dim, inst.n, _ptr(a["km"]), inst.n_f, _ptr(a["fc_axis"]), _ptr(a["fc_pos"]),
-                              _ptr(a["fc_kf"]), _ptr(a["fc_a"]), inst.nrhs, _ptr(a["pD_left"]), _ptr(a["pD_right"]), 0,
-                              JUNCTION[junction], _ptr(a.get("fc_kn")))
+                              _ptr(a["fc_kf"]), _ptr(a["fc_a"]), inst.nrhs, _ptr(a["pD_left"]), _ptr(a["pD_right"]),
+                              on_dev, JUNCTION[junction], _ptr(a.get("fc_kn")))
         h = C.c_void_p()
         self._check(lib().mds_assemble_batch(self.h, arr, len(insts), C.byref(h)))
         return System(self, h)
