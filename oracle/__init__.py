@@ -94,6 +94,9 @@ def lib():
             L.orc_round_lowp.argtypes = [C.c_double, C.c_int]
             L.orc_amg_setup.restype = C.c_void_p
             L.orc_amg_setup.argtypes = [P(_CSR), P(AMGOpts)]
+            L.orc_amg_setup_seg.restype = C.c_void_p
+            L.orc_amg_setup_seg.argtypes = [P(_CSR), P(AMGOpts), C.c_int, _i64p]
+            L.orc_amg_level_seg.argtypes = [C.c_void_p, C.c_int, _i64p]
             L.orc_amg_free.argtypes = [C.c_void_p]
             L.orc_amg_nlevels.restype = C.c_int
             L.orc_amg_nlevels.argtypes = [C.c_void_p]
@@ -112,6 +115,8 @@ def lib():
             L.orc_vcycle.argtypes = [C.c_void_p, _f64p, _f64p]
             L.orc_ml_new.restype = C.c_void_p
             L.orc_ml_new.argtypes = [P(_CSR), C.c_int64, P(AMGOpts), C.c_int]
+            L.orc_ml_new_seg.restype = C.c_void_p
+            L.orc_ml_new_seg.argtypes = [P(_CSR), C.c_int64, P(AMGOpts), C.c_int, C.c_int, _i64p, _i64p]
             L.orc_ml_free.argtypes = [C.c_void_p]
             L.orc_ml_apply.argtypes = [C.c_void_p, _f64p, _f64p]
             L.orc_ml_amg.restype = C.c_void_p
@@ -273,10 +278,16 @@ def round_lowp(x, prec):
 
 
 class AMG:
-    def __init__(self, A, **kw):
+    def __init__(self, A, segments=None, **kw):
+        """segments: row offsets [K + 1] of the instances of a packed batch
+        (each coarsened as if alone); None for one instance."""
         self.opts = amg_opts(**kw)
         self._A = CSR(A)
-        self.h = lib().orc_amg_setup(self._A.ptr, C.byref(self.opts))
+        if segments is None:
+            self.h = lib().orc_amg_setup(self._A.ptr, C.byref(self.opts))
+        else:
+            off = np.ascontiguousarray(segments, dtype=np.int64)
+            self.h = lib().orc_amg_setup_seg(self._A.ptr, C.byref(self.opts), len(off) - 1, _p(off, _i64p))
         if not self.h:
             raise ValueError("AMG setup failed (coarsest matrix not SPD)")
         self.n = A.shape[0]
@@ -300,6 +311,12 @@ class AMG:
         if lib().orc_amg_level_agg(self.h, l, _p(out, _i32p)) != 0:
             return None
         return out
+
+    def segments(self, l):
+        """Instance segment offsets of level l."""
+        out = np.zeros(1025, dtype=np.int64)
+        k = lib().orc_amg_level_seg(self.h, l, _p(out, _i64p))
+        return out[:k + 1].copy()
 
     def roots(self, l):
         n = lib().orc_amg_level_n(self.h, l)
@@ -357,11 +374,19 @@ class ML:
     """Block preconditioner of Sec. 3.2: 'lower' = M_L (Alg. 1), 'diag' =
     block diagonal, 'upper' = block upper triangular."""
 
-    def __init__(self, A, n_m, kind="lower", **kw):
+    def __init__(self, A, n_m, kind="lower", segments=None, **kw):
+        """segments: (moff, foff), the matrix-row and fracture-row offsets
+        [K + 1] of the instances of a packed batch; None for one instance."""
         self.opts = amg_opts(**kw)
         self._A = CSR(A)
         self.n_m, self.N = n_m, A.shape[0]
-        self.h = lib().orc_ml_new(self._A.ptr, n_m, C.byref(self.opts), KIND[kind])
+        if segments is None:
+            self.h = lib().orc_ml_new(self._A.ptr, n_m, C.byref(self.opts), KIND[kind])
+        else:
+            mo = np.ascontiguousarray(segments[0], dtype=np.int64)
+            fo = np.ascontiguousarray(segments[1], dtype=np.int64)
+            self.h = lib().orc_ml_new_seg(self._A.ptr, n_m, C.byref(self.opts), KIND[kind], len(mo) - 1,
+                                          _p(mo, _i64p), _p(fo, _i64p))
         if not self.h:
             raise ValueError("M_L setup failed")
 

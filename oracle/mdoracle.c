@@ -753,8 +753,11 @@ struct orc_amg {
     ocsr *R[MAXLEV];       /* its transpose */
     int dense;             /* last level solved by dense Cholesky */
     int diagonal;          /* last level has no couplings: solved by x = b / a_ii */
-    double *L;             /* dense Cholesky factor (row-major, lower) */
+    double *L;             /* dense Cholesky factors of the coarsest segments (each row-major, lower) */
     int64_t nd;
+    int K;                 /* instances (segments) of a packed batch; 1 for one instance */
+    int64_t *seg[MAXLEV];  /* segment offsets of each level [K + 1] */
+    int64_t *loff;         /* start of each coarsest segment's factor in L [K + 1] */
     double *vb[MAXLEV], *vx[MAXLEV], *vr[MAXLEV];
 };
 
@@ -770,7 +773,24 @@ static int cmp_keyed_desc(const void *a, const void *b) {
 
 /* Greedy MIS on G^2 in descending key order; returns roots[] (1 = root) and
  * the number of roots.  Vertices without a strong neighbour take no part. */
-static int64_t mis2_greedy(const ocsr *G, uint64_t seed, int level, int8_t *roots) {
+/* The segment holding row i (segments [off[k], off[k+1]), k < K). */
+static int seg_of(const int64_t *off, int K, int64_t i) {
+    int lo = 0, hi = K - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) / 2;
+        if (off[mid] <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+/* Greedy MIS-2 in descending key order.  A vertex's key uses its index within
+ * its segment, so every instance of a packed batch draws the keys it would
+ * draw alone (vertices of different instances are never within distance
+ * two, so their relative order does not matter). */
+static int64_t mis2_greedy(const ocsr *G, uint64_t seed, int level, int8_t *roots, int K, const int64_t *off) {
     int64_t n = G->nrow;
     int8_t *state = (int8_t *)calloc((size_t)(n > 0 ? n : 1), 1); /* 0 undecided, 1 root, 2 out */
     keyed *order = (keyed *)malloc((size_t)(n > 0 ? n : 1) * sizeof(keyed));
@@ -781,7 +801,7 @@ static int64_t mis2_greedy(const ocsr *G, uint64_t seed, int level, int8_t *root
             state[i] = 2;
             continue;
         }
-        order[m].key = orc_mis_key(seed, level, i);
+        order[m].key = orc_mis_key(seed, level, i - off[seg_of(off, K, i)]);
         order[m].v = (int32_t)i;
         m++;
     }
@@ -1125,8 +1145,25 @@ static double rnd(double x, int prec) {
 }
 
 orc_amg *orc_amg_setup(const ocsr *A0, const orc_amg_opts *o) {
+    int64_t off[2] = {0, A0->nrow};
+    return orc_amg_setup_seg(A0, o, 1, off);
+}
+
+/* Rows of the largest segment of level l. */
+static int64_t seg_max(const orc_amg *h, int l) {
+    int64_t m = 0;
+    for (int k = 0; k < h->K; k++)
+        if (h->seg[l][k + 1] - h->seg[l][k] > m) m = h->seg[l][k + 1] - h->seg[l][k];
+    return m;
+}
+
+orc_amg *orc_amg_setup_seg(const ocsr *A0, const orc_amg_opts *o, int K, const int64_t *off0) {
+    if (K < 1 || off0[0] != 0 || off0[K] != A0->nrow) return NULL;
     orc_amg *h = (orc_amg *)calloc(1, sizeof(orc_amg));
     h->o = *o;
+    h->K = K;
+    h->seg[0] = (int64_t *)malloc((size_t)(K + 1) * sizeof(int64_t));
+    memcpy(h->seg[0], off0, (size_t)(K + 1) * sizeof(int64_t));
     int maxl = o->max_levels < MAXLEV ? o->max_levels : MAXLEV;
     if (maxl < 1) maxl = 1;
     ocsr *A = orc_csr_new(A0->nrow, A0->ncol, A0->nnz);
@@ -1148,13 +1185,14 @@ orc_amg *orc_amg_setup(const ocsr *A0, const orc_amg_opts *o) {
             h->diagonal = 1;
             break;
         }
-        if (n <= o->n_coarse) {
+        /* the coarsening stops once every instance has at most n_coarse rows */
+        if (seg_max(h, l) <= o->n_coarse) {
             h->dense = 1;
             break;
         }
         if (l == maxl - 1) break;
         ocsr *G = orc_strength(A, o->theta);
-        int64_t nr = mis2_greedy(G, o->seed, l, h->root[l]);
+        int64_t nr = mis2_greedy(G, o->seed, l, h->root[l], K, h->seg[l]);
         (void)nr;
         h->agg[l] = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
         int64_t nc = aggregate(G, h->root[l], h->agg[l]);
@@ -1163,6 +1201,17 @@ orc_amg *orc_amg_setup(const ocsr *A0, const orc_amg_opts *o) {
             free(h->agg[l]);
             h->agg[l] = NULL;
             break;
+        }
+        /* aggregates are numbered by ascending root, so the next level's
+         * segment k starts at the number of roots before segment k */
+        h->seg[l + 1] = (int64_t *)malloc((size_t)(K + 1) * sizeof(int64_t));
+        {
+            int64_t cnt = 0;
+            int k = 0;
+            for (int64_t i = 0; i <= n; i++) {
+                while (k <= K && h->seg[l][k] == i) h->seg[l + 1][k++] = cnt;
+                if (i < n && h->root[l][i]) cnt++;
+            }
         }
         if (o->smoothed) {
             h->P[l] = smoothed_prolongator(A, G, h->agg[l], nc);
@@ -1218,28 +1267,43 @@ orc_amg *orc_amg_setup(const ocsr *A0, const orc_amg_opts *o) {
         h->vr[q] = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
     }
     if (h->dense) {
-        /* textbook Cholesky A = L L^T of the coarsest matrix (FP64) */
+        /* textbook Cholesky A_k = L_k L_k^T of each segment's diagonal block of
+         * the coarsest matrix (FP64); a packed matrix couples no segments */
         ocsr *M = h->A[h->nlev - 1];
-        int64_t n = M->nrow;
-        h->nd = n;
-        h->L = (double *)calloc((size_t)(n * n > 0 ? n * n : 1), sizeof(double));
-        for (int64_t i = 0; i < n; i++)
-            for (int64_t p = M->rp[i]; p < M->rp[i + 1]; p++) h->L[i * n + M->ci[p]] = M->v[p];
-        for (int64_t j = 0; j < n; j++) {
-            double s = h->L[j * n + j];
-            for (int64_t k = 0; k < j; k++) s -= h->L[j * n + k] * h->L[j * n + k];
-            if (!(s > 0.0)) {
-                orc_amg_free(h);
-                return NULL;
+        const int64_t *sg = h->seg[h->nlev - 1];
+        h->nd = M->nrow;
+        h->loff = (int64_t *)malloc((size_t)(K + 1) * sizeof(int64_t));
+        h->loff[0] = 0;
+        for (int k = 0; k < K; k++) h->loff[k + 1] = h->loff[k] + (sg[k + 1] - sg[k]) * (sg[k + 1] - sg[k]);
+        h->L = (double *)calloc((size_t)(h->loff[K] > 0 ? h->loff[K] : 1), sizeof(double));
+        for (int k = 0; k < K; k++) {
+            int64_t s0 = sg[k], n = sg[k + 1] - sg[k];
+            double *Lk = h->L + h->loff[k];
+            for (int64_t i = 0; i < n; i++)
+                for (int64_t p = M->rp[s0 + i]; p < M->rp[s0 + i + 1]; p++) {
+                    int64_t j = M->ci[p] - s0;
+                    if (j < 0 || j >= n) {
+                        orc_amg_free(h);
+                        return NULL;
+                    }
+                    Lk[i * n + j] = M->v[p];
+                }
+            for (int64_t j = 0; j < n; j++) {
+                double s = Lk[j * n + j];
+                for (int64_t q = 0; q < j; q++) s -= Lk[j * n + q] * Lk[j * n + q];
+                if (!(s > 0.0)) {
+                    orc_amg_free(h);
+                    return NULL;
+                }
+                double ljj = sqrt(s);
+                Lk[j * n + j] = ljj;
+                for (int64_t i = j + 1; i < n; i++) {
+                    double t = Lk[i * n + j];
+                    for (int64_t q = 0; q < j; q++) t -= Lk[i * n + q] * Lk[j * n + q];
+                    Lk[i * n + j] = t / ljj;
+                }
+                for (int64_t i = 0; i < j; i++) Lk[i * n + j] = 0.0;
             }
-            double ljj = sqrt(s);
-            h->L[j * n + j] = ljj;
-            for (int64_t i = j + 1; i < n; i++) {
-                double t = h->L[i * n + j];
-                for (int64_t k = 0; k < j; k++) t -= h->L[i * n + k] * h->L[j * n + k];
-                h->L[i * n + j] = t / ljj;
-            }
-            for (int64_t i = 0; i < j; i++) h->L[i * n + j] = 0.0;
         }
     }
     return h;
@@ -1260,8 +1324,10 @@ void orc_amg_free(orc_amg *h) {
         free(h->vb[q]);
         free(h->vx[q]);
         free(h->vr[q]);
+        free(h->seg[q]);
     }
     free(h->L);
+    free(h->loff);
     free(h);
 }
 
@@ -1285,6 +1351,12 @@ int orc_amg_level_stored(const orc_amg *h, int l, double *av, double *rs, double
     if (rs) memcpy(rs, h->rs[l], (size_t)h->A[l]->nrow * sizeof(double));
     if (dinv) memcpy(dinv, h->dinv[l], (size_t)h->A[l]->nrow * sizeof(double));
     return 0;
+}
+
+int orc_amg_level_seg(const orc_amg *h, int l, int64_t *out) {
+    if (l < 0 || l >= h->nlev) return -1;
+    memcpy(out, h->seg[l], (size_t)(h->K + 1) * sizeof(int64_t));
+    return h->K;
 }
 
 int orc_amg_level_lowp(const orc_amg *h, int l) { return (l < 0 || l >= h->nlev) ? -1 : h->lowp[l]; }
@@ -1388,17 +1460,23 @@ static void vcycle_level(orc_amg *h, int l, const double *b, double *x) {
     int64_t n = h->A[l]->nrow;
     int pv = h->o.prec == 64 ? 64 : 32;
     if (l == h->nlev - 1 && h->dense) {
-        /* L y = b, L^T x = y */
-        const double *L = h->L;
-        for (int64_t i = 0; i < n; i++) {
-            double s = b[i];
-            for (int64_t k = 0; k < i; k++) s -= L[i * n + k] * x[k];
-            x[i] = s / L[i * n + i];
-        }
-        for (int64_t i = n - 1; i >= 0; i--) {
-            double s = x[i];
-            for (int64_t k = i + 1; k < n; k++) s -= L[k * n + i] * x[k];
-            x[i] = s / L[i * n + i];
+        /* per segment: L_k y = b_k, L_k^T x_k = y */
+        const int64_t *sg = h->seg[l];
+        for (int k = 0; k < h->K; k++) {
+            const double *L = h->L + h->loff[k];
+            int64_t s0 = sg[k], m = sg[k + 1] - sg[k];
+            const double *bk = b + s0;
+            double *xk = x + s0;
+            for (int64_t i = 0; i < m; i++) {
+                double s = bk[i];
+                for (int64_t q = 0; q < i; q++) s -= L[i * m + q] * xk[q];
+                xk[i] = s / L[i * m + i];
+            }
+            for (int64_t i = m - 1; i >= 0; i--) {
+                double s = xk[i];
+                for (int64_t q = i + 1; q < m; q++) s -= L[q * m + i] * xk[q];
+                xk[i] = s / L[i * m + i];
+            }
         }
         for (int64_t i = 0; i < n; i++) x[i] = rnd(x[i], pv);
         return;
@@ -1467,6 +1545,12 @@ struct orc_ml {
 };
 
 orc_ml *orc_ml_new(const ocsr *A, int64_t n_m, const orc_amg_opts *o, int kind) {
+    int64_t mo[2] = {0, n_m}, fo[2] = {0, A->nrow - n_m};
+    return orc_ml_new_seg(A, n_m, o, kind, 1, mo, fo);
+}
+
+orc_ml *orc_ml_new_seg(const ocsr *A, int64_t n_m, const orc_amg_opts *o, int kind, int K, const int64_t *moff,
+                       const int64_t *foff) {
     orc_ml *m = (orc_ml *)calloc(1, sizeof(orc_ml));
     m->n_m = n_m;
     m->n_f = A->nrow - n_m;
@@ -1477,8 +1561,8 @@ orc_ml *orc_ml_new(const ocsr *A, int64_t n_m, const orc_amg_opts *o, int kind) 
         orc_ml_free(m);
         return NULL;
     }
-    m->amg[0] = orc_amg_setup(m->S, o);
-    m->amg[1] = m->n_f > 0 ? orc_amg_setup(m->Aff, o) : NULL;
+    m->amg[0] = orc_amg_setup_seg(m->S, o, K, moff);
+    m->amg[1] = m->n_f > 0 ? orc_amg_setup_seg(m->Aff, o, K, foff) : NULL;
     m->ff_negative = m->n_f > 0;
     for (int64_t k = 0; k < m->n_f; k++) {
         int f;

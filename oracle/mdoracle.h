@@ -101,6 +101,16 @@ typedef struct {
 double orc_round_lowp(double x, int prec);
 
 orc_amg *orc_amg_setup(const ocsr *A, const orc_amg_opts *o);
+/* A packed batch: K instances whose rows are the segments [off[k], off[k+1])
+ * of a block-diagonal matrix (off[0] = 0, off[K] = rows).  Every instance is
+ * coarsened as if it were alone: MIS-2 keys use a row's index within its
+ * segment, the next level's segments are each instance's aggregates, the
+ * coarsening stops once every segment has at most n_coarse rows, and the
+ * coarsest level is solved with each segment's own dense Cholesky factor.
+ * orc_amg_setup is the case K = 1.  NULL on failure. */
+orc_amg *orc_amg_setup_seg(const ocsr *A, const orc_amg_opts *o, int K, const int64_t *off);
+/* Segment offsets of level l (K + 1 values); returns K, or -1. */
+int orc_amg_level_seg(const orc_amg *h, int l, int64_t *out);
 void orc_amg_free(orc_amg *h);
 int orc_amg_nlevels(const orc_amg *h);
 int64_t orc_amg_level_n(const orc_amg *h, int l);
@@ -129,6 +139,11 @@ typedef int (*orc_prec_fn)(void *ctx, const double *r, double *z);
 typedef struct orc_ml orc_ml;
 /* kind 0 = block lower triangular M_L (Alg. 1), 1 = block diagonal, 2 = block upper. */
 orc_ml *orc_ml_new(const ocsr *A, int64_t n_m, const orc_amg_opts *o, int kind);
+/* M_L of a packed batch: S~ coarsened with the matrix-row segments moff and
+ * A_ff with the fracture-row segments foff (offsets within the fracture
+ * rows), K + 1 values each (see orc_amg_setup_seg). */
+orc_ml *orc_ml_new_seg(const ocsr *A, int64_t n_m, const orc_amg_opts *o, int kind, int K, const int64_t *moff,
+                       const int64_t *foff);
 void orc_ml_free(orc_ml *m);
 int orc_ml_apply(void *ml, const double *r, double *z);
 const orc_amg *orc_ml_amg(const orc_ml *m, int block);  /* 0 = S~, 1 = A_ff */

@@ -481,10 +481,13 @@ int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_preco
         p->sys = sys;
         p->o = o;
         p->S = schur_build(*c, sys->view[0], sys->view[1], sys->view[2], sys->view[3], p->dk);
-        amg_setup(*c, p->S.view(), o, p->h[0]);
+        // a packed batch: every instance's blocks coarsened as if alone
+        const bool packed = sys->n_inst > 1 && sys->own.moff.size() == (size_t)sys->n_inst + 1 &&
+                            sys->own.foff.size() == (size_t)sys->n_inst + 1;
+        amg_setup(*c, p->S.view(), o, p->h[0], packed ? &sys->own.moff : nullptr);
         p->has_f = sys->n_f > 0;
         if (p->has_f) {
-            amg_setup(*c, sys->view[3], o, p->h[1]);
+            amg_setup(*c, sys->view[3], o, p->h[1], packed ? &sys->own.foff : nullptr);
             p->ff_negative = !(row_kinds(*c, sys->view[3]) & 2);
         }
         int64_t mx = sys->n_m > sys->n_f ? sys->n_m : sys->n_f;

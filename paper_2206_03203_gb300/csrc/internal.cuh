@@ -383,14 +383,33 @@ struct Level {
     int64_t sell_nslice = 0, sell_nnz = 0;
     Buf sell_ptr, sell_len, sell_col, sell_val, sell_perm;
     Buf b, x, r, y, d, t;  // work vectors in the vector precision
+    Buf seg_d;             // int64 [K + 1] instance row offsets (packed batches)
+};
+
+// One diagonal block of the coarsest level: its first row, the start of its
+// n x n row-major matrices, its size.
+struct DBlk {
+    int64_t row, off;
+    int32_t n;
+};
+struct DenseBlocks {
+    int K = 0;
+    int64_t nmax = 0, nrow = 0, total = 0;  // largest block, rows, sum of n_b^2
+    std::vector<DBlk> host;
+    Buf blk;  // DBlk [K]
 };
 
 struct Hierarchy {
     std::vector<Level> lv;
+    // instances of a packed batch: per level, the row offsets [K + 1] of
+    // each instance (every instance is coarsened as if alone); K = 1 for one
+    int K = 1;
+    std::vector<std::vector<int64_t>> seg;
+    DenseBlocks db;   // the coarsest level's diagonal blocks (one per instance)
     bool dense = false;
     bool diagonal = false;  // last level has no couplings: x = b / a_ii
     int64_t nd = 0;
-    Buf Ainv;         // FP64 [nd nd] inverse of the coarsest matrix
+    Buf Ainv;         // FP64 inverse of each coarsest block (db)
     int prec = 64;    // vector precision: 64 or 32
     int smoother = 0;
     int sweeps = 1;
@@ -399,7 +418,12 @@ struct Hierarchy {
     bool use_tail = true;  // run the coarse end of the V-cycle as one cluster kernel
 };
 
-void amg_setup(Ctx &c, const mds_csr &A, const mds_setup_opts &o, Hierarchy &h);
+// seg0: the instances' row offsets [K + 1] of a packed batch (NULL: one
+// instance); every instance is coarsened as if alone (MIS-2 keys by the row's
+// index within its instance, stop once every instance has at most n_coarse
+// rows, block-diagonal coarsest solve).
+void amg_setup(Ctx &c, const mds_csr &A, const mds_setup_opts &o, Hierarchy &h,
+               const std::vector<int64_t> *seg0 = nullptr);
 // bit 1: some row holds an off-diagonal entry (or no diagonal); bit 2: some
 // diagonal entry is missing or not negative (synchronises)
 int row_kinds(Ctx &c, const mds_csr &A);
@@ -407,11 +431,12 @@ int row_kinds(Ctx &c, const mds_csr &A);
 void level_storage(Ctx &c, Hierarchy &h, const mds_setup_opts &o);
 
 // ---- dense (k_dense.cu) ----
-// Cholesky of the n x n SPD matrix stored densely, then its inverse.
-void dense_spd_inverse(Ctx &c, const mds_csr &A, Buf &Ainv);
-// y = M x for nr in {1, 2, 4, 8} interleaved columns
-void dense_apply(Ctx &c, const double *M, int64_t n, int nr, const double *x, double *y);
-void dense_apply(Ctx &c, const double *M, int64_t n, int nr, const float *x, float *y);
+// Cholesky of each diagonal block [seg[k], seg[k+1]) of the SPD matrix A
+// (stored densely), then its inverse; fills the block table.
+void dense_spd_inverse(Ctx &c, const mds_csr &A, const std::vector<int64_t> &seg, Buf &Ainv, DenseBlocks &db);
+// y = M x for the block-diagonal inverse M, nr in {1, 2, 4, 8} interleaved columns
+void dense_apply(Ctx &c, const DenseBlocks &db, const double *M, int nr, const double *x, double *y);
+void dense_apply(Ctx &c, const DenseBlocks &db, const double *M, int nr, const float *x, float *y);
 
 // ---- V-cycle (k_vcycle.cu) ----
 // x = V(b) on level 0 of h for nr in {1, 2, 4, 8} interleaved columns; b and

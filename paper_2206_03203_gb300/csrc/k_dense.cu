@@ -2,30 +2,50 @@
 // followed by the explicit inverse A^-1 = L^-T L^-1 (one warp per column), so
 // that each V-cycle applies the coarsest solve as one parallel dense
 // matrix-vector product instead of two sequential triangular solves.
+//
+// The coarsest level of a packed batch is block diagonal (one block per
+// instance): every kernel works on K blocks at once (blockIdx.y = block), each
+// block an n_b x n_b row-major matrix at its own offset; a single instance is
+// the case K = 1.
 #include "internal.cuh"
 
 namespace mds {
 
 constexpr int NB = 32;
 
-__global__ void k_densify(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                          const double *__restrict__ v, double *__restrict__ D) {
+__global__ void k_densify(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                          const double *__restrict__ v, const DBlk *__restrict__ blk, double *__restrict__ D,
+                          int *err) {
     mds_pdl_entry();
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    for (int32_t p = rp[i]; p < rp[i + 1]; p++) D[i * n + ci[p]] = v[p];
+    const DBlk b = blk[blockIdx.y];
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= b.n) return;
+    double *Db = D + b.off;
+    for (int32_t p = rp[b.row + t]; p < rp[b.row + t + 1]; p++) {
+        int64_t j = ci[p] - b.row;
+        if (j < 0 || j >= b.n) {  // an entry coupling two instances
+            atomicOr(err, DERR_CAPACITY);
+            continue;
+        }
+        Db[t * b.n + j] = v[p];
+    }
 }
 
 // factor the nb x nb diagonal tile at k0 in shared memory
-__global__ void k_chol_diag(double *D, int64_t n, int64_t k0, int nb, int *err) {
+__global__ void k_chol_diag(double *D, const DBlk *__restrict__ blk, int64_t k0, int *err) {
     mds_pdl_entry();
+    const DBlk b = blk[blockIdx.y];
+    if (k0 >= b.n) return;
+    const int64_t n = b.n;
+    const int nb = (int)((n - k0) < NB ? (n - k0) : NB);
+    double *Db = D + b.off;
     __shared__ double T[NB][NB + 1];
     __shared__ int bad;
     int t = threadIdx.x;
     if (t == 0) bad = 0;
     for (int q = t; q < nb * nb; q += blockDim.x) {
         int i = q / nb, j = q % nb;
-        T[i][j] = D[(k0 + i) * n + k0 + j];
+        T[i][j] = Db[(k0 + i) * n + k0 + j];
     }
     __syncthreads();
     for (int j = 0; j < nb; j++) {
@@ -48,37 +68,49 @@ __global__ void k_chol_diag(double *D, int64_t n, int64_t k0, int nb, int *err) 
     }
     for (int q = t; q < nb * nb; q += blockDim.x) {
         int i = q / nb, j = q % nb;
-        if (i >= j) D[(k0 + i) * n + k0 + j] = T[i][j];
+        if (i >= j) Db[(k0 + i) * n + k0 + j] = T[i][j];
     }
     if (t == 0 && bad) atomicOr(err, DERR_NOT_SPD);
 }
 
 // rows below the panel: L21 = A21 L11^-T, one thread per row
-__global__ void k_chol_trsm(double *D, int64_t n, int64_t k0, int nb) {
+__global__ void k_chol_trsm(double *D, const DBlk *__restrict__ blk, int64_t k0) {
     mds_pdl_entry();
+    const DBlk b = blk[blockIdx.y];
+    if (k0 >= b.n) return;
+    const int64_t n = b.n;
+    const int nb = (int)((n - k0) < NB ? (n - k0) : NB);
+    double *Db = D + b.off;
     __shared__ double L[NB][NB + 1];
     for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
         int i = q / nb, j = q % nb;
-        L[i][j] = D[(k0 + i) * n + k0 + j];
+        L[i][j] = Db[(k0 + i) * n + k0 + j];
     }
     __syncthreads();
     int64_t i = k0 + nb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double x[NB];
     for (int j = 0; j < nb; j++) {
-        double s = D[i * n + k0 + j];
+        double s = Db[i * n + k0 + j];
         for (int k = 0; k < j; k++) s -= x[k] * L[j][k];
         x[j] = s / L[j][j];
     }
-    for (int j = 0; j < nb; j++) D[i * n + k0 + j] = x[j];
+    for (int j = 0; j < nb; j++) Db[i * n + k0 + j] = x[j];
 }
 
 // trailing update A22 -= L21 L21^T on the lower tiles
-__global__ void k_chol_update(double *D, int64_t n, int64_t k0, int nb) {
+__global__ void k_chol_update(double *D, const DBlk *__restrict__ blk, int64_t k0) {
     mds_pdl_entry();
-    __shared__ double Li[NB][NB + 1], Lj[NB][NB + 1];
-    int64_t base = k0 + nb;
+    const DBlk bk = blk[blockIdx.y];
+    const int64_t n = bk.n;
+    if (k0 + NB >= n) return;  // no trailing matrix
+    const int nb = NB;
+    const int64_t base = k0 + nb;
+    const int64_t m = (n - base + NB - 1) / NB;
     int64_t b = blockIdx.x;
+    if (b >= m * (m + 1) / 2) return;
+    double *Db = D + bk.off;
+    __shared__ double Li[NB][NB + 1], Lj[NB][NB + 1];
     // map b -> (bi, bj), bj <= bi
     int64_t bi = (int64_t)((sqrt(8.0 * (double)b + 1.0) - 1.0) / 2.0);
     while ((bi + 1) * (bi + 2) / 2 <= b) bi++;
@@ -87,8 +119,8 @@ __global__ void k_chol_update(double *D, int64_t n, int64_t k0, int nb) {
     int64_t r0 = base + bi * NB, c0 = base + bj * NB;
     for (int q = threadIdx.x; q < NB * nb; q += blockDim.x) {
         int r = q / nb, k = q % nb;
-        Li[r][k] = (r0 + r < n) ? D[(r0 + r) * n + k0 + k] : 0.0;
-        Lj[r][k] = (c0 + r < n) ? D[(c0 + r) * n + k0 + k] : 0.0;
+        Li[r][k] = (r0 + r < n) ? Db[(r0 + r) * n + k0 + k] : 0.0;
+        Lj[r][k] = (c0 + r < n) ? Db[(c0 + r) * n + k0 + k] : 0.0;
     }
     __syncthreads();
     for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) {
@@ -97,23 +129,29 @@ __global__ void k_chol_update(double *D, int64_t n, int64_t k0, int nb) {
         if (gi >= n || gj >= n || gj > gi) continue;
         double acc = 0.0;
         for (int k = 0; k < nb; k++) acc += Li[r][k] * Lj[s][k];
-        D[gi * n + gj] -= acc;
+        Db[gi * n + gj] -= acc;
     }
 }
 
-__global__ void k_transpose_lower(const double *__restrict__ L, double *__restrict__ U, int64_t n) {
+__global__ void k_transpose_lower(const double *__restrict__ L, double *__restrict__ U, const DBlk *__restrict__ blk) {
     mds_pdl_entry();
+    const DBlk b = blk[blockIdx.y];
+    const int64_t n = b.n;
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n * n) return;
     int64_t i = q / n, j = q % n;
-    U[j * n + i] = (i >= j) ? L[i * n + j] : 0.0;
+    U[b.off + j * n + i] = (i >= j) ? L[b.off + i * n + j] : 0.0;
 }
 
 // column j of A^-1: L y = e_j, then L^T x = y (x overwrites y); one warp per column
-__global__ void k_chol_inverse(const double *__restrict__ L, const double *__restrict__ U, int64_t n,
-                               double *__restrict__ X) {
+__global__ void k_chol_inverse(const double *__restrict__ Lall, const double *__restrict__ Uall,
+                               const DBlk *__restrict__ blk, double *__restrict__ Xall) {
     mds_pdl_entry();
     extern __shared__ double ys[];
+    const DBlk b = blk[blockIdx.y];
+    const int64_t n = b.n;
+    const double *L = Lall + b.off, *U = Uall + b.off;
+    double *X = Xall + b.off;
     int wpb = blockDim.x / 32;
     int w = threadIdx.x / 32, lane = threadIdx.x % 32;
     int64_t j = (int64_t)blockIdx.x * wpb + w;
@@ -138,49 +176,91 @@ __global__ void k_chol_inverse(const double *__restrict__ L, const double *__res
     for (int64_t i = lane; i < n; i += 32) X[j * n + i] = y[i];
 }
 
-void dense_spd_inverse(Ctx &c, const mds_csr &A, Buf &Ainv) {
-    int64_t n = A.nrow;
-    MDS_REQUIRE(n >= 1 && n <= 8192, MDS_ERR_INVALID, "coarsest level size out of range for dense Cholesky");
-    Buf D(&c, sizeof(double) * (size_t)(n * n));
-    MDS_CUDA(cudaMemsetAsync(D.p, 0, sizeof(double) * (size_t)(n * n), c.stream));
-    MDS_LAUNCH(c, KC_NONE, 0, k_densify, grid_for(n, 128), 128, 0, n, A.row_ptr, A.col, A.val, D.as<double>());
+void dense_spd_inverse(Ctx &c, const mds_csr &A, const std::vector<int64_t> &seg, Buf &Ainv, DenseBlocks &db) {
+    const int K = (int)seg.size() - 1;
+    MDS_REQUIRE(K >= 1 && seg[0] == 0 && seg[K] == A.nrow, MDS_ERR_INVALID, "coarsest segments do not cover the level");
+    std::vector<DBlk> hb(K);
+    int64_t nmax = 0, tot = 0;
+    for (int k = 0; k < K; k++) {
+        int64_t n = seg[k + 1] - seg[k];
+        MDS_REQUIRE(n >= 0 && n <= 8192, MDS_ERR_INVALID, "coarsest level size out of range for dense Cholesky");
+        hb[k] = DBlk{seg[k], tot, (int32_t)n};
+        tot += n * n;
+        nmax = n > nmax ? n : nmax;
+    }
+    MDS_REQUIRE(nmax >= 1, MDS_ERR_INVALID, "empty coarsest level");
+    db.K = K;
+    db.nmax = nmax;
+    db.nrow = A.nrow;
+    db.total = tot;
+    db.host = hb;
+    db.blk = Buf(&c, sizeof(DBlk) * (size_t)K);
+    MDS_CUDA(cudaMemcpyAsync(db.blk.p, hb.data(), sizeof(DBlk) * (size_t)K, cudaMemcpyHostToDevice, c.stream));
+    const DBlk *B = db.blk.as<DBlk>();
+    Buf D(&c, sizeof(double) * (size_t)tot);
+    MDS_CUDA(cudaMemsetAsync(D.p, 0, sizeof(double) * (size_t)tot, c.stream));
     c.clear_err();
-    for (int64_t k0 = 0; k0 < n; k0 += NB) {
-        int nb = (int)((n - k0) < NB ? (n - k0) : NB);
-        MDS_LAUNCH(c, KC_NONE, 0, k_chol_diag, 1, 256, 0, D.as<double>(), n, k0, nb, c.d_err);
-        int64_t rest = n - k0 - nb;
+    MDS_LAUNCH(c, KC_NONE, 0, k_densify, dim3(grid_for(nmax, 128), K), 128, 0, A.row_ptr, A.col, A.val, B,
+               D.as<double>(), c.d_err);
+    c.check_err("coarsest level (a coupling between two instances)");
+    c.clear_err();
+    for (int64_t k0 = 0; k0 < nmax; k0 += NB) {
+        MDS_LAUNCH(c, KC_NONE, 0, k_chol_diag, dim3(1, K), 256, 0, D.as<double>(), B, k0, c.d_err);
+        int64_t rest = nmax - k0 - NB;
         if (rest <= 0) break;
-        MDS_LAUNCH(c, KC_NONE, 0, k_chol_trsm, grid_for(rest, 64), 64, 0, D.as<double>(), n, k0, nb);
+        MDS_LAUNCH(c, KC_NONE, 0, k_chol_trsm, dim3(grid_for(rest, 64), K), 64, 0, D.as<double>(), B, k0);
         int64_t m = (rest + NB - 1) / NB;
-        MDS_LAUNCH(c, KC_NONE, 0, k_chol_update, (unsigned)(m * (m + 1) / 2), 256, 0, D.as<double>(), n, k0, nb);
+        MDS_LAUNCH(c, KC_NONE, 0, k_chol_update, dim3((unsigned)(m * (m + 1) / 2), K), 256, 0, D.as<double>(), B, k0);
     }
     c.check_err("coarsest Cholesky");
-    Buf U(&c, sizeof(double) * (size_t)(n * n));
-    MDS_LAUNCH(c, KC_NONE, 0, k_transpose_lower, grid_for(n * n, 256), 256, 0, D.as<double>(), U.as<double>(), n);
-    Ainv = Buf(&c, sizeof(double) * (size_t)(n * n));
+    Buf U(&c, sizeof(double) * (size_t)tot);
+    MDS_LAUNCH(c, KC_NONE, 0, k_transpose_lower, dim3(grid_for(nmax * nmax, 256), K), 256, 0, D.as<double>(),
+               U.as<double>(), B);
+    Ainv = Buf(&c, sizeof(double) * (size_t)tot);
     int wpb = 4;
-    while (wpb > 1 && (size_t)wpb * n * sizeof(double) > 48 * 1024) wpb /= 2;
-    size_t smem = (size_t)wpb * n * sizeof(double);
-    if (smem > 48 * 1024) MDS_CUDA(cudaFuncSetAttribute(k_chol_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    MDS_LAUNCH(c, KC_NONE, 0, k_chol_inverse, grid_for(n, wpb), 32 * wpb, smem, D.as<double>(), U.as<double>(), n,
-               Ainv.as<double>());
+    while (wpb > 1 && (size_t)wpb * nmax * sizeof(double) > 48 * 1024) wpb /= 2;
+    size_t smem = (size_t)wpb * nmax * sizeof(double);
+    if (smem > 48 * 1024)
+        MDS_CUDA(cudaFuncSetAttribute(k_chol_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MDS_LAUNCH(c, KC_NONE, 0, k_chol_inverse, dim3(grid_for(nmax, wpb), K), 32 * wpb, smem, D.as<double>(),
+               U.as<double>(), B, Ainv.as<double>());
 }
 
-// y = M x for NR interleaved columns (entry (i, c) at i * NR + c); one warp
-// per row, FP64 accumulation over k = lane, lane + 32, ... then a lane tree.
-// M (the coarsest inverse) is fixed after set-up: each lane loads its first
-// DPRE entries of the row before waiting for the kernel that produced x.
+// The block holding row `row` of the coarsest level (blocks ascending by row).
+__device__ __forceinline__ int dblk_of(const DBlk *blk, int K, int64_t row) {
+    int lo = 0, hi = K - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (blk[mid].row <= row)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// y = M x for NR interleaved columns (entry (i, c) at i * NR + c), M the
+// block-diagonal inverse; one warp per row, FP64 accumulation over the row of
+// its block (k = lane, lane + 32, ...) then a lane tree.  M is fixed after
+// set-up: each lane loads its first DPRE entries of the row before waiting
+// for the kernel that produced x.
 constexpr int DPRE = 16;
 template <class XT, int NR>
-__global__ void k_dense_apply(const double *__restrict__ M, int64_t n, const XT *__restrict__ x, XT *__restrict__ y) {
+__global__ void k_dense_apply(const double *__restrict__ Mall, const DBlk *__restrict__ blk, int K, int64_t nrow,
+                              const XT *__restrict__ xall, XT *__restrict__ yall) {
     int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     int lane = threadIdx.x % 32;
-    const bool live = row < n;
+    const bool live = row < nrow;
+    DBlk b{0, 0, 0};
+    if (live) b = blk[K > 1 ? dblk_of(blk, K, row) : 0];
+    const int64_t n = b.n, i = row - b.row;
+    const double *M = Mall + b.off + i * n;
+    const XT *x = xall + b.row * NR;
     double pm[DPRE];
 #pragma unroll
     for (int q = 0; q < DPRE; q++) {
         int64_t k = lane + 32 * (int64_t)q;
-        pm[q] = live && k < n ? M[row * n + k] : 0.0;
+        pm[q] = live && k < n ? M[k] : 0.0;
     }
     mds_pdl_wait();
     mds_pdl_trigger();
@@ -197,7 +277,7 @@ __global__ void k_dense_apply(const double *__restrict__ M, int64_t n, const XT 
         }
     }
     for (int64_t k = lane + 32 * DPRE; k < n; k += 32) {
-        double m = M[row * n + k];
+        double m = M[k];
 #pragma unroll
         for (int c = 0; c < NR; c++) s[c] += m * (double)x[k * NR + c];
     }
@@ -206,28 +286,30 @@ __global__ void k_dense_apply(const double *__restrict__ M, int64_t n, const XT 
         for (int o = 16; o > 0; o >>= 1) s[c] += __shfl_down_sync(0xffffffffu, s[c], o);
     if (lane == 0)
 #pragma unroll
-        for (int c = 0; c < NR; c++) y[row * NR + c] = (XT)s[c];
+        for (int c = 0; c < NR; c++) yall[row * NR + c] = (XT)s[c];
 }
 
 template <class XT>
-static void dense_apply_t(Ctx &c, const double *M, int64_t n, int nr, const XT *x, XT *y) {
-    double bytes = 8.0 * n * n + 2.0 * sizeof(XT) * n * nr;
+static void dense_apply_t(Ctx &c, const DenseBlocks &db, const double *M, int nr, const XT *x, XT *y) {
+    const int64_t n = db.nrow;
+    double bytes = 8.0 * (double)db.total + 2.0 * sizeof(XT) * n * nr;
     unsigned g = grid_for(n * 32, 256);
+    const DBlk *B = db.blk.as<DBlk>();
     switch (nr) {
-        case 1: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 1>), g, 256, 0, M, n, x, y); break;
-        case 2: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 2>), g, 256, 0, M, n, x, y); break;
-        case 4: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 4>), g, 256, 0, M, n, x, y); break;
-        case 8: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 8>), g, 256, 0, M, n, x, y); break;
+        case 1: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 1>), g, 256, 0, M, B, db.K, n, x, y); break;
+        case 2: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 2>), g, 256, 0, M, B, db.K, n, x, y); break;
+        case 4: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 4>), g, 256, 0, M, B, db.K, n, x, y); break;
+        case 8: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 8>), g, 256, 0, M, B, db.K, n, x, y); break;
         default: throw Error(MDS_ERR_INVALID, "dense apply: column count must be 1, 2, 4 or 8");
     }
 }
 
-void dense_apply(Ctx &c, const double *M, int64_t n, int nr, const double *x, double *y) {
-    dense_apply_t<double>(c, M, n, nr, x, y);
+void dense_apply(Ctx &c, const DenseBlocks &db, const double *M, int nr, const double *x, double *y) {
+    dense_apply_t<double>(c, db, M, nr, x, y);
 }
 
-void dense_apply(Ctx &c, const double *M, int64_t n, int nr, const float *x, float *y) {
-    dense_apply_t<float>(c, M, n, nr, x, y);
+void dense_apply(Ctx &c, const DenseBlocks &db, const double *M, int nr, const float *x, float *y) {
+    dense_apply_t<float>(c, db, M, nr, x, y);
 }
 
 }  // namespace mds

@@ -178,19 +178,39 @@ __global__ void k_mis_init(int64_t n, const int32_t *__restrict__ deg, int8_t *_
     if (i < n) state[i] = deg[i] == 0 ? 2 : 0;
 }
 
-// m1_i = max key over undecided vertices of {i} and its strong neighbours
-__global__ void k_mis_max1(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                           const int8_t *__restrict__ g, const int8_t *__restrict__ state, uint64_t lkey,
-                           uint64_t *__restrict__ m1) {
+// Index of row i within its instance (packed batches: lid; else i): the keys
+// of an instance do not depend on the other instances packed with it.
+__device__ __forceinline__ int64_t key_index(const int32_t *lid, int64_t i) { return lid ? (int64_t)lid[i] : i; }
+
+// lid[i] = i - seg[k] for the instance k holding row i (seg ascending, K + 1)
+__global__ void k_local_index(int64_t n, const int64_t *__restrict__ seg, int K, int32_t *__restrict__ lid) {
     mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    uint64_t m = state[i] == 0 ? mis_key1(lkey, i) : 0;
+    int lo = 0, hi = K - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (seg[mid] <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    lid[i] = (int32_t)(i - seg[lo]);
+}
+
+// m1_i = max key over undecided vertices of {i} and its strong neighbours
+__global__ void k_mis_max1(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           const int8_t *__restrict__ g, const int8_t *__restrict__ state, uint64_t lkey,
+                           const int32_t *__restrict__ lid, uint64_t *__restrict__ m1) {
+    mds_pdl_entry();
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t m = state[i] == 0 ? mis_key1(lkey, key_index(lid, i)) : 0;
     for (int32_t p = rp[i]; p < rp[i + 1]; p++) {
         if (!g[p]) continue;
         int32_t j = ci[p];
         if (state[j] == 0) {
-            uint64_t k = mis_key1(lkey, j);
+            uint64_t k = mis_key1(lkey, key_index(lid, j));
             m = k > m ? k : m;
         }
     }
@@ -201,7 +221,7 @@ __global__ void k_mis_max1(int64_t n, const int32_t *__restrict__ rp, const int3
 // two becomes a root
 __global__ void k_mis_select(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                              const int8_t *__restrict__ g, const uint64_t *__restrict__ m1, uint64_t lkey,
-                             int8_t *__restrict__ state) {
+                             const int32_t *__restrict__ lid, int8_t *__restrict__ state) {
     mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || state[i] != 0) return;
@@ -211,7 +231,7 @@ __global__ void k_mis_select(int64_t n, const int32_t *__restrict__ rp, const in
             uint64_t k = m1[ci[p]];
             m = k > m ? k : m;
         }
-    if (m == mis_key1(lkey, i)) state[i] = 1;
+    if (m == mis_key1(lkey, key_index(lid, i))) state[i] = 1;
 }
 
 __global__ void k_mis_near_root(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
@@ -665,6 +685,14 @@ static DCsr copy_csr(Ctx &c, const mds_csr &A) {
     return B;
 }
 
+// out[k] = rootid[seg[k]] for k <= K: the first aggregate of each instance
+__global__ void k_seg_next(int K, const int64_t *__restrict__ seg, const int32_t *__restrict__ rootid,
+                           int64_t *__restrict__ out) {
+    mds_pdl_entry();
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k <= K) out[k] = rootid[seg[k]];
+}
+
 static uint64_t host_mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
@@ -673,7 +701,7 @@ static uint64_t host_mix64(uint64_t z) {
 
 // MIS-2 on the strength graph of level l: fills roots, returns their count.
 static int64_t mis2(Ctx &c, const DCsr &A, const int8_t *g, const int32_t *deg, uint64_t seed, int level,
-                    Buf &state) {
+                    const int32_t *lid, Buf &state) {
     int64_t n = A.nrow;
     unsigned gr = grid_for(n, 256);
     state = Buf(&c, (size_t)(n > 0 ? n : 1));
@@ -685,9 +713,9 @@ static int64_t mis2(Ctx &c, const DCsr &A, const int8_t *g, const int32_t *deg, 
     for (int round = 0;; round++) {
         MDS_REQUIRE(round < 10000, MDS_ERR_TIMEOUT, "MIS-2 did not terminate");
         MDS_CUDA(cudaMemsetAsync(und.p, 0, sizeof(int32_t), c.stream));
-        MDS_LAUNCH(c, KC_NONE, 0, k_mis_max1, gr, 256, 0, n, A.rowp(), A.cols(), g, state.as<int8_t>(), lkey,
+        MDS_LAUNCH(c, KC_NONE, 0, k_mis_max1, gr, 256, 0, n, A.rowp(), A.cols(), g, state.as<int8_t>(), lkey, lid,
                    m1.as<uint64_t>());
-        MDS_LAUNCH(c, KC_NONE, 0, k_mis_select, gr, 256, 0, n, A.rowp(), A.cols(), g, m1.as<uint64_t>(), lkey,
+        MDS_LAUNCH(c, KC_NONE, 0, k_mis_select, gr, 256, 0, n, A.rowp(), A.cols(), g, m1.as<uint64_t>(), lkey, lid,
                    state.as<int8_t>());
         MDS_LAUNCH(c, KC_NONE, 0, k_mis_near_root, gr, 256, 0, n, A.rowp(), A.cols(), g, state.as<int8_t>(),
                    e1.as<int8_t>());
@@ -698,15 +726,23 @@ static int64_t mis2(Ctx &c, const DCsr &A, const int8_t *g, const int32_t *deg, 
     return 0;
 }
 
-void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h) {
+void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h, const std::vector<int64_t> *seg0) {
     h.lv.clear();
     h.dense = false;
     h.diagonal = false;
+    h.seg.clear();
+    if (seg0 && seg0->size() >= 2) {
+        MDS_REQUIRE(seg0->front() == 0 && seg0->back() == A0.nrow, MDS_ERR_INVALID, "instance segments do not cover the matrix");
+        h.seg.push_back(*seg0);
+    } else {
+        h.seg.push_back(std::vector<int64_t>{0, A0.nrow});
+    }
+    h.K = (int)h.seg[0].size() - 1;
     h.prec = o.precision == MDS_PREC_FP64 ? 64 : 32;
     h.smoother = o.smoother;
     h.sweeps = o.sweeps < 1 ? 1 : o.sweeps;
     h.cheb_degree = o.cheb_degree < 1 ? 2 : o.cheb_degree;
-    h.use_tail = o.coarse_tail != 0;
+    h.use_tail = o.coarse_tail != 0 && h.K == 1;
     int maxl = o.max_levels < 1 ? 1 : (o.max_levels > 32 ? 32 : o.max_levels);
     h.lv.emplace_back();
     h.lv[0].A = copy_csr(c, A0);
@@ -722,12 +758,24 @@ void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h)
             h.diagonal = true;
             break;
         }
-        if (n <= o.n_coarse) {
+        // the coarsening stops once every instance has at most n_coarse rows
+        const std::vector<int64_t> &sg = h.seg[l];
+        int64_t smax = 0;
+        for (int k = 0; k < h.K; k++) smax = std::max(smax, sg[k + 1] - sg[k]);
+        if (smax <= o.n_coarse) {
             h.dense = true;
             break;
         }
         if (l == maxl - 1) break;
         unsigned gr = grid_for(n, 256);
+        Buf lid;
+        if (h.K > 1) {
+            L.seg_d = Buf(&c, sizeof(int64_t) * (size_t)(h.K + 1));
+            MDS_CUDA(cudaMemcpyAsync(L.seg_d.p, sg.data(), sizeof(int64_t) * (size_t)(h.K + 1),
+                                     cudaMemcpyHostToDevice, c.stream));
+            lid = Buf(&c, sizeof(int32_t) * (size_t)n);
+            MDS_LAUNCH(c, KC_NONE, 0, k_local_index, gr, 256, 0, n, L.seg_d.as<int64_t>(), h.K, lid.as<int32_t>());
+        }
         Buf dg(&c, sizeof(double) * (size_t)n), gf(&c, (size_t)(L.A.nnz > 0 ? L.A.nnz : 1));
         Buf deg(&c, sizeof(int32_t) * (size_t)(n + 1));
         MDS_LAUNCH(c, KC_NONE, 0, k_diag, gr, 256, 0, n, L.A.rowp(), L.A.cols(), L.A.vals(), dg.as<double>(), 0,
@@ -735,7 +783,7 @@ void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h)
         MDS_LAUNCH(c, KC_NONE, 0, k_strength, gr, 256, 0, n, L.A.rowp(), L.A.cols(), L.A.vals(), dg.as<double>(), th2,
                    gf.as<int8_t>(), deg.as<int32_t>());
         Buf state;
-        mis2(c, L.A, gf.as<int8_t>(), deg.as<int32_t>(), o.seed, l, state);
+        mis2(c, L.A, gf.as<int8_t>(), deg.as<int32_t>(), o.seed, l, h.K > 1 ? lid.as<int32_t>() : nullptr, state);
         Buf flag(&c, sizeof(int32_t) * (size_t)(n + 1)), rootid(&c, sizeof(int32_t) * (size_t)(n + 1));
         MDS_LAUNCH(c, KC_NONE, 0, k_root_flags, gr, 256, 0, n, state.as<int8_t>(), L.roots.as<int8_t>(),
                    flag.as<int32_t>());
@@ -749,6 +797,23 @@ void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h)
         if (nc == 0 || (double)nc > o.stall_ratio * (double)n) {
             L.agg.reset();
             break;
+        }
+        // the next level's instance segments: aggregates are numbered by
+        // ascending root, so instance k's first aggregate is the number of
+        // roots before its first row
+        {
+            std::vector<int64_t> nx(h.K + 1, 0);
+            if (h.K > 1) {
+                Buf o_d(&c, sizeof(int64_t) * (size_t)(h.K + 1));
+                MDS_LAUNCH(c, KC_NONE, 0, k_seg_next, grid_for(h.K + 1, 128), 128, 0, h.K, L.seg_d.as<int64_t>(),
+                           rootid.as<int32_t>(), o_d.as<int64_t>());
+                MDS_CUDA(cudaMemcpyAsync(nx.data(), o_d.p, sizeof(int64_t) * (size_t)(h.K + 1), cudaMemcpyDeviceToHost,
+                                         c.stream));
+                c.sync();
+            } else {
+                nx[1] = nc;
+            }
+            h.seg.push_back(nx);
         }
         // members of each aggregate, ascending
         Buf acnt(&c, sizeof(int32_t) * (size_t)(nc + 1));
@@ -835,8 +900,17 @@ void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h)
     if (h.dense) {
         Level &L = h.lv.back();
         h.nd = L.A.nrow;
-        dense_spd_inverse(c, L.A.view(), h.Ainv);
+        dense_spd_inverse(c, L.A.view(), h.seg[h.lv.size() - 1], h.Ainv, h.db);
     }
+    // per-level instance offsets on the device (every level of a packed batch)
+    if (h.K > 1)
+        for (size_t l = 0; l < h.lv.size(); l++) {
+            Level &L = h.lv[l];
+            if (L.seg_d.p) continue;
+            L.seg_d = Buf(&c, sizeof(int64_t) * (size_t)(h.K + 1));
+            MDS_CUDA(cudaMemcpyAsync(L.seg_d.p, h.seg[l].data(), sizeof(int64_t) * (size_t)(h.K + 1),
+                                     cudaMemcpyHostToDevice, c.stream));
+        }
     level_storage(c, h, o);
     c.sync();
 }

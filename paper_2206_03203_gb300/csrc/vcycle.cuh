@@ -944,7 +944,7 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
     Level &L = h.lv[l];
     int last = (int)h.lv.size() - 1;
     if (l == last && h.dense) {
-        dense_apply(c, h.Ainv.as<double>(), h.nd, NR, b, x);
+        dense_apply(c, h.db, h.Ainv.as<double>(), NR, b, x);
         return;
     }
     if (l == last && h.diagonal) {  // no couplings: exact x = b / a_ii

@@ -24,7 +24,9 @@ derived from (seed, instance, fracture, field).
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass, field
+from decimal import Decimal, getcontext
 from typing import List, Optional
 
 import numpy as np
@@ -164,6 +166,74 @@ def rasterize(dim: int, n: int, rects: List[Rect]):
             np.asarray(ap, dtype=np.float64).reshape(nf))
 
 
+# ---------------------------------------------------------------------------
+# exp, log and cos from +, -, *, / and exact power-of-two scaling only (Taylor
+# and atanh series after an argument reduction), evaluated in a fixed order:
+# the generated instances are then bit-identical on every IEEE-754 machine,
+# whereas library transcendental functions differ in their last bits between
+# platforms.  About 1e-16 relative accuracy is all an input generator needs.
+# ---------------------------------------------------------------------------
+
+def _split(x: Decimal):
+    """x = hi + lo with hi holding 32 significant bits (hi * k exact for |k| < 2^21)."""
+    m, e = math.frexp(float(x))
+    hi = math.ldexp(math.floor(m * 2.0 ** 32) / 2.0 ** 32, e)
+    return hi, float(x - Decimal(hi))
+
+
+getcontext().prec = 60
+_LN2 = Decimal("0.69314718055994530941723212145817656807550013436025525412068")
+_LN10 = Decimal("2.30258509299404568401799145468436420760110148862877297603333")
+_PI = Decimal("3.14159265358979323846264338327950288419716939937510582097494")
+_LN2_HI, _LN2_LO = _split(_LN2)
+_LN10_D = float(_LN10)
+_TWO_PI = float(2 * _PI)
+
+
+def portable_exp(x: np.ndarray) -> np.ndarray:
+    """exp(x): x = k ln2 + r, |r| <= ln2 / 2, exp(r) by its Taylor series
+    (Horner, 16 terms), times 2^k."""
+    x = np.asarray(x, dtype=np.float64)
+    k = np.rint(x * (1.0 / float(_LN2)))
+    r = (x - k * _LN2_HI) - k * _LN2_LO
+    p = np.ones_like(r)
+    for n in range(16, 0, -1):
+        p = 1.0 + p * (r / n)
+    return np.ldexp(p, k.astype(np.int64))
+
+
+def portable_log(y: np.ndarray) -> np.ndarray:
+    """log(y), y > 0: y = m 2^e with m in [sqrt(1/2), sqrt(2)), log m =
+    2 atanh(s) with s = (m - 1) / (m + 1), |s| < 0.172 (series to s^27)."""
+    y = np.asarray(y, dtype=np.float64)
+    m, e = np.frexp(y)
+    low = m < 0.70710678118654752440
+    m = np.where(low, m * 2.0, m)
+    e = np.where(low, e - 1, e).astype(np.float64)
+    s = (m - 1.0) / (m + 1.0)
+    s2 = s * s
+    t = np.zeros_like(s)
+    for q in range(27, 1, -2):
+        t = s2 * (1.0 / q + t)
+    logm = 2.0 * (s + s * t)
+    return e * _LN2_HI + (e * _LN2_LO + logm)
+
+
+def portable_cos_2pi(u: np.ndarray) -> np.ndarray:
+    """cos(2 pi u): reduced by symmetry to x = 2 pi w, w in [0, 1/4], then the
+    Taylor series of cos x (14 terms)."""
+    u = np.asarray(u, dtype=np.float64)
+    w = np.abs(u - np.rint(u))          # [0, 1/2]
+    neg = w > 0.25
+    w = np.where(neg, 0.5 - w, w)       # cos(2 pi w) = -cos(2 pi (1/2 - w))
+    x = w * _TWO_PI
+    x2 = x * x
+    c = np.ones_like(x)
+    for n in range(28, 0, -2):
+        c = 1.0 - c * (x2 / (n * (n - 1)))
+    return np.where(neg, -c, c)
+
+
 def lognormal_km(seed: int, inst: int, n_cells: int, sigma: float) -> np.ndarray:
     """k_m = exp(sigma z), z iid N(0,1) per cell by Box-Muller (cosine branch)."""
     if sigma == 0.0:
@@ -172,8 +242,8 @@ def lognormal_km(seed: int, inst: int, n_cells: int, sigma: float) -> np.ndarray
     d = draws(key, 2 * n_cells)
     u1 = to_unit(d[0::2])
     u2 = to_unit(d[1::2])
-    z = np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
-    return np.exp(sigma * z)
+    z = np.sqrt(-2.0 * portable_log(1.0 - u1)) * portable_cos_2pi(u2)
+    return portable_exp(sigma * z)
 
 
 def make_instance(name, dim, n, km, rects, pD_left=None, pD_right=None, meta=None) -> Instance:
@@ -263,7 +333,7 @@ def random_rects_3d(n: int, seed: int, inst: int, n_rect: int, side=(0.2, 0.8),
             hi.append(off + cells)
         if kf is None:
             e = log10kf[0] + (log10kf[1] - log10kf[0]) * float(to_unit(d[6:7])[0])
-            k = float(10.0 ** e)
+            k = float(portable_exp(np.array([e * _LN10_D]))[0])  # 10^e
         else:
             k = kf
         rects.append(Rect(axis, plane, tuple(lo), tuple(hi), k, a))

@@ -673,7 +673,7 @@ def test_packed_batch_of_uneven_instances(ctx, oracle_mod, torch_mod):
     x = np.zeros(2 * sys_.N)
     code, st = ctx.solve(sys_, prec, None, x, nrhs=2)
     assert code == 0 and len(st) == 10
-    M = oracle_mod.ML(Ao, NM)
+    M = oracle_mod.ML(Ao, NM, segments=(mo, fo))
     for k in range(5):
         rows = np.r_[mo[k]:mo[k + 1], NM + fo[k]:NM + fo[k + 1]]
         for c in range(2):
@@ -685,6 +685,38 @@ def test_packed_batch_of_uneven_instances(ctx, oracle_mod, torch_mod):
             xk = x[c * sys_.N:(c + 1) * sys_.N][rows]
             Ak = Ao[rows][:, rows]
             assert np.linalg.norm(be[rows] - Ak @ xk) / np.linalg.norm(be[rows]) <= 1.01e-8
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
+def test_packed_hierarchies_bit_exact(ctx, oracle_mod, precision):
+    """A packed batch is coarsened instance by instance: every level, aggregate
+    map and root set of both hierarchies equals the oracle's segmented set-up,
+    and the last level holds at most n_coarse rows of each instance."""
+    insts = [inputs.random_rects_3d(n, 22060304, k, 1 + k % 4, nrhs=1, random_dirichlet=True)
+             for k, n in enumerate([9, 12, 8, 14, 11, 10])]
+    sys_ = ctx.assemble_batch(insts)
+    mo, fo = sys_.instances()
+    Ao, _, NM = packed_oracle(oracle_mod, insts)
+    code = {"fp64": 64, "bf16": 16}[precision]
+    prec = ctx.setup(sys_, precision=precision, n_coarse=48, format="csr")
+    M = oracle_mod.ML(Ao, NM, segments=(mo, fo), n_coarse=48, prec=code)
+    for block in (0, 1):
+        amg = M.amg(block)
+        assert prec.info(block)["nlevels"] == amg.nlevels
+        assert np.all(np.diff(amg.segments(amg.nlevels - 1)) <= 48)
+        for l in range(amg.nlevels):
+            Ag, agg, roots = prec.level_host(block, l)
+            assert same_csr(Ag, amg.level_A(l)), (block, l)
+            assert np.array_equal(roots, amg.roots(l)), (block, l)
+            ao = amg.agg(l)
+            assert (agg is None and ao is None) or np.array_equal(agg, ao), (block, l)
+    rng = np.random.default_rng(2)
+    for block, n in ((0, NM), (1, sys_.n_f)):
+        b = rng.standard_normal(n)
+        import torch
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        ctx.vcycle(prec, block, torch.as_tensor(b, device="cuda"), x)
+        assert maxrel(x.cpu().numpy(), M.amg(block).vcycle(b)) < (1e-12 if precision == "fp64" else 5e-5)
 
 
 def test_packed_batch_per_problem_iteration_cap(ctx, torch_mod):

@@ -71,3 +71,29 @@ def test_batch_sizes_range():
 def test_planes_3d_counts():
     inst = inputs.planes_3d(n=16)
     assert inst.n_f == 9 * 16 * 16
+
+
+def stored_digests():
+    return dict(l.split() for l in open(os.path.join(GOLD, "input_digests.txt")) if l.strip() and l[0] != "#")
+
+
+def test_generated_instances_match_stored_digests():
+    """The generator uses no library transcendental function, so its output is
+    the same bits on every IEEE-754 machine (the stored digests and iteration
+    counts were written on another machine than the GPU tests run on)."""
+    import sys
+    sys.path.insert(0, GOLD)
+    import make_input_digests
+    assert make_input_digests.digests() == stored_digests()
+
+
+def test_portable_elementary_functions():
+    rng = np.random.default_rng(0)
+    x = rng.uniform(-14.0, 14.0, 100000)
+    assert np.max(np.abs(inputs.portable_exp(x) / np.exp(x) - 1.0)) <= 4e-16
+    assert inputs.portable_exp(np.array([0.0]))[0] == 1.0
+    y = np.concatenate([rng.uniform(0.0, 1.0, 100000), [2.0 ** -53, 0.5, 1.0, 3.0]])
+    assert np.max(np.abs(inputs.portable_log(y) - np.log(y))) <= 2e-15
+    assert inputs.portable_log(np.array([1.0]))[0] == 0.0
+    u = np.concatenate([rng.uniform(0.0, 1.0, 100000), [0.0, 0.25, 0.5, 0.75]])
+    assert np.max(np.abs(inputs.portable_cos_2pi(u) - np.cos(2.0 * np.pi * u))) <= 2e-15
