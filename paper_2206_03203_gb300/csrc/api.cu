@@ -579,9 +579,10 @@ static void vcycle_f64(Ctx &c, Hierarchy &h, const double *b, double *x, int nr)
         return;
     }
     int64_t n = h.lv[0].A.nrow * nr;
-    cast_f64_f32(c, b, h.lv[0].b.as<float>(), n);
+    const LiveMap lm = level_live(c, h.lv[0]);
+    cast_f64_f32(c, b, h.lv[0].b.as<float>(), n, lm, nr);
     vcycle_apply(c, h, h.lv[0].b.p, h.lv[0].x.p, nr);
-    cast_f32_f64(c, h.lv[0].x.as<float>(), x, n);
+    cast_f32_f64(c, h.lv[0].x.as<float>(), x, n, lm, nr);
 }
 
 // Algorithm 1 (block lower), and the block-diagonal / block-upper variants,
@@ -606,7 +607,7 @@ void precond_apply(mds_precond p, const double *r, double *z, int nr) {
     if (kind == MDS_BLOCK_UPPER && p->has_f) {
         // z_f = Q_ff r_f; r_m <- r_m - A_mf z_f; z_m = Q_mm r_m
         vcycle_f64(c, HF, rf, zf, nr);
-        spmv_sub_f64(c, Amf, rm, zf, p->tf64.as<double>(), nr);
+        spmv_sub_f64(c, Amf, rm, zf, p->tf64.as<double>(), nr, level_live(c, HS.lv[0]));
         vcycle_f64(c, HS, p->tf64.as<double>(), zm, nr);
         return;
     }
@@ -632,19 +633,21 @@ void precond_apply(mds_precond p, const double *r, double *z, int nr) {
         MDS_CUDA(cudaStreamWaitEvent(c.stream, c.ev_join, 0));
         return;
     }
-    // step 1: z_m = Q_mm r_m
+    // step 1: z_m = Q_mm r_m  (in a batched solve only the live instances' rows)
+    const LiveMap lmm = level_live(c, HS.lv[0]);
     if (HS.prec == 64) {
         vcycle_apply(c, HS, rm, zm, nr);
     } else {
-        cast_f64_f32(c, rm, HS.lv[0].b.as<float>(), nm * nr);
+        cast_f64_f32(c, rm, HS.lv[0].b.as<float>(), nm * nr, lmm, nr);
         vcycle_apply(c, HS, HS.lv[0].b.p, HS.lv[0].x.p, nr);
-        cast_f32_f64(c, HS.lv[0].x.as<float>(), zm, nm * nr);
+        cast_f32_f64(c, HS.lv[0].x.as<float>(), zm, nm * nr, lmm, nr);
     }
     if (!p->has_f) return;
     // step 2: r_f <- r_f - A_fm z_m (block lower only); step 3: z_f = Q_ff r_f
+    const LiveMap lmf = level_live(c, HF.lv[0]);
     if (HF.prec == 64) {
         if (kind == MDS_BLOCK_LOWER) {
-            spmv_sub_f64(c, Afm, rf, zm, p->tf64.as<double>(), nr);
+            spmv_sub_f64(c, Afm, rf, zm, p->tf64.as<double>(), nr, lmf);
             vcycle_apply(c, HF, p->tf64.as<double>(), zf, nr);
         } else {
             vcycle_apply(c, HF, rf, zf, nr);
@@ -653,11 +656,11 @@ void precond_apply(mds_precond p, const double *r, double *z, int nr) {
     } else {
         float *bf = HF.lv[0].b.as<float>();
         if (kind == MDS_BLOCK_LOWER)
-            spmv_sub_f64_xf(c, Afm, rf, HS.lv[0].x.as<float>(), bf, nr);
+            spmv_sub_f64_xf(c, Afm, rf, HS.lv[0].x.as<float>(), bf, nr, lmf);
         else
-            cast_f64_f32(c, rf, bf, nf * nr);
+            cast_f64_f32(c, rf, bf, nf * nr, lmf, nr);
         vcycle_apply(c, HF, HF.lv[0].b.p, HF.lv[0].x.p, nr);
-        cast_f32_f64(c, HF.lv[0].x.as<float>(), zf, nf * nr);
+        cast_f32_f64(c, HF.lv[0].x.as<float>(), zf, nf * nr, lmf, nr);
         if (kind == MDS_BLOCK_DIAG && p->ff_negative) scale_f64(c, zf, -1.0, nf * nr);
     }
 }

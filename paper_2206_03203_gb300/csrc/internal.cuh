@@ -110,6 +110,60 @@ struct KTimerRec {
     cudaEvent_t e0, e1;
 };
 
+// Rows of a packed batch whose instance is still iterating.  The batched
+// solve's kernels skip every thread block whose rows all belong to finished
+// instances: the system is block diagonal, so no live row reads those rows.
+// Row spaces are one part (the rows of one block of the system or one level
+// of a hierarchy: instance k owns rows [seg[k], seg[k+1])) or two parts (the
+// whole system: matrix rows by seg, then fracture rows n1 + [seg2[k],
+// seg2[k+1])).  seg == NULL: every row is live.
+struct LiveMap {
+    const int64_t *seg = nullptr;
+    const int64_t *seg2 = nullptr;
+    int64_t n1 = 0;
+    const int8_t *live = nullptr;
+    int K = 0;
+};
+
+__device__ __forceinline__ int seg_find(const int64_t *seg, int K, int64_t r) {
+    int lo = 0, hi = K - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (seg[mid] <= r)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool seg_range_live(const int64_t *seg, const int8_t *live, int K, int64_t a, int64_t b) {
+    const int k1 = seg_find(seg, K, b);
+    for (int k = seg_find(seg, K, a); k <= k1; k++)
+        if (live[k]) return true;
+    return false;
+}
+
+// Whether rows [r0, r1) hold a row of a live instance; called by every
+// thread of the block (one thread searches, the block shares the answer).
+// The flags are written by host copies between solver steps, never by a
+// kernel, so this may run before the programmatic dependency wait.
+__device__ __forceinline__ bool block_rows_live(const LiveMap &m, int64_t r0, int64_t r1) {
+    if (!m.seg) return true;
+    __shared__ int any_live;
+    if (threadIdx.x == 0) {
+        bool a = false;
+        if (r0 < r1) {
+            if (r0 < m.n1 || !m.seg2) a = seg_range_live(m.seg, m.live, m.K, r0, (m.seg2 && r1 > m.n1 ? m.n1 : r1) - 1);
+            if (!a && m.seg2 && r1 > m.n1)
+                a = seg_range_live(m.seg2, m.live, m.K, (r0 > m.n1 ? r0 : m.n1) - m.n1, r1 - 1 - m.n1);
+        }
+        any_live = a;
+    }
+    __syncthreads();
+    return any_live != 0;
+}
+
 // One launch recorded while a CUDA graph is being captured: its accounting is
 // replayed, and its events (when its class is timed) read, at every replay.
 struct GraphRec {
@@ -171,6 +225,9 @@ struct Ctx {
     // independent V-cycles of the block-diagonal preconditioner)
     cudaStream_t side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // instance flags of the batched solve in progress (NULL otherwise): the
+    // kernels of a packed batch skip the rows of finished instances
+    const int8_t *live = nullptr;
     // device address of the static workspace of mds_solve_noalloc on this
     // context's device, resolved by mds_create
     double *noalloc_scratch = nullptr;
@@ -325,13 +382,17 @@ int64_t scan_counts(Ctx &c, const int32_t *cnt, int32_t *out, int64_t n);
 void fill_i32(Ctx &c, int32_t *p, int32_t v, int64_t n);
 void fill_f64(Ctx &c, double *p, double v, int64_t n);
 void scale_f64(Ctx &c, double *p, double a, int64_t n);  // p <- a p
-void cast_f64_f32(Ctx &c, const double *in, float *out, int64_t n);
-void cast_f32_f64(Ctx &c, const float *in, double *out, int64_t n);
-// y = A x (FP64 CSR), nr in {1, 2, 4, 8} interleaved columns
-void spmv_f64(Ctx &c, const mds_csr &A, const double *x, double *y, int kclass, int nr = 1);
+// element casts of n = rows x nr interleaved entries; lm: rows to convert
+void cast_f64_f32(Ctx &c, const double *in, float *out, int64_t n, const LiveMap &lm = {}, int nr = 1);
+void cast_f32_f64(Ctx &c, const float *in, double *out, int64_t n, const LiveMap &lm = {}, int nr = 1);
+// y = A x (FP64 CSR), nr in {1, 2, 4, 8} interleaved columns; lm: rows to
+// compute (blocks of finished instances of a batch skipped)
+void spmv_f64(Ctx &c, const mds_csr &A, const double *x, double *y, int kclass, int nr = 1, const LiveMap &lm = {});
 // out = r - A x with out in FP64 or FP32
-void spmv_sub_f64(Ctx &c, const mds_csr &A, const double *r, const double *x, double *out, int nr = 1);
-void spmv_sub_f64_xf(Ctx &c, const mds_csr &A, const double *r, const float *x, float *out, int nr = 1);
+void spmv_sub_f64(Ctx &c, const mds_csr &A, const double *r, const double *x, double *out, int nr = 1,
+                  const LiveMap &lm = {});
+void spmv_sub_f64_xf(Ctx &c, const mds_csr &A, const double *r, const float *x, float *out, int nr = 1,
+                     const LiveMap &lm = {});
 
 // ---- assembly (k_assemble.cu) ----
 struct SystemData {
@@ -384,7 +445,21 @@ struct Level {
     Buf sell_ptr, sell_len, sell_col, sell_val, sell_perm;
     Buf b, x, r, y, d, t;  // work vectors in the vector precision
     Buf seg_d;             // int64 [K + 1] instance row offsets (packed batches)
+    int K = 1;             // instances (packed batches)
+    int sell_sigma = 1;    // SELL sorting window (rows)
 };
+
+// The liveness map of one level (every row live outside a batched solve).
+inline LiveMap level_live(const Ctx &c, const Level &L) {
+    LiveMap m;
+    if (c.live && L.K > 1 && L.seg_d.p) {
+        m.seg = L.seg_d.as<int64_t>();
+        m.n1 = L.A.nrow;
+        m.live = c.live;
+        m.K = L.K;
+    }
+    return m;
+}
 
 // One diagonal block of the coarsest level: its first row, the start of its
 // n x n row-major matrices, its size.
@@ -434,9 +509,12 @@ void level_storage(Ctx &c, Hierarchy &h, const mds_setup_opts &o);
 // Cholesky of each diagonal block [seg[k], seg[k+1]) of the SPD matrix A
 // (stored densely), then its inverse; fills the block table.
 void dense_spd_inverse(Ctx &c, const mds_csr &A, const std::vector<int64_t> &seg, Buf &Ainv, DenseBlocks &db);
-// y = M x for the block-diagonal inverse M, nr in {1, 2, 4, 8} interleaved columns
-void dense_apply(Ctx &c, const DenseBlocks &db, const double *M, int nr, const double *x, double *y);
-void dense_apply(Ctx &c, const DenseBlocks &db, const double *M, int nr, const float *x, float *y);
+// y = M x for the block-diagonal inverse M, nr in {1, 2, 4, 8} interleaved
+// columns; on (optional): per block, whether to compute it
+void dense_apply(Ctx &c, const DenseBlocks &db, const double *M, int nr, const double *x, double *y,
+                 const int8_t *on = nullptr);
+void dense_apply(Ctx &c, const DenseBlocks &db, const double *M, int nr, const float *x, float *y,
+                 const int8_t *on = nullptr);
 
 // ---- V-cycle (k_vcycle.cu) ----
 // x = V(b) on level 0 of h for nr in {1, 2, 4, 8} interleaved columns; b and

@@ -247,12 +247,16 @@ __device__ __forceinline__ int dblk_of(const DBlk *blk, int K, int64_t row) {
 constexpr int DPRE = 16;
 template <class XT, int NR>
 __global__ void k_dense_apply(const double *__restrict__ Mall, const DBlk *__restrict__ blk, int K, int64_t nrow,
-                              const XT *__restrict__ xall, XT *__restrict__ yall) {
+                              const XT *__restrict__ xall, XT *__restrict__ yall, const int8_t *__restrict__ on) {
     int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     int lane = threadIdx.x % 32;
-    const bool live = row < nrow;
+    bool live = row < nrow;
     DBlk b{0, 0, 0};
-    if (live) b = blk[K > 1 ? dblk_of(blk, K, row) : 0];
+    if (live) {
+        const int k = K > 1 ? dblk_of(blk, K, row) : 0;
+        b = blk[k];
+        if (on && !on[k]) live = false;  // a finished instance of a batched solve
+    }
     const int64_t n = b.n, i = row - b.row;
     const double *M = Mall + b.off + i * n;
     const XT *x = xall + b.row * NR;
@@ -290,26 +294,28 @@ __global__ void k_dense_apply(const double *__restrict__ Mall, const DBlk *__res
 }
 
 template <class XT>
-static void dense_apply_t(Ctx &c, const DenseBlocks &db, const double *M, int nr, const XT *x, XT *y) {
+static void dense_apply_t(Ctx &c, const DenseBlocks &db, const double *M, int nr, const XT *x, XT *y,
+                          const int8_t *on) {
     const int64_t n = db.nrow;
     double bytes = 8.0 * (double)db.total + 2.0 * sizeof(XT) * n * nr;
     unsigned g = grid_for(n * 32, 256);
     const DBlk *B = db.blk.as<DBlk>();
     switch (nr) {
-        case 1: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 1>), g, 256, 0, M, B, db.K, n, x, y); break;
-        case 2: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 2>), g, 256, 0, M, B, db.K, n, x, y); break;
-        case 4: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 4>), g, 256, 0, M, B, db.K, n, x, y); break;
-        case 8: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 8>), g, 256, 0, M, B, db.K, n, x, y); break;
+        case 1: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 1>), g, 256, 0, M, B, db.K, n, x, y, on); break;
+        case 2: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 2>), g, 256, 0, M, B, db.K, n, x, y, on); break;
+        case 4: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 4>), g, 256, 0, M, B, db.K, n, x, y, on); break;
+        case 8: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 8>), g, 256, 0, M, B, db.K, n, x, y, on); break;
         default: throw Error(MDS_ERR_INVALID, "dense apply: column count must be 1, 2, 4 or 8");
     }
 }
 
-void dense_apply(Ctx &c, const DenseBlocks &db, const double *M, int nr, const double *x, double *y) {
-    dense_apply_t<double>(c, db, M, nr, x, y);
+void dense_apply(Ctx &c, const DenseBlocks &db, const double *M, int nr, const double *x, double *y,
+                 const int8_t *on) {
+    dense_apply_t<double>(c, db, M, nr, x, y, on);
 }
 
-void dense_apply(Ctx &c, const DenseBlocks &db, const double *M, int nr, const float *x, float *y) {
-    dense_apply_t<float>(c, db, M, nr, x, y);
+void dense_apply(Ctx &c, const DenseBlocks &db, const double *M, int nr, const float *x, float *y, const int8_t *on) {
+    dense_apply_t<float>(c, db, M, nr, x, y, on);
 }
 
 }  // namespace mds

@@ -1012,16 +1012,27 @@ __global__ void k_breduce(const double *__restrict__ partial, int nchunk, int nq
 
 // W(i, c) += SIGN sum_q coef[p][q] V_q(i, c) over one chunk per block;
 // optional partials of W(i, c)^2 as partial[chunk][c] (q = 0 layout).
+// qlim (optional): the chunk's instance uses V_q for q < max over its
+// columns of qlim[p] only (the coefficients beyond a column's own count are
+// zero; later V_q rows of an instance that stopped were never computed).
 template <int NR, int SIGN>
 __global__ void __launch_bounds__(RED_BLOCK) k_bmaxpy(const Chunk *__restrict__ ch, const double *__restrict__ V,
                                                        int64_t ldq, int nq, const double *__restrict__ coef,
                                                        double *__restrict__ W, double *__restrict__ partial,
-                                                       const int8_t *__restrict__ mask) {
+                                                       const int8_t *__restrict__ mask,
+                                                       const int32_t *__restrict__ qlim) {
     mds_pdl_entry();
     __shared__ double cs[NR][32];
     __shared__ double ws[RED_BLOCK / 32][NR];
     Chunk k = ch[blockIdx.x];
     if (chunk_skipped<NR>(mask, k.inst)) return;
+    if (qlim) {
+        int q1 = 0;
+#pragma unroll
+        for (int c = 0; c < NR; c++) q1 = max(q1, qlim[(int64_t)k.inst * NR + c]);
+        if (q1 == 0) return;
+        nq = min(nq, q1);
+    }
     for (int t = threadIdx.x; t < NR * 32; t += blockDim.x) {
         int c = t / 32, q = t % 32;
         cs[c][q] = q < nq ? coef[((int64_t)k.inst * NR + c) * 32 + q] : 0.0;
@@ -1087,6 +1098,7 @@ __global__ void k_bscale(const Chunk *__restrict__ ch, double *__restrict__ W, c
                          const int8_t *__restrict__ active) {
     mds_pdl_entry();
     Chunk k = ch[blockIdx.x];
+    if (chunk_skipped<NR>(active, k.inst)) return;  // a finished instance: its rows are no longer used
     double f[NR];
 #pragma unroll
     for (int c = 0; c < NR; c++) {
@@ -1219,7 +1231,28 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
     Buf part(&c, sizeof(double) * (size_t)(QMAX * nch * NR));
     // per-problem arrays with stride 32: cs, sn, g, y, h1, h2, nsq; scalars stride 8
     Buf pa(&c, sizeof(double) * (size_t)P * 32 * 7), psc(&c, sizeof(double) * (size_t)P * 8);
-    Buf act(&c, (size_t)P), kd(&c, sizeof(int32_t) * (size_t)P), f2(&c, (size_t)P);
+    // act: P problem flags, then K instance flags (an instance is live while
+    // one of its columns iterates; the kernels skip the rows of the others)
+    Buf act(&c, (size_t)(P + K)), kd(&c, sizeof(int32_t) * (size_t)P), f2(&c, (size_t)P);
+    const int8_t *ilive = act.as<int8_t>() + P;
+    Buf mo_d(&c, sizeof(int64_t) * (size_t)(K + 1)), fo_d(&c, sizeof(int64_t) * (size_t)(K + 1));
+    MDS_CUDA(cudaMemcpyAsync(mo_d.p, moff.data(), sizeof(int64_t) * (size_t)(K + 1), cudaMemcpyHostToDevice, c.stream));
+    MDS_CUDA(cudaMemcpyAsync(fo_d.p, foff.data(), sizeof(int64_t) * (size_t)(K + 1), cudaMemcpyHostToDevice, c.stream));
+    LiveMap sysmap;
+    if (K > 1) {
+        sysmap.seg = mo_d.as<int64_t>();
+        sysmap.seg2 = fo_d.as<int64_t>();
+        sysmap.n1 = NM;
+        sysmap.live = ilive;
+        sysmap.K = K;
+    }
+    // the batched preconditioner's kernels read the instance flags from the
+    // context while this solve runs
+    struct LiveScope {
+        Ctx &c;
+        LiveScope(Ctx &cc, const int8_t *l) : c(cc) { c.live = l; }
+        ~LiveScope() { c.live = nullptr; }
+    } live_scope(c, K > 1 ? ilive : nullptr);
     double *cs = pa.as<double>(), *sn = cs + (size_t)P * 32, *g = sn + (size_t)P * 32, *y = g + (size_t)P * 32,
            *h1 = y + (size_t)P * 32, *h2 = h1 + (size_t)P * 32, *nsq = h2 + (size_t)P * 32;
     double *sc = psc.as<double>();
@@ -1231,11 +1264,21 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
     MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, (k_to_interleaved<NR>), eg, RED_BLOCK, 0, N, Xcol, c0, Xi.as<double>());
     dim3 pgrid((unsigned)P, 1);
     // per-problem squared norms of a vector into nsq[p * 32]
-    auto norms = [&](const double *w) {
-        MDS_LAUNCH(c, KC_NONE, 8.0 * N * NR, (k_bdot<NR>), dim3(nch, 1), RED_BLOCK, 0, CHp, nch, Vp, ldq, 0, w, PT,
-                   (const int8_t *)nullptr);
-        MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, 1), 32, 0, PT, nch, 1, NR, IO, IL, P, nsq, 0,
-                   (const int8_t *)nullptr);
+    auto norms = [&](const double *w, const int8_t *mk) {
+        MDS_LAUNCH(c, KC_NONE, 8.0 * N * NR, (k_bdot<NR>), dim3(nch, 1), RED_BLOCK, 0, CHp, nch, Vp, ldq, 0, w, PT, mk);
+        MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, 1), 32, 0, PT, nch, 1, NR, IO, IL, P, nsq, 0, mk);
+    };
+    // upload the problem flags hact and the instance flags derived from them
+    std::vector<int8_t> hbuf(P + K);
+    auto upload_flags = [&](const std::vector<int8_t> &h) {
+        for (int p = 0; p < P; p++) hbuf[p] = h[p];
+        for (int k = 0; k < K; k++) {
+            int8_t a = 0;
+            for (int q = 0; q < NR; q++) a |= h[(size_t)k * NR + q];
+            hbuf[P + k] = a;
+        }
+        std::memcpy(c.h_pin, hbuf.data(), (size_t)(P + K));
+        MDS_CUDA(cudaMemcpyAsync(act.p, c.h_pin, (size_t)(P + K), cudaMemcpyHostToDevice, c.stream));
     };
     std::vector<double> host(P * 8), bn(P);
     auto fetch = [&](const double *d, int stride, int slot) {
@@ -1248,7 +1291,8 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
     };
     MDS_REQUIRE((size_t)P * 32 * sizeof(double) <= Ctx::PIN_BYTES, MDS_ERR_INVALID,
                 "too many batched problems (instances x columns > 4096)");
-    norms(Bi.as<double>());
+    c.live = nullptr;  // b and the first residual: every row
+    norms(Bi.as<double>(), nullptr);
     {
         std::vector<double> b2 = fetch(nsq, 32, 0);
         for (int p = 0; p < P; p++) {
@@ -1263,9 +1307,19 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
         if (out[p].status == MDS_ERR_NONFINITE) done[p] = 1;
     std::vector<int8_t> hact(P);
     std::vector<int32_t> hkd(P);
+    bool first_cycle = true;
     for (;;) {
-        spmv_sub_f64(c, A, Bi.as<double>(), Xi.as<double>(), Vp, NR);  // V0 = B - A X
-        norms(Vp);
+        // V0 = B - A X for the problems not yet done
+        const int8_t *mk = nullptr;
+        if (!first_cycle && K > 1) {
+            for (int p = 0; p < P; p++) hact[p] = done[p] ? 0 : 1;
+            upload_flags(hact);
+            c.live = ilive;
+            mk = act.as<int8_t>();
+        }
+        spmv_sub_f64(c, A, Bi.as<double>(), Xi.as<double>(), Vp, NR, mk ? sysmap : LiveMap{});
+        norms(Vp, mk);
+        first_cycle = false;
         std::vector<double> r2 = fetch(nsq, 32, 0);
         bool any = false;
         for (int p = 0; p < P; p++) {
@@ -1289,18 +1343,15 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
             hact[p] = done[p] ? 0 : 1;
             hkd[p] = 0;
         }
-        std::memcpy(c.h_pin, hact.data(), (size_t)P);
-        MDS_CUDA(cudaMemcpyAsync(act.p, c.h_pin, (size_t)P, cudaMemcpyHostToDevice, c.stream));
+        upload_flags(hact);
+        if (K > 1) c.live = ilive;
         MDS_LAUNCH(c, KC_NONE, 0, k_bcycle_start, grid_for(P, 128), 128, 0, P, nsq, m, g, sc);
         MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, nch, RED_BLOCK, 0, CHp, Vp, sc, 1, act.as<int8_t>());
         for (int j = 0; j < m; j++) {
-            if (j > 0) {
-                std::memcpy(c.h_pin, hact.data(), (size_t)P);
-                MDS_CUDA(cudaMemcpyAsync(act.p, c.h_pin, (size_t)P, cudaMemcpyHostToDevice, c.stream));
-            }
+            if (j > 0) upload_flags(hact);
             double *vj = Vp + (size_t)j * ldq, *zj = Zp + (size_t)j * ldq, *w = Vp + (size_t)(j + 1) * ldq;
             M(vj, zj, NR);
-            spmv_f64(c, A, zj, w, KC_SPMV, NR);
+            spmv_f64(c, A, zj, w, KC_SPMV, NR, sysmap);
             int nq = j + 1;
             double fl = 2.0 * (double)N * NR * nq;
             // classical Gram-Schmidt for every problem; the second pass runs
@@ -1308,13 +1359,14 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
             // others' chunks return at once)
             for (int pass = 0; pass < 2; pass++) {
                 double *hh = pass == 0 ? h1 : h2;
-                const int8_t *mk = pass == 0 ? nullptr : f2.as<int8_t>();
+                // first pass: the active problems' instances; second: the flagged problems'
+                const int8_t *mk = pass == 0 ? act.as<int8_t>() : f2.as<int8_t>();
                 int kd = pass == 0 ? KC_GS_DOT : KC_NONE, ka = pass == 0 ? KC_GS_AXPY : KC_NONE;
                 MDS_LAUNCH_F(c, kd, 8.0 * N * NR * (nq + 1), fl, (k_bdot<NR>), dim3(nch, nq), RED_BLOCK, 0, CHp, nch, Vp,
                              ldq, nq, w, PT, mk);
                 MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, nq), 32, 0, PT, nch, nq, NR, IO, IL, P, hh, 0, mk);
                 MDS_LAUNCH_F(c, ka, 8.0 * N * NR * (nq + 2), fl, (k_bmaxpy<NR, -1>), nch, RED_BLOCK, 0, CHp, Vp, ldq,
-                             nq, hh, w, PT, mk);
+                             nq, hh, w, PT, mk, (const int32_t *)nullptr);
                 MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, 1), 32, 0, PT, nch, 1, NR, IO, IL, P, nsq, 0, mk);
                 if (pass == 0)
                     MDS_LAUNCH(c, KC_NONE, 0, k_bflag, grid_for(P, 128), 128, 0, P, nq, act.as<int8_t>(), h1, nsq,
@@ -1349,13 +1401,14 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
         MDS_CUDA(cudaMemcpyAsync(kd.p, c.h_pin, sizeof(int32_t) * (size_t)P, cudaMemcpyHostToDevice, c.stream));
         MDS_LAUNCH(c, KC_NONE, 0, k_bbacksolve, grid_for(P, 128), 128, 0, P, kd.as<int32_t>(), m, H.as<double>(), g, y);
         MDS_LAUNCH(c, KC_NONE, 8.0 * N * NR * (m + 2), (k_bmaxpy<NR, 1>), nch, RED_BLOCK, 0, CHp, Zp, ldq, m, y,
-                   Xi.as<double>(), nullptr, (const int8_t *)nullptr);
+                   Xi.as<double>(), nullptr, (const int8_t *)nullptr, kd.as<int32_t>());
         for (int p = 0; p < P; p++)
             if (hkd[p] > 0) rs[p]++;
     }
-    // true residuals at exit
+    // true residuals at exit (every row)
+    c.live = nullptr;
     spmv_sub_f64(c, A, Bi.as<double>(), Xi.as<double>(), Vp, NR);
-    norms(Vp);
+    norms(Vp, nullptr);
     std::vector<double> r2 = fetch(nsq, 32, 0);
     for (int p = 0; p < P; p++) {
         out[p].iterations = it[p];

@@ -131,77 +131,88 @@ void scale_f64(Ctx &c, double *p, double a, int64_t n) {
                256, 0, p, a, n);
 }
 
+// One contiguous range of `per` rows (nr entries each) per block, so that a
+// block of finished instances' rows returns at once.
 template <class A, class B>
-__global__ void k_cast(const A *__restrict__ in, B *__restrict__ out, int64_t n) {
+__global__ void k_cast(const A *__restrict__ in, B *__restrict__ out, int64_t rows, int nr, int64_t per, LiveMap lm) {
+    const int64_t r0 = (int64_t)blockIdx.x * per, r1 = r0 + per < rows ? r0 + per : rows;
+    if (!block_rows_live(lm, r0, r1)) return;
     mds_pdl_entry();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = (B)in[i];
+    for (int64_t i = r0 * nr + threadIdx.x; i < r1 * nr; i += blockDim.x) out[i] = (B)in[i];
 }
 
-void cast_f64_f32(Ctx &c, const double *in, float *out, int64_t n) {
+template <class A, class B> static void cast_rows(Ctx &c, const A *in, B *out, int64_t n, const LiveMap &lm, int nr) {
     if (n <= 0) return;
-    unsigned g = grid_for(n, 256);
-    MDS_LAUNCH(c, KC_NONE, 0, (k_cast<double, float>), g, 256, 0, in, out, n);
+    const int64_t rows = n / nr;
+    int64_t per = (rows + 8191) / 8192;  // at most 8192 blocks
+    per = per < 256 ? 256 : per;
+    unsigned g = (unsigned)((rows + per - 1) / per);
+    MDS_LAUNCH(c, KC_NONE, (sizeof(A) + sizeof(B)) * (double)n, (k_cast<A, B>), g, 256, 0, in, out, rows, nr, per, lm);
 }
 
-void cast_f32_f64(Ctx &c, const float *in, double *out, int64_t n) {
-    if (n <= 0) return;
-    unsigned g = grid_for(n, 256);
-    MDS_LAUNCH(c, KC_NONE, 0, (k_cast<float, double>), g, 256, 0, in, out, n);
+void cast_f64_f32(Ctx &c, const double *in, float *out, int64_t n, const LiveMap &lm, int nr) {
+    cast_rows<double, float>(c, in, out, n, lm, nr);
+}
+
+void cast_f32_f64(Ctx &c, const float *in, double *out, int64_t n, const LiveMap &lm, int nr) {
+    cast_rows<float, double>(c, in, out, n, lm, nr);
 }
 
 // ---------------------------------------------------------------- SpMV
 
 template <int G, class XT, class OT, int MODE, int NR>
-static void spmv_launch(Ctx &c, const mds_csr &A, const XT *x, const double *r, OT *y, int kclass) {
+static void spmv_launch(Ctx &c, const mds_csr &A, const XT *x, const double *r, OT *y, int kclass, const LiveMap &lm) {
     const int block = 256;
     double bytes = 12.0 * (double)A.nnz + 4.0 * (double)(A.nrow + 1) +
                    NR * (sizeof(XT) * (double)A.ncol + sizeof(OT) * (double)A.nrow + (MODE == 1 ? 8.0 * A.nrow : 0.0));
     unsigned grid = grid_for(A.nrow * G, block);
     MDS_LAUNCH_F(c, kclass, bytes, 2.0 * NR * A.nnz, (k_spmv_csr<G, double, XT, OT, MODE, NR>), grid, block, 0, A.nrow,
-                 A.row_ptr, A.col, A.val, x, r, y);
+                 A.row_ptr, A.col, A.val, x, r, y, lm);
 }
 
 template <int G, class XT, class OT, int MODE>
-static void spmv_nr(Ctx &c, const mds_csr &A, const XT *x, const double *r, OT *y, int kclass, int nr) {
+static void spmv_nr(Ctx &c, const mds_csr &A, const XT *x, const double *r, OT *y, int kclass, int nr,
+                    const LiveMap &lm) {
     switch (nr) {
-        case 1: spmv_launch<G, XT, OT, MODE, 1>(c, A, x, r, y, kclass); break;
-        case 2: spmv_launch<G, XT, OT, MODE, 2>(c, A, x, r, y, kclass); break;
-        case 4: spmv_launch<G, XT, OT, MODE, 4>(c, A, x, r, y, kclass); break;
-        case 8: spmv_launch<G, XT, OT, MODE, 8>(c, A, x, r, y, kclass); break;
+        case 1: spmv_launch<G, XT, OT, MODE, 1>(c, A, x, r, y, kclass, lm); break;
+        case 2: spmv_launch<G, XT, OT, MODE, 2>(c, A, x, r, y, kclass, lm); break;
+        case 4: spmv_launch<G, XT, OT, MODE, 4>(c, A, x, r, y, kclass, lm); break;
+        case 8: spmv_launch<G, XT, OT, MODE, 8>(c, A, x, r, y, kclass, lm); break;
         default: throw Error(MDS_ERR_INVALID, "SpMV column count must be 1, 2, 4 or 8");
     }
 }
 
 template <class XT, class OT, int MODE>
-static void spmv_dispatch(Ctx &c, const mds_csr &A, const XT *x, const double *r, OT *y, int kclass, int nr) {
+static void spmv_dispatch(Ctx &c, const mds_csr &A, const XT *x, const double *r, OT *y, int kclass, int nr,
+                          const LiveMap &lm) {
     if (A.nrow <= 0) return;
     // lanes per row: one thread per row for stencil-like rows (each thread
     // then has all of its row's loads in flight; measured 24 us vs 41 us with
     // four lanes on a 1.07M-row, 5-per-row FP64 operator), more for long rows
     double avg = A.nrow ? (double)A.nnz / (double)A.nrow : 0.0;
     if (avg <= 8.0)
-        spmv_nr<1, XT, OT, MODE>(c, A, x, r, y, kclass, nr);
+        spmv_nr<1, XT, OT, MODE>(c, A, x, r, y, kclass, nr, lm);
     else if (avg <= 16.0)
-        spmv_nr<2, XT, OT, MODE>(c, A, x, r, y, kclass, nr);
+        spmv_nr<2, XT, OT, MODE>(c, A, x, r, y, kclass, nr, lm);
     else if (avg <= 32.0)
-        spmv_nr<4, XT, OT, MODE>(c, A, x, r, y, kclass, nr);
+        spmv_nr<4, XT, OT, MODE>(c, A, x, r, y, kclass, nr, lm);
     else if (avg <= 64.0)
-        spmv_nr<8, XT, OT, MODE>(c, A, x, r, y, kclass, nr);
+        spmv_nr<8, XT, OT, MODE>(c, A, x, r, y, kclass, nr, lm);
     else
-        spmv_nr<32, XT, OT, MODE>(c, A, x, r, y, kclass, nr);
+        spmv_nr<32, XT, OT, MODE>(c, A, x, r, y, kclass, nr, lm);
 }
 
-void spmv_f64(Ctx &c, const mds_csr &A, const double *x, double *y, int kclass, int nr) {
-    spmv_dispatch<double, double, 0>(c, A, x, nullptr, y, kclass, nr);
+void spmv_f64(Ctx &c, const mds_csr &A, const double *x, double *y, int kclass, int nr, const LiveMap &lm) {
+    spmv_dispatch<double, double, 0>(c, A, x, nullptr, y, kclass, nr, lm);
 }
 
-void spmv_sub_f64(Ctx &c, const mds_csr &A, const double *r, const double *x, double *out, int nr) {
-    spmv_dispatch<double, double, 1>(c, A, x, r, out, KC_NONE, nr);
+void spmv_sub_f64(Ctx &c, const mds_csr &A, const double *r, const double *x, double *out, int nr, const LiveMap &lm) {
+    spmv_dispatch<double, double, 1>(c, A, x, r, out, KC_NONE, nr, lm);
 }
 
-void spmv_sub_f64_xf(Ctx &c, const mds_csr &A, const double *r, const float *x, float *out, int nr) {
-    spmv_dispatch<float, float, 1>(c, A, x, r, out, KC_NONE, nr);
+void spmv_sub_f64_xf(Ctx &c, const mds_csr &A, const double *r, const float *x, float *out, int nr,
+                     const LiveMap &lm) {
+    spmv_dispatch<float, float, 1>(c, A, x, r, out, KC_NONE, nr, lm);
 }
 
 }  // namespace mds

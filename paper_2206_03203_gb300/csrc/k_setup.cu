@@ -770,6 +770,7 @@ void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h,
         unsigned gr = grid_for(n, 256);
         Buf lid;
         if (h.K > 1) {
+            L.K = h.K;
             L.seg_d = Buf(&c, sizeof(int64_t) * (size_t)(h.K + 1));
             MDS_CUDA(cudaMemcpyAsync(L.seg_d.p, sg.data(), sizeof(int64_t) * (size_t)(h.K + 1),
                                      cudaMemcpyHostToDevice, c.stream));
@@ -906,6 +907,7 @@ void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h,
     if (h.K > 1)
         for (size_t l = 0; l < h.lv.size(); l++) {
             Level &L = h.lv[l];
+            L.K = h.K;
             if (L.seg_d.p) continue;
             L.seg_d = Buf(&c, sizeof(int64_t) * (size_t)(h.K + 1));
             MDS_CUDA(cudaMemcpyAsync(L.seg_d.p, h.seg[l].data(), sizeof(int64_t) * (size_t)(h.K + 1),

@@ -153,6 +153,7 @@ __global__ void k_sell_fill(int64_t n, int64_t nslice, int C, const int32_t *__r
 template <class VT> static void build_sell(Ctx &c, Level &L, int C, int sigma) {
     int64_t n = L.A.nrow;
     L.sell_c = C;
+    L.sell_sigma = sigma;
     L.sell_nslice = (n + C - 1) / C;
     int64_t ns = L.sell_nslice;
     L.sell_perm.reset();

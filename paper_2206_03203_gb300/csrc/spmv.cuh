@@ -13,7 +13,11 @@ template <int G, class VT, class XT, class OT, int MODE, int NR>
 __global__ void __launch_bounds__(256) k_spmv_csr(int64_t nrow, const int32_t *__restrict__ rp,
                                                    const int32_t *__restrict__ ci, const VT *__restrict__ v,
                                                    const XT *__restrict__ x, const double *__restrict__ r,
-                                                   OT *__restrict__ y) {
+                                                   OT *__restrict__ y, LiveMap lm) {
+    {
+        const int64_t r0 = (int64_t)blockIdx.x * (256 / G), r1 = r0 + 256 / G < nrow ? r0 + 256 / G : nrow;
+        if (!block_rows_live(lm, r0, r1)) return;
+    }
     mds_pdl_entry();
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t row = t / G;

@@ -46,7 +46,9 @@ template <class VT> struct LvlMat {
     const int32_t *sc;         // SELL columns
     const int32_t *perm;       // SELL stored row -> original row (NULL: identity)
     int C;                     // SELL slice height
+    int sigma;                 // SELL sorting window (a stored row's original row lies in its window)
     const float *rscale;       // row scales (NULL: unscaled)
+    LiveMap lm;                // rows of finished batch instances are skipped
 };
 
 // Matrix entries are streamed once per launch: load them evict-first so the
@@ -154,6 +156,22 @@ template <int G, class VT, class XT, int K, int NR, int PF>
 __global__ void __launch_bounds__(256) k_level(LvlMat<VT> A, const XT *__restrict__ dinv, const XT *__restrict__ b,
                                                const XT *__restrict__ xin, const int32_t *__restrict__ agg,
                                                const XT *__restrict__ xc, XT *__restrict__ out) {
+    {
+        // this block's rows (whole sorting windows for permuted SELL)
+        int64_t r0, r1;
+        if constexpr (G > 0) {
+            r0 = (int64_t)blockIdx.x * (256 / G);
+            r1 = r0 + 256 / G;
+        } else {
+            r0 = (int64_t)blockIdx.x * 256;
+            r1 = r0 + 256;
+            if (A.perm) {
+                r0 = r0 / A.sigma * A.sigma;
+                r1 = (r1 + A.sigma - 1) / A.sigma * A.sigma;
+            }
+        }
+        if (!block_rows_live(A.lm, r0, r1 < A.n ? r1 : A.n)) return;
+    }
     int64_t row;
     int lane;
     row_of<G>(row, lane);
@@ -273,28 +291,33 @@ __global__ void __launch_bounds__(256) k_level(LvlMat<VT> A, const XT *__restric
 // ---- elementwise kernels (NR interleaved columns; row of entry e = e / NR).
 // 1/D1 and the aggregate map are fixed while solving: a thread's first entry
 // of them is loaded before the dependency wait.
+// One contiguous range of `per` rows per block, so that a block of finished
+// batch instances' rows returns at once.
 template <class XT, int NR>
-__global__ void k_vc_x0(int64_t n, const XT *__restrict__ dinv, const XT *__restrict__ b, XT *__restrict__ x) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const XT d0 = e < n * NR ? dinv[e / NR] : (XT)0;
+__global__ void k_vc_x0(int64_t n, const XT *__restrict__ dinv, const XT *__restrict__ b, XT *__restrict__ x,
+                        int64_t per, LiveMap lm) {
+    const int64_t r0 = (int64_t)blockIdx.x * per, r1 = r0 + per < n ? r0 + per : n;
+    if (!block_rows_live(lm, r0, r1)) return;
+    int64_t e = r0 * NR + threadIdx.x;
+    const XT d0 = e < r1 * NR ? dinv[e / NR] : (XT)0;
     mds_pdl_wait();
     mds_pdl_trigger();
-    if (e < n * NR) x[e] = d0 * b[e];
-    for (e += stride; e < n * NR; e += stride) x[e] = dinv[e / NR] * b[e];
+    if (e < r1 * NR) x[e] = d0 * b[e];
+    for (e += blockDim.x; e < r1 * NR; e += blockDim.x) x[e] = dinv[e / NR] * b[e];
 }
 
 // y_(i,c) += x_c(agg_i, c)
 template <class XT, int NR>
 __global__ void k_vc_prolong(int64_t n, const int32_t *__restrict__ agg, const XT *__restrict__ xc,
-                             XT *__restrict__ y) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int32_t a0 = e < n * NR ? agg[e / NR] : -1;
+                             XT *__restrict__ y, int64_t per, LiveMap lm) {
+    const int64_t r0 = (int64_t)blockIdx.x * per, r1 = r0 + per < n ? r0 + per : n;
+    if (!block_rows_live(lm, r0, r1)) return;
+    int64_t e = r0 * NR + threadIdx.x;
+    const int32_t a0 = e < r1 * NR ? agg[e / NR] : -1;
     mds_pdl_wait();
     mds_pdl_trigger();
     if (a0 >= 0) y[e] += xc[(int64_t)a0 * NR + e % NR];
-    for (e += stride; e < n * NR; e += stride) {
+    for (e += blockDim.x; e < r1 * NR; e += blockDim.x) {
         int32_t a = agg[e / NR];
         if (a >= 0) y[e] += xc[(int64_t)a * NR + e % NR];
     }
@@ -331,7 +354,11 @@ __global__ void k_cheb_next(int64_t n, const XT *__restrict__ dinv, const XT *__
 constexpr int RPRE = 8;
 template <class XT, int NR>
 __global__ void k_vc_restrict(int64_t nc, const int32_t *__restrict__ off, const int32_t *__restrict__ mem,
-                              const XT *__restrict__ r, XT *__restrict__ bc) {
+                              const XT *__restrict__ r, XT *__restrict__ bc, LiveMap lm) {
+    {
+        const int64_t r0 = (int64_t)blockIdx.x * blockDim.x, r1 = r0 + blockDim.x < nc ? r0 + blockDim.x : nc;
+        if (!block_rows_live(lm, r0, r1)) return;
+    }
     int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int32_t q0 = 0, q1 = 0;
     if (I < nc) {
@@ -406,9 +433,11 @@ __global__ void k_sa_prolong(int64_t n, const int32_t *__restrict__ rp, const in
 
 // ---------------------------------------------------------------- host dispatch
 
-template <class VT> static LvlMat<VT> lvl_view(const Level &L) {
+template <class VT> static LvlMat<VT> lvl_view(const Ctx &c, const Level &L) {
     LvlMat<VT> m{};
     m.n = L.A.nrow;
+    m.lm = level_live(c, L);
+    m.sigma = L.sell_sigma > 0 ? L.sell_sigma : 1;
     m.rp = L.A.rowp();
     m.ci = L.A.cols();
     m.rscale = L.rscale.p ? L.rscale.as<float>() : nullptr;
@@ -429,7 +458,7 @@ template <class VT> static LvlMat<VT> lvl_view(const Level &L) {
 template <class VT, class XT, int K, int NR, int PF>
 static void launch_level_pf(Ctx &c, const Level &L, const XT *dinv, const XT *b, const XT *xin, const int32_t *agg,
                          const XT *xc, XT *out, int64_t nc) {
-    LvlMat<VT> m = lvl_view<VT>(L);
+    LvlMat<VT> m = lvl_view<VT>(c, L);
     int64_t n = L.A.nrow;
     double vb = L.fmt == FMT_SELL ? (sizeof(VT) + 4.0) * (double)L.sell_nnz : (sizeof(VT) + 4.0) * L.A.nnz;
     double xb = sizeof(XT) * (double)NR;
@@ -530,6 +559,14 @@ static unsigned ew_grid(int64_t n) {
     return g > 4096 ? 4096 : g;
 }
 
+// Elementwise level kernels: `ew_rows(n)` consecutive rows per block (at
+// least 256, at most 8192 blocks), `ew_blocks(n)` blocks.
+static int64_t ew_rows(int64_t n) {
+    int64_t per = (n + 8191) / 8192;
+    return per < 256 ? 256 : per;
+}
+static unsigned ew_blocks(int64_t n) { return (unsigned)((n + ew_rows(n) - 1) / ew_rows(n)); }
+
 // x = S(x0; b): `sweeps` smoother applications starting from x0 (NULL = 0).
 // x0 and x must differ; uses L.r (residual), L.t (copy) and L.d (Chebyshev
 // direction) as scratch.
@@ -549,8 +586,8 @@ static void smooth_stored(Ctx &c, const Hierarchy &h, const Level &L, const XT *
         }
         if (h.smoother == MDS_SMOOTHER_L1JACOBI) {
             if (!cur)
-                MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n * NR, (k_vc_x0<XT, NR>), ew_grid(n * NR), 256, 0, n, dinv,
-                           b, dst);
+                MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n * NR, (k_vc_x0<XT, NR>), ew_blocks(n), 256, 0, n, dinv,
+                           b, dst, ew_rows(n), level_live(c, L));
             else
                 level_op<XT, VK_SMOOTH, NR>(c, L, b, cur, nullptr, nullptr, dst, 0);
         } else {
@@ -944,13 +981,13 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
     Level &L = h.lv[l];
     int last = (int)h.lv.size() - 1;
     if (l == last && h.dense) {
-        dense_apply(c, h.db, h.Ainv.as<double>(), NR, b, x);
+        dense_apply(c, h.db, h.Ainv.as<double>(), NR, b, x, h.K > 1 ? c.live : nullptr);
         return;
     }
     if (l == last && h.diagonal) {  // no couplings: exact x = b / a_ii
         const int64_t nd = L.A.nrow;
-        MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * nd * NR, (k_vc_x0<XT, NR>), ew_grid(nd * NR), 256, 0, nd,
-                   L.dinv.as<XT>(), b, x);
+        MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * nd * NR, (k_vc_x0<XT, NR>), ew_blocks(nd), 256, 0, nd,
+                   L.dinv.as<XT>(), b, x, ew_rows(nd), level_live(c, L));
         return;
     }
     if (h.use_tail && l == tail_start<XT>(h, (int64_t)tail_cluster<XT, NR>(c) * TAIL_THREADS) &&
@@ -971,7 +1008,7 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
             level_op<XT, VK_RESID0, NR>(c, L, b, nullptr, nullptr, nullptr, r, 0);
             MDS_LAUNCH(c, L.timed_level ? KC_VC_RESTRICT : KC_NONE, rbytes, (k_vc_restrict<XT, NR>),
                        grid_for(L.nc, 256), 256, 0, L.nc, L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r,
-                       C.b.as<XT>());
+                       C.b.as<XT>(), level_live(c, C));
             vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
             level_op<XT, VK_POST, NR>(c, L, b, nullptr, L.agg.as<int32_t>(), C.x.as<XT>(), x, L.nc);
         } else {
@@ -997,10 +1034,10 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
             level_op<XT, VK_RESID, NR>(c, L, b, y, nullptr, nullptr, r, 0);
             MDS_LAUNCH(c, L.timed_level ? KC_VC_RESTRICT : KC_NONE, rbytes, (k_vc_restrict<XT, NR>),
                        grid_for(L.nc, 256), 256, 0, L.nc, L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r,
-                       C.b.as<XT>());
+                       C.b.as<XT>(), level_live(c, C));
             vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
-            MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n * NR, (k_vc_prolong<XT, NR>), ew_grid(n * NR), 256, 0, n,
-                       L.agg.as<int32_t>(), C.x.as<XT>(), y);
+            MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n * NR, (k_vc_prolong<XT, NR>), ew_blocks(n), 256, 0, n,
+                       L.agg.as<int32_t>(), C.x.as<XT>(), y, ew_rows(n), level_live(c, L));
         }
     }
     smooth_stored<XT, NR>(c, h, L, b, y, x);  // x = S(y; b)
