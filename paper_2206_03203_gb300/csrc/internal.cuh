@@ -123,6 +123,7 @@ struct LiveMap {
     int64_t n1 = 0;
     const int8_t *live = nullptr;
     int K = 0;
+    double frac = 1.0;  // host side: share of the rows that are live (scales a launch's algorithmic work)
 };
 
 __device__ __forceinline__ int seg_find(const int64_t *seg, int K, int64_t r) {
@@ -226,8 +227,10 @@ struct Ctx {
     cudaStream_t side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // instance flags of the batched solve in progress (NULL otherwise): the
-    // kernels of a packed batch skip the rows of finished instances
+    // kernels of a packed batch skip the rows of finished instances; their
+    // host copy gives the launches' algorithmic work
     const int8_t *live = nullptr;
+    std::vector<int8_t> live_host;
     // device address of the static workspace of mds_solve_noalloc on this
     // context's device, resolved by mds_create
     double *noalloc_scratch = nullptr;
@@ -445,9 +448,20 @@ struct Level {
     Buf sell_ptr, sell_len, sell_col, sell_val, sell_perm;
     Buf b, x, r, y, d, t;  // work vectors in the vector precision
     Buf seg_d;             // int64 [K + 1] instance row offsets (packed batches)
+    std::vector<int64_t> seg_h;  // the same on the host
     int K = 1;             // instances (packed batches)
     int sell_sigma = 1;    // SELL sorting window (rows)
 };
+
+// Share of the rows [seg[k], seg[k+1]) of live instances (host flags).
+inline double live_share(const std::vector<int8_t> &live, const std::vector<int64_t> &seg) {
+    const int K = (int)seg.size() - 1;
+    if (K < 1 || (int)live.size() < K || seg[K] <= 0) return 1.0;
+    int64_t r = 0;
+    for (int k = 0; k < K; k++)
+        if (live[k]) r += seg[k + 1] - seg[k];
+    return (double)r / (double)seg[K];
+}
 
 // The liveness map of one level (every row live outside a batched solve).
 inline LiveMap level_live(const Ctx &c, const Level &L) {
@@ -457,6 +471,7 @@ inline LiveMap level_live(const Ctx &c, const Level &L) {
         m.n1 = L.A.nrow;
         m.live = c.live;
         m.K = L.K;
+        m.frac = live_share(c.live_host, L.seg_h);
     }
     return m;
 }

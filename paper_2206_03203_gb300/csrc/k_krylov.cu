@@ -1251,7 +1251,10 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
     struct LiveScope {
         Ctx &c;
         LiveScope(Ctx &cc, const int8_t *l) : c(cc) { c.live = l; }
-        ~LiveScope() { c.live = nullptr; }
+        ~LiveScope() {
+            c.live = nullptr;
+            c.live_host.clear();
+        }
     } live_scope(c, K > 1 ? ilive : nullptr);
     double *cs = pa.as<double>(), *sn = cs + (size_t)P * 32, *g = sn + (size_t)P * 32, *y = g + (size_t)P * 32,
            *h1 = y + (size_t)P * 32, *h2 = h1 + (size_t)P * 32, *nsq = h2 + (size_t)P * 32;
@@ -1279,6 +1282,13 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
         }
         std::memcpy(c.h_pin, hbuf.data(), (size_t)(P + K));
         MDS_CUDA(cudaMemcpyAsync(act.p, c.h_pin, (size_t)(P + K), cudaMemcpyHostToDevice, c.stream));
+        if (K > 1) {
+            c.live_host.assign(hbuf.begin() + P, hbuf.end());
+            int64_t r = 0;
+            for (int k = 0; k < K; k++)
+                if (hbuf[P + k]) r += (moff[k + 1] - moff[k]) + (foff[k + 1] - foff[k]);
+            sysmap.frac = N > 0 ? (double)r / (double)N : 1.0;
+        }
     };
     std::vector<double> host(P * 8), bn(P);
     auto fetch = [&](const double *d, int stride, int slot) {
@@ -1353,7 +1363,8 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
             M(vj, zj, NR);
             spmv_f64(c, A, zj, w, KC_SPMV, NR, sysmap);
             int nq = j + 1;
-            double fl = 2.0 * (double)N * NR * nq;
+            const double sf = sysmap.frac;  // share of the rows of live instances
+            double fl = 2.0 * (double)N * NR * nq * sf;
             // classical Gram-Schmidt for every problem; the second pass runs
             // for the problems whose first pass cancelled severely (the
             // others' chunks return at once)
@@ -1362,11 +1373,11 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
                 // first pass: the active problems' instances; second: the flagged problems'
                 const int8_t *mk = pass == 0 ? act.as<int8_t>() : f2.as<int8_t>();
                 int kd = pass == 0 ? KC_GS_DOT : KC_NONE, ka = pass == 0 ? KC_GS_AXPY : KC_NONE;
-                MDS_LAUNCH_F(c, kd, 8.0 * N * NR * (nq + 1), fl, (k_bdot<NR>), dim3(nch, nq), RED_BLOCK, 0, CHp, nch, Vp,
-                             ldq, nq, w, PT, mk);
+                MDS_LAUNCH_F(c, kd, 8.0 * N * NR * (nq + 1) * sf, fl, (k_bdot<NR>), dim3(nch, nq), RED_BLOCK, 0, CHp,
+                             nch, Vp, ldq, nq, w, PT, mk);
                 MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, nq), 32, 0, PT, nch, nq, NR, IO, IL, P, hh, 0, mk);
-                MDS_LAUNCH_F(c, ka, 8.0 * N * NR * (nq + 2), fl, (k_bmaxpy<NR, -1>), nch, RED_BLOCK, 0, CHp, Vp, ldq,
-                             nq, hh, w, PT, mk, (const int32_t *)nullptr);
+                MDS_LAUNCH_F(c, ka, 8.0 * N * NR * (nq + 2) * sf, fl, (k_bmaxpy<NR, -1>), nch, RED_BLOCK, 0, CHp, Vp,
+                             ldq, nq, hh, w, PT, mk, (const int32_t *)nullptr);
                 MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, 1), 32, 0, PT, nch, 1, NR, IO, IL, P, nsq, 0, mk);
                 if (pass == 0)
                     MDS_LAUNCH(c, KC_NONE, 0, k_bflag, grid_for(P, 128), 128, 0, P, nq, act.as<int8_t>(), h1, nsq,

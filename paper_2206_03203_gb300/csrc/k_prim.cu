@@ -166,8 +166,8 @@ static void spmv_launch(Ctx &c, const mds_csr &A, const XT *x, const double *r, 
     double bytes = 12.0 * (double)A.nnz + 4.0 * (double)(A.nrow + 1) +
                    NR * (sizeof(XT) * (double)A.ncol + sizeof(OT) * (double)A.nrow + (MODE == 1 ? 8.0 * A.nrow : 0.0));
     unsigned grid = grid_for(A.nrow * G, block);
-    MDS_LAUNCH_F(c, kclass, bytes, 2.0 * NR * A.nnz, (k_spmv_csr<G, double, XT, OT, MODE, NR>), grid, block, 0, A.nrow,
-                 A.row_ptr, A.col, A.val, x, r, y, lm);
+    MDS_LAUNCH_F(c, kclass, bytes * lm.frac, 2.0 * NR * A.nnz * lm.frac, (k_spmv_csr<G, double, XT, OT, MODE, NR>),
+                 grid, block, 0, A.nrow, A.row_ptr, A.col, A.val, x, r, y, lm);
 }
 
 template <int G, class XT, class OT, int MODE>

@@ -771,6 +771,7 @@ void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h,
         Buf lid;
         if (h.K > 1) {
             L.K = h.K;
+            L.seg_h = sg;
             L.seg_d = Buf(&c, sizeof(int64_t) * (size_t)(h.K + 1));
             MDS_CUDA(cudaMemcpyAsync(L.seg_d.p, sg.data(), sizeof(int64_t) * (size_t)(h.K + 1),
                                      cudaMemcpyHostToDevice, c.stream));
@@ -908,6 +909,7 @@ void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h,
         for (size_t l = 0; l < h.lv.size(); l++) {
             Level &L = h.lv[l];
             L.K = h.K;
+            L.seg_h = h.seg[l];
             if (L.seg_d.p) continue;
             L.seg_d = Buf(&c, sizeof(int64_t) * (size_t)(h.K + 1));
             MDS_CUDA(cudaMemcpyAsync(L.seg_d.p, h.seg[l].data(), sizeof(int64_t) * (size_t)(h.K + 1),

@@ -467,6 +467,8 @@ static void launch_level_pf(Ctx &c, const Level &L, const XT *dinv, const XT *b,
                    (K == VK_SMOOTH ? xb * (double)n : 0.0);
     double flops = NR * (2.0 * L.A.nnz + (K == VK_RESID0 ? n : K == VK_POST ? 5.0 * n : K == VK_SMOOTH ? 3.0 * n : 0.0));
     int cls = !L.timed_level ? KC_NONE : (K == VK_RESID0 || K == VK_RESID) ? KC_VC_RESID : KC_VC_POST;
+    bytes *= m.lm.frac;  // rows of finished batch instances are skipped
+    flops *= m.lm.frac;
     if (L.fmt == FMT_SELL) {
         int64_t rows = L.sell_nslice * L.sell_c;
         MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<0, VT, XT, K, NR, PF>), grid_for(rows, 256), 256, 0, m, dinv, b, xin,
@@ -1006,9 +1008,9 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
         if (L.has_coarse) {
             Level &C = h.lv[l + 1];
             level_op<XT, VK_RESID0, NR>(c, L, b, nullptr, nullptr, nullptr, r, 0);
-            MDS_LAUNCH(c, L.timed_level ? KC_VC_RESTRICT : KC_NONE, rbytes, (k_vc_restrict<XT, NR>),
-                       grid_for(L.nc, 256), 256, 0, L.nc, L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r,
-                       C.b.as<XT>(), level_live(c, C));
+            MDS_LAUNCH(c, L.timed_level ? KC_VC_RESTRICT : KC_NONE, rbytes * level_live(c, L).frac,
+                       (k_vc_restrict<XT, NR>), grid_for(L.nc, 256), 256, 0, L.nc, L.mem_off.as<int32_t>(),
+                       L.mem.as<int32_t>(), r, C.b.as<XT>(), level_live(c, C));
             vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
             level_op<XT, VK_POST, NR>(c, L, b, nullptr, L.agg.as<int32_t>(), C.x.as<XT>(), x, L.nc);
         } else {
@@ -1032,9 +1034,9 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
                        n, L.P.rowp(), L.P.cols(), pv, C.x.as<XT>(), y);
         } else {
             level_op<XT, VK_RESID, NR>(c, L, b, y, nullptr, nullptr, r, 0);
-            MDS_LAUNCH(c, L.timed_level ? KC_VC_RESTRICT : KC_NONE, rbytes, (k_vc_restrict<XT, NR>),
-                       grid_for(L.nc, 256), 256, 0, L.nc, L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r,
-                       C.b.as<XT>(), level_live(c, C));
+            MDS_LAUNCH(c, L.timed_level ? KC_VC_RESTRICT : KC_NONE, rbytes * level_live(c, L).frac,
+                       (k_vc_restrict<XT, NR>), grid_for(L.nc, 256), 256, 0, L.nc, L.mem_off.as<int32_t>(),
+                       L.mem.as<int32_t>(), r, C.b.as<XT>(), level_live(c, C));
             vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
             MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n * NR, (k_vc_prolong<XT, NR>), ew_blocks(n), 256, 0, n,
                        L.agg.as<int32_t>(), C.x.as<XT>(), y, ew_rows(n), level_live(c, L));
