@@ -968,9 +968,13 @@ __global__ void __launch_bounds__(RED_BLOCK) k_bdot(const Chunk *__restrict__ ch
                                                      double *__restrict__ partial, const int8_t *__restrict__ mask) {
     mds_pdl_entry();
     __shared__ double ws[RED_BLOCK / 32][NR];
-    Chunk k = ch[blockIdx.x];
+    // the nq blocks of one chunk are adjacent in launch order, so they run
+    // together and the chunk of W is read from DRAM once
+    const int nqb = nq > 0 ? nq : 1;
+    const int64_t chunk = blockIdx.x / nqb;
+    const int q = (int)(blockIdx.x % nqb);
+    Chunk k = ch[chunk];
     if (chunk_skipped<NR>(mask, k.inst)) return;
-    int q = blockIdx.y;
     const double *v = q < nq ? V + (int64_t)q * ldq : W;
     double s[NR];
 #pragma unroll
@@ -989,7 +993,7 @@ __global__ void __launch_bounds__(RED_BLOCK) k_bdot(const Chunk *__restrict__ ch
     if (threadIdx.x < NR) {
         double t = 0.0;
         for (int k2 = 0; k2 < RED_BLOCK / 32; k2++) t += ws[k2][threadIdx.x];
-        partial[((int64_t)q * nchunk + blockIdx.x) * NR + threadIdx.x] = t;
+        partial[((int64_t)q * nchunk + chunk) * NR + threadIdx.x] = t;
     }
 }
 
@@ -1268,7 +1272,7 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
     dim3 pgrid((unsigned)P, 1);
     // per-problem squared norms of a vector into nsq[p * 32]
     auto norms = [&](const double *w, const int8_t *mk) {
-        MDS_LAUNCH(c, KC_NONE, 8.0 * N * NR, (k_bdot<NR>), dim3(nch, 1), RED_BLOCK, 0, CHp, nch, Vp, ldq, 0, w, PT, mk);
+        MDS_LAUNCH(c, KC_NONE, 8.0 * N * NR, (k_bdot<NR>), (unsigned)nch, RED_BLOCK, 0, CHp, nch, Vp, ldq, 0, w, PT, mk);
         MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, 1), 32, 0, PT, nch, 1, NR, IO, IL, P, nsq, 0, mk);
     };
     // upload the problem flags hact and the instance flags derived from them
@@ -1373,7 +1377,7 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
                 // first pass: the active problems' instances; second: the flagged problems'
                 const int8_t *mk = pass == 0 ? act.as<int8_t>() : f2.as<int8_t>();
                 int kd = pass == 0 ? KC_GS_DOT : KC_NONE, ka = pass == 0 ? KC_GS_AXPY : KC_NONE;
-                MDS_LAUNCH_F(c, kd, 8.0 * N * NR * (nq + 1) * sf, fl, (k_bdot<NR>), dim3(nch, nq), RED_BLOCK, 0, CHp,
+                MDS_LAUNCH_F(c, kd, 8.0 * N * NR * (nq + 1) * sf, fl, (k_bdot<NR>), (unsigned)((int64_t)nch * nq), RED_BLOCK, 0, CHp,
                              nch, Vp, ldq, nq, w, PT, mk);
                 MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, nq), 32, 0, PT, nch, nq, NR, IO, IL, P, hh, 0, mk);
                 MDS_LAUNCH_F(c, ka, 8.0 * N * NR * (nq + 2) * sf, fl, (k_bmaxpy<NR, -1>), nch, RED_BLOCK, 0, CHp, Vp,

@@ -88,23 +88,21 @@ __global__ void k_csr_lowp(int64_t n, const int32_t *__restrict__ rp, const doub
     for (int32_t p = rp[i]; p < rp[i + 1]; p++) o[p] = from_d<VT>(v[p], sc);
 }
 
-// SELL: window sort of rows by decreasing length (stable), one thread per window
+// SELL: window sort of rows by decreasing length (stable), one block per
+// window of sigma <= 1024 rows: row i of the window goes to position
+// #{j : len_j > len_i} + #{j < i : len_j == len_i}.
 __global__ void k_sell_perm(int64_t n, const int32_t *__restrict__ rp, int sigma, int32_t *__restrict__ perm) {
     mds_pdl_entry();
-    int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t a = w * sigma;
-    if (a >= n) return;
-    int64_t e = a + sigma < n ? a + sigma : n;
-    for (int64_t i = a; i < e; i++) perm[i] = (int32_t)i;
-    for (int64_t i = a + 1; i < e; i++) {
-        int32_t x = perm[i];
-        int32_t lx = rp[x + 1] - rp[x];
-        int64_t q = i - 1;
-        while (q >= a && (rp[perm[q] + 1] - rp[perm[q]]) < lx) {
-            perm[q + 1] = perm[q];
-            q--;
-        }
-        perm[q + 1] = x;
+    __shared__ int32_t len[1024];
+    const int64_t a = (int64_t)blockIdx.x * sigma;
+    const int m = (int)(a + sigma < n ? sigma : n - a);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) len[i] = rp[a + i + 1] - rp[a + i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const int32_t li = len[i];
+        int pos = 0;
+        for (int j = 0; j < m; j++) pos += len[j] > li || (len[j] == li && j < i);
+        perm[a + pos] = (int32_t)(a + i);
     }
 }
 
@@ -159,8 +157,10 @@ template <class VT> static void build_sell(Ctx &c, Level &L, int C, int sigma) {
     L.sell_perm.reset();
     if (sigma > 1) {
         L.sell_perm = Buf(&c, sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+        MDS_REQUIRE(sigma <= 1024, MDS_ERR_INVALID, "sell_sigma must be at most 1024");
         int64_t nw = (n + sigma - 1) / sigma;
-        MDS_LAUNCH(c, KC_NONE, 0, k_sell_perm, grid_for(nw, 64), 64, 0, n, L.A.rowp(), sigma, L.sell_perm.as<int32_t>());
+        MDS_LAUNCH(c, KC_NONE, 0, k_sell_perm, (unsigned)nw, sigma < 256 ? sigma : 256, 0, n, L.A.rowp(), sigma,
+                   L.sell_perm.as<int32_t>());
     }
     L.sell_len = Buf(&c, sizeof(int32_t) * (size_t)(ns + 1));
     L.sell_ptr = Buf(&c, sizeof(int32_t) * (size_t)(ns + 1));
