@@ -218,6 +218,10 @@ int mds_system_view(mds_system sys, mds_csr blocks[5], const double **b);
 #define MDS_FORMAT_AUTO 0       /* timed choice per level (autotuner) */
 #define MDS_FORMAT_CSR 1
 #define MDS_FORMAT_SELL 2       /* sliced ELLPACK, slice height sell_c, sort window sell_sigma */
+#define MDS_FORMAT_STENCIL 3    /* the finest level of S~ of a primal system assembled by this library
+                                   (a 5- or 7-point stencil per Cartesian instance) stored by
+                                   diagonals, no column indices; CSR on the other levels.
+                                   MDS_FORMAT_AUTO uses it there too when it times fastest */
 #define MDS_BLOCK_LOWER 0       /* M_L, Eq. (8), Algorithm 1 */
 #define MDS_BLOCK_DIAG 1        /* block diagonal B_D with Q blocks */
 #define MDS_BLOCK_UPPER 2       /* block upper triangular B_U with Q blocks */
@@ -286,11 +290,13 @@ int mds_precond_prolongator(mds_precond prec, int block, int level, mds_csr *P);
  * type (MDS_PREC_FP64 / FP32 / BF16 / FP16), the values in the CSR order of
  * mds_precond_level's matrix (for BF16 / FP16: q_ij with a_ij ~ s_i q_ij;
  * NULL on a last level applied through its dense inverse), the float row
- * scales s_i (NULL unless BF16 / FP16) and 1/D1 (double for FP64
- * hierarchies, float otherwise).  MDS_ERR_INVALID for a block or level that
- * does not exist. */
+ * scales s_i (NULL unless BF16 / FP16), 1/D1 (double for FP64
+ * hierarchies, float otherwise) and the storage format the V-cycle reads
+ * (MDS_FORMAT_CSR, MDS_FORMAT_SELL or MDS_FORMAT_STENCIL).  Any output
+ * pointer may be NULL.  MDS_ERR_INVALID for a block or level that does not
+ * exist. */
 int mds_precond_level_storage(mds_precond prec, int block, int level, int *value_type,
-                              const void **values, const float **row_scale, const void **dinv);
+                              const void **values, const float **row_scale, const void **dinv, int *format);
 /* z = M r for device FP64 vectors of length n_m + n_f. */
 int mds_precond_apply(mds_ctx ctx, mds_precond prec, const double *r, double *z);
 /* x = V(b): one V-cycle of block 0 or 1 on device FP64 vectors. */

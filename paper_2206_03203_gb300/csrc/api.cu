@@ -456,7 +456,7 @@ int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_preco
                 MDS_ERR_INVALID, "unknown precision");
     MDS_REQUIRE(o.smoother == MDS_SMOOTHER_L1JACOBI || o.smoother == MDS_SMOOTHER_CHEBYSHEV, MDS_ERR_INVALID,
                 "unknown smoother");
-    MDS_REQUIRE(o.format >= MDS_FORMAT_AUTO && o.format <= MDS_FORMAT_SELL, MDS_ERR_INVALID, "unknown format");
+    MDS_REQUIRE(o.format >= MDS_FORMAT_AUTO && o.format <= MDS_FORMAT_STENCIL, MDS_ERR_INVALID, "unknown format");
     MDS_REQUIRE(o.sell_c == 8 || o.sell_c == 16 || o.sell_c == 32, MDS_ERR_INVALID, "sell_c must be 8, 16 or 32");
     MDS_REQUIRE(o.sell_sigma == 1 || (o.sell_sigma % o.sell_c == 0 && o.sell_sigma <= 1024), MDS_ERR_INVALID,
                 "sell_sigma must be 1 or a multiple of sell_c up to 1024");
@@ -484,6 +484,12 @@ int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_preco
         // a packed batch: every instance's blocks coarsened as if alone
         const bool packed = sys->n_inst > 1 && sys->own.moff.size() == (size_t)sys->n_inst + 1 &&
                             sys->own.foff.size() == (size_t)sys->n_inst + 1;
+        // the S~ of a primal system assembled here is a Cartesian stencil on
+        // its finest level (Eq. (7) restores the links cut by fractures)
+        if (sys->own.stencil && !sys->own.side.empty()) {
+            p->h[0].st_dim = sys->own.dim;
+            p->h[0].st_side = sys->own.side;
+        }
         amg_setup(*c, p->S.view(), o, p->h[0], packed ? &sys->own.moff : nullptr);
         p->has_f = sys->n_f > 0;
         if (p->has_f) {
@@ -554,7 +560,7 @@ int mds_precond_prolongator(mds_precond p, int block, int level, mds_csr *P) {
 }
 
 int mds_precond_level_storage(mds_precond p, int block, int level, int *value_type, const void **values,
-                              const float **row_scale, const void **dinv) {
+                              const float **row_scale, const void **dinv, int *format) {
     if (!p || block < 0 || block > 1 || (block == 1 && !p->has_f)) return MDS_ERR_INVALID;
     const Hierarchy &h = p->h[block];
     if (level < 0 || level >= (int)h.lv.size()) return MDS_ERR_INVALID;
@@ -565,6 +571,7 @@ int mds_precond_level_storage(mds_precond p, int block, int level, int *value_ty
     if (values) *values = dense_last ? nullptr : L.vt == VT_F64 ? (const void *)L.A.vals() : L.vals_lp.p;
     if (row_scale) *row_scale = L.rscale.p ? L.rscale.as<float>() : nullptr;
     if (dinv) *dinv = L.dinv.p;
+    if (format) *format = L.fmt == FMT_DIA ? MDS_FORMAT_STENCIL : L.fmt == FMT_SELL ? MDS_FORMAT_SELL : MDS_FORMAT_CSR;
     return MDS_OK;
 }
 

@@ -82,7 +82,7 @@ enum : int {
 
 // Storage of a V-cycle level: value type and sparse format.
 enum : int { VT_F64 = 0, VT_F32 = 1, VT_BF16 = 2, VT_F16 = 3 };
-enum : int { FMT_CSR = 0, FMT_SELL = 1 };
+enum : int { FMT_CSR = 0, FMT_SELL = 1, FMT_DIA = 2 };
 
 struct TuneChoice {
     int fmt, G, C, sigma;
@@ -404,6 +404,12 @@ struct SystemData {
     // packed instances: instance k owns matrix rows [moff[k], moff[k+1]) and
     // fracture rows n_m + [foff[k], foff[k+1])
     std::vector<int64_t> moff, foff;
+    // Cartesian instances of the primal form: grid dimension and cells per
+    // side of each instance (the matrix block, and S~, is then a 5- or
+    // 7-point stencil per instance); stencil = false otherwise
+    bool stencil = false;
+    int dim = 0;
+    std::vector<int32_t> side;
     DCsr full;
     DCsr blk[4];
     Buf b;  // [nrhs][N]
@@ -449,6 +455,12 @@ struct Level {
     Buf b, x, r, y, d, t;  // work vectors in the vector precision
     Buf seg_d;             // int64 [K + 1] instance row offsets (packed batches)
     std::vector<int64_t> seg_h;  // the same on the host
+    // stencil storage (FMT_DIA): plane d holds each row's coefficient of the
+    // neighbour at offset o_d (ascending), zero where the row has none
+    int dia_D = 0;         // 5 (2D) or 7 (3D); 0: the level is no stencil
+    Buf dia_val;           // [dia_D][n] in the storage type
+    Buf dia_seg;           // int64 [K + 1] instance row offsets
+    Buf dia_side;          // int32 [K] cells per side
     int K = 1;             // instances (packed batches)
     int sell_sigma = 1;    // SELL sorting window (rows)
 };
@@ -506,6 +518,10 @@ struct Hierarchy {
     int cheb_degree = 2;
     int nr_cap = 0;   // columns the level work vectors hold
     bool use_tail = true;  // run the coarse end of the V-cycle as one cluster kernel
+    // level 0 is a Cartesian stencil (the S~ of primal assembled systems):
+    // grid dimension and cells per side of each instance (empty: unknown)
+    int st_dim = 0;
+    std::vector<int32_t> st_side;
 };
 
 // seg0: the instances' row offsets [K + 1] of a packed batch (NULL: one

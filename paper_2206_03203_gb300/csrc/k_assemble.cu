@@ -579,6 +579,13 @@ void pack_instances(Ctx &c, std::vector<SystemData> &parts, SystemData &out) {
     }
     const int64_t NM = out.moff[K], NF = out.foff[K], N = NM + NF;
     MDS_REQUIRE(N < INT32_MAX, MDS_ERR_INVALID, "packed batch exceeds int32 indices");
+    out.stencil = true;
+    out.dim = parts[0].dim;
+    out.side.clear();
+    for (int k = 0; k < K; k++) {
+        out.stencil = out.stencil && parts[k].stencil && parts[k].dim == out.dim && parts[k].side.size() == 1;
+        out.side.push_back(parts[k].side.empty() ? 0 : parts[k].side[0]);
+    }
     out.n_m = NM;
     out.n_f = NF;
     for (int q = 0; q < 4; q++) {
@@ -730,6 +737,9 @@ void assemble_instance(Ctx &c, const mds_instance &in, SystemData &out, bool flu
     out.nrhs = in.nrhs;
     out.moff = {0, nm};
     out.foff = {0, nfb};
+    out.stencil = !flux;
+    out.dim = in.dim;
+    out.side = {in.n};
     split_blocks(c, A.view(), nm, out.blk);
     c.sync();  // staged host copies are released on return
 }

@@ -196,6 +196,78 @@ static void drop_sell(Level &L) {
     L.fmt = FMT_CSR;
 }
 
+// Stencil planes of a level: row i's entry at column i + o_d goes to plane d
+// (offsets ascending per instance, see DiaMat); a column that is no stencil
+// neighbour sets *bad (the level then keeps CSR / SELL storage).
+template <class VT>
+__global__ void k_dia_build(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const double *__restrict__ v, int D, const int64_t *__restrict__ seg,
+                            const int32_t *__restrict__ side, int K, VT *__restrict__ planes, int *bad) {
+    mds_pdl_entry();
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int k = K > 1 ? seg_find(seg, K, i) : 0;
+    const int64_t sd = side[k];
+    int64_t off[7];
+    if (D == 7) {
+        off[0] = -sd * sd; off[1] = -sd; off[2] = -1; off[3] = 0; off[4] = 1; off[5] = sd; off[6] = sd * sd;
+    } else {
+        off[0] = -sd; off[1] = -1; off[2] = 0; off[3] = 1; off[4] = sd;
+    }
+    for (int32_t p = rp[i]; p < rp[i + 1]; p++) {
+        const int64_t o = (int64_t)ci[p] - i;
+        int d = -1;
+        for (int q = 0; q < D; q++)
+            if (off[q] == o) d = q;
+        if (d < 0 || ci[p] < seg[k] || ci[p] >= seg[k + 1]) {
+            atomicOr(bad, 1);
+            return;
+        }
+        planes[(int64_t)d * n + i] = from_d<VT>(v[p], 1.0);
+    }
+}
+
+// Stencil storage of level L (the finest level of a hierarchy whose matrix
+// is a Cartesian stencil per instance); false when a row does not fit.
+static bool build_dia(Ctx &c, Level &L, const Hierarchy &h) {
+    const int64_t n = L.A.nrow;
+    const int D = h.st_dim == 3 ? 7 : 5;
+    const int K = (int)h.st_side.size();
+    if ((h.st_dim != 2 && h.st_dim != 3) || K < 1 || (int)h.seg[0].size() != K + 1 || n < 1) return false;
+    size_t vsz = L.vt == VT_F64 ? sizeof(double) : sizeof(float);
+    L.dia_val = Buf(&c, vsz * (size_t)D * (size_t)n);
+    MDS_CUDA(cudaMemsetAsync(L.dia_val.p, 0, vsz * (size_t)D * (size_t)n, c.stream));
+    L.dia_seg = Buf(&c, sizeof(int64_t) * (size_t)(K + 1));
+    L.dia_side = Buf(&c, sizeof(int32_t) * (size_t)K);
+    MDS_CUDA(cudaMemcpyAsync(L.dia_seg.p, h.seg[0].data(), sizeof(int64_t) * (size_t)(K + 1), cudaMemcpyHostToDevice,
+                             c.stream));
+    MDS_CUDA(cudaMemcpyAsync(L.dia_side.p, h.st_side.data(), sizeof(int32_t) * (size_t)K, cudaMemcpyHostToDevice,
+                             c.stream));
+    Buf bad(&c, sizeof(int));
+    MDS_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), c.stream));
+    if (L.vt == VT_F64)
+        MDS_LAUNCH(c, KC_NONE, 0, k_dia_build<double>, grid_for(n, 256), 256, 0, n, L.A.rowp(), L.A.cols(), L.A.vals(),
+                   D, L.dia_seg.as<int64_t>(), L.dia_side.as<int32_t>(), K, L.dia_val.as<double>(), bad.as<int>());
+    else
+        MDS_LAUNCH(c, KC_NONE, 0, k_dia_build<float>, grid_for(n, 256), 256, 0, n, L.A.rowp(), L.A.cols(), L.A.vals(),
+                   D, L.dia_seg.as<int64_t>(), L.dia_side.as<int32_t>(), K, L.dia_val.as<float>(), bad.as<int>());
+    if (c.read(bad.as<int>()) != 0) {
+        L.dia_val.reset();
+        L.dia_seg.reset();
+        L.dia_side.reset();
+        return false;
+    }
+    L.dia_D = D;
+    return true;
+}
+
+static void drop_dia(Level &L) {
+    L.dia_val.reset();
+    L.dia_seg.reset();
+    L.dia_side.reset();
+    L.dia_D = 0;
+}
+
 static int default_g(const Level &L) {
     double avg = L.A.nrow ? (double)L.A.nnz / (double)L.A.nrow : 0.0;
     return avg <= 8.0 ? 1 : avg <= 16.0 ? 2 : avg <= 32.0 ? 4 : avg <= 64.0 ? 8 : avg <= 128.0 ? 16 : 32;
@@ -208,14 +280,17 @@ template <class XT> static void autotune_level(Ctx &c, Level &L) {
     auto time_level = [](Ctx &cc, const Level &LL) {
         return std::is_same<XT, double>::value ? time_level_f64(cc, LL) : time_level_f32(cc, LL);
     };
-    auto key = std::make_tuple(L.A.nrow, L.A.nnz, L.vt);
+    auto key = std::make_tuple(L.A.nrow, L.A.nnz, L.vt * 2 + (L.dia_D > 0 ? 1 : 0));
     auto it = c.tune_cache.find(key);
     if (it != c.tune_cache.end()) {
         const TuneChoice &t = it->second;
         if (t.fmt == FMT_SELL)
             build_sell_vt(c, L, t.C, t.sigma);
+        else if (t.fmt == FMT_DIA && L.dia_D > 0)
+            L.fmt = FMT_DIA;
         else
             L.G = t.G;
+        if (L.fmt != FMT_DIA) drop_dia(L);
         return;
     }
     // defined inputs for the timing runs
@@ -248,9 +323,22 @@ template <class XT> static void autotune_level(Ctx &c, Level &L) {
         }
         drop_sell(L);
     }
+    if (L.dia_D > 0) {
+        L.fmt = FMT_DIA;
+        float t = time_level(c, L);
+        if (t < tbest) {
+            tbest = t;
+            best = TuneChoice{FMT_DIA, 0, 32, 1};
+        }
+        L.fmt = FMT_CSR;
+    }
     c.tune_cache[key] = best;
     L.G = best.fmt == FMT_CSR ? best.G : default_g(L);
     if (best.fmt == FMT_SELL) build_sell_vt(c, L, best.C, best.sigma);
+    if (best.fmt == FMT_DIA)
+        L.fmt = FMT_DIA;
+    else
+        drop_dia(L);
 }
 
 void level_storage(Ctx &c, Hierarchy &h, const mds_setup_opts &o) {
@@ -290,7 +378,12 @@ void level_storage(Ctx &c, Hierarchy &h, const mds_setup_opts &o) {
             MDS_LAUNCH(c, KC_NONE, 0, k_csr_lowp<__half>, gr, 256, 0, n, L.A.rowp(), L.A.vals(), s,
                        L.vals_lp.as<__half>());
         }
-        if (o.format == MDS_FORMAT_SELL) {
+        const bool stencil_ok = l == 0 && h.st_dim > 0 && (L.vt == VT_F32 || L.vt == VT_F64) &&
+                                (o.format == MDS_FORMAT_STENCIL || o.format == MDS_FORMAT_AUTO);
+        if (stencil_ok) build_dia(c, L, h);
+        if (o.format == MDS_FORMAT_STENCIL) {
+            if (L.dia_D > 0) L.fmt = FMT_DIA;
+        } else if (o.format == MDS_FORMAT_SELL) {
             build_sell_vt(c, L, o.sell_c, o.sell_sigma);
         } else if (o.format == MDS_FORMAT_AUTO && n >= 20000) {
             if (h.prec == 64)
@@ -298,6 +391,7 @@ void level_storage(Ctx &c, Hierarchy &h, const mds_setup_opts &o) {
             else
                 autotune_level<float>(c, L);
         }
+        if (L.fmt != FMT_DIA) drop_dia(L);
     }
 }
 

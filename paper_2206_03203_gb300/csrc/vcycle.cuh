@@ -288,6 +288,128 @@ __global__ void __launch_bounds__(256) k_level(LvlMat<VT> A, const XT *__restric
     }
 }
 
+// ---- stencil storage (FMT_DIA): the finest level of S~ of a primal system on
+// Cartesian instances.  Plane d holds every row's coefficient of its
+// neighbour at offset o_d, ascending (3D: -s^2, -s, -1, 0, 1, s, s^2 with s
+// the instance's cells per side; 2D: -s, -1, 0, 1, s), zero where the row has
+// no such neighbour.  No column indices are stored or loaded, the planes and
+// the neighbours' vector entries are read contiguously along each warp, and
+// the row's products are added in ascending column order with the absent
+// ones contributing exact zeros, so the result is the CSR one-thread-per-row
+// result bit for bit.
+template <class VT> struct DiaMat {
+    int64_t n;
+    int D;
+    const VT *v;            // [D][n]
+    const int64_t *seg;     // instance row offsets [K + 1]
+    const int32_t *side;    // cells per side [K]
+    int K;
+    LiveMap lm;
+};
+
+template <class VT, class XT, int K, int NR>
+__global__ void __launch_bounds__(256) k_level_dia(DiaMat<VT> A, const XT *__restrict__ dinv, const XT *__restrict__ b,
+                                                   const XT *__restrict__ xin, const int32_t *__restrict__ agg,
+                                                   const XT *__restrict__ xc, XT *__restrict__ out) {
+    const int64_t r0 = (int64_t)blockIdx.x * 256, r1 = r0 + 256 < A.n ? r0 + 256 : A.n;
+    if (!block_rows_live(A.lm, r0, r1)) return;
+    // the instance of the block's rows: one search per block, per row only
+    // in a block that straddles two instances
+    __shared__ int kb, straddle;
+    if (threadIdx.x == 0) {
+        const int k = A.K > 1 ? seg_find(A.seg, A.K, r0) : 0;
+        kb = k;
+        straddle = A.K > 1 && A.seg[k + 1] < r1;
+    }
+    __syncthreads();
+    const int64_t row = r0 + threadIdx.x;
+    const bool live = row < A.n;
+    int k = kb;
+    if (straddle && live) k = seg_find(A.seg, A.K, row);
+    const int64_t sd = live ? A.side[k] : 0;
+    int64_t off[7];
+    if (A.D == 7) {
+        off[0] = -sd * sd; off[1] = -sd; off[2] = -1; off[3] = 0; off[4] = 1; off[5] = sd; off[6] = sd * sd;
+    } else {
+        off[0] = -sd; off[1] = -1; off[2] = 0; off[3] = 1; off[4] = sd; off[5] = 0; off[6] = 0;
+    }
+    // constants of this launch (values, 1/D1, aggregates) before the wait
+    constexpr bool FUSED = K == VK_RESID0 || K == VK_POST;
+    VT pa[7];
+    int64_t pj[7];
+    XT pd[FUSED ? 7 : 1];
+    int32_t pg[K == VK_POST ? 7 : 1];
+#pragma unroll
+    for (int d = 0; d < 7; d++) {
+        pa[d] = (VT)0;
+        pj[d] = row;
+        if (d < A.D && live) {
+            pa[d] = ld_stream(A.v + (int64_t)d * A.n + row);
+            if (cvt<XT>(pa[d]) != (XT)0) pj[d] = row + off[d];  // absent neighbours read the row itself
+        }
+    }
+    if constexpr (FUSED) {
+#pragma unroll
+        for (int d = 0; d < 7; d++)
+            if (d < A.D && live) {
+                pd[d] = __ldg(dinv + pj[d]);
+                if constexpr (K == VK_POST) pg[d] = agg ? __ldg(agg + pj[d]) : -1;
+            }
+    }
+    XT dd = (XT)0;
+    int32_t ag = -1;
+    if (live) {
+        if (K == VK_POST || K == VK_SMOOTH) dd = dinv[row];
+        if (K == VK_POST && agg) ag = agg[row];
+    }
+    mds_pdl_wait();
+    mds_pdl_trigger();
+    if (!live) return;
+    Nb<XT, NR, K> f{dinv, b, xin, xc, agg};
+    Vec<XT, NR> bo = ldv<XT, NR>(b, row), yo;
+#pragma unroll
+    for (int c = 0; c < NR; c++) yo.v[c] = (XT)0;
+    if (K == VK_SMOOTH) yo = ldv<XT, NR>(xin, row);
+    if (K == VK_POST && ag >= 0) yo = ldv<XT, NR>(xc, ag);
+    XT s[NR];
+#pragma unroll
+    for (int c = 0; c < NR; c++) s[c] = 0;
+#pragma unroll
+    for (int d = 0; d < 7; d++)
+        if (d < A.D) {
+            XT a = cvt<XT>(pa[d]);
+            Vec<XT, NR> y;
+            if constexpr (K == VK_POST)
+                y = f.with((int32_t)pj[d], pd[d], pg[d]);
+            else if constexpr (K == VK_RESID0)
+                y = f.with((int32_t)pj[d], pd[d], -1);
+            else
+                y = f((int32_t)pj[d]);
+#pragma unroll
+            for (int c = 0; c < NR; c++) s[c] += a * y.v[c];
+        }
+    Vec<XT, NR> res;
+    if (K == VK_RESID0 || K == VK_RESID) {
+#pragma unroll
+        for (int c = 0; c < NR; c++) res.v[c] = bo.v[c] - s[c];
+    } else {
+        Vec<XT, NR> y;
+        if (K == VK_POST) {
+#pragma unroll
+            for (int c = 0; c < NR; c++) y.v[c] = dd * bo.v[c];
+            if (ag >= 0) {
+#pragma unroll
+                for (int c = 0; c < NR; c++) y.v[c] += yo.v[c];
+            }
+        } else {
+            y = yo;
+        }
+#pragma unroll
+        for (int c = 0; c < NR; c++) res.v[c] = y.v[c] + dd * (bo.v[c] - s[c]);
+    }
+    stv<XT, NR>(out, row, res);
+}
+
 // ---- elementwise kernels (NR interleaved columns; row of entry e = e / NR).
 // 1/D1 and the aggregate map are fixed while solving: a thread's first entry
 // of them is loaded before the dependency wait.
@@ -467,6 +589,14 @@ static void launch_level_pf(Ctx &c, const Level &L, const XT *dinv, const XT *b,
                    (K == VK_SMOOTH ? xb * (double)n : 0.0);
     double flops = NR * (2.0 * L.A.nnz + (K == VK_RESID0 ? n : K == VK_POST ? 5.0 * n : K == VK_SMOOTH ? 3.0 * n : 0.0));
     int cls = !L.timed_level ? KC_NONE : (K == VK_RESID0 || K == VK_RESID) ? KC_VC_RESID : KC_VC_POST;
+    if (L.fmt == FMT_DIA) {
+        DiaMat<VT> dm{n, L.dia_D, L.dia_val.as<VT>(), L.dia_seg.as<int64_t>(), L.dia_side.as<int32_t>(), L.K, m.lm};
+        // algorithmic bytes: the planes instead of values, columns and row pointers
+        bytes = bytes - vb - 4.0 * (n + 1) + (double)L.dia_D * sizeof(VT) * n;
+        MDS_LAUNCH_F(c, cls, bytes * m.lm.frac, flops * m.lm.frac, (k_level_dia<VT, XT, K, NR>), grid_for(n, 256), 256,
+                     0, dm, dinv, b, xin, agg, xc, out);
+        return;
+    }
     bytes *= m.lm.frac;  // rows of finished batch instances are skipped
     flops *= m.lm.frac;
     if (L.fmt == FMT_SELL) {

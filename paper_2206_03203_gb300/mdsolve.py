@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(PKG, "_build", "libmdsolve.so")
 MDS_OK = 0
 MDS_WARN_NOT_CONVERGED = 1
 PREC = {"fp64": 64, "fp32": 32, "bf16": 16, "fp16": 17}
-FORMAT = {"auto": 0, "csr": 1, "sell": 2}
+FORMAT = {"auto": 0, "csr": 1, "sell": 2, "stencil": 3}
 PROLONG = {"piecewise": 0, "smoothed": 1}
 SMOOTHER = {"l1jacobi": 0, "chebyshev": 1}
 KIND = {"lower": 0, "diag": 1, "upper": 2}
@@ -130,7 +130,7 @@ _SIGS = {
     "mds_precond_prolongator": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(Csr)]),
     "mds_precond_level_storage": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int),
                                             C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
-                                            C.POINTER(C.c_void_p)]),
+                                            C.POINTER(C.c_void_p), C.POINTER(C.c_int)]),
     "mds_precond_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mds_vcycle": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "mds_spmv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -582,10 +582,11 @@ class Precond:
     def level_storage_host(self, block: int, level: int):
         """(value type, stored values in CSR order as float64 or None, row
         scales or None, 1/D1) of a level, as its V-cycle applies them."""
-        vt = C.c_int()
+        vt, fmt = C.c_int(), C.c_int()
         vals, rs, dv = C.c_void_p(), C.c_void_p(), C.c_void_p()
         self.ctx._check(lib().mds_precond_level_storage(self.h, block, level, C.byref(vt), C.byref(vals),
-                                                        C.byref(rs), C.byref(dv)))
+                                                        C.byref(rs), C.byref(dv), C.byref(fmt)))
+
         A, _, _ = self.level_host(block, level)
         n, nnz = A.shape[0], A.nnz
         v = None
@@ -602,6 +603,12 @@ class Precond:
         r = self.ctx.to_host(rs.value, n, np.float32).astype(np.float64) if rs.value else None
         d = self.ctx.to_host(dv.value, n, np.float64 if vt.value == 64 else np.float32).astype(np.float64)
         return vt.value, v, r, d
+
+    def level_format(self, block: int, level: int) -> str:
+        """Storage format the V-cycle reads on a level: csr, sell or stencil."""
+        fmt = C.c_int()
+        self.ctx._check(lib().mds_precond_level_storage(self.h, block, level, None, None, None, None, C.byref(fmt)))
+        return {1: "csr", 2: "sell", 3: "stencil"}.get(fmt.value, str(fmt.value))
 
     def level_host(self, block: int, level: int):
         A = Csr()

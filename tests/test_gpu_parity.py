@@ -848,3 +848,37 @@ def test_fp64_path_agrees_with_oracle_to_1e10(ctx, oracle_mod, torch_mod, case):
     assert np.linalg.norm(Ao @ (xg - res.x)) / nb <= 1e-10
     xd = spla.spsolve(Ao.tocsc(), bo[0])
     assert np.linalg.norm(xg - xd) <= 1e-9 * np.linalg.norm(xd)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("case", ["fixed2d-37", "planes3d-13-kf1", "rects3d-18", "packed"])
+def test_stencil_storage_is_csr_bit_for_bit(ctx, torch_mod, case, precision):
+    """The finest S~ level stored by diagonals (no column indices) gives the
+    one-thread-per-row CSR results bit for bit: V-cycles, M_L and whole
+    solves (same iteration counts, identical solutions), single instances in
+    2D and 3D and a packed batch of instances of different sizes."""
+    torch = torch_mod
+    if case == "packed":
+        insts = [inputs.random_rects_3d(n, 22060304, k, 1 + k % 3, nrhs=2, random_dirichlet=True)
+                 for k, n in enumerate([9, 12, 7, 10])]
+        sys_ = ctx.assemble_batch(insts)
+    else:
+        sys_ = ctx.assemble(CASES[case]())
+    nr = sys_.nrhs
+    ps = ctx.setup(sys_, precision=precision, format="stencil")
+    pc = ctx.setup(sys_, precision=precision, format="csr")
+    assert ps.level_format(0, 0) == "stencil" and pc.level_format(0, 0) == "csr"
+    rng = np.random.default_rng(5)
+    r = dev(torch, rng.standard_normal(sys_.N))
+    zs = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+    zc = torch.zeros_like(zs)
+    ctx.precond_apply(ps, r, zs)
+    ctx.precond_apply(pc, r, zc)
+    assert torch.equal(zs, zc)
+    xs = torch.zeros(sys_.N * nr, dtype=torch.float64, device="cuda")
+    xc = torch.zeros_like(xs)
+    c1, s1 = ctx.solve(sys_, ps, None, xs, nrhs=nr, max_iters=3000)
+    c2, s2 = ctx.solve(sys_, pc, None, xc, nrhs=nr, max_iters=3000)
+    assert c1 == c2 == 0
+    assert [q.iterations for q in s1] == [q.iterations for q in s2]
+    assert torch.equal(xs, xc)
