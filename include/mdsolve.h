@@ -369,6 +369,8 @@ typedef struct {
     int iterations;     /* out */
     double setup_ms;    /* out: wall time of mds_setup */
     double solve_ms;    /* out: wall time of mds_solve */
+    int64_t n_coarse;   /* in: coarsest-level size N_c (dense Cholesky once every instance has at
+                           most N_c rows; 1..8192), 0 = the base options' value */
 } mds_tune_candidate;
 int mds_tune(mds_ctx ctx, mds_system sys, const mds_setup_opts *base, const mds_solve_opts *sopts,
              const double *b, mds_tune_candidate *cands, int n_cands, int *best);

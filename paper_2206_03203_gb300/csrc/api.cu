@@ -297,6 +297,8 @@ static int assemble_any(mds_ctx ctx, const mds_instance *inst, int n_inst, mds_s
         s->ctx = c;
         if (n_inst == 1) {
             assemble_instance(*c, inst[0], s->own, flux);
+        } else if (!flux) {
+            assemble_batch_primal(*c, inst, n_inst, s->own);
         } else {
             std::vector<SystemData> parts(n_inst);
             for (int k = 0; k < n_inst; k++) assemble_instance(*c, inst[k], parts[k], flux);
@@ -912,6 +914,7 @@ int mds_tune(mds_ctx ctx, mds_system sys, const mds_setup_opts *base, const mds_
         o.sweeps = k.sweeps;
         o.cheb_degree = k.cheb_degree;
         o.precision = k.precision;
+        if (k.n_coarse > 0) o.n_coarse = k.n_coarse;
         k.iterations = 0;
         k.setup_ms = k.solve_ms = 0.0;
         mds_precond p = nullptr;

@@ -113,16 +113,14 @@ struct KTimerRec {
 // Rows of a packed batch whose instance is still iterating.  The batched
 // solve's kernels skip every thread block whose rows all belong to finished
 // instances: the system is block diagonal, so no live row reads those rows.
-// Row spaces are one part (the rows of one block of the system or one level
-// of a hierarchy: instance k owns rows [seg[k], seg[k+1])) or two parts (the
-// whole system: matrix rows by seg, then fracture rows n1 + [seg2[k],
-// seg2[k+1])).  seg == NULL: every row is live.
+// A row space (the rows of one block of the system, one level of a
+// hierarchy, or the whole system: matrix rows, then fracture rows) is cut
+// into chunks of 256 rows; ck[2 c] and ck[2 c + 1] are the least and the
+// greatest instance owning a row of chunk c.  ck == NULL: every row is live.
+constexpr int LIVE_CHUNK_LOG2 = 8;
 struct LiveMap {
-    const int64_t *seg = nullptr;
-    const int64_t *seg2 = nullptr;
-    int64_t n1 = 0;
+    const int32_t *ck = nullptr;
     const int8_t *live = nullptr;
-    int K = 0;
     double frac = 1.0;  // host side: share of the rows that are live (scales a launch's algorithmic work)
 };
 
@@ -138,31 +136,21 @@ __device__ __forceinline__ int seg_find(const int64_t *seg, int K, int64_t r) {
     return lo;
 }
 
-__device__ __forceinline__ bool seg_range_live(const int64_t *seg, const int8_t *live, int K, int64_t a, int64_t b) {
-    const int k1 = seg_find(seg, K, b);
-    for (int k = seg_find(seg, K, a); k <= k1; k++)
-        if (live[k]) return true;
-    return false;
-}
-
-// Whether rows [r0, r1) hold a row of a live instance; called by every
-// thread of the block (one thread searches, the block shares the answer).
-// The flags are written by host copies between solver steps, never by a
-// kernel, so this may run before the programmatic dependency wait.
+// Whether rows [r0, r1) hold a row of a live instance.  Every thread of a
+// block gets the same answer from the same (broadcast) loads, so no barrier
+// is needed.  The flags are written by host copies between solver steps,
+// never by a kernel, so this may run before the programmatic dependency wait.
 __device__ __forceinline__ bool block_rows_live(const LiveMap &m, int64_t r0, int64_t r1) {
-    if (!m.seg) return true;
-    __shared__ int any_live;
-    if (threadIdx.x == 0) {
-        bool a = false;
-        if (r0 < r1) {
-            if (r0 < m.n1 || !m.seg2) a = seg_range_live(m.seg, m.live, m.K, r0, (m.seg2 && r1 > m.n1 ? m.n1 : r1) - 1);
-            if (!a && m.seg2 && r1 > m.n1)
-                a = seg_range_live(m.seg2, m.live, m.K, (r0 > m.n1 ? r0 : m.n1) - m.n1, r1 - 1 - m.n1);
-        }
-        any_live = a;
+    if (!m.ck || r0 >= r1) return true;
+    const int64_t c0 = r0 >> LIVE_CHUNK_LOG2, c1 = (r1 - 1) >> LIVE_CHUNK_LOG2;
+    int lo = __ldg(m.ck + 2 * c0), hi = __ldg(m.ck + 2 * c0 + 1);
+    for (int64_t c = c0 + 1; c <= c1; c++) {
+        lo = min(lo, __ldg(m.ck + 2 * c));
+        hi = max(hi, __ldg(m.ck + 2 * c + 1));
     }
-    __syncthreads();
-    return any_live != 0;
+    for (int k = lo; k <= hi; k++)
+        if (m.live[k]) return true;
+    return false;
 }
 
 // One launch recorded while a CUDA graph is being captured: its accounting is
@@ -419,6 +407,8 @@ struct SystemData {
 void assemble_instance(Ctx &c, const mds_instance &inst, SystemData &out, bool flux = false);
 // pack several assembled instances into one block-diagonal system
 void pack_instances(Ctx &c, std::vector<SystemData> &parts, SystemData &out);
+// assemble K instances of the primal form straight into the packed system
+void assemble_batch_primal(Ctx &c, const mds_instance *inst, int K, SystemData &out);
 void split_blocks(Ctx &c, const mds_csr &full, int64_t n_m, DCsr blk[4]);
 void merge_blocks(Ctx &c, const mds_csr blk[4], int64_t n_m, int64_t n_f, DCsr &full);
 
@@ -455,6 +445,7 @@ struct Level {
     Buf b, x, r, y, d, t;  // work vectors in the vector precision
     Buf seg_d;             // int64 [K + 1] instance row offsets (packed batches)
     std::vector<int64_t> seg_h;  // the same on the host
+    Buf ck;                // int32 [2 chunks] least / greatest instance of each 256-row chunk
     // stencil storage (FMT_DIA): plane d holds each row's coefficient of the
     // neighbour at offset o_d (ascending), zero where the row has none
     int dia_D = 0;         // 5 (2D) or 7 (3D); 0: the level is no stencil
@@ -478,15 +469,18 @@ inline double live_share(const std::vector<int8_t> &live, const std::vector<int6
 // The liveness map of one level (every row live outside a batched solve).
 inline LiveMap level_live(const Ctx &c, const Level &L) {
     LiveMap m;
-    if (c.live && L.K > 1 && L.seg_d.p) {
-        m.seg = L.seg_d.as<int64_t>();
-        m.n1 = L.A.nrow;
+    if (c.live && L.K > 1 && L.ck.p) {
+        m.ck = L.ck.as<int32_t>();
         m.live = c.live;
-        m.K = L.K;
         m.frac = live_share(c.live_host, L.seg_h);
     }
     return m;
 }
+
+// The chunk table of a row space of `rows` rows whose instance k owns the
+// rows [a[k], a[k+1]) and, when b is given, also [n1 + b[k], n1 + b[k+1]).
+Buf live_chunks(Ctx &c, int64_t rows, const std::vector<int64_t> &a, const std::vector<int64_t> *b = nullptr,
+                int64_t n1 = 0);
 
 // One diagonal block of the coarsest level: its first row, the start of its
 // n x n row-major matrices, its size.

@@ -46,11 +46,10 @@ __device__ __forceinline__ int64_t cell_id(const GridD &g, const int64_t c[3]) {
     return c[0] + (int64_t)g.n * (c[1] + (int64_t)g.n * c[2]);
 }
 
-__global__ void k_map_scatter(GridD g, const int32_t *__restrict__ axis, const int32_t *__restrict__ pos,
-                              int32_t *__restrict__ map, int *err) {
-    mds_pdl_entry();
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= g.nf) return;
+// Fracture cell k claims its face in the face map (error bits on a bad or
+// doubly claimed face).
+__device__ __forceinline__ void scatter_face(const GridD &g, const int32_t *axis, const int32_t *pos, int32_t *map,
+                                             int *err, int64_t k) {
     int d = axis[k];
     int64_t x = pos[3 * k], y = pos[3 * k + 1], z = g.dim == 3 ? pos[3 * k + 2] : 0;
     int64_t c[3] = {x, y, z};
@@ -64,6 +63,14 @@ __global__ void k_map_scatter(GridD g, const int32_t *__restrict__ axis, const i
         return;
     }
     if (atomicCAS(map + f, -1, (int32_t)k) != -1) atomicOr(err, DERR_DUP_FACE);
+}
+
+__global__ void k_map_scatter(GridD g, const int32_t *__restrict__ axis, const int32_t *__restrict__ pos,
+                              int32_t *__restrict__ map, int *err) {
+    mds_pdl_entry();
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.nf) return;
+    scatter_face(g, axis, pos, map, err, k);
 }
 
 struct Ent {
@@ -308,6 +315,85 @@ __global__ void k_junc_phi(int64_t nI, const int32_t *__restrict__ ioff, int32_t
     for (int32_t p = ioff[I]; p < ioff[I + 1]; p++) phi_int[p] = (int32_t)I;
 }
 
+// Position of a local unknown of an instance in the output system: the
+// identity for a single instance; in a packed batch, matrix rows at mo + i and
+// fracture rows at fbase + (i - n_m).  Monotone, so sorted rows stay sorted.
+struct Remap {
+    int64_t n_m, mo, fbase;
+    __device__ __forceinline__ int64_t operator()(int64_t j) const { return j < n_m ? mo + j : fbase + (j - n_m); }
+};
+
+// Row i of the primal system (a matrix or a fracture cell): its entries in
+// ascending column order, the diagonal, and its right-hand sides, written at
+// the remapped row and columns (entries from rp[row], b[r NT + row]).
+__device__ void fill_primal_row(const GridD &g, const int32_t *map, const double *km, const int32_t *axis,
+                                const int32_t *pos, const double *kf, const double *ap, int nrhs, const double *pL,
+                                const double *pR, int64_t i, const Remap &rm, int64_t NT, const int32_t *rp,
+                                int32_t *ci, double *val, double *b) {
+    Ent row[16];
+    double tb[2];
+    int has[2];
+    int64_t bfa[2] = {0, 0}, bfb[2] = {0, 0};
+    bool is_m = i < g.n_m;
+    int cnt = is_m ? matrix_entries(g, map, km, kf, ap, i, row, tb, has)
+                   : fracture_entries(g, map, km, axis, pos, kf, ap, i - g.n_m, row, tb, has, bfa, bfb);
+    sort_ents(row, cnt);
+    // diagonal: the transmissibilities of the row (flux columns carry none)
+    double diag = 0.0;
+    for (int q = 0; q < cnt; q++)
+        if (row[q].c < g.NO) diag += row[q].t;
+    for (int s = 0; s < 2; s++)
+        if (has[s]) diag += tb[s];
+    const int64_t oi = rm(i);
+    int64_t p = rp[oi];
+    bool placed = false;
+    for (int q = 0; q < cnt; q++) {
+        if (!placed && row[q].c > i) {
+            ci[p] = (int32_t)oi;
+            val[p++] = diag;
+            placed = true;
+        }
+        ci[p] = (int32_t)rm(row[q].c);
+        val[p++] = row[q].c < g.NO ? -row[q].t : row[q].t;
+    }
+    if (!placed) {
+        ci[p] = (int32_t)oi;
+        val[p] = diag;
+    }
+    for (int r = 0; r < nrhs; r++) {
+        const double *L = pL + (int64_t)r * g.nb, *R = pR + (int64_t)r * g.nb;
+        double acc = 0.0;
+        if (is_m) {
+            int64_t n = g.n;
+            int64_t bf = (i / n) % n + (g.dim == 3 ? n * (i / (n * n)) : 0);
+            if (has[0]) acc += tb[0] * L[bf];
+            if (has[1]) acc += tb[1] * R[bf];
+        } else {
+            for (int s = 0; s < 2; s++) {
+                if (!has[s]) continue;
+                const double *P = s == 0 ? L : R;
+                double pv = (P[bfa[s]] + P[bfb[s]]) * 0.5;
+                acc += tb[s] * pv;
+            }
+        }
+        b[(int64_t)r * NT + oi] = acc;
+    }
+}
+
+
+// Entries (diagonal included) of row i of the primal system.
+__device__ __forceinline__ int count_primal_row(const GridD &g, const int32_t *map, const double *km,
+                                                const int32_t *axis, const int32_t *pos, const double *kf,
+                                                const double *ap, int64_t i) {
+    Ent row[16];
+    double tb[2];
+    int has[2];
+    int64_t bfa[2], bfb[2];
+    int m = i < g.n_m ? matrix_entries(g, map, km, kf, ap, i, row, tb, has)
+                      : fracture_entries(g, map, km, axis, pos, kf, ap, i - g.n_m, row, tb, has, bfa, bfb);
+    return m + 1;
+}
+
 __global__ void k_count(GridD g, const int32_t *__restrict__ map, const double *__restrict__ km,
                         const int32_t *__restrict__ axis, const int32_t *__restrict__ pos,
                         const double *__restrict__ kf, const double *__restrict__ ap, int32_t *__restrict__ cnt) {
@@ -323,13 +409,7 @@ __global__ void k_count(GridD g, const int32_t *__restrict__ map, const double *
         cnt[i] = 1 + (g.ioff[I + 1] - g.ioff[I]);
         return;
     }
-    Ent row[16];
-    double tb[2];
-    int has[2];
-    int64_t bfa[2], bfb[2];
-    int m = i < g.n_m ? matrix_entries(g, map, km, kf, ap, i, row, tb, has)
-                      : fracture_entries(g, map, km, axis, pos, kf, ap, i - g.n_m, row, tb, has, bfa, bfb);
-    cnt[i] = m + 1;
+    cnt[i] = count_primal_row(g, map, km, axis, pos, kf, ap, i);
 }
 
 __global__ void k_fill(GridD g, const int32_t *__restrict__ map, const double *__restrict__ km,
@@ -387,53 +467,7 @@ __global__ void k_fill(GridD g, const int32_t *__restrict__ map, const double *_
         for (int r = 0; r < nrhs; r++) b[(int64_t)r * g.NT + i] = 0.0;
         return;
     }
-    Ent row[16];
-    double tb[2];
-    int has[2];
-    int64_t bfa[2] = {0, 0}, bfb[2] = {0, 0};
-    bool is_m = i < g.n_m;
-    int cnt = is_m ? matrix_entries(g, map, km, kf, ap, i, row, tb, has)
-                   : fracture_entries(g, map, km, axis, pos, kf, ap, i - g.n_m, row, tb, has, bfa, bfb);
-    sort_ents(row, cnt);
-    // diagonal: the transmissibilities of the row (flux columns carry none)
-    double diag = 0.0;
-    for (int q = 0; q < cnt; q++)
-        if (row[q].c < g.NO) diag += row[q].t;
-    for (int s = 0; s < 2; s++)
-        if (has[s]) diag += tb[s];
-    int64_t p = rp[i];
-    bool placed = false;
-    for (int q = 0; q < cnt; q++) {
-        if (!placed && row[q].c > i) {
-            ci[p] = (int32_t)i;
-            val[p++] = diag;
-            placed = true;
-        }
-        ci[p] = row[q].c;
-        val[p++] = row[q].c < g.NO ? -row[q].t : row[q].t;
-    }
-    if (!placed) {
-        ci[p] = (int32_t)i;
-        val[p] = diag;
-    }
-    for (int r = 0; r < nrhs; r++) {
-        const double *L = pL + (int64_t)r * g.nb, *R = pR + (int64_t)r * g.nb;
-        double acc = 0.0;
-        if (is_m) {
-            int64_t n = g.n;
-            int64_t bf = (i / n) % n + (g.dim == 3 ? n * (i / (n * n)) : 0);
-            if (has[0]) acc += tb[0] * L[bf];
-            if (has[1]) acc += tb[1] * R[bf];
-        } else {
-            for (int s = 0; s < 2; s++) {
-                if (!has[s]) continue;
-                const double *P = s == 0 ? L : R;
-                double pv = (P[bfa[s]] + P[bfb[s]]) * 0.5;
-                acc += tb[s] * pv;
-            }
-        }
-        b[(int64_t)r * g.NT + i] = acc;
-    }
+    fill_primal_row(g, map, km, axis, pos, kf, ap, nrhs, pL, pR, i, Remap{g.n_m, 0, g.n_m}, g.NT, rp, ci, val, b);
 }
 
 // ---------------------------------------------------------------- block split / merge
@@ -628,6 +662,49 @@ void pack_instances(Ctx &c, std::vector<SystemData> &parts, SystemData &out) {
     c.sync();
 }
 
+// ---------------------------------------------------------------- packed batches (primal form)
+//
+// Every instance of a batch is assembled straight into the packed system
+// [m_0 .. m_K-1; f_0 .. f_K-1]: one launch per phase for all instances
+// (blockIdx.y = instance), one prefix sum over the packed rows.  Each row is
+// computed by the same functions as for a single instance, its row and
+// columns remapped to their packed positions.
+
+struct BInst {
+    GridD g;
+    const double *km, *kf, *ap, *pL, *pR;
+    const int32_t *ax, *ps;
+    int32_t *map;          // the instance's face map
+    int64_t mo, fbase;     // packed rows of its first matrix cell and first fracture cell
+};
+
+__global__ void k_map_scatter_b(const BInst *__restrict__ bi, int *err) {
+    mds_pdl_entry();
+    const BInst &B = bi[blockIdx.y];
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= B.g.nf) return;
+    scatter_face(B.g, B.ax, B.ps, B.map, err, k);
+}
+
+__global__ void k_count_b(const BInst *__restrict__ bi, int32_t *__restrict__ cnt) {
+    mds_pdl_entry();
+    const BInst &B = bi[blockIdx.y];
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B.g.N) return;
+    const Remap rm{B.g.n_m, B.mo, B.fbase};
+    cnt[rm(i)] = count_primal_row(B.g, B.map, B.km, B.ax, B.ps, B.kf, B.ap, i);
+}
+
+__global__ void k_fill_b(const BInst *__restrict__ bi, int nrhs, int64_t NT, const int32_t *__restrict__ rp,
+                         int32_t *__restrict__ ci, double *__restrict__ val, double *__restrict__ b) {
+    mds_pdl_entry();
+    const BInst &B = bi[blockIdx.y];
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B.g.N) return;
+    fill_primal_row(B.g, B.map, B.km, B.ax, B.ps, B.kf, B.ap, nrhs, B.pL, B.pR, i, Remap{B.g.n_m, B.mo, B.fbase}, NT,
+                    rp, ci, val, b);
+}
+
 // ---------------------------------------------------------------- driver
 
 template <class T>
@@ -638,7 +715,9 @@ static const T *stage(Ctx &c, const T *p, size_t count, bool on_device, Buf &hol
     return hold.as<T>();
 }
 
-void assemble_instance(Ctx &c, const mds_instance &in, SystemData &out, bool flux) {
+// The grid description of an instance (faces counted in *faces); checks the
+// instance's sizes and arrays.
+static GridD grid_of(const mds_instance &in, bool flux, int64_t *faces) {
     MDS_REQUIRE(in.dim == 2 || in.dim == 3, MDS_ERR_INVALID, "dim must be 2 or 3");
     MDS_REQUIRE(in.n >= 1 && in.nrhs >= 1 && in.n_f >= 0, MDS_ERR_INVALID, "bad instance sizes");
     MDS_REQUIRE(in.km && in.pD_left && in.pD_right, MDS_ERR_INVALID, "missing instance arrays");
@@ -666,6 +745,93 @@ void assemble_instance(Ctx &c, const mds_instance &in, SystemData &out, bool flu
     g.junction = in.junction;
     g.nb = in.dim == 3 ? n * n : n;
     MDS_REQUIRE(g.N + 2 * g.nf < INT32_MAX, MDS_ERR_INVALID, "too many unknowns for int32 indices");
+    // the primal form has no intersection unknowns nor fluxes
+    g.NO = g.N;
+    g.GF = g.NO;
+    g.NT = g.N;
+    *faces = total;
+    return g;
+}
+
+void assemble_batch_primal(Ctx &c, const mds_instance *inst, int K, SystemData &out) {
+    MDS_REQUIRE(K >= 1 && K <= 65535, MDS_ERR_INVALID, "a batch holds 1 to 65535 instances");
+    std::vector<BInst> hb(K);
+    std::vector<int64_t> faces(K);
+    std::vector<Buf> hold;
+    hold.reserve((size_t)K * 8);
+    auto stg = [&](auto p, size_t count, bool dev) {
+        using T = std::remove_const_t<std::remove_pointer_t<decltype(p)>>;
+        hold.emplace_back();
+        return stage<T>(c, p, count, dev, hold.back());
+    };
+    out.nrhs = inst[0].nrhs;
+    out.moff.assign(K + 1, 0);
+    out.foff.assign(K + 1, 0);
+    out.stencil = true;
+    out.dim = inst[0].dim;
+    out.side.assign(K, 0);
+    int64_t total_faces = 0, maxN = 0, maxf = 0;
+    for (int k = 0; k < K; k++) {
+        const mds_instance &in = inst[k];
+        MDS_REQUIRE(in.nrhs == out.nrhs, MDS_ERR_INVALID, "instances of a batch need the same nrhs");
+        GridD g = grid_of(in, false, &faces[k]);
+        bool dev = in.on_device != 0;
+        BInst &B = hb[k];
+        B.km = stg(in.km, (size_t)g.n_m, dev);
+        B.ax = stg(in.fc_axis, (size_t)g.nf, dev);
+        B.ps = stg(in.fc_pos, (size_t)(3 * g.nf), dev);
+        B.kf = stg(in.fc_kf, (size_t)g.nf, dev);
+        B.ap = stg(in.fc_a, (size_t)g.nf, dev);
+        B.pL = stg(in.pD_left, (size_t)(in.nrhs * g.nb), dev);
+        B.pR = stg(in.pD_right, (size_t)(in.nrhs * g.nb), dev);
+        g.kn = in.fc_kn ? stg(in.fc_kn, (size_t)g.nf, dev) : B.kf;
+        B.g = g;
+        out.moff[k + 1] = out.moff[k] + g.n_m;
+        out.foff[k + 1] = out.foff[k] + g.nf;
+        out.stencil = out.stencil && in.dim == out.dim;
+        out.side[k] = in.n;
+        total_faces += faces[k];
+        maxN = std::max(maxN, g.N);
+        maxf = std::max(maxf, g.nf);
+    }
+    const int64_t NM = out.moff[K], NF = out.foff[K], N = NM + NF;
+    MDS_REQUIRE(N < INT32_MAX, MDS_ERR_INVALID, "packed batch exceeds int32 indices");
+    Buf map(&c, sizeof(int32_t) * (size_t)(total_faces > 0 ? total_faces : 1));
+    fill_i32(c, map.as<int32_t>(), -1, total_faces);
+    int64_t at = 0;
+    for (int k = 0; k < K; k++) {
+        hb[k].map = map.as<int32_t>() + at;
+        at += faces[k];
+        hb[k].mo = out.moff[k];
+        hb[k].fbase = NM + out.foff[k];
+    }
+    Buf bi(&c, sizeof(BInst) * (size_t)K);
+    MDS_CUDA(cudaMemcpyAsync(bi.p, hb.data(), sizeof(BInst) * (size_t)K, cudaMemcpyHostToDevice, c.stream));
+    const BInst *B = bi.as<BInst>();
+    c.clear_err();
+    if (maxf > 0)
+        MDS_LAUNCH(c, KC_NONE, 0, k_map_scatter_b, dim3(grid_for(maxf, 256), K), 256, 0, B, c.d_err);
+    c.check_err("fracture list");
+    Buf cnt(&c, sizeof(int32_t) * (size_t)(N + 1));
+    MDS_LAUNCH(c, KC_NONE, 0, k_count_b, dim3(grid_for(maxN, 128), K), 128, 0, B, cnt.as<int32_t>());
+    DCsr &A = out.full;
+    A.nrow = A.ncol = N;
+    A.rp = Buf(&c, sizeof(int32_t) * (size_t)(N + 1));
+    A.nnz = scan_counts(c, cnt.as<int32_t>(), A.rowp(), N);
+    A.ci = Buf(&c, sizeof(int32_t) * (size_t)A.nnz);
+    A.v = Buf(&c, sizeof(double) * (size_t)A.nnz);
+    out.b = Buf(&c, sizeof(double) * (size_t)(N * out.nrhs));
+    MDS_LAUNCH(c, KC_NONE, 0, k_fill_b, dim3(grid_for(maxN, 128), K), 128, 0, B, out.nrhs, N, A.rowp(), A.cols(),
+               A.vals(), out.b.as<double>());
+    out.n_m = NM;
+    out.n_f = NF;
+    split_blocks(c, A.view(), NM, out.blk);
+    c.sync();  // staged host copies are released on return
+}
+
+void assemble_instance(Ctx &c, const mds_instance &in, SystemData &out, bool flux) {
+    int64_t total = 0;
+    GridD g = grid_of(in, flux, &total);
 
     bool dev = in.on_device != 0;
     Buf h0, h1, h2, h3, h4, h5, h6;

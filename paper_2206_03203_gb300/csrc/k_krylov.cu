@@ -1239,16 +1239,12 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
     // one of its columns iterates; the kernels skip the rows of the others)
     Buf act(&c, (size_t)(P + K)), kd(&c, sizeof(int32_t) * (size_t)P), f2(&c, (size_t)P);
     const int8_t *ilive = act.as<int8_t>() + P;
-    Buf mo_d(&c, sizeof(int64_t) * (size_t)(K + 1)), fo_d(&c, sizeof(int64_t) * (size_t)(K + 1));
-    MDS_CUDA(cudaMemcpyAsync(mo_d.p, moff.data(), sizeof(int64_t) * (size_t)(K + 1), cudaMemcpyHostToDevice, c.stream));
-    MDS_CUDA(cudaMemcpyAsync(fo_d.p, foff.data(), sizeof(int64_t) * (size_t)(K + 1), cudaMemcpyHostToDevice, c.stream));
     LiveMap sysmap;
+    Buf sys_ck;
     if (K > 1) {
-        sysmap.seg = mo_d.as<int64_t>();
-        sysmap.seg2 = fo_d.as<int64_t>();
-        sysmap.n1 = NM;
+        sys_ck = live_chunks(c, N, moff, &foff, NM);
+        sysmap.ck = sys_ck.as<int32_t>();
         sysmap.live = ilive;
-        sysmap.K = K;
     }
     // the batched preconditioner's kernels read the instance flags from the
     // context while this solve runs

@@ -125,6 +125,33 @@ __global__ void k_scale(double *__restrict__ p, double a, int64_t n) {
         p[i] = a * p[i];
 }
 
+Buf live_chunks(Ctx &c, int64_t rows, const std::vector<int64_t> &a, const std::vector<int64_t> *b, int64_t n1) {
+    const int64_t nch = (rows + (1 << LIVE_CHUNK_LOG2) - 1) >> LIVE_CHUNK_LOG2;
+    std::vector<int32_t> ck((size_t)(2 * (nch > 0 ? nch : 1)));
+    for (int64_t q = 0; q < nch; q++) {
+        ck[2 * q] = INT32_MAX;
+        ck[2 * q + 1] = -1;
+    }
+    auto mark = [&](const std::vector<int64_t> &seg, int64_t base) {
+        for (size_t k = 0; k + 1 < seg.size(); k++) {
+            if (seg[k + 1] <= seg[k]) continue;
+            const int64_t q0 = (base + seg[k]) >> LIVE_CHUNK_LOG2, q1 = (base + seg[k + 1] - 1) >> LIVE_CHUNK_LOG2;
+            for (int64_t q = q0; q <= q1; q++) {
+                ck[2 * q] = std::min(ck[2 * q], (int32_t)k);
+                ck[2 * q + 1] = std::max(ck[2 * q + 1], (int32_t)k);
+            }
+        }
+    };
+    mark(a, 0);
+    if (b) mark(*b, n1);
+    for (int64_t q = 0; q < nch; q++)
+        if (ck[2 * q + 1] < 0) ck[2 * q] = 0, ck[2 * q + 1] = -1;  // no rows: never live
+    Buf d(&c, sizeof(int32_t) * ck.size());
+    MDS_CUDA(cudaMemcpyAsync(d.p, ck.data(), sizeof(int32_t) * ck.size(), cudaMemcpyHostToDevice, c.stream));
+    c.sync();  // the host table is released on return
+    return d;
+}
+
 void scale_f64(Ctx &c, double *p, double a, int64_t n) {
     if (n <= 0) return;
     MDS_LAUNCH(c, KC_NONE, 2.0 * sizeof(double) * n, k_scale, grid_for(n, 256) > 4096 ? 4096 : grid_for(n, 256),

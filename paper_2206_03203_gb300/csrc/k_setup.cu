@@ -910,6 +910,7 @@ void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h,
             Level &L = h.lv[l];
             L.K = h.K;
             L.seg_h = h.seg[l];
+            L.ck = live_chunks(c, L.A.nrow, h.seg[l]);
             if (L.seg_d.p) continue;
             L.seg_d = Buf(&c, sizeof(int64_t) * (size_t)(h.K + 1));
             MDS_CUDA(cudaMemcpyAsync(L.seg_d.p, h.seg[l].data(), sizeof(int64_t) * (size_t)(h.K + 1),

@@ -303,6 +303,7 @@ template <class VT> struct DiaMat {
     const VT *v;            // [D][n]
     const int64_t *seg;     // instance row offsets [K + 1]
     const int32_t *side;    // cells per side [K]
+    const int32_t *ck;      // least / greatest instance of each 256-row chunk (K > 1)
     int K;
     LiveMap lm;
 };
@@ -313,19 +314,16 @@ __global__ void __launch_bounds__(256) k_level_dia(DiaMat<VT> A, const XT *__res
                                                    const XT *__restrict__ xc, XT *__restrict__ out) {
     const int64_t r0 = (int64_t)blockIdx.x * 256, r1 = r0 + 256 < A.n ? r0 + 256 : A.n;
     if (!block_rows_live(A.lm, r0, r1)) return;
-    // the instance of the block's rows: one search per block, per row only
-    // in a block that straddles two instances
-    __shared__ int kb, straddle;
-    if (threadIdx.x == 0) {
-        const int k = A.K > 1 ? seg_find(A.seg, A.K, r0) : 0;
-        kb = k;
-        straddle = A.K > 1 && A.seg[k + 1] < r1;
-    }
-    __syncthreads();
     const int64_t row = r0 + threadIdx.x;
     const bool live = row < A.n;
-    int k = kb;
-    if (straddle && live) k = seg_find(A.seg, A.K, row);
+    // the row's instance: from its 256-row chunk, searched only in a chunk
+    // that holds rows of two instances
+    int k = 0;
+    if (A.K > 1 && live) {
+        const int64_t c = row >> LIVE_CHUNK_LOG2;
+        const int lo = __ldg(A.ck + 2 * c), hi = __ldg(A.ck + 2 * c + 1);
+        k = lo == hi ? lo : seg_find(A.seg, A.K, row);
+    }
     const int64_t sd = live ? A.side[k] : 0;
     int64_t off[7];
     if (A.D == 7) {
@@ -590,7 +588,8 @@ static void launch_level_pf(Ctx &c, const Level &L, const XT *dinv, const XT *b,
     double flops = NR * (2.0 * L.A.nnz + (K == VK_RESID0 ? n : K == VK_POST ? 5.0 * n : K == VK_SMOOTH ? 3.0 * n : 0.0));
     int cls = !L.timed_level ? KC_NONE : (K == VK_RESID0 || K == VK_RESID) ? KC_VC_RESID : KC_VC_POST;
     if (L.fmt == FMT_DIA) {
-        DiaMat<VT> dm{n, L.dia_D, L.dia_val.as<VT>(), L.dia_seg.as<int64_t>(), L.dia_side.as<int32_t>(), L.K, m.lm};
+        DiaMat<VT> dm{n, L.dia_D, L.dia_val.as<VT>(), L.dia_seg.as<int64_t>(), L.dia_side.as<int32_t>(),
+                      L.ck.p ? L.ck.as<int32_t>() : nullptr, L.ck.p ? L.K : 1, m.lm};
         // algorithmic bytes: the planes instead of values, columns and row pointers
         bytes = bytes - vb - 4.0 * (n + 1) + (double)L.dia_D * sizeof(VT) * n;
         MDS_LAUNCH_F(c, cls, bytes * m.lm.frac, flops * m.lm.frac, (k_level_dia<VT, XT, K, NR>), grid_for(n, 256), 256,

@@ -52,10 +52,11 @@ class Csr(C.Structure):
 
 class TuneCandidate(C.Structure):
     _fields_ = [("smoother", C.c_int), ("sweeps", C.c_int), ("cheb_degree", C.c_int), ("precision", C.c_int),
-                ("status", C.c_int), ("iterations", C.c_int), ("setup_ms", C.c_double), ("solve_ms", C.c_double)]
+                ("status", C.c_int), ("iterations", C.c_int), ("setup_ms", C.c_double), ("solve_ms", C.c_double),
+                ("n_coarse", C.c_int64)]
 
 
-# smoother, sweeps, Chebyshev degree, precision
+# smoother, sweeps, Chebyshev degree, precision[, coarsest size N_c (0: the base options')]
 TUNE_DEFAULT = [("l1jacobi", 1, 2, "fp64"), ("l1jacobi", 2, 2, "fp64"), ("chebyshev", 1, 2, "fp64"),
                 ("chebyshev", 1, 3, "fp64"), ("l1jacobi", 1, 2, "fp32"), ("l1jacobi", 2, 2, "fp32"),
                 ("chebyshev", 1, 2, "fp32"), ("chebyshev", 1, 3, "fp32")]
@@ -401,8 +402,10 @@ class Context:
         candidate])."""
         cands = candidates or TUNE_DEFAULT
         arr = (TuneCandidate * len(cands))()
-        for k, (sm, sw, dg, pr) in enumerate(cands):
-            arr[k] = TuneCandidate(SMOOTHER.get(sm, sm), sw, dg, PREC.get(pr, pr), 0, 0, 0.0, 0.0)
+        for k, cand in enumerate(cands):
+            sm, sw, dg, pr = cand[:4]
+            nc = cand[4] if len(cand) > 4 else 0
+            arr[k] = TuneCandidate(SMOOTHER.get(sm, sm), sw, dg, PREC.get(pr, pr), 0, 0, 0.0, 0.0, nc)
         so = setup_opts(**(base or {}))
         o = solve_opts(**solve_kw)
         best = C.c_int(-1)

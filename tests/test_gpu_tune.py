@@ -47,3 +47,22 @@ def test_tune_reports_no_convergence(env):
     sys_ = ctx.assemble(inputs.fixed_2d(n=32))
     best, res = ctx.tune(sys_, [("l1jacobi", 1, 2, "fp64")], max_iters=2)
     assert best == -1 and res[0]["status"] == 1 and res[0]["iterations"] == 2
+
+
+def test_tune_coarsest_size(env):
+    """The coarsest-level size N_c as a tuned option: each candidate's count is
+    that of a plain set-up with that N_c, and a larger N_c (an exact solve on
+    a bigger coarsest level) never needs more iterations here."""
+    torch, mdsolve, ctx = env
+    inst = inputs.random_rects_3d(24, 22060304, 3, 4, nrhs=1)
+    sys_ = ctx.assemble(inst)
+    cands = [("l1jacobi", 1, 2, "fp64", nc) for nc in (64, 256, 1024)]
+    best, res = ctx.tune(sys_, cands, base={"format": "csr"}, rtol=1e-8, max_iters=3000)
+    assert all(r["status"] == 0 for r in res) and best >= 0
+    for k, nc in enumerate((64, 256, 1024)):
+        p = ctx.setup(sys_, format="csr", n_coarse=nc)
+        x = torch.zeros(sys_.N, dtype=torch.float64, device="cuda")
+        code, st = ctx.solve(sys_, p, None, x, rtol=1e-8, max_iters=3000)
+        assert code == 0 and st[0].iterations == res[k]["iterations"]
+        p.close()
+    assert res[2]["iterations"] <= res[0]["iterations"]
