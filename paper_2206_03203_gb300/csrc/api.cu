@@ -135,8 +135,8 @@ void graph_launch(Ctx &c, Graph &g) {
     MDS_CUDA(cudaGraphLaunch(g.exec, c.stream));
     for (auto &r : g.recs) {
         c.launches[r.cls]++;
-        c.bytes[r.cls] += r.bytes;
-        c.flops[r.cls] += r.flops;
+        c.bytes[r.cls] += r.bytes * g.scale;
+        c.flops[r.cls] += r.flops * g.scale;
     }
     c.total_launches += g.launches;
 }
@@ -148,8 +148,8 @@ void graph_collect(Ctx &c, Graph &g) {
             if (cudaEventElapsedTime(&t, r.e0, r.e1) == cudaSuccess) {
                 c.graph_ms[r.cls] += t;
                 c.tlaunches[r.cls]++;
-                c.tbytes[r.cls] += r.bytes;
-                c.tflops[r.cls] += r.flops;
+                c.tbytes[r.cls] += r.bytes * g.scale;
+                c.tflops[r.cls] += r.flops * g.scale;
             }
         }
 }

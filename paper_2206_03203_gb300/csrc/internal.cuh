@@ -167,6 +167,10 @@ struct Graph {
     cudaGraphExec_t exec = nullptr;
     std::vector<GraphRec> recs;
     int64_t launches = 0;
+    // share of a packed batch's rows live when captured: a replay scales the
+    // recorded algorithmic work by (share at replay) / cap_share
+    double cap_share = 1.0;
+    double scale = 1.0;
     Graph() = default;
     Graph(const Graph &) = delete;
     Graph &operator=(const Graph &) = delete;

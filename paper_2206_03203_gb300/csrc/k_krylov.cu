@@ -1317,6 +1317,70 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
         if (out[p].status == MDS_ERR_NONFINITE) done[p] = 1;
     std::vector<int8_t> hact(P);
     std::vector<int32_t> hkd(P);
+    // One lockstep Arnoldi step j of every problem: z_j = M v_j, w = A z_j,
+    // the Gram-Schmidt passes (the second one masked to the flagged
+    // problems), the Arnoldi / Givens update and the scaled v_{j+1}, and the
+    // step's scalars copied to pinned host memory.  The kernels read the
+    // problem and instance flags from device memory, so the sequence of
+    // launches of step j does not change between restart cycles: it is
+    // captured as a CUDA graph on its second use (the first one grows the
+    // preconditioner's work vectors) and replayed.
+    auto step_body = [&](int j) {
+        double *vj = Vp + (size_t)j * ldq, *zj = Zp + (size_t)j * ldq, *w = Vp + (size_t)(j + 1) * ldq;
+        M(vj, zj, NR);
+        spmv_f64(c, A, zj, w, KC_SPMV, NR, sysmap);
+        int nq = j + 1;
+        const double sf = sysmap.frac;  // share of the rows of live instances
+        double fl = 2.0 * (double)N * NR * nq * sf;
+        // classical Gram-Schmidt for every problem; the second pass runs
+        // for the problems whose first pass cancelled severely (the
+        // others' chunks return at once)
+        for (int pass = 0; pass < 2; pass++) {
+            double *hh = pass == 0 ? h1 : h2;
+            // first pass: the active problems' instances; second: the flagged problems'
+            const int8_t *mk = pass == 0 ? act.as<int8_t>() : f2.as<int8_t>();
+            int kd = pass == 0 ? KC_GS_DOT : KC_NONE, ka = pass == 0 ? KC_GS_AXPY : KC_NONE;
+            MDS_LAUNCH_F(c, kd, 8.0 * N * NR * (nq + 1) * sf, fl, (k_bdot<NR>), (unsigned)((int64_t)nch * nq), RED_BLOCK, 0, CHp,
+                         nch, Vp, ldq, nq, w, PT, mk);
+            MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, nq), 32, 0, PT, nch, nq, NR, IO, IL, P, hh, 0, mk);
+            MDS_LAUNCH_F(c, ka, 8.0 * N * NR * (nq + 2) * sf, fl, (k_bmaxpy<NR, -1>), nch, RED_BLOCK, 0, CHp, Vp,
+                         ldq, nq, hh, w, PT, mk, (const int32_t *)nullptr);
+            MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, 1), 32, 0, PT, nch, 1, NR, IO, IL, P, nsq, 0, mk);
+            if (pass == 0)
+                MDS_LAUNCH(c, KC_NONE, 0, k_bflag, grid_for(P, 128), 128, 0, P, nq, act.as<int8_t>(), h1, nsq,
+                           o.reorth_eta2, f2.as<int8_t>(), h2);
+        }
+        MDS_LAUNCH(c, KC_NONE, 0, k_barnoldi, grid_for(P, 128), 128, 0, P, j, m, act.as<int8_t>(), H.as<double>(),
+                   h1, h2, nsq, cs, sn, g, sc);
+        MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, nch, RED_BLOCK, 0, CHp, w, sc, 3, act.as<int8_t>());
+        MDS_CUDA(cudaMemcpyAsync(c.h_pin, sc, sizeof(double) * (size_t)P * 8, cudaMemcpyDeviceToHost, c.stream));
+    };
+    std::vector<std::unique_ptr<Graph>> graphs(m);
+    bool graphs_ok = o.graphs != 0, warmed = false;
+    auto run_step = [&](int j) {
+        Graph *gj = nullptr;
+        if (graphs_ok && warmed) {
+            auto &slot = graphs[j];
+            if (!slot) {
+                slot.reset(new Graph);
+                slot->cap_share = sysmap.frac;
+                if (!graph_capture(c, *slot, [&] { step_body(j); })) {
+                    slot.reset();
+                    graphs_ok = false;
+                }
+            }
+            gj = slot.get();
+        }
+        if (gj) {
+            gj->scale = gj->cap_share > 0.0 ? sysmap.frac / gj->cap_share : 1.0;
+            graph_launch(c, *gj);
+        } else {
+            step_body(j);
+        }
+        warmed = true;
+        c.sync();
+        if (gj) graph_collect(c, *gj);
+    };
     bool first_cycle = true;
     for (;;) {
         // V0 = B - A X for the problems not yet done
@@ -1359,35 +1423,7 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
         MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, nch, RED_BLOCK, 0, CHp, Vp, sc, 1, act.as<int8_t>());
         for (int j = 0; j < m; j++) {
             if (j > 0) upload_flags(hact);
-            double *vj = Vp + (size_t)j * ldq, *zj = Zp + (size_t)j * ldq, *w = Vp + (size_t)(j + 1) * ldq;
-            M(vj, zj, NR);
-            spmv_f64(c, A, zj, w, KC_SPMV, NR, sysmap);
-            int nq = j + 1;
-            const double sf = sysmap.frac;  // share of the rows of live instances
-            double fl = 2.0 * (double)N * NR * nq * sf;
-            // classical Gram-Schmidt for every problem; the second pass runs
-            // for the problems whose first pass cancelled severely (the
-            // others' chunks return at once)
-            for (int pass = 0; pass < 2; pass++) {
-                double *hh = pass == 0 ? h1 : h2;
-                // first pass: the active problems' instances; second: the flagged problems'
-                const int8_t *mk = pass == 0 ? act.as<int8_t>() : f2.as<int8_t>();
-                int kd = pass == 0 ? KC_GS_DOT : KC_NONE, ka = pass == 0 ? KC_GS_AXPY : KC_NONE;
-                MDS_LAUNCH_F(c, kd, 8.0 * N * NR * (nq + 1) * sf, fl, (k_bdot<NR>), (unsigned)((int64_t)nch * nq), RED_BLOCK, 0, CHp,
-                             nch, Vp, ldq, nq, w, PT, mk);
-                MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, nq), 32, 0, PT, nch, nq, NR, IO, IL, P, hh, 0, mk);
-                MDS_LAUNCH_F(c, ka, 8.0 * N * NR * (nq + 2) * sf, fl, (k_bmaxpy<NR, -1>), nch, RED_BLOCK, 0, CHp, Vp,
-                             ldq, nq, hh, w, PT, mk, (const int32_t *)nullptr);
-                MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, 1), 32, 0, PT, nch, 1, NR, IO, IL, P, nsq, 0, mk);
-                if (pass == 0)
-                    MDS_LAUNCH(c, KC_NONE, 0, k_bflag, grid_for(P, 128), 128, 0, P, nq, act.as<int8_t>(), h1, nsq,
-                               o.reorth_eta2, f2.as<int8_t>(), h2);
-            }
-            MDS_LAUNCH(c, KC_NONE, 0, k_barnoldi, grid_for(P, 128), 128, 0, P, j, m, act.as<int8_t>(), H.as<double>(),
-                       h1, h2, nsq, cs, sn, g, sc);
-            MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, nch, RED_BLOCK, 0, CHp, w, sc, 3, act.as<int8_t>());
-            MDS_CUDA(cudaMemcpyAsync(c.h_pin, sc, sizeof(double) * (size_t)P * 8, cudaMemcpyDeviceToHost, c.stream));
-            c.sync();
+            run_step(j);
             const double *hp = static_cast<const double *>(c.h_pin);
             bool live = false;
             for (int p = 0; p < P; p++) {
