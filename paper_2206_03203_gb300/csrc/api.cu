@@ -483,6 +483,9 @@ int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_preco
         p->sys = sys;
         p->o = o;
         p->S = schur_build(*c, sys->view[0], sys->view[1], sys->view[2], sys->view[3], p->dk);
+        // the storage autotuner times with the column count of the system's
+        // right-hand sides (interleaved in a multi-column solve)
+        p->h[0].tune_nr = p->h[1].tune_nr = sys->nrhs;
         // a packed batch: every instance's blocks coarsened as if alone
         const bool packed = sys->n_inst > 1 && sys->own.moff.size() == (size_t)sys->n_inst + 1 &&
                             sys->own.foff.size() == (size_t)sys->n_inst + 1;

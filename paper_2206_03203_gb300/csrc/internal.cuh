@@ -515,6 +515,7 @@ struct Hierarchy {
     int sweeps = 1;
     int cheb_degree = 2;
     int nr_cap = 0;   // columns the level work vectors hold
+    int tune_nr = 1;  // columns the storage autotuner times with (those of the system's right-hand sides)
     bool use_tail = true;  // run the coarse end of the V-cycle as one cluster kernel
     // level 0 is a Cartesian stencil (the S~ of primal assembled systems):
     // grid dimension and cells per side of each instance (empty: unknown)

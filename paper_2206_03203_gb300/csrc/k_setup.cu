@@ -898,7 +898,9 @@ void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h,
                        L.l1.as<double>(), L.dinv.as<float>());
     }
     h.nr_cap = 0;
-    hierarchy_reserve(c, h, 1);
+    // work vectors for the columns the solves will use (the autotuner times
+    // the level kernels with them)
+    hierarchy_reserve(c, h, h.tune_nr >= 8 ? 8 : h.tune_nr >= 4 ? 4 : h.tune_nr >= 2 ? 2 : 1);
     if (h.dense) {
         Level &L = h.lv.back();
         h.nd = L.A.nrow;

@@ -19,8 +19,8 @@ namespace mds {
 // per vector type (k_vcycle_f64.cu, k_vcycle_f32.cu)
 void vcycle_run_f64(Ctx &c, Hierarchy &h, const double *b, double *x, int nr);
 void vcycle_run_f32(Ctx &c, Hierarchy &h, const float *b, float *x, int nr);
-float time_level_f64(Ctx &c, const Level &L);
-float time_level_f32(Ctx &c, const Level &L);
+float time_level_f64(Ctx &c, const Level &L, int nr);
+float time_level_f32(Ctx &c, const Level &L, int nr);
 
 // The level work vectors hold up to nr_cap interleaved columns.
 void hierarchy_reserve(Ctx &c, Hierarchy &h, int nr) {
@@ -276,11 +276,11 @@ static int default_g(const Level &L) {
 // Autotuner: time CSR with G/2, G, 2G lanes per row and SELL-C-sigma for a
 // few (C, sigma) pairs on this level, keep the fastest.  Choices are cached in
 // the context by (rows, nonzeros, storage type).
-template <class XT> static void autotune_level(Ctx &c, Level &L) {
-    auto time_level = [](Ctx &cc, const Level &LL) {
-        return std::is_same<XT, double>::value ? time_level_f64(cc, LL) : time_level_f32(cc, LL);
+template <class XT> static void autotune_level(Ctx &c, Level &L, int nr) {
+    auto time_level = [nr](Ctx &cc, const Level &LL) {
+        return std::is_same<XT, double>::value ? time_level_f64(cc, LL, nr) : time_level_f32(cc, LL, nr);
     };
-    auto key = std::make_tuple(L.A.nrow, L.A.nnz, L.vt * 2 + (L.dia_D > 0 ? 1 : 0));
+    auto key = std::make_tuple(L.A.nrow, L.A.nnz, (L.vt * 2 + (L.dia_D > 0 ? 1 : 0)) * 16 + nr);
     auto it = c.tune_cache.find(key);
     if (it != c.tune_cache.end()) {
         const TuneChoice &t = it->second;
@@ -294,7 +294,7 @@ template <class XT> static void autotune_level(Ctx &c, Level &L) {
         return;
     }
     // defined inputs for the timing runs
-    size_t vb = sizeof(XT) * (size_t)L.A.nrow;
+    size_t vb = sizeof(XT) * (size_t)L.A.nrow * (size_t)nr;
     MDS_CUDA(cudaMemsetAsync(L.b.p, 0, vb, c.stream));
     MDS_CUDA(cudaMemsetAsync(L.x.p, 0, vb, c.stream));
     TuneChoice best{FMT_CSR, default_g(L), 32, 1};
@@ -387,9 +387,9 @@ void level_storage(Ctx &c, Hierarchy &h, const mds_setup_opts &o) {
             build_sell_vt(c, L, o.sell_c, o.sell_sigma);
         } else if (o.format == MDS_FORMAT_AUTO && n >= 20000) {
             if (h.prec == 64)
-                autotune_level<double>(c, L);
+                autotune_level<double>(c, L, h.nr_cap);
             else
-                autotune_level<float>(c, L);
+                autotune_level<float>(c, L, h.nr_cap);
         }
         if (L.fmt != FMT_DIA) drop_dia(L);
     }

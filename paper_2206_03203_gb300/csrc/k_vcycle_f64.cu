@@ -6,6 +6,6 @@ namespace mds {
 
 void vcycle_run_f64(Ctx &c, Hierarchy &h, const double *b, double *x, int nr) { vcycle_nr<double>(c, h, b, x, nr); }
 
-float time_level_f64(Ctx &c, const Level &L) { return time_level<double>(c, L); }
+float time_level_f64(Ctx &c, const Level &L, int nr) { return time_level<double>(c, L, nr); }
 
 }  // namespace mds

@@ -325,6 +325,10 @@ __global__ void __launch_bounds__(256) k_level_dia(DiaMat<VT> A, const XT *__res
         k = lo == hi ? lo : seg_find(A.seg, A.K, row);
     }
     const int64_t sd = live ? A.side[k] : 0;
+    // rows of the instance: neighbour indices are clamped into them, so the
+    // gathers do not wait for the coefficient loads (an absent neighbour's
+    // coefficient is zero, and the clamped row's entries are finite)
+    const int64_t lo = live ? (A.K > 1 ? A.seg[k] : 0) : 0, hi = live ? (A.K > 1 ? A.seg[k + 1] : A.n) - 1 : 0;
     int64_t off[7];
     if (A.D == 7) {
         off[0] = -sd * sd; off[1] = -sd; off[2] = -1; off[3] = 0; off[4] = 1; off[5] = sd; off[6] = sd * sd;
@@ -343,7 +347,8 @@ __global__ void __launch_bounds__(256) k_level_dia(DiaMat<VT> A, const XT *__res
         pj[d] = row;
         if (d < A.D && live) {
             pa[d] = ld_stream(A.v + (int64_t)d * A.n + row);
-            if (cvt<XT>(pa[d]) != (XT)0) pj[d] = row + off[d];  // absent neighbours read the row itself
+            const int64_t j = row + off[d];
+            pj[d] = j < lo ? lo : (j > hi ? hi : j);
         }
     }
     if constexpr (FUSED) {
@@ -1185,16 +1190,14 @@ static void vcycle_nr(Ctx &c, Hierarchy &h, const XT *b, XT *x, int nr) {
     }
 }
 
-// Time the stored-residual kernel on the level in its current storage (best
-// of three after a warm-up launch).
-template <class XT> static float time_level(Ctx &c, const Level &L) {
+template <class XT, int NR> static float time_level_nr(Ctx &c, const Level &L) {
     cudaEvent_t e0, e1;
     MDS_CUDA(cudaEventCreate(&e0));
     MDS_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
     for (int rep = 0; rep < 4; rep++) {
         MDS_CUDA(cudaEventRecord(e0, c.stream));
-        level_op<XT, VK_RESID, 1>(c, L, L.b.as<XT>(), L.x.as<XT>(), nullptr, nullptr, L.r.as<XT>(), 0);
+        level_op<XT, VK_RESID, NR>(c, L, L.b.as<XT>(), L.x.as<XT>(), nullptr, nullptr, L.r.as<XT>(), 0);
         MDS_CUDA(cudaEventRecord(e1, c.stream));
         MDS_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -1204,6 +1207,17 @@ template <class XT> static float time_level(Ctx &c, const Level &L) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return best;
+}
+
+// Time the stored-residual kernel on the level in its current storage with
+// nr interleaved columns (best of three after a warm-up launch).
+template <class XT> static float time_level(Ctx &c, const Level &L, int nr) {
+    switch (nr) {
+        case 8: return time_level_nr<XT, 8>(c, L);
+        case 4: return time_level_nr<XT, 4>(c, L);
+        case 2: return time_level_nr<XT, 2>(c, L);
+        default: return time_level_nr<XT, 1>(c, L);
+    }
 }
 
 }  // namespace mds
