@@ -456,6 +456,8 @@ struct Level {
     Buf dia_val;           // [dia_D][n] in the storage type
     Buf dia_seg;           // int64 [K + 1] instance row offsets
     Buf dia_side;          // int32 [K] cells per side
+    Buf dia_ck;            // int32 [4 chunks]: (first row, last row, cells per side, instance) of the
+                           // instance of each 256-row chunk; instance -1 for a chunk holding two
     int K = 1;             // instances (packed batches)
     int sell_sigma = 1;    // SELL sorting window (rows)
 };
@@ -496,7 +498,9 @@ struct DenseBlocks {
     int K = 0;
     int64_t nmax = 0, nrow = 0, total = 0;  // largest block, rows, sum of n_b^2
     std::vector<DBlk> host;
-    Buf blk;  // DBlk [K]
+    Buf blk;              // DBlk [K]
+    Buf tiles;            // int2 [ntiles]: (block, first row) of each 32-row tile of a block
+    int64_t ntiles = 0;
 };
 
 struct Hierarchy {

@@ -12,6 +12,7 @@
 namespace mds {
 
 constexpr int NB = 32;
+constexpr int DTILE = 32;  // rows of a block applied by one thread block
 
 __global__ void k_densify(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                           const double *__restrict__ v, const DBlk *__restrict__ blk, double *__restrict__ D,
@@ -176,6 +177,107 @@ __global__ void k_chol_inverse(const double *__restrict__ Lall, const double *__
     for (int64_t i = lane; i < n; i += 32) X[j * n + i] = y[i];
 }
 
+// Columns j0 .. j0 + 31 of A^-1 for one block (one thread block per 32-column
+// tile, 256 threads): L Y = E, then L^T X = Y, by 32-row panels with the
+// 32 right-hand sides in shared memory (row stride 33).  Each panel first
+// takes the product of the finished panels (every lane one column, every
+// warp four rows: FP64 products from shared memory, no reductions), then a
+// warp solves the panel's 32 x 32 triangle (right-looking, column per lane).
+// A^-1 is symmetric: the tile writes rows j0 .. j0 + 31 of the inverse.
+constexpr int INV_PAD = 33;
+__global__ void __launch_bounds__(256) k_chol_inv_tiles(const double *__restrict__ Lall, const DBlk *__restrict__ blk,
+                                                        const int2 *__restrict__ tiles, double *__restrict__ Xall) {
+    mds_pdl_entry();
+    extern __shared__ double Y[];  // [n][INV_PAD]
+    __shared__ double T[32][33];   // the panel's diagonal block of L
+    const int2 tl = tiles[blockIdx.x];
+    const DBlk b = blk[tl.x];
+    const int n = b.n, j0 = tl.y, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const double *L = Lall + b.off;
+    double *X = Xall + b.off;
+    for (int e = tid; e < n * 32; e += blockDim.x) {
+        const int i = e >> 5, c = e & 31;
+        Y[i * INV_PAD + c] = i == j0 + c ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    // forward: rows below j0 of Y stay zero
+    for (int p0 = j0; p0 < n; p0 += 32) {
+        const int pn = min(32, n - p0);
+        if (p0 > j0) {
+            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int k = j0; k < p0; k++) {
+                const double y = Y[k * INV_PAD + lane];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int r = w * 4 + q;
+                    if (r < pn) acc[q] += L[(int64_t)(p0 + r) * n + k] * y;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int r = w * 4 + q;
+                if (r < pn) Y[(p0 + r) * INV_PAD + lane] -= acc[q];
+            }
+        }
+        for (int e = tid; e < pn * pn; e += blockDim.x) {
+            const int r = e / pn, q = e % pn;
+            T[r][q] = q <= r ? L[(int64_t)(p0 + r) * n + p0 + q] : 0.0;
+        }
+        __syncthreads();
+        if (w == 0) {
+            for (int i = 0; i < pn; i++) {
+                const double yi = Y[(p0 + i) * INV_PAD + lane] / T[i][i];
+                Y[(p0 + i) * INV_PAD + lane] = yi;
+                for (int k = i + 1; k < pn; k++) Y[(p0 + k) * INV_PAD + lane] -= T[k][i] * yi;
+            }
+        }
+        __syncthreads();
+    }
+    // backward over every row, panels on the same 32-row grid as the forward
+    // pass, from the last one up
+    const int top = j0 - ((j0 + 31) / 32) * 32;  // <= 0: the first panel may start above row 0
+    int last = j0;
+    while (last + 32 < n) last += 32;
+    for (int s0 = last; s0 >= top; s0 -= 32) {
+        const int a = max(s0, 0), e1 = min(s0 + 32, n), pn = e1 - a;
+        if (pn <= 0) continue;
+        if (e1 < n) {
+            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int k = e1; k < n; k++) {
+                const double x = Y[k * INV_PAD + lane];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int r = w * 4 + q;
+                    if (r < pn) acc[q] += L[(int64_t)k * n + a + r] * x;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int r = w * 4 + q;
+                if (r < pn) Y[(a + r) * INV_PAD + lane] -= acc[q];
+            }
+        }
+        for (int e = tid; e < pn * pn; e += blockDim.x) {
+            const int r = e / pn, q = e % pn;
+            T[r][q] = q <= r ? L[(int64_t)(a + r) * n + a + q] : 0.0;
+        }
+        __syncthreads();
+        if (w == 0) {
+            for (int i = pn - 1; i >= 0; i--) {
+                const double xi = Y[(a + i) * INV_PAD + lane] / T[i][i];
+                Y[(a + i) * INV_PAD + lane] = xi;
+                for (int k = 0; k < i; k++) Y[(a + k) * INV_PAD + lane] -= T[i][k] * xi;
+            }
+        }
+        __syncthreads();
+    }
+    const int nc = min(32, n - j0);
+    for (int e = tid; e < nc * n; e += blockDim.x) {
+        const int c = e / n, i = e % n;
+        X[(int64_t)(j0 + c) * n + i] = Y[i * INV_PAD + c];
+    }
+}
+
 void dense_spd_inverse(Ctx &c, const mds_csr &A, const std::vector<int64_t> &seg, Buf &Ainv, DenseBlocks &db) {
     const int K = (int)seg.size() - 1;
     MDS_REQUIRE(K >= 1 && seg[0] == 0 && seg[K] == A.nrow, MDS_ERR_INVALID, "coarsest segments do not cover the level");
@@ -196,6 +298,15 @@ void dense_spd_inverse(Ctx &c, const mds_csr &A, const std::vector<int64_t> &seg
     db.host = hb;
     db.blk = Buf(&c, sizeof(DBlk) * (size_t)K);
     MDS_CUDA(cudaMemcpyAsync(db.blk.p, hb.data(), sizeof(DBlk) * (size_t)K, cudaMemcpyHostToDevice, c.stream));
+    {
+        std::vector<int2> tl;
+        for (int k = 0; k < K; k++)
+            for (int32_t r = 0; r < hb[k].n; r += DTILE) tl.push_back(make_int2(k, r));
+        db.ntiles = (int64_t)tl.size();
+        db.tiles = Buf(&c, sizeof(int2) * tl.size());
+        MDS_CUDA(cudaMemcpyAsync(db.tiles.p, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice, c.stream));
+        c.sync();
+    }
     const DBlk *B = db.blk.as<DBlk>();
     Buf D(&c, sizeof(double) * (size_t)tot);
     MDS_CUDA(cudaMemsetAsync(D.p, 0, sizeof(double) * (size_t)tot, c.stream));
@@ -213,10 +324,18 @@ void dense_spd_inverse(Ctx &c, const mds_csr &A, const std::vector<int64_t> &seg
         MDS_LAUNCH(c, KC_NONE, 0, k_chol_update, dim3((unsigned)(m * (m + 1) / 2), K), 256, 0, D.as<double>(), B, k0);
     }
     c.check_err("coarsest Cholesky");
+    Ainv = Buf(&c, sizeof(double) * (size_t)tot);
+    const size_t tsmem = sizeof(double) * (size_t)nmax * INV_PAD;
+    if (tsmem <= 200 * 1024) {
+        if (tsmem > 48 * 1024)
+            MDS_CUDA(cudaFuncSetAttribute(k_chol_inv_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
+        MDS_LAUNCH(c, KC_NONE, 0, k_chol_inv_tiles, (unsigned)db.ntiles, 256, tsmem, D.as<double>(), B,
+                   db.tiles.as<int2>(), Ainv.as<double>());
+        return;
+    }
     Buf U(&c, sizeof(double) * (size_t)tot);
     MDS_LAUNCH(c, KC_NONE, 0, k_transpose_lower, dim3(grid_for(nmax * nmax, 256), K), 256, 0, D.as<double>(),
                U.as<double>(), B);
-    Ainv = Buf(&c, sizeof(double) * (size_t)tot);
     int wpb = 4;
     while (wpb > 1 && (size_t)wpb * nmax * sizeof(double) > 48 * 1024) wpb /= 2;
     size_t smem = (size_t)wpb * nmax * sizeof(double);
@@ -293,13 +412,103 @@ __global__ void k_dense_apply(const double *__restrict__ Mall, const DBlk *__res
         for (int c = 0; c < NR; c++) yall[row * NR + c] = (XT)s[c];
 }
 
+// Sum of v[0..15] over the 32 lanes of a warp by halving exchanges: after
+// the steps lanes 2u and 2u + 1 hold the total of value u = (lane >> 1) & 15
+// (16 additions per lane instead of 5 per value).
+__device__ __forceinline__ double warp_sum16(double (&v)[16]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int h = 8, m = 16; h >= 1; h >>= 1, m >>= 1) {
+        const bool up = (lane & m) != 0;
+#pragma unroll
+        for (int i = 0; i < h; i++) {
+            const double keep = up ? v[i + h] : v[i], send = up ? v[i] : v[i + h];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// y = M x on 32-row tiles: one thread block per tile (64 NR threads), the
+// tile's block of x staged once in shared memory in FP64 (column-major, so a
+// warp's reads are contiguous), each warp 16 / NR rows with the lanes
+// striding over the columns of M; FP64 products and sums.
+template <class XT, int NR>
+__global__ void __launch_bounds__(64 * NR) k_dense_apply_tiles(const double *__restrict__ Mall,
+                                                               const DBlk *__restrict__ blk,
+                                                               const int2 *__restrict__ tiles,
+                                                               const XT *__restrict__ xall, XT *__restrict__ yall,
+                                                               const int8_t *__restrict__ on) {
+    constexpr int RPW = 16 / NR;  // rows per warp
+    extern __shared__ double xs[];  // [NR][n]
+    const int2 t = tiles[blockIdx.x];
+    if (on && !on[t.x]) return;  // a finished instance of a batched solve
+    const DBlk b = blk[t.x];
+    const int n = b.n, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int r0 = t.y + w * RPW;
+    const double *M = Mall + b.off;
+    // the first column stripe of the warp's rows (M is fixed after set-up)
+    double m0[RPW];
+#pragma unroll
+    for (int r = 0; r < RPW; r++) m0[r] = r0 + r < n && lane < n ? M[(int64_t)(r0 + r) * n + lane] : 0.0;
+    mds_pdl_wait();
+    mds_pdl_trigger();
+    const XT *x = xall + b.row * NR;
+    for (int e = threadIdx.x; e < n * NR; e += blockDim.x) xs[(e % NR) * n + e / NR] = (double)x[e];
+    __syncthreads();
+    if (r0 >= n) return;  // a warp past the block's last row (after the barrier)
+    double s[16];
+#pragma unroll
+    for (int v = 0; v < 16; v++) s[v] = 0.0;
+    if (lane < n) {
+#pragma unroll
+        for (int r = 0; r < RPW; r++)
+#pragma unroll
+            for (int c = 0; c < NR; c++) s[r * NR + c] = m0[r] * xs[c * n + lane];
+    }
+    for (int k = lane + 32; k < n; k += 32) {
+        double xv[NR];
+#pragma unroll
+        for (int c = 0; c < NR; c++) xv[c] = xs[c * n + k];
+#pragma unroll
+        for (int r = 0; r < RPW; r++) {
+            const double mk = r0 + r < n ? M[(int64_t)(r0 + r) * n + k] : 0.0;
+#pragma unroll
+            for (int c = 0; c < NR; c++) s[r * NR + c] += mk * xv[c];
+        }
+    }
+    const double tot = warp_sum16(s);
+    const int u = (lane >> 1) & 15, r = u / NR, c = u % NR;
+    if ((lane & 1) == 0 && r0 + r < n) yall[(b.row + r0 + r) * NR + c] = (XT)tot;
+}
+
 template <class XT>
 static void dense_apply_t(Ctx &c, const DenseBlocks &db, const double *M, int nr, const XT *x, XT *y,
                           const int8_t *on) {
     const int64_t n = db.nrow;
     double bytes = 8.0 * (double)db.total + 2.0 * sizeof(XT) * n * nr;
-    unsigned g = grid_for(n * 32, 256);
     const DBlk *B = db.blk.as<DBlk>();
+    const size_t smem = sizeof(double) * (size_t)db.nmax * (size_t)nr;
+    if (db.ntiles > 0 && smem <= 96 * 1024) {
+        const int2 *T = db.tiles.as<int2>();
+        const unsigned g = (unsigned)db.ntiles;
+        switch (nr) {
+#define MDS_DTILE_CASE(NRV)                                                                                        \
+    case NRV:                                                                                                      \
+        if (smem > 48 * 1024)                                                                                      \
+            MDS_CUDA(cudaFuncSetAttribute(k_dense_apply_tiles<XT, NRV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                          (int)smem));                                                             \
+        MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply_tiles<XT, NRV>), g, 64 * NRV, smem, M, B, T, x, y, on);     \
+        return;
+            MDS_DTILE_CASE(1)
+            MDS_DTILE_CASE(2)
+            MDS_DTILE_CASE(4)
+            MDS_DTILE_CASE(8)
+#undef MDS_DTILE_CASE
+            default: throw Error(MDS_ERR_INVALID, "dense apply: column count must be 1, 2, 4 or 8");
+        }
+    }
+    unsigned g = grid_for(n * 32, 256);
     switch (nr) {
         case 1: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 1>), g, 256, 0, M, B, db.K, n, x, y, on); break;
         case 2: MDS_LAUNCH(c, KC_NONE, bytes, (k_dense_apply<XT, 2>), g, 256, 0, M, B, db.K, n, x, y, on); break;

@@ -1097,21 +1097,31 @@ __global__ void k_bflag(int P, int nq, const int8_t *__restrict__ active, const 
 // W(i, c) *= f[p]  (f = sc[p * 8 + slot]) for active problems; inactive ones
 // get exact zeros, so the vectors of a problem that has stopped stay bounded
 // (and 0 * their entries stays 0 in the shared kernels).
+// The chunk is scaled element by element (entry (i, c) at i * NR + c): the
+// block size is a multiple of NR, so each thread keeps one column c and one
+// factor, and a warp's loads and stores are contiguous.
 template <int NR>
-__global__ void k_bscale(const Chunk *__restrict__ ch, double *__restrict__ W, const double *__restrict__ sc, int slot,
-                         const int8_t *__restrict__ active) {
+__global__ void __launch_bounds__(RED_BLOCK) k_bscale(const Chunk *__restrict__ ch, double *__restrict__ W,
+                                                       const double *__restrict__ sc, int slot,
+                                                       const int8_t *__restrict__ active) {
+    static_assert(RED_BLOCK % NR == 0, "block size must be a multiple of the column count");
     mds_pdl_entry();
     Chunk k = ch[blockIdx.x];
     if (chunk_skipped<NR>(active, k.inst)) return;  // a finished instance: its rows are no longer used
-    double f[NR];
-#pragma unroll
-    for (int c = 0; c < NR; c++) {
-        int64_t p = (int64_t)k.inst * NR + c;
-        f[c] = active[p] ? sc[p * 8 + slot] : 0.0;
+    const int64_t p = (int64_t)k.inst * NR + threadIdx.x % NR;
+    const double f = active[p] ? sc[p * 8 + slot] : 0.0;
+    double *w = W + k.b * NR;
+    const int64_t m = (k.e - k.b) * NR;
+    constexpr int B = RED_BLOCK;
+    int64_t i = threadIdx.x;
+    for (; i + 3 * B < m; i += 4 * B) {
+        const double a0 = w[i], a1 = w[i + B], a2 = w[i + 2 * B], a3 = w[i + 3 * B];
+        w[i] = f == 0.0 ? 0.0 : a0 * f;
+        w[i + B] = f == 0.0 ? 0.0 : a1 * f;
+        w[i + 2 * B] = f == 0.0 ? 0.0 : a2 * f;
+        w[i + 3 * B] = f == 0.0 ? 0.0 : a3 * f;
     }
-    for (int64_t i = k.b + threadIdx.x; i < k.e; i += blockDim.x)
-#pragma unroll
-        for (int c = 0; c < NR; c++) W[i * NR + c] = f[c] == 0.0 ? 0.0 : W[i * NR + c] * f[c];
+    for (; i < m; i += B) w[i] = f == 0.0 ? 0.0 : w[i] * f;
 }
 
 // per problem: beta = sqrt(nsq), g = (beta, 0, ...), sc[1] = 1/beta

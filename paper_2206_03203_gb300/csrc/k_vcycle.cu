@@ -243,6 +243,7 @@ static bool build_dia(Ctx &c, Level &L, const Hierarchy &h) {
                              c.stream));
     MDS_CUDA(cudaMemcpyAsync(L.dia_side.p, h.st_side.data(), sizeof(int32_t) * (size_t)K, cudaMemcpyHostToDevice,
                              c.stream));
+    if (n >= INT32_MAX) return false;  // the stencil kernel indexes rows in 32 bits
     Buf bad(&c, sizeof(int));
     MDS_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), c.stream));
     if (L.vt == VT_F64)
@@ -257,6 +258,27 @@ static bool build_dia(Ctx &c, Level &L, const Hierarchy &h) {
         L.dia_side.reset();
         return false;
     }
+    // per 256-row chunk: the bounds and cells per side of its instance, so
+    // that a row finds its stencil offsets and clamp with two independent
+    // loads instead of a chain of dependent ones
+    {
+        const std::vector<int64_t> &sg = h.seg[0];
+        const int64_t nch = (n + (1 << LIVE_CHUNK_LOG2) - 1) >> LIVE_CHUNK_LOG2;
+        std::vector<int32_t> t((size_t)(4 * nch), 0);
+        int k = 0;
+        for (int64_t q = 0; q < nch; q++) {
+            const int64_t r0 = q << LIVE_CHUNK_LOG2, r1 = std::min(n, r0 + (1 << LIVE_CHUNK_LOG2));
+            while (k + 1 < K && sg[k + 1] <= r0) k++;
+            const bool one = sg[k] <= r0 && r1 <= sg[k + 1];
+            t[4 * q] = one ? (int32_t)sg[k] : 0;
+            t[4 * q + 1] = one ? (int32_t)(sg[k + 1] - 1) : 0;
+            t[4 * q + 2] = one ? h.st_side[k] : 0;
+            t[4 * q + 3] = one ? k : -1;
+        }
+        L.dia_ck = Buf(&c, sizeof(int32_t) * t.size());
+        MDS_CUDA(cudaMemcpyAsync(L.dia_ck.p, t.data(), sizeof(int32_t) * t.size(), cudaMemcpyHostToDevice, c.stream));
+        c.sync();
+    }
     L.dia_D = D;
     return true;
 }
@@ -265,6 +287,7 @@ static void drop_dia(Level &L) {
     L.dia_val.reset();
     L.dia_seg.reset();
     L.dia_side.reset();
+    L.dia_ck.reset();
     L.dia_D = 0;
 }
 

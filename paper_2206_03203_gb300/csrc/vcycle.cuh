@@ -299,62 +299,75 @@ __global__ void __launch_bounds__(256) k_level(LvlMat<VT> A, const XT *__restric
 // result bit for bit.
 template <class VT> struct DiaMat {
     int64_t n;
-    int D;
     const VT *v;            // [D][n]
     const int64_t *seg;     // instance row offsets [K + 1]
     const int32_t *side;    // cells per side [K]
-    const int32_t *ck;      // least / greatest instance of each 256-row chunk (K > 1)
+    const int4 *ck;         // (first row, last row, cells per side, instance) of each 256-row chunk's
+                            // instance; instance -1: the chunk holds rows of two instances
     int K;
     LiveMap lm;
 };
 
-template <class VT, class XT, int K, int NR>
-__global__ void __launch_bounds__(256) k_level_dia(DiaMat<VT> A, const XT *__restrict__ dinv, const XT *__restrict__ b,
-                                                   const XT *__restrict__ xin, const int32_t *__restrict__ agg,
-                                                   const XT *__restrict__ xc, XT *__restrict__ out) {
+// Resident blocks per SM asked of the compiler (measured on the finest level
+// of a 256-instance batch): FP32 vectors of up to four columns, six for the
+// residual forms (40 registers) and five for the post-smoothing form, which
+// holds two gathers per neighbour; FP64 vectors of up to four columns, four;
+// wider vectors, no bound.
+template <class XT, int K, int NR> constexpr int dia_min_blocks() {
+    return NR > 4 ? 1 : sizeof(XT) > 4 ? 4 : K == VK_POST ? 5 : 6;
+}
+
+template <class VT, class XT, int K, int NR, int D>
+__global__ void __launch_bounds__(256, dia_min_blocks<XT, K, NR>())
+    k_level_dia(DiaMat<VT> A, const XT *__restrict__ dinv, const XT *__restrict__ b, const XT *__restrict__ xin,
+                const int32_t *__restrict__ agg, const XT *__restrict__ xc, XT *__restrict__ out) {
     const int64_t r0 = (int64_t)blockIdx.x * 256, r1 = r0 + 256 < A.n ? r0 + 256 : A.n;
     if (!block_rows_live(A.lm, r0, r1)) return;
-    const int64_t row = r0 + threadIdx.x;
+    // level rows fit in 32 bits (column indices are 32-bit on every level)
+    const int row = (int)r0 + (int)threadIdx.x;
     const bool live = row < A.n;
-    // the row's instance: from its 256-row chunk, searched only in a chunk
-    // that holds rows of two instances
-    int k = 0;
-    if (A.K > 1 && live) {
-        const int64_t c = row >> LIVE_CHUNK_LOG2;
-        const int lo = __ldg(A.ck + 2 * c), hi = __ldg(A.ck + 2 * c + 1);
-        k = lo == hi ? lo : seg_find(A.seg, A.K, row);
+    // the bounds and grid side of the row's instance from its 256-row chunk
+    // (one broadcast load); searched only in a chunk that holds rows of two
+    // instances. Neighbour indices are clamped into the instance (an absent
+    // neighbour has a zero coefficient), so no instance reads another's rows.
+    int lo = 0, hi = 0, sd = 0;
+    if (live) {
+        const int4 t = __ldg(A.ck + (row >> LIVE_CHUNK_LOG2));
+        lo = t.x;
+        hi = t.y;
+        sd = t.z;
+        if (t.w < 0) {
+            const int k = seg_find(A.seg, A.K, row);
+            lo = (int)A.seg[k];
+            hi = (int)A.seg[k + 1] - 1;
+            sd = A.side[k];
+        }
     }
-    const int64_t sd = live ? A.side[k] : 0;
-    // rows of the instance: neighbour indices are clamped into them, so the
-    // gathers do not wait for the coefficient loads (an absent neighbour's
-    // coefficient is zero, and the clamped row's entries are finite)
-    const int64_t lo = live ? (A.K > 1 ? A.seg[k] : 0) : 0, hi = live ? (A.K > 1 ? A.seg[k + 1] : A.n) - 1 : 0;
-    int64_t off[7];
-    if (A.D == 7) {
+    int off[D];
+    if constexpr (D == 7) {
         off[0] = -sd * sd; off[1] = -sd; off[2] = -1; off[3] = 0; off[4] = 1; off[5] = sd; off[6] = sd * sd;
     } else {
-        off[0] = -sd; off[1] = -1; off[2] = 0; off[3] = 1; off[4] = sd; off[5] = 0; off[6] = 0;
+        off[0] = -sd; off[1] = -1; off[2] = 0; off[3] = 1; off[4] = sd;
     }
     // constants of this launch (values, 1/D1, aggregates) before the wait
     constexpr bool FUSED = K == VK_RESID0 || K == VK_POST;
-    VT pa[7];
-    int64_t pj[7];
-    XT pd[FUSED ? 7 : 1];
-    int32_t pg[K == VK_POST ? 7 : 1];
+    VT pa[D];
+    int32_t pj[D];
+    XT pd[FUSED ? D : 1];
+    int32_t pg[K == VK_POST ? D : 1];
 #pragma unroll
-    for (int d = 0; d < 7; d++) {
+    for (int d = 0; d < D; d++) {
         pa[d] = (VT)0;
         pj[d] = row;
-        if (d < A.D && live) {
+        if (live) {
             pa[d] = ld_stream(A.v + (int64_t)d * A.n + row);
-            const int64_t j = row + off[d];
-            pj[d] = j < lo ? lo : (j > hi ? hi : j);
+            if (off[d] != 0 || d != D / 2) pj[d] = min(max(row + off[d], lo), hi);
         }
     }
     if constexpr (FUSED) {
 #pragma unroll
-        for (int d = 0; d < 7; d++)
-            if (d < A.D && live) {
+        for (int d = 0; d < D; d++)
+            if (live) {
                 pd[d] = __ldg(dinv + pj[d]);
                 if constexpr (K == VK_POST) pg[d] = agg ? __ldg(agg + pj[d]) : -1;
             }
@@ -378,16 +391,15 @@ __global__ void __launch_bounds__(256) k_level_dia(DiaMat<VT> A, const XT *__res
 #pragma unroll
     for (int c = 0; c < NR; c++) s[c] = 0;
 #pragma unroll
-    for (int d = 0; d < 7; d++)
-        if (d < A.D) {
+    for (int d = 0; d < D; d++) {
             XT a = cvt<XT>(pa[d]);
             Vec<XT, NR> y;
             if constexpr (K == VK_POST)
-                y = f.with((int32_t)pj[d], pd[d], pg[d]);
+                y = f.with(pj[d], pd[d], pg[d]);
             else if constexpr (K == VK_RESID0)
-                y = f.with((int32_t)pj[d], pd[d], -1);
+                y = f.with(pj[d], pd[d], -1);
             else
-                y = f((int32_t)pj[d]);
+                y = f(pj[d]);
 #pragma unroll
             for (int c = 0; c < NR; c++) s[c] += a * y.v[c];
         }
@@ -593,13 +605,21 @@ static void launch_level_pf(Ctx &c, const Level &L, const XT *dinv, const XT *b,
     double flops = NR * (2.0 * L.A.nnz + (K == VK_RESID0 ? n : K == VK_POST ? 5.0 * n : K == VK_SMOOTH ? 3.0 * n : 0.0));
     int cls = !L.timed_level ? KC_NONE : (K == VK_RESID0 || K == VK_RESID) ? KC_VC_RESID : KC_VC_POST;
     if (L.fmt == FMT_DIA) {
-        DiaMat<VT> dm{n, L.dia_D, L.dia_val.as<VT>(), L.dia_seg.as<int64_t>(), L.dia_side.as<int32_t>(),
-                      L.ck.p ? L.ck.as<int32_t>() : nullptr, L.ck.p ? L.K : 1, m.lm};
-        // algorithmic bytes: the planes instead of values, columns and row pointers
-        bytes = bytes - vb - 4.0 * (n + 1) + (double)L.dia_D * sizeof(VT) * n;
-        MDS_LAUNCH_F(c, cls, bytes * m.lm.frac, flops * m.lm.frac, (k_level_dia<VT, XT, K, NR>), grid_for(n, 256), 256,
-                     0, dm, dinv, b, xin, agg, xc, out);
-        return;
+        if constexpr (std::is_same<VT, float>::value || std::is_same<VT, double>::value) {
+            DiaMat<VT> dm{n, L.dia_val.as<VT>(), L.dia_seg.as<int64_t>(), L.dia_side.as<int32_t>(),
+                          L.dia_ck.as<int4>(), (int)(L.dia_side.bytes / sizeof(int32_t)), m.lm};
+            // algorithmic bytes: the planes instead of values, columns and row pointers
+            bytes = bytes - vb - 4.0 * (n + 1) + (double)L.dia_D * sizeof(VT) * n;
+            if (L.dia_D == 7)
+                MDS_LAUNCH_F(c, cls, bytes * m.lm.frac, flops * m.lm.frac, (k_level_dia<VT, XT, K, NR, 7>),
+                             grid_for(n, 256), 256, 0, dm, dinv, b, xin, agg, xc, out);
+            else
+                MDS_LAUNCH_F(c, cls, bytes * m.lm.frac, flops * m.lm.frac, (k_level_dia<VT, XT, K, NR, 5>),
+                             grid_for(n, 256), 256, 0, dm, dinv, b, xin, agg, xc, out);
+            return;
+        } else {
+            throw Error(MDS_ERR_INVALID, "stencil storage holds FP32 or FP64 values only");
+        }
     }
     bytes *= m.lm.frac;  // rows of finished batch instances are skipped
     flops *= m.lm.frac;
