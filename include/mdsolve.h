@@ -71,7 +71,10 @@ typedef struct {
 
 /* Create a context on CUDA device `device` that enqueues on `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream).  `alloc` may be NULL
- * for stream-ordered cudaMallocAsync/cudaFreeAsync.  The allocator struct is
+ * for stream-ordered allocation from a memory pool the context owns: blocks
+ * freed by one set-up or solve stay mapped in that pool for the next one
+ * (the pool holds the largest working set the context has used), and
+ * mds_destroy returns the pool to the driver.  The allocator struct is
  * copied; its callbacks must stay valid for the context's lifetime.  The
  * environment variable MDS_PDL=0 makes the context launch its kernels in
  * plain stream order, without programmatic dependent launch (for diagnosis;

@@ -54,13 +54,23 @@ void *Ctx::raw_alloc(size_t n) {
         p = alloc.alloc(n, alloc.user);
         if (!p) throw Error(MDS_ERR_OOM, "allocator returned NULL for " + std::to_string(n) + " bytes");
     } else {
-        cudaError_t e = cudaMallocAsync(&p, n, stream);
+        cudaError_t e = cudaMallocFromPoolAsync(&p, n, pool, stream);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            throw Error(MDS_ERR_OOM, "cudaMallocAsync(" + std::to_string(n) + "): " + cudaGetErrorString(e));
+            throw Error(MDS_ERR_OOM, "cudaMallocFromPoolAsync(" + std::to_string(n) + "): " + cudaGetErrorString(e));
         }
     }
     return p;
+}
+
+int resident_blocks(Ctx &c, const void *kern, int block) {
+    auto it = c.resident.find(kern);
+    if (it != c.resident.end()) return it->second;
+    int per = 0;
+    MDS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, block, 0));
+    const int total = (per > 0 ? per : 1) * (c.num_sms > 0 ? c.num_sms : 1);
+    c.resident[kern] = total;
+    return total;
 }
 
 void Ctx::raw_free(void *p) {
@@ -223,7 +233,16 @@ int mds_create(mds_ctx *out, int device, void *stream, const mds_allocator *allo
         if (alloc && alloc->alloc && alloc->free) {
             c->alloc = *alloc;
             c->custom_alloc = true;
+        } else {
+            cudaMemPoolProps pp{};
+            pp.allocType = cudaMemAllocationTypePinned;
+            pp.location.type = cudaMemLocationTypeDevice;
+            pp.location.id = device;
+            MDS_CUDA(cudaMemPoolCreate(&c->pool, &pp));
+            uint64_t keep = UINT64_MAX;
+            MDS_CUDA(cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep));
         }
+        MDS_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
         MDS_CUDA(cudaMalloc(&c->d_err, sizeof(int)));
         MDS_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
         MDS_CUDA(cudaMallocHost(&c->h_pin, Ctx::PIN_BYTES));
@@ -234,6 +253,7 @@ int mds_create(mds_ctx *out, int device, void *stream, const mds_allocator *allo
         int code = e.code;
         if (c->d_err) cudaFree(c->d_err);
         if (c->h_pin) cudaFreeHost(c->h_pin);
+        if (c->pool) cudaMemPoolDestroy(c->pool);
         delete h;
         return code;
     }
@@ -256,6 +276,10 @@ static void ctx_release(mds_ctx ctx) {
     if (c.side_stream) cudaStreamDestroy(c.side_stream);
     if (c.ev_fork) cudaEventDestroy(c.ev_fork);
     if (c.ev_join) cudaEventDestroy(c.ev_join);
+    if (c.pool) {
+        cudaStreamSynchronize(c.stream);
+        cudaMemPoolDestroy(c.pool);
+    }
     delete ctx;
 }
 

@@ -12,6 +12,7 @@
 #include <thread>
 #include <tuple>
 #include <utility>
+#include <unordered_map>
 #include <vector>
 
 #include "mdsolve.h"
@@ -110,6 +111,10 @@ struct KTimerRec {
     cudaEvent_t e0, e1;
 };
 
+// FP64 levels up to this many rows run the fused L1-Jacobi forms (latency
+// rather than the FP64 units bounds them); larger ones keep y stored.
+constexpr int64_t FUSE_FP64_ROWS = 65536;
+
 // Rows of a packed batch whose instance is still iterating.  The batched
 // solve's kernels skip every thread block whose rows all belong to finished
 // instances: the system is block diagonal, so no live row reads those rows.
@@ -182,6 +187,12 @@ struct Ctx {
     cudaStream_t stream = nullptr;
     mds_allocator alloc{};
     bool custom_alloc = false;
+    // the context's own stream-ordered pool (no custom allocator): freed
+    // blocks stay mapped in it for the next set-up or solve, instead of going
+    // back to the driver at the next synchronization; released by mds_destroy
+    cudaMemPool_t pool = nullptr;
+    int num_sms = 0;
+    std::unordered_map<const void *, int> resident;  // kernel -> blocks of 256 threads the device holds at once
     std::string last_error;
     int *d_err = nullptr;      // device error word
     void *h_pin = nullptr;     // pinned host scratch (PIN_BYTES)
@@ -348,6 +359,16 @@ inline unsigned grid_for(int64_t n, int block) {
     int64_t g = (n + block - 1) / block;
     if (g < 1) g = 1;
     return (unsigned)g;
+}
+
+// Grid of a grid-stride launch over nvb blocks of work: at most as many
+// blocks as the device holds at once, so that every block starts right away
+// and none queues behind a long-running one (cached per kernel).
+int resident_blocks(Ctx &c, const void *kern, int block);
+template <class... KArgs> unsigned stride_grid(Ctx &c, void (*kern)(KArgs...), int block, int64_t nvb) {
+    const int64_t cap = resident_blocks(c, (const void *)kern, block);
+    int64_t g = nvb < cap ? nvb : cap;
+    return (unsigned)(g < 1 ? 1 : g);
 }
 
 // Owned CSR (int32 row pointers and columns, FP64 values).

@@ -327,8 +327,9 @@ void dense_spd_inverse(Ctx &c, const mds_csr &A, const std::vector<int64_t> &seg
     Ainv = Buf(&c, sizeof(double) * (size_t)tot);
     const size_t tsmem = sizeof(double) * (size_t)nmax * INV_PAD;
     if (tsmem <= 200 * 1024) {
-        if (tsmem > 48 * 1024)
-            MDS_CUDA(cudaFuncSetAttribute(k_chol_inv_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
+        // with the kernel's static panel tile, even a dynamic size under
+        // 48 KB can take the block past the default limit: always opt in
+        MDS_CUDA(cudaFuncSetAttribute(k_chol_inv_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
         MDS_LAUNCH(c, KC_NONE, 0, k_chol_inv_tiles, (unsigned)db.ntiles, 256, tsmem, D.as<double>(), B,
                    db.tiles.as<int2>(), Ainv.as<double>());
         return;

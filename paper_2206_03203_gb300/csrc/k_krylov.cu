@@ -969,7 +969,8 @@ __global__ void __launch_bounds__(RED_BLOCK) k_bdot(const Chunk *__restrict__ ch
     mds_pdl_entry();
     __shared__ double ws[RED_BLOCK / 32][NR];
     // the nq blocks of one chunk are adjacent in launch order, so they run
-    // together and the chunk of W is read from DRAM once
+    // together and the chunk of W is read from DRAM once (a grid-stride loop
+    // over a resident grid loses this order, measured slower)
     const int nqb = nq > 0 ? nq : 1;
     const int64_t chunk = blockIdx.x / nqb;
     const int q = (int)(blockIdx.x % nqb);
@@ -1037,9 +1038,12 @@ __global__ void __launch_bounds__(RED_BLOCK) k_bmaxpy(const Chunk *__restrict__ 
         if (q1 == 0) return;
         nq = min(nq, q1);
     }
+    // the coefficients carry the sign, so W(i, c) itself starts each row's
+    // chain of fused multiply-adds
     for (int t = threadIdx.x; t < NR * 32; t += blockDim.x) {
         int c = t / 32, q = t % 32;
-        cs[c][q] = q < nq ? coef[((int64_t)k.inst * NR + c) * 32 + q] : 0.0;
+        const double a = q < nq ? coef[((int64_t)k.inst * NR + c) * 32 + q] : 0.0;
+        cs[c][q] = SIGN > 0 ? a : -a;
     }
     __syncthreads();
     double nrm[NR];
@@ -1048,17 +1052,16 @@ __global__ void __launch_bounds__(RED_BLOCK) k_bmaxpy(const Chunk *__restrict__ 
     for (int64_t i = k.b + threadIdx.x; i < k.e; i += blockDim.x) {
         double s[NR];
 #pragma unroll
-        for (int c = 0; c < NR; c++) s[c] = 0.0;
+        for (int c = 0; c < NR; c++) s[c] = W[i * NR + c];
         for (int q = 0; q < nq; q++) {
             const double *v = V + (int64_t)q * ldq + i * NR;
 #pragma unroll
-            for (int c = 0; c < NR; c++) s[c] += cs[c][q] * v[c];
+            for (int c = 0; c < NR; c++) s[c] = fma(cs[c][q], v[c], s[c]);
         }
 #pragma unroll
         for (int c = 0; c < NR; c++) {
-            double x = SIGN > 0 ? W[i * NR + c] + s[c] : W[i * NR + c] - s[c];
-            W[i * NR + c] = x;
-            nrm[c] += x * x;
+            W[i * NR + c] = s[c];
+            nrm[c] += s[c] * s[c];
         }
     }
     if (partial) {

@@ -19,8 +19,8 @@ namespace mds {
 // per vector type (k_vcycle_f64.cu, k_vcycle_f32.cu)
 void vcycle_run_f64(Ctx &c, Hierarchy &h, const double *b, double *x, int nr);
 void vcycle_run_f32(Ctx &c, Hierarchy &h, const float *b, float *x, int nr);
-float time_level_f64(Ctx &c, const Level &L, int nr);
-float time_level_f32(Ctx &c, const Level &L, int nr);
+float time_level_f64(Ctx &c, const Level &L, int nr, const void *xc);
+float time_level_f32(Ctx &c, const Level &L, int nr, const void *xc);
 
 // The level work vectors hold up to nr_cap interleaved columns.
 void hierarchy_reserve(Ctx &c, Hierarchy &h, int nr) {
@@ -297,13 +297,15 @@ static int default_g(const Level &L) {
 }
 
 // Autotuner: time CSR with G/2, G, 2G lanes per row and SELL-C-sigma for a
-// few (C, sigma) pairs on this level, keep the fastest.  Choices are cached in
-// the context by (rows, nonzeros, storage type).
-template <class XT> static void autotune_level(Ctx &c, Level &L, int nr) {
-    auto time_level = [nr](Ctx &cc, const Level &LL) {
-        return std::is_same<XT, double>::value ? time_level_f64(cc, LL, nr) : time_level_f32(cc, LL, nr);
+// few (C, sigma) pairs on this level, keep the fastest.  xc (the coarser
+// level's x) != NULL: the level runs the fused pair (residual, post-smoothing)
+// and both are timed; otherwise the stored residual.  Choices are cached in
+// the context by (rows, nonzeros, storage type, columns, timed forms).
+template <class XT> static void autotune_level(Ctx &c, Level &L, int nr, void *xc, int64_t nc) {
+    auto time_level = [nr, xc](Ctx &cc, const Level &LL) {
+        return std::is_same<XT, double>::value ? time_level_f64(cc, LL, nr, xc) : time_level_f32(cc, LL, nr, xc);
     };
-    auto key = std::make_tuple(L.A.nrow, L.A.nnz, (L.vt * 2 + (L.dia_D > 0 ? 1 : 0)) * 16 + nr);
+    auto key = std::make_tuple(L.A.nrow, L.A.nnz, ((L.vt * 2 + (L.dia_D > 0 ? 1 : 0)) * 2 + (xc ? 1 : 0)) * 16 + nr);
     auto it = c.tune_cache.find(key);
     if (it != c.tune_cache.end()) {
         const TuneChoice &t = it->second;
@@ -320,6 +322,7 @@ template <class XT> static void autotune_level(Ctx &c, Level &L, int nr) {
     size_t vb = sizeof(XT) * (size_t)L.A.nrow * (size_t)nr;
     MDS_CUDA(cudaMemsetAsync(L.b.p, 0, vb, c.stream));
     MDS_CUDA(cudaMemsetAsync(L.x.p, 0, vb, c.stream));
+    if (xc) MDS_CUDA(cudaMemsetAsync(xc, 0, sizeof(XT) * (size_t)nc * (size_t)nr, c.stream));
     TuneChoice best{FMT_CSR, default_g(L), 32, 1};
     float tbest = 1e30f;
     int g0 = default_g(L);
@@ -409,10 +412,15 @@ void level_storage(Ctx &c, Hierarchy &h, const mds_setup_opts &o) {
         } else if (o.format == MDS_FORMAT_SELL) {
             build_sell_vt(c, L, o.sell_c, o.sell_sigma);
         } else if (o.format == MDS_FORMAT_AUTO && n >= 20000) {
+            // the forms the V-cycle runs on this level (fused pair or stored residual)
+            const bool fused = h.smoother == MDS_SMOOTHER_L1JACOBI && h.sweeps == 1 && !L.smoothed &&
+                               (h.prec != 64 || n <= FUSE_FP64_ROWS) && L.has_coarse && l + 1 < h.lv.size();
+            void *xc = fused ? h.lv[l + 1].x.p : nullptr;
+            const int64_t nc = fused ? h.lv[l + 1].A.nrow : 0;
             if (h.prec == 64)
-                autotune_level<double>(c, L, h.nr_cap);
+                autotune_level<double>(c, L, h.nr_cap, xc, nc);
             else
-                autotune_level<float>(c, L, h.nr_cap);
+                autotune_level<float>(c, L, h.nr_cap, xc, nc);
         }
         if (L.fmt != FMT_DIA) drop_dia(L);
     }

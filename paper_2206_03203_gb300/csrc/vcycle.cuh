@@ -77,6 +77,22 @@ template <class XT, int NR> __device__ __forceinline__ void stv(XT *p, int64_t j
 
 enum { VK_RESID0 = 0, VK_POST = 1, VK_RESID = 2, VK_SMOOTH = 3 };
 
+// Explicitly rounded arithmetic of the level kernels: every storage (CSR,
+// SELL, stencil planes), the fused and the stored-y forms and the coarse-tail
+// kernel round each product, sum and difference at the same points whatever
+// the compiler would contract, so that they agree bit for bit.  y_j = D1_j b_j
+// [+ x_c] is two roundings (as when y is stored), the row sum one fused
+// multiply-add per entry, x = y + D1 (b - s) a difference and a fused
+// multiply-add.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Neighbour values each kernel multiplies by a_ij (NR columns at once).
 template <class XT, int NR, int K> struct Nb {
     const XT *dinv, *b, *xin, *xc;
@@ -87,13 +103,13 @@ template <class XT, int NR, int K> struct Nb {
             XT d = __ldg(dinv + j);
             Vec<XT, NR> bj = ldv<XT, NR>(b, j);
 #pragma unroll
-            for (int c = 0; c < NR; c++) y.v[c] = d * bj.v[c];
+            for (int c = 0; c < NR; c++) y.v[c] = mul_rn(d, bj.v[c]);
             if (K == VK_POST && agg) {
                 int32_t a = __ldg(agg + j);
                 if (a >= 0) {
                     Vec<XT, NR> xa = ldv<XT, NR>(xc, a);
 #pragma unroll
-                    for (int c = 0; c < NR; c++) y.v[c] += xa.v[c];
+                    for (int c = 0; c < NR; c++) y.v[c] = add_rn(y.v[c], xa.v[c]);
                 }
             }
         } else {
@@ -106,11 +122,11 @@ template <class XT, int NR, int K> struct Nb {
         Vec<XT, NR> y;
         Vec<XT, NR> bj = ldv<XT, NR>(b, j);
 #pragma unroll
-        for (int c = 0; c < NR; c++) y.v[c] = d * bj.v[c];
+        for (int c = 0; c < NR; c++) y.v[c] = mul_rn(d, bj.v[c]);
         if (K == VK_POST && a >= 0) {
             Vec<XT, NR> xa = ldv<XT, NR>(xc, a);
 #pragma unroll
-            for (int c = 0; c < NR; c++) y.v[c] += xa.v[c];
+            for (int c = 0; c < NR; c++) y.v[c] = add_rn(y.v[c], xa.v[c]);
         }
         return y;
     }
@@ -124,8 +140,8 @@ template <int G, class XT> __device__ __forceinline__ XT lane_reduce(XT s) {
     return s;
 }
 
-template <int G> __device__ __forceinline__ void row_of(int64_t &row, int &lane) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+template <int G> __device__ __forceinline__ void row_of(int64_t vb, int64_t &row, int &lane) {
+    int64_t t = vb * blockDim.x + threadIdx.x;
     if constexpr (G > 0) {
         row = t / G;
         lane = (int)(t % G);
@@ -153,17 +169,18 @@ constexpr int PREFETCH = 8;
 // about one wave of resident blocks; larger launches (PF = 0) keep registers
 // low for occupancy instead.
 template <int G, class VT, class XT, int K, int NR, int PF>
-__global__ void __launch_bounds__(256) k_level(LvlMat<VT> A, const XT *__restrict__ dinv, const XT *__restrict__ b,
-                                               const XT *__restrict__ xin, const int32_t *__restrict__ agg,
-                                               const XT *__restrict__ xc, XT *__restrict__ out) {
+__device__ __forceinline__ void level_block(int64_t vb, const LvlMat<VT> &A, const XT *__restrict__ dinv,
+                                            const XT *__restrict__ b, const XT *__restrict__ xin,
+                                            const int32_t *__restrict__ agg, const XT *__restrict__ xc,
+                                            XT *__restrict__ out) {
     {
         // this block's rows (whole sorting windows for permuted SELL)
         int64_t r0, r1;
         if constexpr (G > 0) {
-            r0 = (int64_t)blockIdx.x * (256 / G);
+            r0 = vb * (256 / G);
             r1 = r0 + 256 / G;
         } else {
-            r0 = (int64_t)blockIdx.x * 256;
+            r0 = vb * 256;
             r1 = r0 + 256;
             if (A.perm) {
                 r0 = r0 / A.sigma * A.sigma;
@@ -174,7 +191,7 @@ __global__ void __launch_bounds__(256) k_level(LvlMat<VT> A, const XT *__restric
     }
     int64_t row;
     int lane;
-    row_of<G>(row, lane);
+    row_of<G>(vb, row, lane);
     const bool live = row < A.n;
     // this lane's entries: index i0 + k * st for k < cnt
     const int32_t *cp = G > 0 ? A.ci : A.sc;
@@ -249,43 +266,53 @@ __global__ void __launch_bounds__(256) k_level(LvlMat<VT> A, const XT *__restric
             else
                 y = f(pj[k]);
 #pragma unroll
-            for (int c = 0; c < NR; c++) s[c] += a * y.v[c];
+            for (int c = 0; c < NR; c++) s[c] = fma_rn(a, y.v[c], s[c]);
         }
 #pragma unroll 4
     for (int k = PF; k < cnt; k++) {
         XT a = cvt<XT>(ld_stream(A.v + i0 + (int64_t)k * st));
         Vec<XT, NR> y = f(ld_stream(cp + i0 + (int64_t)k * st));
 #pragma unroll
-        for (int c = 0; c < NR; c++) s[c] += a * y.v[c];
+        for (int c = 0; c < NR; c++) s[c] = fma_rn(a, y.v[c], s[c]);
     }
 #pragma unroll
     for (int c = 0; c < NR; c++) s[c] = lane_reduce<G, XT>(s[c]);
     if (live && lane == 0) {
         if (A.rscale) {
 #pragma unroll
-            for (int c = 0; c < NR; c++) s[c] *= sc;
+            for (int c = 0; c < NR; c++) s[c] = mul_rn(s[c], sc);
         }
         Vec<XT, NR> res;
         if (K == VK_RESID0 || K == VK_RESID) {
 #pragma unroll
-            for (int c = 0; c < NR; c++) res.v[c] = bo.v[c] - s[c];
+            for (int c = 0; c < NR; c++) res.v[c] = sub_rn(bo.v[c], s[c]);
         } else {
             Vec<XT, NR> y;
             if (K == VK_POST) {
 #pragma unroll
-                for (int c = 0; c < NR; c++) y.v[c] = d * bo.v[c];
+                for (int c = 0; c < NR; c++) y.v[c] = mul_rn(d, bo.v[c]);
                 if (ag >= 0) {
 #pragma unroll
-                    for (int c = 0; c < NR; c++) y.v[c] += yo.v[c];
+                    for (int c = 0; c < NR; c++) y.v[c] = add_rn(y.v[c], yo.v[c]);
                 }
             } else {
                 y = yo;
             }
 #pragma unroll
-            for (int c = 0; c < NR; c++) res.v[c] = y.v[c] + d * (bo.v[c] - s[c]);
+            for (int c = 0; c < NR; c++) res.v[c] = fma_rn(d, sub_rn(bo.v[c], s[c]), y.v[c]);
         }
         stv<XT, NR>(out, o, res);
     }
+}
+
+// One launch covers `nvb` blocks of rows (virtual blocks): a grid of at most
+// the resident blocks strides over them, so that the blocks of finished batch
+// instances cost a flag check each instead of a block launch.
+template <int G, class VT, class XT, int K, int NR, int PF>
+__global__ void __launch_bounds__(256) k_level(LvlMat<VT> A, const XT *__restrict__ dinv, const XT *__restrict__ b,
+                                               const XT *__restrict__ xin, const int32_t *__restrict__ agg,
+                                               const XT *__restrict__ xc, XT *__restrict__ out, int64_t nvb) {
+    for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) level_block<G, VT, XT, K, NR, PF>(vb, A, dinv, b, xin, agg, xc, out);
 }
 
 // ---- stencil storage (FMT_DIA): the finest level of S~ of a primal system on
@@ -318,10 +345,11 @@ template <class XT, int K, int NR> constexpr int dia_min_blocks() {
 }
 
 template <class VT, class XT, int K, int NR, int D>
-__global__ void __launch_bounds__(256, dia_min_blocks<XT, K, NR>())
-    k_level_dia(DiaMat<VT> A, const XT *__restrict__ dinv, const XT *__restrict__ b, const XT *__restrict__ xin,
-                const int32_t *__restrict__ agg, const XT *__restrict__ xc, XT *__restrict__ out) {
-    const int64_t r0 = (int64_t)blockIdx.x * 256, r1 = r0 + 256 < A.n ? r0 + 256 : A.n;
+__device__ __forceinline__ void level_dia_block(int64_t vb, const DiaMat<VT> &A, const XT *__restrict__ dinv,
+                                                const XT *__restrict__ b, const XT *__restrict__ xin,
+                                                const int32_t *__restrict__ agg, const XT *__restrict__ xc,
+                                                XT *__restrict__ out) {
+    const int64_t r0 = vb * 256, r1 = r0 + 256 < A.n ? r0 + 256 : A.n;
     if (!block_rows_live(A.lm, r0, r1)) return;
     // level rows fit in 32 bits (column indices are 32-bit on every level)
     const int row = (int)r0 + (int)threadIdx.x;
@@ -401,28 +429,36 @@ __global__ void __launch_bounds__(256, dia_min_blocks<XT, K, NR>())
             else
                 y = f(pj[d]);
 #pragma unroll
-            for (int c = 0; c < NR; c++) s[c] += a * y.v[c];
+            for (int c = 0; c < NR; c++) s[c] = fma_rn(a, y.v[c], s[c]);
         }
     Vec<XT, NR> res;
     if (K == VK_RESID0 || K == VK_RESID) {
 #pragma unroll
-        for (int c = 0; c < NR; c++) res.v[c] = bo.v[c] - s[c];
+        for (int c = 0; c < NR; c++) res.v[c] = sub_rn(bo.v[c], s[c]);
     } else {
         Vec<XT, NR> y;
         if (K == VK_POST) {
 #pragma unroll
-            for (int c = 0; c < NR; c++) y.v[c] = dd * bo.v[c];
+            for (int c = 0; c < NR; c++) y.v[c] = mul_rn(dd, bo.v[c]);
             if (ag >= 0) {
 #pragma unroll
-                for (int c = 0; c < NR; c++) y.v[c] += yo.v[c];
+                for (int c = 0; c < NR; c++) y.v[c] = add_rn(y.v[c], yo.v[c]);
             }
         } else {
             y = yo;
         }
 #pragma unroll
-        for (int c = 0; c < NR; c++) res.v[c] = y.v[c] + dd * (bo.v[c] - s[c]);
+        for (int c = 0; c < NR; c++) res.v[c] = fma_rn(dd, sub_rn(bo.v[c], s[c]), y.v[c]);
     }
     stv<XT, NR>(out, row, res);
+}
+
+// grid-stride over the level's 256-row blocks (as k_level)
+template <class VT, class XT, int K, int NR, int D>
+__global__ void __launch_bounds__(256, dia_min_blocks<XT, K, NR>())
+    k_level_dia(DiaMat<VT> A, const XT *__restrict__ dinv, const XT *__restrict__ b, const XT *__restrict__ xin,
+                const int32_t *__restrict__ agg, const XT *__restrict__ xc, XT *__restrict__ out, int64_t nvb) {
+    for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) level_dia_block<VT, XT, K, NR, D>(vb, A, dinv, b, xin, agg, xc, out);
 }
 
 // ---- elementwise kernels (NR interleaved columns; row of entry e = e / NR).
@@ -439,8 +475,8 @@ __global__ void k_vc_x0(int64_t n, const XT *__restrict__ dinv, const XT *__rest
     const XT d0 = e < r1 * NR ? dinv[e / NR] : (XT)0;
     mds_pdl_wait();
     mds_pdl_trigger();
-    if (e < r1 * NR) x[e] = d0 * b[e];
-    for (e += blockDim.x; e < r1 * NR; e += blockDim.x) x[e] = dinv[e / NR] * b[e];
+    if (e < r1 * NR) x[e] = mul_rn(d0, b[e]);
+    for (e += blockDim.x; e < r1 * NR; e += blockDim.x) x[e] = mul_rn(dinv[e / NR], b[e]);
 }
 
 // y_(i,c) += x_c(agg_i, c)
@@ -453,10 +489,10 @@ __global__ void k_vc_prolong(int64_t n, const int32_t *__restrict__ agg, const X
     const int32_t a0 = e < r1 * NR ? agg[e / NR] : -1;
     mds_pdl_wait();
     mds_pdl_trigger();
-    if (a0 >= 0) y[e] += xc[(int64_t)a0 * NR + e % NR];
+    if (a0 >= 0) y[e] = add_rn(y[e], xc[(int64_t)a0 * NR + e % NR]);
     for (e += blockDim.x; e < r1 * NR; e += blockDim.x) {
         int32_t a = agg[e / NR];
-        if (a >= 0) y[e] += xc[(int64_t)a * NR + e % NR];
+        if (a >= 0) y[e] = add_rn(y[e], xc[(int64_t)a * NR + e % NR]);
     }
 }
 
@@ -490,13 +526,14 @@ __global__ void k_cheb_next(int64_t n, const XT *__restrict__ dinv, const XT *__
 // loaded before the dependency wait.
 constexpr int RPRE = 8;
 template <class XT, int NR>
-__global__ void k_vc_restrict(int64_t nc, const int32_t *__restrict__ off, const int32_t *__restrict__ mem,
-                              const XT *__restrict__ r, XT *__restrict__ bc, LiveMap lm) {
+__device__ __forceinline__ void restrict_block(int64_t vb, int64_t nc, const int32_t *__restrict__ off,
+                                               const int32_t *__restrict__ mem, const XT *__restrict__ r,
+                                               XT *__restrict__ bc, const LiveMap &lm) {
     {
-        const int64_t r0 = (int64_t)blockIdx.x * blockDim.x, r1 = r0 + blockDim.x < nc ? r0 + blockDim.x : nc;
+        const int64_t r0 = vb * blockDim.x, r1 = r0 + blockDim.x < nc ? r0 + blockDim.x : nc;
         if (!block_rows_live(lm, r0, r1)) return;
     }
-    int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t I = vb * blockDim.x + threadIdx.x;
     int32_t q0 = 0, q1 = 0;
     if (I < nc) {
         q0 = off[I];
@@ -528,6 +565,14 @@ __global__ void k_vc_restrict(int64_t nc, const int32_t *__restrict__ off, const
     stv<XT, NR>(bc, I, s);
 }
 
+// grid-stride over the aggregates' 256-row blocks (as k_level)
+template <class XT, int NR>
+__global__ void __launch_bounds__(256) k_vc_restrict(int64_t nc, const int32_t *__restrict__ off,
+                                                     const int32_t *__restrict__ mem, const XT *__restrict__ r,
+                                                     XT *__restrict__ bc, LiveMap lm, int64_t nvb) {
+    for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) restrict_block<XT, NR>(vb, nc, off, mem, r, bc, lm);
+}
+
 // Smoothed aggregation transfers (NR columns): b_c = R r and y += P x_c, one
 // thread per output row, entries in CSR order.
 template <class XT, int NR>
@@ -543,7 +588,7 @@ __global__ void k_sa_restrict(int64_t nc, const int32_t *__restrict__ rp, const 
         XT a = v[p];
         Vec<XT, NR> x = ldv<XT, NR>(r, ci[p]);
 #pragma unroll
-        for (int c = 0; c < NR; c++) s.v[c] += a * x.v[c];
+        for (int c = 0; c < NR; c++) s.v[c] = fma_rn(a, x.v[c], s.v[c]);
     }
     stv<XT, NR>(bc, I, s);
 }
@@ -561,10 +606,10 @@ __global__ void k_sa_prolong(int64_t n, const int32_t *__restrict__ rp, const in
         XT a = v[p];
         Vec<XT, NR> x = ldv<XT, NR>(xc, ci[p]);
 #pragma unroll
-        for (int c = 0; c < NR; c++) t.v[c] += a * x.v[c];
+        for (int c = 0; c < NR; c++) t.v[c] = fma_rn(a, x.v[c], t.v[c]);
     }
 #pragma unroll
-    for (int c = 0; c < NR; c++) s.v[c] += t.v[c];
+    for (int c = 0; c < NR; c++) s.v[c] = add_rn(s.v[c], t.v[c]);
     stv<XT, NR>(y, i, s);
 }
 
@@ -612,10 +657,12 @@ static void launch_level_pf(Ctx &c, const Level &L, const XT *dinv, const XT *b,
             bytes = bytes - vb - 4.0 * (n + 1) + (double)L.dia_D * sizeof(VT) * n;
             if (L.dia_D == 7)
                 MDS_LAUNCH_F(c, cls, bytes * m.lm.frac, flops * m.lm.frac, (k_level_dia<VT, XT, K, NR, 7>),
-                             grid_for(n, 256), 256, 0, dm, dinv, b, xin, agg, xc, out);
+                             stride_grid(c, k_level_dia<VT, XT, K, NR, 7>, 256, grid_for(n, 256)), 256, 0, dm, dinv,
+                             b, xin, agg, xc, out, (int64_t)grid_for(n, 256));
             else
                 MDS_LAUNCH_F(c, cls, bytes * m.lm.frac, flops * m.lm.frac, (k_level_dia<VT, XT, K, NR, 5>),
-                             grid_for(n, 256), 256, 0, dm, dinv, b, xin, agg, xc, out);
+                             stride_grid(c, k_level_dia<VT, XT, K, NR, 5>, 256, grid_for(n, 256)), 256, 0, dm, dinv,
+                             b, xin, agg, xc, out, (int64_t)grid_for(n, 256));
             return;
         } else {
             throw Error(MDS_ERR_INVALID, "stencil storage holds FP32 or FP64 values only");
@@ -625,34 +672,42 @@ static void launch_level_pf(Ctx &c, const Level &L, const XT *dinv, const XT *b,
     flops *= m.lm.frac;
     if (L.fmt == FMT_SELL) {
         int64_t rows = L.sell_nslice * L.sell_c;
-        MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<0, VT, XT, K, NR, PF>), grid_for(rows, 256), 256, 0, m, dinv, b, xin,
-                     agg, xc, out);
+        const int64_t nvb = grid_for(rows, 256);
+        MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<0, VT, XT, K, NR, PF>),
+                     stride_grid(c, k_level<0, VT, XT, K, NR, PF>, 256, nvb), 256, 0, m, dinv, b, xin, agg, xc, out,
+                     nvb);
         return;
     }
     switch (L.G) {
         case 1:
-            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<1, VT, XT, K, NR, PF>), grid_for(n, 256), 256, 0, m, dinv, b, xin,
-                         agg, xc, out);
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<1, VT, XT, K, NR, PF>),
+                         stride_grid(c, k_level<1, VT, XT, K, NR, PF>, 256, grid_for(n, 256)), 256, 0, m,
+                         dinv, b, xin, agg, xc, out, (int64_t)grid_for(n, 256));
             break;
         case 2:
-            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<2, VT, XT, K, NR, PF>), grid_for(n * 2, 256), 256, 0, m, dinv, b,
-                         xin, agg, xc, out);
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<2, VT, XT, K, NR, PF>),
+                         stride_grid(c, k_level<2, VT, XT, K, NR, PF>, 256, grid_for(n * 2, 256)), 256, 0, m,
+                         dinv, b, xin, agg, xc, out, (int64_t)grid_for(n * 2, 256));
             break;
         case 4:
-            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<4, VT, XT, K, NR, PF>), grid_for(n * 4, 256), 256, 0, m, dinv, b,
-                         xin, agg, xc, out);
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<4, VT, XT, K, NR, PF>),
+                         stride_grid(c, k_level<4, VT, XT, K, NR, PF>, 256, grid_for(n * 4, 256)), 256, 0, m,
+                         dinv, b, xin, agg, xc, out, (int64_t)grid_for(n * 4, 256));
             break;
         case 8:
-            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<8, VT, XT, K, NR, PF>), grid_for(n * 8, 256), 256, 0, m, dinv, b,
-                         xin, agg, xc, out);
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<8, VT, XT, K, NR, PF>),
+                         stride_grid(c, k_level<8, VT, XT, K, NR, PF>, 256, grid_for(n * 8, 256)), 256, 0, m,
+                         dinv, b, xin, agg, xc, out, (int64_t)grid_for(n * 8, 256));
             break;
         case 16:
-            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<16, VT, XT, K, NR, PF>), grid_for(n * 16, 256), 256, 0, m, dinv, b,
-                         xin, agg, xc, out);
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<16, VT, XT, K, NR, PF>),
+                         stride_grid(c, k_level<16, VT, XT, K, NR, PF>, 256, grid_for(n * 16, 256)), 256, 0, m,
+                         dinv, b, xin, agg, xc, out, (int64_t)grid_for(n * 16, 256));
             break;
         default:
-            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<32, VT, XT, K, NR, PF>), grid_for(n * 32, 256), 256, 0, m, dinv, b,
-                         xin, agg, xc, out);
+            MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<32, VT, XT, K, NR, PF>),
+                         stride_grid(c, k_level<32, VT, XT, K, NR, PF>, 256, grid_for(n * 32, 256)), 256, 0, m,
+                         dinv, b, xin, agg, xc, out, (int64_t)grid_for(n * 32, 256));
             break;
     }
 }
@@ -915,9 +970,9 @@ __device__ __forceinline__ void tail_run(const TailArgs<XT> &a, int kind, int li
                 if (q.p + k * G < q.p1) {
 #pragma unroll
                     for (int c = 0; c < NR; c++) {
-                        XT yj = q.dj[k] * __ldcg(L.b + (int64_t)q.j[k] * NR + c);
-                        if (kind == TP_POST && q.aj[k] >= 0) yj += __ldcg(xc + (int64_t)q.aj[k] * NR + c);
-                        s[c] += q.v[k] * yj;
+                        XT yj = mul_rn(q.dj[k], __ldcg(L.b + (int64_t)q.j[k] * NR + c));
+                        if (kind == TP_POST && q.aj[k] >= 0) yj = add_rn(yj, __ldcg(xc + (int64_t)q.aj[k] * NR + c));
+                        s[c] = fma_rn(q.v[k], yj, s[c]);
                     }
                 }
             }
@@ -928,9 +983,9 @@ __device__ __forceinline__ void tail_run(const TailArgs<XT> &a, int kind, int li
                 int32_t aj = xc ? L.agg[j] : -1;
 #pragma unroll
                 for (int c = 0; c < NR; c++) {
-                    XT yj = dj * __ldcg(L.b + (int64_t)j * NR + c);
-                    if (aj >= 0) yj += __ldcg(xc + (int64_t)aj * NR + c);
-                    s[c] += av * yj;
+                    XT yj = mul_rn(dj, __ldcg(L.b + (int64_t)j * NR + c));
+                    if (aj >= 0) yj = add_rn(yj, __ldcg(xc + (int64_t)aj * NR + c));
+                    s[c] = fma_rn(av, yj, s[c]);
                 }
             }
         }
@@ -942,13 +997,13 @@ __device__ __forceinline__ void tail_run(const TailArgs<XT> &a, int kind, int li
 #pragma unroll
             for (int c = 0; c < NR; c++) {
                 XT bi = __ldcg(L.b + i * NR + c);
-                XT sv = L.rscale ? s[c] * q.sc : s[c];
+                XT sv = L.rscale ? mul_rn(s[c], q.sc) : s[c];
                 if (kind == TP_RES) {
-                    __stcg(L.r + i * NR + c, bi - sv);
+                    __stcg(L.r + i * NR + c, sub_rn(bi, sv));
                 } else {
-                    XT yi = q.di * bi;
-                    if (q.ai >= 0) yi += __ldcg(xc + (int64_t)q.ai * NR + c);
-                    __stcg(L.x + i * NR + c, yi + q.di * (bi - sv));
+                    XT yi = mul_rn(q.di, bi);
+                    if (q.ai >= 0) yi = add_rn(yi, __ldcg(xc + (int64_t)q.ai * NR + c));
+                    __stcg(L.x + i * NR + c, fma_rn(q.di, sub_rn(bi, sv), yi));
                 }
             }
         }
@@ -1130,7 +1185,6 @@ static bool vcycle_tail(Ctx &c, Hierarchy &h, int l0, const XT *b, XT *x) {
     return true;
 }
 
-constexpr int64_t FUSE_FP64_ROWS = 65536;
 
 template <class XT, int NR>
 static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
@@ -1163,8 +1217,9 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
             Level &C = h.lv[l + 1];
             level_op<XT, VK_RESID0, NR>(c, L, b, nullptr, nullptr, nullptr, r, 0);
             MDS_LAUNCH(c, L.timed_level ? KC_VC_RESTRICT : KC_NONE, rbytes * level_live(c, L).frac,
-                       (k_vc_restrict<XT, NR>), grid_for(L.nc, 256), 256, 0, L.nc, L.mem_off.as<int32_t>(),
-                       L.mem.as<int32_t>(), r, C.b.as<XT>(), level_live(c, C));
+                       (k_vc_restrict<XT, NR>), stride_grid(c, k_vc_restrict<XT, NR>, 256, grid_for(L.nc, 256)),
+                       256, 0, L.nc, L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r, C.b.as<XT>(), level_live(c, C),
+                       (int64_t)grid_for(L.nc, 256));
             vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
             level_op<XT, VK_POST, NR>(c, L, b, nullptr, L.agg.as<int32_t>(), C.x.as<XT>(), x, L.nc);
         } else {
@@ -1189,8 +1244,9 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
         } else {
             level_op<XT, VK_RESID, NR>(c, L, b, y, nullptr, nullptr, r, 0);
             MDS_LAUNCH(c, L.timed_level ? KC_VC_RESTRICT : KC_NONE, rbytes * level_live(c, L).frac,
-                       (k_vc_restrict<XT, NR>), grid_for(L.nc, 256), 256, 0, L.nc, L.mem_off.as<int32_t>(),
-                       L.mem.as<int32_t>(), r, C.b.as<XT>(), level_live(c, C));
+                       (k_vc_restrict<XT, NR>), stride_grid(c, k_vc_restrict<XT, NR>, 256, grid_for(L.nc, 256)),
+                       256, 0, L.nc, L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r, C.b.as<XT>(), level_live(c, C),
+                       (int64_t)grid_for(L.nc, 256));
             vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
             MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n * NR, (k_vc_prolong<XT, NR>), ew_blocks(n), 256, 0, n,
                        L.agg.as<int32_t>(), C.x.as<XT>(), y, ew_rows(n), level_live(c, L));
@@ -1210,14 +1266,23 @@ static void vcycle_nr(Ctx &c, Hierarchy &h, const XT *b, XT *x, int nr) {
     }
 }
 
-template <class XT, int NR> static float time_level_nr(Ctx &c, const Level &L) {
+// xc == NULL: the stored-residual kernel; otherwise the pair of fused
+// kernels the V-cycle runs on a level with a coarser one (the residual with
+// y = D1^-1 b formed per neighbour, and the post-smoothing with y = D1^-1 b +
+// P x_c formed per neighbour, x_c = xc).
+template <class XT, int NR> static float time_level_nr(Ctx &c, const Level &L, const XT *xc) {
     cudaEvent_t e0, e1;
     MDS_CUDA(cudaEventCreate(&e0));
     MDS_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
     for (int rep = 0; rep < 4; rep++) {
         MDS_CUDA(cudaEventRecord(e0, c.stream));
-        level_op<XT, VK_RESID, NR>(c, L, L.b.as<XT>(), L.x.as<XT>(), nullptr, nullptr, L.r.as<XT>(), 0);
+        if (xc) {
+            level_op<XT, VK_RESID0, NR>(c, L, L.b.as<XT>(), nullptr, nullptr, nullptr, L.r.as<XT>(), 0);
+            level_op<XT, VK_POST, NR>(c, L, L.b.as<XT>(), nullptr, L.agg.as<int32_t>(), xc, L.x.as<XT>(), L.nc);
+        } else {
+            level_op<XT, VK_RESID, NR>(c, L, L.b.as<XT>(), L.x.as<XT>(), nullptr, nullptr, L.r.as<XT>(), 0);
+        }
         MDS_CUDA(cudaEventRecord(e1, c.stream));
         MDS_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -1229,14 +1294,15 @@ template <class XT, int NR> static float time_level_nr(Ctx &c, const Level &L) {
     return best;
 }
 
-// Time the stored-residual kernel on the level in its current storage with
-// nr interleaved columns (best of three after a warm-up launch).
-template <class XT> static float time_level(Ctx &c, const Level &L, int nr) {
+// Time the level's kernels in its current storage with nr interleaved
+// columns (best of three after a warm-up launch).
+template <class XT> static float time_level(Ctx &c, const Level &L, int nr, const void *xc) {
+    const XT *x = (const XT *)xc;
     switch (nr) {
-        case 8: return time_level_nr<XT, 8>(c, L);
-        case 4: return time_level_nr<XT, 4>(c, L);
-        case 2: return time_level_nr<XT, 2>(c, L);
-        default: return time_level_nr<XT, 1>(c, L);
+        case 8: return time_level_nr<XT, 8>(c, L, x);
+        case 4: return time_level_nr<XT, 4>(c, L, x);
+        case 2: return time_level_nr<XT, 2>(c, L, x);
+        default: return time_level_nr<XT, 1>(c, L, x);
     }
 }
 
