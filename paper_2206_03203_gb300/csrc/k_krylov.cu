@@ -1240,12 +1240,42 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
         MDS_CUDA(cudaMemcpyAsync(dil.p, ilist.data(), sizeof(int32_t) * ilist.size(), cudaMemcpyHostToDevice, c.stream));
     const Chunk *CHp = dch.as<Chunk>();
     const int32_t *IO = dioff.as<int32_t>(), *IL = dil.as<int32_t>();
+    // Finer chunks (2,048 rows) for the kernels whose block walks a chunk's
+    // rows for every basis vector (the Gram-Schmidt update, the x update, the
+    // scaling and the squared norms): once most instances have finished, the
+    // few live ones still spread over many blocks.
+    constexpr int64_t CHF = 2048;
+    std::vector<Chunk> fchunks;
+    std::vector<std::vector<int32_t>> fper(K);
+    auto fadd = [&](int64_t b, int64_t e, int k) {
+        for (int64_t s = b; s < e; s += CHF) {
+            fper[k].push_back((int32_t)fchunks.size());
+            fchunks.push_back(Chunk{s, std::min(e, s + CHF), k});
+        }
+    };
+    for (int k = 0; k < K; k++) fadd(moff[k], moff[k + 1], k);
+    for (int k = 0; k < K; k++) fadd(NM + foff[k], NM + foff[k + 1], k);
+    std::vector<int32_t> fioff(K + 1, 0), filist;
+    for (int k = 0; k < K; k++) {
+        fioff[k + 1] = fioff[k] + (int32_t)fper[k].size();
+        filist.insert(filist.end(), fper[k].begin(), fper[k].end());
+    }
+    const int nchf = (int)fchunks.size();
+    Buf dchf(&c, sizeof(Chunk) * fchunks.size()), dfioff(&c, sizeof(int32_t) * fioff.size()),
+        dfil(&c, sizeof(int32_t) * (filist.size() ? filist.size() : 1));
+    MDS_CUDA(cudaMemcpyAsync(dchf.p, fchunks.data(), sizeof(Chunk) * fchunks.size(), cudaMemcpyHostToDevice, c.stream));
+    MDS_CUDA(cudaMemcpyAsync(dfioff.p, fioff.data(), sizeof(int32_t) * fioff.size(), cudaMemcpyHostToDevice, c.stream));
+    if (filist.size())
+        MDS_CUDA(cudaMemcpyAsync(dfil.p, filist.data(), sizeof(int32_t) * filist.size(), cudaMemcpyHostToDevice,
+                                 c.stream));
+    const Chunk *CHFp = dchf.as<Chunk>();
+    const int32_t *IOF = dfioff.as<int32_t>(), *ILF = dfil.as<int32_t>();
 
     const int64_t ld = (N + 63) / 64 * 64, ldq = ld * NR;
     Buf Bi(&c, sizeof(double) * (size_t)(N * NR)), Xi(&c, sizeof(double) * (size_t)(N * NR));
     Buf V(&c, sizeof(double) * (size_t)(m + 1) * ldq), Z(&c, sizeof(double) * (size_t)m * ldq);
     Buf H(&c, sizeof(double) * (size_t)P * (m + 1) * m);
-    Buf part(&c, sizeof(double) * (size_t)(QMAX * nch * NR));
+    Buf part(&c, sizeof(double) * (size_t)(std::max<int64_t>((int64_t)QMAX * nch, nchf) * NR));
     // per-problem arrays with stride 32: cs, sn, g, y, h1, h2, nsq; scalars stride 8
     Buf pa(&c, sizeof(double) * (size_t)P * 32 * 7), psc(&c, sizeof(double) * (size_t)P * 8);
     // act: P problem flags, then K instance flags (an instance is live while
@@ -1281,8 +1311,9 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
     dim3 pgrid((unsigned)P, 1);
     // per-problem squared norms of a vector into nsq[p * 32]
     auto norms = [&](const double *w, const int8_t *mk) {
-        MDS_LAUNCH(c, KC_NONE, 8.0 * N * NR, (k_bdot<NR>), (unsigned)nch, RED_BLOCK, 0, CHp, nch, Vp, ldq, 0, w, PT, mk);
-        MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, 1), 32, 0, PT, nch, 1, NR, IO, IL, P, nsq, 0, mk);
+        MDS_LAUNCH(c, KC_NONE, 8.0 * N * NR, (k_bdot<NR>), (unsigned)nchf, RED_BLOCK, 0, CHFp, nchf, Vp, ldq, 0, w, PT,
+                   mk);
+        MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, 1), 32, 0, PT, nchf, 1, NR, IOF, ILF, P, nsq, 0, mk);
     };
     // upload the problem flags hact and the instance flags derived from them
     std::vector<int8_t> hbuf(P + K);
@@ -1356,16 +1387,16 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
             MDS_LAUNCH_F(c, kd, 8.0 * N * NR * (nq + 1) * sf, fl, (k_bdot<NR>), (unsigned)((int64_t)nch * nq), RED_BLOCK, 0, CHp,
                          nch, Vp, ldq, nq, w, PT, mk);
             MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, nq), 32, 0, PT, nch, nq, NR, IO, IL, P, hh, 0, mk);
-            MDS_LAUNCH_F(c, ka, 8.0 * N * NR * (nq + 2) * sf, fl, (k_bmaxpy<NR, -1>), nch, RED_BLOCK, 0, CHp, Vp,
+            MDS_LAUNCH_F(c, ka, 8.0 * N * NR * (nq + 2) * sf, fl, (k_bmaxpy<NR, -1>), nchf, RED_BLOCK, 0, CHFp, Vp,
                          ldq, nq, hh, w, PT, mk, (const int32_t *)nullptr);
-            MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, 1), 32, 0, PT, nch, 1, NR, IO, IL, P, nsq, 0, mk);
+            MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, 1), 32, 0, PT, nchf, 1, NR, IOF, ILF, P, nsq, 0, mk);
             if (pass == 0)
                 MDS_LAUNCH(c, KC_NONE, 0, k_bflag, grid_for(P, 128), 128, 0, P, nq, act.as<int8_t>(), h1, nsq,
                            o.reorth_eta2, f2.as<int8_t>(), h2);
         }
         MDS_LAUNCH(c, KC_NONE, 0, k_barnoldi, grid_for(P, 128), 128, 0, P, j, m, act.as<int8_t>(), H.as<double>(),
                    h1, h2, nsq, cs, sn, g, sc);
-        MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, nch, RED_BLOCK, 0, CHp, w, sc, 3, act.as<int8_t>());
+        MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, nchf, RED_BLOCK, 0, CHFp, w, sc, 3, act.as<int8_t>());
         MDS_CUDA(cudaMemcpyAsync(c.h_pin, sc, sizeof(double) * (size_t)P * 8, cudaMemcpyDeviceToHost, c.stream));
     };
     std::vector<std::unique_ptr<Graph>> graphs(m);
@@ -1433,7 +1464,7 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
         upload_flags(hact);
         if (K > 1) c.live = ilive;
         MDS_LAUNCH(c, KC_NONE, 0, k_bcycle_start, grid_for(P, 128), 128, 0, P, nsq, m, g, sc);
-        MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, nch, RED_BLOCK, 0, CHp, Vp, sc, 1, act.as<int8_t>());
+        MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, nchf, RED_BLOCK, 0, CHFp, Vp, sc, 1, act.as<int8_t>());
         for (int j = 0; j < m; j++) {
             if (j > 0) upload_flags(hact);
             run_step(j);
@@ -1460,7 +1491,7 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
         std::memcpy(c.h_pin, hkd.data(), sizeof(int32_t) * (size_t)P);
         MDS_CUDA(cudaMemcpyAsync(kd.p, c.h_pin, sizeof(int32_t) * (size_t)P, cudaMemcpyHostToDevice, c.stream));
         MDS_LAUNCH(c, KC_NONE, 0, k_bbacksolve, grid_for(P, 128), 128, 0, P, kd.as<int32_t>(), m, H.as<double>(), g, y);
-        MDS_LAUNCH(c, KC_NONE, 8.0 * N * NR * (m + 2), (k_bmaxpy<NR, 1>), nch, RED_BLOCK, 0, CHp, Zp, ldq, m, y,
+        MDS_LAUNCH(c, KC_NONE, 8.0 * N * NR * (m + 2), (k_bmaxpy<NR, 1>), nchf, RED_BLOCK, 0, CHFp, Zp, ldq, m, y,
                    Xi.as<double>(), nullptr, (const int8_t *)nullptr, kd.as<int32_t>());
         for (int p = 0; p < P; p++)
             if (hkd[p] > 0) rs[p]++;
