@@ -123,11 +123,40 @@ constexpr int64_t FUSE_FP64_ROWS = 65536;
 // into chunks of 256 rows; ck[2 c] and ck[2 c + 1] are the least and the
 // greatest instance owning a row of chunk c.  ck == NULL: every row is live.
 constexpr int LIVE_CHUNK_LOG2 = 8;
+//
+// Once instances have finished, launches are also compacted: rt lists the
+// 256-row chunks that hold a live row as merged ranges (rt[0] = R, then for
+// range r its first chunk rt[1 + 2r] and the chunks of the ranges before it
+// rt[2 + 2r]); a launch covers only those nch chunks and maps its block
+// index through the table.  rt == NULL: every chunk, in order.
 struct LiveMap {
     const int32_t *ck = nullptr;
     const int8_t *live = nullptr;
     double frac = 1.0;  // host side: share of the rows that are live (scales a launch's algorithmic work)
+    const int64_t *rt = nullptr;
+    int64_t nch = -1;   // host side: chunks of a compacted launch (-1: not compacted)
 };
+
+// The i-th chunk of a launch over the map's chunks.
+__device__ __forceinline__ int64_t live_chunk(const LiveMap &m, int64_t i) {
+    if (!m.rt) return i;
+    int lo = 0, hi = (int)m.rt[0] - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (m.rt[2 + 2 * mid] <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return m.rt[1 + 2 * lo] + (i - m.rt[2 + 2 * lo]);
+}
+// Blocks of a launch with g blocks per 256-row chunk: all of them, or only
+// those of the live chunks.
+inline int64_t live_blocks(const LiveMap &m, int64_t all, int g) { return m.nch >= 0 ? m.nch * g : all; }
+// The block a launch's i-th block stands for (g blocks per chunk).
+__device__ __forceinline__ int64_t live_block(const LiveMap &m, int64_t i, int g) {
+    return m.rt ? live_chunk(m, i / g) * g + i % g : i;
+}
 
 __device__ __forceinline__ int seg_find(const int64_t *seg, int K, int64_t r) {
     int lo = 0, hi = K - 1;
@@ -234,6 +263,11 @@ struct Ctx {
     // host copy gives the launches' algorithmic work
     const int8_t *live = nullptr;
     std::vector<int8_t> live_host;
+    // compacted launches (some instance has finished): live_ver counts the
+    // changes of live_host, so that each row space rebuilds its chunk ranges
+    // once per change
+    bool compact = false;
+    int live_ver = 0;
     // device address of the static workspace of mds_solve_noalloc on this
     // context's device, resolved by mds_create
     double *noalloc_scratch = nullptr;
@@ -471,6 +505,9 @@ struct Level {
     Buf seg_d;             // int64 [K + 1] instance row offsets (packed batches)
     std::vector<int64_t> seg_h;  // the same on the host
     Buf ck;                // int32 [2 chunks] least / greatest instance of each 256-row chunk
+    mutable Buf rt;        // int64 chunk ranges of the live instances (compacted launches)
+    mutable int64_t rt_nch = 0;
+    mutable int rt_ver = -1;
     // stencil storage (FMT_DIA): plane d holds each row's coefficient of the
     // neighbour at offset o_d (ascending), zero where the row has none
     int dia_D = 0;         // 5 (2D) or 7 (3D); 0: the level is no stencil
@@ -493,13 +530,31 @@ inline double live_share(const std::vector<int8_t> &live, const std::vector<int6
     return (double)r / (double)seg[K];
 }
 
+// Chunk ranges of the live instances of a row space (instance k owns the
+// rows [a[k], a[k+1]) and, when b is given, also [n1 + b[k], n1 + b[k+1])),
+// in the LiveMap::rt layout; returns the number of chunks.
+int64_t live_ranges(const std::vector<int8_t> &live, const std::vector<int64_t> &a, const std::vector<int64_t> *b,
+                    int64_t n1, std::vector<int64_t> &t);
+// Upload t to dev (allocated for up to K ranges) on the context stream.
+void upload_ranges(Ctx &c, Buf &dev, const std::vector<int64_t> &t, int K);
+
 // The liveness map of one level (every row live outside a batched solve).
-inline LiveMap level_live(const Ctx &c, const Level &L) {
+inline LiveMap level_live(Ctx &c, const Level &L) {
     LiveMap m;
     if (c.live && L.K > 1 && L.ck.p) {
         m.ck = L.ck.as<int32_t>();
         m.live = c.live;
         m.frac = live_share(c.live_host, L.seg_h);
+        if (c.compact) {
+            if (L.rt_ver != c.live_ver) {
+                std::vector<int64_t> t;
+                L.rt_nch = live_ranges(c.live_host, L.seg_h, nullptr, 0, t);
+                upload_ranges(c, L.rt, t, L.K);
+                L.rt_ver = c.live_ver;
+            }
+            m.rt = L.rt.as<int64_t>();
+            m.nch = L.rt_nch;
+        }
     }
     return m;
 }

@@ -965,14 +965,15 @@ template <int NR> __device__ __forceinline__ bool chunk_skipped(const int8_t *ma
 template <int NR>
 __global__ void __launch_bounds__(RED_BLOCK) k_bdot(const Chunk *__restrict__ ch, int nchunk, const double *__restrict__ V,
                                                      int64_t ldq, int nq, const double *__restrict__ W,
-                                                     double *__restrict__ partial, const int8_t *__restrict__ mask) {
+                                                     double *__restrict__ partial, const int8_t *__restrict__ mask,
+                                                     const int32_t *__restrict__ lc) {
     mds_pdl_entry();
     __shared__ double ws[RED_BLOCK / 32][NR];
     // the nq blocks of one chunk are adjacent in launch order, so they run
     // together and the chunk of W is read from DRAM once (a grid-stride loop
     // over a resident grid loses this order, measured slower)
     const int nqb = nq > 0 ? nq : 1;
-    const int64_t chunk = blockIdx.x / nqb;
+    const int64_t chunk = lc ? lc[blockIdx.x / nqb] : blockIdx.x / nqb;  // lc: the live chunks only
     const int q = (int)(blockIdx.x % nqb);
     Chunk k = ch[chunk];
     if (chunk_skipped<NR>(mask, k.inst)) return;
@@ -1025,11 +1026,12 @@ __global__ void __launch_bounds__(RED_BLOCK) k_bmaxpy(const Chunk *__restrict__ 
                                                        int64_t ldq, int nq, const double *__restrict__ coef,
                                                        double *__restrict__ W, double *__restrict__ partial,
                                                        const int8_t *__restrict__ mask,
-                                                       const int32_t *__restrict__ qlim) {
+                                                       const int32_t *__restrict__ qlim, const int32_t *__restrict__ lc) {
     mds_pdl_entry();
     __shared__ double cs[NR][32];
     __shared__ double ws[RED_BLOCK / 32][NR];
-    Chunk k = ch[blockIdx.x];
+    const int64_t chunk = lc ? lc[blockIdx.x] : blockIdx.x;  // lc: the live chunks only
+    Chunk k = ch[chunk];
     if (chunk_skipped<NR>(mask, k.inst)) return;
     if (qlim) {
         int q1 = 0;
@@ -1076,7 +1078,7 @@ __global__ void __launch_bounds__(RED_BLOCK) k_bmaxpy(const Chunk *__restrict__ 
         if (threadIdx.x < NR) {
             double t = 0.0;
             for (int k2 = 0; k2 < RED_BLOCK / 32; k2++) t += ws[k2][threadIdx.x];
-            partial[(int64_t)blockIdx.x * NR + threadIdx.x] = t;
+            partial[chunk * NR + threadIdx.x] = t;
         }
     }
 }
@@ -1106,10 +1108,10 @@ __global__ void k_bflag(int P, int nq, const int8_t *__restrict__ active, const 
 template <int NR>
 __global__ void __launch_bounds__(RED_BLOCK) k_bscale(const Chunk *__restrict__ ch, double *__restrict__ W,
                                                        const double *__restrict__ sc, int slot,
-                                                       const int8_t *__restrict__ active) {
+                                                       const int8_t *__restrict__ active, const int32_t *__restrict__ lc) {
     static_assert(RED_BLOCK % NR == 0, "block size must be a multiple of the column count");
     mds_pdl_entry();
-    Chunk k = ch[blockIdx.x];
+    Chunk k = ch[lc ? lc[blockIdx.x] : blockIdx.x];  // lc: the live chunks only
     if (chunk_skipped<NR>(active, k.inst)) return;  // a finished instance: its rows are no longer used
     const int64_t p = (int64_t)k.inst * NR + threadIdx.x % NR;
     const double f = active[p] ? sc[p * 8 + slot] : 0.0;
@@ -1283,7 +1285,37 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
     Buf act(&c, (size_t)(P + K)), kd(&c, sizeof(int32_t) * (size_t)P), f2(&c, (size_t)P);
     const int8_t *ilive = act.as<int8_t>() + P;
     LiveMap sysmap;
-    Buf sys_ck;
+    Buf sys_ck, sys_rt;
+    // the chunks (coarse and fine) of the live instances, for the compacted
+    // Gram-Schmidt, scaling and update launches
+    struct LiveChunks {
+        Ctx &c;
+        const std::vector<Chunk> &coarse, &fine;
+        Buf dcoarse, dfine;
+        int64_t nc = 0, nf = 0;
+        bool on = false;
+        void build(const std::vector<int8_t> &live) {
+            std::vector<int32_t> a, b;
+            for (size_t i = 0; i < coarse.size(); i++)
+                if (live[coarse[i].inst]) a.push_back((int32_t)i);
+            for (size_t i = 0; i < fine.size(); i++)
+                if (live[fine[i].inst]) b.push_back((int32_t)i);
+            // never empty: chunk 0 stands in, and the kernels' masks skip it
+            if (a.empty()) a.push_back(0);
+            if (b.empty()) b.push_back(0);
+            if (!dcoarse.p) dcoarse = Buf(&c, sizeof(int32_t) * (coarse.size() + 1));
+            if (!dfine.p) dfine = Buf(&c, sizeof(int32_t) * (fine.size() + 1));
+            MDS_CUDA(cudaMemcpyAsync(dcoarse.p, a.data(), sizeof(int32_t) * a.size(), cudaMemcpyHostToDevice, c.stream));
+            MDS_CUDA(cudaMemcpyAsync(dfine.p, b.data(), sizeof(int32_t) * b.size(), cudaMemcpyHostToDevice, c.stream));
+            nc = (int64_t)a.size();
+            nf = (int64_t)b.size();
+            on = true;
+        }
+        const int32_t *lcoarse() const { return on ? dcoarse.as<int32_t>() : nullptr; }
+        const int32_t *lfine() const { return on ? dfine.as<int32_t>() : nullptr; }
+        int64_t ncoarse(int64_t all) const { return on ? nc : all; }
+        int64_t nfine(int64_t all) const { return on ? nf : all; }
+    } cl{c, chunks, fchunks};
     if (K > 1) {
         sys_ck = live_chunks(c, N, moff, &foff, NM);
         sysmap.ck = sys_ck.as<int32_t>();
@@ -1297,6 +1329,7 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
         ~LiveScope() {
             c.live = nullptr;
             c.live_host.clear();
+            c.compact = false;
         }
     } live_scope(c, K > 1 ? ilive : nullptr);
     double *cs = pa.as<double>(), *sn = cs + (size_t)P * 32, *g = sn + (size_t)P * 32, *y = g + (size_t)P * 32,
@@ -1311,8 +1344,8 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
     dim3 pgrid((unsigned)P, 1);
     // per-problem squared norms of a vector into nsq[p * 32]
     auto norms = [&](const double *w, const int8_t *mk) {
-        MDS_LAUNCH(c, KC_NONE, 8.0 * N * NR, (k_bdot<NR>), (unsigned)nchf, RED_BLOCK, 0, CHFp, nchf, Vp, ldq, 0, w, PT,
-                   mk);
+        MDS_LAUNCH(c, KC_NONE, 8.0 * N * NR, (k_bdot<NR>), (unsigned)(mk ? cl.nfine(nchf) : nchf), RED_BLOCK, 0, CHFp, nchf, Vp,
+                   ldq, 0, w, PT, mk, mk ? cl.lfine() : nullptr);
         MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, 1), 32, 0, PT, nchf, 1, NR, IOF, ILF, P, nsq, 0, mk);
     };
     // upload the problem flags hact and the instance flags derived from them
@@ -1327,11 +1360,32 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
         std::memcpy(c.h_pin, hbuf.data(), (size_t)(P + K));
         MDS_CUDA(cudaMemcpyAsync(act.p, c.h_pin, (size_t)(P + K), cudaMemcpyHostToDevice, c.stream));
         if (K > 1) {
+            const bool changed = c.live_host.size() != (size_t)K ||
+                                 !std::equal(c.live_host.begin(), c.live_host.end(), hbuf.begin() + P);
             c.live_host.assign(hbuf.begin() + P, hbuf.end());
             int64_t r = 0;
+            int nlive = 0;
             for (int k = 0; k < K; k++)
-                if (hbuf[P + k]) r += (moff[k + 1] - moff[k]) + (foff[k + 1] - foff[k]);
+                if (hbuf[P + k]) {
+                    r += (moff[k + 1] - moff[k]) + (foff[k + 1] - foff[k]);
+                    nlive++;
+                }
             sysmap.frac = N > 0 ? (double)r / (double)N : 1.0;
+            // compacted launches once an instance has finished
+            c.compact = nlive < K;
+            if (changed) c.live_ver++;
+            if (c.compact && changed) {
+                std::vector<int64_t> t;
+                sysmap.nch = live_ranges(c.live_host, moff, &foff, NM, t);
+                upload_ranges(c, sys_rt, t, K);
+                sysmap.rt = sys_rt.as<int64_t>();
+                cl.build(c.live_host);
+            }
+            if (!c.compact) {
+                sysmap.rt = nullptr;
+                sysmap.nch = -1;
+                cl.on = false;
+            }
         }
     };
     std::vector<double> host(P * 8), bn(P);
@@ -1384,11 +1438,11 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
             // first pass: the active problems' instances; second: the flagged problems'
             const int8_t *mk = pass == 0 ? act.as<int8_t>() : f2.as<int8_t>();
             int kd = pass == 0 ? KC_GS_DOT : KC_NONE, ka = pass == 0 ? KC_GS_AXPY : KC_NONE;
-            MDS_LAUNCH_F(c, kd, 8.0 * N * NR * (nq + 1) * sf, fl, (k_bdot<NR>), (unsigned)((int64_t)nch * nq), RED_BLOCK, 0, CHp,
-                         nch, Vp, ldq, nq, w, PT, mk);
+            MDS_LAUNCH_F(c, kd, 8.0 * N * NR * (nq + 1) * sf, fl, (k_bdot<NR>), (unsigned)((int64_t)cl.ncoarse(nch) * nq),
+                         RED_BLOCK, 0, CHp, nch, Vp, ldq, nq, w, PT, mk, cl.lcoarse());
             MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, nq), 32, 0, PT, nch, nq, NR, IO, IL, P, hh, 0, mk);
-            MDS_LAUNCH_F(c, ka, 8.0 * N * NR * (nq + 2) * sf, fl, (k_bmaxpy<NR, -1>), nchf, RED_BLOCK, 0, CHFp, Vp,
-                         ldq, nq, hh, w, PT, mk, (const int32_t *)nullptr);
+            MDS_LAUNCH_F(c, ka, 8.0 * N * NR * (nq + 2) * sf, fl, (k_bmaxpy<NR, -1>), (unsigned)cl.nfine(nchf), RED_BLOCK, 0,
+                         CHFp, Vp, ldq, nq, hh, w, PT, mk, (const int32_t *)nullptr, cl.lfine());
             MDS_LAUNCH(c, KC_NONE, 0, k_breduce, dim3(P, 1), 32, 0, PT, nchf, 1, NR, IOF, ILF, P, nsq, 0, mk);
             if (pass == 0)
                 MDS_LAUNCH(c, KC_NONE, 0, k_bflag, grid_for(P, 128), 128, 0, P, nq, act.as<int8_t>(), h1, nsq,
@@ -1396,14 +1450,17 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
         }
         MDS_LAUNCH(c, KC_NONE, 0, k_barnoldi, grid_for(P, 128), 128, 0, P, j, m, act.as<int8_t>(), H.as<double>(),
                    h1, h2, nsq, cs, sn, g, sc);
-        MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, nchf, RED_BLOCK, 0, CHFp, w, sc, 3, act.as<int8_t>());
+        MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, (unsigned)cl.nfine(nchf), RED_BLOCK, 0, CHFp, w, sc, 3,
+                   act.as<int8_t>(), cl.lfine());
         MDS_CUDA(cudaMemcpyAsync(c.h_pin, sc, sizeof(double) * (size_t)P * 8, cudaMemcpyDeviceToHost, c.stream));
     };
     std::vector<std::unique_ptr<Graph>> graphs(m);
     bool graphs_ok = o.graphs != 0, warmed = false;
     auto run_step = [&](int j) {
         Graph *gj = nullptr;
-        if (graphs_ok && warmed) {
+        // graphs while every instance iterates; compacted direct launches
+        // (grids sized to the live chunks) once some have finished
+        if (graphs_ok && warmed && !c.compact) {
             auto &slot = graphs[j];
             if (!slot) {
                 slot.reset(new Graph);
@@ -1464,7 +1521,8 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
         upload_flags(hact);
         if (K > 1) c.live = ilive;
         MDS_LAUNCH(c, KC_NONE, 0, k_bcycle_start, grid_for(P, 128), 128, 0, P, nsq, m, g, sc);
-        MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, nchf, RED_BLOCK, 0, CHFp, Vp, sc, 1, act.as<int8_t>());
+        MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, (unsigned)cl.nfine(nchf), RED_BLOCK, 0, CHFp, Vp, sc, 1,
+                   act.as<int8_t>(), cl.lfine());
         for (int j = 0; j < m; j++) {
             if (j > 0) upload_flags(hact);
             run_step(j);
@@ -1491,8 +1549,10 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
         std::memcpy(c.h_pin, hkd.data(), sizeof(int32_t) * (size_t)P);
         MDS_CUDA(cudaMemcpyAsync(kd.p, c.h_pin, sizeof(int32_t) * (size_t)P, cudaMemcpyHostToDevice, c.stream));
         MDS_LAUNCH(c, KC_NONE, 0, k_bbacksolve, grid_for(P, 128), 128, 0, P, kd.as<int32_t>(), m, H.as<double>(), g, y);
+        // every chunk: the problems that finished during this cycle are no
+        // longer live but still take their update (qlim = their step count)
         MDS_LAUNCH(c, KC_NONE, 8.0 * N * NR * (m + 2), (k_bmaxpy<NR, 1>), nchf, RED_BLOCK, 0, CHFp, Zp, ldq, m, y,
-                   Xi.as<double>(), nullptr, (const int8_t *)nullptr, kd.as<int32_t>());
+                   Xi.as<double>(), nullptr, (const int8_t *)nullptr, kd.as<int32_t>(), (const int32_t *)nullptr);
         for (int p = 0; p < P; p++)
             if (hkd[p] > 0) rs[p]++;
     }

@@ -1,4 +1,6 @@
 // Primitives: scan, fills, precision casts, CSR SpMV.
+#include <algorithm>
+
 #include "internal.cuh"
 #include "spmv.cuh"
 
@@ -125,6 +127,53 @@ __global__ void k_scale(double *__restrict__ p, double a, int64_t n) {
         p[i] = a * p[i];
 }
 
+int64_t live_ranges(const std::vector<int8_t> &live, const std::vector<int64_t> &a, const std::vector<int64_t> *b,
+                    int64_t n1, std::vector<int64_t> &t) {
+    std::vector<std::pair<int64_t, int64_t>> iv;
+    auto add = [&](const std::vector<int64_t> &seg, int64_t base) {
+        for (size_t k = 0; k + 1 < seg.size(); k++)
+            if (k < live.size() && live[k] && seg[k + 1] > seg[k])
+                iv.emplace_back((base + seg[k]) >> LIVE_CHUNK_LOG2,
+                                ((base + seg[k + 1] - 1) >> LIVE_CHUNK_LOG2) + 1);
+    };
+    add(a, 0);
+    if (b) add(*b, n1);
+    std::sort(iv.begin(), iv.end());
+    t.assign(1, 0);
+    int64_t total = 0, lo = -1, hi = -1;
+    auto flush = [&]() {
+        if (hi > lo) {
+            t.push_back(lo);
+            t.push_back(total);
+            total += hi - lo;
+            t[0]++;
+        }
+    };
+    for (auto &v : iv) {
+        if (v.first <= hi) {
+            hi = std::max(hi, v.second);
+        } else {
+            flush();
+            lo = v.first;
+            hi = v.second;
+        }
+    }
+    flush();
+    if (t[0] == 0) {  // nothing live: one empty range keeps the table well formed
+        t.push_back(0);
+        t.push_back(0);
+        t[0] = 1;
+    }
+    return total;
+}
+
+void upload_ranges(Ctx &c, Buf &dev, const std::vector<int64_t> &t, int K) {
+    const size_t cap = sizeof(int64_t) * (size_t)(2 * (2 * (size_t)K + 1) + 1);
+    if (!dev.p || dev.bytes < cap) dev = Buf(&c, cap);
+    MDS_REQUIRE(sizeof(int64_t) * t.size() <= dev.bytes, MDS_ERR_INVALID, "live chunk table overflow");
+    MDS_CUDA(cudaMemcpyAsync(dev.p, t.data(), sizeof(int64_t) * t.size(), cudaMemcpyHostToDevice, c.stream));
+}
+
 Buf live_chunks(Ctx &c, int64_t rows, const std::vector<int64_t> &a, const std::vector<int64_t> *b, int64_t n1) {
     const int64_t nch = (rows + (1 << LIVE_CHUNK_LOG2) - 1) >> LIVE_CHUNK_LOG2;
     std::vector<int32_t> ck((size_t)(2 * (nch > 0 ? nch : 1)));
@@ -162,7 +211,7 @@ void scale_f64(Ctx &c, double *p, double a, int64_t n) {
 // block of finished instances' rows returns at once.
 template <class A, class B>
 __global__ void k_cast(const A *__restrict__ in, B *__restrict__ out, int64_t rows, int nr, int64_t per, LiveMap lm) {
-    const int64_t r0 = (int64_t)blockIdx.x * per, r1 = r0 + per < rows ? r0 + per : rows;
+    const int64_t r0 = live_block(lm, blockIdx.x, 1) * per, r1 = r0 + per < rows ? r0 + per : rows;
     if (!block_rows_live(lm, r0, r1)) return;
     mds_pdl_entry();
     for (int64_t i = r0 * nr + threadIdx.x; i < r1 * nr; i += blockDim.x) out[i] = (B)in[i];
@@ -174,6 +223,10 @@ template <class A, class B> static void cast_rows(Ctx &c, const A *in, B *out, i
     int64_t per = (rows + 8191) / 8192;  // at most 8192 blocks
     per = per < 256 ? 256 : per;
     unsigned g = (unsigned)((rows + per - 1) / per);
+    if (lm.rt) {  // only the live chunks, one per block
+        per = 256;
+        g = (unsigned)(lm.nch > 0 ? lm.nch : 1);
+    }
     MDS_LAUNCH(c, KC_NONE, (sizeof(A) + sizeof(B)) * (double)n, (k_cast<A, B>), g, 256, 0, in, out, rows, nr, per, lm);
 }
 
@@ -192,9 +245,9 @@ static void spmv_launch(Ctx &c, const mds_csr &A, const XT *x, const double *r, 
     const int block = 256;
     double bytes = 12.0 * (double)A.nnz + 4.0 * (double)(A.nrow + 1) +
                    NR * (sizeof(XT) * (double)A.ncol + sizeof(OT) * (double)A.nrow + (MODE == 1 ? 8.0 * A.nrow : 0.0));
-    unsigned grid = grid_for(A.nrow * G, block);
+    const unsigned grid = (unsigned)live_blocks(lm, grid_for(A.nrow * G, block), G);
     MDS_LAUNCH_F(c, kclass, bytes * lm.frac, 2.0 * NR * A.nnz * lm.frac, (k_spmv_csr<G, double, XT, OT, MODE, NR>),
-                 grid, block, 0, A.nrow, A.row_ptr, A.col, A.val, x, r, y, lm);
+                 grid > 0 ? grid : 1, block, 0, A.nrow, A.row_ptr, A.col, A.val, x, r, y, lm);
 }
 
 template <int G, class XT, class OT, int MODE>

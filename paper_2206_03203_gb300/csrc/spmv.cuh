@@ -14,12 +14,14 @@ __global__ void __launch_bounds__(256) k_spmv_csr(int64_t nrow, const int32_t *_
                                                    const int32_t *__restrict__ ci, const VT *__restrict__ v,
                                                    const XT *__restrict__ x, const double *__restrict__ r,
                                                    OT *__restrict__ y, LiveMap lm) {
+    // the block's rows: block b of the launch, or of its live chunks only
+    const int64_t vb = live_block(lm, blockIdx.x, G);
     {
-        const int64_t r0 = (int64_t)blockIdx.x * (256 / G), r1 = r0 + 256 / G < nrow ? r0 + 256 / G : nrow;
+        const int64_t r0 = vb * (256 / G), r1 = r0 + 256 / G < nrow ? r0 + 256 / G : nrow;
         if (!block_rows_live(lm, r0, r1)) return;
     }
     mds_pdl_entry();
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t t = vb * blockDim.x + threadIdx.x;
     int64_t row = t / G;
     int lane = (int)(t % G);
     double s[NR];

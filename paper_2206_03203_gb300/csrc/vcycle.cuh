@@ -312,7 +312,9 @@ template <int G, class VT, class XT, int K, int NR, int PF>
 __global__ void __launch_bounds__(256) k_level(LvlMat<VT> A, const XT *__restrict__ dinv, const XT *__restrict__ b,
                                                const XT *__restrict__ xin, const int32_t *__restrict__ agg,
                                                const XT *__restrict__ xc, XT *__restrict__ out, int64_t nvb) {
-    for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) level_block<G, VT, XT, K, NR, PF>(vb, A, dinv, b, xin, agg, xc, out);
+    constexpr int GC = G > 0 ? G : 1;  // blocks per 256-row chunk
+    for (int64_t i = blockIdx.x; i < nvb; i += gridDim.x)
+        level_block<G, VT, XT, K, NR, PF>(live_block(A.lm, i, GC), A, dinv, b, xin, agg, xc, out);
 }
 
 // ---- stencil storage (FMT_DIA): the finest level of S~ of a primal system on
@@ -458,7 +460,8 @@ template <class VT, class XT, int K, int NR, int D>
 __global__ void __launch_bounds__(256, dia_min_blocks<XT, K, NR>())
     k_level_dia(DiaMat<VT> A, const XT *__restrict__ dinv, const XT *__restrict__ b, const XT *__restrict__ xin,
                 const int32_t *__restrict__ agg, const XT *__restrict__ xc, XT *__restrict__ out, int64_t nvb) {
-    for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) level_dia_block<VT, XT, K, NR, D>(vb, A, dinv, b, xin, agg, xc, out);
+    for (int64_t i = blockIdx.x; i < nvb; i += gridDim.x)
+        level_dia_block<VT, XT, K, NR, D>(live_block(A.lm, i, 1), A, dinv, b, xin, agg, xc, out);
 }
 
 // ---- elementwise kernels (NR interleaved columns; row of entry e = e / NR).
@@ -469,7 +472,7 @@ __global__ void __launch_bounds__(256, dia_min_blocks<XT, K, NR>())
 template <class XT, int NR>
 __global__ void k_vc_x0(int64_t n, const XT *__restrict__ dinv, const XT *__restrict__ b, XT *__restrict__ x,
                         int64_t per, LiveMap lm) {
-    const int64_t r0 = (int64_t)blockIdx.x * per, r1 = r0 + per < n ? r0 + per : n;
+    const int64_t r0 = live_block(lm, blockIdx.x, 1) * per, r1 = r0 + per < n ? r0 + per : n;
     if (!block_rows_live(lm, r0, r1)) return;
     int64_t e = r0 * NR + threadIdx.x;
     const XT d0 = e < r1 * NR ? dinv[e / NR] : (XT)0;
@@ -483,7 +486,7 @@ __global__ void k_vc_x0(int64_t n, const XT *__restrict__ dinv, const XT *__rest
 template <class XT, int NR>
 __global__ void k_vc_prolong(int64_t n, const int32_t *__restrict__ agg, const XT *__restrict__ xc,
                              XT *__restrict__ y, int64_t per, LiveMap lm) {
-    const int64_t r0 = (int64_t)blockIdx.x * per, r1 = r0 + per < n ? r0 + per : n;
+    const int64_t r0 = live_block(lm, blockIdx.x, 1) * per, r1 = r0 + per < n ? r0 + per : n;
     if (!block_rows_live(lm, r0, r1)) return;
     int64_t e = r0 * NR + threadIdx.x;
     const int32_t a0 = e < r1 * NR ? agg[e / NR] : -1;
@@ -570,7 +573,7 @@ template <class XT, int NR>
 __global__ void __launch_bounds__(256) k_vc_restrict(int64_t nc, const int32_t *__restrict__ off,
                                                      const int32_t *__restrict__ mem, const XT *__restrict__ r,
                                                      XT *__restrict__ bc, LiveMap lm, int64_t nvb) {
-    for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) restrict_block<XT, NR>(vb, nc, off, mem, r, bc, lm);
+    for (int64_t i = blockIdx.x; i < nvb; i += gridDim.x) restrict_block<XT, NR>(live_block(lm, i, 1), nc, off, mem, r, bc, lm);
 }
 
 // Smoothed aggregation transfers (NR columns): b_c = R r and y += P x_c, one
@@ -615,7 +618,7 @@ __global__ void k_sa_prolong(int64_t n, const int32_t *__restrict__ rp, const in
 
 // ---------------------------------------------------------------- host dispatch
 
-template <class VT> static LvlMat<VT> lvl_view(const Ctx &c, const Level &L) {
+template <class VT> static LvlMat<VT> lvl_view(Ctx &c, const Level &L) {
     LvlMat<VT> m{};
     m.n = L.A.nrow;
     m.lm = level_live(c, L);
@@ -657,12 +660,12 @@ static void launch_level_pf(Ctx &c, const Level &L, const XT *dinv, const XT *b,
             bytes = bytes - vb - 4.0 * (n + 1) + (double)L.dia_D * sizeof(VT) * n;
             if (L.dia_D == 7)
                 MDS_LAUNCH_F(c, cls, bytes * m.lm.frac, flops * m.lm.frac, (k_level_dia<VT, XT, K, NR, 7>),
-                             stride_grid(c, k_level_dia<VT, XT, K, NR, 7>, 256, grid_for(n, 256)), 256, 0, dm, dinv,
-                             b, xin, agg, xc, out, (int64_t)grid_for(n, 256));
+                             stride_grid(c, k_level_dia<VT, XT, K, NR, 7>, 256, live_blocks(m.lm, grid_for(n, 256), 1)),
+                             256, 0, dm, dinv, b, xin, agg, xc, out, live_blocks(m.lm, grid_for(n, 256), 1));
             else
                 MDS_LAUNCH_F(c, cls, bytes * m.lm.frac, flops * m.lm.frac, (k_level_dia<VT, XT, K, NR, 5>),
-                             stride_grid(c, k_level_dia<VT, XT, K, NR, 5>, 256, grid_for(n, 256)), 256, 0, dm, dinv,
-                             b, xin, agg, xc, out, (int64_t)grid_for(n, 256));
+                             stride_grid(c, k_level_dia<VT, XT, K, NR, 5>, 256, live_blocks(m.lm, grid_for(n, 256), 1)),
+                             256, 0, dm, dinv, b, xin, agg, xc, out, live_blocks(m.lm, grid_for(n, 256), 1));
             return;
         } else {
             throw Error(MDS_ERR_INVALID, "stencil storage holds FP32 or FP64 values only");
@@ -672,7 +675,7 @@ static void launch_level_pf(Ctx &c, const Level &L, const XT *dinv, const XT *b,
     flops *= m.lm.frac;
     if (L.fmt == FMT_SELL) {
         int64_t rows = L.sell_nslice * L.sell_c;
-        const int64_t nvb = grid_for(rows, 256);
+        const int64_t nvb = live_blocks(m.lm, grid_for(rows, 256), 1);
         MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<0, VT, XT, K, NR, PF>),
                      stride_grid(c, k_level<0, VT, XT, K, NR, PF>, 256, nvb), 256, 0, m, dinv, b, xin, agg, xc, out,
                      nvb);
@@ -681,33 +684,33 @@ static void launch_level_pf(Ctx &c, const Level &L, const XT *dinv, const XT *b,
     switch (L.G) {
         case 1:
             MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<1, VT, XT, K, NR, PF>),
-                         stride_grid(c, k_level<1, VT, XT, K, NR, PF>, 256, grid_for(n, 256)), 256, 0, m,
-                         dinv, b, xin, agg, xc, out, (int64_t)grid_for(n, 256));
+                         stride_grid(c, k_level<1, VT, XT, K, NR, PF>, 256, live_blocks(m.lm, grid_for(n, 256), 1)),
+                         256, 0, m, dinv, b, xin, agg, xc, out, live_blocks(m.lm, grid_for(n, 256), 1));
             break;
         case 2:
             MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<2, VT, XT, K, NR, PF>),
-                         stride_grid(c, k_level<2, VT, XT, K, NR, PF>, 256, grid_for(n * 2, 256)), 256, 0, m,
-                         dinv, b, xin, agg, xc, out, (int64_t)grid_for(n * 2, 256));
+                         stride_grid(c, k_level<2, VT, XT, K, NR, PF>, 256, live_blocks(m.lm, grid_for(n * 2, 256), 2)),
+                         256, 0, m, dinv, b, xin, agg, xc, out, live_blocks(m.lm, grid_for(n * 2, 256), 2));
             break;
         case 4:
             MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<4, VT, XT, K, NR, PF>),
-                         stride_grid(c, k_level<4, VT, XT, K, NR, PF>, 256, grid_for(n * 4, 256)), 256, 0, m,
-                         dinv, b, xin, agg, xc, out, (int64_t)grid_for(n * 4, 256));
+                         stride_grid(c, k_level<4, VT, XT, K, NR, PF>, 256, live_blocks(m.lm, grid_for(n * 4, 256), 4)),
+                         256, 0, m, dinv, b, xin, agg, xc, out, live_blocks(m.lm, grid_for(n * 4, 256), 4));
             break;
         case 8:
             MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<8, VT, XT, K, NR, PF>),
-                         stride_grid(c, k_level<8, VT, XT, K, NR, PF>, 256, grid_for(n * 8, 256)), 256, 0, m,
-                         dinv, b, xin, agg, xc, out, (int64_t)grid_for(n * 8, 256));
+                         stride_grid(c, k_level<8, VT, XT, K, NR, PF>, 256, live_blocks(m.lm, grid_for(n * 8, 256), 8)),
+                         256, 0, m, dinv, b, xin, agg, xc, out, live_blocks(m.lm, grid_for(n * 8, 256), 8));
             break;
         case 16:
             MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<16, VT, XT, K, NR, PF>),
-                         stride_grid(c, k_level<16, VT, XT, K, NR, PF>, 256, grid_for(n * 16, 256)), 256, 0, m,
-                         dinv, b, xin, agg, xc, out, (int64_t)grid_for(n * 16, 256));
+                         stride_grid(c, k_level<16, VT, XT, K, NR, PF>, 256, live_blocks(m.lm, grid_for(n * 16, 256), 16)),
+                         256, 0, m, dinv, b, xin, agg, xc, out, live_blocks(m.lm, grid_for(n * 16, 256), 16));
             break;
         default:
             MDS_LAUNCH_F(c, cls, bytes, flops, (k_level<32, VT, XT, K, NR, PF>),
-                         stride_grid(c, k_level<32, VT, XT, K, NR, PF>, 256, grid_for(n * 32, 256)), 256, 0, m,
-                         dinv, b, xin, agg, xc, out, (int64_t)grid_for(n * 32, 256));
+                         stride_grid(c, k_level<32, VT, XT, K, NR, PF>, 256, live_blocks(m.lm, grid_for(n * 32, 256), 32)),
+                         256, 0, m, dinv, b, xin, agg, xc, out, live_blocks(m.lm, grid_for(n * 32, 256), 32));
             break;
     }
 }
@@ -777,6 +780,11 @@ static int64_t ew_rows(int64_t n) {
     return per < 256 ? 256 : per;
 }
 static unsigned ew_blocks(int64_t n) { return (unsigned)((n + ew_rows(n) - 1) / ew_rows(n)); }
+// the same for a launch over the live chunks of lm (256 rows per block)
+static int64_t ew_rows(int64_t n, const LiveMap &lm) { return lm.rt ? 256 : ew_rows(n); }
+static unsigned ew_blocks(int64_t n, const LiveMap &lm) {
+    return lm.rt ? (unsigned)(lm.nch > 0 ? lm.nch : 1) : ew_blocks(n);
+}
 
 // x = S(x0; b): `sweeps` smoother applications starting from x0 (NULL = 0).
 // x0 and x must differ; uses L.r (residual), L.t (copy) and L.d (Chebyshev
@@ -797,8 +805,11 @@ static void smooth_stored(Ctx &c, const Hierarchy &h, const Level &L, const XT *
         }
         if (h.smoother == MDS_SMOOTHER_L1JACOBI) {
             if (!cur)
-                MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n * NR, (k_vc_x0<XT, NR>), ew_blocks(n), 256, 0, n, dinv,
-                           b, dst, ew_rows(n), level_live(c, L));
+            {
+                const LiveMap lm = level_live(c, L);
+                MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n * NR, (k_vc_x0<XT, NR>), ew_blocks(n, lm), 256, 0, n,
+                           dinv, b, dst, ew_rows(n, lm), lm);
+            }
             else
                 level_op<XT, VK_SMOOTH, NR>(c, L, b, cur, nullptr, nullptr, dst, 0);
         } else {
@@ -1196,8 +1207,9 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
     }
     if (l == last && h.diagonal) {  // no couplings: exact x = b / a_ii
         const int64_t nd = L.A.nrow;
-        MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * nd * NR, (k_vc_x0<XT, NR>), ew_blocks(nd), 256, 0, nd,
-                   L.dinv.as<XT>(), b, x, ew_rows(nd), level_live(c, L));
+        const LiveMap lm = level_live(c, L);
+        MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * nd * NR, (k_vc_x0<XT, NR>), ew_blocks(nd, lm), 256, 0, nd,
+                   L.dinv.as<XT>(), b, x, ew_rows(nd, lm), lm);
         return;
     }
     if (h.use_tail && l == tail_start<XT>(h, (int64_t)tail_cluster<XT, NR>(c) * TAIL_THREADS) &&
@@ -1215,11 +1227,12 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
     if (fused) {
         if (L.has_coarse) {
             Level &C = h.lv[l + 1];
+            const LiveMap lmc = level_live(c, C);
             level_op<XT, VK_RESID0, NR>(c, L, b, nullptr, nullptr, nullptr, r, 0);
             MDS_LAUNCH(c, L.timed_level ? KC_VC_RESTRICT : KC_NONE, rbytes * level_live(c, L).frac,
-                       (k_vc_restrict<XT, NR>), stride_grid(c, k_vc_restrict<XT, NR>, 256, grid_for(L.nc, 256)),
-                       256, 0, L.nc, L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r, C.b.as<XT>(), level_live(c, C),
-                       (int64_t)grid_for(L.nc, 256));
+                       (k_vc_restrict<XT, NR>), stride_grid(c, k_vc_restrict<XT, NR>, 256, live_blocks(lmc, grid_for(L.nc, 256), 1)),
+                       256, 0, L.nc, L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r, C.b.as<XT>(), lmc,
+                       live_blocks(lmc, grid_for(L.nc, 256), 1));
             vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
             level_op<XT, VK_POST, NR>(c, L, b, nullptr, L.agg.as<int32_t>(), C.x.as<XT>(), x, L.nc);
         } else {
@@ -1242,14 +1255,16 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
             MDS_LAUNCH(c, KC_NONE, tb + sizeof(XT) * NR * (double)n, (k_sa_prolong<XT, NR>), grid_for(n, 256), 256, 0,
                        n, L.P.rowp(), L.P.cols(), pv, C.x.as<XT>(), y);
         } else {
+            const LiveMap lmc = level_live(c, C);
             level_op<XT, VK_RESID, NR>(c, L, b, y, nullptr, nullptr, r, 0);
             MDS_LAUNCH(c, L.timed_level ? KC_VC_RESTRICT : KC_NONE, rbytes * level_live(c, L).frac,
-                       (k_vc_restrict<XT, NR>), stride_grid(c, k_vc_restrict<XT, NR>, 256, grid_for(L.nc, 256)),
-                       256, 0, L.nc, L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r, C.b.as<XT>(), level_live(c, C),
-                       (int64_t)grid_for(L.nc, 256));
+                       (k_vc_restrict<XT, NR>), stride_grid(c, k_vc_restrict<XT, NR>, 256, live_blocks(lmc, grid_for(L.nc, 256), 1)),
+                       256, 0, L.nc, L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r, C.b.as<XT>(), lmc,
+                       live_blocks(lmc, grid_for(L.nc, 256), 1));
             vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
-            MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n * NR, (k_vc_prolong<XT, NR>), ew_blocks(n), 256, 0, n,
-                       L.agg.as<int32_t>(), C.x.as<XT>(), y, ew_rows(n), level_live(c, L));
+            const LiveMap lml = level_live(c, L);
+            MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * n * NR, (k_vc_prolong<XT, NR>), ew_blocks(n, lml), 256, 0, n,
+                       L.agg.as<int32_t>(), C.x.as<XT>(), y, ew_rows(n, lml), lml);
         }
     }
     smooth_stored<XT, NR>(c, h, L, b, y, x);  // x = S(y; b)
