@@ -389,20 +389,30 @@ def run_gpu(args):
                                    fc_kf=pinned(b.fc_kf), fc_a=pinned(b.fc_a), pD_left=pinned(b.pD_left),
                                    pD_right=pinned(b.pD_right)) for b in batch]
     xh = pinned(np.zeros(N * NRHS))
-    e2e_steps = 2
+
+    def e2e_step():
+        s = ctx.assemble_batch(batch_h)
+        p = ctx.setup(s, precision="bf16", format="auto")
+        code, _ = ctx.solve(s, p, None, xh, x0_zero=True, **sopt)  # x is output only
+        p.close()
+        s.close()
+        if code != 0:
+            raise RuntimeError(f"end-to-end batch solve returned {code}")
+
+    # untimed warm-up steps: the first host-array step grows the context's
+    # memory pool for the staged inputs and the host solution
+    e2e_warmup, e2e_steps = 2, 3
+    for _ in range(e2e_warmup):
+        e2e_step()
     e2e_t = 0.0
     for _ in range(e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s = ctx.assemble_batch(batch_h)
-        p = ctx.setup(s, precision="bf16", format="auto")
-        xh[:] = 0.0
-        code, _ = ctx.solve(s, p, None, xh, **sopt)
-        p.close()
-        s.close()
+        e2e_step()
+        torch.cuda.synchronize()
         e2e_t += time.perf_counter() - t0
     h2d = sum(b.km.nbytes + b.fc_axis.nbytes + b.fc_pos.nbytes + b.fc_kf.nbytes + b.fc_a.nbytes +
-              b.pD_left.nbytes + b.pD_right.nbytes for b in batch) + 8 * N * NRHS
+              b.pD_left.nbytes + b.pD_right.nbytes for b in batch)
     d2h = 8 * N * NRHS
     e2e_t, e2e_solves = sharding.reduce_over_ranks(e2e_t, len(batch) * NRHS * e2e_steps)
 
@@ -435,7 +445,8 @@ def run_gpu(args):
         "accuracy": accuracy,
         "roofline": roof,
         "e2e": {"value": e2e_solves / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "host_buffers": "pinned; instance arrays in, 1,024 solution columns out, every step; host clock"},
+                "host_buffers": "pinned; instance arrays in, 1,024 solution columns out (zero initial guess: x is "
+                                "output only), every step; host clock", "steps": e2e_steps, "warmup": e2e_warmup},
         "gpu_launches": launches,
         "clocks": clk,
     }

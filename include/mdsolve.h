@@ -327,6 +327,9 @@ typedef struct {
     double reorth_eta2;  /* FGMRES runs a second classical Gram-Schmidt pass when
                             ||w_new||^2 < reorth_eta2 ||w||^2 (1e-8; 0.5 = the DGKS rule,
                             >= 1 always); batched solves decide per problem */
+    int x0_zero;         /* 1 = the initial guess is zero (the paper's x0, Sec. 4) and x is
+                            output only: its contents are not read, and a host x is not
+                            copied to the device (0: x holds x0) */
 } mds_solve_opts;
 
 typedef struct {

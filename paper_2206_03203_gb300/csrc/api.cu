@@ -753,6 +753,7 @@ int mds_solve_opts_default(mds_solve_opts *o) {
     o->graphs = 1;
     o->batched = 1;
     o->reorth_eta2 = 1e-8;
+    o->x0_zero = 0;
     return MDS_OK;
 }
 
@@ -787,9 +788,10 @@ static int solve_impl(mds_ctx ctx, mds_system sys, mds_precond prec, const doubl
     }
     if (!xdev) {
         xst = Buf(c, bytes);
-        MDS_CUDA(cudaMemcpyAsync(xst.p, x, bytes, cudaMemcpyHostToDevice, c->stream));
+        if (!o.x0_zero) MDS_CUDA(cudaMemcpyAsync(xst.p, x, bytes, cudaMemcpyHostToDevice, c->stream));
         Xd = xst.as<double>();
     }
+    if (o.x0_zero) MDS_CUDA(cudaMemsetAsync(Xd, 0, bytes, c->stream));
     bool batched = sys->n_inst > 1 || (nrhs > 1 && o.batched);
     if (batched) {
         MDS_REQUIRE(o.krylov == MDS_KRYLOV_FGMRES, MDS_ERR_INVALID, "batched solves run FGMRES");
@@ -998,6 +1000,7 @@ int mds_solve_noalloc(mds_ctx ctx, mds_system sys, mds_precond prec, const doubl
     const double *B = b ? b : sys->b;
     MDS_REQUIRE(is_device_ptr(B) && is_device_ptr(x), MDS_ERR_INVALID,
                 "mds_solve_noalloc needs device pointers for b and x");
+    if (o.x0_zero) MDS_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, c->stream));
     size_t need = fgmres_workspace_doubles(n, o.restart);
     MDS_REQUIRE(need <= noalloc_scratch_doubles(), MDS_ERR_INVALID, "mds_solve_noalloc: workspace exceeds the array");
     FgmresWorkspace ws = fgmres_workspace_carve(noalloc_scratch(*c), n, o.restart);

@@ -72,7 +72,8 @@ class SetupOpts(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("krylov", C.c_int), ("restart", C.c_int), ("rtol", C.c_double), ("max_iters", C.c_int),
-                ("use_precond", C.c_int), ("graphs", C.c_int), ("batched", C.c_int), ("reorth_eta2", C.c_double)]
+                ("use_precond", C.c_int), ("graphs", C.c_int), ("batched", C.c_int), ("reorth_eta2", C.c_double),
+                ("x0_zero", C.c_int)]
 
 
 class RhsStats(C.Structure):
@@ -388,7 +389,8 @@ class Context:
 
     def solve(self, sys: "System", prec: Optional["Precond"], b=None, x=None, nrhs: int = 1, **opts):
         """Solve on device tensors (or host numpy arrays).  x holds x0 and is
-        overwritten.  Returns (status, [Stats])."""
+        overwritten (x0_zero=True: the initial guess is zero and x is output
+        only).  Returns (status, [Stats])."""
         o = solve_opts(**opts)
         st = (RhsStats * (nrhs * sys.n_inst))()
         code = lib().mds_solve(self.h, sys.h, prec.h if prec is not None else None, C.c_void_p(_ptr(b)),

@@ -56,7 +56,7 @@ def test_default_options(built):
     o = mdsolve.setup_opts()
     assert o.theta < 0 and o.n_coarse == 512 and o.max_levels == 25  # theta resolved by mds_setup
     s = mdsolve.solve_opts()
-    assert s.restart == 30 and s.rtol == 1e-8
+    assert s.restart == 30 and s.rtol == 1e-8 and s.x0_zero == 0
 
 
 def test_sm103a_target_in_build_flags():

@@ -905,3 +905,24 @@ def test_batched_graphs_match_direct_launches(ctx, torch_mod, precision):
         its.append([q.iterations for q in st])
     assert its[0] == its[1] and max(its[0]) > 20  # several restart cycles replayed
     assert torch.equal(xs[0], xs[1])
+
+
+def test_zero_initial_guess_option(ctx, torch_mod):
+    """x0_zero: x is output only.  Host and device x filled with garbage give,
+    bit for bit, the solution of the solve from an explicitly zeroed x, for a
+    single instance and a packed batch."""
+    torch = torch_mod
+    for sys_ in (ctx.assemble(CASES["seg2d-96"]()),
+                 ctx.assemble_batch([inputs.random_rects_3d(n, 7, k, 2, nrhs=2) for k, n in enumerate([9, 11, 8])])):
+        nr = sys_.nrhs
+        prec = ctx.setup(sys_, precision="bf16")
+        ref = torch.zeros(sys_.N * nr, dtype=torch.float64, device="cuda")
+        c0, s0 = ctx.solve(sys_, prec, None, ref, nrhs=nr)
+        xd = torch.full_like(ref, float("nan"))
+        c1, s1 = ctx.solve(sys_, prec, None, xd, nrhs=nr, x0_zero=True)
+        xh = np.full(sys_.N * nr, 1e300)
+        c2, s2 = ctx.solve(sys_, prec, None, xh, nrhs=nr, x0_zero=True)
+        assert c0 == c1 == c2 == 0
+        assert [q.iterations for q in s0] == [q.iterations for q in s1] == [q.iterations for q in s2]
+        assert torch.equal(xd, ref)
+        assert np.array_equal(xh, ref.cpu().numpy())
