@@ -225,6 +225,12 @@ int mds_system_view(mds_system sys, mds_csr blocks[5], const double **b);
                                    (a 5- or 7-point stencil per Cartesian instance) stored by
                                    diagonals, no column indices; CSR on the other levels.
                                    MDS_FORMAT_AUTO uses it there too when it times fastest */
+#define MDS_FORMAT_STENCIL_BULK 4  /* MDS_FORMAT_STENCIL whose kernel stages each 256-row block's
+                                      coefficient planes and the window of the vector its
+                                      neighbours at +-1 and +-s read into shared memory by bulk
+                                      asynchronous copies (cp.async.bulk, mbarrier completion);
+                                      the same results bit for bit.  MDS_FORMAT_AUTO times it as a
+                                      candidate where it applies (vectors of 16-byte rows) */
 #define MDS_BLOCK_LOWER 0       /* M_L, Eq. (8), Algorithm 1 */
 #define MDS_BLOCK_DIAG 1        /* block diagonal B_D with Q blocks */
 #define MDS_BLOCK_UPPER 2       /* block upper triangular B_U with Q blocks */

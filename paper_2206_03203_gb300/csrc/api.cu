@@ -90,6 +90,7 @@ void Ctx::check_err(const char *where) {
     if (e & DERR_CAPACITY) throw Error(MDS_ERR_CAPACITY, w + ": a row exceeded the kernel's row capacity");
     if (e & DERR_NOT_SPD) throw Error(MDS_ERR_NOT_SPD, w + ": non-positive pivot");
     if (e & DERR_ZERO_DIAG) throw Error(MDS_ERR_ZERO_DIAG, w + ": zero diagonal");
+    if (e & DERR_TIMEOUT) throw Error(MDS_ERR_TIMEOUT, w + ": an asynchronous copy did not complete");
     throw Error(MDS_ERR_NONFINITE, w + ": non-finite value");
 }
 
@@ -482,7 +483,7 @@ int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_preco
                 MDS_ERR_INVALID, "unknown precision");
     MDS_REQUIRE(o.smoother == MDS_SMOOTHER_L1JACOBI || o.smoother == MDS_SMOOTHER_CHEBYSHEV, MDS_ERR_INVALID,
                 "unknown smoother");
-    MDS_REQUIRE(o.format >= MDS_FORMAT_AUTO && o.format <= MDS_FORMAT_STENCIL, MDS_ERR_INVALID, "unknown format");
+    MDS_REQUIRE(o.format >= MDS_FORMAT_AUTO && o.format <= MDS_FORMAT_STENCIL_BULK, MDS_ERR_INVALID, "unknown format");
     MDS_REQUIRE(o.sell_c == 8 || o.sell_c == 16 || o.sell_c == 32, MDS_ERR_INVALID, "sell_c must be 8, 16 or 32");
     MDS_REQUIRE(o.sell_sigma == 1 || (o.sell_sigma % o.sell_c == 0 && o.sell_sigma <= 1024), MDS_ERR_INVALID,
                 "sell_sigma must be 1 or a multiple of sell_c up to 1024");
@@ -600,7 +601,10 @@ int mds_precond_level_storage(mds_precond p, int block, int level, int *value_ty
     if (values) *values = dense_last ? nullptr : L.vt == VT_F64 ? (const void *)L.A.vals() : L.vals_lp.p;
     if (row_scale) *row_scale = L.rscale.p ? L.rscale.as<float>() : nullptr;
     if (dinv) *dinv = L.dinv.p;
-    if (format) *format = L.fmt == FMT_DIA ? MDS_FORMAT_STENCIL : L.fmt == FMT_SELL ? MDS_FORMAT_SELL : MDS_FORMAT_CSR;
+    if (format)
+        *format = L.fmt == FMT_DIA    ? (L.dia_bulk ? MDS_FORMAT_STENCIL_BULK : MDS_FORMAT_STENCIL)
+                  : L.fmt == FMT_SELL ? MDS_FORMAT_SELL
+                                      : MDS_FORMAT_CSR;
     return MDS_OK;
 }
 

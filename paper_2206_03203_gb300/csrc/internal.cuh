@@ -67,6 +67,7 @@ enum : int {
     DERR_NOT_SPD = 8,
     DERR_ZERO_DIAG = 16,
     DERR_NONFINITE = 32,
+    DERR_TIMEOUT = 64,  // an asynchronous copy did not complete within its time limit
 };
 
 // Kernel classes for event timing (match the C ABI's numbering).
@@ -511,7 +512,9 @@ struct Level {
     // stencil storage (FMT_DIA): plane d holds each row's coefficient of the
     // neighbour at offset o_d (ascending), zero where the row has none
     int dia_D = 0;         // 5 (2D) or 7 (3D); 0: the level is no stencil
-    Buf dia_val;           // [dia_D][n] in the storage type
+    int64_t dia_stride = 0;  // rows per plane (n padded to a multiple of 32)
+    bool dia_bulk = false;   // stencil kernel staging each row block by bulk copies
+    Buf dia_val;           // [dia_D][dia_stride] in the storage type
     Buf dia_seg;           // int64 [K + 1] instance row offsets
     Buf dia_side;          // int32 [K] cells per side
     Buf dia_ck;            // int32 [4 chunks]: (first row, last row, cells per side, instance) of the

@@ -202,7 +202,8 @@ static void drop_sell(Level &L) {
 template <class VT>
 __global__ void k_dia_build(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                             const double *__restrict__ v, int D, const int64_t *__restrict__ seg,
-                            const int32_t *__restrict__ side, int K, VT *__restrict__ planes, int *bad) {
+                            const int32_t *__restrict__ side, int K, VT *__restrict__ planes, int64_t stride,
+                            int *bad) {
     mds_pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -223,7 +224,7 @@ __global__ void k_dia_build(int64_t n, const int32_t *__restrict__ rp, const int
             atomicOr(bad, 1);
             return;
         }
-        planes[(int64_t)d * n + i] = from_d<VT>(v[p], 1.0);
+        planes[(int64_t)d * stride + i] = from_d<VT>(v[p], 1.0);
     }
 }
 
@@ -235,8 +236,13 @@ static bool build_dia(Ctx &c, Level &L, const Hierarchy &h) {
     const int K = (int)h.st_side.size();
     if ((h.st_dim != 2 && h.st_dim != 3) || K < 1 || (int)h.seg[0].size() != K + 1 || n < 1) return false;
     size_t vsz = L.vt == VT_F64 ? sizeof(double) : sizeof(float);
-    L.dia_val = Buf(&c, vsz * (size_t)D * (size_t)n);
-    MDS_CUDA(cudaMemsetAsync(L.dia_val.p, 0, vsz * (size_t)D * (size_t)n, c.stream));
+    // planes padded to a multiple of 32 rows: every plane and every 256-row
+    // block of it starts on a 128-byte boundary (bulk copies), and a block's
+    // copy rounded up to 16 bytes stays inside its plane
+    const int64_t stride = (n + 31) / 32 * 32;
+    L.dia_val = Buf(&c, vsz * (size_t)D * (size_t)stride);
+    MDS_CUDA(cudaMemsetAsync(L.dia_val.p, 0, vsz * (size_t)D * (size_t)stride, c.stream));
+    L.dia_stride = stride;
     L.dia_seg = Buf(&c, sizeof(int64_t) * (size_t)(K + 1));
     L.dia_side = Buf(&c, sizeof(int32_t) * (size_t)K);
     MDS_CUDA(cudaMemcpyAsync(L.dia_seg.p, h.seg[0].data(), sizeof(int64_t) * (size_t)(K + 1), cudaMemcpyHostToDevice,
@@ -248,10 +254,10 @@ static bool build_dia(Ctx &c, Level &L, const Hierarchy &h) {
     MDS_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), c.stream));
     if (L.vt == VT_F64)
         MDS_LAUNCH(c, KC_NONE, 0, k_dia_build<double>, grid_for(n, 256), 256, 0, n, L.A.rowp(), L.A.cols(), L.A.vals(),
-                   D, L.dia_seg.as<int64_t>(), L.dia_side.as<int32_t>(), K, L.dia_val.as<double>(), bad.as<int>());
+                   D, L.dia_seg.as<int64_t>(), L.dia_side.as<int32_t>(), K, L.dia_val.as<double>(), stride, bad.as<int>());
     else
         MDS_LAUNCH(c, KC_NONE, 0, k_dia_build<float>, grid_for(n, 256), 256, 0, n, L.A.rowp(), L.A.cols(), L.A.vals(),
-                   D, L.dia_seg.as<int64_t>(), L.dia_side.as<int32_t>(), K, L.dia_val.as<float>(), bad.as<int>());
+                   D, L.dia_seg.as<int64_t>(), L.dia_side.as<int32_t>(), K, L.dia_val.as<float>(), stride, bad.as<int>());
     if (c.read(bad.as<int>()) != 0) {
         L.dia_val.reset();
         L.dia_seg.reset();
@@ -284,11 +290,19 @@ static bool build_dia(Ctx &c, Level &L, const Hierarchy &h) {
 }
 
 static void drop_dia(Level &L) {
+    L.dia_bulk = false;
     L.dia_val.reset();
     L.dia_seg.reset();
     L.dia_side.reset();
     L.dia_ck.reset();
     L.dia_D = 0;
+}
+
+// The bulk-staged stencil kernel applies to vectors whose interleaved rows
+// are multiples of 16 bytes (FP32 with 4 or 8 columns, FP64 with 2, 4 or 8).
+static bool dia_bulk_ok(const Level &L, int nr, size_t xsize) {
+    return L.dia_D > 0 && (nr * xsize) % 16 == 0 && L.dia_stride % 32 == 0 &&
+           (reinterpret_cast<uintptr_t>(L.dia_val.p) & 15) == 0;
 }
 
 static int default_g(const Level &L) {
@@ -311,10 +325,12 @@ template <class XT> static void autotune_level(Ctx &c, Level &L, int nr, void *x
         const TuneChoice &t = it->second;
         if (t.fmt == FMT_SELL)
             build_sell_vt(c, L, t.C, t.sigma);
-        else if (t.fmt == FMT_DIA && L.dia_D > 0)
+        else if (t.fmt == FMT_DIA && L.dia_D > 0) {
             L.fmt = FMT_DIA;
-        else
+            L.dia_bulk = t.C == 1;
+        } else {
             L.G = t.G;
+        }
         if (L.fmt != FMT_DIA) drop_dia(L);
         return;
     }
@@ -350,21 +366,28 @@ template <class XT> static void autotune_level(Ctx &c, Level &L, int nr, void *x
         drop_sell(L);
     }
     if (L.dia_D > 0) {
-        L.fmt = FMT_DIA;
-        float t = time_level(c, L);
-        if (t < tbest) {
-            tbest = t;
-            best = TuneChoice{FMT_DIA, 0, 32, 1};
+        // stencil planes, read directly (C = 0) and staged by bulk copies (C = 1)
+        for (int bulk = 0; bulk < (dia_bulk_ok(L, nr, sizeof(XT)) ? 2 : 1); bulk++) {
+            L.fmt = FMT_DIA;
+            L.dia_bulk = bulk != 0;
+            float t = time_level(c, L);
+            if (t < tbest) {
+                tbest = t;
+                best = TuneChoice{FMT_DIA, 0, bulk, 1};
+            }
         }
         L.fmt = FMT_CSR;
+        L.dia_bulk = false;
     }
     c.tune_cache[key] = best;
     L.G = best.fmt == FMT_CSR ? best.G : default_g(L);
     if (best.fmt == FMT_SELL) build_sell_vt(c, L, best.C, best.sigma);
-    if (best.fmt == FMT_DIA)
+    if (best.fmt == FMT_DIA) {
         L.fmt = FMT_DIA;
-    else
+        L.dia_bulk = best.C == 1;
+    } else {
         drop_dia(L);
+    }
 }
 
 void level_storage(Ctx &c, Hierarchy &h, const mds_setup_opts &o) {
@@ -405,10 +428,14 @@ void level_storage(Ctx &c, Hierarchy &h, const mds_setup_opts &o) {
                        L.vals_lp.as<__half>());
         }
         const bool stencil_ok = l == 0 && h.st_dim > 0 && (L.vt == VT_F32 || L.vt == VT_F64) &&
-                                (o.format == MDS_FORMAT_STENCIL || o.format == MDS_FORMAT_AUTO);
+                                (o.format == MDS_FORMAT_STENCIL || o.format == MDS_FORMAT_STENCIL_BULK ||
+                                 o.format == MDS_FORMAT_AUTO);
         if (stencil_ok) build_dia(c, L, h);
-        if (o.format == MDS_FORMAT_STENCIL) {
+        if (o.format == MDS_FORMAT_STENCIL || o.format == MDS_FORMAT_STENCIL_BULK) {
             if (L.dia_D > 0) L.fmt = FMT_DIA;
+            // staged only where the kernel applies (16-byte vector rows); else read directly
+            L.dia_bulk = L.dia_D > 0 && o.format == MDS_FORMAT_STENCIL_BULK &&
+                         dia_bulk_ok(L, h.nr_cap, h.prec == 64 ? sizeof(double) : sizeof(float));
         } else if (o.format == MDS_FORMAT_SELL) {
             build_sell_vt(c, L, o.sell_c, o.sell_sigma);
         } else if (o.format == MDS_FORMAT_AUTO && n >= 20000) {

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(PKG, "_build", "libmdsolve.so")
 MDS_OK = 0
 MDS_WARN_NOT_CONVERGED = 1
 PREC = {"fp64": 64, "fp32": 32, "bf16": 16, "fp16": 17}
-FORMAT = {"auto": 0, "csr": 1, "sell": 2, "stencil": 3}
+FORMAT = {"auto": 0, "csr": 1, "sell": 2, "stencil": 3, "stencil-bulk": 4}
 PROLONG = {"piecewise": 0, "smoothed": 1}
 SMOOTHER = {"l1jacobi": 0, "chebyshev": 1}
 KIND = {"lower": 0, "diag": 1, "upper": 2}
@@ -610,10 +610,11 @@ class Precond:
         return vt.value, v, r, d
 
     def level_format(self, block: int, level: int) -> str:
-        """Storage format the V-cycle reads on a level: csr, sell or stencil."""
+        """Storage format the V-cycle reads on a level: csr, sell, stencil or
+        stencil-bulk (stencil planes staged by bulk copies)."""
         fmt = C.c_int()
         self.ctx._check(lib().mds_precond_level_storage(self.h, block, level, None, None, None, None, C.byref(fmt)))
-        return {1: "csr", 2: "sell", 3: "stencil"}.get(fmt.value, str(fmt.value))
+        return {1: "csr", 2: "sell", 3: "stencil", 4: "stencil-bulk"}.get(fmt.value, str(fmt.value))
 
     def level_host(self, block: int, level: int):
         A = Csr()

@@ -884,6 +884,29 @@ def test_stencil_storage_is_csr_bit_for_bit(ctx, torch_mod, case, precision):
     assert torch.equal(xs, xc)
 
 
+@pytest.mark.parametrize("precision,nr", [("bf16", 4), ("fp32", 4), ("fp64", 2), ("fp64", 4)])
+def test_stencil_bulk_staging_is_csr_bit_for_bit(ctx, torch_mod, precision, nr):
+    """The stencil kernel that stages each row block's planes and its
+    neighbours' window by bulk asynchronous copies (vectors of 16-byte
+    rows: FP32 with 4 columns, FP64 with 2 or 4) gives the CSR results bit
+    for bit: a packed batch of uneven 3D instances (instances of different
+    cells per side, blocks straddling two instances), whole lockstep solves."""
+    torch = torch_mod
+    insts = [inputs.random_rects_3d(n, 22060304, k, 1 + k % 3, nrhs=nr, random_dirichlet=True)
+             for k, n in enumerate([9, 12, 7, 10, 23])]
+    sys_ = ctx.assemble_batch(insts)
+    ps = ctx.setup(sys_, precision=precision, format="stencil-bulk")
+    pc = ctx.setup(sys_, precision=precision, format="csr")
+    assert ps.level_format(0, 0) == "stencil-bulk" and pc.level_format(0, 0) == "csr"
+    xs = torch.zeros(sys_.N * nr, dtype=torch.float64, device="cuda")
+    xc = torch.zeros_like(xs)
+    c1, s1 = ctx.solve(sys_, ps, None, xs, nrhs=nr, max_iters=3000)
+    c2, s2 = ctx.solve(sys_, pc, None, xc, nrhs=nr, max_iters=3000)
+    assert c1 == c2 == 0
+    assert [q.iterations for q in s1] == [q.iterations for q in s2]
+    assert torch.equal(xs, xc)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "bf16"])
 def test_batched_graphs_match_direct_launches(ctx, torch_mod, precision):
     """The lockstep batched FGMRES replays each Arnoldi step as a CUDA graph
