@@ -411,6 +411,25 @@ def run_gpu(args):
         e2e_step()
         torch.cuda.synchronize()
         e2e_t += time.perf_counter() - t0
+    # one more step with a synchronisation after each phase: where the
+    # end-to-end time goes (not part of the value)
+    e2e_phases = {}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s_ = ctx.assemble_batch(batch_h)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    p_ = ctx.setup(s_, precision="bf16", format="auto")
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    ctx.solve(s_, p_, None, xh, x0_zero=True, **sopt)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    p_.close()
+    s_.close()
+    t4 = time.perf_counter()
+    e2e_phases = {"assemble_from_host_ms": (t1 - t0) * 1e3, "setup_ms": (t2 - t1) * 1e3,
+                  "solve_to_host_ms": (t3 - t2) * 1e3, "release_ms": (t4 - t3) * 1e3}
     h2d = sum(b.km.nbytes + b.fc_axis.nbytes + b.fc_pos.nbytes + b.fc_kf.nbytes + b.fc_a.nbytes +
               b.pD_left.nbytes + b.pD_right.nbytes for b in batch)
     d2h = 8 * N * NRHS
@@ -446,7 +465,8 @@ def run_gpu(args):
         "roofline": roof,
         "e2e": {"value": e2e_solves / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "host_buffers": "pinned; instance arrays in, 1,024 solution columns out (zero initial guess: x is "
-                                "output only), every step; host clock", "steps": e2e_steps, "warmup": e2e_warmup},
+                                "output only), every step; host clock", "steps": e2e_steps, "warmup": e2e_warmup,
+                "phases_one_more_step": e2e_phases},
         "gpu_launches": launches,
         "clocks": clk,
     }

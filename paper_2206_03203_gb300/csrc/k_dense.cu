@@ -177,46 +177,55 @@ __global__ void k_chol_inverse(const double *__restrict__ Lall, const double *__
     for (int64_t i = lane; i < n; i += 32) X[j * n + i] = y[i];
 }
 
-// Columns j0 .. j0 + 31 of A^-1 for one block (one thread block per 32-column
-// tile, 256 threads): L Y = E, then L^T X = Y, by 32-row panels with the
-// 32 right-hand sides in shared memory (row stride 33).  Each panel first
-// takes the product of the finished panels (every lane one column, every
-// warp four rows: FP64 products from shared memory, no reductions), then a
-// warp solves the panel's 32 x 32 triangle (right-looking, column per lane).
-// A^-1 is symmetric: the tile writes rows j0 .. j0 + 31 of the inverse.
-constexpr int INV_PAD = 33;
+// Columns j0 .. j0 + CW - 1 of A^-1 for one block (one thread block per
+// CW-column tile, 256 threads): L Y = E, then L^T X = Y, by 32-row panels
+// with the CW right-hand sides in shared memory (row stride CW + 1).  Each
+// panel first takes the product of the finished panels (a group of CW
+// lanes per 32 / (256 / CW) rows, one column per lane: FP64 products from
+// shared memory, no reductions), then CW lanes solve the panel's 32 x 32
+// triangle (right-looking, column per lane).  A^-1 is symmetric: the tile
+// writes rows j0 .. j0 + CW - 1 of the inverse.  CW = 16 keeps a block's
+// shared memory at 136 n bytes, so that two or more blocks share an SM.
+constexpr int INV_CW = 16;
+template <int CW>
 __global__ void __launch_bounds__(256) k_chol_inv_tiles(const double *__restrict__ Lall, const DBlk *__restrict__ blk,
                                                         const int2 *__restrict__ tiles, double *__restrict__ Xall) {
+    constexpr int P = CW + 1;          // row stride of Y
+    constexpr int RG = 32 * CW / 256;  // panel rows per lane group
     mds_pdl_entry();
-    extern __shared__ double Y[];  // [n][INV_PAD]
+    extern __shared__ double Y[];  // [n][P]
     __shared__ double T[32][33];   // the panel's diagonal block of L
     const int2 tl = tiles[blockIdx.x];
     const DBlk b = blk[tl.x];
-    const int n = b.n, j0 = tl.y, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int n = b.n, j0 = tl.y, tid = threadIdx.x, c = tid % CW, g = tid / CW;
     const double *L = Lall + b.off;
     double *X = Xall + b.off;
-    for (int e = tid; e < n * 32; e += blockDim.x) {
-        const int i = e >> 5, c = e & 31;
-        Y[i * INV_PAD + c] = i == j0 + c ? 1.0 : 0.0;
+    for (int e = tid; e < n * CW; e += blockDim.x) {
+        const int i = e / CW, cc = e % CW;
+        Y[i * P + cc] = i == j0 + cc ? 1.0 : 0.0;
     }
     __syncthreads();
-    // forward: rows below j0 of Y stay zero
-    for (int p0 = j0; p0 < n; p0 += 32) {
+    // forward from the 32-row panel holding j0 (rows below j0 of Y are zero):
+    // the panels, and so every rounding, are those of a 32-column tile
+    const int jb = j0 / 32 * 32;
+    for (int p0 = jb; p0 < n; p0 += 32) {
         const int pn = min(32, n - p0);
-        if (p0 > j0) {
-            double acc[4] = {0.0, 0.0, 0.0, 0.0};
-            for (int k = j0; k < p0; k++) {
-                const double y = Y[k * INV_PAD + lane];
+        if (p0 > jb) {
+            double acc[RG];
 #pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const int r = w * 4 + q;
+            for (int q = 0; q < RG; q++) acc[q] = 0.0;
+            for (int k = jb; k < p0; k++) {
+                const double y = Y[k * P + c];
+#pragma unroll
+                for (int q = 0; q < RG; q++) {
+                    const int r = g * RG + q;
                     if (r < pn) acc[q] += L[(int64_t)(p0 + r) * n + k] * y;
                 }
             }
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int r = w * 4 + q;
-                if (r < pn) Y[(p0 + r) * INV_PAD + lane] -= acc[q];
+            for (int q = 0; q < RG; q++) {
+                const int r = g * RG + q;
+                if (r < pn) Y[(p0 + r) * P + c] -= acc[q];
             }
         }
         for (int e = tid; e < pn * pn; e += blockDim.x) {
@@ -224,37 +233,39 @@ __global__ void __launch_bounds__(256) k_chol_inv_tiles(const double *__restrict
             T[r][q] = q <= r ? L[(int64_t)(p0 + r) * n + p0 + q] : 0.0;
         }
         __syncthreads();
-        if (w == 0) {
+        if (tid < CW) {
             for (int i = 0; i < pn; i++) {
-                const double yi = Y[(p0 + i) * INV_PAD + lane] / T[i][i];
-                Y[(p0 + i) * INV_PAD + lane] = yi;
-                for (int k = i + 1; k < pn; k++) Y[(p0 + k) * INV_PAD + lane] -= T[k][i] * yi;
+                const double yi = Y[(p0 + i) * P + c] / T[i][i];
+                Y[(p0 + i) * P + c] = yi;
+                for (int k = i + 1; k < pn; k++) Y[(p0 + k) * P + c] -= T[k][i] * yi;
             }
         }
         __syncthreads();
     }
     // backward over every row, panels on the same 32-row grid as the forward
     // pass, from the last one up
-    const int top = j0 - ((j0 + 31) / 32) * 32;  // <= 0: the first panel may start above row 0
-    int last = j0;
+    int last = jb;
     while (last + 32 < n) last += 32;
+    const int top = 0;
     for (int s0 = last; s0 >= top; s0 -= 32) {
         const int a = max(s0, 0), e1 = min(s0 + 32, n), pn = e1 - a;
         if (pn <= 0) continue;
         if (e1 < n) {
-            double acc[4] = {0.0, 0.0, 0.0, 0.0};
-            for (int k = e1; k < n; k++) {
-                const double x = Y[k * INV_PAD + lane];
+            double acc[RG];
 #pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const int r = w * 4 + q;
+            for (int q = 0; q < RG; q++) acc[q] = 0.0;
+            for (int k = e1; k < n; k++) {
+                const double x = Y[k * P + c];
+#pragma unroll
+                for (int q = 0; q < RG; q++) {
+                    const int r = g * RG + q;
                     if (r < pn) acc[q] += L[(int64_t)k * n + a + r] * x;
                 }
             }
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int r = w * 4 + q;
-                if (r < pn) Y[(a + r) * INV_PAD + lane] -= acc[q];
+            for (int q = 0; q < RG; q++) {
+                const int r = g * RG + q;
+                if (r < pn) Y[(a + r) * P + c] -= acc[q];
             }
         }
         for (int e = tid; e < pn * pn; e += blockDim.x) {
@@ -262,19 +273,19 @@ __global__ void __launch_bounds__(256) k_chol_inv_tiles(const double *__restrict
             T[r][q] = q <= r ? L[(int64_t)(a + r) * n + a + q] : 0.0;
         }
         __syncthreads();
-        if (w == 0) {
+        if (tid < CW) {
             for (int i = pn - 1; i >= 0; i--) {
-                const double xi = Y[(a + i) * INV_PAD + lane] / T[i][i];
-                Y[(a + i) * INV_PAD + lane] = xi;
-                for (int k = 0; k < i; k++) Y[(a + k) * INV_PAD + lane] -= T[i][k] * xi;
+                const double xi = Y[(a + i) * P + c] / T[i][i];
+                Y[(a + i) * P + c] = xi;
+                for (int k = 0; k < i; k++) Y[(a + k) * P + c] -= T[i][k] * xi;
             }
         }
         __syncthreads();
     }
-    const int nc = min(32, n - j0);
+    const int nc = min(CW, n - j0);
     for (int e = tid; e < nc * n; e += blockDim.x) {
-        const int c = e / n, i = e % n;
-        X[(int64_t)(j0 + c) * n + i] = Y[i * INV_PAD + c];
+        const int cc = e / n, i = e % n;
+        X[(int64_t)(j0 + cc) * n + i] = Y[i * P + cc];
     }
 }
 
@@ -325,13 +336,21 @@ void dense_spd_inverse(Ctx &c, const mds_csr &A, const std::vector<int64_t> &seg
     }
     c.check_err("coarsest Cholesky");
     Ainv = Buf(&c, sizeof(double) * (size_t)tot);
-    const size_t tsmem = sizeof(double) * (size_t)nmax * INV_PAD;
+    const size_t tsmem = sizeof(double) * (size_t)nmax * (INV_CW + 1);
     if (tsmem <= 200 * 1024) {
+        // INV_CW-column tiles of every block
+        std::vector<int2> tl;
+        for (int k = 0; k < K; k++)
+            for (int32_t j = 0; j < hb[k].n; j += INV_CW) tl.push_back(make_int2(k, j));
+        Buf tiles(&c, sizeof(int2) * tl.size());
+        MDS_CUDA(cudaMemcpyAsync(tiles.p, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice, c.stream));
         // with the kernel's static panel tile, even a dynamic size under
         // 48 KB can take the block past the default limit: always opt in
-        MDS_CUDA(cudaFuncSetAttribute(k_chol_inv_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
-        MDS_LAUNCH(c, KC_NONE, 0, k_chol_inv_tiles, (unsigned)db.ntiles, 256, tsmem, D.as<double>(), B,
-                   db.tiles.as<int2>(), Ainv.as<double>());
+        MDS_CUDA(cudaFuncSetAttribute(k_chol_inv_tiles<INV_CW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)tsmem));
+        MDS_LAUNCH(c, KC_NONE, 0, k_chol_inv_tiles<INV_CW>, (unsigned)tl.size(), 256, tsmem, D.as<double>(), B,
+                   tiles.as<int2>(), Ainv.as<double>());
+        c.sync();  // the host tile list is released on return
         return;
     }
     Buf U(&c, sizeof(double) * (size_t)tot);
