@@ -705,6 +705,17 @@ void precond_apply(mds_precond p, const double *r, double *z, int nr) {
     }
 }
 
+// The device address of page-locked host memory mapped into the device's
+// address space (NULL for any other pointer).
+template <class T> static T *mapped_host_ptr(T *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer ? static_cast<T *>(a.devicePointer) : nullptr;
+}
+
 static bool is_device_ptr(const void *p) {
     if (!p) return true;
     cudaPointerAttributes a;
@@ -785,6 +796,17 @@ static int solve_impl(mds_ctx ctx, mds_system sys, mds_precond prec, const doubl
     const double *Bd = B;
     double *Xd = x;
     size_t bytes = sizeof(double) * (size_t)n * (size_t)nrhs;
+    bool batched = sys->n_inst > 1 || (nrhs > 1 && o.batched);
+    // A batched FGMRES reads x once (its initial guess, not at all when
+    // x0_zero) and writes it once at the end: page-locked host memory that
+    // the device can address is then read and written in place by those two
+    // kernels instead of through a device copy.
+    if (!xdev && batched && o.krylov == MDS_KRYLOV_FGMRES) {
+        if (double *mapped = mapped_host_ptr(x)) {
+            Xd = mapped;
+            xdev = true;
+        }
+    }
     if (!bdev) {
         bst = Buf(c, bytes);
         MDS_CUDA(cudaMemcpyAsync(bst.p, B, bytes, cudaMemcpyHostToDevice, c->stream));
@@ -795,8 +817,7 @@ static int solve_impl(mds_ctx ctx, mds_system sys, mds_precond prec, const doubl
         if (!o.x0_zero) MDS_CUDA(cudaMemcpyAsync(xst.p, x, bytes, cudaMemcpyHostToDevice, c->stream));
         Xd = xst.as<double>();
     }
-    if (o.x0_zero) MDS_CUDA(cudaMemsetAsync(Xd, 0, bytes, c->stream));
-    bool batched = sys->n_inst > 1 || (nrhs > 1 && o.batched);
+    if (o.x0_zero && !batched) MDS_CUDA(cudaMemsetAsync(Xd, 0, bytes, c->stream));
     if (batched) {
         MDS_REQUIRE(o.krylov == MDS_KRYLOV_FGMRES, MDS_ERR_INVALID, "batched solves run FGMRES");
         BatchPrecFn BM;

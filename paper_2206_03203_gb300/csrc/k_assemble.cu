@@ -753,16 +753,58 @@ static GridD grid_of(const mds_instance &in, bool flux, int64_t *faces) {
     return g;
 }
 
+// One copy segment of the batched host-to-device gather.
+struct CopySeg {
+    const uint4 *src;  // device address of page-locked host memory (16-byte aligned)
+    uint4 *dst;        // 16-byte aligned
+    int64_t bytes;
+};
+
+// All segments in one launch: block b copies segment b, its threads striding
+// over 16-byte units (the host arrays are read once over the host link) and
+// the last thread copying the bytes after the last full unit.
+__global__ void k_gather_segments(const CopySeg *__restrict__ seg) {
+    mds_pdl_entry();
+    const CopySeg g = seg[blockIdx.x];
+    const int64_t n16 = g.bytes / 16;
+    for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) g.dst[i] = g.src[i];
+    if (threadIdx.x == blockDim.x - 1)
+        for (int64_t b = n16 * 16; b < g.bytes; b++)
+            reinterpret_cast<char *>(g.dst)[b] = reinterpret_cast<const char *>(g.src)[b];
+}
+
 void assemble_batch_primal(Ctx &c, const mds_instance *inst, int K, SystemData &out) {
     MDS_REQUIRE(K >= 1 && K <= 65535, MDS_ERR_INVALID, "a batch holds 1 to 65535 instances");
     std::vector<BInst> hb(K);
     std::vector<int64_t> faces(K);
     std::vector<Buf> hold;
     hold.reserve((size_t)K * 8);
-    auto stg = [&](auto p, size_t count, bool dev) {
+    // Host arrays in page-locked memory the device can address are gathered
+    // by one kernel into one device buffer (instead of one copy call per
+    // array); the others are staged one copy each.
+    struct Pend {
+        const void *src;
+        size_t bytes;
+        const void **slot;
+    };
+    std::vector<Pend> pend;
+    size_t pend_bytes = 0;
+    // *dst = a device copy of p[0 .. count) (p itself when on the device)
+    auto stg = [&](auto **dst, auto p, size_t count, bool dev) {
         using T = std::remove_const_t<std::remove_pointer_t<decltype(p)>>;
+        if (!dev && count > 0) {
+            cudaPointerAttributes a;
+            if (cudaPointerGetAttributes(&a, p) == cudaSuccess && a.type == cudaMemoryTypeHost && a.devicePointer &&
+                (reinterpret_cast<uintptr_t>(a.devicePointer) & 15) == 0) {
+                pend.push_back(Pend{a.devicePointer, sizeof(T) * count, reinterpret_cast<const void **>(dst)});
+                pend_bytes += (sizeof(T) * count + 15) / 16 * 16;
+                *dst = nullptr;  // set after the gather
+                return;
+            }
+            cudaGetLastError();
+        }
         hold.emplace_back();
-        return stage<T>(c, p, count, dev, hold.back());
+        *dst = stage<T>(c, p, count, dev, hold.back());
     };
     out.nrhs = inst[0].nrhs;
     out.moff.assign(K + 1, 0);
@@ -777,15 +819,15 @@ void assemble_batch_primal(Ctx &c, const mds_instance *inst, int K, SystemData &
         GridD g = grid_of(in, false, &faces[k]);
         bool dev = in.on_device != 0;
         BInst &B = hb[k];
-        B.km = stg(in.km, (size_t)g.n_m, dev);
-        B.ax = stg(in.fc_axis, (size_t)g.nf, dev);
-        B.ps = stg(in.fc_pos, (size_t)(3 * g.nf), dev);
-        B.kf = stg(in.fc_kf, (size_t)g.nf, dev);
-        B.ap = stg(in.fc_a, (size_t)g.nf, dev);
-        B.pL = stg(in.pD_left, (size_t)(in.nrhs * g.nb), dev);
-        B.pR = stg(in.pD_right, (size_t)(in.nrhs * g.nb), dev);
-        g.kn = in.fc_kn ? stg(in.fc_kn, (size_t)g.nf, dev) : B.kf;
         B.g = g;
+        stg(&B.km, in.km, (size_t)g.n_m, dev);
+        stg(&B.ax, in.fc_axis, (size_t)g.nf, dev);
+        stg(&B.ps, in.fc_pos, (size_t)(3 * g.nf), dev);
+        stg(&B.kf, in.fc_kf, (size_t)g.nf, dev);
+        stg(&B.ap, in.fc_a, (size_t)g.nf, dev);
+        stg(&B.pL, in.pD_left, (size_t)(in.nrhs * g.nb), dev);
+        stg(&B.pR, in.pD_right, (size_t)(in.nrhs * g.nb), dev);
+        if (in.fc_kn) stg(&B.g.kn, in.fc_kn, (size_t)g.nf, dev);
         out.moff[k + 1] = out.moff[k] + g.n_m;
         out.foff[k + 1] = out.foff[k] + g.nf;
         out.stencil = out.stencil && in.dim == out.dim;
@@ -794,6 +836,24 @@ void assemble_batch_primal(Ctx &c, const mds_instance *inst, int K, SystemData &
         maxN = std::max(maxN, g.N);
         maxf = std::max(maxf, g.nf);
     }
+    if (!pend.empty()) {
+        Buf gath(&c, pend_bytes);
+        std::vector<CopySeg> segs;
+        size_t o = 0;
+        for (const Pend &q : pend) {
+            char *d = static_cast<char *>(gath.p) + o;
+            segs.push_back(CopySeg{static_cast<const uint4 *>(q.src), reinterpret_cast<uint4 *>(d), (int64_t)q.bytes});
+            *q.slot = d;
+            o += (q.bytes + 15) / 16 * 16;
+        }
+        Buf dseg(&c, sizeof(CopySeg) * segs.size());
+        MDS_CUDA(cudaMemcpyAsync(dseg.p, segs.data(), sizeof(CopySeg) * segs.size(), cudaMemcpyHostToDevice, c.stream));
+        MDS_LAUNCH(c, KC_NONE, 0, k_gather_segments, (unsigned)segs.size(), 256, 0, dseg.as<CopySeg>());
+        c.sync();  // the segment table is released on return
+        hold.push_back(std::move(gath));
+    }
+    for (int k = 0; k < K; k++)
+        if (!inst[k].fc_kn) hb[k].g.kn = hb[k].kf;  // the normal permeability defaults to k_f
     const int64_t NM = out.moff[K], NF = out.foff[K], N = NM + NF;
     MDS_REQUIRE(N < INT32_MAX, MDS_ERR_INVALID, "packed batch exceeds int32 indices");
     Buf map(&c, sizeof(int32_t) * (size_t)(total_faces > 0 ? total_faces : 1));

@@ -1340,7 +1340,10 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
     MDS_CUDA(cudaMemsetAsync(psc.p, 0, psc.bytes, c.stream));
     unsigned eg = red_grid(N * NR);
     MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, (k_to_interleaved<NR>), eg, RED_BLOCK, 0, N, Bcol, c0, Bi.as<double>());
-    MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, (k_to_interleaved<NR>), eg, RED_BLOCK, 0, N, Xcol, c0, Xi.as<double>());
+    if (o.x0_zero)  // the zero initial guess: X is output only
+        MDS_CUDA(cudaMemsetAsync(Xi.p, 0, sizeof(double) * (size_t)(N * NR), c.stream));
+    else
+        MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, (k_to_interleaved<NR>), eg, RED_BLOCK, 0, N, Xcol, c0, Xi.as<double>());
     dim3 pgrid((unsigned)P, 1);
     // per-problem squared norms of a vector into nsq[p * 32]
     auto norms = [&](const double *w, const int8_t *mk) {

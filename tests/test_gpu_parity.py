@@ -949,3 +949,37 @@ def test_zero_initial_guess_option(ctx, torch_mod):
         assert [q.iterations for q in s0] == [q.iterations for q in s1] == [q.iterations for q in s2]
         assert torch.equal(xd, ref)
         assert np.array_equal(xh, ref.cpu().numpy())
+
+
+def test_pinned_host_batch_paths(ctx, oracle_mod, torch_mod):
+    """A packed batch from page-locked host arrays (gathered by one kernel
+    that reads host memory) assembles the oracle's system bit for bit, and a
+    lockstep solve into a page-locked host x (written in place by the device)
+    equals the solve into a device x bit for bit, with x0 read from the
+    buffer and with x0_zero."""
+    torch = torch_mod
+
+    def pinned(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+    insts = [inputs.random_rects_3d(n, 22060304, k, 1 + k % 4, nrhs=2, random_dirichlet=True)
+             for k, n in enumerate([9, 12, 8, 14, 11])]
+    import dataclasses
+    ph = [dataclasses.replace(b, km=pinned(b.km), fc_axis=pinned(b.fc_axis), fc_pos=pinned(b.fc_pos),
+                              fc_kf=pinned(b.fc_kf), fc_a=pinned(b.fc_a), pD_left=pinned(b.pD_left),
+                              pD_right=pinned(b.pD_right)) for b in insts]
+    sys_ = ctx.assemble_batch(ph)
+    (_, _, _, _, A), b = sys_.to_host()
+    Ao, bo, NM = packed_oracle(oracle_mod, insts)
+    assert same_csr(A, Ao) and np.array_equal(b, bo)
+    prec = ctx.setup(sys_, precision="bf16")
+    xd = torch.zeros(2 * sys_.N, dtype=torch.float64, device="cuda")
+    c0, s0 = ctx.solve(sys_, prec, None, xd, nrhs=2)
+    xh = pinned(np.zeros(2 * sys_.N))
+    c1, s1 = ctx.solve(sys_, prec, None, xh, nrhs=2)
+    xz = pinned(np.full(2 * sys_.N, np.nan))
+    c2, s2 = ctx.solve(sys_, prec, None, xz, nrhs=2, x0_zero=True)
+    assert c0 == c1 == c2 == 0
+    assert [q.iterations for q in s0] == [q.iterations for q in s1] == [q.iterations for q in s2]
+    ref = xd.cpu().numpy()
+    assert np.array_equal(xh, ref) and np.array_equal(xz, ref)
