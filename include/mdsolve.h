@@ -229,8 +229,10 @@ int mds_system_view(mds_system sys, mds_csr blocks[5], const double **b);
                                       coefficient planes and the window of the vector its
                                       neighbours at +-1 and +-s read into shared memory by bulk
                                       asynchronous copies (cp.async.bulk, mbarrier completion);
-                                      the same results bit for bit.  MDS_FORMAT_AUTO times it as a
-                                      candidate where it applies (vectors of 16-byte rows) */
+                                      the same results bit for bit, where it applies (vectors of
+                                      16-byte rows; the direct kernel otherwise).  Slower than
+                                      MDS_FORMAT_STENCIL in a solve, so MDS_FORMAT_AUTO does not
+                                      choose it */
 #define MDS_BLOCK_LOWER 0       /* M_L, Eq. (8), Algorithm 1 */
 #define MDS_BLOCK_DIAG 1        /* block diagonal B_D with Q blocks */
 #define MDS_BLOCK_UPPER 2       /* block upper triangular B_U with Q blocks */

@@ -366,8 +366,11 @@ template <class XT> static void autotune_level(Ctx &c, Level &L, int nr, void *x
         drop_sell(L);
     }
     if (L.dia_D > 0) {
-        // stencil planes, read directly (C = 0) and staged by bulk copies (C = 1)
-        for (int bulk = 0; bulk < (dia_bulk_ok(L, nr, sizeof(XT)) ? 2 : 1); bulk++) {
+        // stencil planes read directly.  The bulk-staged form is not a
+        // candidate: timed alone it can tie with the direct kernel, in the
+        // solve (overlapped with its neighbours by programmatic dependent
+        // launch) it is 12-15% slower
+        for (int bulk = 0; bulk < 1; bulk++) {
             L.fmt = FMT_DIA;
             L.dia_bulk = bulk != 0;
             float t = time_level(c, L);
