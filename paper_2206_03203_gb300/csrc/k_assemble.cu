@@ -29,6 +29,7 @@ struct GridD {
     const int32_t *imem;      // [4 nI] members of each intersection, ascending
     const int32_t *phi_int;   // [nIF] intersection of each flux
     const double *kn;         // [nf] normal permeability (kappa = 2 kn / a)
+    const double *hk;         // [n_m] h / (2 k_m) of each matrix cell, or null (computed per use)
 };
 
 __device__ __forceinline__ int64_t face_id(const GridD &g, int d, int64_t x, int64_t y, int64_t z) {
@@ -44,6 +45,13 @@ __device__ __forceinline__ int32_t frac_at(const GridD &g, const int32_t *map, i
 
 __device__ __forceinline__ int64_t cell_id(const GridD &g, const int64_t c[3]) {
     return c[0] + (int64_t)g.n * (c[1] + (int64_t)g.n * c[2]);
+}
+
+// Half-cell resistance h / (2 k_m) of matrix cell j, the term each side of
+// a face contributes to the two-point transmissibility (the same division as
+// written inline, so the values are identical to the bit).
+__device__ __forceinline__ double half_res(const GridD &g, const double *km, int64_t j) {
+    return g.hk ? g.hk[j] : g.h / (2.0 * km[j]);
 }
 
 // Fracture cell k claims its face in the face map (error bits on a bad or
@@ -227,7 +235,7 @@ __device__ int fracture_entries(const GridD &g, const int32_t *map, const double
             row[cnt].t = -1.0;
         } else {
             row[cnt].c = (int32_t)j;
-            row[cnt].t = g.F / (g.h / (2.0 * km[j]) + 1.0 / kappa);
+            row[cnt].t = g.F / (half_res(g, km, j) + 1.0 / kappa);
         }
         cnt++;
     }
@@ -323,6 +331,113 @@ struct Remap {
     __device__ __forceinline__ int64_t operator()(int64_t j) const { return j < n_m ? mo + j : fbase + (j - n_m); }
 };
 
+__global__ void k_half_res(int64_t n_m, double h, const double *__restrict__ km, double *__restrict__ hk) {
+    mds_pdl_entry();
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_m) hk[i] = h / (2.0 * km[i]);
+}
+
+// Matrix row i: the faces are visited in ascending order of the neighbour
+// they lead to (-z, -y, -x, +x, +y, +z), so the matrix columns come out
+// sorted without a sort; fracture (or flux) columns, all above the matrix
+// block, follow in ascending order.  The diagonal sums the transmissibilities
+// in ascending column order and then the Dirichlet faces, as the general
+// path does.  Everything is held in registers (fixed slot per face).
+__device__ void fill_matrix_row(const GridD &g, const int32_t *map, const double *km, const double *ap, int nrhs,
+                                const double *pL, const double *pR, int64_t i, const Remap &rm, int64_t NT,
+                                const int32_t *rp, int32_t *ci, double *val, double *b) {
+    const int64_t n = g.n;
+    const int64_t c[3] = {i % n, (i / n) % n, g.dim == 3 ? i / (n * n) : 0};
+    const double ki = km[i];
+    const double ri = half_res(g, km, i);
+    int64_t col[6];
+    double t[6];
+    bool fr[6];
+    double tb[2] = {0.0, 0.0};
+    bool has[2] = {false, false};
+    int nmat = 0, nlow = 0, nfr = 0;
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+        const int d = q < 3 ? 2 - q : q - 3;
+        const int s = q < 3 ? 0 : 1;
+        col[q] = -1;
+        t[q] = 0.0;
+        fr[q] = false;
+        if (d >= g.dim) continue;
+        const int64_t plane = c[d] + s;
+        if (plane == 0 || plane == n) {
+            if (d == 0) {
+                tb[s] = (g.F * (2.0 * ki)) / g.h;
+                has[s] = true;
+            }
+            continue;
+        }
+        int64_t fc[3] = {c[0], c[1], c[2]};
+        fc[d] = plane;
+        const int32_t k = frac_at(g, map, d, fc);
+        if (k >= 0) {
+            const double kappa = (2.0 * g.kn[k]) / ap[k];
+            fr[q] = true;
+            nfr++;
+            if (g.flux) {
+                col[q] = g.NO + 2 * (int64_t)k + (s ? 0 : 1);
+                t[q] = 1.0;
+            } else {
+                col[q] = g.n_m + k;
+                t[q] = g.F / (ri + 1.0 / kappa);
+            }
+        } else {
+            int64_t nc[3] = {c[0], c[1], c[2]};
+            nc[d] = c[d] + (s ? 1 : -1);
+            const int64_t j = cell_id(g, nc);
+            col[q] = j;
+            t[q] = g.F / (ri + half_res(g, km, j));
+            nmat++;
+            nlow += s == 0 ? 1 : 0;
+        }
+    }
+    const int64_t oi = rm(i);
+    const int64_t p0 = rp[oi];
+    double diag = 0.0;
+    int64_t p = p0;
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+        if (col[q] < 0 || fr[q]) continue;
+        if (p == p0 + nlow) p++;  // the diagonal's place
+        ci[p] = (int32_t)rm(col[q]);
+        val[p++] = -t[q];
+        diag += t[q];
+    }
+    // fracture / flux columns: selection in ascending order (at most six)
+    int64_t last = -1;
+    for (int r = 0; r < nfr; r++) {
+        int64_t best = INT64_MAX;
+        double bt = 0.0;
+#pragma unroll
+        for (int q = 0; q < 6; q++)
+            if (fr[q] && col[q] > last && col[q] < best) {
+                best = col[q];
+                bt = t[q];
+            }
+        ci[p0 + nmat + 1 + r] = (int32_t)rm(best);
+        val[p0 + nmat + 1 + r] = best < g.NO ? -bt : bt;
+        if (best < g.NO) diag += bt;
+        last = best;
+    }
+    for (int s = 0; s < 2; s++)
+        if (has[s]) diag += tb[s];
+    ci[p0 + nlow] = (int32_t)oi;
+    val[p0 + nlow] = diag;
+    const int64_t bf = (i / n) % n + (g.dim == 3 ? n * (i / (n * n)) : 0);
+    for (int r = 0; r < nrhs; r++) {
+        const double *L = pL + (int64_t)r * g.nb, *R = pR + (int64_t)r * g.nb;
+        double acc = 0.0;
+        if (has[0]) acc += tb[0] * L[bf];
+        if (has[1]) acc += tb[1] * R[bf];
+        b[(int64_t)r * NT + oi] = acc;
+    }
+}
+
 // Row i of the primal system (a matrix or a fracture cell): its entries in
 // ascending column order, the diagonal, and its right-hand sides, written at
 // the remapped row and columns (entries from rp[row], b[r NT + row]).
@@ -330,6 +445,10 @@ __device__ void fill_primal_row(const GridD &g, const int32_t *map, const double
                                 const int32_t *pos, const double *kf, const double *ap, int nrhs, const double *pL,
                                 const double *pR, int64_t i, const Remap &rm, int64_t NT, const int32_t *rp,
                                 int32_t *ci, double *val, double *b) {
+    if (i < g.n_m) {
+        fill_matrix_row(g, map, km, ap, nrhs, pL, pR, i, rm, NT, rp, ci, val, b);
+        return;
+    }
     Ent row[16];
     double tb[2];
     int has[2];
@@ -675,8 +794,16 @@ struct BInst {
     const double *km, *kf, *ap, *pL, *pR;
     const int32_t *ax, *ps;
     int32_t *map;          // the instance's face map
+    double *hk;            // its half-cell resistances (g.hk points here)
     int64_t mo, fbase;     // packed rows of its first matrix cell and first fracture cell
 };
+
+__global__ void k_half_res_b(const BInst *__restrict__ bi) {
+    mds_pdl_entry();
+    const BInst &B = bi[blockIdx.y];
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < B.g.n_m) B.hk[i] = B.g.h / (2.0 * B.km[i]);
+}
 
 __global__ void k_map_scatter_b(const BInst *__restrict__ bi, int *err) {
     mds_pdl_entry();
@@ -858,9 +985,13 @@ void assemble_batch_primal(Ctx &c, const mds_instance *inst, int K, SystemData &
     MDS_REQUIRE(N < INT32_MAX, MDS_ERR_INVALID, "packed batch exceeds int32 indices");
     Buf map(&c, sizeof(int32_t) * (size_t)(total_faces > 0 ? total_faces : 1));
     fill_i32(c, map.as<int32_t>(), -1, total_faces);
-    int64_t at = 0;
+    Buf hk(&c, sizeof(double) * (size_t)(NM > 0 ? NM : 1));
+    int64_t at = 0, maxm = 0;
     for (int k = 0; k < K; k++) {
         hb[k].map = map.as<int32_t>() + at;
+        hb[k].hk = hk.as<double>() + out.moff[k];
+        hb[k].g.hk = hb[k].hk;
+        maxm = std::max(maxm, hb[k].g.n_m);
         at += faces[k];
         hb[k].mo = out.moff[k];
         hb[k].fbase = NM + out.foff[k];
@@ -872,6 +1003,7 @@ void assemble_batch_primal(Ctx &c, const mds_instance *inst, int K, SystemData &
     if (maxf > 0)
         MDS_LAUNCH(c, KC_NONE, 0, k_map_scatter_b, dim3(grid_for(maxf, 256), K), 256, 0, B, c.d_err);
     c.check_err("fracture list");
+    if (maxm > 0) MDS_LAUNCH(c, KC_NONE, 0, k_half_res_b, dim3(grid_for(maxm, 256), K), 256, 0, B);
     Buf cnt(&c, sizeof(int32_t) * (size_t)(N + 1));
     MDS_LAUNCH(c, KC_NONE, 0, k_count_b, dim3(grid_for(maxN, 128), K), 128, 0, B, cnt.as<int32_t>());
     DCsr &A = out.full;
@@ -944,6 +1076,9 @@ void assemble_instance(Ctx &c, const mds_instance &in, SystemData &out, bool flu
     g.phi_int = phi.p ? phi.as<int32_t>() : nullptr;
     MDS_REQUIRE(g.NT < INT32_MAX, MDS_ERR_INVALID, "too many unknowns for int32 indices");
 
+    Buf hk(&c, sizeof(double) * (size_t)(g.n_m > 0 ? g.n_m : 1));
+    if (g.n_m > 0) MDS_LAUNCH(c, KC_NONE, 0, k_half_res, grid_for(g.n_m, 256), 256, 0, g.n_m, g.h, km, hk.as<double>());
+    g.hk = hk.as<double>();
     Buf cnt(&c, sizeof(int32_t) * (size_t)(g.NT + 1));
     MDS_LAUNCH(c, KC_NONE, 0, k_count, grid_for(g.NT, 128), 128, 0, g, map.as<int32_t>(), km, ax, ps, kf, ap,
                cnt.as<int32_t>());

@@ -183,9 +183,12 @@ __global__ void k_chol_inverse(const double *__restrict__ Lall, const double *__
 // panel first takes the product of the finished panels (a group of CW
 // lanes per 32 / (256 / CW) rows, one column per lane: FP64 products from
 // shared memory, no reductions), then CW lanes solve the panel's 32 x 32
-// triangle (right-looking, column per lane).  A^-1 is symmetric: the tile
-// writes rows j0 .. j0 + CW - 1 of the inverse.  CW = 16 keeps a block's
-// shared memory at 136 n bytes, so that two or more blocks share an SM.
+// triangle (right-looking, column per lane).  A^-1 is symmetric, so the
+// backward pass stops at the 32-row panel holding j0 (half the products of
+// a full one): the tile writes the entries of its columns from that panel
+// down, and mirrors those of the later panels into the rows j0 .. j0 + CW - 1
+// of the other tiles' columns.  CW = 16 keeps a block's shared memory at
+// 136 n bytes, so that two or more blocks share an SM.
 constexpr int INV_CW = 16;
 template <int CW>
 __global__ void __launch_bounds__(256) k_chol_inv_tiles(const double *__restrict__ Lall, const DBlk *__restrict__ blk,
@@ -242,11 +245,13 @@ __global__ void __launch_bounds__(256) k_chol_inv_tiles(const double *__restrict
         }
         __syncthreads();
     }
-    // backward over every row, panels on the same 32-row grid as the forward
-    // pass, from the last one up
+    // backward over the rows from the panel holding j0 down (the same 32-row
+    // grid as the forward pass, from the last panel up): A^-1 is symmetric,
+    // so its entries above that panel are taken from the tiles owning their
+    // columns (written below as mirrored rows)
     int last = jb;
     while (last + 32 < n) last += 32;
-    const int top = 0;
+    const int top = jb;
     for (int s0 = last; s0 >= top; s0 -= 32) {
         const int a = max(s0, 0), e1 = min(s0 + 32, n), pn = e1 - a;
         if (pn <= 0) continue;
@@ -282,10 +287,19 @@ __global__ void __launch_bounds__(256) k_chol_inv_tiles(const double *__restrict
         }
         __syncthreads();
     }
-    const int nc = min(CW, n - j0);
-    for (int e = tid; e < nc * n; e += blockDim.x) {
-        const int cc = e / n, i = e % n;
+    // entry (i, j) of A^-1 goes to X[j n + i] for rows i >= jb, and, for
+    // rows in the later panels (i >= jb + 32), also to X[i n + j]: every
+    // entry is written once, by the tile whose column it is when i and j
+    // share a 32-row panel or i lies below, by the mirror otherwise
+    const int nc = min(CW, n - j0), nr = n - jb;
+    for (int e = tid; e < nc * nr; e += blockDim.x) {
+        const int cc = e / nr, i = jb + e % nr;
         X[(int64_t)(j0 + cc) * n + i] = Y[i * P + cc];
+    }
+    const int nm = max(nr - 32, 0);
+    for (int e = tid; e < nc * nm; e += blockDim.x) {
+        const int i = jb + 32 + e / nc, cc = e % nc;
+        X[(int64_t)i * n + j0 + cc] = Y[i * P + cc];
     }
 }
 

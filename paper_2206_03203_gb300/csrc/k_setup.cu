@@ -198,11 +198,17 @@ __global__ void k_local_index(int64_t n, const int64_t *__restrict__ seg, int K,
     lid[i] = (int32_t)(i - seg[lo]);
 }
 
+// The rounds below run on 256-row blocks; act[b] = 0 marks a block that
+// holds no undecided vertex nor a strong neighbour of one, whose keys and
+// flags no later step reads (it returns at once).
+
 // m1_i = max key over undecided vertices of {i} and its strong neighbours
 __global__ void k_mis_max1(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                            const int8_t *__restrict__ g, const int8_t *__restrict__ state, uint64_t lkey,
-                           const int32_t *__restrict__ lid, uint64_t *__restrict__ m1) {
+                           const int32_t *__restrict__ lid, const int8_t *__restrict__ act,
+                           uint64_t *__restrict__ m1) {
     mds_pdl_entry();
+    if (!act[blockIdx.x]) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint64_t m = state[i] == 0 ? mis_key1(lkey, key_index(lid, i)) : 0;
@@ -221,8 +227,10 @@ __global__ void k_mis_max1(int64_t n, const int32_t *__restrict__ rp, const int3
 // two becomes a root
 __global__ void k_mis_select(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                              const int8_t *__restrict__ g, const uint64_t *__restrict__ m1, uint64_t lkey,
-                             const int32_t *__restrict__ lid, int8_t *__restrict__ state) {
+                             const int32_t *__restrict__ lid, const int8_t *__restrict__ act,
+                             int8_t *__restrict__ state) {
     mds_pdl_entry();
+    if (!act[blockIdx.x]) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || state[i] != 0) return;
     uint64_t m = m1[i];
@@ -236,8 +244,9 @@ __global__ void k_mis_select(int64_t n, const int32_t *__restrict__ rp, const in
 
 __global__ void k_mis_near_root(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                 const int8_t *__restrict__ g, const int8_t *__restrict__ state,
-                                int8_t *__restrict__ e1) {
+                                const int8_t *__restrict__ act, int8_t *__restrict__ e1) {
     mds_pdl_entry();
+    if (!act[blockIdx.x]) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int8_t e = state[i] == 1;
@@ -248,17 +257,24 @@ __global__ void k_mis_near_root(int64_t n, const int32_t *__restrict__ rp, const
 
 __global__ void k_mis_exclude(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                               const int8_t *__restrict__ g, const int8_t *__restrict__ e1, int8_t *__restrict__ state,
+                              const int8_t *__restrict__ act, int8_t *__restrict__ act_next,
                               int32_t *__restrict__ undecided) {
     mds_pdl_entry();
+    if (!act[blockIdx.x]) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || state[i] != 0) return;
     bool ex = e1[i];
     for (int32_t p = rp[i]; p < rp[i + 1] && !ex; p++)
         if (g[p] && e1[ci[p]]) ex = true;
-    if (ex)
+    if (ex) {
         state[i] = 2;
-    else
+    } else {
         atomicAdd(undecided, 1);
+        // the next round reads the keys and flags of i and its strong neighbours
+        act_next[i >> 8] = 1;
+        for (int32_t p = rp[i]; p < rp[i + 1]; p++)
+            if (g[p]) act_next[ci[p] >> 8] = 1;
+    }
 }
 
 // ---------------------------------------------------------------- aggregation
@@ -349,13 +365,25 @@ __global__ void k_agg_sort(int64_t nc, const int32_t *__restrict__ off, int32_t 
     }
 }
 
+// Upper bound of the entries of coarse row I: those of its members' rows.
+__global__ void k_rap_bound(int64_t nc, const int32_t *__restrict__ off, const int32_t *__restrict__ mem,
+                            const int32_t *__restrict__ rp, int32_t *__restrict__ ub) {
+    mds_pdl_entry();
+    int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    int32_t u = 0;
+    for (int32_t q = off[I]; q < off[I + 1]; q++) u += rp[mem[q] + 1] - rp[mem[q]];
+    ub[I] = u;
+}
+
 // Coarse row I = sum over members i of I (ascending) of row i of A mapped
-// through agg, accumulated in CSR order.
-template <bool FILL>
+// through agg, accumulated in CSR order; its entries, sorted by column, go to
+// the scratch rows starting at uoff[I] (room for the bound above) and their
+// count to cnt[I], in one pass (no separate symbolic pass).
 __global__ void k_rap(int64_t nc, const int32_t *__restrict__ off, const int32_t *__restrict__ mem,
                       const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
-                      const int32_t *__restrict__ agg, int32_t *__restrict__ cnt, const int32_t *__restrict__ crp,
-                      int32_t *__restrict__ cci, double *__restrict__ cv, int *err) {
+                      const int32_t *__restrict__ agg, const int32_t *__restrict__ uoff, int32_t *__restrict__ cnt,
+                      int32_t *__restrict__ tci, double *__restrict__ tv, int *err) {
     mds_pdl_entry();
     int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
@@ -372,6 +400,7 @@ __global__ void k_rap(int64_t nc, const int32_t *__restrict__ off, const int32_t
             if (t == m) {
                 if (m >= RAP_CAP) {
                     atomicOr(err, DERR_CAPACITY);
+                    cnt[I] = 0;
                     return;
                 }
                 cols[m] = J;
@@ -380,10 +409,6 @@ __global__ void k_rap(int64_t nc, const int32_t *__restrict__ off, const int32_t
             acc[t] = acc[t] + v[p];
         }
     }
-    if constexpr (!FILL) {
-        cnt[I] = m;
-        return;
-    } else {
     for (int a = 1; a < m; a++) {
         int32_t x = cols[a];
         double y = acc[a];
@@ -396,11 +421,26 @@ __global__ void k_rap(int64_t nc, const int32_t *__restrict__ off, const int32_t
         cols[q + 1] = x;
         acc[q + 1] = y;
     }
-    int32_t o = crp[I];
+    const int32_t o = uoff[I];
     for (int a = 0; a < m; a++) {
-        cci[o + a] = cols[a];
-        cv[o + a] = acc[a];
+        tci[o + a] = cols[a];
+        tv[o + a] = acc[a];
     }
+    cnt[I] = m;
+}
+
+// The scratch rows moved to the coarse CSR arrays, one warp per row.
+__global__ void k_rap_compact(int64_t nc, const int32_t *__restrict__ uoff, const int32_t *__restrict__ crp,
+                              const int32_t *__restrict__ tci, const double *__restrict__ tv,
+                              int32_t *__restrict__ cci, double *__restrict__ cv) {
+    mds_pdl_entry();
+    const int64_t I = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (I >= nc) return;
+    const int32_t s = uoff[I], d = crp[I], m = crp[I + 1] - crp[I];
+    for (int32_t a = lane; a < m; a += 32) {
+        cci[d + a] = tci[s + a];
+        cv[d + a] = tv[s + a];
     }
 }
 
@@ -708,19 +748,25 @@ static int64_t mis2(Ctx &c, const DCsr &A, const int8_t *g, const int32_t *deg, 
     Buf m1(&c, sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
     Buf e1(&c, (size_t)(n > 0 ? n : 1));
     Buf und(&c, sizeof(int32_t));
+    // active-block flags of this round and the next (every block in the first)
+    Buf act[2] = {Buf(&c, (size_t)gr + 1), Buf(&c, (size_t)gr + 1)};
+    MDS_CUDA(cudaMemsetAsync(act[0].p, 1, (size_t)gr + 1, c.stream));
     uint64_t lkey = host_mix64(seed + 0x9E3779B97F4A7C15ULL * (uint64_t)(level + 1));
     MDS_LAUNCH(c, KC_NONE, 0, k_mis_init, gr, 256, 0, n, deg, state.as<int8_t>());
     for (int round = 0;; round++) {
         MDS_REQUIRE(round < 10000, MDS_ERR_TIMEOUT, "MIS-2 did not terminate");
+        const int8_t *a = act[round & 1].as<int8_t>();
+        int8_t *an = act[(round + 1) & 1].as<int8_t>();
         MDS_CUDA(cudaMemsetAsync(und.p, 0, sizeof(int32_t), c.stream));
+        MDS_CUDA(cudaMemsetAsync(an, 0, (size_t)gr + 1, c.stream));
         MDS_LAUNCH(c, KC_NONE, 0, k_mis_max1, gr, 256, 0, n, A.rowp(), A.cols(), g, state.as<int8_t>(), lkey, lid,
-                   m1.as<uint64_t>());
+                   a, m1.as<uint64_t>());
         MDS_LAUNCH(c, KC_NONE, 0, k_mis_select, gr, 256, 0, n, A.rowp(), A.cols(), g, m1.as<uint64_t>(), lkey, lid,
-                   state.as<int8_t>());
-        MDS_LAUNCH(c, KC_NONE, 0, k_mis_near_root, gr, 256, 0, n, A.rowp(), A.cols(), g, state.as<int8_t>(),
+                   a, state.as<int8_t>());
+        MDS_LAUNCH(c, KC_NONE, 0, k_mis_near_root, gr, 256, 0, n, A.rowp(), A.cols(), g, state.as<int8_t>(), a,
                    e1.as<int8_t>());
         MDS_LAUNCH(c, KC_NONE, 0, k_mis_exclude, gr, 256, 0, n, A.rowp(), A.cols(), g, e1.as<int8_t>(),
-                   state.as<int8_t>(), und.as<int32_t>());
+                   state.as<int8_t>(), a, an, und.as<int32_t>());
         if (c.read(und.as<int32_t>()) == 0) break;
     }
     return 0;
@@ -862,21 +908,24 @@ void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h,
         }
         // Galerkin product
         c.clear_err();
+        Buf ub(&c, sizeof(int32_t) * (size_t)(nc + 1)), uoff(&c, sizeof(int32_t) * (size_t)(nc + 1));
+        MDS_LAUNCH(c, KC_NONE, 0, k_rap_bound, grid_for(nc, 256), 256, 0, nc, L.mem_off.as<int32_t>(),
+                   L.mem.as<int32_t>(), L.A.rowp(), ub.as<int32_t>());
+        const int64_t utot = scan_counts(c, ub.as<int32_t>(), uoff.as<int32_t>(), nc);
+        Buf tci(&c, sizeof(int32_t) * (size_t)(utot > 0 ? utot : 1)), tv(&c, sizeof(double) * (size_t)(utot > 0 ? utot : 1));
         Buf ccnt(&c, sizeof(int32_t) * (size_t)(nc + 1));
-        MDS_LAUNCH(c, KC_NONE, 0, k_rap<false>, grid_for(nc, 64), 64, 0, nc, L.mem_off.as<int32_t>(),
-                   L.mem.as<int32_t>(), L.A.rowp(), L.A.cols(), L.A.vals(), L.agg.as<int32_t>(), ccnt.as<int32_t>(),
-                   nullptr, nullptr, nullptr, c.d_err);
-        c.check_err("Galerkin product (symbolic)");
+        MDS_LAUNCH(c, KC_NONE, 0, k_rap, grid_for(nc, 64), 64, 0, nc, L.mem_off.as<int32_t>(), L.mem.as<int32_t>(),
+                   L.A.rowp(), L.A.cols(), L.A.vals(), L.agg.as<int32_t>(), uoff.as<int32_t>(), ccnt.as<int32_t>(),
+                   tci.as<int32_t>(), tv.as<double>(), c.d_err);
+        c.check_err("Galerkin product");
         DCsr Ac;
         Ac.nrow = Ac.ncol = nc;
         Ac.rp = Buf(&c, sizeof(int32_t) * (size_t)(nc + 1));
         Ac.nnz = scan_counts(c, ccnt.as<int32_t>(), Ac.rowp(), nc);
         Ac.ci = Buf(&c, sizeof(int32_t) * (size_t)(Ac.nnz > 0 ? Ac.nnz : 1));
         Ac.v = Buf(&c, sizeof(double) * (size_t)(Ac.nnz > 0 ? Ac.nnz : 1));
-        MDS_LAUNCH(c, KC_NONE, 0, k_rap<true>, grid_for(nc, 64), 64, 0, nc, L.mem_off.as<int32_t>(),
-                   L.mem.as<int32_t>(), L.A.rowp(), L.A.cols(), L.A.vals(), L.agg.as<int32_t>(), nullptr,
-                   Ac.rowp(), Ac.cols(), Ac.vals(), c.d_err);
-        c.check_err("Galerkin product");
+        MDS_LAUNCH(c, KC_NONE, 0, k_rap_compact, grid_for(nc * 32, 256), 256, 0, nc, uoff.as<int32_t>(), Ac.rowp(),
+                   tci.as<int32_t>(), tv.as<double>(), Ac.cols(), Ac.vals());
         L.has_coarse = true;
         L.nc = nc;
         h.lv.emplace_back();
