@@ -233,6 +233,15 @@ int mds_system_view(mds_system sys, mds_csr blocks[5], const double **b);
                                       16-byte rows; the direct kernel otherwise).  Slower than
                                       MDS_FORMAT_STENCIL in a solve, so MDS_FORMAT_AUTO does not
                                       choose it */
+#define MDS_FORM_AUTO 0         /* the fused form, or the stored one on a level where the storage
+                                   autotuner (MDS_FORMAT_AUTO) times it faster */
+#define MDS_FORM_FUSED 1        /* a level with a coarser one applies its one L1-Jacobi sweep before
+                                   and after the coarse correction in two launches, the smoothed
+                                   iterate D1^-1 b (+ P x_c) formed per neighbour, never stored */
+#define MDS_FORM_STORED 2       /* the iterate stored: y = D1^-1 b, r = b - A y, y += P x_c,
+                                   x = y + D1^-1 (b - A y), four launches; one gather per neighbour
+                                   instead of two to four.  The same roundings as the fused form: the
+                                   results are equal bit for bit */
 #define MDS_BLOCK_LOWER 0       /* M_L, Eq. (8), Algorithm 1 */
 #define MDS_BLOCK_DIAG 1        /* block diagonal B_D with Q blocks */
 #define MDS_BLOCK_UPPER 2       /* block upper triangular B_U with Q blocks */
@@ -265,6 +274,9 @@ typedef struct {
     int cheb_degree;         /* degree of the Chebyshev smoother, 1..8 (2): residual polynomial
                                 T_k((theta - t)/delta) / T_k(theta/delta) of D1^-1 A on
                                 [0.3, 1] (Saad, Iterative Methods, Alg. 12.1) */
+    int level_form;          /* MDS_FORM_* (MDS_FORM_AUTO); levels with one L1-Jacobi sweep, unsmoothed
+                                prolongation, FP32 / BF16 / FP16 values or FP64 values of at most
+                                65,536 rows (larger FP64 levels always store the iterate) */
 } mds_setup_opts;
 
 /* Fill `o` with the defaults listed above. */

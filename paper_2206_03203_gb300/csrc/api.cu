@@ -465,6 +465,7 @@ int mds_setup_opts_default(mds_setup_opts *o) {
     o->prolongation = MDS_PROLONG_PIECEWISE;
     o->coarse_tail = 0;
     o->cheb_degree = 2;
+    o->level_form = MDS_FORM_AUTO;
     return MDS_OK;
 }
 
@@ -484,6 +485,8 @@ int mds_setup(mds_ctx ctx, mds_system sys, const mds_setup_opts *opts, mds_preco
     MDS_REQUIRE(o.smoother == MDS_SMOOTHER_L1JACOBI || o.smoother == MDS_SMOOTHER_CHEBYSHEV, MDS_ERR_INVALID,
                 "unknown smoother");
     MDS_REQUIRE(o.format >= MDS_FORMAT_AUTO && o.format <= MDS_FORMAT_STENCIL_BULK, MDS_ERR_INVALID, "unknown format");
+    MDS_REQUIRE(o.level_form >= MDS_FORM_AUTO && o.level_form <= MDS_FORM_STORED, MDS_ERR_INVALID,
+                "unknown level form");
     MDS_REQUIRE(o.sell_c == 8 || o.sell_c == 16 || o.sell_c == 32, MDS_ERR_INVALID, "sell_c must be 8, 16 or 32");
     MDS_REQUIRE(o.sell_sigma == 1 || (o.sell_sigma % o.sell_c == 0 && o.sell_sigma <= 1024), MDS_ERR_INVALID,
                 "sell_sigma must be 1 or a multiple of sell_c up to 1024");

@@ -88,6 +88,7 @@ enum : int { FMT_CSR = 0, FMT_SELL = 1, FMT_DIA = 2 };
 
 struct TuneChoice {
     int fmt, G, C, sigma;
+    int stored;  // the level runs the stored form (faster than the fused pair)
 };
 
 struct Ctx;
@@ -486,6 +487,7 @@ struct Level {
     // the finest level of a large hierarchy: its V-cycle kernels are the ones
     // counted in the timed classes (coarse levels launch as KC_NONE)
     bool timed_level = false;
+    bool stored = false;  // runs the stored form where the fused one would apply
     Buf l1;           // FP64 [n]
     Buf dinv;         // [n] 1/l1 in the vector precision
     bool has_coarse = false;
@@ -597,6 +599,7 @@ struct Hierarchy {
     int smoother = 0;
     int sweeps = 1;
     int cheb_degree = 2;
+    int form = 0;     // MDS_FORM_*
     int nr_cap = 0;   // columns the level work vectors hold
     int tune_nr = 1;  // columns the storage autotuner times with (those of the system's right-hand sides)
     bool use_tail = true;  // run the coarse end of the V-cycle as one cluster kernel

@@ -523,7 +523,10 @@ static void dense_apply_t(Ctx &c, const DenseBlocks &db, const double *M, int nr
     double bytes = 8.0 * (double)db.total + 2.0 * sizeof(XT) * n * nr;
     const DBlk *B = db.blk.as<DBlk>();
     const size_t smem = sizeof(double) * (size_t)db.nmax * (size_t)nr;
-    if (db.ntiles > 0 && smem <= 96 * 1024) {
+    // tiles when there are enough of them to fill the SMs (a batch's blocks);
+    // a single small block keeps a warp per row (n warps instead of n / 32
+    // thread blocks)
+    if (db.ntiles >= (c.num_sms > 0 ? c.num_sms : 1) && smem <= 96 * 1024) {
         const int2 *T = db.tiles.as<int2>();
         const unsigned g = (unsigned)db.ntiles;
         switch (nr) {

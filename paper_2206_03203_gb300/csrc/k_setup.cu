@@ -788,6 +788,7 @@ void amg_setup(Ctx &c, const mds_csr &A0, const mds_setup_opts &o, Hierarchy &h,
     h.smoother = o.smoother;
     h.sweeps = o.sweeps < 1 ? 1 : o.sweeps;
     h.cheb_degree = o.cheb_degree < 1 ? 2 : o.cheb_degree;
+    h.form = o.level_form;
     h.use_tail = o.coarse_tail != 0 && h.K == 1;
     int maxl = o.max_levels < 1 ? 1 : (o.max_levels > 32 ? 32 : o.max_levels);
     h.lv.emplace_back();

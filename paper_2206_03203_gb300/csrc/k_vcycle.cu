@@ -19,8 +19,8 @@ namespace mds {
 // per vector type (k_vcycle_f64.cu, k_vcycle_f32.cu)
 void vcycle_run_f64(Ctx &c, Hierarchy &h, const double *b, double *x, int nr);
 void vcycle_run_f32(Ctx &c, Hierarchy &h, const float *b, float *x, int nr);
-float time_level_f64(Ctx &c, const Level &L, int nr, const void *xc);
-float time_level_f32(Ctx &c, const Level &L, int nr, const void *xc);
+float time_level_f64(Ctx &c, const Level &L, int nr, const void *xc, bool stored);
+float time_level_f32(Ctx &c, const Level &L, int nr, const void *xc, bool stored);
 
 // The level work vectors hold up to nr_cap interleaved columns.
 void hierarchy_reserve(Ctx &c, Hierarchy &h, int nr) {
@@ -313,16 +313,22 @@ static int default_g(const Level &L) {
 // Autotuner: time CSR with G/2, G, 2G lanes per row and SELL-C-sigma for a
 // few (C, sigma) pairs on this level, keep the fastest.  xc (the coarser
 // level's x) != NULL: the level runs the fused pair (residual, post-smoothing)
-// and both are timed; otherwise the stored residual.  Choices are cached in
+// and both are timed; otherwise the stored residual.  With may_store, the
+// four launches of the stored form are then timed in the chosen storage and
+// taken when at least 5% faster than the fused pair.  Choices are cached in
 // the context by (rows, nonzeros, storage type, columns, timed forms).
-template <class XT> static void autotune_level(Ctx &c, Level &L, int nr, void *xc, int64_t nc) {
-    auto time_level = [nr, xc](Ctx &cc, const Level &LL) {
-        return std::is_same<XT, double>::value ? time_level_f64(cc, LL, nr, xc) : time_level_f32(cc, LL, nr, xc);
+template <class XT> static void autotune_level(Ctx &c, Level &L, int nr, void *xc, int64_t nc, bool may_store) {
+    auto time_form = [nr, xc](Ctx &cc, const Level &LL, bool stored) {
+        return std::is_same<XT, double>::value ? time_level_f64(cc, LL, nr, xc, stored)
+                                               : time_level_f32(cc, LL, nr, xc, stored);
     };
-    auto key = std::make_tuple(L.A.nrow, L.A.nnz, ((L.vt * 2 + (L.dia_D > 0 ? 1 : 0)) * 2 + (xc ? 1 : 0)) * 16 + nr);
+    auto time_level = [&](Ctx &cc, const Level &LL) { return time_form(cc, LL, false); };
+    auto key = std::make_tuple(L.A.nrow, L.A.nnz,
+                               (((L.vt * 2 + (L.dia_D > 0 ? 1 : 0)) * 2 + (xc ? 1 : 0)) * 2 + (may_store ? 1 : 0)) * 16 + nr);
     auto it = c.tune_cache.find(key);
     if (it != c.tune_cache.end()) {
         const TuneChoice &t = it->second;
+        L.stored = t.stored != 0;
         if (t.fmt == FMT_SELL)
             build_sell_vt(c, L, t.C, t.sigma);
         else if (t.fmt == FMT_DIA && L.dia_D > 0) {
@@ -382,7 +388,6 @@ template <class XT> static void autotune_level(Ctx &c, Level &L, int nr, void *x
         L.fmt = FMT_CSR;
         L.dia_bulk = false;
     }
-    c.tune_cache[key] = best;
     L.G = best.fmt == FMT_CSR ? best.G : default_g(L);
     if (best.fmt == FMT_SELL) build_sell_vt(c, L, best.C, best.sigma);
     if (best.fmt == FMT_DIA) {
@@ -391,6 +396,12 @@ template <class XT> static void autotune_level(Ctx &c, Level &L, int nr, void *x
     } else {
         drop_dia(L);
     }
+    if (xc && may_store) {
+        const float ts = time_form(c, L, true);
+        best.stored = ts < 0.95f * tbest ? 1 : 0;
+    }
+    L.stored = best.stored != 0;
+    c.tune_cache[key] = best;
 }
 
 void level_storage(Ctx &c, Hierarchy &h, const mds_setup_opts &o) {
@@ -444,14 +455,17 @@ void level_storage(Ctx &c, Hierarchy &h, const mds_setup_opts &o) {
         } else if (o.format == MDS_FORMAT_AUTO && n >= 20000) {
             // the forms the V-cycle runs on this level (fused pair or stored residual)
             const bool fused = h.smoother == MDS_SMOOTHER_L1JACOBI && h.sweeps == 1 && !L.smoothed &&
-                               (h.prec != 64 || n <= FUSE_FP64_ROWS) && L.has_coarse && l + 1 < h.lv.size();
+                               (h.prec != 64 || n <= FUSE_FP64_ROWS) && L.has_coarse && l + 1 < h.lv.size() &&
+                               h.form != MDS_FORM_STORED;
             void *xc = fused ? h.lv[l + 1].x.p : nullptr;
             const int64_t nc = fused ? h.lv[l + 1].A.nrow : 0;
+            const bool may_store = h.form == MDS_FORM_AUTO;
             if (h.prec == 64)
-                autotune_level<double>(c, L, h.nr_cap, xc, nc);
+                autotune_level<double>(c, L, h.nr_cap, xc, nc, may_store);
             else
-                autotune_level<float>(c, L, h.nr_cap, xc, nc);
+                autotune_level<float>(c, L, h.nr_cap, xc, nc, may_store);
         }
+        if (h.form == MDS_FORM_STORED) L.stored = true;
         if (L.fmt != FMT_DIA) drop_dia(L);
     }
 }

@@ -6,8 +6,8 @@ namespace mds {
 
 void vcycle_run_f32(Ctx &c, Hierarchy &h, const float *b, float *x, int nr) { vcycle_nr<float>(c, h, b, x, nr); }
 
-float time_level_f32(Ctx &c, const Level &L, int nr, const void *xc) {
-    return time_level<float>(c, L, nr, xc);
+float time_level_f32(Ctx &c, const Level &L, int nr, const void *xc, bool stored) {
+    return time_level<float>(c, L, nr, xc, stored);
 }
 
 }  // namespace mds

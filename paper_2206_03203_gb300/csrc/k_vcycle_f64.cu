@@ -6,8 +6,8 @@ namespace mds {
 
 void vcycle_run_f64(Ctx &c, Hierarchy &h, const double *b, double *x, int nr) { vcycle_nr<double>(c, h, b, x, nr); }
 
-float time_level_f64(Ctx &c, const Level &L, int nr, const void *xc) {
-    return time_level<double>(c, L, nr, xc);
+float time_level_f64(Ctx &c, const Level &L, int nr, const void *xc, bool stored) {
+    return time_level<double>(c, L, nr, xc, stored);
 }
 
 }  // namespace mds

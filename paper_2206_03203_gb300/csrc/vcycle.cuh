@@ -1434,9 +1434,12 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
     // Fused form (y = D1^-1 b [+ P x_c] formed per neighbour, no stored
     // iterate): FP32 levels, and FP64 levels small enough to be bound by
     // latency rather than by the FP64 units (the fused form spends one to two
-    // more FP64 operations per nonzero and saves two launches per level).
+    // more FP64 operations per nonzero and saves two launches per level),
+    // unless the level takes the stored form (chosen, or timed faster: on
+    // levels with many entries per row the fused post-smoothing's gathers of
+    // b, 1/D1, the aggregate and x_c per neighbour cost more than storing y)
     bool fused = h.smoother == MDS_SMOOTHER_L1JACOBI && h.sweeps == 1 && !L.smoothed &&
-                 (!std::is_same<XT, double>::value || n <= FUSE_FP64_ROWS);
+                 (!std::is_same<XT, double>::value || n <= FUSE_FP64_ROWS) && !L.stored;
     if (fused) {
         if (L.has_coarse) {
             Level &C = h.lv[l + 1];
@@ -1497,15 +1500,27 @@ static void vcycle_nr(Ctx &c, Hierarchy &h, const XT *b, XT *x, int nr) {
 // xc == NULL: the stored-residual kernel; otherwise the pair of fused
 // kernels the V-cycle runs on a level with a coarser one (the residual with
 // y = D1^-1 b formed per neighbour, and the post-smoothing with y = D1^-1 b +
-// P x_c formed per neighbour, x_c = xc).
-template <class XT, int NR> static float time_level_nr(Ctx &c, const Level &L, const XT *xc) {
+// P x_c formed per neighbour, x_c = xc), or with `stored` the four launches
+// of the stored form in their place (y = D1^-1 b, the residual, y += P x_c,
+// the smoothing from y).
+template <class XT, int NR> static float time_level_nr(Ctx &c, const Level &L, const XT *xc, bool stored) {
     cudaEvent_t e0, e1;
     MDS_CUDA(cudaEventCreate(&e0));
     MDS_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
     for (int rep = 0; rep < 4; rep++) {
         MDS_CUDA(cudaEventRecord(e0, c.stream));
-        if (xc) {
+        if (xc && stored) {
+            const int64_t n = L.A.nrow;
+            const LiveMap lm = level_live(c, L);
+            XT *y = L.y.as<XT>();
+            MDS_LAUNCH(c, KC_NONE, 0, (k_vc_x0<XT, NR>), ew_blocks(n, lm), 256, 0, n, L.dinv.as<XT>(), L.b.as<XT>(), y,
+                       ew_rows(n, lm), lm);
+            level_op<XT, VK_RESID, NR>(c, L, L.b.as<XT>(), y, nullptr, nullptr, L.r.as<XT>(), 0);
+            MDS_LAUNCH(c, KC_NONE, 0, (k_vc_prolong<XT, NR>), ew_blocks(n, lm), 256, 0, n, L.agg.as<int32_t>(), xc, y,
+                       ew_rows(n, lm), lm);
+            level_op<XT, VK_SMOOTH, NR>(c, L, L.b.as<XT>(), y, nullptr, nullptr, L.x.as<XT>(), 0);
+        } else if (xc) {
             level_op<XT, VK_RESID0, NR>(c, L, L.b.as<XT>(), nullptr, nullptr, nullptr, L.r.as<XT>(), 0);
             level_op<XT, VK_POST, NR>(c, L, L.b.as<XT>(), nullptr, L.agg.as<int32_t>(), xc, L.x.as<XT>(), L.nc);
         } else {
@@ -1524,13 +1539,13 @@ template <class XT, int NR> static float time_level_nr(Ctx &c, const Level &L, c
 
 // Time the level's kernels in its current storage with nr interleaved
 // columns (best of three after a warm-up launch).
-template <class XT> static float time_level(Ctx &c, const Level &L, int nr, const void *xc) {
+template <class XT> static float time_level(Ctx &c, const Level &L, int nr, const void *xc, bool stored) {
     const XT *x = (const XT *)xc;
     switch (nr) {
-        case 8: return time_level_nr<XT, 8>(c, L, x);
-        case 4: return time_level_nr<XT, 4>(c, L, x);
-        case 2: return time_level_nr<XT, 2>(c, L, x);
-        default: return time_level_nr<XT, 1>(c, L, x);
+        case 8: return time_level_nr<XT, 8>(c, L, x, stored);
+        case 4: return time_level_nr<XT, 4>(c, L, x, stored);
+        case 2: return time_level_nr<XT, 2>(c, L, x, stored);
+        default: return time_level_nr<XT, 1>(c, L, x, stored);
     }
 }
 

@@ -22,6 +22,7 @@ MDS_OK = 0
 MDS_WARN_NOT_CONVERGED = 1
 PREC = {"fp64": 64, "fp32": 32, "bf16": 16, "fp16": 17}
 FORMAT = {"auto": 0, "csr": 1, "sell": 2, "stencil": 3, "stencil-bulk": 4}
+FORM = {"auto": 0, "fused": 1, "stored": 2}
 PROLONG = {"piecewise": 0, "smoothed": 1}
 SMOOTHER = {"l1jacobi": 0, "chebyshev": 1}
 KIND = {"lower": 0, "diag": 1, "upper": 2}
@@ -67,7 +68,7 @@ class SetupOpts(C.Structure):
                 ("stall_ratio", C.c_double), ("seed", C.c_uint64), ("smoother", C.c_int),
                 ("precision", C.c_int), ("lowp_from_level", C.c_int), ("kind", C.c_int), ("format", C.c_int),
                 ("sell_c", C.c_int), ("sell_sigma", C.c_int), ("sweeps", C.c_int), ("prolongation", C.c_int),
-                ("coarse_tail", C.c_int), ("cheb_degree", C.c_int)]
+                ("coarse_tail", C.c_int), ("cheb_degree", C.c_int), ("level_form", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -197,6 +198,8 @@ def setup_opts(**kw) -> SetupOpts:
             v = FORMAT.get(v, v)
         elif k == "prolongation":
             v = PROLONG.get(v, v)
+        elif k == "level_form":
+            v = FORM.get(v, v)
         setattr(o, k, v)
     return o
 

@@ -55,6 +55,7 @@ def test_default_options(built):
     from paper_2206_03203_gb300 import mdsolve
     o = mdsolve.setup_opts()
     assert o.theta < 0 and o.n_coarse == 512 and o.max_levels == 25  # theta resolved by mds_setup
+    assert o.level_form == 0 and o.cheb_degree == 2 and mdsolve.setup_opts(level_form="stored").level_form == 2
     s = mdsolve.solve_opts()
     assert s.restart == 30 and s.rtol == 1e-8 and s.x0_zero == 0
 

@@ -719,6 +719,37 @@ def test_packed_hierarchies_bit_exact(ctx, oracle_mod, precision):
         assert maxrel(x.cpu().numpy(), M.amg(block).vcycle(b)) < (1e-12 if precision == "fp64" else 5e-5)
 
 
+def test_packed_coarsest_tiles_many_instances(ctx, oracle_mod, torch_mod):
+    """A batch with more coarsest-level tiles than the GPU has SMs takes the
+    tiled coarsest inverse (symmetric, mirrored) and the tiled apply: its
+    V-cycles agree with the oracle's segmented ones (FP64), and sampled
+    problems of the batched solve converge as the oracle's do."""
+    import torch
+    insts = [inputs.random_rects_3d(6 + k % 3, 22060304, k, 1, nrhs=1, random_dirichlet=True)
+             for k in range(160)]
+    sys_ = ctx.assemble_batch(insts)
+    mo, fo = sys_.instances()
+    Ao, bo, NM = packed_oracle(oracle_mod, insts)
+    prec = ctx.setup(sys_, precision="fp64", format="csr")
+    M = oracle_mod.ML(Ao, NM, segments=(mo, fo))
+    rng = np.random.default_rng(5)
+    for block, n in ((0, NM), (1, sys_.n_f)):
+        assert prec.info(block)["dense"]
+        b = rng.standard_normal(n)
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        ctx.vcycle(prec, block, torch.as_tensor(b, device="cuda"), x)
+        assert maxrel(x.cpu().numpy(), M.amg(block).vcycle(b)) < 1e-12, block
+    x = np.zeros(sys_.N)
+    code, st = ctx.solve(sys_, prec, None, x, nrhs=1, rtol=1e-8)
+    assert code == 0
+    for k in (0, 57, 101, 159):
+        rows = np.r_[mo[k]:mo[k + 1], NM + fo[k]:NM + fo[k + 1]]
+        be = np.zeros(sys_.N)
+        be[rows] = bo[0][rows]
+        r = oracle_mod.fgmres(Ao, be, M)
+        assert abs(st[k].iterations - r.iterations) <= 1, (k, st[k].iterations, r.iterations)
+
+
 def test_packed_batch_per_problem_iteration_cap(ctx, torch_mod):
     insts = [inputs.random_rects_3d(n, 3, k, 2, nrhs=1) for k, n in enumerate([8, 10])]
     sys_ = ctx.assemble_batch(insts)
@@ -905,6 +936,29 @@ def test_stencil_bulk_staging_is_csr_bit_for_bit(ctx, torch_mod, precision, nr):
     assert c1 == c2 == 0
     assert [q.iterations for q in s1] == [q.iterations for q in s2]
     assert torch.equal(xs, xc)
+
+
+@pytest.mark.parametrize("precision,nr,fmt", [("bf16", 4, "csr"), ("bf16", 4, "stencil"), ("fp32", 1, "sell"),
+                                               ("fp64", 4, "stencil"), ("fp64", 1, "csr")])
+def test_stored_level_form_is_fused_bit_for_bit(ctx, torch_mod, precision, nr, fmt):
+    """The stored form of a level's smoothing (y = D1^-1 b, residual, y +=
+    P x_c, smoothing from y: four launches) rounds as the fused pair does,
+    which forms y per neighbour: whole lockstep solves of a packed batch of
+    uneven 3D instances are equal bit for bit, on CSR, SELL and stencil
+    storage, with BF16, FP32 and FP64 levels."""
+    torch = torch_mod
+    insts = [inputs.random_rects_3d(n, 22060304, k, 1 + k % 3, nrhs=nr, random_dirichlet=True)
+             for k, n in enumerate([9, 12, 7, 10, 23])]
+    sys_ = ctx.assemble_batch(insts)
+    pf = ctx.setup(sys_, precision=precision, format=fmt, level_form="fused")
+    ps = ctx.setup(sys_, precision=precision, format=fmt, level_form="stored")
+    xf = torch.zeros(sys_.N * nr, dtype=torch.float64, device="cuda")
+    xs = torch.zeros_like(xf)
+    c1, s1 = ctx.solve(sys_, pf, None, xf, nrhs=nr, max_iters=3000)
+    c2, s2 = ctx.solve(sys_, ps, None, xs, nrhs=nr, max_iters=3000)
+    assert c1 == c2 == 0
+    assert [q.iterations for q in s1] == [q.iterations for q in s2]
+    assert torch.equal(xf, xs)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "bf16"])
