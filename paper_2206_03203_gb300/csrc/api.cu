@@ -682,8 +682,9 @@ void precond_apply(mds_precond p, const double *r, double *z, int nr) {
         vcycle_apply(c, HS, rm, zm, nr);
     } else {
         cast_f64_f32(c, rm, HS.lv[0].b.as<float>(), nm * nr, lmm, nr);
-        vcycle_apply(c, HS, HS.lv[0].b.p, HS.lv[0].x.p, nr);
-        cast_f32_f64(c, HS.lv[0].x.as<float>(), zm, nm * nr, lmm, nr);
+        // the top level's last kernel writes z_m in FP64 (else x, converted)
+        if (!vcycle_apply_to64(c, HS, HS.lv[0].b.as<float>(), HS.lv[0].x.as<float>(), zm, nr))
+            cast_f32_f64(c, HS.lv[0].x.as<float>(), zm, nm * nr, lmm, nr);
     }
     if (!p->has_f) return;
     // step 2: r_f <- r_f - A_fm z_m (block lower only); step 3: z_f = Q_ff r_f
@@ -698,12 +699,14 @@ void precond_apply(mds_precond p, const double *r, double *z, int nr) {
         if (kind == MDS_BLOCK_DIAG && p->ff_negative) scale_f64(c, zf, -1.0, nf * nr);
     } else {
         float *bf = HF.lv[0].b.as<float>();
+        // r_f - A_fm z_m with z_m read in FP64: the same values as the
+        // V-cycle's FP32 x (exactly widened), so the same products
         if (kind == MDS_BLOCK_LOWER)
-            spmv_sub_f64_xf(c, Afm, rf, HS.lv[0].x.as<float>(), bf, nr, lmf);
+            spmv_sub_f64_to_f32(c, Afm, rf, zm, bf, nr, lmf);
         else
             cast_f64_f32(c, rf, bf, nf * nr, lmf, nr);
-        vcycle_apply(c, HF, HF.lv[0].b.p, HF.lv[0].x.p, nr);
-        cast_f32_f64(c, HF.lv[0].x.as<float>(), zf, nf * nr, lmf, nr);
+        if (!vcycle_apply_to64(c, HF, bf, HF.lv[0].x.as<float>(), zf, nr))
+            cast_f32_f64(c, HF.lv[0].x.as<float>(), zf, nf * nr, lmf, nr);
         if (kind == MDS_BLOCK_DIAG && p->ff_negative) scale_f64(c, zf, -1.0, nf * nr);
     }
 }

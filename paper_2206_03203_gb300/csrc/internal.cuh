@@ -269,6 +269,10 @@ struct Ctx {
     // changes of live_host, so that each row space rebuilds its chunk ranges
     // once per change
     bool compact = false;
+    // set around one level operation: it writes its rows to this FP64 vector
+    // instead of its own output (the top level of an FP32 V-cycle handing
+    // its result to the FP64 Krylov method without a separate conversion)
+    double *level_out64 = nullptr;
     int live_ver = 0;
     // device address of the static workspace of mds_solve_noalloc on this
     // context's device, resolved by mds_create
@@ -445,6 +449,8 @@ void spmv_sub_f64(Ctx &c, const mds_csr &A, const double *r, const double *x, do
                   const LiveMap &lm = {});
 void spmv_sub_f64_xf(Ctx &c, const mds_csr &A, const double *r, const float *x, float *out, int nr = 1,
                      const LiveMap &lm = {});
+void spmv_sub_f64_to_f32(Ctx &c, const mds_csr &A, const double *r, const double *x, float *out, int nr = 1,
+                         const LiveMap &lm = {});
 
 // ---- assembly (k_assemble.cu) ----
 struct SystemData {
@@ -636,6 +642,10 @@ void dense_apply(Ctx &c, const DenseBlocks &db, const double *M, int nr, const f
 // x = V(b) on level 0 of h for nr in {1, 2, 4, 8} interleaved columns; b and
 // x in the hierarchy's vector precision.
 void vcycle_apply(Ctx &c, Hierarchy &h, const void *b, void *x, int nr = 1);
+// An FP32 V-cycle (h.prec 32) whose top level writes its result to z64 (FP64,
+// the same interleaved rows) instead of x where its last operation allows;
+// returns false when x was written instead (the caller converts).
+bool vcycle_apply_to64(Ctx &c, Hierarchy &h, const float *b, float *x, double *z64, int nr);
 // grow the level work vectors to hold nr interleaved columns
 void hierarchy_reserve(Ctx &c, Hierarchy &h, int nr);
 

@@ -295,4 +295,9 @@ void spmv_sub_f64_xf(Ctx &c, const mds_csr &A, const double *r, const float *x, 
     spmv_dispatch<float, float, 1>(c, A, x, r, out, KC_NONE, nr, lm);
 }
 
+void spmv_sub_f64_to_f32(Ctx &c, const mds_csr &A, const double *r, const double *x, float *out, int nr,
+                         const LiveMap &lm) {
+    spmv_dispatch<double, float, 1>(c, A, x, r, out, KC_NONE, nr, lm);
+}
+
 }  // namespace mds

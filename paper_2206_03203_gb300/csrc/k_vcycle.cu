@@ -19,6 +19,7 @@ namespace mds {
 // per vector type (k_vcycle_f64.cu, k_vcycle_f32.cu)
 void vcycle_run_f64(Ctx &c, Hierarchy &h, const double *b, double *x, int nr);
 void vcycle_run_f32(Ctx &c, Hierarchy &h, const float *b, float *x, int nr);
+bool vcycle_run_f32_to64(Ctx &c, Hierarchy &h, const float *b, float *x, double *z64, int nr);
 float time_level_f64(Ctx &c, const Level &L, int nr, const void *xc, bool stored);
 float time_level_f32(Ctx &c, const Level &L, int nr, const void *xc, bool stored);
 
@@ -36,6 +37,13 @@ void hierarchy_reserve(Ctx &c, Hierarchy &h, int nr) {
         if (h.smoother == MDS_SMOOTHER_CHEBYSHEV) L.d = Buf(&c, nb);
     }
     h.nr_cap = nr;
+}
+
+bool vcycle_apply_to64(Ctx &c, Hierarchy &h, const float *b, float *x, double *z64, int nr) {
+    MDS_REQUIRE(nr <= h.nr_cap, MDS_ERR_INVALID, "V-cycle work vectors hold fewer columns");
+    MDS_REQUIRE(h.prec != 64, MDS_ERR_INVALID, "FP64 hierarchies write their own FP64 result");
+    KTimer all(c, KC_VCYCLE, 0.0);
+    return vcycle_run_f32_to64(c, h, b, x, z64, nr);
 }
 
 void vcycle_apply(Ctx &c, Hierarchy &h, const void *b, void *x, int nr) {

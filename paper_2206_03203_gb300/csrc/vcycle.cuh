@@ -49,6 +49,7 @@ template <class VT> struct LvlMat {
     int sigma;                 // SELL sorting window (a stored row's original row lies in its window)
     const float *rscale;       // row scales (NULL: unscaled)
     LiveMap lm;                // rows of finished batch instances are skipped
+    double *out64;             // NULL, or the FP64 vector the rows are written to instead of out
 };
 
 // Matrix entries are streamed once per launch: load them evict-first so the
@@ -73,6 +74,20 @@ template <class XT, int NR> __device__ __forceinline__ Vec<XT, NR> ldv(const XT 
 }
 template <class XT, int NR> __device__ __forceinline__ void stv(XT *p, int64_t j, const Vec<XT, NR> &x) {
     reinterpret_cast<Vec<XT, NR> *>(p)[j] = x;
+}
+// a level kernel's output row: in FP64 to out64 when given (the top level of
+// an FP32 V-cycle writing the Krylov method's vector; the widening is exact),
+// else in the vector type to out
+template <class XT, int NR>
+__device__ __forceinline__ void st_out(XT *out, double *out64, int64_t j, const Vec<XT, NR> &x) {
+    if (out64) {
+        Vec<double, NR> w;
+#pragma unroll
+        for (int c = 0; c < NR; c++) w.v[c] = (double)x.v[c];
+        stv<double, NR>(out64, j, w);
+    } else {
+        stv<XT, NR>(out, j, x);
+    }
 }
 
 enum { VK_RESID0 = 0, VK_POST = 1, VK_RESID = 2, VK_SMOOTH = 3 };
@@ -301,7 +316,7 @@ __device__ __forceinline__ void level_block(int64_t vb, const LvlMat<VT> &A, con
 #pragma unroll
             for (int c = 0; c < NR; c++) res.v[c] = fma_rn(d, sub_rn(bo.v[c], s[c]), y.v[c]);
         }
-        stv<XT, NR>(out, o, res);
+        st_out<XT, NR>(out, A.out64, o, res);
     }
 }
 
@@ -337,6 +352,7 @@ template <class VT> struct DiaMat {
     int K;
     LiveMap lm;
     int *err;               // device error word (a bulk copy that never completed)
+    double *out64;          // NULL, or the FP64 vector the rows are written to instead of out
 };
 
 // Resident blocks per SM asked of the compiler (measured on the finest level
@@ -454,7 +470,7 @@ __device__ __forceinline__ void level_dia_block(int64_t vb, const DiaMat<VT> &A,
 #pragma unroll
         for (int c = 0; c < NR; c++) res.v[c] = fma_rn(dd, sub_rn(bo.v[c], s[c]), y.v[c]);
     }
-    stv<XT, NR>(out, row, res);
+    st_out<XT, NR>(out, A.out64, row, res);
 }
 
 // grid-stride over the level's 256-row blocks (as k_level)
@@ -605,7 +621,7 @@ __global__ void __launch_bounds__(256, dia_min_blocks<XT, K, NR>())
                 Vec<XT, NR> nan;
 #pragma unroll
                 for (int c = 0; c < NR; c++) nan.v[c] = (XT)NAN;
-                stv<XT, NR>(out, row, nan);
+                st_out<XT, NR>(out, A.out64, row, nan);
             }
             return;
         }
@@ -657,7 +673,7 @@ __global__ void __launch_bounds__(256, dia_min_blocks<XT, K, NR>())
 #pragma unroll
                 for (int c = 0; c < NR; c++) res.v[c] = fma_rn(dd, sub_rn(bo.v[c], s[c]), y.v[c]);
             }
-            stv<XT, NR>(out, row, res);
+            st_out<XT, NR>(out, A.out64, row, res);
         }
         __syncthreads();  // the block's reads of sp and sw before the next block's copies
     }
@@ -825,6 +841,7 @@ template <class VT> static LvlMat<VT> lvl_view(Ctx &c, const Level &L) {
     m.rp = L.A.rowp();
     m.ci = L.A.cols();
     m.rscale = L.rscale.p ? L.rscale.as<float>() : nullptr;
+    m.out64 = c.level_out64;
     if (L.fmt == FMT_SELL) {
         m.v = L.sell_val.as<VT>();
         m.sp = L.sell_ptr.as<int32_t>();
@@ -848,13 +865,15 @@ static void launch_level_pf(Ctx &c, const Level &L, const XT *dinv, const XT *b,
     double xb = sizeof(XT) * (double)NR;
     double bytes = vb + (L.fmt == FMT_SELL ? 8.0 * L.sell_nslice : 4.0 * (n + 1)) + sizeof(XT) * n + 2.0 * xb * n +
                    (K == VK_POST && agg ? 4.0 * n + xb * (double)nc : 0.0) + (L.rscale.p ? 4.0 * n : 0.0) +
-                   (K == VK_SMOOTH ? xb * (double)n : 0.0);
+                   (K == VK_SMOOTH ? xb * (double)n : 0.0) +
+                   (c.level_out64 ? (8.0 - sizeof(XT)) * NR * (double)n : 0.0);
     double flops = NR * (2.0 * L.A.nnz + (K == VK_RESID0 ? n : K == VK_POST ? 5.0 * n : K == VK_SMOOTH ? 3.0 * n : 0.0));
     int cls = !L.timed_level ? KC_NONE : (K == VK_RESID0 || K == VK_RESID) ? KC_VC_RESID : KC_VC_POST;
     if (L.fmt == FMT_DIA) {
         if constexpr (std::is_same<VT, float>::value || std::is_same<VT, double>::value) {
             DiaMat<VT> dm{n, L.dia_stride, L.dia_val.as<VT>(), L.dia_seg.as<int64_t>(), L.dia_side.as<int32_t>(),
-                          L.dia_ck.as<int4>(), (int)(L.dia_side.bytes / sizeof(int32_t)), m.lm, c.d_err};
+                          L.dia_ck.as<int4>(), (int)(L.dia_side.bytes / sizeof(int32_t)), m.lm, c.d_err,
+                          c.level_out64};
             // algorithmic bytes: the planes instead of values, columns and row pointers
             bytes = bytes - vb - 4.0 * (n + 1) + (double)L.dia_D * sizeof(VT) * n;
             if constexpr ((NR * sizeof(XT)) % 16 == 0) {
@@ -1410,24 +1429,35 @@ static bool vcycle_tail(Ctx &c, Hierarchy &h, int l0, const XT *b, XT *x) {
 }
 
 
+// The level's last operation writes its rows to z64 in FP64 instead of x
+// (for the duration of one level operation).
+struct Out64Scope {
+    Ctx &c;
+    Out64Scope(Ctx &cc, double *p) : c(cc) { c.level_out64 = p; }
+    ~Out64Scope() { c.level_out64 = nullptr; }
+};
+
+// One V-cycle from level l.  z64 (top level only): its last operation writes
+// FP64 rows there instead of x where it is one level kernel; returns whether
+// it did (false: x holds the result).
 template <class XT, int NR>
-static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
+static bool vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x, double *z64 = nullptr) {
     Level &L = h.lv[l];
     int last = (int)h.lv.size() - 1;
     if (l == last && h.dense) {
         dense_apply(c, h.db, h.Ainv.as<double>(), NR, b, x, h.K > 1 ? c.live : nullptr);
-        return;
+        return false;
     }
     if (l == last && h.diagonal) {  // no couplings: exact x = b / a_ii
         const int64_t nd = L.A.nrow;
         const LiveMap lm = level_live(c, L);
         MDS_LAUNCH(c, KC_NONE, 3.0 * sizeof(XT) * nd * NR, (k_vc_x0<XT, NR>), ew_blocks(nd, lm), 256, 0, nd,
                    L.dinv.as<XT>(), b, x, ew_rows(nd, lm), lm);
-        return;
+        return false;
     }
     if (h.use_tail && l == tail_start<XT>(h, (int64_t)tail_cluster<XT, NR>(c) * TAIL_THREADS) &&
         vcycle_tail<XT, NR>(c, h, l, b, x))
-        return;
+        return false;
     int64_t n = L.A.nrow;
     XT *r = L.r.as<XT>();
     double rbytes = 4.0 * (L.nc + 1) + 4.0 * n + sizeof(XT) * NR * (double)(n + L.nc);
@@ -1450,11 +1480,13 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
                        256, 0, L.nc, L.mem_off.as<int32_t>(), L.mem.as<int32_t>(), r, C.b.as<XT>(), lmc,
                        live_blocks(lmc, grid_for(L.nc, 256), 1));
             vcycle_level<XT, NR>(c, h, l + 1, C.b.as<XT>(), C.x.as<XT>());
+            Out64Scope o64(c, z64);
             level_op<XT, VK_POST, NR>(c, L, b, nullptr, L.agg.as<int32_t>(), C.x.as<XT>(), x, L.nc);
         } else {
+            Out64Scope o64(c, z64);
             level_op<XT, VK_POST, NR>(c, L, b, nullptr, nullptr, nullptr, x, 0);
         }
-        return;
+        return z64 != nullptr;
     }
     XT *y = L.y.as<XT>();
     smooth_stored<XT, NR>(c, h, L, b, nullptr, y);  // y = S(0; b)
@@ -1483,16 +1515,23 @@ static void vcycle_level(Ctx &c, Hierarchy &h, int l, const XT *b, XT *x) {
                        L.agg.as<int32_t>(), C.x.as<XT>(), y, ew_rows(n, lml), lml);
         }
     }
+    if (z64 && h.smoother == MDS_SMOOTHER_L1JACOBI && h.sweeps == 1) {
+        // x = S(y; b) is one smoothing kernel
+        Out64Scope o64(c, z64);
+        level_op<XT, VK_SMOOTH, NR>(c, L, b, y, nullptr, nullptr, x, 0);
+        return true;
+    }
     smooth_stored<XT, NR>(c, h, L, b, y, x);  // x = S(y; b)
+    return false;
 }
 
 template <class XT>
-static void vcycle_nr(Ctx &c, Hierarchy &h, const XT *b, XT *x, int nr) {
+static bool vcycle_nr(Ctx &c, Hierarchy &h, const XT *b, XT *x, int nr, double *z64 = nullptr) {
     switch (nr) {
-        case 1: vcycle_level<XT, 1>(c, h, 0, b, x); break;
-        case 2: vcycle_level<XT, 2>(c, h, 0, b, x); break;
-        case 4: vcycle_level<XT, 4>(c, h, 0, b, x); break;
-        case 8: vcycle_level<XT, 8>(c, h, 0, b, x); break;
+        case 1: return vcycle_level<XT, 1>(c, h, 0, b, x, z64);
+        case 2: return vcycle_level<XT, 2>(c, h, 0, b, x, z64);
+        case 4: return vcycle_level<XT, 4>(c, h, 0, b, x, z64);
+        case 8: return vcycle_level<XT, 8>(c, h, 0, b, x, z64);
         default: throw Error(MDS_ERR_INVALID, "V-cycle column count must be 1, 2, 4 or 8");
     }
 }
