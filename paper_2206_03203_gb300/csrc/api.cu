@@ -681,7 +681,9 @@ void precond_apply(mds_precond p, const double *r, double *z, int nr) {
     if (HS.prec == 64) {
         vcycle_apply(c, HS, rm, zm, nr);
     } else {
-        cast_f64_f32(c, rm, HS.lv[0].b.as<float>(), nm * nr, lmm, nr);
+        // the input in FP32: already written by the batched FGMRES's scaling
+        // kernel when it stages into this buffer, else converted here
+        if (c.in_stage != HS.lv[0].b.as<float>()) cast_f64_f32(c, rm, HS.lv[0].b.as<float>(), nm * nr, lmm, nr);
         // the top level's last kernel writes z_m in FP64 (else x, converted)
         if (!vcycle_apply_to64(c, HS, HS.lv[0].b.as<float>(), HS.lv[0].x.as<float>(), zm, nr))
             cast_f32_f64(c, HS.lv[0].x.as<float>(), zm, nm * nr, lmm, nr);
@@ -839,6 +841,22 @@ static int solve_impl(mds_ctx ctx, mds_system sys, mds_precond prec, const doubl
             foff = {0, sys->n_f};
         }
         std::vector<KrylovResult> res;
+        // the mixed M_L's S~ V-cycle input is staged in FP32 by the scaling
+        // kernel that writes each basis vector (its work vectors sized for
+        // the widest column group first, so the buffer stays in place)
+        struct StageScope {
+            Ctx &c;
+            ~StageScope() {
+                c.in_stage = nullptr;
+                c.in_stage_rows = 0;
+            }
+        } stage_scope{*c};
+        if (o.use_precond && prec && prec->o.kind == MDS_BLOCK_LOWER && prec->h[0].prec == 32 && sys->n_m > 0) {
+            const int nr0 = nrhs >= 8 ? 8 : nrhs >= 4 ? 4 : nrhs >= 2 ? 2 : 1;
+            hierarchy_reserve(*c, prec->h[0], nr0);
+            c->in_stage = prec->h[0].lv[0].b.as<float>();
+            c->in_stage_rows = sys->n_m;
+        }
         fgmres_batched(*c, sys->view[4], BM, moff, foff, Bd, Xd, nrhs, o, res);
         for (size_t q = 0; q < res.size(); q++) {
             const KrylovResult &r = res[q];

@@ -273,6 +273,13 @@ struct Ctx {
     // instead of its own output (the top level of an FP32 V-cycle handing
     // its result to the FP64 Krylov method without a separate conversion)
     double *level_out64 = nullptr;
+    // during a batched FGMRES with the mixed M_L: every new basis vector's
+    // first in_stage_rows rows (the matrix block) are also written in FP32
+    // to in_stage (the S~ V-cycle's input) by the scaling kernel that
+    // produces it, so the preconditioner skips its input conversion; null
+    // otherwise
+    float *in_stage = nullptr;
+    int64_t in_stage_rows = 0;
     int live_ver = 0;
     // device address of the static workspace of mds_solve_noalloc on this
     // context's device, resolved by mds_create

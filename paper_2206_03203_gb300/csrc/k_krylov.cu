@@ -1104,11 +1104,14 @@ __global__ void k_bflag(int P, int nq, const int8_t *__restrict__ active, const 
 // (and 0 * their entries stays 0 in the shared kernels).
 // The chunk is scaled element by element (entry (i, c) at i * NR + c): the
 // block size is a multiple of NR, so each thread keeps one column c and one
-// factor, and a warp's loads and stores are contiguous.
+// factor, and a warp's loads and stores are contiguous.  With st, the
+// entries of rows below st_rows are also written in FP32 to st (same
+// layout): the preconditioner's FP32 input, converted as it would convert it.
 template <int NR>
 __global__ void __launch_bounds__(RED_BLOCK) k_bscale(const Chunk *__restrict__ ch, double *__restrict__ W,
                                                        const double *__restrict__ sc, int slot,
-                                                       const int8_t *__restrict__ active, const int32_t *__restrict__ lc) {
+                                                       const int8_t *__restrict__ active, const int32_t *__restrict__ lc,
+                                                       float *__restrict__ st, int64_t st_rows) {
     static_assert(RED_BLOCK % NR == 0, "block size must be a multiple of the column count");
     mds_pdl_entry();
     Chunk k = ch[lc ? lc[blockIdx.x] : blockIdx.x];  // lc: the live chunks only
@@ -1117,16 +1120,35 @@ __global__ void __launch_bounds__(RED_BLOCK) k_bscale(const Chunk *__restrict__ 
     const double f = active[p] ? sc[p * 8 + slot] : 0.0;
     double *w = W + k.b * NR;
     const int64_t m = (k.e - k.b) * NR;
+    // entries of this chunk that are also staged in FP32
+    const int64_t ms = st ? (st_rows > k.e ? m : st_rows > k.b ? (st_rows - k.b) * NR : 0) : 0;
+    float *s = st ? st + k.b * NR : nullptr;
     constexpr int B = RED_BLOCK;
     int64_t i = threadIdx.x;
     for (; i + 3 * B < m; i += 4 * B) {
         const double a0 = w[i], a1 = w[i + B], a2 = w[i + 2 * B], a3 = w[i + 3 * B];
-        w[i] = f == 0.0 ? 0.0 : a0 * f;
-        w[i + B] = f == 0.0 ? 0.0 : a1 * f;
-        w[i + 2 * B] = f == 0.0 ? 0.0 : a2 * f;
-        w[i + 3 * B] = f == 0.0 ? 0.0 : a3 * f;
+        const double v0 = f == 0.0 ? 0.0 : a0 * f, v1 = f == 0.0 ? 0.0 : a1 * f, v2 = f == 0.0 ? 0.0 : a2 * f,
+                     v3 = f == 0.0 ? 0.0 : a3 * f;
+        w[i] = v0;
+        w[i + B] = v1;
+        w[i + 2 * B] = v2;
+        w[i + 3 * B] = v3;
+        if (i + 3 * B < ms) {
+            s[i] = (float)v0;
+            s[i + B] = (float)v1;
+            s[i + 2 * B] = (float)v2;
+            s[i + 3 * B] = (float)v3;
+        } else if (i < ms) {
+            s[i] = (float)v0;
+            if (i + B < ms) s[i + B] = (float)v1;
+            if (i + 2 * B < ms) s[i + 2 * B] = (float)v2;
+        }
     }
-    for (; i < m; i += B) w[i] = f == 0.0 ? 0.0 : w[i] * f;
+    for (; i < m; i += B) {
+        const double v = f == 0.0 ? 0.0 : w[i] * f;
+        w[i] = v;
+        if (i < ms) s[i] = (float)v;
+    }
 }
 
 // per problem: beta = sqrt(nsq), g = (beta, 0, ...), sc[1] = 1/beta
@@ -1453,8 +1475,9 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
         }
         MDS_LAUNCH(c, KC_NONE, 0, k_barnoldi, grid_for(P, 128), 128, 0, P, j, m, act.as<int8_t>(), H.as<double>(),
                    h1, h2, nsq, cs, sn, g, sc);
-        MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, (unsigned)cl.nfine(nchf), RED_BLOCK, 0, CHFp, w, sc, 3,
-                   act.as<int8_t>(), cl.lfine());
+        MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR + 4.0 * c.in_stage_rows * NR, k_bscale<NR>, (unsigned)cl.nfine(nchf),
+                   RED_BLOCK, 0, CHFp, w, sc, 3,
+                   act.as<int8_t>(), cl.lfine(), c.in_stage, c.in_stage_rows);
         MDS_CUDA(cudaMemcpyAsync(c.h_pin, sc, sizeof(double) * (size_t)P * 8, cudaMemcpyDeviceToHost, c.stream));
     };
     std::vector<std::unique_ptr<Graph>> graphs(m);
@@ -1524,8 +1547,9 @@ static void fgmres_group(Ctx &c, const mds_csr &A, const BatchPrecFn &M, const s
         upload_flags(hact);
         if (K > 1) c.live = ilive;
         MDS_LAUNCH(c, KC_NONE, 0, k_bcycle_start, grid_for(P, 128), 128, 0, P, nsq, m, g, sc);
-        MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR, k_bscale<NR>, (unsigned)cl.nfine(nchf), RED_BLOCK, 0, CHFp, Vp, sc, 1,
-                   act.as<int8_t>(), cl.lfine());
+        MDS_LAUNCH(c, KC_NONE, 16.0 * N * NR + 4.0 * c.in_stage_rows * NR, k_bscale<NR>, (unsigned)cl.nfine(nchf),
+                   RED_BLOCK, 0, CHFp, Vp, sc, 1,
+                   act.as<int8_t>(), cl.lfine(), c.in_stage, c.in_stage_rows);
         for (int j = 0; j < m; j++) {
             if (j > 0) upload_flags(hact);
             run_step(j);
