@@ -1216,18 +1216,43 @@ __global__ void k_bbacksolve(int P, const int32_t *__restrict__ kdone, int m, co
     }
 }
 
-// interleave NR columns of a column-major [ncol][N] array / scatter back
+// interleave NR columns of a column-major [ncol][N] array / scatter back,
+// RED_BLOCK rows per block through shared memory, so that both the column
+// runs and the interleaved rows move in whole contiguous segments (the
+// column-major side may be page-locked host memory read or written in place)
+constexpr int IL_PAD = 1;  // shared row stride NR + 1: conflict-free column walks
 template <int NR>
-__global__ void k_to_interleaved(int64_t N, const double *__restrict__ src, int c0, double *__restrict__ dst) {
+__global__ void __launch_bounds__(RED_BLOCK) k_to_interleaved(int64_t N, const double *__restrict__ src, int c0,
+                                                              double *__restrict__ dst) {
+    __shared__ double t[RED_BLOCK * (NR + IL_PAD)];
     mds_pdl_entry();
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N * NR; e += (int64_t)gridDim.x * blockDim.x)
-        dst[e] = src[(int64_t)(c0 + e % NR) * N + e / NR];
+    const int64_t nb = (N + RED_BLOCK - 1) / RED_BLOCK;
+    for (int64_t blk = blockIdx.x; blk < nb; blk += gridDim.x) {
+        const int64_t r0 = blk * RED_BLOCK, rows = N - r0 < RED_BLOCK ? N - r0 : RED_BLOCK;
+        if ((int64_t)threadIdx.x < rows)
+#pragma unroll
+            for (int c = 0; c < NR; c++) t[threadIdx.x * (NR + IL_PAD) + c] = src[(int64_t)(c0 + c) * N + r0 + threadIdx.x];
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * NR; e += RED_BLOCK)
+            dst[r0 * NR + e] = t[(e / NR) * (NR + IL_PAD) + e % NR];
+        __syncthreads();
+    }
 }
 template <int NR>
-__global__ void k_from_interleaved(int64_t N, const double *__restrict__ src, int c0, double *__restrict__ dst) {
+__global__ void __launch_bounds__(RED_BLOCK) k_from_interleaved(int64_t N, const double *__restrict__ src, int c0,
+                                                                double *__restrict__ dst) {
+    __shared__ double t[RED_BLOCK * (NR + IL_PAD)];
     mds_pdl_entry();
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N * NR; e += (int64_t)gridDim.x * blockDim.x)
-        dst[(int64_t)(c0 + e % NR) * N + e / NR] = src[e];
+    const int64_t nb = (N + RED_BLOCK - 1) / RED_BLOCK;
+    for (int64_t blk = blockIdx.x; blk < nb; blk += gridDim.x) {
+        const int64_t r0 = blk * RED_BLOCK, rows = N - r0 < RED_BLOCK ? N - r0 : RED_BLOCK;
+        for (int e = threadIdx.x; e < rows * NR; e += RED_BLOCK) t[(e / NR) * (NR + IL_PAD) + e % NR] = src[r0 * NR + e];
+        __syncthreads();
+        if ((int64_t)threadIdx.x < rows)
+#pragma unroll
+            for (int c = 0; c < NR; c++) dst[(int64_t)(c0 + c) * N + r0 + threadIdx.x] = t[threadIdx.x * (NR + IL_PAD) + c];
+        __syncthreads();
+    }
 }
 
 template <int NR>
