@@ -10,6 +10,7 @@
 #include <memory>
 #include <mutex>
 
+#include "conv.cuh"
 #include "internal.cuh"
 #include "krylov.cuh"
 
@@ -1106,7 +1107,8 @@ __global__ void k_bflag(int P, int nq, const int8_t *__restrict__ active, const 
 // block size is a multiple of NR, so each thread keeps one column c and one
 // factor, and a warp's loads and stores are contiguous.  With st, the
 // entries of rows below st_rows are also written in FP32 to st (same
-// layout): the preconditioner's FP32 input, converted as it would convert it.
+// layout): the preconditioner's FP32 input, rounded to nearest as its own
+// conversion rounds, by integer operations (the FP64 unit does the scaling).
 template <int NR>
 __global__ void __launch_bounds__(RED_BLOCK) k_bscale(const Chunk *__restrict__ ch, double *__restrict__ W,
                                                        const double *__restrict__ sc, int slot,
@@ -1134,20 +1136,20 @@ __global__ void __launch_bounds__(RED_BLOCK) k_bscale(const Chunk *__restrict__ 
         w[i + 2 * B] = v2;
         w[i + 3 * B] = v3;
         if (i + 3 * B < ms) {
-            s[i] = (float)v0;
-            s[i + B] = (float)v1;
-            s[i + 2 * B] = (float)v2;
-            s[i + 3 * B] = (float)v3;
+            s[i] = d2f_int(v0);
+            s[i + B] = d2f_int(v1);
+            s[i + 2 * B] = d2f_int(v2);
+            s[i + 3 * B] = d2f_int(v3);
         } else if (i < ms) {
-            s[i] = (float)v0;
-            if (i + B < ms) s[i + B] = (float)v1;
-            if (i + 2 * B < ms) s[i + 2 * B] = (float)v2;
+            s[i] = d2f_int(v0);
+            if (i + B < ms) s[i + B] = d2f_int(v1);
+            if (i + 2 * B < ms) s[i + 2 * B] = d2f_int(v2);
         }
     }
     for (; i < m; i += B) {
         const double v = f == 0.0 ? 0.0 : w[i] * f;
         w[i] = v;
-        if (i < ms) s[i] = (float)v;
+        if (i < ms) s[i] = d2f_int(v);
     }
 }
 

@@ -1,6 +1,7 @@
 // Primitives: scan, fills, precision casts, CSR SpMV.
 #include <algorithm>
 
+#include "conv.cuh"
 #include "internal.cuh"
 #include "spmv.cuh"
 
@@ -214,7 +215,16 @@ __global__ void k_cast(const A *__restrict__ in, B *__restrict__ out, int64_t ro
     const int64_t r0 = live_block(lm, blockIdx.x, 1) * per, r1 = r0 + per < rows ? r0 + per : rows;
     if (!block_rows_live(lm, r0, r1)) return;
     mds_pdl_entry();
-    for (int64_t i = r0 * nr + threadIdx.x; i < r1 * nr; i += blockDim.x) out[i] = (B)in[i];
+    for (int64_t i = r0 * nr + threadIdx.x; i < r1 * nr; i += blockDim.x) {
+        // FP64 <-> FP32 by integer operations (the same results as the
+        // hardware conversions; those issue on the FP64 unit)
+        if constexpr (std::is_same<A, double>::value && std::is_same<B, float>::value)
+            out[i] = d2f_int(in[i]);
+        else if constexpr (std::is_same<A, float>::value && std::is_same<B, double>::value)
+            out[i] = f2d_int(in[i]);
+        else
+            out[i] = (B)in[i];
+    }
 }
 
 template <class A, class B> static void cast_rows(Ctx &c, const A *in, B *out, int64_t n, const LiveMap &lm, int nr) {

@@ -29,6 +29,7 @@
 #include <tuple>
 #include <type_traits>
 
+#include "conv.cuh"
 #include "internal.cuh"
 
 namespace mds {
@@ -76,14 +77,21 @@ template <class XT, int NR> __device__ __forceinline__ void stv(XT *p, int64_t j
     reinterpret_cast<Vec<XT, NR> *>(p)[j] = x;
 }
 // a level kernel's output row: in FP64 to out64 when given (the top level of
-// an FP32 V-cycle writing the Krylov method's vector; the widening is exact),
-// else in the vector type to out
+// an FP32 V-cycle writing the Krylov method's vector; the widening is exact,
+// done by integer operations so that it leaves the FP64 unit free), else in
+// the vector type to out
+template <class XT> __device__ __forceinline__ double widen64(XT v) {
+    if constexpr (std::is_same<XT, float>::value)
+        return f2d_int(v);
+    else
+        return (double)v;
+}
 template <class XT, int NR>
 __device__ __forceinline__ void st_out(XT *out, double *out64, int64_t j, const Vec<XT, NR> &x) {
     if (out64) {
         Vec<double, NR> w;
 #pragma unroll
-        for (int c = 0; c < NR; c++) w.v[c] = (double)x.v[c];
+        for (int c = 0; c < NR; c++) w.v[c] = widen64<XT>(x.v[c]);
         stv<double, NR>(out64, j, w);
     } else {
         stv<XT, NR>(out, j, x);
