@@ -947,9 +947,13 @@ def test_stored_level_form_is_fused_bit_for_bit(ctx, torch_mod, precision, nr, f
     uneven 3D instances are equal bit for bit, on CSR, SELL and stencil
     storage, with BF16, FP32 and FP64 levels."""
     torch = torch_mod
+    from paper_2206_03203_gb300 import mdsolve
     insts = [inputs.random_rects_3d(n, 22060304, k, 1 + k % 3, nrhs=nr, random_dirichlet=True)
              for k, n in enumerate([9, 12, 7, 10, 23])]
     sys_ = ctx.assemble_batch(insts)
+    with pytest.raises(mdsolve.MDSError) as e:
+        ctx.setup(sys_, precision=precision, format=fmt, level_form=3)
+    assert e.value.code == -1
     pf = ctx.setup(sys_, precision=precision, format=fmt, level_form="fused")
     ps = ctx.setup(sys_, precision=precision, format=fmt, level_form="stored")
     xf = torch.zeros(sys_.N * nr, dtype=torch.float64, device="cuda")
